@@ -1,0 +1,143 @@
+"""Pins for oracle.sampler: an independent Philox, exact inverse-CDF intervals, chi-square fits."""
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle
+
+_TRITON_SCRIPT = textwrap.dedent(
+    """
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import torch, triton, triton.language as tl
+    from triton.language.random import philox
+
+    @triton.jit
+    def kern(ctr_ptr, out_ptr, seed, N: tl.constexpr):
+        i = tl.arange(0, N)
+        c0 = tl.load(ctr_ptr + 4 * i + 0)
+        c1 = tl.load(ctr_ptr + 4 * i + 1)
+        c2 = tl.load(ctr_ptr + 4 * i + 2)
+        c3 = tl.load(ctr_ptr + 4 * i + 3)
+        a, b, c, d = philox(seed, c0, c1, c2, c3, 10)
+        tl.store(out_ptr + 4 * i + 0, a)
+        tl.store(out_ptr + 4 * i + 1, b)
+        tl.store(out_ptr + 4 * i + 2, c)
+        tl.store(out_ptr + 4 * i + 3, d)
+
+    data = json.loads(sys.stdin.read())
+    ctr = torch.tensor(data["ctr"], dtype=torch.int64).to(torch.uint32).view(torch.int32)
+    out = torch.zeros_like(ctr)
+    kern[(1,)](ctr, out, data["seed"], N=len(data["ctr"]) // 4)
+    print(json.dumps([int(v) & 0xFFFFFFFF for v in out.tolist()]))
+    """
+)
+
+
+def test_philox_against_independent_implementation():
+    """Triton's Philox4x32-10 (run by its CPU interpreter) is a separate implementation."""
+    pytest.importorskip("triton")
+    import json
+    rng = np.random.default_rng(11)
+    n = 16
+    ctr = rng.integers(0, 2 ** 32, size=4 * n, dtype=np.uint64)
+    ctr[:4] = 0
+    ctr[4:8] = 0xFFFFFFFF
+    seed = int(rng.integers(0, 2 ** 63))
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT],
+                          input=json.dumps({"ctr": [int(v) for v in ctr], "seed": seed}),
+                          capture_output=True, text=True, timeout=600)
+    if proc.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + proc.stderr[-300:])
+    want = np.array(json.loads(proc.stdout.strip().splitlines()[-1]), dtype=np.uint64).reshape(n, 4)
+    c = ctr.reshape(n, 4)
+    got = oracle.philox4x32_10(c[:, 0], c[:, 1], c[:, 2], c[:, 3], seed & 0xFFFFFFFF, seed >> 32)
+    np.testing.assert_array_equal(np.stack(got, axis=1), want)
+
+
+def test_philox_zero_block_and_bijection_sample():
+    # different counters give different outputs (a bijection per key)
+    t = np.arange(4096, dtype=np.uint64)
+    x0, x1, x2, x3 = oracle.philox4x32_10(t, 0, 0, 0, 5, 7)
+    words = set(zip(x0.tolist(), x1.tolist(), x2.tolist(), x3.tolist()))
+    assert len(words) == 4096
+
+
+def test_inverse_cdf_exact_intervals():
+    """Draw j is chosen exactly for r in [ceil(S_{j-1} 2^64 / T), ceil(S_j 2^64 / T))."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        W = rng.integers(0, 50, size=int(rng.integers(1, 12))).astype(np.uint64)
+        if W.sum() == 0:
+            W[0] = 1
+        S = np.cumsum(W, dtype=np.uint64)
+        T = int(S[-1])
+        prev = 0
+        for j in range(len(W)):
+            lo = -(-prev * 2 ** 64 // T)
+            hi = -(-int(S[j]) * 2 ** 64 // T)  # exclusive
+            if hi > lo:
+                r = np.array([lo, hi - 1], dtype=np.uint64)
+                np.testing.assert_array_equal(oracle.inverse_cdf(S, r), [j, j])
+                # the count of r values mapping to j is within one of W_j 2^64 / T
+                assert abs((hi - lo) - int(W[j]) * 2 ** 64 / T) <= 1.0
+            else:
+                assert W[j] == 0
+            prev = int(S[j])
+
+
+def test_fixed_point_weights_exact():
+    p = np.array([0.0, 1.0, 0.5, 2.0 ** -62, 2.0 ** -63, 1.0 / 3.0])
+    W = oracle.fixed_point_weights(p)
+    from fractions import Fraction
+    third = int(Fraction(1.0 / 3.0) * 2 ** 62)  # floor of the exact value of the double
+    assert [int(v) for v in W] == [0, 2 ** 62, 2 ** 61, 1, 0, third]
+    with pytest.raises(ValueError):
+        oracle.fixed_point_weights(np.array([0.5, -0.1]))
+    with pytest.raises(ValueError):
+        oracle.fixed_point_weights(np.array([np.nan]))
+
+
+def test_chi_square_goodness_of_fit():
+    from scipy import stats
+    rng = np.random.default_rng(4)
+    p = rng.random(37) ** 2
+    p[5] = 0.0
+    p /= p.sum()
+    draws = oracle.sample_segments(p, [0, len(p)], [200_000], seed=12345, sid=0)
+    assert not np.any(draws == 5)
+    obs = np.bincount(draws, minlength=len(p))
+    keep = p > 0
+    chi2, pval = stats.chisquare(obs[keep], 200_000 * p[keep])
+    assert pval > 1e-4
+
+
+def test_segments_number_draws_consecutively():
+    # Alg. 2 enumerates draws segment by segment; segment k's draws are t = D_k .. D_k + c_k - 1
+    off = np.array([0, 4, 10, 13])
+    p = np.concatenate([np.full(4, 0.25), np.full(6, 1 / 6), np.full(3, 1 / 3)])
+    ck = np.array([2, 3, 4])
+    idx = oracle.sample_segments(p, off, ck, seed=9, sid=3)
+    r = oracle.uniform64(9, 3, np.arange(9, dtype=np.uint64))
+    for k, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        d0 = int(ck[:k].sum())
+        S = np.cumsum(oracle.fixed_point_weights(p[a:b]), dtype=np.uint64)
+        np.testing.assert_array_equal(idx[d0:d0 + ck[k]], a + oracle.inverse_cdf(S, r[d0:d0 + ck[k]]))
+        assert np.all((idx[d0:d0 + ck[k]] >= a) & (idx[d0:d0 + ck[k]] < b))
+
+
+def test_alg2_scales_and_streams():
+    off = np.array([0, 5, 9])
+    p = np.array([0.1, 0.2, 0.3, 0.4, 0.0, 0.25, 0.25, 0.25, 0.25])
+    ck = np.array([3, 2])
+    idx, scale = oracle.sample_alg2(p, off, ck, seed=1, sid=oracle.stream_id(0, oracle.PURPOSE_MAIN))
+    np.testing.assert_allclose(scale * np.repeat(ck, ck) * p[idx], 1.0, rtol=1e-15)
+    idx2, _ = oracle.sample_alg2(p, off, ck, seed=1, sid=oracle.stream_id(0, oracle.PURPOSE_PILOT))
+    idx3, _ = oracle.sample_alg2(p, off, ck, seed=1, sid=oracle.stream_id(0, oracle.PURPOSE_MAIN))
+    np.testing.assert_array_equal(idx, idx3)
+    with pytest.raises(ValueError):
+        oracle.sample_segments(np.zeros(3), [0, 3], [1], seed=0, sid=0)
