@@ -1,0 +1,225 @@
+/*
+ * bmm.h -- C ABI of the GB300 (sm_103a) randomized block matrix multiplication library.
+ *
+ * Method: Niu & Li, "Optimal Sampling Algorithms for Block Matrix Multiplication".
+ * MN (M m x n, N n x p) is approximated by sampling outer products M^{k(i)} N_{k(i)}
+ * inside each of K contraction blocks (Alg. 2, eq. 3.3), or whole blocks (the
+ * baselines of eq. 1.2 and eq. 1.4).  A product runs as
+ *
+ *     bmm_probs -> bmm_blocksizes -> bmm_sample -> bmm_apply   (+ bmm_backward)
+ *
+ * Conventions shared by every call
+ *   - Every pointer inside the descriptors and every array argument is DEVICE memory
+ *     owned by the caller, unless marked "host".  The library allocates nothing and
+ *     keeps no state between calls; all work is enqueued on the caller's stream and
+ *     the calls return without synchronising (except bmm_read_device_status).
+ *   - Argument, shape and feasibility errors are returned before anything is launched.
+ *     Conditions only the GPU can see (non-finite data, bad offsets, a probability
+ *     segment with zero mass, a bounded wait that expired) are recorded in a sticky
+ *     status word at the start of the workspace; read it with bmm_read_device_status.
+ *     Nothing traps.
+ *   - Workspace: ws must be 256-byte aligned and hold bmm_workspace_size(...) bytes.
+ *     Its first 256 bytes are the status block; bmm_clear_device_status zeroes it.
+ *     The rest is scratch that no call preserves.
+ *   - Calls that share a workspace must be ordered (same stream or events).
+ */
+#ifndef BMM_H_
+#define BMM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* bmm_stream_t;
+
+typedef enum {
+    BMM_OK = 0,
+    BMM_ERR_ARG = 1,         /* null pointer, unknown enum, bad probability vector */
+    BMM_ERR_SHAPE = 2,       /* inconsistent dimensions, leading dimensions or block offsets */
+    BMM_ERR_DTYPE = 3,       /* element type not supported by this call */
+    BMM_ERR_INFEASIBLE = 4,  /* budget outside what Alg. 2 allows (c < K or c > n) */
+    BMM_ERR_NONFINITE = 5,   /* NaN or Inf met in the data (device-detected) */
+    BMM_ERR_WORKSPACE = 6,   /* workspace too small or misaligned */
+    BMM_ERR_CUDA = 7,        /* a CUDA runtime call failed */
+    BMM_ERR_TIMEOUT = 8,     /* a bounded device-side wait expired; the kernel returned early */
+    BMM_ERR_UNSUPPORTED = 9  /* valid request this build or device does not support */
+} bmm_status;
+
+/* Element types. */
+enum { BMM_F64 = 0, BMM_F32 = 1, BMM_BF16 = 2 };
+/* Storage orders. ROW: element (r, c) at data[r * ld + c]; COL: at data[c * ld + r]. */
+enum { BMM_ROW_MAJOR = 0, BMM_COL_MAJOR = 1 };
+
+/* Probabilities (Sec. 1 and Table 2). */
+enum {
+    BMM_P_COL_OPT = 0,      /* eq. 3.8: p_{k_i} = ||M^{k(i)}|| ||N_{k(i)}|| / a_k, per column, sums to 1 in each block */
+    BMM_P_COL_UNIFORM = 1,  /* Table 2 (UU, ONU pilot): p_{k_i} = 1/n_k */
+    BMM_P_BLK_PRODNORM = 2, /* eq. 1.2: p_k = ||M^k N_k||_F / sum_j ||M^j N_j||_F, per block */
+    BMM_P_BLK_NORMPROD = 3  /* eq. 1.4 (SSM): p_k = ||M^k||_F ||N_k||_F / sum_j (...), per block */
+};
+
+/* Block sizes (Thm 2.2, Sec. 3). */
+enum {
+    BMM_CK_OPT = 0,   /* eq. 3.9: c_k proportional to (a_k^2 - ||M^k N_k||_F^2)^{1/2}; needs st->f */
+    BMM_CK_HAT = 1,   /* eq. 4.2: c_k proportional to a_k */
+    BMM_CK_TILDE = 2, /* eq. 4.7 / Alg. 3: c_k proportional to |a_k^2 - ||C^{0k} D_{0k}||_F^2|^{1/2} */
+    BMM_CK_EQUAL = 3  /* Table 2 (UU): c_k = c/K */
+};
+
+/* How ||M^k N_k||_F^2 is computed by bmm_probs. */
+enum {
+    BMM_F_NONE = 0,  /* not computed (st->f untouched) */
+    BMM_F_EXACT = 1  /* trace identity <M^kT M^k, N_k N_kT>_F with FP64-accurate sums on CUDA cores */
+};
+/* Flag or-ed into bmm_probs' fmode: st already holds this M, N's statistics (and f when
+ * needed); only p is computed.  COL_UNIFORM never reads st, M or N. */
+enum { BMM_REUSE_STATS = 0x100 };
+
+/* Sampling unit. */
+enum {
+    BMM_UNIT_COLUMN = 0, /* Alg. 2: idx are column indices of M (row indices of N) in [0, n) */
+    BMM_UNIT_BLOCK = 1   /* block sampling: idx are block indices in [0, K) */
+};
+
+/* Arithmetic of the sampled product. */
+enum {
+    BMM_GEMM_F64 = 0,        /* FP64 operands and accumulation on CUDA cores; out is FP64 */
+    BMM_GEMM_BF16 = 1,       /* BF16 operands on tcgen05 tensor cores, FP32 accumulation; out is FP32 */
+    BMM_GEMM_SPLIT_BF16 = 2  /* x = hi + lo (both BF16); hi*hi + hi*lo + lo*hi on tcgen05, FP32 accumulation */
+};
+
+/* Purposes folded into a stream id: stream_id = (replicate << 8) | purpose. */
+enum { BMM_PURPOSE_MAIN = 0, BMM_PURPOSE_PILOT = 1 };
+
+/* A dense matrix in device memory. */
+typedef struct {
+    const void* data;  /* device pointer, aligned to its element size */
+    int64_t rows;      /* logical rows */
+    int64_t cols;      /* logical columns */
+    int64_t ld;        /* leading dimension in elements (>= cols for ROW, >= rows for COL) */
+    int32_t dtype;     /* BMM_F64 / BMM_F32 / BMM_BF16 */
+    int32_t layout;    /* BMM_ROW_MAJOR / BMM_COL_MAJOR */
+} bmm_mat;
+
+/* The K contraction blocks of eq. 2.3: block k holds indices [offsets[k], offsets[k+1]). */
+typedef struct {
+    int64_t K;               /* number of blocks, >= 1 */
+    int64_t n;               /* contraction length, = offsets[K] */
+    int64_t max_nk;          /* host: largest block size (sizes workspace for block sampling) */
+    const int64_t* offsets;  /* device [K+1]: offsets[0] = 0, strictly increasing, offsets[K] = n */
+} bmm_blocks;
+
+/* Statistics of Sec. 2-3, all device FP64 arrays owned by the caller. */
+typedef struct {
+    double* x;   /* [n] ||M^{(i)}||_2^2 */
+    double* y;   /* [n] ||N_{(i)}||_2^2 */
+    double* a;   /* [K] a_k = sum_{i in k} ||M^{k(i)}|| ||N_{k(i)}||   (eq. 3.8 denominator) */
+    double* s;   /* [K] s_k = sum_{i in k} ||M^{k(i)}||^2 ||N_{k(i)}||^2 */
+    double* mf;  /* [K] ||M^k||_F^2 */
+    double* nf;  /* [K] ||N_k||_F^2 */
+    double* f;   /* [K] ||M^k N_k||_F^2 (eq. 1.2, eq. 3.9); may be NULL when not requested */
+} bmm_stats;
+
+/*
+ * Bytes of workspace that any call below needs for this problem.  unit is the sampling
+ * unit that bmm_apply / bmm_backward will see; max_draws the largest draw count (c, and
+ * the Alg. 3 pilot's total draws) passed to any call; gemm_mode the largest mode used
+ * (SPLIT_BF16 needs the most).  Returns 0 on invalid input.  Host-only, no CUDA calls.
+ */
+size_t bmm_workspace_size(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                          int64_t max_draws, int32_t gemm_mode);
+
+/*
+ * bmm_probs -- statistics and sampling probabilities.
+ * Sec. 2-3: x_i, y_i, a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 in one read of M and N,
+ * optionally f_k = ||M^k N_k||_F^2 (fmode), then p by pkind (eq. 3.8, Table 2,
+ * eq. 1.2, eq. 1.4).  M is m x n, N is n x p, either storage order, same dtype.
+ *   p_out: [n] for the column kinds, [K] for the block kinds.  May be NULL.
+ *   st:    all pointers but f required; f required when fmode != BMM_F_NONE or
+ *          pkind == BMM_P_BLK_PRODNORM.  With BMM_REUSE_STATS the pass over M and N is
+ *          skipped and st is read, not written.
+ * A block with a_k = 0 gets uniform column probabilities; all-zero block weights give 1/K.
+ */
+bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
+                     int32_t pkind, int32_t fmode, double* p_out, const bmm_stats* st,
+                     void* ws, size_t ws_bytes, bmm_stream_t stream);
+
+/*
+ * bmm_blocksizes -- integer block sizes c_k for Alg. 2 (Thm 2.2 eq. 3.9, eq. 4.2,
+ * eq. 4.7 with Alg. 3 step 1, Table 2 c/K).  c is the total number of outer products
+ * (the paper's c); K <= c <= n is required (each block gets 1 <= c_k <= n_k).
+ * Weights g_k (all zero falls back to a_k, then to n_k) are turned into integers by the
+ * largest FP64 lam with sum_k clamp(floor(lam g_k), 1, n_k) <= c, the remainder going one
+ * each, in increasing k, to the blocks that grow at the next representable lam.
+ *   st:          a (and f for BMM_CK_OPT) used; may be NULL for BMM_CK_EQUAL.
+ *   pilot_idx, pilot_scale, pilot_per_block: BMM_CK_TILDE only -- the Alg. 3 step-1
+ *                sample (draws of block k at positions [k*per_block, (k+1)*per_block),
+ *                scale 1/(c0' p0) each), from which ||C^{0k} D_{0k}||_F^2 is computed.
+ *   ck_out:      device int64 [K].   g_out, fhat_out: optional device FP64 [K].
+ */
+bmm_status bmm_blocksizes(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
+                          const bmm_stats* st, int32_t ckind, int64_t c,
+                          const int32_t* pilot_idx, const double* pilot_scale, int64_t pilot_per_block,
+                          int64_t* ck_out, double* g_out, double* fhat_out,
+                          void* ws, size_t ws_bytes, bmm_stream_t stream);
+
+/*
+ * bmm_sample -- i.i.d. draws with replacement (Alg. 1 step 1(a), Alg. 2 step 1).
+ * Philox4x32-10 with key (seed_lo, seed_hi) and counter (t_lo, t_hi, sid_lo, sid_hi) for
+ * global draw number t gives r = (x1 << 32) | x0; W_j = floor(p_j 2^62); the draw is the
+ * smallest j of its segment with prefix S_j > floor(r T / 2^64).
+ *   BMM_UNIT_COLUMN: p is [n]; block k gets ck[k] draws (device int64 [K], sum = c),
+ *                    numbered consecutively block after block; scale = 1/(c_k p_i) (eq. 3.2).
+ *   BMM_UNIT_BLOCK:  p is [K]; c draws over the blocks; scale = 1/(c p_k); ck ignored.
+ *   idx_out: device int32 [c] global indices; scale_out: device FP64 [c].
+ * p must be finite in [0, 1] with non-zero mass in every segment (device-checked).
+ */
+bmm_status bmm_sample(const double* p, int32_t unit, const bmm_blocks* B, const int64_t* ck,
+                      int64_t c, uint64_t seed, uint64_t stream_id,
+                      int32_t* idx_out, double* scale_out,
+                      void* ws, size_t ws_bytes, bmm_stream_t stream);
+
+/*
+ * bmm_apply -- the sampled product CD = sum_t scale_t M^{(i_t)} N_{(i_t)} (eq. 3.3,
+ * Alg. 2 step 4), or sum_t scale_t M^{k_t} N_{k_t} for BMM_UNIT_BLOCK.
+ * The chosen columns/rows are gathered, multiplied by sqrt(scale_t) (Alg. 1 step 1(b)),
+ * converted to the mode's operand type and multiplied on the tensor cores.
+ *   out: m x p, row-major (layout must be ROW), FP32 for the BF16 modes, FP64 for F64.
+ *   accumulate: 0 -> out = CD, 1 -> out += CD.   count = number of draws (>= 0).
+ */
+bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                     const int32_t* idx, const double* scale, int64_t count, int32_t gemm_mode,
+                     const bmm_mat* out, int32_t accumulate,
+                     void* ws, size_t ws_bytes, bmm_stream_t stream);
+
+/*
+ * bmm_backward -- adjoint of bmm_apply for a loss l(CD) with G = dl/d(CD) (m x p).
+ * The sample is not stored: it is redrawn from (p, ck, c, seed, stream_id) exactly as
+ * bmm_sample draws it, and p is held constant (stop-gradient).  For every distinct index i
+ * drawn with total weight w_i = sum_{t: i_t = i} scale_t:
+ *     dM^{(i)} += w_i G N_{(i)}^T,   dN_{(i)} += w_i M^{(i)T} G
+ * (whole blocks for BMM_UNIT_BLOCK).  Columns/rows never drawn are left unchanged
+ * (accumulate = 1) or set to zero (accumulate = 0).  Either of dM, dN may be NULL.
+ *   G, dM, dN: row-major, dtype FP32 for the BF16 modes, FP64 for BMM_GEMM_F64.
+ */
+bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
+                        int32_t unit, const double* p, const int64_t* ck, int64_t c,
+                        uint64_t seed, uint64_t stream_id, int32_t gemm_mode,
+                        const bmm_mat* dM, const bmm_mat* dN, int32_t accumulate,
+                        void* ws, size_t ws_bytes, bmm_stream_t stream);
+
+/* Synchronises the stream, then returns the first device-recorded error (BMM_OK if none). */
+bmm_status bmm_read_device_status(const void* ws, bmm_stream_t stream);
+/* Enqueues a reset of the device status word. */
+bmm_status bmm_clear_device_status(void* ws, bmm_stream_t stream);
+/* Static, NUL-terminated description of a status code. */
+const char* bmm_status_string(bmm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BMM_H_ */

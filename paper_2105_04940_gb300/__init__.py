@@ -1,0 +1,25 @@
+"""GB300 (sm_103a) randomized block matrix multiplication (Niu & Li, "Optimal Sampling
+Algorithms for Block Matrix Multiplication").
+
+The compute lives in libbmm.so (C ABI: include/bmm.h); this package is its thin Python
+binding (``_abi``, the same entry-point names) plus the call sequence of a product and a
+torch.autograd.Function (``pipeline``).  There is no CPU path: without a CUDA device or
+without the built library every call raises.
+"""
+from . import _abi
+from ._abi import (BmmError, bmm_apply, bmm_backward, bmm_blocksizes, bmm_clear_device_status, bmm_probs,
+                   bmm_read_device_status, bmm_sample, bmm_workspace_size)
+from .pipeline import (METHODS, MODES, Problem, SampledMatmul, check_status, equal_budget, prepare, run,
+                       sampled_matmul, stream_id)
+
+__all__ = [
+    "BmmError", "bmm_apply", "bmm_backward", "bmm_blocksizes", "bmm_clear_device_status", "bmm_probs",
+    "bmm_read_device_status", "bmm_sample", "bmm_workspace_size", "METHODS", "MODES", "Problem",
+    "SampledMatmul", "check_status", "equal_budget", "prepare", "run", "sampled_matmul", "stream_id",
+]
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    """Compile the CUDA library in-tree (see build.py)."""
+    from .build import build as _build
+    return _build(verbose=verbose, force=force)

@@ -1,0 +1,193 @@
+"""ctypes binding of include/bmm.h -- argument marshalling only.
+
+Every function below calls the C entry point of the same name in libbmm.so and raises
+BmmError on a non-OK status.  Tensors are torch CUDA tensors; their device pointers,
+shapes and strides are passed through, nothing is computed here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbmm.so")
+
+# enums of include/bmm.h
+OK, ERR_ARG, ERR_SHAPE, ERR_DTYPE, ERR_INFEASIBLE, ERR_NONFINITE, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(10)
+F64, F32, BF16 = 0, 1, 2
+ROW_MAJOR, COL_MAJOR = 0, 1
+P_COL_OPT, P_COL_UNIFORM, P_BLK_PRODNORM, P_BLK_NORMPROD = 0, 1, 2, 3
+CK_OPT, CK_HAT, CK_TILDE, CK_EQUAL = 0, 1, 2, 3
+F_NONE, F_EXACT = 0, 1
+REUSE_STATS = 0x100
+UNIT_COLUMN, UNIT_BLOCK = 0, 1
+GEMM_F64, GEMM_BF16, GEMM_SPLIT_BF16 = 0, 1, 2
+PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
+
+EXPORTED = (
+    "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
+    "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string",
+)
+
+
+class BmmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+
+
+class Mat(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32)]
+
+
+class Blocks(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("n", ctypes.c_int64), ("max_nk", ctypes.c_int64),
+                ("offsets", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("x", "y", "a", "s", "mf", "nf", "f")]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbmm.so and declare the signatures; fails loudly if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2105_04940_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i32, i64, u64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    lib.bmm_workspace_size.argtypes = [P(Mat), P(Mat), P(Blocks), i32, i64, i32]
+    lib.bmm_workspace_size.restype = sz
+    lib.bmm_probs.argtypes = [P(Mat), P(Mat), P(Blocks), i32, i32, vp, P(Stats), vp, sz, vp]
+    lib.bmm_blocksizes.argtypes = [P(Mat), P(Mat), P(Blocks), P(Stats), i32, i64, vp, vp, i64, vp, vp, vp, vp, sz, vp]
+    lib.bmm_sample.argtypes = [vp, i32, P(Blocks), vp, i64, u64, u64, vp, vp, vp, sz, vp]
+    lib.bmm_apply.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, i32, P(Mat), i32, vp, sz, vp]
+    lib.bmm_backward.argtypes = [P(Mat), P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, u64, u64, i32,
+                                 P(Mat), P(Mat), i32, vp, sz, vp]
+    lib.bmm_read_device_status.argtypes = [vp, vp]
+    lib.bmm_clear_device_status.argtypes = [vp, vp]
+    lib.bmm_status_string.argtypes = [i32]
+    lib.bmm_status_string.restype = ctypes.c_char_p
+    for name in ("bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
+                 "bmm_read_device_status", "bmm_clear_device_status"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().bmm_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise BmmError(code, where)
+
+
+# ---------------------------------------------------------------- marshalling helpers
+_DT = None
+
+
+def _dtypes():
+    global _DT
+    if _DT is None:
+        import torch
+        _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+    return _DT
+
+
+def mat(t) -> Mat:
+    """bmm_mat of a 2-D tensor: row-major if its last stride is 1, column-major if its first is."""
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    dt = _dtypes().get(t.dtype)
+    if dt is None:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    r, c = t.shape
+    s0, s1 = t.stride()
+    if s1 == 1 or c <= 1:
+        return Mat(t.data_ptr(), r, c, max(s0, c, 1), dt, ROW_MAJOR)
+    if s0 == 1 or r <= 1:
+        return Mat(t.data_ptr(), r, c, max(s1, r, 1), dt, COL_MAJOR)
+    raise ValueError("tensor must have a unit stride in one dimension")
+
+
+def blocks(offsets_dev, n: int, max_nk: int) -> Blocks:
+    return Blocks(len(offsets_dev) - 1, n, max_nk, offsets_dev.data_ptr())
+
+
+def stats(d: dict) -> Stats:
+    return Stats(*[(d[k].data_ptr() if d.get(k) is not None else None) for k in ("x", "y", "a", "s", "mf", "nf", "f")])
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- the entry points
+def bmm_workspace_size(M, N, B: Blocks, unit: int, max_draws: int, gemm_mode: int) -> int:
+    return int(load().bmm_workspace_size(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B),
+                                         unit, max_draws, gemm_mode))
+
+
+def bmm_probs(M, N, B: Blocks, pkind: int, fmode: int, p_out, st: dict, ws, stream=None):
+    Mm = ctypes.byref(mat(M)) if M is not None else None
+    Nm = ctypes.byref(mat(N)) if N is not None else None
+    sp = ctypes.byref(stats(st)) if st is not None else None
+    _check(load().bmm_probs(Mm, Nm, ctypes.byref(B), pkind, fmode, _ptr(p_out), sp, ws.data_ptr(), ws.numel(),
+                            _stream(stream)), "bmm_probs")
+
+
+def bmm_blocksizes(M, N, B: Blocks, st: dict, ckind: int, c: int, pilot_idx, pilot_scale, pilot_per_block: int,
+                   ck_out, g_out, fhat_out, ws, stream=None):
+    Mm = ctypes.byref(mat(M)) if M is not None else None
+    Nm = ctypes.byref(mat(N)) if N is not None else None
+    sp = ctypes.byref(stats(st)) if st is not None else None
+    _check(load().bmm_blocksizes(Mm, Nm, ctypes.byref(B), sp, ckind, c, _ptr(pilot_idx), _ptr(pilot_scale),
+                                 pilot_per_block, _ptr(ck_out), _ptr(g_out), _ptr(fhat_out), ws.data_ptr(),
+                                 ws.numel(), _stream(stream)), "bmm_blocksizes")
+
+
+def bmm_sample(p, unit: int, B: Blocks, ck, c: int, seed: int, stream_id: int, idx_out, scale_out, ws, stream=None):
+    _check(load().bmm_sample(_ptr(p), unit, ctypes.byref(B), _ptr(ck), c, seed & 0xFFFFFFFFFFFFFFFF,
+                             stream_id & 0xFFFFFFFFFFFFFFFF, _ptr(idx_out), _ptr(scale_out), ws.data_ptr(),
+                             ws.numel(), _stream(stream)), "bmm_sample")
+
+
+def bmm_apply(M, N, B: Blocks, unit: int, idx, scale, count: int, gemm_mode: int, out, accumulate: bool, ws,
+              stream=None):
+    _check(load().bmm_apply(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), unit, _ptr(idx),
+                            _ptr(scale), count, gemm_mode, ctypes.byref(mat(out)), int(bool(accumulate)),
+                            ws.data_ptr(), ws.numel(), _stream(stream)), "bmm_apply")
+
+
+def bmm_backward(G, M, N, B: Blocks, unit: int, p, ck, c: int, seed: int, stream_id: int, gemm_mode: int, dM, dN,
+                 accumulate: bool, ws, stream=None):
+    dMm = ctypes.byref(mat(dM)) if dM is not None else None
+    dNm = ctypes.byref(mat(dN)) if dN is not None else None
+    _check(load().bmm_backward(ctypes.byref(mat(G)), ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B),
+                               unit, _ptr(p), _ptr(ck), c, seed & 0xFFFFFFFFFFFFFFFF, stream_id & 0xFFFFFFFFFFFFFFFF,
+                               gemm_mode, dMm, dNm, int(bool(accumulate)), ws.data_ptr(), ws.numel(),
+                               _stream(stream)), "bmm_backward")
+
+
+def bmm_read_device_status(ws, stream=None) -> int:
+    return int(load().bmm_read_device_status(ws.data_ptr(), _stream(stream)))
+
+
+def bmm_clear_device_status(ws, stream=None):
+    _check(load().bmm_clear_device_status(ws.data_ptr(), _stream(stream)), "bmm_clear_device_status")

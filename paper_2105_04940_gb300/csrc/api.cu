@@ -1,0 +1,543 @@
+// api.cu -- the exported C ABI (include/bmm.h): argument checks, workspace carving, launch order.
+#include <string.h>
+
+#include "internal.h"
+
+#define BMM_API extern "C" __attribute__((visibility("default")))
+
+namespace bmm {
+
+VecSet vecset_of_M(const bmm_mat* M) {
+    VecSet v;
+    v.data = M->data;
+    v.len = M->rows;
+    v.count = M->cols;
+    v.ld = M->ld;
+    v.dtype = M->dtype;
+    v.mode = (M->layout == BMM_ROW_MAJOR) ? VEC_STRIDED : VEC_CONTIG;
+    return v;
+}
+
+VecSet vecset_of_N(const bmm_mat* N) {
+    VecSet v;
+    v.data = N->data;
+    v.len = N->cols;
+    v.count = N->rows;
+    v.ld = N->ld;
+    v.dtype = N->dtype;
+    v.mode = (N->layout == BMM_ROW_MAJOR) ? VEC_CONTIG : VEC_STRIDED;
+    return v;
+}
+
+namespace {
+
+constexpr size_t kStatusBytes = 256;
+
+// bump allocator over the workspace scratch; with base == nullptr it only counts
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T> T* take(int64_t n) {
+        const size_t b = (size_t)round_up(imax(n, 1) * (int64_t)sizeof(T), 256);
+        T* r = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += b;
+        return r;
+    }
+};
+
+size_t esize(int dtype) { return dtype == BMM_F64 ? 8 : (dtype == BMM_F32 ? 4 : 2); }
+
+bmm_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return BMM_OK;
+    if (e == cudaErrorInvalidValue) return BMM_ERR_UNSUPPORTED;
+    return BMM_ERR_CUDA;
+}
+
+#define BMM_TRY(expr)                                   \
+    do {                                                \
+        const bmm_status _s = from_cuda(expr);          \
+        if (_s != BMM_OK) return _s;                    \
+    } while (0)
+
+bmm_status check_mat(const bmm_mat* A) {
+    if (A == nullptr || A->data == nullptr) return BMM_ERR_ARG;
+    if (A->dtype != BMM_F64 && A->dtype != BMM_F32 && A->dtype != BMM_BF16) return BMM_ERR_DTYPE;
+    if (A->layout != BMM_ROW_MAJOR && A->layout != BMM_COL_MAJOR) return BMM_ERR_ARG;
+    if (A->rows < 0 || A->cols < 0) return BMM_ERR_SHAPE;
+    const int64_t inner = (A->layout == BMM_ROW_MAJOR) ? A->cols : A->rows;
+    if (A->ld < imax(inner, 1)) return BMM_ERR_SHAPE;
+    if (reinterpret_cast<uintptr_t>(A->data) % esize(A->dtype)) return BMM_ERR_ARG;
+    return BMM_OK;
+}
+
+bmm_status check_blocks(const bmm_blocks* B) {
+    if (B == nullptr || B->offsets == nullptr) return BMM_ERR_ARG;
+    if (B->K < 1 || B->n < B->K || B->max_nk < 1 || B->max_nk > B->n) return BMM_ERR_SHAPE;
+    if (B->n > 0x7fffffffLL) return BMM_ERR_UNSUPPORTED;  // indices are int32
+    return BMM_OK;
+}
+
+bmm_status check_problem(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B) {
+    bmm_status s;
+    if ((s = check_mat(M)) != BMM_OK) return s;
+    if ((s = check_mat(N)) != BMM_OK) return s;
+    if ((s = check_blocks(B)) != BMM_OK) return s;
+    if (M->cols != N->rows || M->cols != B->n) return BMM_ERR_SHAPE;
+    if (M->dtype != N->dtype) return BMM_ERR_DTYPE;
+    return BMM_OK;
+}
+
+bmm_status check_ws(const void* ws, size_t ws_bytes, size_t need) {
+    if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255)) return BMM_ERR_WORKSPACE;
+    if (ws_bytes < need + kStatusBytes) return BMM_ERR_WORKSPACE;
+    return BMM_OK;
+}
+
+DevStatus* status_of(void* ws) { return static_cast<DevStatus*>(ws); }
+
+// ------------------------------------------------------------------ per-call workspace plans
+struct ProbsPlan {
+    double* partial;
+    int64_t partial_cap;
+    double* gpart;
+    int64_t gpart_cap;
+};
+void plan_probs(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, bool need_f, ProbsPlan* p) {
+    p->partial_cap = imax(vec_sqnorms_partial_elems(vecset_of_M(M)), vec_sqnorms_partial_elems(vecset_of_N(N)));
+    p->partial = cv.take<double>(p->partial_cap);
+    p->gpart_cap = need_f ? gram_frob_partial_elems(B->K, B->max_nk) : 0;
+    p->gpart = need_f ? cv.take<double>(p->gpart_cap) : nullptr;
+}
+
+struct SizesPlan {
+    double* g;
+    double* fhat;
+    double* gpart;
+    int64_t gpart_cap;
+};
+void plan_sizes(Carver& cv, const bmm_blocks* B, int ckind, int64_t per, double* g_out, double* fhat_out,
+                SizesPlan* p) {
+    p->g = g_out ? g_out : cv.take<double>(B->K);
+    p->fhat = nullptr;
+    p->gpart = nullptr;
+    p->gpart_cap = 0;
+    if (ckind == BMM_CK_TILDE) {
+        p->fhat = fhat_out ? fhat_out : cv.take<double>(B->K);
+        p->gpart_cap = gram_frob_partial_elems(B->K, per);
+        p->gpart = cv.take<double>(p->gpart_cap);
+    }
+}
+
+void* plan_sample(Carver& cv, int unit, const bmm_blocks* B) {
+    const int64_t len = unit == BMM_UNIT_COLUMN ? B->n : B->K;
+    return cv.take<char>(sampler_scratch_bytes(len, B->K));
+}
+
+struct ApplyPlan {
+    int32_t* col;
+    double* w;
+    int64_t* prefix;
+    int64_t* ext;
+    void* A;
+    void* Bop;
+    int64_t lmax, kseg_max, ktot;
+};
+void plan_apply(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int unit, int64_t count,
+                int mode, ApplyPlan* p) {
+    p->lmax = unit == BMM_UNIT_COLUMN ? count : count * B->max_nk;
+    p->col = nullptr;
+    p->w = nullptr;
+    p->prefix = nullptr;
+    if (unit == BMM_UNIT_BLOCK) {
+        p->col = cv.take<int32_t>(p->lmax);
+        p->w = cv.take<double>(p->lmax);
+        p->prefix = cv.take<int64_t>(count);
+    }
+    p->ext = cv.take<int64_t>(1);
+    p->kseg_max = round_up(imax(p->lmax, 1), 64);
+    p->ktot = p->kseg_max * (mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1);
+    const size_t es = mode == BMM_GEMM_F64 ? 8 : 2;
+    p->A = cv.take<char>(M->rows * p->ktot * (int64_t)es);
+    p->Bop = cv.take<char>(N->cols * p->ktot * (int64_t)es);
+}
+
+struct BackPlan {
+    int32_t* idx;
+    double* scale;
+    void* sscr;
+    void* uscr;
+    int32_t* uidx;
+    double* uw;
+    int64_t* ucount;
+    int32_t* col;
+    double* w;
+    int64_t* prefix;
+    int64_t* ext;
+    int64_t lmax, ldG, ldGT, ldOM, ldON;
+    void *Gop, *Nu, *outM, *GT, *MuT, *outN;
+};
+void plan_backward(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int unit, int64_t c, int mode,
+                   bool want_dM, bool want_dN, BackPlan* p) {
+    const int64_t space = unit == BMM_UNIT_COLUMN ? B->n : B->K;
+    const int64_t m = M->rows, pp = N->cols;
+    const int64_t nuniq = imax(1, imin(c, space));
+    p->idx = cv.take<int32_t>(c);
+    p->scale = cv.take<double>(c);
+    p->sscr = plan_sample(cv, unit, B);
+    p->uscr = cv.take<char>(unique_scratch_bytes(space, c));
+    p->uidx = cv.take<int32_t>(nuniq);
+    p->uw = cv.take<double>(nuniq);
+    p->ucount = cv.take<int64_t>(1);
+    if (unit == BMM_UNIT_BLOCK) {
+        p->lmax = nuniq * B->max_nk;
+        p->col = cv.take<int32_t>(p->lmax);
+        p->w = cv.take<double>(p->lmax);
+        p->prefix = cv.take<int64_t>(nuniq);
+        p->ext = cv.take<int64_t>(1);
+    } else {
+        p->lmax = nuniq;
+        p->col = p->uidx;
+        p->w = p->uw;
+        p->prefix = nullptr;
+        p->ext = p->ucount;
+    }
+    const bool f64 = mode == BMM_GEMM_F64;
+    const int64_t es = f64 ? 8 : 2;
+    p->ldG = f64 ? pp : round_up(pp, 8);
+    p->ldGT = f64 ? m : round_up(m, 8);
+    p->ldOM = round_up(p->lmax, 4);
+    p->ldON = round_up(pp, 4);
+    p->Gop = p->Nu = p->outM = p->GT = p->MuT = p->outN = nullptr;
+    if (want_dM) {
+        p->Gop = cv.take<char>(m * p->ldG * es);
+        p->Nu = cv.take<char>(p->lmax * p->ldG * es);
+        p->outM = cv.take<char>(m * p->ldOM * (f64 ? 8 : 4));
+    }
+    if (want_dN) {
+        p->GT = cv.take<char>(pp * p->ldGT * es);
+        p->MuT = cv.take<char>(p->lmax * p->ldGT * es);
+        p->outN = cv.take<char>(p->lmax * p->ldON * (f64 ? 8 : 4));
+    }
+}
+
+bool valid_gemm_mode(int mode) {
+    return mode == BMM_GEMM_F64 || mode == BMM_GEMM_BF16 || mode == BMM_GEMM_SPLIT_BF16;
+}
+
+}  // namespace
+}  // namespace bmm
+
+using namespace bmm;
+
+BMM_API size_t bmm_workspace_size(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                                  int64_t max_draws, int32_t gemm_mode) {
+    if (check_problem(M, N, B) != BMM_OK || max_draws < 0 || !valid_gemm_mode(gemm_mode)) return 0;
+    if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return 0;
+    size_t need = 0;
+    {
+        Carver cv{nullptr};
+        ProbsPlan p;
+        plan_probs(cv, M, N, B, true, &p);
+        need = cv.off > need ? cv.off : need;
+    }
+    {
+        Carver cv{nullptr};
+        SizesPlan p;
+        plan_sizes(cv, B, BMM_CK_TILDE, ceil_div(imax(max_draws, 1), B->K), nullptr, nullptr, &p);
+        need = cv.off > need ? cv.off : need;
+    }
+    {
+        Carver cv{nullptr};
+        plan_sample(cv, BMM_UNIT_COLUMN, B);
+        plan_sample(cv, BMM_UNIT_BLOCK, B);
+        need = cv.off > need ? cv.off : need;
+    }
+    {
+        Carver cv{nullptr};
+        ApplyPlan p;
+        plan_apply(cv, M, N, B, unit, max_draws, gemm_mode, &p);
+        need = cv.off > need ? cv.off : need;
+    }
+    {
+        Carver cv{nullptr};
+        BackPlan p;
+        plan_backward(cv, M, N, B, unit, max_draws, gemm_mode, true, true, &p);
+        need = cv.off > need ? cv.off : need;
+    }
+    return need + kStatusBytes;
+}
+
+BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t pkind, int32_t fmode,
+                             double* p_out, const bmm_stats* st, void* ws, size_t ws_bytes, bmm_stream_t stream) {
+    const bool reuse = (fmode & BMM_REUSE_STATS) != 0;
+    fmode &= ~BMM_REUSE_STATS;
+    if (pkind < BMM_P_COL_OPT || pkind > BMM_P_BLK_NORMPROD) return BMM_ERR_ARG;
+    if (fmode != BMM_F_NONE && fmode != BMM_F_EXACT) return BMM_ERR_ARG;
+    bmm_status s;
+    if (pkind == BMM_P_COL_UNIFORM && (reuse || st == nullptr)) {  // needs the blocks only
+        if ((s = check_blocks(B)) != BMM_OK) return s;
+        if (p_out == nullptr) return BMM_OK;
+        if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < kStatusBytes) return BMM_ERR_WORKSPACE;
+        BMM_TRY(launch_probs(pkind, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, B->offsets, B->K, B->n, p_out,
+                             status_of(ws), reinterpret_cast<cudaStream_t>(stream)));
+        return BMM_OK;
+    }
+    s = check_problem(M, N, B);
+    if (s != BMM_OK) return s;
+    if (st == nullptr || !st->x || !st->y || !st->a || !st->s || !st->mf || !st->nf) return BMM_ERR_ARG;
+    const bool need_f = fmode != BMM_F_NONE || pkind == BMM_P_BLK_PRODNORM;
+    if (need_f && st->f == nullptr) return BMM_ERR_ARG;
+    if (reuse) {
+        if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < kStatusBytes) return BMM_ERR_WORKSPACE;
+        if (p_out)
+            BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, B->offsets, B->K, B->n, p_out,
+                                 status_of(ws), reinterpret_cast<cudaStream_t>(stream)));
+        return BMM_OK;
+    }
+    Carver cnt{nullptr};
+    ProbsPlan plan;
+    plan_probs(cnt, M, N, B, need_f, &plan);
+    if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
+    Carver cv{static_cast<char*>(ws) + kStatusBytes};
+    plan_probs(cv, M, N, B, need_f, &plan);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    DevStatus* dst = status_of(ws);
+    const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
+    BMM_TRY(launch_vec_sqnorms(vM, st->x, plan.partial, plan.partial_cap, cs));
+    BMM_TRY(launch_vec_sqnorms(vN, st->y, plan.partial, plan.partial_cap, cs));
+    BMM_TRY(launch_block_stats(st->x, st->y, B->offsets, B->K, B->n, st->a, st->s, st->mf, st->nf, dst, cs));
+    if (need_f)
+        BMM_TRY(launch_gram_frob(vM, vN, B->offsets, B->K, B->max_nk, nullptr, nullptr, 0, st->f, plan.gpart,
+                                 plan.gpart_cap, dst, cs));
+    if (p_out)
+        BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, B->offsets, B->K, B->n, p_out, dst,
+                             cs));
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_blocksizes(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, const bmm_stats* st,
+                                  int32_t ckind, int64_t c, const int32_t* pilot_idx, const double* pilot_scale,
+                                  int64_t pilot_per_block, int64_t* ck_out, double* g_out, double* fhat_out, void* ws,
+                                  size_t ws_bytes, bmm_stream_t stream) {
+    bmm_status s = check_blocks(B);
+    if (s != BMM_OK) return s;
+    if (ckind < BMM_CK_OPT || ckind > BMM_CK_EQUAL || ck_out == nullptr) return BMM_ERR_ARG;
+    if (ckind != BMM_CK_EQUAL && (st == nullptr || st->a == nullptr)) return BMM_ERR_ARG;
+    if (ckind == BMM_CK_OPT && st->f == nullptr) return BMM_ERR_ARG;
+    if (ckind == BMM_CK_TILDE) {
+        if ((s = check_problem(M, N, B)) != BMM_OK) return s;
+        if (pilot_idx == nullptr || pilot_scale == nullptr || pilot_per_block < 1) return BMM_ERR_ARG;
+    }
+    if (c < B->K || c > B->n) return BMM_ERR_INFEASIBLE;
+    const int64_t per = ckind == BMM_CK_TILDE ? pilot_per_block : 0;
+    Carver cnt{nullptr};
+    SizesPlan plan;
+    plan_sizes(cnt, B, ckind, per, g_out, fhat_out, &plan);
+    if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
+    Carver cv{static_cast<char*>(ws) + kStatusBytes};
+    plan_sizes(cv, B, ckind, per, g_out, fhat_out, &plan);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    DevStatus* dst = status_of(ws);
+    const double* fvec = nullptr;
+    if (ckind == BMM_CK_OPT) fvec = st->f;
+    if (ckind == BMM_CK_TILDE) {
+        BMM_TRY(launch_gram_frob(vecset_of_M(M), vecset_of_N(N), B->offsets, B->K, per, pilot_idx, pilot_scale, per,
+                                 plan.fhat, plan.gpart, plan.gpart_cap, dst, cs));
+        fvec = plan.fhat;
+    }
+    BMM_TRY(launch_blocksizes(ckind, ckind == BMM_CK_EQUAL ? nullptr : st->a, fvec, B->offsets, B->K, B->n, c, ck_out, plan.g,
+                              dst, cs));
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_sample(const double* p, int32_t unit, const bmm_blocks* B, const int64_t* ck, int64_t c,
+                              uint64_t seed, uint64_t stream_id, int32_t* idx_out, double* scale_out, void* ws,
+                              size_t ws_bytes, bmm_stream_t stream) {
+    bmm_status s = check_blocks(B);
+    if (s != BMM_OK) return s;
+    if (p == nullptr || idx_out == nullptr || scale_out == nullptr || c < 0) return BMM_ERR_ARG;
+    if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
+    if (unit == BMM_UNIT_COLUMN && ck == nullptr) return BMM_ERR_ARG;
+    if (c > 0x7fffffffLL) return BMM_ERR_UNSUPPORTED;
+    Carver cnt{nullptr};
+    plan_sample(cnt, unit, B);
+    if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
+    Carver cv{static_cast<char*>(ws) + kStatusBytes};
+    void* scr = plan_sample(cv, unit, B);
+    BMM_TRY(launch_sample(p, unit, B->offsets, B->K, B->n, ck, c, seed, stream_id, idx_out, scale_out, scr,
+                          status_of(ws), reinterpret_cast<cudaStream_t>(stream)));
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                             const int32_t* idx, const double* scale, int64_t count, int32_t gemm_mode,
+                             const bmm_mat* out, int32_t accumulate, void* ws, size_t ws_bytes, bmm_stream_t stream) {
+    bmm_status s = check_problem(M, N, B);
+    if (s != BMM_OK) return s;
+    if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
+    if (!valid_gemm_mode(gemm_mode) || count < 0 || (count > 0 && (idx == nullptr || scale == nullptr)))
+        return BMM_ERR_ARG;
+    if ((s = check_mat(out)) != BMM_OK) return s;
+    if (out->layout != BMM_ROW_MAJOR || out->rows != M->rows || out->cols != N->cols) return BMM_ERR_SHAPE;
+    if (out->dtype != (gemm_mode == BMM_GEMM_F64 ? BMM_F64 : BMM_F32)) return BMM_ERR_DTYPE;
+    if (gemm_mode != BMM_GEMM_F64 && !tc_gemm_supported()) return BMM_ERR_UNSUPPORTED;
+    if (count > 0x7fffffffLL) return BMM_ERR_UNSUPPORTED;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    void* odata = const_cast<void*>(out->data);
+    if (count == 0 || M->rows == 0 || N->cols == 0) {
+        if (!accumulate) BMM_TRY(launch_zero_matrix(odata, out->dtype, out->rows, out->cols, out->ld, cs));
+        return BMM_OK;
+    }
+    Carver cnt{nullptr};
+    ApplyPlan plan;
+    plan_apply(cnt, M, N, B, unit, count, gemm_mode, &plan);
+    if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
+    Carver cv{static_cast<char*>(ws) + kStatusBytes};
+    plan_apply(cv, M, N, B, unit, count, gemm_mode, &plan);
+    DevStatus* dst = status_of(ws);
+    const int32_t* col = idx;
+    const double* w = scale;
+    if (unit == BMM_UNIT_COLUMN) {
+        BMM_TRY(launch_set_extent(plan.ext, count, cs));
+    } else {
+        BMM_TRY(launch_expand_blocks(idx, scale, count, nullptr, B->offsets, B->K, B->n, B->max_nk, plan.col, plan.w,
+                                     plan.ext, plan.prefix, dst, cs));
+        col = plan.col;
+        w = plan.w;
+    }
+    const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
+    BMM_TRY(launch_gather_operand(vM, col, w, plan.ext, plan.lmax, gemm_mode, 0, true, plan.A, plan.ktot, dst, cs));
+    BMM_TRY(launch_gather_operand(vN, col, w, plan.ext, plan.lmax, gemm_mode, 1, true, plan.Bop, plan.ktot, dst, cs));
+    if (gemm_mode == BMM_GEMM_F64) {
+        BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.A), plan.ktot, static_cast<const double*>(plan.Bop),
+                                plan.ktot, M->rows, N->cols, 0, plan.ext, static_cast<double*>(odata), out->ld,
+                                accumulate, cs));
+    } else {
+        BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(plan.A), plan.ktot,
+                                    static_cast<const __nv_bfloat16*>(plan.Bop), plan.ktot, M->rows, N->cols,
+                                    plan.ktot, 0, plan.ext, gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1,
+                                    static_cast<float*>(odata), out->ld, accumulate, dst, cs));
+    }
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
+                                int32_t unit, const double* p, const int64_t* ck, int64_t c, uint64_t seed,
+                                uint64_t stream_id, int32_t gemm_mode, const bmm_mat* dM, const bmm_mat* dN,
+                                int32_t accumulate, void* ws, size_t ws_bytes, bmm_stream_t stream) {
+    bmm_status s = check_problem(M, N, B);
+    if (s != BMM_OK) return s;
+    if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
+    if (!valid_gemm_mode(gemm_mode) || p == nullptr || c < 0 || (unit == BMM_UNIT_COLUMN && ck == nullptr))
+        return BMM_ERR_ARG;
+    if (gemm_mode == BMM_GEMM_SPLIT_BF16) return BMM_ERR_UNSUPPORTED;
+    const int gd = gemm_mode == BMM_GEMM_F64 ? BMM_F64 : BMM_F32;
+    if ((s = check_mat(G)) != BMM_OK) return s;
+    if (G->layout != BMM_ROW_MAJOR || G->rows != M->rows || G->cols != N->cols) return BMM_ERR_SHAPE;
+    if (G->dtype != gd) return BMM_ERR_DTYPE;
+    if (dM) {
+        if ((s = check_mat(dM)) != BMM_OK) return s;
+        if (dM->rows != M->rows || dM->cols != M->cols) return BMM_ERR_SHAPE;
+        if (dM->dtype != gd) return BMM_ERR_DTYPE;
+    }
+    if (dN) {
+        if ((s = check_mat(dN)) != BMM_OK) return s;
+        if (dN->rows != N->rows || dN->cols != N->cols) return BMM_ERR_SHAPE;
+        if (dN->dtype != gd) return BMM_ERR_DTYPE;
+    }
+    if (gemm_mode != BMM_GEMM_F64 && !tc_gemm_supported()) return BMM_ERR_UNSUPPORTED;
+    if (c > 0x7fffffffLL) return BMM_ERR_UNSUPPORTED;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (!accumulate) {
+        if (dM) BMM_TRY(launch_zero_matrix(const_cast<void*>(dM->data), gd, dM->layout == BMM_ROW_MAJOR ? dM->rows : dM->cols,
+                                           dM->layout == BMM_ROW_MAJOR ? dM->cols : dM->rows, dM->ld, cs));
+        if (dN) BMM_TRY(launch_zero_matrix(const_cast<void*>(dN->data), gd, dN->layout == BMM_ROW_MAJOR ? dN->rows : dN->cols,
+                                           dN->layout == BMM_ROW_MAJOR ? dN->cols : dN->rows, dN->ld, cs));
+    }
+    if (c == 0 || (!dM && !dN)) return BMM_OK;
+    Carver cnt{nullptr};
+    BackPlan plan;
+    plan_backward(cnt, M, N, B, unit, c, gemm_mode, dM != nullptr, dN != nullptr, &plan);
+    if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
+    Carver cv{static_cast<char*>(ws) + kStatusBytes};
+    plan_backward(cv, M, N, B, unit, c, gemm_mode, dM != nullptr, dN != nullptr, &plan);
+    DevStatus* dst = status_of(ws);
+    const int64_t space = unit == BMM_UNIT_COLUMN ? B->n : B->K;
+    const int64_t m = M->rows, pp = N->cols;
+    const bool f64 = gemm_mode == BMM_GEMM_F64;
+    BMM_TRY(launch_sample(p, unit, B->offsets, B->K, B->n, ck, c, seed, stream_id, plan.idx, plan.scale, plan.sscr,
+                          dst, cs));
+    BMM_TRY(launch_unique(plan.idx, plan.scale, c, space, plan.uidx, plan.uw, plan.ucount, plan.uscr, dst, cs));
+    if (unit == BMM_UNIT_BLOCK)
+        BMM_TRY(launch_expand_blocks(plan.uidx, plan.uw, imin(c, space), plan.ucount, B->offsets, B->K, B->n,
+                                     B->max_nk, plan.col, plan.w, plan.ext, plan.prefix, dst, cs));
+    const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
+    if (dM) {
+        // outM[h][j] = sum_f G[h,f] N[col_j, f]
+        if (f64) BMM_TRY(launch_convert_to_f64(G->data, G->dtype, m, pp, G->ld, false, static_cast<double*>(plan.Gop), plan.ldG, cs));
+        else BMM_TRY(launch_convert_f32_to_bf16(static_cast<const float*>(G->data), m, pp, G->ld,
+                                                static_cast<__nv_bfloat16*>(plan.Gop), plan.ldG, cs));
+        BMM_TRY(launch_gather_rows(vN, plan.col, plan.ext, plan.lmax, plan.Nu, plan.ldG, f64, cs));
+        if (f64)
+            BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.Gop), plan.ldG, static_cast<const double*>(plan.Nu),
+                                    plan.ldG, m, plan.lmax, pp, nullptr, static_cast<double*>(plan.outM), plan.ldOM, 0, cs));
+        else
+            BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(plan.Gop), plan.ldG,
+                                        static_cast<const __nv_bfloat16*>(plan.Nu), plan.ldG, m, plan.lmax, pp,
+                                        round_up(pp, 64), nullptr, 1, static_cast<float*>(plan.outM), plan.ldOM, 0,
+                                        dst, cs));
+        const int mode = dM->layout == BMM_ROW_MAJOR ? VEC_STRIDED : VEC_CONTIG;
+        BMM_TRY(launch_scatter_grad(const_cast<void*>(dM->data), gd, dM->ld, mode, m, plan.outM, gd, plan.ldOM, false,
+                                    plan.col, plan.w, plan.ext, plan.lmax, cs));
+    }
+    if (dN) {
+        // outN[j][f] = sum_h M[h, col_j] G[h, f]
+        if (f64) BMM_TRY(launch_convert_to_f64(G->data, G->dtype, m, pp, G->ld, true, static_cast<double*>(plan.GT), plan.ldGT, cs));
+        else BMM_TRY(launch_transpose_f32_to_bf16(static_cast<const float*>(G->data), m, pp, G->ld,
+                                                  static_cast<__nv_bfloat16*>(plan.GT), plan.ldGT, cs));
+        BMM_TRY(launch_gather_rows(vM, plan.col, plan.ext, plan.lmax, plan.MuT, plan.ldGT, f64, cs));
+        if (f64)
+            BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.MuT), plan.ldGT, static_cast<const double*>(plan.GT),
+                                    plan.ldGT, plan.lmax, pp, m, nullptr, static_cast<double*>(plan.outN), plan.ldON, 0, cs));
+        else
+            BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(plan.MuT), plan.ldGT,
+                                        static_cast<const __nv_bfloat16*>(plan.GT), plan.ldGT, plan.lmax, pp, m,
+                                        round_up(m, 64), nullptr, 1, static_cast<float*>(plan.outN), plan.ldON, 0,
+                                        dst, cs));
+        const int mode = dN->layout == BMM_ROW_MAJOR ? VEC_CONTIG : VEC_STRIDED;
+        BMM_TRY(launch_scatter_grad(const_cast<void*>(dN->data), gd, dN->ld, mode, pp, plan.outN, gd, plan.ldON, true,
+                                    plan.col, plan.w, plan.ext, plan.lmax, cs));
+    }
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_read_device_status(const void* ws, bmm_stream_t stream) {
+    if (ws == nullptr) return BMM_ERR_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return BMM_ERR_CUDA;
+    DevStatus h{0, 0};
+    if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return BMM_ERR_CUDA;
+    return static_cast<bmm_status>(h.code);
+}
+
+BMM_API bmm_status bmm_clear_device_status(void* ws, bmm_stream_t stream) {
+    if (ws == nullptr) return BMM_ERR_ARG;
+    return cudaMemsetAsync(ws, 0, kStatusBytes, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? BMM_OK
+                                                                                                       : BMM_ERR_CUDA;
+}
+
+BMM_API const char* bmm_status_string(bmm_status s) {
+    switch (s) {
+        case BMM_OK: return "ok";
+        case BMM_ERR_ARG: return "invalid argument";
+        case BMM_ERR_SHAPE: return "inconsistent shape or block offsets";
+        case BMM_ERR_DTYPE: return "unsupported element type";
+        case BMM_ERR_INFEASIBLE: return "infeasible budget (need K <= c <= n)";
+        case BMM_ERR_NONFINITE: return "non-finite value in the data";
+        case BMM_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case BMM_ERR_CUDA: return "CUDA runtime error";
+        case BMM_ERR_TIMEOUT: return "bounded device wait expired";
+        case BMM_ERR_UNSUPPORTED: return "not supported by this build or device";
+    }
+    return "unknown status";
+}

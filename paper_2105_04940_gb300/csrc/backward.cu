@@ -1,0 +1,328 @@
+// backward.cu -- adjoint of the sampled product (dM^{(i)} += w_i G N_{(i)}^T, dN_{(i)} += w_i M^{(i)T} G).
+//
+// The redrawn indices are reduced to their distinct values (ascending) with multiplicities, so the
+// gradient scatter writes every touched column/row exactly once: no float atomics, deterministic.
+// Duplicate draws of index i carry the same scale 1/(c_k p_i), hence w_i = mult_i * scale_i.
+#include "internal.h"
+
+namespace bmm {
+
+constexpr int kTileScan = 1024;
+
+__device__ __forceinline__ unsigned long long warp_scan_incl(unsigned long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+__device__ unsigned long long block_scan_incl(unsigned long long v, unsigned long long* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long inc = warp_scan_incl(v);
+    if (lane == 31) sm[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = sm[lane];
+        sm[lane] = warp_scan_incl(w) - w;
+    }
+    __syncthreads();
+    const unsigned long long r = inc + sm[warp];
+    __syncthreads();
+    return r;
+}
+
+__global__ void hist_kernel(const int32_t* __restrict__ idx, const double* __restrict__ scale, int64_t count,
+                            int64_t space, int* __restrict__ cnt, double* __restrict__ sval, DevStatus* st) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t i = idx[t];
+    if (i < 0 || i >= space) {
+        set_status(st, BMM_ERR_ARG, (int)t);
+        return;
+    }
+    atomicAdd(&cnt[i], 1);
+    sval[i] = scale[t];  // identical for every draw of i
+}
+
+__global__ void __launch_bounds__(kTileScan) flag_scan_kernel(const int* __restrict__ cnt, int64_t space,
+                                                              unsigned long long* __restrict__ pos,
+                                                              unsigned long long* __restrict__ tot) {
+    __shared__ unsigned long long sm[32];
+    const int64_t i = (int64_t)blockIdx.x * kTileScan + threadIdx.x;
+    const unsigned long long f = (i < space && cnt[i] > 0) ? 1ull : 0ull;
+    const unsigned long long inc = block_scan_incl(f, sm);
+    if (i < space) pos[i] = inc - f;
+    if (threadIdx.x == kTileScan - 1) tot[blockIdx.x] = inc;
+}
+
+__global__ void __launch_bounds__(kTileScan) tot_scan_kernel(unsigned long long* __restrict__ tot, int64_t ntiles) {
+    __shared__ unsigned long long sm[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < ntiles; b += kTileScan) {
+        const int64_t i = b + threadIdx.x;
+        const unsigned long long v = i < ntiles ? tot[i] : 0ull;
+        const unsigned long long inc = block_scan_incl(v, sm);
+        const unsigned long long c0 = carry;
+        if (i < ntiles) tot[i] = c0 + inc - v;
+        __syncthreads();
+        if (threadIdx.x == kTileScan - 1) carry = c0 + inc;
+        __syncthreads();
+    }
+}
+
+__global__ void compact_kernel(const int* __restrict__ cnt, const double* __restrict__ sval,
+                               const unsigned long long* __restrict__ pos, const unsigned long long* __restrict__ tot,
+                               int64_t space, int32_t* __restrict__ uidx, double* __restrict__ uw,
+                               int64_t* __restrict__ ucount) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= space) return;
+    const unsigned long long q = pos[i] + tot[i / kTileScan];
+    const int c = cnt[i];
+    if (c > 0) {
+        uidx[q] = (int32_t)i;
+        uw[q] = __dmul_rn((double)c, sval[i]);
+    }
+    if (i == space - 1) *ucount = (int64_t)(q + (c > 0 ? 1 : 0));
+}
+
+int64_t unique_scratch_bytes(int64_t space, int64_t count) {
+    (void)count;
+    const int64_t ntiles = ceil_div(imax(space, 1), kTileScan);
+    return round_up(space * 4, 256) + round_up(space * 8, 256) + round_up(space * 8, 256) + round_up(ntiles * 8, 256);
+}
+
+cudaError_t launch_unique(const int32_t* idx, const double* scale, int64_t count, int64_t space, int32_t* uidx,
+                          double* uw, int64_t* ucount_dev, void* scratch, DevStatus* st, cudaStream_t s) {
+    char* w = static_cast<char*>(scratch);
+    int* cnt = reinterpret_cast<int*>(w);
+    w += round_up(space * 4, 256);
+    double* sval = reinterpret_cast<double*>(w);
+    w += round_up(space * 8, 256);
+    unsigned long long* pos = reinterpret_cast<unsigned long long*>(w);
+    w += round_up(space * 8, 256);
+    unsigned long long* tot = reinterpret_cast<unsigned long long*>(w);
+    const int64_t ntiles = ceil_div(space, kTileScan);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, space * 4, s);
+    if (e != cudaSuccess) return e;
+    if (count > 0) hist_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(idx, scale, count, space, cnt, sval, st);
+    flag_scan_kernel<<<(unsigned)ntiles, kTileScan, 0, s>>>(cnt, space, pos, tot);
+    tot_scan_kernel<<<1, kTileScan, 0, s>>>(tot, ntiles);
+    compact_kernel<<<(unsigned)ceil_div(space, 256), 256, 0, s>>>(cnt, sval, pos, tot, space, uidx, uw, ucount_dev);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- conversions of G
+__global__ void convert_f32_bf16_kernel(const float* __restrict__ G, int64_t rows, int64_t cols, int64_t ldg,
+                                        __nv_bfloat16* __restrict__ out, int64_t ldo) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y)
+        if (c < cols) out[r * ldo + c] = __float2bfloat16_rn(G[r * ldg + c]);
+}
+
+__global__ void transpose_f32_bf16_kernel(const float* __restrict__ G, int64_t rows, int64_t cols, int64_t ldg,
+                                          __nv_bfloat16* __restrict__ out, int64_t ldo) {
+    __shared__ float t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? G[r * ldg + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[c * ldo + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+    }
+}
+
+__global__ void convert_f64_kernel(const double* __restrict__ G, int64_t rows, int64_t cols, int64_t ldg,
+                                   bool transpose, double* __restrict__ out, int64_t ldo) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        if (c >= cols) continue;
+        const double v = G[r * ldg + c];
+        if (transpose) out[c * ldo + r] = v; else out[r * ldo + c] = v;
+    }
+}
+
+cudaError_t launch_convert_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg, __nv_bfloat16* out,
+                                       int64_t ldo, cudaStream_t s) {
+    dim3 grid((unsigned)ceil_div(cols, 256), (unsigned)imin(imax(rows, 1), 8192));
+    convert_f32_bf16_kernel<<<grid, 256, 0, s>>>(G, rows, cols, ldg, out, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg, __nv_bfloat16* out,
+                                         int64_t ldo, cudaStream_t s) {
+    if (ceil_div(rows, 32) > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
+    transpose_f32_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(G, rows, cols, ldg, out, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_to_f64(const void* G, int dtype, int64_t rows, int64_t cols, int64_t ldg, bool transpose,
+                                  double* out, int64_t ldo, cudaStream_t s) {
+    if (dtype != BMM_F64) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)ceil_div(cols, 256), (unsigned)imin(imax(rows, 1), 8192));
+    convert_f64_kernel<<<grid, 256, 0, s>>>(static_cast<const double*>(G), rows, cols, ldg, transpose, out, ldo);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- gathered vectors as rows
+// out[j][r] = vec_{col_j}[r] for j < ext (zero rows for ext <= j < jmax)
+template <typename T, typename O>
+__global__ void gather_rows_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int mode, int64_t nvec,
+                                   const int32_t* __restrict__ col, const int64_t* __restrict__ ext_dev, int64_t jmax,
+                                   O* __restrict__ out, int64_t ldo) {
+    __shared__ float t[32][33];
+    const int64_t ext = *ext_dev;
+    const int64_t j0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (mode == VEC_CONTIG) {  // vector j is a storage row: copy along r
+        for (int jj = ty; jj < 32; jj += blockDim.y) {
+            const int64_t j = j0 + jj, r = r0 + tx;
+            if (j >= jmax || r >= len) continue;
+            O v = O(0.f);
+            if (j < ext) {
+                const int64_t c = col[j];
+                if (c >= 0 && c < nvec) v = (O)(float)X[c * ld + r];
+            }
+            out[j * ldo + r] = v;
+        }
+        return;
+    }
+    // vector j is a storage column: read X[r*ld + col_j] along j, write along r
+    for (int rr = ty; rr < 32; rr += blockDim.y) {
+        const int64_t r = r0 + rr, j = j0 + tx;
+        float v = 0.f;
+        if (r < len && j < ext) {
+            const int64_t c = col[j];
+            if (c >= 0 && c < nvec) v = (float)X[r * ld + c];
+        }
+        t[rr][tx] = v;
+    }
+    __syncthreads();
+    for (int jj = ty; jj < 32; jj += blockDim.y) {
+        const int64_t j = j0 + jj, r = r0 + tx;
+        if (j < jmax && r < len) out[j * ldo + r] = (O)t[tx][jj];
+    }
+}
+
+template <typename T>
+__global__ void gather_rows_f64_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int mode, int64_t nvec,
+                                       const int32_t* __restrict__ col, const int64_t* __restrict__ ext_dev,
+                                       int64_t jmax, double* __restrict__ out, int64_t ldo) {
+    const int64_t ext = *ext_dev;
+    const int64_t j = blockIdx.x;
+    if (j >= jmax) return;
+    const int64_t c = (j < ext) ? (int64_t)col[j] : -1;
+    for (int64_t r = threadIdx.x; r < len; r += blockDim.x) {
+        double v = 0.0;
+        if (c >= 0 && c < nvec) v = (double)((mode == VEC_CONTIG) ? X[c * ld + r] : X[r * ld + c]);
+        out[j * ldo + r] = v;
+    }
+}
+
+template <typename T>
+static cudaError_t gather_rows_t(const VecSet& v, const int32_t* col, const int64_t* ext_dev, int64_t jmax, void* out,
+                                 int64_t ldo, bool f64, cudaStream_t s) {
+    const T* X = static_cast<const T*>(v.data);
+    if (f64) {
+        gather_rows_f64_kernel<T><<<(unsigned)jmax, 256, 0, s>>>(X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax,
+                                                               static_cast<double*>(out), ldo);
+    } else {
+        if (ceil_div(v.len, 32) > 65535) return cudaErrorInvalidValue;
+        dim3 grid((unsigned)ceil_div(jmax, 32), (unsigned)ceil_div(v.len, 32));
+        gather_rows_kernel<T, __nv_bfloat16><<<grid, dim3(32, 8), 0, s>>>(
+            X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax, static_cast<__nv_bfloat16*>(out), ldo);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const VecSet& v, const int32_t* col, const int64_t* ext_dev, int64_t jmax, void* out,
+                               int64_t ldo, bool f64, cudaStream_t s) {
+    if (jmax <= 0) return cudaSuccess;
+    switch (v.dtype) {
+        case BMM_F64: return gather_rows_t<double>(v, col, ext_dev, jmax, out, ldo, f64, s);
+        case BMM_F32: return gather_rows_t<float>(v, col, ext_dev, jmax, out, ldo, f64, s);
+        default: return gather_rows_t<__nv_bfloat16>(v, col, ext_dev, jmax, out, ldo, f64, s);
+    }
+}
+
+// ---------------------------------------------------------------- scatter
+template <typename D, typename S>
+__global__ void scatter_kernel(D* __restrict__ dst, int64_t dst_ld, int dst_mode, int64_t len,
+                               const S* __restrict__ src, int64_t src_ld, bool src_rows,
+                               const int32_t* __restrict__ col, const double* __restrict__ w,
+                               const int64_t* __restrict__ ext_dev) {
+    const int64_t ext = *ext_dev;
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    if (j0 >= ext) return;
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // dst_mode CONTIG: element r of vector c at dst[c*ld + r] -> let tx run along r
+    // dst_mode STRIDED: at dst[r*ld + c] -> let tx run along j (adjacent columns)
+    for (int q = ty; q < 32; q += blockDim.y) {
+        int64_t j, r;
+        if (dst_mode == VEC_CONTIG) { j = j0 + q; r = r0 + tx; }
+        else { j = j0 + tx; r = r0 + q; }
+        if (j >= ext || r >= len) continue;
+        const int64_t c = col[j];
+        const double sv = src_rows ? (double)src[j * src_ld + r] : (double)src[r * src_ld + j];
+        D* d = (dst_mode == VEC_CONTIG) ? dst + c * dst_ld + r : dst + r * dst_ld + c;
+        *d = (D)((double)*d + w[j] * sv);
+    }
+}
+
+template <>
+__global__ void scatter_kernel<float, float>(float* __restrict__ dst, int64_t dst_ld, int dst_mode, int64_t len,
+                                             const float* __restrict__ src, int64_t src_ld, bool src_rows,
+                                             const int32_t* __restrict__ col, const double* __restrict__ w,
+                                             const int64_t* __restrict__ ext_dev) {
+    const int64_t ext = *ext_dev;
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    if (j0 >= ext) return;
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int q = ty; q < 32; q += blockDim.y) {
+        int64_t j, r;
+        if (dst_mode == VEC_CONTIG) { j = j0 + q; r = r0 + tx; }
+        else { j = j0 + tx; r = r0 + q; }
+        if (j >= ext || r >= len) continue;
+        const int64_t c = col[j];
+        const float sv = src_rows ? src[j * src_ld + r] : src[r * src_ld + j];
+        float* d = (dst_mode == VEC_CONTIG) ? dst + c * dst_ld + r : dst + r * dst_ld + c;
+        *d = __fmaf_rn((float)w[j], sv, *d);
+    }
+}
+
+cudaError_t launch_scatter_grad(void* dst, int dst_dtype, int64_t dst_ld, int dst_mode, int64_t len, const void* src,
+                                int src_dtype, int64_t src_ld, bool src_rows, const int32_t* col, const double* w,
+                                const int64_t* ext_dev, int64_t ext_max, cudaStream_t s) {
+    if (ext_max <= 0 || len <= 0) return cudaSuccess;
+    if (ceil_div(len, 32) > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)ceil_div(ext_max, 32), (unsigned)ceil_div(len, 32));
+    dim3 block(32, 8);
+    if (dst_dtype == BMM_F64 && src_dtype == BMM_F64)
+        scatter_kernel<double, double><<<grid, block, 0, s>>>(static_cast<double*>(dst), dst_ld, dst_mode, len,
+                                                             static_cast<const double*>(src), src_ld, src_rows, col, w,
+                                                             ext_dev);
+    else if (dst_dtype == BMM_F32 && src_dtype == BMM_F32)
+        scatter_kernel<float, float><<<grid, block, 0, s>>>(static_cast<float*>(dst), dst_ld, dst_mode, len,
+                                                           static_cast<const float*>(src), src_ld, src_rows, col, w,
+                                                           ext_dev);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_matrix(void* dst, int dtype, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s) {
+    const size_t es = dtype == BMM_F64 ? 8 : (dtype == BMM_F32 ? 4 : 2);
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    return cudaMemset2DAsync(dst, (size_t)ld * es, 0, (size_t)cols * es, (size_t)rows, s);
+}
+
+}  // namespace bmm

@@ -1,0 +1,108 @@
+// common.cuh -- device helpers shared by the kernels of the sm_103a library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/bmm.h"
+
+namespace bmm {
+
+// ---------------------------------------------------------------- status word
+// The first 256 bytes of the workspace: int32 status (first error wins), int32 detail.
+struct DevStatus {
+    int code;
+    int detail;
+};
+
+__device__ __forceinline__ void set_status(DevStatus* st, int code, int detail = 0) {
+    if (st != nullptr && atomicCAS(&st->code, 0, code) == 0) {
+        atomicExch(&st->detail, detail);
+    }
+}
+
+// ---------------------------------------------------------------- element loads
+template <typename T> struct Elem;
+template <> struct Elem<double> {
+    static __device__ __forceinline__ double to_f64(double v) { return v; }
+};
+template <> struct Elem<float> {
+    static __device__ __forceinline__ double to_f64(float v) { return (double)v; }
+};
+template <> struct Elem<__nv_bfloat16> {
+    static __device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+};
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---------------------------------------------------------------- float-float sums
+// A sum carried as hi + lo in FP32 with error-free transformations (TwoSum,
+// and the exact FMA residual of a product).  The intrinsics keep the compiler
+// from contracting or reassociating.  Callers fold the pair into FP64 every few
+// dozen terms so the lo part never accumulates more than ~2^-48 relative error.
+struct FF {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+    // += a * b, exactly captured up to the FP32 rounding of lo
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        float pr = __fmul_rn(a, b);
+        float pe = __fmaf_rn(a, b, -pr);
+        float t = __fadd_rn(hi, pr);
+        float bp = __fsub_rn(t, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(M0, ctr.x), lo0 = M0 * ctr.x;
+        uint32_t hi1 = __umulhi(M1, ctr.z), lo1 = M1 * ctr.z;
+        U4 n;
+        n.x = hi1 ^ ctr.y ^ k0;
+        n.y = lo1;
+        n.z = hi0 ^ ctr.w ^ k1;
+        n.w = lo0;
+        ctr = n;
+        k0 += W0;
+        k1 += W1;
+    }
+    return ctr;
+}
+
+// 64-bit uniform of global draw t in stream sid: (x1 << 32) | x0.
+__device__ __forceinline__ uint64_t draw_bits(uint64_t seed, uint64_t sid, uint64_t t) {
+    U4 c{(uint32_t)t, (uint32_t)(t >> 32), (uint32_t)sid, (uint32_t)(sid >> 32)};
+    U4 o = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return ((uint64_t)o.y << 32) | (uint64_t)o.x;
+}
+
+// ---------------------------------------------------------------- misc
+__host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }
+__host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace bmm

@@ -1,0 +1,385 @@
+// gemm_tc.cu -- the sampled product CD = C D on the sm_103a tensor cores (Alg. 2 step 4, eq. 3.3).
+//
+// out[M x N] (+)= A[M x K] * B[N x K]^T with A, B BF16 and K-major (rows of length K).
+// Persistent kernel, one CTA per SM, 192 threads:
+//   warp 0   one lane issues TMA loads of 128 x 64 (A) and BN x 64 (B) tiles, 128-byte
+//            swizzled, into a ring of shared-memory stages (mbarrier complete_tx);
+//   warp 1   allocates 2*BN TMEM columns; one lane issues tcgen05.mma (kind::f16, M=128,
+//            N=BN, K=16) into one of two TMEM accumulators and commits stages back;
+//   warps 2-5 drain the other accumulator with tcgen05.ld (one TMEM lane quadrant per warp)
+//            and store FP32 rows, overlapping the next tile's MMAs.
+// Every wait is bounded (globaltimer); on expiry the CTA records BMM_ERR_TIMEOUT, lets its
+// copies and MMAs in flight finish (again bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+
+namespace bmm {
+namespace {
+
+constexpr int BM = 128, BK = 64;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+
+template <int BN> struct Cfg {
+    static constexpr int STAGES = (BN == 256) ? 4 : 6;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+    // instruction descriptor, kind::f16: D=F32 (bits 4-5), A=B=BF16 (bits 7-9, 10-12),
+    // both K-major, N>>3 at bits 17-22, M>>4 at bits 24-28
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait.  abort_flag != nullptr: give up when another role aborted, and raise the flag on expiry.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag != nullptr && *abort_flag) return false;
+        if (globaltimer() - t0 > kTimeoutNs) {
+            if (abort_flag != nullptr) *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int32_t x, int32_t y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte swizzle,
+// 8-row core-matrix groups 1024 bytes apart (SBO), descriptor version 1 (bit 46).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+#define TMEM_LD_32X32B_X32(taddr, r)                                                                                  \
+    asm volatile(                                                                                                     \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"  \
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                              \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), \
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),      \
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),     \
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                   \
+        : "r"(taddr))
+
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int* tm, int* tn) {
+    constexpr int G = 8;  // M-tiles per raster group, so concurrent CTAs share A and B panels in L2
+    const int span = G * tiles_n;
+    const int group = tile / span;
+    const int first = group * G;
+    const int gm = min(tiles_m - first, G);
+    const int r = tile - group * span;
+    *tm = first + r % gm;
+    *tn = r / gm;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+                        int N, long long k_host, const long long* k_dev, int k_mult, float* __restrict__ out,
+                        long long ldo, int accumulate, int vec_ok, DevStatus* st) {
+    using C = Cfg<BN>;
+    extern __shared__ uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t bar_full[C::STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[C::STAGES];
+    __shared__ __align__(8) uint64_t bar_tfull[2];
+    __shared__ __align__(8) uint64_t bar_tempty[2];
+    __shared__ __align__(8) uint64_t bar_drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = base;
+    uint8_t* sB = base + C::STAGES * C::A_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const long long K = k_dev ? (long long)k_mult * (((*k_dev) + 63) / 64 * 64) : k_host;
+    const int num_kb = (int)(K / BK);
+    const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+    const int num_tiles = tiles_m * tiles_n;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&bar_tfull[a]), 1);
+            mbar_init(smem_u32(&bar_tempty[a]), 4);
+        }
+        mbar_init(smem_u32(&bar_drain), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ TMA producer
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t issued_mask = 0, issued_phase = 0;
+        bool aborted = false;
+        for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x) {
+            int tm, tn;
+            tile_coords(tile, tiles_m, tiles_n, &tm, &tn);
+            for (int kb = 0; kb < num_kb; ++kb) {
+                if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
+                    aborted = true;
+                    break;
+                }
+                const uint32_t fb = smem_u32(&bar_full[stage]);
+                mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
+                tma_load_2d(smem_u32(sA + stage * C::A_BYTES), &tmA, fb, kb * BK, tm * BM);
+                tma_load_2d(smem_u32(sB + stage * C::B_BYTES), &tmB, fb, kb * BK, tn * BN);
+                issued_mask |= 1u << stage;
+                issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+                if (++stage == C::STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+        if (aborted) {  // let the copies in flight land before the CTA's shared memory goes away
+            for (int s = 0; s < C::STAGES; ++s)
+                if (issued_mask & (1u << s)) mbar_wait(smem_u32(&bar_full[s]), (issued_phase >> s) & 1u, nullptr);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        int stage = 0;
+        uint32_t phase = 0;
+        int it = 0;
+        bool aborted = false;
+        for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            if (!mbar_wait(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
+                aborted = true;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(acc * BN);
+            for (int kb = 0; kb < num_kb; ++kb) {
+                if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &s_abort)) {
+                    aborted = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t ad = sw128_desc(smem_u32(sA + stage * C::A_BYTES));
+                const uint64_t bd = sw128_desc(smem_u32(sB + stage * C::B_BYTES));
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    tc_mma_bf16(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                tc_commit(smem_u32(&bar_empty[stage]));
+                if (++stage == C::STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (aborted) break;
+            tc_commit(smem_u32(&bar_tfull[acc]));
+        }
+        if (aborted) {  // wait for the MMAs already issued before TMEM is freed
+            tc_commit(smem_u32(&bar_drain));
+            mbar_wait(smem_u32(&bar_drain), 0u, nullptr);
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            if (!mbar_wait(smem_u32(&bar_tfull[acc]), aph, &s_abort)) break;
+            tc_fence_after();
+            int tm, tn;
+            tile_coords(tile, tiles_m, tiles_n, &tm, &tn);
+            const int row = tm * BM + q * 32 + lane;
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + cc * 32);
+                TMEM_LD_32X32B_X32(taddr, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (num_kb == 0) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) r[e] = 0u;
+                }
+                const int col0 = tn * BN + cc * 32;
+                if (row < M && col0 < N) {
+                    float* o = out + (long long)row * ldo + col0;
+                    if (vec_ok && col0 + 32 <= N) {
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) {
+                            float4 val = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                                     __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+                            if (accumulate) {
+                                const float4 old = *reinterpret_cast<const float4*>(o + 4 * v);
+                                val.x += old.x; val.y += old.y; val.z += old.z; val.w += old.w;
+                            }
+                            *reinterpret_cast<float4*>(o + 4 * v) = val;
+                        }
+                    } else {
+                        const int ne = min(32, N - col0);
+                        for (int e = 0; e < ne; ++e) o[e] = (accumulate ? o[e] : 0.0f) + __uint_as_float(r[e]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[acc]));
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && s_abort) set_status(st, BMM_ERR_TIMEOUT, 1);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn == nullptr) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kdim, int64_t ld, int box_rows) {
+    auto fn = encode_fn();
+    if (fn == nullptr) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+template <int BN>
+cudaError_t launch_bn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M, int64_t N,
+                      int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out, int64_t ldo,
+                      int accumulate, DevStatus* st, cudaStream_t s) {
+    using C = Cfg<BN>;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, kdim, lda, BM) || !make_map(&mb, B, N, kdim, ldb, BN)) return cudaErrorInvalidValue;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t tiles = ceil_div(M, BM) * ceil_div(N, BN);
+    const int grid = (int)imin(tiles, num_sms());
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (ldo % 4 == 0);
+    gemm_bf16_tc_kernel<BN><<<grid, 192, C::SMEM, s>>>(ma, mb, (int)M, (int)N, (long long)k_host,
+                                                       reinterpret_cast<const long long*>(k_dev), k_mult, out,
+                                                       (long long)ldo, accumulate, vec_ok, st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_gemm_supported() {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_gemm_bf16_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M,
+                                int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
+                                int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (M > 0x7fffffff || N > 0x7fffffff || (lda % 8) != 0 || (ldb % 8) != 0 || kdim <= 0 || kdim > lda ||
+        kdim > ldb || (k_dev == nullptr && (k_host % 64) != 0))
+        return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return cudaErrorInvalidValue;
+    if (N <= 128) return launch_bn<128>(A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate, st, s);
+    return launch_bn<256>(A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate, st, s);
+}
+
+}  // namespace bmm

@@ -1,0 +1,114 @@
+// internal.h -- host-side launchers shared between the translation units of the library.
+// Nothing here is exported; the ABI is include/bmm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace bmm {
+
+// A matrix seen through its storage: `rows_s` storage rows of `cols_s` elements, stride ld.
+struct View {
+    const void* data;
+    int64_t rows_s, cols_s, ld;
+    int dtype;
+};
+
+// Vectors of the contraction index i: column i of M (length m) or row i of N (length p).
+// CONTIG: vector i is storage row i (element h at data[i*ld + h]).
+// STRIDED: vector i is storage column i (element h at data[h*ld + i]).
+enum VecMode { VEC_CONTIG = 0, VEC_STRIDED = 1 };
+struct VecSet {
+    const void* data;
+    int64_t len;   // vector length (m for M, p for N)
+    int64_t count; // number of vectors (n)
+    int64_t ld;
+    int dtype;
+    int mode;      // VecMode
+};
+
+VecSet vecset_of_M(const bmm_mat* M);  // columns of M
+VecSet vecset_of_N(const bmm_mat* N);  // rows of N
+
+// ---- norms.cu
+// out[i] = ||vector i||^2 for i < count (FP64-accurate)
+cudaError_t launch_vec_sqnorms(const VecSet& v, double* out, double* partial, int64_t partial_cap,
+                               cudaStream_t s);
+int64_t vec_sqnorms_partial_elems(const VecSet& v);
+cudaError_t launch_block_stats(const double* x, const double* y, const int64_t* off, int64_t K, int64_t n,
+                               double* a, double* ssum, double* mf, double* nf, DevStatus* st, cudaStream_t s);
+
+// ---- frob.cu
+// Per segment k: f[k] = || sum_t w_t u_t v_t^T ||_F^2 over the listed vectors of the segment,
+// computed as sum_{t,t'} w_t w_t' <u_t,u_t'> <v_t,v_t'> with FP64-accurate dot products.
+// cols == nullptr: segment k lists its own contraction indices off[k]..off[k+1]-1 with w = 1.
+// cols != nullptr: segment k lists cols[k*per + j], j < per, with weights wts[...].
+cudaError_t launch_gram_frob(const VecSet& U, const VecSet& V, const int64_t* off, int64_t K, int64_t max_len,
+                             const int32_t* cols, const double* wts, int64_t per,
+                             double* f, double* partial, int64_t partial_cap, DevStatus* st, cudaStream_t s);
+int64_t gram_frob_partial_elems(int64_t K, int64_t max_len);
+
+// ---- design.cu
+cudaError_t launch_probs(int kind, const double* x, const double* y, const double* a, const double* mf,
+                         const double* nf, const double* f, const int64_t* off, int64_t K, int64_t n,
+                         double* p, DevStatus* st, cudaStream_t s);
+cudaError_t launch_blocksizes(int kind, const double* a, const double* f, const int64_t* off, int64_t K, int64_t n,
+                              int64_t c, int64_t* ck, double* g, DevStatus* st, cudaStream_t s);
+
+// ---- sampler.cu
+int64_t sampler_scratch_bytes(int64_t len, int64_t K);
+cudaError_t launch_sample(const double* p, int unit, const int64_t* off, int64_t K, int64_t n, const int64_t* ck,
+                          int64_t c, uint64_t seed, uint64_t sid, int32_t* idx, double* scale,
+                          void* scratch, DevStatus* st, cudaStream_t s);
+
+// ---- gather.cu
+// Column list of the product: col[j], w[j] for j < ext, ext on the device (*ext_dev).
+// count_dev (optional): the number of valid draws on the device (<= count).
+cudaError_t launch_expand_blocks(const int32_t* kidx, const double* kscale, int64_t count, const int64_t* count_dev,
+                                 const int64_t* off, int64_t K, int64_t n, int64_t max_nk, int32_t* col, double* w,
+                                 int64_t* ext_dev, int64_t* prefix_scratch, DevStatus* st, cudaStream_t s);
+cudaError_t launch_set_extent(int64_t* ext_dev, int64_t value, cudaStream_t s);
+// Operand rows: out[r][j] = cvt(sqrt(w_j) * vec_{col_j}[r]) for r < v.len, j < ext, zero up to the padded extent.
+// mode: BMM_GEMM_BF16 (bf16), BMM_GEMM_SPLIT_BF16 (bf16 segments; `split_role` 0 = [hi|hi|lo], 1 = [hi|lo|hi]),
+//       BMM_GEMM_F64 (double).  ldo = storage row stride of out in elements.
+cudaError_t launch_gather_operand(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
+                                  int64_t ext_max, int mode, int split_role, bool apply_weight, void* out,
+                                  int64_t ldo, DevStatus* st, cudaStream_t s);
+
+// ---- gemm_tc.cu / gemm_f64.cu
+// out[M x N] (+)= A[M x K] * B[N x K]^T, A and B K-major bf16 with row strides lda/ldb (elements,
+// multiples of 8).  Columns >= kdim of A and B read as zero.  The K loop runs to
+// k_mult * round_up(*k_dev, 64) if k_dev, else to k_host (a multiple of 64).
+cudaError_t launch_gemm_bf16_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
+                                int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult,
+                                float* out, int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s);
+cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,
+                            int64_t k_host, const int64_t* k_dev, double* out, int64_t ldo, int accumulate,
+                            cudaStream_t s);
+bool tc_gemm_supported();
+
+// ---- backward.cu
+int64_t unique_scratch_bytes(int64_t space, int64_t count);
+// Distinct indices of idx[0..count) (values in [0, space)), ascending, with summed weights.
+cudaError_t launch_unique(const int32_t* idx, const double* scale, int64_t count, int64_t space,
+                          int32_t* uidx, double* uw, int64_t* ucount_dev, void* scratch, DevStatus* st,
+                          cudaStream_t s);
+cudaError_t launch_transpose_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg,
+                                         __nv_bfloat16* out, int64_t ldo, cudaStream_t s);
+cudaError_t launch_convert_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg,
+                                       __nv_bfloat16* out, int64_t ldo, cudaStream_t s);
+cudaError_t launch_convert_to_f64(const void* G, int dtype, int64_t rows, int64_t cols, int64_t ldg, bool transpose,
+                                  double* out, int64_t ldo, cudaStream_t s);
+// dst vector col_j (of a VecSet-shaped gradient) += w_j * src[j] (src: GEMM result, one row or column per j)
+cudaError_t launch_scatter_grad(void* dst, int dst_dtype, int64_t dst_ld, int dst_mode, int64_t len,
+                                const void* src, int src_dtype, int64_t src_ld, bool src_rows,
+                                const int32_t* col, const double* w, const int64_t* ext_dev, int64_t ext_max,
+                                cudaStream_t s);
+// out[j][r] = vec_{col_j}[r] for j < *ext_dev, zero rows up to jmax (bf16, or double if f64)
+cudaError_t launch_gather_rows(const VecSet& v, const int32_t* col, const int64_t* ext_dev, int64_t jmax, void* out,
+                               int64_t ldo, bool f64, cudaStream_t s);
+cudaError_t launch_zero_matrix(void* dst, int dtype, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s);
+
+}  // namespace bmm

@@ -1,0 +1,213 @@
+"""The sampled product as a sequence of C-ABI calls, and its torch.autograd.Function.
+
+Method presets (Table 2 of the paper, plus the block-sampling baselines of Sec. 1):
+
+  OPL     p eq. 3.8, c_k eq. 3.9 (needs ||M^k N_k||_F)        Alg. 2
+  ONC     p eq. 3.8, c_k eq. 4.2                               Alg. 2
+  ONU     p eq. 3.8, c_k eq. 4.7, pilot p0 = 1/n_k             Alg. 3
+  ONMCNR  p eq. 3.8, c_k eq. 4.7, pilot p0 = eq. 3.8           Alg. 3
+  UU      p = 1/n_k, c_k = c/K                                 Alg. 2
+  SSM     c whole blocks, p_k eq. 1.4                          block sampling
+  WU      c whole blocks, p_k eq. 1.2                          block sampling
+
+Only memory allocation and argument passing happen here; every arithmetic step runs in
+the CUDA kernels behind include/bmm.h.  For the Alg. 2/3 methods ``c`` counts outer
+products (the paper's c); for SSM/WU it counts blocks.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _abi as A
+
+COLUMN_METHODS = ("OPL", "ONC", "ONU", "ONMCNR", "UU")
+BLOCK_METHODS = ("SSM", "WU")
+METHODS = COLUMN_METHODS + BLOCK_METHODS
+MODES = {"f64": A.GEMM_F64, "bf16": A.GEMM_BF16, "split_bf16": A.GEMM_SPLIT_BF16}
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the sampled product runs on the GPU only: no CUDA device is available")
+    return torch
+
+
+def stream_id(replicate: int, purpose: int) -> int:
+    return (int(replicate) << 8) | int(purpose)
+
+
+def equal_budget(c_blocks: int, n: int, K: int) -> int:
+    """Outer products matching c whole blocks: L = round(c n / K)."""
+    return int(np.floor(c_blocks * n / K + 0.5))
+
+
+@dataclass
+class Problem:
+    """Device-resident M, N, block offsets, statistics buffers and one workspace."""
+    M: object
+    N: object
+    offsets: np.ndarray
+    offsets_dev: object
+    B: A.Blocks
+    ws: object
+    st: dict = field(default_factory=dict)
+
+    @property
+    def K(self) -> int:
+        return len(self.offsets) - 1
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[-1])
+
+
+def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode: int = A.GEMM_SPLIT_BF16,
+            ws=None) -> Problem:
+    torch = _torch()
+    off = np.asarray(offsets, dtype=np.int64)
+    n = int(off[-1])
+    max_nk = int(np.diff(off).max())
+    dev = M.device
+    off_dev = torch.as_tensor(off, device=dev)
+    B = A.blocks(off_dev, n, max_nk)
+    if ws is None:
+        need = max(A.bmm_workspace_size(M, N, B, unit, max_draws, gemm_mode),
+                   A.bmm_workspace_size(M, N, B, A.UNIT_COLUMN, max_draws, A.GEMM_F64))
+        if need == 0:
+            raise ValueError("invalid problem description")
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    if ws.data_ptr() % 256:
+        raise ValueError("workspace must be 256-byte aligned")
+    K = len(off) - 1
+    f64 = dict(dtype=torch.float64, device=dev)
+    st = {"x": torch.empty(n, **f64), "y": torch.empty(n, **f64), "a": torch.empty(K, **f64),
+          "s": torch.empty(K, **f64), "mf": torch.empty(K, **f64), "nf": torch.empty(K, **f64),
+          "f": torch.empty(K, **f64)}
+    A.bmm_clear_device_status(ws)
+    return Problem(M, N, off, off_dev, B, ws, st)
+
+
+def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
+        gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True) -> dict:
+    """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring)."""
+    torch = _torch()
+    M, N, B, ws, st = prob.M, prob.N, prob.B, prob.ws, prob.st
+    dev = M.device
+    K, n = prob.K, prob.n
+    sid = stream_id(replicate, A.PURPOSE_MAIN)
+    res = {"method": method, "c": c, "seed": seed, "sid": sid}
+    if out is None and compute_product:
+        out = torch.empty(M.shape[0], N.shape[1], device=dev,
+                          dtype=torch.float64 if gemm_mode == A.GEMM_F64 else torch.float32)
+    if method in BLOCK_METHODS:
+        pblk = torch.empty(K, dtype=torch.float64, device=dev)
+        if method == "SSM":
+            A.bmm_probs(M, N, B, A.P_BLK_NORMPROD, A.F_NONE, pblk, st, ws)
+        else:
+            A.bmm_probs(M, N, B, A.P_BLK_PRODNORM, A.F_EXACT, pblk, st, ws)
+        idx = torch.empty(c, dtype=torch.int32, device=dev)
+        scale = torch.empty(c, dtype=torch.float64, device=dev)
+        A.bmm_sample(pblk, A.UNIT_BLOCK, B, None, c, seed, sid, idx, scale, ws)
+        if compute_product:
+            A.bmm_apply(M, N, B, A.UNIT_BLOCK, idx, scale, c, gemm_mode, out, False, ws)
+        res.update(p=pblk, idx=idx, scale=scale, unit=A.UNIT_BLOCK, out=out, ck=None)
+        return res
+    if method not in COLUMN_METHODS:
+        raise ValueError(f"unknown method {method}")
+    p = torch.empty(n, dtype=torch.float64, device=dev)
+    ck = torch.empty(K, dtype=torch.int64, device=dev)
+    g = torch.empty(K, dtype=torch.float64, device=dev)
+    if method == "UU":
+        A.bmm_probs(None, None, B, A.P_COL_UNIFORM, A.F_NONE, p, None, ws)
+        A.bmm_blocksizes(None, None, B, None, A.CK_EQUAL, c, None, None, 0, ck, g, None, ws)
+    elif method == "OPL":
+        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_EXACT, p, st, ws)
+        A.bmm_blocksizes(M, N, B, st, A.CK_OPT, c, None, None, 0, ck, g, None, ws)
+    elif method == "ONC":
+        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
+        A.bmm_blocksizes(M, N, B, st, A.CK_HAT, c, None, None, 0, ck, g, None, ws)
+    else:  # Alg. 3: pilot sample, then c~_k
+        if c0 is None:
+            raise ValueError("two-step methods need c0")
+        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
+        if method == "ONU":
+            p0 = torch.empty(n, dtype=torch.float64, device=dev)
+            A.bmm_probs(None, None, B, A.P_COL_UNIFORM, A.F_NONE, p0, None, ws)
+        else:
+            p0 = p
+        per = max(1, c0 // K)
+        ck0 = torch.full((K,), per, dtype=torch.int64, device=dev)
+        pidx = torch.empty(K * per, dtype=torch.int32, device=dev)
+        pscale = torch.empty(K * per, dtype=torch.float64, device=dev)
+        A.bmm_sample(p0, A.UNIT_COLUMN, B, ck0, K * per, seed, stream_id(replicate, A.PURPOSE_PILOT), pidx, pscale, ws)
+        fhat = torch.empty(K, dtype=torch.float64, device=dev)
+        A.bmm_blocksizes(M, N, B, st, A.CK_TILDE, c, pidx, pscale, per, ck, g, fhat, ws)
+        res.update(p0=p0, pilot_idx=pidx, pilot_scale=pscale, fhat=fhat)
+    idx = torch.empty(c, dtype=torch.int32, device=dev)
+    scale = torch.empty(c, dtype=torch.float64, device=dev)
+    A.bmm_sample(p, A.UNIT_COLUMN, B, ck, c, seed, sid, idx, scale, ws)
+    if compute_product:
+        A.bmm_apply(M, N, B, A.UNIT_COLUMN, idx, scale, c, gemm_mode, out, False, ws)
+    res.update(p=p, ck=ck, g=g, idx=idx, scale=scale, unit=A.UNIT_COLUMN, out=out)
+    return res
+
+
+def check_status(prob: Problem):
+    code = A.bmm_read_device_status(prob.ws)
+    if code != A.OK:
+        raise A.BmmError(code, "device status")
+
+
+def sampled_matmul(M, N, offsets, method: str = "ONC", c: int = None, seed: int = 0, replicate: int = 0,
+                   c0: int | None = None, mode: str = "bf16"):
+    """CD approximating M @ N, differentiable in M and N (the sample and p are held fixed)."""
+    return SampledMatmul.apply(M, N, dict(offsets=offsets, method=method, c=c, seed=seed, replicate=replicate,
+                                          c0=c0, mode=mode))
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class _SampledMatmul(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, M, N, cfg):
+            gm = MODES[cfg["mode"]]
+            prob = prepare(M.detach(), N.detach(), cfg["offsets"], cfg["c"], gemm_mode=gm)
+            res = run(prob, cfg["method"], cfg["c"], cfg["seed"], cfg["replicate"], cfg["c0"], gemm_mode=gm)
+            ctx.prob = prob
+            ctx.cfg = cfg
+            ctx.res = {k: res[k] for k in ("p", "ck", "unit", "sid")}
+            return res["out"]
+
+        @staticmethod
+        def backward(ctx, G):
+            prob, cfg, res = ctx.prob, ctx.cfg, ctx.res
+            gm = MODES[cfg["mode"]]
+            gdt = torch.float64 if gm == A.GEMM_F64 else torch.float32
+            G = G.to(gdt).contiguous()
+            dM = torch.empty(prob.M.shape, dtype=gdt, device=G.device) if ctx.needs_input_grad[0] else None
+            dN = torch.empty(prob.N.shape, dtype=gdt, device=G.device) if ctx.needs_input_grad[1] else None
+            A.bmm_backward(G, prob.M, prob.N, prob.B, res["unit"], res["p"], res["ck"], cfg["c"], cfg["seed"],
+                           res["sid"], gm, dM, dN, False, prob.ws)
+            if dM is not None and dM.dtype != prob.M.dtype:
+                dM = dM.to(prob.M.dtype)
+            if dN is not None and dN.dtype != prob.N.dtype:
+                dN = dN.to(prob.N.dtype)
+            return dM, dN, None
+
+    return _SampledMatmul
+
+
+class _Lazy:
+    _fn = None
+
+    def apply(self, *args):
+        if _Lazy._fn is None:
+            _Lazy._fn = _autograd_function()
+        return _Lazy._fn.apply(*args)
+
+
+SampledMatmul = _Lazy()

@@ -1,0 +1,66 @@
+"""The C ABI library builds, loads without a GPU and exports every entry point of include/bmm.h."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2105_04940_gb300 import build, _abi
+    build()
+    return _abi.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "bmm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bmm_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2105_04940_gb300 import _abi
+    declared = _declared()
+    assert declared == sorted(_abi.EXPORTED)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_only_the_abi_is_exported():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_2105_04940_gb300", "libbmm.so")],
+                         capture_output=True, text=True).stdout
+    funcs = sorted(l.split()[-1] for l in out.splitlines() if " T " in l)
+    assert funcs == _declared()
+
+
+def test_status_strings_and_workspace_size_on_host(lib):
+    from paper_2105_04940_gb300 import _abi
+    assert _abi.status_string(0) == "ok"
+    assert "workspace" in _abi.status_string(_abi.ERR_WORKSPACE)
+    fake = 1 << 20  # never dereferenced: the size query only reads the descriptors
+    M = _abi.Mat(fake, 256, 4096, 4096, _abi.F32, _abi.ROW_MAJOR)
+    N = _abi.Mat(fake, 4096, 256, 256, _abi.F32, _abi.ROW_MAJOR)
+    B = _abi.Blocks(64, 4096, 64, fake)
+    sz = lib.bmm_workspace_size(ctypes.byref(M), ctypes.byref(N), ctypes.byref(B), _abi.UNIT_COLUMN, 1024,
+                                _abi.GEMM_SPLIT_BF16)
+    # at least the two split-BF16 operands (256 x 3*1024 bf16 each) plus the status block
+    assert sz >= 2 * 256 * 3 * 1024 * 2 + 256
+    bad = _abi.Mat(fake, 256, 4000, 4096, _abi.F32, _abi.ROW_MAJOR)
+    assert lib.bmm_workspace_size(ctypes.byref(bad), ctypes.byref(N), ctypes.byref(B), 0, 1024, 1) == 0
+    blk = lib.bmm_workspace_size(ctypes.byref(M), ctypes.byref(N), ctypes.byref(B), _abi.UNIT_BLOCK, 16,
+                                 _abi.GEMM_BF16)
+    assert blk >= 2 * 256 * 16 * 64 * 2
+
+
+def test_product_path_fails_loudly_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+    import paper_2105_04940_gb300 as P
+    with pytest.raises(RuntimeError):
+        P.prepare(torch.zeros(4, 4), torch.zeros(4, 4), np.array([0, 2, 4]), max_draws=2)

@@ -1,0 +1,362 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances, derived from the arithmetic of each step:
+  statistics, probabilities   1e-12 relative (FP64-accurate sums on both sides)
+  exact f_k (trace identity)  1e-10 relative (FP64-accurate dot products, cancellation in
+                              the off-diagonal terms)
+  block sizes, sample indices bit-exact given identical FP64 inputs
+  sampled product             |CD_gpu - CD| <= tol * sum_t scale_t |M_{h,i_t}| |N_{i_t,f}| with
+                              tol = 2^-7 + L 2^-22 (BF16: two operand roundings of 2^-8 plus
+                              FP32 accumulation), 2^-14 + L 2^-22 (split BF16: hi+lo keeps
+                              ~16 bits, lo*lo dropped), 1e-13 + L 2^-52 (FP64)
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from tests._gpu_util import as_layout, host, product_bound, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bmm():
+    import paper_2105_04940_gb300 as P
+    P.build()
+    P._abi.load()
+    assert torch.cuda.is_available()
+    return P
+
+
+def _problem(m, n, p, K, seed, dtype=np.float64, lo=None, hi=None, sigma=1.0):
+    if lo is None:
+        off = S.block_offsets_equal(n, K)
+    else:
+        off = S.block_offsets_uneven(n, K, lo, hi, seed=seed)
+    M, N = S.scaled_gaussian(m, n, p, off, sigma, seed=seed + 1, dtype=np.float64)
+    if dtype == "bf16":
+        Mt, Nt = to_dev(M, torch.bfloat16), to_dev(N, torch.bfloat16)
+        M, N = host(Mt.double()), host(Nt.double())
+    else:
+        Mt, Nt = to_dev(M.astype(dtype)), to_dev(N.astype(dtype))
+        M, N = M.astype(dtype).astype(np.float64), N.astype(dtype).astype(np.float64)
+    return off, M, N, Mt, Nt
+
+
+def _tol(mode, L):
+    if mode == "bf16":
+        return 2.0 ** -7 + L * 2.0 ** -22
+    if mode == "split_bf16":
+        return 2.0 ** -14 + L * 2.0 ** -22
+    return 1e-13 + L * 2.0 ** -52
+
+
+# ---------------------------------------------------------------- statistics and probabilities
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, "bf16"])
+@pytest.mark.parametrize("layouts", [("row", "row"), ("col", "col"), ("row", "col")])
+def test_stats_and_probs(bmm, dtype, layouts):
+    off, M, N, Mt, Nt = _problem(203, 3001, 157, 37, seed=3, dtype=dtype, lo=40, hi=120)
+    Mt, Nt = as_layout(Mt, layouts[0]), as_layout(Nt, layouts[1])
+    prob = bmm.prepare(Mt, Nt, off, max_draws=500)
+    p = torch.empty(3001, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_NONE, p, prob.st, prob.ws)
+    bmm.check_status(prob)
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    assert rel_err(host(prob.st["x"]), x) < 1e-12
+    assert rel_err(host(prob.st["y"]), y) < 1e-12
+    for k in ("a", "s", "mf", "nf"):
+        assert rel_err(host(prob.st[k]), st[k]) < 1e-12, k
+    assert rel_err(host(p), oracle.p_col_opt(st["w"], st["a"], off)) < 1e-12
+    # block probabilities of eq. 1.4 and uniform ones, reusing the statistics
+    pb = torch.empty(37, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_BLK_NORMPROD, bmm._abi.F_NONE | bmm._abi.REUSE_STATS, pb, prob.st, prob.ws)
+    assert rel_err(host(pb), oracle.p_blk_normprod(st["mf"], st["nf"])) < 1e-12
+    bmm.bmm_probs(None, None, prob.B, bmm._abi.P_COL_UNIFORM, bmm._abi.F_NONE, p, None, prob.ws)
+    np.testing.assert_array_equal(host(p), oracle.p_col_uniform(off))
+    bmm.check_status(prob)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_exact_block_frobenius(bmm, dtype):
+    off, M, N, Mt, Nt = _problem(150, 1400, 90, 20, seed=5, dtype=dtype, lo=20, hi=110)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=300)
+    pb = torch.empty(20, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_BLK_PRODNORM, bmm._abi.F_EXACT, pb, prob.st, prob.ws)
+    bmm.check_status(prob)
+    f = oracle.block_frob_sq(M, N, off)
+    assert rel_err(host(prob.st["f"]), f) < 1e-10
+    assert rel_err(host(pb), oracle.p_blk_prodnorm(f)) < 1e-10
+
+
+# ---------------------------------------------------------------- block sizes (identical inputs)
+@pytest.mark.parametrize("kind", ["opt", "hat", "equal"])
+def test_blocksizes_bit_exact(bmm, kind):
+    rng = np.random.default_rng(9)
+    K = 300
+    nk = rng.integers(1, 200, size=K)
+    off = np.concatenate([[0], np.cumsum(nk)]).astype(np.int64)
+    n = int(off[-1])
+    a = rng.lognormal(0, 2, size=K)
+    f = a * a * rng.uniform(0, 1, size=K)
+    f[::17] = a[::17] ** 2  # rank-one aligned blocks: g = 0
+    dev = torch.device("cuda:0")
+    st = {k: torch.zeros(K if k not in ("x", "y") else n, dtype=torch.float64, device=dev)
+          for k in ("x", "y", "a", "s", "mf", "nf", "f")}
+    st["a"].copy_(torch.from_numpy(a))
+    st["f"].copy_(torch.from_numpy(f))
+    off_dev = torch.as_tensor(off, device=dev)
+    B = bmm._abi.blocks(off_dev, n, int(nk.max()))
+    ws = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+    ck = torch.empty(K, dtype=torch.int64, device=dev)
+    g = torch.empty(K, dtype=torch.float64, device=dev)
+    ckind = {"opt": bmm._abi.CK_OPT, "hat": bmm._abi.CK_HAT, "equal": bmm._abi.CK_EQUAL}[kind]
+    gw = {"opt": oracle.g_opt(a, f), "hat": oracle.g_hat(a), "equal": oracle.g_equal(K)}[kind]
+    for c in (K, K + 1, 2 * K + 7, n // 3, n - 1, n):
+        bmm.bmm_blocksizes(None, None, B, st, ckind, c, None, None, 0, ck, g, None, ws)
+        assert bmm.bmm_read_device_status(ws) == 0
+        want = oracle.apportion(oracle.g_with_fallback(gw, a, nk), nk, c)
+        np.testing.assert_array_equal(host(ck), want, err_msg=f"c={c}")
+        np.testing.assert_array_equal(host(g), oracle.g_with_fallback(gw, a, nk))
+    with pytest.raises(bmm.BmmError):
+        bmm.bmm_blocksizes(None, None, B, st, ckind, K - 1, None, None, 0, ck, g, None, ws)
+
+
+# ---------------------------------------------------------------- sampler (identical p)
+@pytest.mark.parametrize("seed", [0, 1, 2 ** 40 + 5])
+def test_sampler_bit_exact_columns(bmm, seed):
+    off = S.block_offsets_uneven(5000, 40, 20, 400, seed=seed % 97)
+    p = S.random_probabilities(off, seed=seed % 89, zero_frac=0.2)
+    K = 40
+    nk = np.diff(off)
+    ck = oracle.apportion(oracle.g_hat(np.ones(K)), nk, 1500)
+    sid = oracle.stream_id(3, oracle.PURPOSE_MAIN)
+    want_idx, want_scale = oracle.sample_alg2(p, off, ck, seed, sid)
+    dev = torch.device("cuda:0")
+    off_dev = torch.as_tensor(off, device=dev)
+    B = bmm._abi.blocks(off_dev, 5000, int(nk.max()))
+    ws = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+    idx = torch.empty(1500, dtype=torch.int32, device=dev)
+    scale = torch.empty(1500, dtype=torch.float64, device=dev)
+    bmm.bmm_sample(to_dev(p), bmm._abi.UNIT_COLUMN, B, to_dev(ck), 1500, seed, sid, idx, scale, ws)
+    assert bmm.bmm_read_device_status(ws) == 0
+    np.testing.assert_array_equal(host(idx), want_idx)
+    np.testing.assert_array_equal(host(scale), want_scale)
+
+
+def test_sampler_bit_exact_blocks_and_long_segment(bmm):
+    dev = torch.device("cuda:0")
+    ws = torch.zeros(1 << 22, dtype=torch.uint8, device=dev)
+    # one segment longer than a scan tile (K = 1: Alg. 1)
+    n = 70000
+    off = np.array([0, n])
+    p = S.random_probabilities(off, seed=4, zero_frac=0.5)
+    B = bmm._abi.blocks(torch.as_tensor(off, device=dev), n, n)
+    idx = torch.empty(3000, dtype=torch.int32, device=dev)
+    scale = torch.empty(3000, dtype=torch.float64, device=dev)
+    bmm.bmm_sample(to_dev(p), bmm._abi.UNIT_COLUMN, B, to_dev(np.array([3000])), 3000, 77, 0, idx, scale, ws)
+    wi, wsc = oracle.sample_alg2(p, off, np.array([3000]), 77, 0)
+    np.testing.assert_array_equal(host(idx), wi)
+    np.testing.assert_array_equal(host(scale), wsc)
+    # block sampling over K blocks
+    off = S.block_offsets_uneven(20000, 2500, 4, 12, seed=1)
+    pb = S.random_probabilities(np.array([0, 2500]), seed=2, zero_frac=0.3)
+    B = bmm._abi.blocks(torch.as_tensor(off, device=dev), 20000, 12)
+    idx = torch.empty(700, dtype=torch.int32, device=dev)
+    scale = torch.empty(700, dtype=torch.float64, device=dev)
+    bmm.bmm_sample(to_dev(pb), bmm._abi.UNIT_BLOCK, B, None, 700, 5, 1, idx, scale, ws)
+    assert bmm.bmm_read_device_status(ws) == 0
+    wi, wsc = oracle.sample_blocks(pb, 700, 5, 1)
+    np.testing.assert_array_equal(host(idx), wi)
+    np.testing.assert_array_equal(host(scale), wsc)
+
+
+# ---------------------------------------------------------------- sampled product
+@pytest.mark.parametrize("mode", ["f64", "bf16", "split_bf16"])
+@pytest.mark.parametrize("shape", [(300, 2000, 520), (70, 1200, 100)])
+@pytest.mark.parametrize("layouts", [("row", "row"), ("col", "row")])
+def test_apply_columns(bmm, mode, shape, layouts):
+    m, n, p = shape
+    off, M, N, Mt, Nt = _problem(m, n, p, 25, seed=11, dtype=np.float32, lo=20, hi=140)
+    Mt, Nt = as_layout(Mt, layouts[0]), as_layout(Nt, layouts[1])
+    L = 517
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L)
+    r = bmm.run(prob, "ONC", L, seed=4, gemm_mode=bmm.MODES[mode])
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]), host(r["scale"])
+    want = oracle.sampled_product_columns(M, N, idx, scale)
+    bound = product_bound(M, N, idx, scale)
+    got = host(r["out"]).astype(np.float64)
+    assert np.all(np.abs(got - want) <= _tol(mode, L) * bound + 1e-300), np.max(np.abs(got - want) / bound)
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16"])
+def test_apply_blocks(bmm, mode):
+    off, M, N, Mt, Nt = _problem(260, 3000, 300, 50, seed=12, dtype=np.float32, lo=10, hi=110)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=9, unit=bmm._abi.UNIT_BLOCK)
+    r = bmm.run(prob, "SSM", 9, seed=2, gemm_mode=bmm.MODES[mode])
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]), host(r["scale"])
+    want = oracle.sampled_product_blocks(M, N, off, idx, scale)
+    bound = product_bound(M, N, idx, scale, off, unit="block")
+    L = int(sum(off[k + 1] - off[k] for k in idx))
+    got = host(r["out"]).astype(np.float64)
+    assert np.all(np.abs(got - want) <= _tol(mode, L) * bound + 1e-300)
+
+
+def test_apply_accumulate_and_empty(bmm):
+    off, M, N, Mt, Nt = _problem(64, 256, 64, 4, seed=13, dtype=np.float64)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=16)
+    out = torch.ones(64, 64, dtype=torch.float64, device=Mt.device)
+    idx = to_dev(np.arange(0, 256, 16).astype(np.int32))
+    scale = to_dev(np.full(16, 2.0))
+    bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, idx, scale, 16, bmm._abi.GEMM_F64, out, True, prob.ws)
+    want = 1.0 + 2.0 * M[:, ::16] @ N[::16, :]
+    np.testing.assert_allclose(host(out), want, rtol=1e-12, atol=1e-12)
+    bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, idx, scale, 0, bmm._abi.GEMM_F64, out, False, prob.ws)
+    assert np.all(host(out) == 0.0)
+
+
+def test_every_index_once_reproduces_product(bmm):
+    off, M, N, Mt, Nt = _problem(200, 640, 180, 10, seed=14, dtype=np.float64)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=640)
+    out = torch.empty(200, 180, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, to_dev(np.arange(640, dtype=np.int32)),
+                  to_dev(np.ones(640)), 640, bmm._abi.GEMM_F64, out, False, prob.ws)
+    np.testing.assert_allclose(host(out), M @ N, rtol=1e-12, atol=1e-10)
+
+
+# ---------------------------------------------------------------- methods end to end
+@pytest.mark.parametrize("method", ["OPL", "ONC", "ONU", "ONMCNR", "UU", "SSM", "WU"])
+def test_methods_match_oracle(bmm, method):
+    off = S.block_offsets_equal(4096, 64)
+    M, N = S.scaled_gaussian(256, 4096, 256, off, 1.0, seed=1)
+    Mt, Nt = to_dev(M), to_dev(N)
+    c = 16 if method in ("SSM", "WU") else 1024
+    prob = bmm.prepare(Mt, Nt, off, max_draws=1024, unit=bmm._abi.UNIT_BLOCK if method in ("SSM", "WU") else 0)
+    r = bmm.run(prob, method, c, seed=7, c0=256, gemm_mode=bmm._abi.GEMM_F64)
+    bmm.check_status(prob)
+    o = oracle.run_method(M, N, off, method, c, seed=7, c0=256)
+    assert rel_err(host(r["p"]), o["p"]) < 1e-12
+    if "ck" in o:
+        np.testing.assert_array_equal(host(r["ck"]), o["ck"])
+    if "fhat" in o:
+        assert rel_err(host(r["fhat"]), o["fhat"]) < 1e-10
+    np.testing.assert_array_equal(host(r["idx"]), o["idx"])
+    np.testing.assert_allclose(host(r["scale"]), o["scale"], rtol=1e-12)
+    np.testing.assert_allclose(host(r["out"]), o["CD"], rtol=1e-10, atol=1e-10 * np.abs(o["CD"]).max())
+
+
+def test_tilde_block_sizes_from_pilot(bmm):
+    off = S.block_offsets_uneven(3000, 30, 40, 160, seed=2)
+    M, N = S.scaled_gaussian(120, 3000, 90, off, 1.5, seed=3)
+    Mt, Nt = to_dev(M), to_dev(N)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=2000)
+    r = bmm.run(prob, "ONU", 600, seed=3, c0=30 * 40, gemm_mode=bmm._abi.GEMM_F64)
+    bmm.check_status(prob)
+    fhat, pidx, pscale, _ = None, host(r["pilot_idx"]), host(r["pilot_scale"]), None
+    fh_or, idx_or, sc_or = oracle.pilot_frob_sq(M, N, off, oracle.p_col_uniform(off), 40, seed=3,
+                                                sid=oracle.stream_id(0, oracle.PURPOSE_PILOT))
+    np.testing.assert_array_equal(pidx, idx_or)
+    np.testing.assert_array_equal(pscale, sc_or)
+    assert rel_err(host(r["fhat"]), fh_or) < 1e-10
+    # the integer decision, given the GPU's own fhat, is the oracle's
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    g = oracle.g_tilde(host(prob.st["a"]), host(r["fhat"]))
+    np.testing.assert_array_equal(host(r["ck"]), oracle.apportion(oracle.g_with_fallback(g, st["a"], np.diff(off)), np.diff(off), 600))
+
+
+# ---------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("mode", ["f64", "bf16"])
+@pytest.mark.parametrize("unit", ["column", "block"])
+def test_backward(bmm, mode, unit):
+    off, M, N, Mt, Nt = _problem(136, 1500, 200, 15, seed=21, dtype=np.float32 if mode == "bf16" else np.float64,
+                                 lo=40, hi=160)
+    method, c = ("ONC", 400) if unit == "column" else ("SSM", 6)
+    gm = bmm.MODES[mode]
+    prob = bmm.prepare(Mt, Nt, off, max_draws=c, unit=bmm._abi.UNIT_BLOCK if unit == "block" else 0)
+    r = bmm.run(prob, method, c, seed=8, gemm_mode=gm)
+    G = np.random.default_rng(5).standard_normal((136, 200))
+    gdt = torch.float64 if mode == "f64" else torch.float32
+    Gt = to_dev(G.astype(np.float64 if mode == "f64" else np.float32))
+    dM = torch.full(Mt.shape, 7.0, dtype=gdt, device=Mt.device)
+    dN = torch.full(Nt.shape, 7.0, dtype=gdt, device=Mt.device)
+    bmm.bmm_backward(Gt, Mt, Nt, prob.B, r["unit"], r["p"], r["ck"], c, 8, r["sid"], gm, dM, dN, False, prob.ws)
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]), host(r["scale"])
+    Gd = host(Gt).astype(np.float64)
+    if unit == "column":
+        wM, wN = oracle.adjoint_columns(M, N, idx, scale, Gd)
+    else:
+        wM, wN = oracle.adjoint_blocks(M, N, off, idx, scale, Gd)
+    tol = 1e-11 if mode == "f64" else 2.0 ** -7 + 300 * 2.0 ** -22
+    # error scale: the same sums with absolute values
+    if unit == "column":
+        bM, bN = oracle.adjoint_columns(np.abs(M), np.abs(N), idx, scale, np.abs(Gd))
+    else:
+        bM, bN = oracle.adjoint_blocks(np.abs(M), np.abs(N), off, idx, scale, np.abs(Gd))
+    assert np.all(np.abs(host(dM) - wM) <= tol * bM + 1e-300)
+    assert np.all(np.abs(host(dN) - wN) <= tol * bN + 1e-300)
+    # accumulate=1 adds onto the existing gradient
+    dM2 = torch.ones_like(dM)
+    bmm.bmm_backward(Gt, Mt, Nt, prob.B, r["unit"], r["p"], r["ck"], c, 8, r["sid"], gm, dM2, None, True, prob.ws)
+    np.testing.assert_allclose(host(dM2) - 1.0, host(dM), rtol=1e-6 if mode == "bf16" else 1e-13,
+                               atol=1e-6 * np.abs(host(dM)).max())
+
+
+def test_autograd_function(bmm):
+    off = S.block_offsets_equal(512, 8)
+    M, N = S.scaled_gaussian(64, 512, 64, off, 1.0, seed=11)
+    Mt = to_dev(M).requires_grad_(True)
+    Nt = to_dev(N).requires_grad_(True)
+    out = bmm.sampled_matmul(Mt, Nt, off, method="ONC", c=128, seed=5, mode="f64")
+    R = to_dev(np.random.default_rng(12).standard_normal((64, 64)))
+    (out * R).sum().backward()
+    r = oracle.run_method(M, N, off, "ONC", 128, seed=5)
+    wM, wN = oracle.adjoint_columns(M, N, r["idx"], r["scale"], host(R))
+    np.testing.assert_allclose(host(Mt.grad), wM, rtol=1e-10, atol=1e-10 * np.abs(wM).max())
+    np.testing.assert_allclose(host(Nt.grad), wN, rtol=1e-10, atol=1e-10 * np.abs(wN).max())
+
+
+# ---------------------------------------------------------------- device-detected conditions
+def test_device_status_conditions(bmm):
+    off, M, N, Mt, Nt = _problem(32, 128, 16, 4, seed=30, dtype=np.float64)
+    Mt[3, 5] = float("nan")
+    prob = bmm.prepare(Mt, Nt, off, max_draws=32)
+    p = torch.empty(128, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_NONE, p, prob.st, prob.ws)
+    assert bmm.bmm_read_device_status(prob.ws) == bmm._abi.ERR_NONFINITE
+    bmm.bmm_clear_device_status(prob.ws)
+    assert bmm.bmm_read_device_status(prob.ws) == 0
+    # a probability segment without mass
+    pz = torch.zeros(128, dtype=torch.float64, device=Mt.device)
+    ck = to_dev(np.full(4, 2, dtype=np.int64))
+    idx = torch.empty(8, dtype=torch.int32, device=Mt.device)
+    sc = torch.empty(8, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_sample(pz, bmm._abi.UNIT_COLUMN, prob.B, ck, 8, 1, 0, idx, sc, prob.ws)
+    assert bmm.bmm_read_device_status(prob.ws) == bmm._abi.ERR_ARG
+    bmm.bmm_clear_device_status(prob.ws)
+    # c_k that do not add up to c
+    bmm.bmm_sample(to_dev(oracle.p_col_uniform(off)), bmm._abi.UNIT_COLUMN, prob.B, ck, 7, 1, 0, idx, sc, prob.ws)
+    assert bmm.bmm_read_device_status(prob.ws) == bmm._abi.ERR_INFEASIBLE
+    bmm.bmm_clear_device_status(prob.ws)
+    # offsets that are not increasing (validated on the device, nothing read out of range)
+    bad = to_dev(np.array([0, 40, 30, 90, 128], dtype=np.int64))
+    Bbad = bmm._abi.blocks(bad, 128, 60)
+    Mt[3, 5] = 0.0
+    bmm.bmm_probs(Mt, Nt, Bbad, bmm._abi.P_COL_OPT, bmm._abi.F_NONE, p, prob.st, prob.ws)
+    assert bmm.bmm_read_device_status(prob.ws) == bmm._abi.ERR_SHAPE
+    bmm.bmm_clear_device_status(prob.ws)
+    # host-side rejections
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, idx, sc, 8, bmm._abi.GEMM_BF16,
+                      torch.empty(32, 16, dtype=torch.float64, device=Mt.device), False, prob.ws)
+    assert e.value.code == bmm._abi.ERR_DTYPE
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, idx, sc, 8, bmm._abi.GEMM_F64,
+                      torch.empty(32, 16, dtype=torch.float64, device=Mt.device), False, prob.ws[:100])
+    assert e.value.code == bmm._abi.ERR_WORKSPACE
