@@ -1,0 +1,483 @@
+#!/usr/bin/env python
+"""Benchmark: milliseconds per approximate product (randomized block matrix multiplication).
+
+Workload (the large FP32 configuration): M 8192 x 65536 and N 65536 x 8192, FP32, entries
+N(0,1) * s_k with s_k ~ LogNormal(0, 1.5) shared by column block k of M and row block k of N;
+K = 1024 blocks with sizes drawn uniformly from {16..128} and adjusted to sum to n; c = K/8 = 128
+blocks, i.e. L = round(c n / K) = 8192 outer products for the Alg. 2 methods.
+
+A step is one approximate product by the A-optimal method (OPL: statistics pass, exact
+||M^k N_k||_F, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
+BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flush is
+needed).  Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ms per approx product at fixed rel-Frobenius error vs exact GEMM; % roofline"
+WORKLOAD = dict(m=8192, n=65536, p=8192, K=1024, nk_lo=16, nk_hi=128, sigma=1.5, c_blocks=128, data_seed=3)
+SMALL = dict(m=256, n=4096, p=256, K=64, nk_lo=64, nk_hi=64, sigma=1.0, c_blocks=16, data_seed=1)
+# profiling case: the large workload's n, K and blocks with m = p = 2048 (inputs 1 GB, > L2)
+PROFILE = dict(WORKLOAD, m=2048, p=2048)
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
+# committed ncu capture (profiles/); None until a capture of the current kernel exists.
+TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--method", default="OPL")
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "split_bf16", "f64"])
+    ap.add_argument("--small", action="store_true", help="256 x 4096 x 256 case (L2-resident)")
+    ap.add_argument("--profile-case", action="store_true", help="2048 x 65536 x 2048 case for ncu captures")
+    ap.add_argument("--quick", action="store_true", help="skip e2e, methods, error and CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-methods", action="store_true")
+    ap.add_argument("--no-error", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    if args.small:
+        return SMALL
+    return PROFILE if args.profile_case else WORKLOAD
+
+
+def offsets_of(w):
+    import synthetic as S
+    if w["nk_lo"] == w["nk_hi"]:
+        return S.block_offsets_equal(w["n"], w["K"])
+    return S.block_offsets_uneven(w["n"], w["K"], w["nk_lo"], w["nk_hi"], seed=w["data_seed"])
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm": d["hbm_gbs"], "bf16": d["bf16_tflops"], "bf16_sustained": d.get("bf16_tflops_sustained"),
+                "sm_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "sm_mhz": 2070.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "native" else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+def oracle_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads", 1) for d in threadpool_info() if d.get("user_api") == "blas"]
+        return int(max(n)) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_sample(w, method, sub=256, seed=11):
+    """The oracle's pipeline on a bounded sample: the same n, K and blocks with m' = p' = sub rows of M
+    and columns of N; each stage's time is scaled to the full m, p by its work ratio."""
+    import oracle
+    import synthetic as S
+    off = offsets_of(w)
+    M, N = S.scaled_gaussian(sub, w["n"], sub, off, w["sigma"], seed=seed)
+    L = oracle.equal_budget(w["c_blocks"], w["n"], w["K"])
+    nk = np.diff(off)
+    t = {}
+    t0 = time.perf_counter()
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    t["stats"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    f = oracle.block_frob_sq(M, N, off) if method in ("OPL", "WU") else None
+    t["exact_f"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    p = oracle.p_col_opt(st["w"], st["a"], off)
+    ck = oracle.apportion(oracle.g_with_fallback(oracle.g_opt(st["a"], f) if f is not None else oracle.g_hat(st["a"]),
+                                                 st["a"], nk), nk, L)
+    idx, scale = oracle.sample_alg2(p, off, ck, seed, 0)
+    t["design_sample"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.sampled_product_columns(M, N, idx, scale)
+    t["product"] = time.perf_counter() - t0
+    m, pp = w["m"], w["p"]
+    scale_f = {"stats": (m + pp) / (2 * sub), "exact_f": (m * pp) / (sub * sub), "design_sample": 1.0,
+               "product": (m * pp) / (sub * sub)}
+    est = sum(t[k] * scale_f[k] for k in t)
+    return est * 1e3, t, f"m'=p'={sub} of {m} rows of M / {pp} columns of N, full n={w['n']}, K={w['K']}, L={L}; " \
+                         f"stage times scaled by (m+p)/(m'+p') (statistics) and mp/(m'p') (f_k, product)"
+
+
+def reference_arm(args, ws, rank):
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    w = workload(args)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, args.method, sub=64)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, _, sample = cpu_oracle_sample(w, args.method, sub=64)
+        vals.append(v)
+    wall = time.perf_counter() - t_all
+    value = float(np.mean(vals))
+    cores = oracle_cores()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(args.steps, 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "method": args.method},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def workload_name(args):
+    w = workload(args)
+    return (f"M {w['m']}x{w['n']} @ N {w['n']}x{w['p']} FP32, N(0,1)*LogNormal(0,{w['sigma']}) block scales, "
+            f"K={w['K']} blocks of {w['nk_lo']}..{w['nk_hi']}, c=K/8={w['c_blocks']} blocks "
+            f"(L={int(np.floor(w['c_blocks'] * w['n'] / w['K'] + 0.5))} outer products)")
+
+
+# ---------------------------------------------------------------- native arm
+def stage_work(w, L, nk, method):
+    """Algorithmic work per product of each stage (bytes for HBM-bound, flops for compute-bound)."""
+    m, n, p = w["m"], w["n"], w["p"]
+    return {
+        "stats": {"bound": "hbm", "bytes": (m * n + n * p) * 4 + 8 * (2 * n + 4 * w["K"])},
+        "exact_f": {"bound": "alu", "flops": float(2 * (m + p) * np.sum(nk.astype(np.float64) ** 2))},
+        "apply": {"bound": "tensor", "flops": float(2 * m * p * L)},
+    }
+
+
+def native_arm(args, ws, rank, local):
+    import torch
+
+    import paper_2105_04940_gb300 as P
+    import synthetic as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.build()
+    w = workload(args)
+    off = offsets_of(w)
+    nk = np.diff(off)
+    K, n = w["K"], w["n"]
+    L = P.equal_budget(w["c_blocks"], n, K)
+    c = L if args.method not in ("SSM", "WU") else w["c_blocks"]
+    gm = P.MODES[args.mode]
+    M, N, _ = S.scaled_gaussian_torch(w["m"], n, w["p"], off, w["sigma"], w["data_seed"] + 1000 * rank,
+                                      dtype=torch.float64 if args.mode == "f64" else torch.float32, device=dev)
+    unit = 1 if args.method in ("SSM", "WU") else 0
+    prob = P.prepare(M, N, off, max_draws=max(c, L), unit=unit, gemm_mode=gm)
+    out = torch.empty(w["m"], w["p"], device=dev, dtype=torch.float64 if args.mode == "f64" else torch.float32)
+    c0 = 4 * K
+
+    def step(s, events=None):
+        return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events)
+
+    for s in range(args.warmup):
+        step(10_000 + s)
+    torch.cuda.synchronize()
+    P.check_status(prob)
+
+    # ---- timed region: K steps, per-stage events on the launching (current) stream
+    stage_ev = []
+    barrier(ws)
+    torch.cuda.synchronize()
+    n_launch0 = P._abi.bmm_launch_count()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record()
+        for s in range(args.steps):
+            ev = []
+            step(s, ev)
+            stage_ev.append(ev)
+        t_end.record()
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = P._abi.bmm_launch_count() - n_launch0
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), ws, dev)
+    P.check_status(prob)
+    stages = {}
+    for ev in stage_ev:
+        for (a, ea), (b, eb) in zip(ev[:-1], ev[1:]):
+            stages[b] = stages.get(b, 0.0) + ea.elapsed_time(eb)
+    stages = {k: v / args.steps for k, v in stages.items()}
+    ms_step = elapsed_ms / args.steps
+    value = elapsed_ms / (args.steps * ws)
+
+    pk = peaks()
+    work = stage_work(w, L, nk, args.method)
+    roof_all = {}
+    for name, wk in work.items():
+        if name not in stages:
+            continue
+        t = stages[name] * 1e-3
+        if wk["bound"] == "hbm":
+            ach = wk["bytes"] / t / 1e9
+            roof_all[name] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+                              "frac": ach / pk["hbm"], "ms": stages[name]}
+        elif wk["bound"] == "tensor":
+            ach = wk["flops"] / t / 1e12
+            peak = pk["bf16_sustained"] or pk["bf16"]
+            roof_all[name] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                              "frac": ach / peak, "ms": stages[name]}
+        else:
+            # FP32 CUDA-core FMA peak: 152 SMs x 128 lanes x 2 flops x max SM clock
+            peak = 152 * 128 * 2 * pk["sm_mhz"] * 1e6 / 1e12
+            ach = wk["flops"] / t / 1e12
+            roof_all[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                              "frac": ach / peak, "ms": stages[name]}
+    dom = max(roof_all, key=lambda k: roof_all[k]["ms"]) if roof_all else None
+    roofline = None
+    if dom is not None:
+        r = dict(roof_all[dom])
+        r["kernel"] = dom
+        r["traffic"] = TRAFFIC.get(dom)
+        r["peak_source"] = pk["source"] + (" (sustained bf16)" if r["bound"] == "tensor" else "")
+        roofline = r
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.mode, "data": "synthetic",
+        "config": {"workload": workload_name(args), "method": args.method, "gemm": args.mode, "c": c,
+                   "l2": "small case, L2-resident" if args.small else "inputs larger than the 129 MB L2, no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline, "stages_ms": stages, "stage_rooflines": roof_all,
+        "clocks": clk.summary(), "gpu_launches": int(launches),
+    }
+
+    if rank == 0 and not args.quick:
+        # ---- exact GEMM baselines and the measured error at this c (outside the timed region)
+        if not args.no_error:
+            result.update(error_and_baselines(P, prob, args, w, c, gm, out, dev))
+        if not args.no_methods:
+            result["methods_ms"] = time_methods(P, prob, args, w, L, gm, out, c0, rank)
+    if not args.quick and not args.no_e2e:
+        result["e2e"] = e2e(P, prob, args, w, c, gm, out, c0, rank, ws, dev)
+    if rank == 0 and not args.quick and not args.no_cpu_baseline:
+        v, t, sample = cpu_oracle_sample(w, args.method)
+        result["cpu_baseline"] = {"value": v, "unit": "ms", "cores": oracle_cores(), "kind": "oracle",
+                                  "sample": sample, "stage_seconds": t}
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def error_and_baselines(P, prob, args, w, c, gm, out, dev):
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    M, N = prob.M, prob.N
+    ex = torch.matmul(M, N)  # exact FP32 GEMM (TF32 off)
+    torch.cuda.synchronize()
+
+    def timeit(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    t_fp32 = timeit(lambda: torch.matmul(M, N, out=ex), reps=3)
+    torch.backends.cuda.matmul.allow_tf32 = True
+    t_tf32 = timeit(lambda: torch.matmul(M, N), reps=3)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Mb, Nb = M.to(torch.bfloat16), N.to(torch.bfloat16)
+    t_bf16 = timeit(lambda: torch.matmul(Mb, Nb), reps=5)
+    del Mb, Nb
+    ex_norm = torch.linalg.norm(ex.double()).item()
+    errs, exps = [], []
+    for s in range(8):
+        r = P.run(prob, args.method, c, seed=50_000 + s, c0=4 * w["K"], gemm_mode=gm, out=out)
+        errs.append(torch.linalg.norm((out - ex).double()).item() / ex_norm)
+        if args.method in ("OPL", "ONC", "ONU", "ONMCNR", "UU"):
+            x, y = prob.st["x"].double(), prob.st["y"].double()
+            p = r["p"].double()
+            xy = x * y
+            q = torch.where(p > 0, xy / torch.where(p > 0, p, torch.ones_like(p)), torch.zeros_like(p))
+            seg = torch.repeat_interleave(torch.arange(prob.K, device=dev), torch.as_tensor(np.diff(prob.offsets), device=dev))
+            qk = torch.zeros(prob.K, dtype=torch.float64, device=dev).index_add_(0, seg, q)
+            f = prob.st["f"] if args.method == "OPL" else None
+            if f is None:  # f_k for the closed form (computed once, outside the timed region)
+                P.bmm_probs(prob.M, prob.N, prob.B, P._abi.P_COL_OPT, P._abi.F_EXACT | P._abi.REUSE_STATS, None,
+                            prob.st, prob.ws)
+                f = prob.st["f"]
+            E = torch.sum((qk - f) / r["ck"].double()).item()
+            exps.append(np.sqrt(max(E, 0.0)) / ex_norm)
+    rms = float(np.sqrt(np.mean(np.square(errs))))
+    res = {"exact_fp32_gemm_ms": t_fp32, "exact_tf32_gemm_ms": t_tf32, "exact_bf16_gemm_ms": t_bf16,
+           "rel_err_rms": rms, "rel_err_seeds": len(errs)}
+    if exps:
+        res["rel_err_expected"] = float(np.mean(exps))
+        res["rel_err_ratio"] = rms / float(np.mean(exps))
+    return res
+
+
+def time_methods(P, prob, args, w, L, gm, out, c0, rank):
+    import torch
+    res = {}
+    for meth in ("OPL", "ONC", "ONU", "ONMCNR", "UU", "SSM", "WU"):
+        c = L if meth not in ("SSM", "WU") else w["c_blocks"]
+        if meth in ("SSM", "WU"):
+            unit_prob = P.prepare(prob.M, prob.N, prob.offsets, max_draws=c, unit=1, gemm_mode=gm)
+        else:
+            unit_prob = prob
+        P.run(unit_prob, meth, c, seed=1, c0=c0, gemm_mode=gm, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(3):
+            P.run(unit_prob, meth, c, seed=2 + s, c0=c0, gemm_mode=gm, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        res[meth] = e0.elapsed_time(e1) / 3
+        if unit_prob is not prob:
+            del unit_prob
+    return res
+
+
+def e2e(P, prob, args, w, c, gm, out, c0, rank, ws, dev):
+    """Same metric through the C ABI with host buffers: H2D of M and N and D2H of CD inside the timing."""
+    import torch
+    Mh = prob.M.cpu().pin_memory()
+    Nh = prob.N.cpu().pin_memory()
+    outh = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    steps = max(2, min(args.steps, 5))
+
+    def one(s):
+        prob.M.copy_(Mh, non_blocking=True)
+        prob.N.copy_(Nh, non_blocking=True)
+        P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out)
+        outh.copy_(out, non_blocking=True)
+
+    one(900)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        one(901 + s)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    return {"value": t / (steps * ws), "unit": "ms",
+            "h2d_bytes_per_step": int(Mh.numel() * Mh.element_size() + Nh.numel() * Nh.element_size()),
+            "d2h_bytes_per_step": int(outh.numel() * outh.element_size()), "steps": steps}
+
+
+def main():
+    args = parse()
+    if args.gpus > 1 and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        raise SystemExit("for --gpus > 1 launch with torch.distributed.run (one rank per GPU)")
+    ws, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            reference_arm(args, ws, rank)
+        else:
+            native_arm(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

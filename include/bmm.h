@@ -11,7 +11,8 @@
  * Conventions shared by every call
  *   - Every pointer inside the descriptors and every array argument is DEVICE memory
  *     owned by the caller, unless marked "host".  The library allocates nothing and
- *     keeps no state between calls; all work is enqueued on the caller's stream and
+ *     keeps no state between calls (beyond a diagnostic launch counter and the cached
+ *     driver entry point of the tensor-map encoder); all work is enqueued on the caller's stream and
  *     the calls return without synchronising (except bmm_read_device_status).
  *   - Argument, shape and feasibility errors are returned before anything is launched.
  *     Conditions only the GPU can see (non-finite data, bad offsets, a probability
@@ -75,8 +76,9 @@ enum {
     BMM_F_NONE = 0,  /* not computed (st->f untouched) */
     BMM_F_EXACT = 1  /* trace identity <M^kT M^k, N_k N_kT>_F with FP64-accurate sums on CUDA cores */
 };
-/* Flag or-ed into bmm_probs' fmode: st already holds this M, N's statistics (and f when
- * needed); only p is computed.  COL_UNIFORM never reads st, M or N. */
+/* Flag or-ed into bmm_probs' fmode: st already holds this M, N's statistics.  The pass
+ * over M and N is skipped; f is computed if fmode says so (else st->f is used as given),
+ * then p.  COL_UNIFORM never reads st, M or N. */
 enum { BMM_REUSE_STATS = 0x100 };
 
 /* Sampling unit. */
@@ -141,7 +143,7 @@ size_t bmm_workspace_size(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* 
  *   p_out: [n] for the column kinds, [K] for the block kinds.  May be NULL.
  *   st:    all pointers but f required; f required when fmode != BMM_F_NONE or
  *          pkind == BMM_P_BLK_PRODNORM.  With BMM_REUSE_STATS the pass over M and N is
- *          skipped and st is read, not written.
+ *          skipped and only st->f (if computed) is written.
  * A block with a_k = 0 gets uniform column probabilities; all-zero block weights give 1/K.
  */
 bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
@@ -218,6 +220,9 @@ bmm_status bmm_read_device_status(const void* ws, bmm_stream_t stream);
 bmm_status bmm_clear_device_status(void* ws, bmm_stream_t stream);
 /* Static, NUL-terminated description of a status code. */
 const char* bmm_status_string(bmm_status s);
+/* Diagnostics (no counterpart in the paper): number of CUDA kernels this library has
+ * enqueued since it was loaded, summed over all threads and calls. */
+uint64_t bmm_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
 
 EXPORTED = (
     "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
-    "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string",
+    "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
 )
 
 
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.bmm_clear_device_status.argtypes = [vp, vp]
     lib.bmm_status_string.argtypes = [i32]
     lib.bmm_status_string.restype = ctypes.c_char_p
+    lib.bmm_launch_count.argtypes = []
+    lib.bmm_launch_count.restype = ctypes.c_uint64
     for name in ("bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
                  "bmm_read_device_status", "bmm_clear_device_status"):
         getattr(lib, name).restype = i32
@@ -191,3 +193,8 @@ def bmm_read_device_status(ws, stream=None) -> int:
 
 def bmm_clear_device_status(ws, stream=None):
     _check(load().bmm_clear_device_status(ws.data_ptr(), _stream(stream)), "bmm_clear_device_status")
+
+
+def bmm_launch_count() -> int:
+    """Kernels launched by libbmm.so since it was loaded (diagnostic)."""
+    return int(load().bmm_launch_count())

@@ -287,11 +287,20 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
     if (st == nullptr || !st->x || !st->y || !st->a || !st->s || !st->mf || !st->nf) return BMM_ERR_ARG;
     const bool need_f = fmode != BMM_F_NONE || pkind == BMM_P_BLK_PRODNORM;
     if (need_f && st->f == nullptr) return BMM_ERR_ARG;
-    if (reuse) {
-        if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < kStatusBytes) return BMM_ERR_WORKSPACE;
+    if (reuse) {  // statistics given; compute f (fmode EXACT) and p only
+        Carver cnt{nullptr};
+        ProbsPlan plan;
+        plan_probs(cnt, M, N, B, fmode != BMM_F_NONE, &plan);
+        if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
+        Carver cv{static_cast<char*>(ws) + kStatusBytes};
+        plan_probs(cv, M, N, B, fmode != BMM_F_NONE, &plan);
+        cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+        if (fmode != BMM_F_NONE)
+            BMM_TRY(launch_gram_frob(vecset_of_M(M), vecset_of_N(N), B->offsets, B->K, B->max_nk, nullptr, nullptr, 0,
+                                     st->f, plan.gpart, plan.gpart_cap, status_of(ws), cs));
         if (p_out)
             BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, B->offsets, B->K, B->n, p_out,
-                                 status_of(ws), reinterpret_cast<cudaStream_t>(stream)));
+                                 status_of(ws), cs));
         return BMM_OK;
     }
     Carver cnt{nullptr};
@@ -541,3 +550,5 @@ BMM_API const char* bmm_status_string(bmm_status s) {
     }
     return "unknown status";
 }
+
+BMM_API uint64_t bmm_launch_count(void) { return launch_counter().load(std::memory_order_relaxed); }

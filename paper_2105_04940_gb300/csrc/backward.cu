@@ -108,10 +108,10 @@ cudaError_t launch_unique(const int32_t* idx, const double* scale, int64_t count
     const int64_t ntiles = ceil_div(space, kTileScan);
     cudaError_t e = cudaMemsetAsync(cnt, 0, space * 4, s);
     if (e != cudaSuccess) return e;
-    if (count > 0) hist_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(idx, scale, count, space, cnt, sval, st);
-    flag_scan_kernel<<<(unsigned)ntiles, kTileScan, 0, s>>>(cnt, space, pos, tot);
-    tot_scan_kernel<<<1, kTileScan, 0, s>>>(tot, ntiles);
-    compact_kernel<<<(unsigned)ceil_div(space, 256), 256, 0, s>>>(cnt, sval, pos, tot, space, uidx, uw, ucount_dev);
+    if (count > 0) (count_launch(), hist_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(idx, scale, count, space, cnt, sval, st));
+    (count_launch(), flag_scan_kernel<<<(unsigned)ntiles, kTileScan, 0, s>>>(cnt, space, pos, tot));
+    (count_launch(), tot_scan_kernel<<<1, kTileScan, 0, s>>>(tot, ntiles));
+    (count_launch(), compact_kernel<<<(unsigned)ceil_div(space, 256), 256, 0, s>>>(cnt, sval, pos, tot, space, uidx, uw, ucount_dev));
     return cudaGetLastError();
 }
 
@@ -151,7 +151,7 @@ __global__ void convert_f64_kernel(const double* __restrict__ G, int64_t rows, i
 cudaError_t launch_convert_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg, __nv_bfloat16* out,
                                        int64_t ldo, cudaStream_t s) {
     dim3 grid((unsigned)ceil_div(cols, 256), (unsigned)imin(imax(rows, 1), 8192));
-    convert_f32_bf16_kernel<<<grid, 256, 0, s>>>(G, rows, cols, ldg, out, ldo);
+    (count_launch(), convert_f32_bf16_kernel<<<grid, 256, 0, s>>>(G, rows, cols, ldg, out, ldo));
     return cudaGetLastError();
 }
 
@@ -159,7 +159,7 @@ cudaError_t launch_transpose_f32_to_bf16(const float* G, int64_t rows, int64_t c
                                          int64_t ldo, cudaStream_t s) {
     if (ceil_div(rows, 32) > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
-    transpose_f32_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(G, rows, cols, ldg, out, ldo);
+    (count_launch(), transpose_f32_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(G, rows, cols, ldg, out, ldo));
     return cudaGetLastError();
 }
 
@@ -167,7 +167,7 @@ cudaError_t launch_convert_to_f64(const void* G, int dtype, int64_t rows, int64_
                                   double* out, int64_t ldo, cudaStream_t s) {
     if (dtype != BMM_F64) return cudaErrorInvalidValue;
     dim3 grid((unsigned)ceil_div(cols, 256), (unsigned)imin(imax(rows, 1), 8192));
-    convert_f64_kernel<<<grid, 256, 0, s>>>(static_cast<const double*>(G), rows, cols, ldg, transpose, out, ldo);
+    (count_launch(), convert_f64_kernel<<<grid, 256, 0, s>>>(static_cast<const double*>(G), rows, cols, ldg, transpose, out, ldo));
     return cudaGetLastError();
 }
 
@@ -231,13 +231,13 @@ static cudaError_t gather_rows_t(const VecSet& v, const int32_t* col, const int6
                                  int64_t ldo, bool f64, cudaStream_t s) {
     const T* X = static_cast<const T*>(v.data);
     if (f64) {
-        gather_rows_f64_kernel<T><<<(unsigned)jmax, 256, 0, s>>>(X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax,
-                                                               static_cast<double*>(out), ldo);
+        (count_launch(), gather_rows_f64_kernel<T><<<(unsigned)jmax, 256, 0, s>>>(X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax,
+                                                               static_cast<double*>(out), ldo));
     } else {
         if (ceil_div(v.len, 32) > 65535) return cudaErrorInvalidValue;
         dim3 grid((unsigned)ceil_div(jmax, 32), (unsigned)ceil_div(v.len, 32));
-        gather_rows_kernel<T, __nv_bfloat16><<<grid, dim3(32, 8), 0, s>>>(
-            X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax, static_cast<__nv_bfloat16*>(out), ldo);
+        (count_launch(), gather_rows_kernel<T, __nv_bfloat16><<<grid, dim3(32, 8), 0, s>>>(
+            X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax, static_cast<__nv_bfloat16*>(out), ldo));
     }
     return cudaGetLastError();
 }
@@ -307,13 +307,13 @@ cudaError_t launch_scatter_grad(void* dst, int dst_dtype, int64_t dst_ld, int ds
     dim3 grid((unsigned)ceil_div(ext_max, 32), (unsigned)ceil_div(len, 32));
     dim3 block(32, 8);
     if (dst_dtype == BMM_F64 && src_dtype == BMM_F64)
-        scatter_kernel<double, double><<<grid, block, 0, s>>>(static_cast<double*>(dst), dst_ld, dst_mode, len,
+        (count_launch(), scatter_kernel<double, double><<<grid, block, 0, s>>>(static_cast<double*>(dst), dst_ld, dst_mode, len,
                                                              static_cast<const double*>(src), src_ld, src_rows, col, w,
-                                                             ext_dev);
+                                                             ext_dev));
     else if (dst_dtype == BMM_F32 && src_dtype == BMM_F32)
-        scatter_kernel<float, float><<<grid, block, 0, s>>>(static_cast<float*>(dst), dst_ld, dst_mode, len,
+        (count_launch(), scatter_kernel<float, float><<<grid, block, 0, s>>>(static_cast<float*>(dst), dst_ld, dst_mode, len,
                                                            static_cast<const float*>(src), src_ld, src_rows, col, w,
-                                                           ext_dev);
+                                                           ext_dev));
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

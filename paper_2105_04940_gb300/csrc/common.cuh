@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/bmm.h"
 
 namespace bmm {
@@ -87,6 +89,14 @@ __device__ __forceinline__ uint64_t draw_bits(uint64_t seed, uint64_t sid, uint6
     U4 o = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     return ((uint64_t)o.y << 32) | (uint64_t)o.x;
 }
+
+// ---------------------------------------------------------------- diagnostics
+// Kernels launched by this library since it was loaded (read by bmm_launch_count).
+inline std::atomic<unsigned long long>& launch_counter() {
+    static std::atomic<unsigned long long> n{0};
+    return n;
+}
+inline void count_launch() { launch_counter().fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- misc
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

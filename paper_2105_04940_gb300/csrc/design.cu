@@ -77,9 +77,9 @@ cudaError_t launch_probs(int kind, const double* x, const double* y, const doubl
                          const double* nf, const double* f, const int64_t* off, int64_t K, int64_t n, double* p,
                          DevStatus* st, cudaStream_t s) {
     if (kind == BMM_P_COL_OPT || kind == BMM_P_COL_UNIFORM) {
-        probs_col_kernel<<<(unsigned)ceil_div(K * 32, 256), 256, 0, s>>>(kind, x, y, a, off, K, n, p, st);
+        (count_launch(), probs_col_kernel<<<(unsigned)ceil_div(K * 32, 256), 256, 0, s>>>(kind, x, y, a, off, K, n, p, st));
     } else {
-        probs_blk_kernel<<<1, 1024, 0, s>>>(kind, mf, nf, f, K, p, st);
+        (count_launch(), probs_blk_kernel<<<1, 1024, 0, s>>>(kind, mf, nf, f, K, p, st));
     }
     return cudaGetLastError();
 }
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
 
 cudaError_t launch_blocksizes(int kind, const double* a, const double* f, const int64_t* off, int64_t K, int64_t n,
                               int64_t c, int64_t* ck, double* g, DevStatus* st, cudaStream_t s) {
-    blocksizes_kernel<<<1, 1024, 0, s>>>(kind, a, f, off, K, n, c, ck, g, st);
+    (count_launch(), blocksizes_kernel<<<1, 1024, 0, s>>>(kind, a, f, off, K, n, c, ck, g, st));
     return cudaGetLastError();
 }
 

@@ -174,10 +174,10 @@ static cudaError_t gram_frob_t(const VecSet& U, const VecSet& V, const int64_t* 
     const int tiles = tiles_for(cols ? per : max_len);
     const int pairs = tiles * (tiles + 1) / 2;
     dim3 grid((unsigned)K, (unsigned)pairs);
-    gram_frob_kernel<T><<<grid, 256, 0, s>>>(static_cast<const T*>(U.data), U.len, U.ld, U.mode,
+    (count_launch(), gram_frob_kernel<T><<<grid, 256, 0, s>>>(static_cast<const T*>(U.data), U.len, U.ld, U.mode,
                                              static_cast<const T*>(V.data), V.len, V.ld, V.mode, U.count, off, K,
-                                             cols, wts, per, tiles, partial, st);
-    sum_pairs_kernel<<<(unsigned)ceil_div(K, 256), 256, 0, s>>>(partial, K, pairs, f);
+                                             cols, wts, per, tiles, partial, st));
+    (count_launch(), sum_pairs_kernel<<<(unsigned)ceil_div(K, 256), 256, 0, s>>>(partial, K, pairs, f));
     return cudaGetLastError();
 }
 

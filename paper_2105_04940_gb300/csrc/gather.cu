@@ -88,17 +88,17 @@ __global__ void expand_fill_kernel(const int32_t* __restrict__ kidx, const doubl
 cudaError_t launch_expand_blocks(const int32_t* kidx, const double* kscale, int64_t count, const int64_t* count_dev,
                                  const int64_t* off, int64_t K, int64_t n, int64_t max_nk, int32_t* col, double* w,
                                  int64_t* ext_dev, int64_t* prefix_scratch, DevStatus* st, cudaStream_t s) {
-    expand_prefix_kernel<<<1, 1024, 0, s>>>(kidx, count, count_dev, off, K, n, max_nk, prefix_scratch, ext_dev, st);
+    (count_launch(), expand_prefix_kernel<<<1, 1024, 0, s>>>(kidx, count, count_dev, off, K, n, max_nk, prefix_scratch, ext_dev, st));
     if (count > 0)
-        expand_fill_kernel<<<(unsigned)count, 128, 0, s>>>(kidx, kscale, count, count_dev, off, K, n, max_nk,
-                                                           prefix_scratch, col, w);
+        (count_launch(), expand_fill_kernel<<<(unsigned)count, 128, 0, s>>>(kidx, kscale, count, count_dev, off, K, n, max_nk,
+                                                           prefix_scratch, col, w));
     return cudaGetLastError();
 }
 
 __global__ void set_extent_kernel(int64_t* ext, int64_t v) { *ext = v; }
 
 cudaError_t launch_set_extent(int64_t* ext_dev, int64_t value, cudaStream_t s) {
-    set_extent_kernel<<<1, 1, 0, s>>>(ext_dev, value);
+    (count_launch(), set_extent_kernel<<<1, 1, 0, s>>>(ext_dev, value));
     return cudaGetLastError();
 }
 
@@ -213,10 +213,10 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
     const T* X = static_cast<const T*>(v.data);
     if (v.mode == VEC_STRIDED) {
         dim3 grid((unsigned)ceil_div(kmax, 128), (unsigned)imin(imax(v.len, 1), 4096));
-        gather_strided_kernel<T, V><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, apply_weight, wr, st);
+        (count_launch(), gather_strided_kernel<T, V><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, apply_weight, wr, st));
     } else {
         dim3 grid((unsigned)ceil_div(kmax, 32), (unsigned)imin(imax(ceil_div(v.len, 64), 1), 2048));
-        gather_contig_kernel<T, V><<<grid, 256, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, apply_weight, wr, st);
+        (count_launch(), gather_contig_kernel<T, V><<<grid, 256, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, apply_weight, wr, st));
     }
     return cudaGetLastError();
 }

@@ -61,7 +61,7 @@ cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (ceil_div(M, 64) > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
-    gemm_f64_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, M, N, k_host, k_dev, out, ldo, accumulate);
+    (count_launch(), gemm_f64_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, M, N, k_host, k_dev, out, ldo, accumulate));
     return cudaGetLastError();
 }
 

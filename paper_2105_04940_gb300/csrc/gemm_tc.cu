@@ -354,9 +354,9 @@ cudaError_t launch_bn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* 
     const int64_t tiles = ceil_div(M, BM) * ceil_div(N, BN);
     const int grid = (int)imin(tiles, num_sms());
     const int vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (ldo % 4 == 0);
-    gemm_bf16_tc_kernel<BN><<<grid, 192, C::SMEM, s>>>(ma, mb, (int)M, (int)N, (long long)k_host,
+    (count_launch(), gemm_bf16_tc_kernel<BN><<<grid, 192, C::SMEM, s>>>(ma, mb, (int)M, (int)N, (long long)k_host,
                                                        reinterpret_cast<const long long*>(k_dev), k_mult, out,
-                                                       (long long)ldo, accumulate, vec_ok, st);
+                                                       (long long)ldo, accumulate, vec_ok, st));
     return cudaGetLastError();
 }
 

@@ -182,7 +182,7 @@ static cudaError_t sqnorms_t(const VecSet& v, double* out, double* partial, int6
     if (v.mode == VEC_CONTIG) {
         const int64_t warps_needed = v.count;
         int64_t blocks = imin(ceil_div(warps_needed, 8), 152 * 64);
-        sqnorm_rows_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, v.count, v.len, v.ld, vec_ok, out);
+        (count_launch(), sqnorm_rows_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, v.count, v.len, v.ld, vec_ok, out));
         return cudaGetLastError();
     }
     int64_t gx, S, rps;
@@ -193,12 +193,12 @@ static cudaError_t sqnorms_t(const VecSet& v, double* out, double* partial, int6
     }
     if (S <= 1) {
         dim3 grid((unsigned)gx, 1);
-        sqnorm_cols_kernel<T><<<grid, 128, 0, s>>>(X, v.len, v.count, v.ld, imax(v.len, 1), vec_ok, out);
+        (count_launch(), sqnorm_cols_kernel<T><<<grid, 128, 0, s>>>(X, v.len, v.count, v.ld, imax(v.len, 1), vec_ok, out));
         return cudaGetLastError();
     }
     dim3 grid((unsigned)gx, (unsigned)S);
-    sqnorm_cols_kernel<T><<<grid, 128, 0, s>>>(X, v.len, v.count, v.ld, rps, vec_ok, partial);
-    sum_slices_kernel<<<(unsigned)ceil_div(v.count, 256), 256, 0, s>>>(partial, S, v.count, out);
+    (count_launch(), sqnorm_cols_kernel<T><<<grid, 128, 0, s>>>(X, v.len, v.count, v.ld, rps, vec_ok, partial));
+    (count_launch(), sum_slices_kernel<<<(unsigned)ceil_div(v.count, 256), 256, 0, s>>>(partial, S, v.count, out));
     return cudaGetLastError();
 }
 
@@ -250,7 +250,7 @@ __global__ void block_stats_kernel(const double* __restrict__ x, const double* _
 
 cudaError_t launch_block_stats(const double* x, const double* y, const int64_t* off, int64_t K, int64_t n,
                                double* a, double* ssum, double* mf, double* nf, DevStatus* st, cudaStream_t s) {
-    block_stats_kernel<<<(unsigned)ceil_div(K * 32, 256), 256, 0, s>>>(x, y, off, K, n, a, ssum, mf, nf, st);
+    (count_launch(), block_stats_kernel<<<(unsigned)ceil_div(K * 32, 256), 256, 0, s>>>(x, y, off, K, n, a, ssum, mf, nf, st));
     return cudaGetLastError();
 }
 

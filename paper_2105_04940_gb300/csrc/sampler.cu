@@ -169,13 +169,13 @@ cudaError_t launch_sample(const double* p, int unit, const int64_t* off, int64_t
     w += round_up(ntiles * 8, 256);
     int64_t* D = reinterpret_cast<int64_t*>(w);
     if (c == 0) return cudaSuccess;
-    weights_scan_kernel<<<(unsigned)ntiles, kScanTile, 0, s>>>(p, len, G, tot, st);
+    (count_launch(), weights_scan_kernel<<<(unsigned)ntiles, kScanTile, 0, s>>>(p, len, G, tot, st));
     if (ntiles > 1) {
-        tile_prefix_kernel<<<1, kScanTile, 0, s>>>(tot, ntiles);
-        add_tile_prefix_kernel<<<(unsigned)ceil_div(len, 256), 256, 0, s>>>(G, tot, len);
+        (count_launch(), tile_prefix_kernel<<<1, kScanTile, 0, s>>>(tot, ntiles));
+        (count_launch(), add_tile_prefix_kernel<<<(unsigned)ceil_div(len, 256), 256, 0, s>>>(G, tot, len));
     }
-    if (unit == BMM_UNIT_COLUMN) draw_offsets_kernel<<<1, kScanTile, 0, s>>>(ck, K, c, D, st);
-    draw_kernel<<<(unsigned)ceil_div(c, 128), 128, 0, s>>>(p, unit, off, K, len, D, ck, c, seed, sid, G, idx, scale, st);
+    if (unit == BMM_UNIT_COLUMN) (count_launch(), draw_offsets_kernel<<<1, kScanTile, 0, s>>>(ck, K, c, D, st));
+    (count_launch(), draw_kernel<<<(unsigned)ceil_div(c, 128), 128, 0, s>>>(p, unit, off, K, len, D, ck, c, seed, sid, G, idx, scale, st));
     return cudaGetLastError();
 }
 

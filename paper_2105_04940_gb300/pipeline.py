@@ -54,6 +54,7 @@ class Problem:
     B: A.Blocks
     ws: object
     st: dict = field(default_factory=dict)
+    pilot_counts: dict = field(default_factory=dict)
 
     @property
     def K(self) -> int:
@@ -64,9 +65,12 @@ class Problem:
         return int(self.offsets[-1])
 
 
-def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode: int = A.GEMM_SPLIT_BF16,
+def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode: int | None = None,
             ws=None) -> Problem:
+    """Upload the offsets, allocate statistics and a workspace large enough for ``gemm_mode``
+    (all modes when None) and for draws of ``unit`` up to ``max_draws``."""
     torch = _torch()
+    modes = (A.GEMM_F64, A.GEMM_SPLIT_BF16) if gemm_mode is None else (gemm_mode,)
     off = np.asarray(offsets, dtype=np.int64)
     n = int(off[-1])
     max_nk = int(np.diff(off).max())
@@ -74,8 +78,7 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
     off_dev = torch.as_tensor(off, device=dev)
     B = A.blocks(off_dev, n, max_nk)
     if ws is None:
-        need = max(A.bmm_workspace_size(M, N, B, unit, max_draws, gemm_mode),
-                   A.bmm_workspace_size(M, N, B, A.UNIT_COLUMN, max_draws, A.GEMM_F64))
+        need = max(A.bmm_workspace_size(M, N, B, unit, max_draws, md) for md in modes)
         if need == 0:
             raise ValueError("invalid problem description")
         ws = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -91,14 +94,26 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
 
 
 def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
-        gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True) -> dict:
-    """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring)."""
+        gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None) -> dict:
+    """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring).
+
+    events: if a list, (stage name, torch.cuda.Event) pairs are appended at the stage
+    boundaries (recorded on the current stream; used for timing only).
+    """
     torch = _torch()
     M, N, B, ws, st = prob.M, prob.N, prob.B, prob.ws, prob.st
     dev = M.device
     K, n = prob.K, prob.n
     sid = stream_id(replicate, A.PURPOSE_MAIN)
     res = {"method": method, "c": c, "seed": seed, "sid": sid}
+
+    def mark(name):
+        if events is not None:
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            events.append((name, ev))
+
+    mark("start")
     if out is None and compute_product:
         out = torch.empty(M.shape[0], N.shape[1], device=dev,
                           dtype=torch.float64 if gemm_mode == A.GEMM_F64 else torch.float32)
@@ -106,13 +121,19 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         pblk = torch.empty(K, dtype=torch.float64, device=dev)
         if method == "SSM":
             A.bmm_probs(M, N, B, A.P_BLK_NORMPROD, A.F_NONE, pblk, st, ws)
+            mark("stats")
         else:
-            A.bmm_probs(M, N, B, A.P_BLK_PRODNORM, A.F_EXACT, pblk, st, ws)
+            A.bmm_probs(M, N, B, A.P_BLK_NORMPROD, A.F_NONE, None, st, ws)
+            mark("stats")
+            A.bmm_probs(M, N, B, A.P_BLK_PRODNORM, A.F_EXACT | A.REUSE_STATS, pblk, st, ws)
+            mark("exact_f")
         idx = torch.empty(c, dtype=torch.int32, device=dev)
         scale = torch.empty(c, dtype=torch.float64, device=dev)
         A.bmm_sample(pblk, A.UNIT_BLOCK, B, None, c, seed, sid, idx, scale, ws)
+        mark("sample")
         if compute_product:
             A.bmm_apply(M, N, B, A.UNIT_BLOCK, idx, scale, c, gemm_mode, out, False, ws)
+            mark("apply")
         res.update(p=pblk, idx=idx, scale=scale, unit=A.UNIT_BLOCK, out=out, ck=None)
         return res
     if method not in COLUMN_METHODS:
@@ -122,35 +143,50 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
     g = torch.empty(K, dtype=torch.float64, device=dev)
     if method == "UU":
         A.bmm_probs(None, None, B, A.P_COL_UNIFORM, A.F_NONE, p, None, ws)
+        mark("stats")
         A.bmm_blocksizes(None, None, B, None, A.CK_EQUAL, c, None, None, 0, ck, g, None, ws)
+        mark("blocksizes")
     elif method == "OPL":
-        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_EXACT, p, st, ws)
+        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
+        mark("stats")
+        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_EXACT | A.REUSE_STATS, None, st, ws)
+        mark("exact_f")
         A.bmm_blocksizes(M, N, B, st, A.CK_OPT, c, None, None, 0, ck, g, None, ws)
+        mark("blocksizes")
     elif method == "ONC":
         A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
+        mark("stats")
         A.bmm_blocksizes(M, N, B, st, A.CK_HAT, c, None, None, 0, ck, g, None, ws)
+        mark("blocksizes")
     else:  # Alg. 3: pilot sample, then c~_k
         if c0 is None:
             raise ValueError("two-step methods need c0")
         A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
+        mark("stats")
         if method == "ONU":
             p0 = torch.empty(n, dtype=torch.float64, device=dev)
             A.bmm_probs(None, None, B, A.P_COL_UNIFORM, A.F_NONE, p0, None, ws)
         else:
             p0 = p
         per = max(1, c0 // K)
-        ck0 = torch.full((K,), per, dtype=torch.int64, device=dev)
+        ck0 = prob.pilot_counts.get(per)
+        if ck0 is None:  # uploaded once per problem, outside any timed loop
+            ck0 = torch.as_tensor(np.full(K, per, dtype=np.int64), device=dev)
+            prob.pilot_counts[per] = ck0
         pidx = torch.empty(K * per, dtype=torch.int32, device=dev)
         pscale = torch.empty(K * per, dtype=torch.float64, device=dev)
         A.bmm_sample(p0, A.UNIT_COLUMN, B, ck0, K * per, seed, stream_id(replicate, A.PURPOSE_PILOT), pidx, pscale, ws)
         fhat = torch.empty(K, dtype=torch.float64, device=dev)
         A.bmm_blocksizes(M, N, B, st, A.CK_TILDE, c, pidx, pscale, per, ck, g, fhat, ws)
+        mark("pilot_blocksizes")
         res.update(p0=p0, pilot_idx=pidx, pilot_scale=pscale, fhat=fhat)
     idx = torch.empty(c, dtype=torch.int32, device=dev)
     scale = torch.empty(c, dtype=torch.float64, device=dev)
     A.bmm_sample(p, A.UNIT_COLUMN, B, ck, c, seed, sid, idx, scale, ws)
+    mark("sample")
     if compute_product:
         A.bmm_apply(M, N, B, A.UNIT_COLUMN, idx, scale, c, gemm_mode, out, False, ws)
+        mark("apply")
     res.update(p=p, ck=ck, g=g, idx=idx, scale=scale, unit=A.UNIT_COLUMN, out=out)
     return res
 
