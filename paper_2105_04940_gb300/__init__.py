@@ -20,6 +20,6 @@ __all__ = [
 
 
 def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile the CUDA library in-tree (see build.py)."""
-    from .build import build as _build
+    """Compile the CUDA library in-tree (see buildlib.py)."""
+    from .buildlib import build as _build
     return _build(verbose=verbose, force=force)

@@ -86,21 +86,16 @@ cudaError_t launch_probs(int kind, const double* x, const double* y, const doubl
 
 // ---------------------------------------------------------------- block sizes (one CTA)
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+constexpr int kActiveCap = 4096;  // blocks tracked in the shared-memory active lists (K above: no pruning)
 
 __device__ __forceinline__ long long count_at(double lam, double g, long long nk) {
     if (!(g > 0.0)) return 1;
-    double v = floor(__dmul_rn(lam, g));
-    v = fmin(fmax(v, 1.0), (double)nk);
-    return (long long)v;
+    // trunc == floor for lam * g >= 0; the conversion saturates, so +inf and huge values clamp to nk
+    long long v = __double2ll_rz(__dmul_rn(lam, g));
+    return v < 1 ? 1 : (v > nk ? nk : v);
 }
 
-// F(lam) summed by one warp (exact integer sum)
-__device__ long long warp_F(double lam, const double* g, const int64_t* off, int64_t K) {
-    const int lane = threadIdx.x & 31;
-    long long acc = 0;
-    for (int64_t k = lane; k < K; k += 32) acc += count_at(lam, g[k], off[k + 1] - off[k]);
-    return warp_sum_ll(acc);
-}
+__device__ __forceinline__ double bits_to_lam(unsigned long long u) { return __longlong_as_double((long long)u); }
 
 // exclusive scan of one value per thread over a 1024-thread block (exact)
 __device__ long long block_exclusive_scan(long long v, long long* sm, long long* total) {
@@ -131,15 +126,31 @@ __device__ long long block_exclusive_scan(long long v, long long* sm, long long*
     return res;
 }
 
+__device__ long long block_sum_ll(long long v, long long* sm) {
+    long long t;
+    block_exclusive_scan(v, sm, &t);
+    return t;
+}
+
+// F(u) = sum_k count(u, k) over all blocks, by the whole CTA (exact)
+__device__ long long block_F(unsigned long long u, const double* g, const int64_t* off, int64_t K, long long* sm) {
+    const double lam = bits_to_lam(u);
+    long long acc = 0;
+    for (int64_t k = threadIdx.x; k < K; k += 1024) acc += count_at(lam, g[k], off[k + 1] - off[k]);
+    return block_sum_ll(acc, sm);
+}
+
 __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double* __restrict__ a,
                                                           const double* __restrict__ f,
                                                           const int64_t* __restrict__ off, int64_t K, int64_t n,
-                                                          int64_t c,
-                                                          int64_t* __restrict__ ck, double* __restrict__ g,
+                                                          int64_t c, int64_t* __restrict__ ck, double* __restrict__ g,
                                                           DevStatus* st) {
     __shared__ long long sF[32];
     __shared__ unsigned long long sLoHi[2];
     __shared__ long long sScan[33];
+    __shared__ int sAct[2][kActiveCap];
+    __shared__ int sNact[2];
+    __shared__ double sRed[33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // 1. weights g_k
@@ -179,30 +190,71 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
     }
     __syncthreads();
 
-    // 2. lam* = largest FP64 with F(lam) <= c (bit-pattern search)
-    if (warp == 0) {
-        const long long Finf = warp_F(__longlong_as_double((long long)kInfBits), g, off, K);
-        if (lane == 0) sF[0] = Finf;
-    }
-    if (tid == 0) { sLoHi[0] = 0ull; sLoHi[1] = kInfBits; }
-    __syncthreads();
-    const bool inf_case = sF[0] <= c;
+    // 2. lam* = the largest FP64 lam with F(lam) <= c.  F is monotone, so any bracket
+    //    lo < hi with F(lo) <= c < F(hi) leads to the same lam*.
+    const long long Finf = block_F(kInfBits, g, off, K, sScan);
+    const bool inf_case = Finf <= c;
     unsigned long long lo = 0ull, hi = kInfBits;
-    __syncthreads();
     if (!inf_case) {
+        // a guess lam0 = c / sum g narrows the bracket when it verifies
+        double gs = 0.0;
+        for (int64_t k = tid; k < K; k += 1024) gs += g[k];
+        gs = warp_sum(gs);
+        if (lane == 0) sRed[warp] = gs;
+        __syncthreads();
+        if (warp == 0) {
+            double t = warp_sum(sRed[lane]);
+            if (lane == 0) sRed[32] = t;
+        }
+        __syncthreads();
+        const double lam0 = (double)c / sRed[32];
+        if (isfinite(lam0) && lam0 > 0.0) {
+            const unsigned long long ulo = (unsigned long long)__double_as_longlong(lam0 * 0.25);
+            const unsigned long long uhi = (unsigned long long)__double_as_longlong(lam0 * 4.0);
+            if (uhi < kInfBits && block_F(ulo, g, off, K, sScan) <= c) lo = ulo;
+            if (uhi < kInfBits && block_F(uhi, g, off, K, sScan) > c) hi = uhi;
+        }
+        // active list: blocks whose count may still change inside (lo, hi)
+        const bool track = K <= kActiveCap;
+        if (tid == 0) { sNact[0] = 0; sLoHi[0] = lo; sLoHi[1] = hi; }
+        __syncthreads();
+        int cur = 0;
+        long long base = 0;
+        if (track) {
+            long long mine = 0;
+            for (int64_t k = tid; k < K; k += 1024) {
+                const long long nk = off[k + 1] - off[k];
+                const long long clo = count_at(bits_to_lam(lo), g[k], nk), chi = count_at(bits_to_lam(hi), g[k], nk);
+                if (clo == chi) mine += clo;
+                else sAct[0][atomicAdd(&sNact[0], 1)] = (int)k;
+            }
+            base = block_sum_ll(mine, sScan);
+        }
         while (hi - lo > 1ull) {
             const unsigned long long d = hi - lo;
+            const int nact = track ? sNact[cur] : 0;
             if (warp >= 1) {
                 const unsigned long long w = (unsigned long long)warp;
                 const unsigned long long u = lo + (d >> 5) * w + (((d & 31ull) * w) >> 5);
-                const long long F = warp_F(__longlong_as_double((long long)u), g, off, K);
-                if (lane == 0) sF[warp] = F;
+                const double lam = bits_to_lam(u);
+                long long acc = 0;
+                if (track) {
+                    for (int i = lane; i < nact; i += 32) {
+                        const int k = sAct[cur][i];
+                        acc += count_at(lam, g[k], off[k + 1] - off[k]);
+                    }
+                } else {
+                    for (int64_t k = lane; k < K; k += 32) acc += count_at(lam, g[k], off[k + 1] - off[k]);
+                }
+                acc = warp_sum_ll(acc);
+                if (lane == 0) sF[warp] = base + acc;
             }
             __syncthreads();
             if (tid == 0) {
                 unsigned long long nlo = lo, nhi = hi;
                 for (int w = 1; w < 32; ++w) {
-                    const unsigned long long u = lo + (d >> 5) * (unsigned long long)w + (((d & 31ull) * (unsigned long long)w) >> 5);
+                    const unsigned long long u =
+                        lo + (d >> 5) * (unsigned long long)w + (((d & 31ull) * (unsigned long long)w) >> 5);
                     if (sF[w] <= c) {
                         if (u > nlo) nlo = u;
                     } else if (u < nhi) {
@@ -211,15 +263,29 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
                 }
                 sLoHi[0] = nlo;
                 sLoHi[1] = nhi;
+                sNact[cur ^ 1] = 0;
             }
             __syncthreads();
             lo = sLoHi[0];
             hi = sLoHi[1];
+            if (track) {  // drop the blocks whose count is now constant on [lo, hi]
+                long long mine = 0;
+                for (int i = tid; i < nact; i += 1024) {
+                    const int k = sAct[cur][i];
+                    const long long nk = off[k + 1] - off[k];
+                    const long long clo = count_at(bits_to_lam(lo), g[k], nk);
+                    const long long chi = count_at(bits_to_lam(hi), g[k], nk);
+                    if (clo == chi) mine += clo;
+                    else sAct[cur ^ 1][atomicAdd(&sNact[cur ^ 1], 1)] = k;
+                }
+                base += block_sum_ll(mine, sScan);
+                cur ^= 1;
+            }
             __syncthreads();
         }
     }
     const unsigned long long ustar = inf_case ? kInfBits : lo;
-    const double lam = __longlong_as_double((long long)ustar);
+    const double lam = bits_to_lam(ustar);
 
     // 3. counts at lam*, each thread owning a contiguous run of k
     const int64_t chunk = ceil_div(K, 1024);
@@ -235,7 +301,7 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
     const long long r = c - total;
     if (r > 0) {
         if (!inf_case) {
-            const double lam2 = __longlong_as_double((long long)(ustar + 1ull));
+            const double lam2 = bits_to_lam(ustar + 1ull);
             long long gcount = 0;
             for (int64_t k = k0; k < k1; ++k) gcount += count_at(lam2, g[k], off[k + 1] - off[k]) > ck[k];
             long long gt;

@@ -134,7 +134,10 @@ struct OpWriter {
     }
 };
 
-// vectors are storage columns: element r of vector i at X[r*ld + i]; one thread per column j
+// vectors are storage columns: element r of vector i at X[r*ld + i].  One thread per column j and
+// a run of kGatherRows rows, so the weight's square root is taken once per run.
+constexpr int kGatherRows = 64;
+
 template <typename T, typename V>
 __global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
                                       const int32_t* __restrict__ col, const double* __restrict__ w,
@@ -152,9 +155,21 @@ __global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int6
         sw = apply_weight ? (V)sqrt(w[j]) : V(1);
         if (c < 0 || c >= nvec) { set_status(st, BMM_ERR_ARG, (int)j); c = -1; }
     }
-    for (int64_t r = blockIdx.y; r < len; r += gridDim.y) {
-        const V v = (c >= 0) ? ldv<T, V>(X + r * ld + c) * sw : V(0);
-        wr.put(r, j, v);
+    for (int64_t r0 = (int64_t)blockIdx.y * kGatherRows; r0 < len; r0 += (int64_t)gridDim.y * kGatherRows) {
+        const int64_t r1 = imin(len, r0 + kGatherRows);
+        if (c < 0) {
+            for (int64_t r = r0; r < r1; ++r) wr.put(r, j, V(0));
+            continue;
+        }
+        int64_t r = r0;
+        for (; r + 4 <= r1; r += 4) {
+            V v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = ldv<T, V>(X + (r + u) * ld + c);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wr.put(r + u, j, v[u] * sw);
+        }
+        for (; r < r1; ++r) wr.put(r, j, ldv<T, V>(X + r * ld + c) * sw);
     }
 }
 
@@ -212,7 +227,7 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
     const int64_t kmax = round_up(imax(ext_max, 1), 64);
     const T* X = static_cast<const T*>(v.data);
     if (v.mode == VEC_STRIDED) {
-        dim3 grid((unsigned)ceil_div(kmax, 128), (unsigned)imin(imax(v.len, 1), 4096));
+        dim3 grid((unsigned)ceil_div(kmax, 128), (unsigned)imin(imax(ceil_div(v.len, kGatherRows), 1), 4096));
         (count_launch(), gather_strided_kernel<T, V><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, apply_weight, wr, st));
     } else {
         dim3 grid((unsigned)ceil_div(kmax, 32), (unsigned)imin(imax(ceil_div(v.len, 64), 1), 2048));
