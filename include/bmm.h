@@ -151,6 +151,23 @@ bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
                      void* ws, size_t ws_bytes, bmm_stream_t stream);
 
 /*
+ * bmm_probs_static -- bmm_probs without a workspace.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at call time, such as a plugin whose
+ * host program owns all GPU memory through a fixed pool, or a latency-critical loop that cannot
+ * afford cudaMalloc's implicit synchronisation.  The statistics pass keeps its partial column sums
+ * in a 16 MiB array compiled into the library (held on every GPU that loads it until exit);
+ * problems needing more are rejected with BMM_ERR_WORKSPACE before any launch.
+ *   pkind:      BMM_P_COL_OPT, BMM_P_COL_UNIFORM or BMM_P_BLK_NORMPROD (no ||M^k N_k||_F).
+ *   status_out: device int32[2], zeroed by the caller; receives what bmm_probs records in the
+ *               workspace status block (first error code, detail).
+ *   M, N, B, p_out, st: as for bmm_probs (st->f unused).
+ * The first call on each device looks up the array's address with that device current; make it
+ * before any stream capture starts.  Calls share the array: calls that overlap on the GPU race.
+ */
+bmm_status bmm_probs_static(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t pkind,
+                            double* p_out, const bmm_stats* st, int32_t* status_out, bmm_stream_t stream);
+
+/*
  * bmm_blocksizes -- integer block sizes c_k for Alg. 2 (Thm 2.2 eq. 3.9, eq. 4.2,
  * eq. 4.7 with Alg. 3 step 1, Table 2 c/K).  c is the total number of outer products
  * (the paper's c); K <= c <= n is required (each block gets 1 <= c_k <= n_k).

@@ -27,6 +27,7 @@ PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
 EXPORTED = (
     "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
     "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
+    "bmm_probs_static",
 )
 
 
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH):
     lib.bmm_clear_device_status.argtypes = [vp, vp]
     lib.bmm_status_string.argtypes = [i32]
     lib.bmm_status_string.restype = ctypes.c_char_p
+    lib.bmm_probs_static.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, P(Stats), vp, vp]
+    lib.bmm_probs_static.restype = i32
     lib.bmm_launch_count.argtypes = []
     lib.bmm_launch_count.restype = ctypes.c_uint64
     for name in ("bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
@@ -198,3 +201,9 @@ def bmm_clear_device_status(ws, stream=None):
 def bmm_launch_count() -> int:
     """Kernels launched by libbmm.so since it was loaded (diagnostic)."""
     return int(load().bmm_launch_count())
+
+
+def bmm_probs_static(M, N, B: Blocks, pkind: int, p_out, st: dict, status_out, stream=None):
+    """bmm_probs with the library's fixed device scratch instead of a workspace (see include/bmm.h)."""
+    _check(load().bmm_probs_static(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), pkind, _ptr(p_out),
+                                   ctypes.byref(stats(st)), _ptr(status_out), _stream(stream)), "bmm_probs_static")
