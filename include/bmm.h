@@ -74,7 +74,10 @@ enum {
 /* How ||M^k N_k||_F^2 is computed by bmm_probs. */
 enum {
     BMM_F_NONE = 0,  /* not computed (st->f untouched) */
-    BMM_F_EXACT = 1  /* trace identity <M^kT M^k, N_k N_kT>_F with FP64-accurate sums on CUDA cores */
+    BMM_F_EXACT = 1, /* trace identity <M^kT M^k, N_k N_kT>_F with FP64-accurate sums on CUDA cores */
+    BMM_F_TC = 2     /* s_k (exact) + off-diagonal part of the trace identity from TF32 tcgen05 Grams,
+                        fused with the statistics pass (FP32 data, row- or column-major, ld % 4 == 0,
+                        blocks of at most 128); other inputs fall back to BMM_F_EXACT */
 };
 /* Flag or-ed into bmm_probs' fmode: st already holds this M, N's statistics.  The pass
  * over M and N is skipped; f is computed if fmode says so (else st->f is used as given),

@@ -18,7 +18,7 @@ F64, F32, BF16 = 0, 1, 2
 ROW_MAJOR, COL_MAJOR = 0, 1
 P_COL_OPT, P_COL_UNIFORM, P_BLK_PRODNORM, P_BLK_NORMPROD = 0, 1, 2, 3
 CK_OPT, CK_HAT, CK_TILDE, CK_EQUAL = 0, 1, 2, 3
-F_NONE, F_EXACT = 0, 1
+F_NONE, F_EXACT, F_TC = 0, 1, 2
 REUSE_STATS = 0x100
 UNIT_COLUMN, UNIT_BLOCK = 0, 1
 GEMM_F64, GEMM_BF16, GEMM_SPLIT_BF16 = 0, 1, 2

@@ -101,12 +101,14 @@ struct ProbsPlan {
     int64_t partial_cap;
     double* gpart;
     int64_t gpart_cap;
+    int* counter;
 };
 void plan_probs(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, bool need_f, ProbsPlan* p) {
     p->partial_cap = imax(vec_sqnorms_partial_elems(vecset_of_M(M)), vec_sqnorms_partial_elems(vecset_of_N(N)));
     p->partial = cv.take<double>(p->partial_cap);
     p->gpart_cap = need_f ? gram_frob_partial_elems(B->K, B->max_nk) : 0;
     p->gpart = need_f ? cv.take<double>(p->gpart_cap) : nullptr;
+    p->counter = cv.take<int>(1);
 }
 
 struct SizesPlan {
@@ -272,7 +274,7 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
     const bool reuse = (fmode & BMM_REUSE_STATS) != 0;
     fmode &= ~BMM_REUSE_STATS;
     if (pkind < BMM_P_COL_OPT || pkind > BMM_P_BLK_NORMPROD) return BMM_ERR_ARG;
-    if (fmode != BMM_F_NONE && fmode != BMM_F_EXACT) return BMM_ERR_ARG;
+    if (fmode != BMM_F_NONE && fmode != BMM_F_EXACT && fmode != BMM_F_TC) return BMM_ERR_ARG;
     bmm_status s;
     if (pkind == BMM_P_COL_UNIFORM && (reuse || st == nullptr)) {  // needs the blocks only
         if ((s = check_blocks(B)) != BMM_OK) return s;
@@ -295,9 +297,13 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
         Carver cv{static_cast<char*>(ws) + kStatusBytes};
         plan_probs(cv, M, N, B, fmode != BMM_F_NONE, &plan);
         cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-        if (fmode != BMM_F_NONE)
-            BMM_TRY(launch_gram_frob(vecset_of_M(M), vecset_of_N(N), B->offsets, B->K, B->max_nk, nullptr, nullptr, 0,
-                                     st->f, plan.gpart, plan.gpart_cap, status_of(ws), cs));
+        const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
+        if (fmode == BMM_F_TC && blockstats_tc_supported(vM, vN, B->max_nk))
+            BMM_TRY(launch_blockstats_tc(vM, vN, B->offsets, B->K, B->n, false, plan.counter, st->x, st->y, st->a,
+                                         st->s, st->mf, st->nf, st->f, status_of(ws), cs));
+        else if (fmode != BMM_F_NONE)
+            BMM_TRY(launch_gram_frob(vM, vN, B->offsets, B->K, B->max_nk, nullptr, nullptr, 0, st->f, plan.gpart,
+                                     plan.gpart_cap, status_of(ws), cs));
         if (p_out)
             BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, B->offsets, B->K, B->n, p_out,
                                  status_of(ws), cs));
@@ -312,12 +318,18 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     DevStatus* dst = status_of(ws);
     const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
-    BMM_TRY(launch_vec_sqnorms(vM, st->x, plan.partial, plan.partial_cap, cs));
-    BMM_TRY(launch_vec_sqnorms(vN, st->y, plan.partial, plan.partial_cap, cs));
-    BMM_TRY(launch_block_stats(st->x, st->y, B->offsets, B->K, B->n, st->a, st->s, st->mf, st->nf, dst, cs));
-    if (need_f)
-        BMM_TRY(launch_gram_frob(vM, vN, B->offsets, B->K, B->max_nk, nullptr, nullptr, 0, st->f, plan.gpart,
-                                 plan.gpart_cap, dst, cs));
+    if (fmode == BMM_F_TC && blockstats_tc_supported(vM, vN, B->max_nk)) {
+        // one fused pass: statistics and f_k
+        BMM_TRY(launch_blockstats_tc(vM, vN, B->offsets, B->K, B->n, true, plan.counter, st->x, st->y, st->a, st->s,
+                                     st->mf, st->nf, st->f, dst, cs));
+    } else {
+        BMM_TRY(launch_vec_sqnorms(vM, st->x, plan.partial, plan.partial_cap, cs));
+        BMM_TRY(launch_vec_sqnorms(vN, st->y, plan.partial, plan.partial_cap, cs));
+        BMM_TRY(launch_block_stats(st->x, st->y, B->offsets, B->K, B->n, st->a, st->s, st->mf, st->nf, dst, cs));
+        if (need_f)
+            BMM_TRY(launch_gram_frob(vM, vN, B->offsets, B->K, B->max_nk, nullptr, nullptr, 0, st->f, plan.gpart,
+                                     plan.gpart_cap, dst, cs));
+    }
     if (p_out)
         BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, B->offsets, B->K, B->n, p_out, dst,
                              cs));

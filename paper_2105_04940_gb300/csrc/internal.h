@@ -50,6 +50,13 @@ cudaError_t launch_gram_frob(const VecSet& U, const VecSet& V, const int64_t* of
                              double* f, double* partial, int64_t partial_cap, DevStatus* st, cudaStream_t s);
 int64_t gram_frob_partial_elems(int64_t K, int64_t max_len);
 
+// ---- blockstats_tc.cu
+bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk);
+// stats = true: writes x, y, a, ssum, mf, nf and f; stats = false: reads ssum, writes f only
+cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n,
+                                 bool stats, int* counter, double* x, double* y, double* a, double* ssum, double* mf,
+                                 double* nf, double* f, DevStatus* st, cudaStream_t s);
+
 // ---- design.cu
 cudaError_t launch_probs(int kind, const double* x, const double* y, const double* a, const double* mf,
                          const double* nf, const double* f, const int64_t* off, int64_t K, int64_t n,

@@ -94,8 +94,12 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
 
 
 def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
-        gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None) -> dict:
+        gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None,
+        fmode: int = A.F_TC) -> dict:
     """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring).
+
+    fmode: how OPL and WU compute ||M^k N_k||_F^2 -- A.F_TC (fused with the statistics pass on the
+    tensor cores when the inputs allow it, else exact) or A.F_EXACT.
 
     events: if a list, (stage name, torch.cuda.Event) pairs are appended at the stage
     boundaries (recorded on the current stream; used for timing only).
@@ -122,6 +126,9 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         if method == "SSM":
             A.bmm_probs(M, N, B, A.P_BLK_NORMPROD, A.F_NONE, pblk, st, ws)
             mark("stats")
+        elif fmode == A.F_TC:
+            A.bmm_probs(M, N, B, A.P_BLK_PRODNORM, A.F_TC, pblk, st, ws)
+            mark("stats_f")
         else:
             A.bmm_probs(M, N, B, A.P_BLK_NORMPROD, A.F_NONE, None, st, ws)
             mark("stats")
@@ -147,10 +154,14 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         A.bmm_blocksizes(None, None, B, None, A.CK_EQUAL, c, None, None, 0, ck, g, None, ws)
         mark("blocksizes")
     elif method == "OPL":
-        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
-        mark("stats")
-        A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_EXACT | A.REUSE_STATS, None, st, ws)
-        mark("exact_f")
+        if fmode == A.F_TC:
+            A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_TC, p, st, ws)
+            mark("stats_f")
+        else:
+            A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
+            mark("stats")
+            A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_EXACT | A.REUSE_STATS, None, st, ws)
+            mark("exact_f")
         A.bmm_blocksizes(M, N, B, st, A.CK_OPT, c, None, None, 0, ck, g, None, ws)
         mark("blocksizes")
     elif method == "ONC":

@@ -92,6 +92,72 @@ def test_exact_block_frobenius(bmm, dtype):
     assert rel_err(host(pb), oracle.p_blk_prodnorm(f)) < 1e-10
 
 
+def _tf32_gram_bound(M, N, off, m, p):
+    """Error scale of the off-diagonal trace from TF32 Grams: tau * sum_{i != j} (|M|^T|M| |G_N| + |G_M| |N||N|^T)
+    with tau = 2^-9 (both factors truncated to TF32) + len * 2^-23 (FP32 accumulation)."""
+    out = []
+    for a_, b_ in zip(off[:-1], off[1:]):
+        A, B = M[:, a_:b_], N[a_:b_, :]
+        GM, GN = A.T @ A, B @ B.T
+        AM, AN = np.abs(A).T @ np.abs(A), np.abs(B) @ np.abs(B).T
+        tM, tN = 2.0 ** -9 + m * 2.0 ** -23, 2.0 ** -9 + p * 2.0 ** -23
+        E = tM * AM * np.abs(GN) + tN * np.abs(GM) * AN + tM * tN * AM * AN
+        np.fill_diagonal(E, 0.0)
+        out.append(E.sum())
+    return np.array(out)
+
+
+@pytest.mark.parametrize("layouts", [("row", "row"), ("col", "col"), ("row", "col"), ("col", "row")])
+def test_fused_statistics_and_tensor_core_f(bmm, layouts):
+    """One pass for x, y, a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 and f_k = s_k + TF32 off-diagonal trace."""
+    m, n, p = 300, 6000, 261
+    off, M, N, Mt, Nt = _problem(m, n, p, 60, seed=41, dtype=np.float32, lo=16, hi=128)
+    Mt, Nt = as_layout(Mt, layouts[0]), as_layout(Nt, layouts[1])
+    prob = bmm.prepare(Mt, Nt, off, max_draws=100)
+    pv = torch.empty(n, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, pv, prob.st, prob.ws)
+    bmm.check_status(prob)
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    assert rel_err(host(prob.st["x"]), x) < 1e-12
+    assert rel_err(host(prob.st["y"]), y) < 1e-12
+    for k in ("a", "s", "mf", "nf"):
+        assert rel_err(host(prob.st[k]), st[k]) < 1e-12, k
+    assert rel_err(host(pv), oracle.p_col_opt(st["w"], st["a"], off)) < 1e-12
+    f = oracle.block_frob_sq(M, N, off)
+    bound = _tf32_gram_bound(M, N, off, m, p)
+    err = np.abs(host(prob.st["f"]) - f)
+    assert np.all(err <= bound + 1e-12 * f), np.max(err / (bound + 1e-300))
+    # the statistics-reusing form computes f only, from the given s_k
+    prob.st["f"].zero_()
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_BLK_PRODNORM, bmm._abi.F_TC | bmm._abi.REUSE_STATS, None, prob.st, prob.ws)
+    bmm.check_status(prob)
+    err = np.abs(host(prob.st["f"]) - f)
+    assert np.all(err <= bound + 1e-12 * f)
+
+
+def test_fused_statistics_low_rank_blocks(bmm):
+    """Rank-one aligned blocks (off-diagonal trace as large as the diagonal) and one full 128 block."""
+    rng = np.random.default_rng(3)
+    sizes = np.array([128, 5, 77, 16, 100, 33])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n, m, p = int(off[-1]), 96, 150
+    M = rng.standard_normal((m, n)).astype(np.float32)
+    N = rng.standard_normal((n, p)).astype(np.float32)
+    u, v = rng.standard_normal(m), rng.standard_normal(p)
+    w = rng.standard_normal(sizes[2])
+    M[:, off[2]:off[3]] = np.outer(u, w)
+    N[off[2]:off[3], :] = np.outer(w, v)
+    M, N = M.astype(np.float64), N.astype(np.float64)
+    Mt, Nt = to_dev(M.astype(np.float32)), to_dev(N.astype(np.float32))
+    prob = bmm.prepare(Mt, Nt, off, max_draws=50)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, None, prob.st, prob.ws)
+    bmm.check_status(prob)
+    f = oracle.block_frob_sq(M, N, off)
+    err = np.abs(host(prob.st["f"]) - f)
+    assert np.all(err <= _tf32_gram_bound(M, N, off, m, p) + 1e-12 * f)
+
+
 # ---------------------------------------------------------------- block sizes (identical inputs)
 @pytest.mark.parametrize("kind", ["opt", "hat", "equal"])
 def test_blocksizes_bit_exact(bmm, kind):
