@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-error", action="store_true")
+    ap.add_argument("--fused-stats", action="store_true", help="statistics and f_k in one pass (OPL, WU)")
     return ap.parse_args()
 
 
@@ -235,6 +236,8 @@ def stage_work(w, L, nk, method):
     return {
         "stats": {"bound": "hbm", "bytes": (m * n + n * p) * 4 + 8 * (2 * n + 4 * w["K"])},
         "exact_f": {"bound": "alu", "flops": float(2 * (m + p) * np.sum(nk.astype(np.float64) ** 2))},
+        "gram_f": {"bound": "hbm", "bytes": (m * n + n * p) * 4},
+        "stats_f": {"bound": "hbm", "bytes": (m * n + n * p) * 4 + 8 * (2 * n + 5 * w["K"])},
         "apply": {"bound": "tensor", "flops": float(2 * m * p * L)},
     }
 
@@ -263,7 +266,8 @@ def native_arm(args, ws, rank, local):
     c0 = 4 * K
 
     def step(s, events=None):
-        return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events)
+        return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events,
+                     fused_stats=args.fused_stats)
 
     for s in range(args.warmup):
         step(10_000 + s)

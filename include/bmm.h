@@ -219,6 +219,22 @@ bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, in
                      void* ws, size_t ws_bytes, bmm_stream_t stream);
 
 /*
+ * bmm_apply_batched -- bmm_apply for `count` independent products of any shapes (the batched
+ * configuration of many uneven products).  Host arrays of length count describe product i:
+ * Ms[i], Ns[i], Bs[i], idx[i], scale[i], draws[i] (its draw count), outs[i], and ws[i] / ws_bytes[i],
+ * a workspace of its own sized by bmm_workspace_size.  Each product's operands are gathered as in
+ * bmm_apply; the BF16 / split-BF16 products then share persistent tcgen05 launches whose tile
+ * scheduler walks the tiles of up to 80 products at a time (the FP64 mode runs per product).
+ * Device-detected errors of the gathers go to each product's status block, those of the shared
+ * GEMM launches to ws[0]'s.  Nothing is synchronised or allocated; the sequence can be recorded
+ * into a CUDA graph together with the calls that produce idx and scale.
+ */
+bmm_status bmm_apply_batched(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns, const bmm_blocks* Bs,
+                             int32_t unit, const int32_t* const* idx, const double* const* scale,
+                             const int64_t* draws, int32_t gemm_mode, const bmm_mat* outs, int32_t accumulate,
+                             void* const* ws, const size_t* ws_bytes, bmm_stream_t stream);
+
+/*
  * bmm_backward -- adjoint of bmm_apply for a loss l(CD) with G = dl/d(CD) (m x p).
  * The sample is not stored: it is redrawn from (p, ck, c, seed, stream_id) exactly as
  * bmm_sample draws it, and p is held constant (stop-gradient).  For every distinct index i

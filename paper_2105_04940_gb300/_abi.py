@@ -27,7 +27,7 @@ PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
 EXPORTED = (
     "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
     "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
-    "bmm_probs_static",
+    "bmm_probs_static", "bmm_apply_batched",
 )
 
 
@@ -78,6 +78,9 @@ def load(path: str = LIB_PATH):
     lib.bmm_status_string.restype = ctypes.c_char_p
     lib.bmm_probs_static.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, P(Stats), vp, vp]
     lib.bmm_probs_static.restype = i32
+    lib.bmm_apply_batched.argtypes = [i64, P(Mat), P(Mat), P(Blocks), i32, P(vp), P(vp), P(i64), i32, P(Mat), i32,
+                                      P(vp), P(sz), vp]
+    lib.bmm_apply_batched.restype = i32
     lib.bmm_launch_count.argtypes = []
     lib.bmm_launch_count.restype = ctypes.c_uint64
     for name in ("bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
@@ -207,3 +210,16 @@ def bmm_probs_static(M, N, B: Blocks, pkind: int, p_out, st: dict, status_out, s
     """bmm_probs with the library's fixed device scratch instead of a workspace (see include/bmm.h)."""
     _check(load().bmm_probs_static(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), pkind, _ptr(p_out),
                                    ctypes.byref(stats(st)), _ptr(status_out), _stream(stream)), "bmm_probs_static")
+
+
+def bmm_apply_batched(Ms, Ns, Bs, unit: int, idxs, scales, draws, gemm_mode: int, outs, accumulate: bool, wss,
+                      stream=None):
+    """bmm_apply over many independent products (lists of equal length; see include/bmm.h)."""
+    n = len(Ms)
+    MatA, BlkA, VpA = Mat * n, Blocks * n, ctypes.c_void_p * n
+    _check(load().bmm_apply_batched(
+        n, MatA(*[mat(m) for m in Ms]), MatA(*[mat(x) for x in Ns]), BlkA(*Bs), unit,
+        VpA(*[i.data_ptr() for i in idxs]), VpA(*[s.data_ptr() for s in scales]),
+        (ctypes.c_int64 * n)(*[int(d) for d in draws]), gemm_mode, MatA(*[mat(o) for o in outs]),
+        int(bool(accumulate)), VpA(*[w.data_ptr() for w in wss]), (ctypes.c_size_t * n)(*[w.numel() for w in wss]),
+        _stream(stream)), "bmm_apply_batched")

@@ -1,6 +1,8 @@
 // api.cu -- the exported C ABI (include/bmm.h): argument checks, workspace carving, launch order.
 #include <string.h>
 
+#include <vector>
+
 #include "internal.h"
 
 #define BMM_API extern "C" __attribute__((visibility("default")))
@@ -390,9 +392,14 @@ BMM_API bmm_status bmm_sample(const double* p, int32_t unit, const bmm_blocks* B
     return BMM_OK;
 }
 
-BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
-                             const int32_t* idx, const double* scale, int64_t count, int32_t gemm_mode,
-                             const bmm_mat* out, int32_t accumulate, void* ws, size_t ws_bytes, bmm_stream_t stream) {
+namespace bmm {
+namespace {
+// Checks and gathers of one product of bmm_apply / bmm_apply_batched.  On BMM_OK either *done
+// (nothing left to compute) or *g describes the product's GEMM (BF16 modes; FP64 is launched here).
+bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit, const int32_t* idx,
+                         const double* scale, int64_t count, int32_t gemm_mode, const bmm_mat* out,
+                         int32_t accumulate, void* ws, size_t ws_bytes, cudaStream_t cs, GemmArgs* g, bool* done) {
+    *done = true;
     bmm_status s = check_problem(M, N, B);
     if (s != BMM_OK) return s;
     if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
@@ -403,7 +410,6 @@ BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_block
     if (out->dtype != (gemm_mode == BMM_GEMM_F64 ? BMM_F64 : BMM_F32)) return BMM_ERR_DTYPE;
     if (gemm_mode != BMM_GEMM_F64 && !tc_gemm_supported()) return BMM_ERR_UNSUPPORTED;
     if (count > 0x7fffffffLL) return BMM_ERR_UNSUPPORTED;
-    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     void* odata = const_cast<void*>(out->data);
     if (count == 0 || M->rows == 0 || N->cols == 0) {
         if (!accumulate) BMM_TRY(launch_zero_matrix(odata, out->dtype, out->rows, out->cols, out->ld, cs));
@@ -433,12 +439,51 @@ BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_block
         BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.A), plan.ktot, static_cast<const double*>(plan.Bop),
                                 plan.ktot, M->rows, N->cols, 0, plan.ext, static_cast<double*>(odata), out->ld,
                                 accumulate, cs));
-    } else {
-        BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(plan.A), plan.ktot,
-                                    static_cast<const __nv_bfloat16*>(plan.Bop), plan.ktot, M->rows, N->cols,
-                                    plan.ktot, 0, plan.ext, gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1,
-                                    static_cast<float*>(odata), out->ld, accumulate, dst, cs));
+        return BMM_OK;
     }
+    *g = GemmArgs{static_cast<const __nv_bfloat16*>(plan.A), plan.ktot, static_cast<const __nv_bfloat16*>(plan.Bop),
+                  plan.ktot, M->rows, N->cols, plan.ktot, 0, plan.ext, gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1,
+                  static_cast<float*>(odata), out->ld, accumulate};
+    *done = false;
+    return BMM_OK;
+}
+}  // namespace
+}  // namespace bmm
+
+BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                             const int32_t* idx, const double* scale, int64_t count, int32_t gemm_mode,
+                             const bmm_mat* out, int32_t accumulate, void* ws, size_t ws_bytes, bmm_stream_t stream) {
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    GemmArgs g;
+    bool done = true;
+    bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs, &g, &done);
+    if (s != BMM_OK || done) return s;
+    BMM_TRY(launch_gemm_bf16_tc(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out, g.ldo,
+                                g.accumulate, status_of(ws), cs));
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_apply_batched(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns, const bmm_blocks* Bs,
+                                     int32_t unit, const int32_t* const* idx, const double* const* scale,
+                                     const int64_t* draws, int32_t gemm_mode, const bmm_mat* outs,
+                                     int32_t accumulate, void* const* ws, const size_t* ws_bytes,
+                                     bmm_stream_t stream) {
+    if (count < 0) return BMM_ERR_ARG;
+    if (count == 0) return BMM_OK;
+    if (!Ms || !Ns || !Bs || !idx || !scale || !draws || !outs || !ws || !ws_bytes) return BMM_ERR_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<GemmArgs> gemms;
+    gemms.reserve((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        GemmArgs g;
+        bool done = true;
+        const bmm_status s = apply_prepare(&Ms[i], &Ns[i], &Bs[i], unit, idx[i], scale[i], draws[i], gemm_mode, &outs[i],
+                                           accumulate, ws[i], ws_bytes[i], cs, &g, &done);
+        if (s != BMM_OK) return s;
+        if (!done) gemms.push_back(g);
+    }
+    if (!gemms.empty())
+        BMM_TRY(launch_gemm_bf16_tc_grouped(gemms.data(), (int64_t)gemms.size(), status_of(ws[0]), cs));
     return BMM_OK;
 }
 

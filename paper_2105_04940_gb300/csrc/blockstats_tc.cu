@@ -7,13 +7,14 @@
 //
 // One CTA per SM pulls blocks from a global counter.  For block k it streams the vectors of the
 // block -- columns of M (length m), then rows of N (length p) -- in chunks of 32 coordinates:
-//   warp 0      one lane: TMA loads of 32 x 32 FP32 boxes (128-byte swizzle) into a stage ring;
+//   warp 0      one lane: TMA loads of 32 x 32 FP32 boxes (128-byte swizzle) into an 8-deep ring;
 //   warp 1      one lane: tcgen05.mma kind::tf32 (M = 128, N = n_k rounded to 16, K = 8) with the
 //               same operand tile as A and B, G_M and G_N in two TMEM accumulators, double
 //               buffered across blocks (512 columns);
 //   warps 2-9   sum squares of every element they see (exact norms); for vectors stored as
 //               storage columns (row-major M) they also transpose the tile into the K-major
-//               operand layout; at the end of a block they fold the norms into a_k, s_k,
+//               operand layout (a 2-deep ring of operand tiles, so the TMA ring is released as
+//               soon as a tile is read); at the end of a block they fold the norms into a_k, s_k,
 //               ||M^k||_F^2, ||N_k||_F^2 and reduce the off-diagonal Gram products from TMEM.
 // A strided operand's first box starts at the 16-byte boundary at or below the block's first
 // column (TMA needs a 16-byte-aligned inner coordinate); the transpose skips the d = off_k mod 4
@@ -28,16 +29,17 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kStages = 4;
+constexpr int kRawStages = 8;                    // TMA ring: covers DRAM latency
+constexpr int kOpStages = 2;                     // transposed operand tiles for the MMA
 constexpr int kBoxBytes = 32 * 32 * 4;           // one 32 x 32 FP32 box
 constexpr int kRawBoxes = 5;                     // strided operand: 3 leading columns + 128
 constexpr int kRawBytes = kRawBoxes * kBoxBytes;  // 20 KB
 constexpr int kOpBytes = 4 * kBoxBytes;           // 128 vectors x 32 coordinates
-constexpr int kStageBytes = kRawBytes + kOpBytes;
+constexpr int kFoldEvery = 8;                    // chunks between FP64 folds of the float-float sums
 constexpr int kConvWarps = 8;
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kThreads = 64 + kConvThreads;
-constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int kSmem = kRawStages * kRawBytes + kOpStages * kOpBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxBlock = 128;
 
@@ -76,24 +78,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                          double* __restrict__ y, double* __restrict__ a, double* __restrict__ ssum,
                          double* __restrict__ mf, double* __restrict__ nf, double* __restrict__ f, DevStatus* st) {
     extern __shared__ uint8_t dsmem[];
-    __shared__ __align__(8) uint64_t bar_full[kStages], bar_conv[kStages], bar_empty[kStages];
+    __shared__ __align__(8) uint64_t bar_full[kRawStages], bar_empty[kRawStages];
+    __shared__ __align__(8) uint64_t bar_opfull[kOpStages], bar_opempty[kOpStages];
     __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_drain, bar_cs;
-    __shared__ StageInfo info[kStages];
+    __shared__ StageInfo info[kRawStages];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ double part[2][2][kMaxBlock];  // [phase][coordinate half][vector]
     __shared__ double red[kConvWarps][5];
 
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
-    auto raw = [&](int s) { return base + s * kStageBytes; };
-    auto opt = [&](int s) { return base + s * kStageBytes + kRawBytes; };
+    auto raw = [&](int s) { return base + s * kRawBytes; };
+    auto opt = [&](int s) { return base + kRawStages * kRawBytes + s * kOpBytes; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kRawStages; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_conv[s]), kConvWarps);
+            // released by the 8 converter warps plus the MMA thread: its commit when the tile is used
+            // in place, a plain arrival once it has read the stage's record when the tile was
+            // transposed.  The MMA thread's arrival is what keeps the producer from overwriting a
+            // record (or advancing bar_full by a whole phase) before the MMA has read it.
             mbar_init(smem_u32(&bar_empty[s]), kConvWarps + 1);
+        }
+        for (int s = 0; s < kOpStages; ++s) {
+            mbar_init(smem_u32(&bar_opfull[s]), kConvWarps);
+            mbar_init(smem_u32(&bar_opempty[s]), 1);
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(smem_u32(&bar_tfull[q]), 1);
@@ -105,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // operand tiles start as zeros, so rows no copy ever wrote are finite
-    for (int e = threadIdx.x; e < kStages * kStageBytes / 16; e += kThreads)
+    for (int e = threadIdx.x; e < (kRawStages * kRawBytes + kOpStages * kOpBytes) / 16; e += kThreads)
         reinterpret_cast<uint4*>(base)[e] = make_uint4(0, 0, 0, 0);
     if (warp == 1) tmem_alloc(smem_u32(&s_tmem), kTmemCols);
     tc_fence_before();
@@ -156,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         si.strided = strided;
                         const uint32_t fb = smem_u32(&bar_full[stage]);
                         mbar_expect_tx(fb, (uint32_t)(nb * kBoxBytes));
-                        uint8_t* dst = strided ? raw(stage) : opt(stage);
+                        uint8_t* dst = raw(stage);  // both kinds of tile land in the TMA ring
                         for (int b = 0; b < nb; ++b) {
                             if (strided)
                                 tma_load_2d(smem_u32(dst + b * kBoxBytes), map, fb, (int32_t)(lo - d + 32 * b),
@@ -167,19 +177,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         issued_mask |= 1u << stage;
                         issued_phase = (issued_phase & ~(1u << stage)) | (ph << stage);
-                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                        if (++stage == kRawStages) { stage = 0; ph ^= 1u; }
                     }
                 }
             }
             if (aborted)
-                for (int s = 0; s < kStages; ++s)
+                for (int s = 0; s < kRawStages; ++s)
                     if (issued_mask & (1u << s)) mbar_wait(smem_u32(&bar_full[s]), (issued_phase >> s) & 1u, nullptr);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------ MMA issuer
-            int stage = 0;
-            uint32_t ph = 0;
+            int stage = 0, ostage = 0;
+            uint32_t ph = 0, oph = 0;
             int it = 0, acc = 0;
             bool aborted = false;
             while (true) {
@@ -193,20 +203,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                 }
-                if (si.strided && !mbar_wait(smem_u32(&bar_conv[stage]), ph, &s_abort)) { aborted = true; break; }
+                uint8_t* tile = raw(stage);
+                if (si.strided) {
+                    mbar_arrive(smem_u32(&bar_empty[stage]));  // record read; the raw tile is not used here
+                    if (!mbar_wait(smem_u32(&bar_opfull[ostage]), oph, &s_abort)) { aborted = true; break; }
+                    tile = opt(ostage);
+                }
                 tc_fence_after();
                 const int npad = (si.nk + 15) & ~15;
                 const uint32_t d = tmem + (uint32_t)(acc * 256 + si.phase * 128);
-                const uint64_t desc = sw128_desc(smem_u32(opt(stage)));
+                const uint64_t desc = sw128_desc(smem_u32(tile));
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
                     tc_mma_tf32(d, desc + 2ull * kk, desc + 2ull * kk, idesc_tf32(npad), (!si.first || kk > 0) ? 1u : 0u);
-                tc_commit(smem_u32(&bar_empty[stage]));
+                if (si.strided) {
+                    tc_commit(smem_u32(&bar_opempty[ostage]));
+                    if (++ostage == kOpStages) { ostage = 0; oph ^= 1u; }
+                } else {
+                    tc_commit(smem_u32(&bar_empty[stage]));
+                }
                 if (si.last && si.phase == 1) {
                     tc_commit(smem_u32(&bar_tfull[acc]));
                     ++it;
                 }
-                if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                if (++stage == kRawStages) { stage = 0; ph ^= 1u; }
             }
             if (aborted) {
                 tc_commit(smem_u32(&bar_drain));
@@ -218,8 +238,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int t = threadIdx.x - 64;
         const int i = t & 127, hh = t >> 7;
         const int cw = warp - 2;  // converter warp 0..7
-        int stage = 0;
-        uint32_t ph = 0;
+        int stage = 0, ostage = 0;
+        uint32_t ph = 0, oph = 0;
         int it = 0;
         FF ff;
         ff.zero();
@@ -227,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int since_fold = 0;
         int cs_uses = 0;
         const uint32_t cs_bar = smem_u32(&bar_cs);
+        bool aborted = false;
         while (true) {
             if (!mbar_wait(smem_u32(&bar_full[stage]), ph, &s_abort)) break;
             const StageInfo si = info[stage];
@@ -247,36 +268,41 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[q] = 0.f;
                 }
+                // the raw tile is read: hand it back to the producer
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
                 if (mine) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) ff.add_prod(v[q], v[q]);
                 }
-                uint8_t* dst = opt(stage) + i * 128;
+                if (!mbar_wait(smem_u32(&bar_opempty[ostage]), oph ^ 1u, &s_abort)) { aborted = true; break; }
+                uint8_t* dst = opt(ostage) + i * 128;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int chunk = (4 * hh + q) ^ (i & 7);
                     *reinterpret_cast<float4*>(dst + chunk * 16) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
                 fence_async_smem();
-            } else if (mine) {
-                const uint8_t* row = opt(stage) + i * 128;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bar_opfull[ostage]));
+                if (++ostage == kOpStages) { ostage = 0; oph ^= 1u; }
+            } else {
+                if (mine) {
+                    const uint8_t* row = raw(stage) + i * 128;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 w4 = *reinterpret_cast<const float4*>(row + (((4 * hh + q) ^ (i & 7)) << 4));
-                    ff.add_prod(w4.x, w4.x);
-                    ff.add_prod(w4.y, w4.y);
-                    ff.add_prod(w4.z, w4.z);
-                    ff.add_prod(w4.w, w4.w);
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 w4 = *reinterpret_cast<const float4*>(row + (((4 * hh + q) ^ (i & 7)) << 4));
+                        ff.add_prod(w4.x, w4.x);
+                        ff.add_prod(w4.y, w4.y);
+                        ff.add_prod(w4.z, w4.z);
+                        ff.add_prod(w4.w, w4.w);
+                    }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
             }
-            // bar_conv advances on every use of the stage (contiguous tiles too), so its phase stays
-            // that of the stage ring; the MMA waits on it only for transposed tiles
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(smem_u32(&bar_conv[stage]));
-                mbar_arrive(smem_u32(&bar_empty[stage]));
-            }
-            if (++since_fold == 2) {
+            ff.renorm();
+            if (++since_fold == kFoldEvery) {
                 dacc += ff.value();
                 ff.zero();
                 since_fold = 0;
@@ -288,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (STATS) part[si.phase][hh][i] = dacc;
                 dacc = 0.0;
             }
-            if (++stage == kStages) { stage = 0; ph ^= 1u; }
+            if (++stage == kRawStages) { stage = 0; ph ^= 1u; }
             if (!(si.last && si.phase == 1)) continue;
 
             // ---- block epilogue
@@ -309,7 +335,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // off-diagonal Gram products from TMEM (rows = lanes of this warp's quadrant)
             const int acc = it & 1;
-            double offd = 0.0;
+            FF offf;
+            offf.zero();
             if (mbar_wait(smem_u32(&bar_tfull[acc]), (uint32_t)(it >> 1) & 1u, &s_abort)) {
                 tc_fence_after();
                 const int q4 = warp & 3, half = cw >> 2;
@@ -326,8 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
                             const int jj = c0 + e;
-                            if (jj < nk && jj != r)
-                                offd += (double)__uint_as_float(gm[e]) * (double)__uint_as_float(gn[e]);
+                            if (jj < nk && jj != r) offf.add_prod(__uint_as_float(gm[e]), __uint_as_float(gn[e]));
                         }
                     }
                 }
@@ -336,6 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[acc]));
             }
             ++it;
+            double offd = offf.value();
             sa = warp_sum(sa);
             ss = warp_sum(ss);
             sx = warp_sum(sx);

@@ -57,6 +57,12 @@ struct FF {
         hi = t;
         lo = __fadd_rn(lo, __fadd_rn(e, pe));
     }
+    // Fast2Sum: |hi| >= |lo| holds for the sums of squares and products accumulated here
+    __device__ __forceinline__ void renorm() {
+        const float s = __fadd_rn(hi, lo);
+        lo = __fsub_rn(lo, __fsub_rn(s, hi));
+        hi = s;
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 

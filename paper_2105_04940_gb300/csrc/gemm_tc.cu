@@ -43,11 +43,43 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
     *tn = r / gm;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(192, 1)
-    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-                        int N, long long k_host, const long long* k_dev, int k_mult, float* __restrict__ out,
-                        long long ldo, int accumulate, int vec_ok, DevStatus* st) {
+// One product of a (possibly grouped) launch.  The table travels as a __grid_constant__ kernel
+// parameter, so the tensor maps are used in place and the whole launch can sit in a CUDA graph.
+struct GemmProblem {
+    CUtensorMap mapA;
+    CUtensorMap mapB;
+    float* out;
+    long long ldo;
+    const long long* k_dev;
+    long long k_host;
+    int M, N;
+    int tiles_m, tiles_n;
+    int tile_begin;
+    int k_mult;
+    int accumulate;
+    int vec_ok;
+};
+template <int G> struct GemmTable {
+    int count;
+    int total_tiles;
+    GemmProblem prob[G];
+};
+constexpr int kMaxGroup = 80;  // 80 x 384-byte entries keep the table under the 32 KB kernel-parameter limit
+
+template <int G>
+__device__ __forceinline__ int find_problem(const GemmTable<G>& tab, int tile) {
+    int pi = 0;
+    while (pi + 1 < tab.count && tile >= tab.prob[pi + 1].tile_begin) ++pi;
+    return pi;
+}
+
+__device__ __forceinline__ int problem_kb(const GemmProblem& pr) {
+    const long long K = pr.k_dev ? (long long)pr.k_mult * (((*pr.k_dev) + 63) / 64 * 64) : pr.k_host;
+    return (int)(K / BK);
+}
+
+template <int BN, int G>
+__global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_constant__ GemmTable<G> tab, DevStatus* st) {
     using C = Cfg<BN>;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t bar_full[C::STAGES];
@@ -62,11 +94,7 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t* sA = base;
     uint8_t* sB = base + C::STAGES * C::A_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    const long long K = k_dev ? (long long)k_mult * (((*k_dev) + 63) / 64 * 64) : k_host;
-    const int num_kb = (int)(K / BK);
-    const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-    const int num_tiles = tiles_m * tiles_n;
+    const int num_tiles = tab.total_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -81,12 +109,7 @@ __global__ void __launch_bounds__(192, 1)
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"((uint32_t)C::TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 1) tmem_alloc(smem_u32(&s_tmem), (uint32_t)C::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -99,8 +122,10 @@ __global__ void __launch_bounds__(192, 1)
         uint32_t issued_mask = 0, issued_phase = 0;
         bool aborted = false;
         for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x) {
+            const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             int tm, tn;
-            tile_coords(tile, tiles_m, tiles_n, &tm, &tn);
+            tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, &tm, &tn);
+            const int num_kb = problem_kb(pr);
             for (int kb = 0; kb < num_kb; ++kb) {
                 if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
                     aborted = true;
@@ -108,8 +133,8 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 const uint32_t fb = smem_u32(&bar_full[stage]);
                 mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
-                tma_load_2d(smem_u32(sA + stage * C::A_BYTES), &tmA, fb, kb * BK, tm * BM);
-                tma_load_2d(smem_u32(sB + stage * C::B_BYTES), &tmB, fb, kb * BK, tn * BN);
+                tma_load_2d(smem_u32(sA + stage * C::A_BYTES), &pr.mapA, fb, kb * BK, tm * BM);
+                tma_load_2d(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb, kb * BK, tn * BN);
                 issued_mask |= 1u << stage;
                 issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                 if (++stage == C::STAGES) {
@@ -129,6 +154,8 @@ __global__ void __launch_bounds__(192, 1)
         int it = 0;
         bool aborted = false;
         for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x, ++it) {
+            const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
+            const int num_kb = problem_kb(pr);
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             if (!mbar_wait(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
@@ -166,32 +193,35 @@ __global__ void __launch_bounds__(192, 1)
         const int q = warp & 3;
         int it = 0;
         for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+            const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
+            const int num_kb = problem_kb(pr);
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             if (!mbar_wait(smem_u32(&bar_tfull[acc]), aph, &s_abort)) break;
             tc_fence_after();
             int tm, tn;
-            tile_coords(tile, tiles_m, tiles_n, &tm, &tn);
+            tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, &tm, &tn);
             const int row = tm * BM + q * 32 + lane;
+            const int M = pr.M, N = pr.N;
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
                 uint32_t r[32];
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + cc * 32);
                 TMEM_LD_32X32B_X32(taddr, r);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tmem_ld_wait();
                 if (num_kb == 0) {
 #pragma unroll
                     for (int e = 0; e < 32; ++e) r[e] = 0u;
                 }
                 const int col0 = tn * BN + cc * 32;
                 if (row < M && col0 < N) {
-                    float* o = out + (long long)row * ldo + col0;
-                    if (vec_ok && col0 + 32 <= N) {
+                    float* o = pr.out + (long long)row * pr.ldo + col0;
+                    if (pr.vec_ok && col0 + 32 <= N) {
 #pragma unroll
                         for (int v = 0; v < 8; ++v) {
                             float4 val = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
                                                      __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
-                            if (accumulate) {
+                            if (pr.accumulate) {
                                 const float4 old = *reinterpret_cast<const float4*>(o + 4 * v);
                                 val.x += old.x; val.y += old.y; val.z += old.z; val.w += old.w;
                             }
@@ -199,7 +229,7 @@ __global__ void __launch_bounds__(192, 1)
                         }
                     } else {
                         const int ne = min(32, N - col0);
-                        for (int e = 0; e < ne; ++e) o[e] = (accumulate ? o[e] : 0.0f) + __uint_as_float(r[e]);
+                        for (int e = 0; e < ne; ++e) o[e] = (pr.accumulate ? o[e] : 0.0f) + __uint_as_float(r[e]);
                     }
                 }
             }
@@ -214,8 +244,7 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
-                     : "memory");
+        tmem_dealloc(tmem, (uint32_t)C::TMEM_COLS);
     }
     if (threadIdx.x == 0 && s_abort) set_status(st, BMM_ERR_TIMEOUT, 1);
 }
@@ -253,26 +282,47 @@ int num_sms() {
     return n > 0 ? n : 1;
 }
 
-template <int BN>
-cudaError_t launch_bn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M, int64_t N,
-                      int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out, int64_t ldo,
-                      int accumulate, DevStatus* st, cudaStream_t s) {
+// Fill one table entry; returns false when a tensor map cannot be made.
+bool fill_problem(GemmProblem* pr, int BN, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
+                  int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
+                  int64_t ldo, int accumulate) {
+    if (!make_map(&pr->mapA, A, M, kdim, lda, BM) || !make_map(&pr->mapB, B, N, kdim, ldb, BN)) return false;
+    pr->out = out;
+    pr->ldo = ldo;
+    pr->k_dev = reinterpret_cast<const long long*>(k_dev);
+    pr->k_host = k_host;
+    pr->M = (int)M;
+    pr->N = (int)N;
+    pr->tiles_m = (int)ceil_div(M, BM);
+    pr->tiles_n = (int)ceil_div(N, BN);
+    pr->k_mult = k_mult;
+    pr->accumulate = accumulate;
+    pr->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (ldo % 4 == 0);
+    return true;
+}
+
+template <int BN, int G>
+cudaError_t launch_table(const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
     using C = Cfg<BN>;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, M, kdim, lda, BM) || !make_map(&mb, B, N, kdim, ldb, BN)) return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int64_t tiles = ceil_div(M, BM) * ceil_div(N, BN);
-    const int grid = (int)imin(tiles, num_sms());
-    const int vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (ldo % 4 == 0);
-    (count_launch(), gemm_bf16_tc_kernel<BN><<<grid, 192, C::SMEM, s>>>(ma, mb, (int)M, (int)N, (long long)k_host,
-                                                       reinterpret_cast<const long long*>(k_dev), k_mult, out,
-                                                       (long long)ldo, accumulate, vec_ok, st));
+    if (tab.total_tiles == 0) return cudaSuccess;
+    const int grid = (int)imin(tab.total_tiles, num_sms());
+    (count_launch(), gemm_bf16_tc_kernel<BN, G><<<grid, 192, C::SMEM, s>>>(tab, st));
     return cudaGetLastError();
+}
+
+bool gemm_args_ok(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M, int64_t N,
+                  int64_t kdim, int64_t k_host, const int64_t* k_dev) {
+    if (M > 0x7fffffff || N > 0x7fffffff || (lda % 8) != 0 || (ldb % 8) != 0 || kdim <= 0 || kdim > lda ||
+        kdim > ldb || (k_dev == nullptr && (k_host % 64) != 0))
+        return false;
+    return !((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15));
 }
 
 }  // namespace
@@ -289,12 +339,47 @@ cudaError_t launch_gemm_bf16_tc(const __nv_bfloat16* A, int64_t lda, const __nv_
                                 int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
                                 int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    if (M > 0x7fffffff || N > 0x7fffffff || (lda % 8) != 0 || (ldb % 8) != 0 || kdim <= 0 || kdim > lda ||
-        kdim > ldb || (k_dev == nullptr && (k_host % 64) != 0))
+    if (!gemm_args_ok(A, lda, B, ldb, M, N, kdim, k_host, k_dev)) return cudaErrorInvalidValue;
+    const int BN = N <= 128 ? 128 : 256;
+    GemmTable<1> tab;
+    tab.count = 1;
+    if (!fill_problem(&tab.prob[0], BN, A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate))
         return cudaErrorInvalidValue;
-    if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return cudaErrorInvalidValue;
-    if (N <= 128) return launch_bn<128>(A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate, st, s);
-    return launch_bn<256>(A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate, st, s);
+    tab.prob[0].tile_begin = 0;
+    tab.total_tiles = tab.prob[0].tiles_m * tab.prob[0].tiles_n;
+    return BN == 128 ? launch_table<128, 1>(tab, st, s) : launch_table<256, 1>(tab, st, s);
+}
+
+cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, DevStatus* st, cudaStream_t s) {
+    // products are grouped by tile width; each launch takes up to kMaxGroup of them
+    for (int pass = 0; pass < 2; ++pass) {
+        const int BN = pass == 0 ? 128 : 256;
+        static GemmTable<kMaxGroup> tab;  // host-side staging of the kernel parameter (30 KB)
+        tab.count = 0;
+        tab.total_tiles = 0;
+        for (int64_t i = 0; i <= count; ++i) {
+            const bool flush = (i == count) || tab.count == kMaxGroup;
+            if (flush && tab.count > 0) {
+                cudaError_t e = BN == 128 ? launch_table<128, kMaxGroup>(tab, st, s) : launch_table<256, kMaxGroup>(tab, st, s);
+                if (e != cudaSuccess) return e;
+                tab.count = 0;
+                tab.total_tiles = 0;
+            }
+            if (i == count) break;
+            const GemmArgs& g = args[i];
+            if (g.M <= 0 || g.N <= 0) continue;
+            if ((g.N <= 128 ? 128 : 256) != BN) continue;
+            if (!gemm_args_ok(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev)) return cudaErrorInvalidValue;
+            GemmProblem& pr = tab.prob[tab.count];
+            if (!fill_problem(&pr, BN, g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out,
+                              g.ldo, g.accumulate))
+                return cudaErrorInvalidValue;
+            pr.tile_begin = tab.total_tiles;
+            tab.total_tiles += pr.tiles_m * pr.tiles_n;
+            ++tab.count;
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace bmm

@@ -95,6 +95,20 @@ cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64
                             int64_t k_host, const int64_t* k_dev, double* out, int64_t ldo, int accumulate,
                             cudaStream_t s);
 bool tc_gemm_supported();
+// Many independent products in as few persistent launches as the kernel-parameter limit allows.
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    int64_t lda;
+    const __nv_bfloat16* B;
+    int64_t ldb;
+    int64_t M, N, kdim, k_host;
+    const int64_t* k_dev;
+    int k_mult;
+    float* out;
+    int64_t ldo;
+    int accumulate;
+};
+cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, DevStatus* st, cudaStream_t s);
 
 // ---- backward.cu
 int64_t unique_scratch_bytes(int64_t space, int64_t count);

@@ -4,7 +4,8 @@
 // tiny kernel folds them into the per-block a_k, s_k, ||M^k||_F^2, ||N_k||_F^2.
 // The pass is HBM-bound: 16-byte vector loads, many loads in flight per thread,
 // FP64-accurate sums built from FP32 float-float pairs (GB300's FP64 rate is too
-// low to square every element in FP64 at HBM speed) folded into FP64 every 32 terms.
+// low to square every element in FP64 at HBM speed), renormalised every 32 terms and folded
+// into FP64 every 128 (one warp-wide FP64 instruction costs about 64 FP32 ones on GB300).
 #include "internal.h"
 
 namespace bmm {
@@ -26,6 +27,7 @@ struct SqAcc {
     __device__ __forceinline__ void add(float v) { ff.add_prod(v, v); }
     __device__ __forceinline__ void add(double v) { d = fma(v, v, d); }
     __device__ __forceinline__ void fold() { d += ff.value(); ff.zero(); }
+    __device__ __forceinline__ void renorm() { ff.renorm(); }
     __device__ __forceinline__ double value() const { return d + ff.value(); }
 };
 
@@ -83,13 +85,18 @@ __global__ void __launch_bounds__(256) sqnorm_rows_kernel(const T* __restrict__ 
         if (vec_ok) {
             const int64_t nvec = len / E;
             int64_t it = lane;
+            int batches = 0;
             for (; it + 7 * 32 < nvec; it += 8 * 32) {
                 uint4 raw[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) raw[u] = ldg16(row + (it + u * 32) * E);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) acc16(acc, raw[u], T());
-                acc.fold();
+                acc.renorm();
+                if (++batches == 4) {
+                    acc.fold();
+                    batches = 0;
+                }
             }
             for (; it < nvec; it += 32) acc16(acc, ldg16(row + it * E), T());
             acc.fold();
@@ -124,7 +131,11 @@ __global__ void __launch_bounds__(128) sqnorm_cols_kernel(const T* __restrict__ 
             for (int u = 0; u < 8; ++u) raw[u] = ldg16(X + (r + u) * ld + c0);
 #pragma unroll
             for (int u = 0; u < 8; ++u) acc16_split(acc, raw[u], T());
-            if (++batches == 4) {
+            if ((++batches & 3) == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[e].renorm();
+            }
+            if (batches == 16) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc[e].fold();
                 batches = 0;

@@ -95,11 +95,12 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
 
 def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
         gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None,
-        fmode: int = A.F_TC) -> dict:
+        fmode: int = A.F_TC, fused_stats: bool = False) -> dict:
     """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring).
 
-    fmode: how OPL and WU compute ||M^k N_k||_F^2 -- A.F_TC (fused with the statistics pass on the
-    tensor cores when the inputs allow it, else exact) or A.F_EXACT.
+    fmode: how OPL and WU compute ||M^k N_k||_F^2 -- A.F_TC (tensor-core Grams when the inputs
+    allow it, else exact) or A.F_EXACT.  fused_stats: with F_TC, one pass computes the statistics
+    and f together; otherwise the norm pass runs first and the Gram pass reuses its statistics.
 
     events: if a list, (stage name, torch.cuda.Event) pairs are appended at the stage
     boundaries (recorded on the current stream; used for timing only).
@@ -126,14 +127,14 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         if method == "SSM":
             A.bmm_probs(M, N, B, A.P_BLK_NORMPROD, A.F_NONE, pblk, st, ws)
             mark("stats")
-        elif fmode == A.F_TC:
+        elif fmode == A.F_TC and fused_stats:
             A.bmm_probs(M, N, B, A.P_BLK_PRODNORM, A.F_TC, pblk, st, ws)
             mark("stats_f")
         else:
             A.bmm_probs(M, N, B, A.P_BLK_NORMPROD, A.F_NONE, None, st, ws)
             mark("stats")
-            A.bmm_probs(M, N, B, A.P_BLK_PRODNORM, A.F_EXACT | A.REUSE_STATS, pblk, st, ws)
-            mark("exact_f")
+            A.bmm_probs(M, N, B, A.P_BLK_PRODNORM, fmode | A.REUSE_STATS, pblk, st, ws)
+            mark("exact_f" if fmode == A.F_EXACT else "gram_f")
         idx = torch.empty(c, dtype=torch.int32, device=dev)
         scale = torch.empty(c, dtype=torch.float64, device=dev)
         A.bmm_sample(pblk, A.UNIT_BLOCK, B, None, c, seed, sid, idx, scale, ws)
@@ -154,14 +155,14 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         A.bmm_blocksizes(None, None, B, None, A.CK_EQUAL, c, None, None, 0, ck, g, None, ws)
         mark("blocksizes")
     elif method == "OPL":
-        if fmode == A.F_TC:
+        if fmode == A.F_TC and fused_stats:
             A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_TC, p, st, ws)
             mark("stats_f")
         else:
             A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
             mark("stats")
-            A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_EXACT | A.REUSE_STATS, None, st, ws)
-            mark("exact_f")
+            A.bmm_probs(M, N, B, A.P_COL_OPT, fmode | A.REUSE_STATS, None, st, ws)
+            mark("exact_f" if fmode == A.F_EXACT else "gram_f")
         A.bmm_blocksizes(M, N, B, st, A.CK_OPT, c, None, None, 0, ck, g, None, ws)
         mark("blocksizes")
     elif method == "ONC":
@@ -258,3 +259,40 @@ class _Lazy:
 
 
 SampledMatmul = _Lazy()
+
+
+def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF16, outs=None, streams=None,
+                c0: int | None = None, fmode: int = A.F_TC) -> list:
+    """Many independent products (the batched configuration).
+
+    The design and the draws of each product (bmm_probs, bmm_blocksizes, bmm_sample) are spread
+    round-robin over ``streams`` so that small products overlap; the products themselves run
+    through one bmm_apply_batched call, whose BF16 GEMMs share persistent tensor-core launches.
+    Every step is an asynchronous C-ABI call, so the whole sequence can be captured with
+    torch.cuda.graph and replayed as one graph launch.  Each Problem needs its own workspace.
+    """
+    torch = _torch()
+    main = torch.cuda.current_stream()
+    if streams is None:
+        streams = [main]
+    for s in streams:
+        if s is not main:
+            s.wait_stream(main)
+    results = []
+    for i, prob in enumerate(probs):
+        with torch.cuda.stream(streams[i % len(streams)]):
+            results.append(run(prob, method, int(cs[i]), int(seeds[i]), c0=c0, gemm_mode=gemm_mode,
+                               compute_product=False, fmode=fmode))
+    for s in streams:
+        if s is not main:
+            main.wait_stream(s)
+    if outs is None:
+        dt = torch.float64 if gemm_mode == A.GEMM_F64 else torch.float32
+        outs = [torch.empty(p.M.shape[0], p.N.shape[1], dtype=dt, device=p.M.device) for p in probs]
+    unit = results[0]["unit"] if results else A.UNIT_COLUMN
+    A.bmm_apply_batched([p.M for p in probs], [p.N for p in probs], [p.B for p in probs], unit,
+                        [r["idx"] for r in results], [r["scale"] for r in results], [int(c) for c in cs],
+                        gemm_mode, outs, False, [p.ws for p in probs])
+    for r, o in zip(results, outs):
+        r["out"] = o
+    return results

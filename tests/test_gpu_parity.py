@@ -108,15 +108,25 @@ def _tf32_gram_bound(M, N, off, m, p):
 
 
 @pytest.mark.parametrize("layouts", [("row", "row"), ("col", "col"), ("row", "col"), ("col", "row")])
-def test_fused_statistics_and_tensor_core_f(bmm, layouts):
-    """One pass for x, y, a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 and f_k = s_k + TF32 off-diagonal trace."""
-    m, n, p = 300, 6000, 261
+@pytest.mark.parametrize("p", [264, 261])
+def test_fused_statistics_and_tensor_core_f(bmm, layouts, p):
+    """One pass for x, y, a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 and f_k = s_k + TF32 off-diagonal trace.
+
+    p = 264 keeps every leading dimension a multiple of 4, so each storage order runs the fused
+    tensor-core pass; p = 261 makes some leading dimensions odd, which takes the exact fallback."""
+    m, n = 300, 6000
     off, M, N, Mt, Nt = _problem(m, n, p, 60, seed=41, dtype=np.float32, lo=16, hi=128)
     Mt, Nt = as_layout(Mt, layouts[0]), as_layout(Nt, layouts[1])
     prob = bmm.prepare(Mt, Nt, off, max_draws=100)
     pv = torch.empty(n, dtype=torch.float64, device=Mt.device)
+    launches = bmm._abi.bmm_launch_count()
     bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, pv, prob.st, prob.ws)
     bmm.check_status(prob)
+    # the fused pass is one kernel (plus the probabilities); odd leading dimensions fall back
+    ld_m = n if layouts[0] == "row" else m
+    ld_n = p if layouts[1] == "row" else n
+    fused = ld_m % 4 == 0 and ld_n % 4 == 0
+    assert (bmm._abi.bmm_launch_count() - launches == 2) == fused
     x, y = oracle.col_row_sq_norms(M, N)
     st = oracle.block_stats(x, y, off)
     assert rel_err(host(prob.st["x"]), x) < 1e-12
@@ -139,9 +149,9 @@ def test_fused_statistics_and_tensor_core_f(bmm, layouts):
 def test_fused_statistics_low_rank_blocks(bmm):
     """Rank-one aligned blocks (off-diagonal trace as large as the diagonal) and one full 128 block."""
     rng = np.random.default_rng(3)
-    sizes = np.array([128, 5, 77, 16, 100, 33])
+    sizes = np.array([128, 5, 77, 16, 100, 34])  # n = 360: every leading dimension % 4 == 0
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    n, m, p = int(off[-1]), 96, 150
+    n, m, p = int(off[-1]), 96, 152
     M = rng.standard_normal((m, n)).astype(np.float32)
     N = rng.standard_normal((n, p)).astype(np.float32)
     u, v = rng.standard_normal(m), rng.standard_normal(p)
@@ -151,8 +161,10 @@ def test_fused_statistics_low_rank_blocks(bmm):
     M, N = M.astype(np.float64), N.astype(np.float64)
     Mt, Nt = to_dev(M.astype(np.float32)), to_dev(N.astype(np.float32))
     prob = bmm.prepare(Mt, Nt, off, max_draws=50)
+    launches = bmm._abi.bmm_launch_count()
     bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, None, prob.st, prob.ws)
     bmm.check_status(prob)
+    assert bmm._abi.bmm_launch_count() - launches == 1  # the fused pass alone (no p requested)
     f = oracle.block_frob_sq(M, N, off)
     err = np.abs(host(prob.st["f"]) - f)
     assert np.all(err <= _tf32_gram_bound(M, N, off, m, p) + 1e-12 * f)
@@ -426,3 +438,89 @@ def test_device_status_conditions(bmm):
         bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, idx, sc, 8, bmm._abi.GEMM_F64,
                       torch.empty(32, 16, dtype=torch.float64, device=Mt.device), False, prob.ws[:100])
     assert e.value.code == bmm._abi.ERR_WORKSPACE
+
+
+def test_mlp_forward_backward_matches_oracle_chain(bmm):
+    """Differentiation configuration at small size: y_l = GELU(y_{l-1} W_l) with every product sampled
+    (ONC, K = 8 blocks of 64, c = 2 blocks -> L = 128), forward and backward in FP64 through the
+    autograd function, against the same chain built from the oracle's sample and adjoint."""
+    import math
+    rng = np.random.default_rng(17)
+    m, n = 64, 512
+    off = S.block_offsets_equal(n, 8)
+    L = bmm.equal_budget(2, n, 8)
+    X = rng.standard_normal((m, n))
+    Ws = [rng.standard_normal((n, n)) / math.sqrt(n) for _ in range(4)]
+    R = rng.standard_normal((m, n))
+
+    def gelu(z):
+        return 0.5 * z * (1.0 + np.vectorize(math.erf)(z / math.sqrt(2.0)))
+
+    def dgelu(z):
+        return 0.5 * (1.0 + np.vectorize(math.erf)(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+
+    # oracle chain
+    h, pre, samples = X, [], []
+    for l, W in enumerate(Ws):
+        r = oracle.run_method(h, W, off, "ONC", L, seed=100 + l)
+        pre.append((h, r["CD"]))
+        samples.append((r["idx"], r["scale"]))
+        h = gelu(r["CD"])
+    G = R.copy()
+    dWs = [None] * 4
+    for l in range(3, -1, -1):
+        hin, z = pre[l]
+        G = G * dgelu(z)
+        dh, dW = oracle.adjoint_columns(hin, Ws[l], samples[l][0], samples[l][1], G)
+        dWs[l], G = dW, dh
+    # GPU chain through SampledMatmul
+    Xt = to_dev(X).requires_grad_(True)
+    Wt = [to_dev(W).requires_grad_(True) for W in Ws]
+    h = Xt
+    for l, W in enumerate(Wt):
+        h = torch.nn.functional.gelu(bmm.sampled_matmul(h, W, off, method="ONC", c=L, seed=100 + l, mode="f64"))
+    (h * to_dev(R)).sum().backward()
+    np.testing.assert_allclose(host(Xt.grad), G, rtol=1e-8, atol=1e-8 * np.abs(G).max())
+    for l in range(4):
+        np.testing.assert_allclose(host(Wt[l].grad), dWs[l], rtol=1e-8, atol=1e-8 * np.abs(dWs[l]).max())
+
+
+def test_batched_uneven_products_and_graph_replay(bmm):
+    """Uneven products (both GEMM tile widths) through bmm_apply_batched, then the same sequence
+    captured as one CUDA graph and replayed: identical outputs, each within the BF16 bound."""
+    rng = np.random.default_rng(23)
+    probs, host_inputs, cs = [], [], []
+    for i in range(9):
+        m = int(rng.integers(1, 5)) * 128 - (17 if i % 3 == 0 else 0)
+        p = int(rng.choice([96, 200, 384, 520]))
+        n = int(rng.integers(2, 5)) * 1024
+        K = n // 64
+        off = S.block_offsets_uneven(n, K, 32, 100, seed=100 + i)
+        M, N = S.scaled_gaussian(m, n, p, off, 1.0, seed=200 + i, dtype=np.float32)
+        Mt, Nt = to_dev(M), to_dev(N)
+        c = bmm.equal_budget(max(1, K // 8), n, K)
+        probs.append(bmm.prepare(Mt, Nt, off, max_draws=c, gemm_mode=bmm._abi.GEMM_BF16))
+        host_inputs.append((M.astype(np.float64), N.astype(np.float64), off))
+        cs.append(c)
+    seeds = list(range(50, 59))
+    res = bmm.run_batched(probs, "ONC", cs, seeds, gemm_mode=bmm._abi.GEMM_BF16)
+    for pr in probs:
+        bmm.check_status(pr)
+    eager = [host(r["out"]).astype(np.float64) for r in res]
+    for (M, N, off), r, c, got in zip(host_inputs, res, cs, eager):
+        idx, scale = host(r["idx"]), host(r["scale"])
+        want = oracle.sampled_product_columns(M, N, idx, scale)
+        assert np.all(np.abs(got - want) <= _tol("bf16", c) * product_bound(M, N, idx, scale) + 1e-300)
+    # one graph: design, draws and the batched product of all nine
+    side = [torch.cuda.Stream() for _ in range(3)]
+    outs = [torch.empty_like(r["out"]) for r in res]
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        gres = bmm.run_batched(probs, "ONC", cs, seeds, gemm_mode=bmm._abi.GEMM_BF16, outs=outs, streams=side)
+    g.replay()
+    torch.cuda.synchronize()
+    for pr in probs:
+        bmm.check_status(pr)
+    for a_, b_ in zip(eager, outs):
+        np.testing.assert_array_equal(host(b_).astype(np.float64), a_)
