@@ -7,20 +7,25 @@
 //
 // One CTA per SM pulls blocks from a global counter.  For block k it streams the vectors of the
 // block -- columns of M (length m), then rows of N (length p) -- in chunks of 32 coordinates:
-//   warp 0      one lane: TMA loads of 32 x 32 FP32 boxes (128-byte swizzle) into an 8-deep ring;
-//   warp 1      one lane: tcgen05.mma kind::tf32 (M = 128, N = n_k rounded to 16, K = 8) with the
-//               same operand tile as A and B, G_M and G_N in two TMEM accumulators, double
-//               buffered across blocks (512 columns);
-//   warps 2-9   sum squares of every element they see (exact norms); for vectors stored as
-//               storage columns (row-major M) they also transpose the tile into the K-major
-//               operand layout (a 2-deep ring of operand tiles, so the TMA ring is released as
-//               soon as a tile is read); at the end of a block they fold the norms into a_k, s_k,
-//               ||M^k||_F^2, ||N_k||_F^2 and reduce the off-diagonal Gram products from TMEM.
+//   warp 0      one lane: TMA loads of 32 x 32 FP32 boxes into an 8-deep ring (128-byte swizzle,
+//               in 32-byte atoms for strided storage);
+//   warp 1      one lane: tcgen05.mma kind::tf32 (M = 128, N = the block's operand rows rounded to
+//               16, K = 8) with the same operand tile as A and B, G_M and G_N in two TMEM
+//               accumulators, double buffered across blocks (512 columns).  A tile whose vectors
+//               are its rows (contiguous storage) is a K-major operand, one whose vectors are its
+//               columns (strided storage: row-major M, column-major N) an MN-major operand; both are
+//               read where TMA put them;
+//   warps 2-9   sum squares of every element they see (exact norms) and, at the end of a block,
+//               fold the norms into a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 and reduce the off-diagonal
+//               Gram products from TMEM.
 // A strided operand's first box starts at the 16-byte boundary at or below the block's first
-// column (TMA needs a 16-byte-aligned inner coordinate); the transpose skips the d = off_k mod 4
-// leading columns.  Rows of the operand tile beyond n_k hold neighbouring data or zeros and are
-// masked out of every sum.  All waits are bounded; on expiry the CTA records BMM_ERR_TIMEOUT,
-// lets its copies and MMAs in flight land, frees TMEM and returns.
+// column (TMA needs a 16-byte-aligned inner coordinate), so its vectors are operand rows
+// d .. d + n_k - 1 with d = off_k mod 4; the contiguous operand of the same block is loaded d rows
+// early to match.  When d + n_k exceeds the MMA's 128 rows (n_k > 125) the strided tiles are
+// transposed by warps 2-9 into a 2-deep ring of K-major tiles instead, with the block at row 0.
+// Operand rows outside the block hold neighbouring data or zeros and are masked out of every
+// sum.  All waits are bounded; on expiry the CTA records BMM_ERR_TIMEOUT, lets its copies and
+// MMAs in flight land, frees TMEM and returns.
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -43,21 +48,35 @@ constexpr int kSmem = kRawStages * kRawBytes + kOpStages * kOpBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxBlock = 128;
 
-struct StageInfo {
-    int block;    // -1: no more work
-    int phase;    // 0: columns of M, 1: rows of N
-    int nk;       // block size
-    int d;        // leading columns to skip in a strided tile
-    int nb;       // boxes loaded
-    int first;    // first chunk of the phase
-    int last;     // last chunk of the phase
-    int strided;  // operand tile needs the transpose
+// How a stage's tile reaches the MMA.
+enum TileMode : int {
+    TILE_KMAJOR = 0,     // vectors are tile rows (contiguous storage): K-major operand in place
+    TILE_MNMAJOR = 1,    // vectors are tile columns (strided storage): MN-major operand in place
+    TILE_TRANSPOSE = 2,  // strided, but the aligned window exceeds 128 vectors: transposed copy
 };
 
-__device__ __forceinline__ uint32_t idesc_tf32(int npad) {
-    // D = F32 (bits 4-5), A = B = TF32 (2 at bits 7-9, 10-12), K-major, N>>3 at 17, M>>4 at 24
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+struct StageInfo {
+    int block;  // -1: no more work
+    int phase;  // 0: columns of M, 1: rows of N
+    int nk;     // block size
+    int d;      // tile row (K-major) or column (strided) of the block's first vector
+    int dpos;   // operand row of the block's first vector, the same in both phases of a block
+    int nb;     // boxes loaded
+    int first;  // first chunk of the phase
+    int last;   // last chunk of the phase
+    int mode;   // TileMode
+};
+
+__device__ __forceinline__ uint32_t idesc_tf32(int npad, bool mn_major) {
+    // D = F32 (bits 4-5), A = B = TF32 (2 at bits 7-9, 10-12), A and B MN-major (bits 15, 16) or
+    // K-major, N>>3 at 17, M>>4 at 24
+    const uint32_t major = mn_major ? (3u << 15) : 0u;
+    return (1u << 4) | (2u << 7) | (2u << 10) | major | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
+
+// Byte offset of element (row h, column cc) in a 32 x 32 FP32 box of a strided operand, loaded
+// with the 128-byte swizzle of 32-byte atoms: chunk cc / 8 of row h sits at chunk (cc / 8) ^ (h mod 4).
+__device__ __forceinline__ int strided_offset(int h, int cc) { return h * 128 + ((((cc >> 3) ^ (h & 3)) << 5) | ((cc & 7) << 2)); }
 
 // Barrier over the converter warps built on an mbarrier, so that its wait is bounded like every
 // other wait (a bar.sync could not give up if a warp left the loop after a timeout).
@@ -146,12 +165,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     f[k] = 0.0;
                     continue;
                 }
+                // A strided tile starts at the 16-byte boundary at or below lo, so the block's vectors
+                // sit at tile columns dlo .. dlo + nk - 1.  Used in place (MN-major) they are operand
+                // rows dlo.., and a contiguous tile of the same block starts dlo rows early so that
+                // both Grams index a vector alike.  A window wider than the MMA's 128 rows (nk > 125)
+                // sends the strided tiles through the transposed copy at operand row 0 instead.
+                const int dlo = (int)(lo & 3);
+                const bool any_strided = M_strided || N_strided;
+                const bool wide = any_strided && dlo + nk > 128;
+                const int dpos = (any_strided && !wide) ? dlo : 0;
                 for (int phase = 0; phase < 2 && !aborted; ++phase) {
                     const int strided = phase == 0 ? M_strided : N_strided;
                     const long long len = phase == 0 ? m : p;
                     const long long nchunks = (len + 31) / 32;
-                    const int d = strided ? (int)(lo & 3) : 0;
-                    const int nb = strided ? (int)((d + nk + 31) / 32) : (int)((nk + 31) / 32);
+                    const int mode = !strided ? TILE_KMAJOR : (wide ? TILE_TRANSPOSE : TILE_MNMAJOR);
+                    const int d = strided ? dlo : dpos;
+                    const int nb = (int)((d + nk + 31) / 32);
                     const CUtensorMap* map = phase == 0 ? &tmM : &tmN;
                     for (long long c = 0; c < nchunks; ++c) {
                         if (!mbar_wait(smem_u32(&bar_empty[stage]), ph ^ 1u, &s_abort)) { aborted = true; break; }
@@ -160,20 +189,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                         si.phase = phase;
                         si.nk = (int)nk;
                         si.d = d;
+                        si.dpos = dpos;
                         si.nb = nb;
                         si.first = c == 0;
                         si.last = c == nchunks - 1;
-                        si.strided = strided;
+                        si.mode = mode;
                         const uint32_t fb = smem_u32(&bar_full[stage]);
                         mbar_expect_tx(fb, (uint32_t)(nb * kBoxBytes));
-                        uint8_t* dst = raw(stage);  // both kinds of tile land in the TMA ring
+                        uint8_t* dst = raw(stage);  // every tile lands in the TMA ring
                         for (int b = 0; b < nb; ++b) {
                             if (strided)
                                 tma_load_2d(smem_u32(dst + b * kBoxBytes), map, fb, (int32_t)(lo - d + 32 * b),
                                             (int32_t)(32 * c));
                             else
                                 tma_load_2d(smem_u32(dst + b * kBoxBytes), map, fb, (int32_t)(32 * c),
-                                            (int32_t)(lo + 32 * b));
+                                            (int32_t)(lo - d + 32 * b));
                         }
                         issued_mask |= 1u << stage;
                         issued_phase = (issued_phase & ~(1u << stage)) | (ph << stage);
@@ -203,20 +233,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                 }
+                const bool transposed = si.mode == TILE_TRANSPOSE;
                 uint8_t* tile = raw(stage);
-                if (si.strided) {
+                if (transposed) {
                     mbar_arrive(smem_u32(&bar_empty[stage]));  // record read; the raw tile is not used here
                     if (!mbar_wait(smem_u32(&bar_opfull[ostage]), oph, &s_abort)) { aborted = true; break; }
                     tile = opt(ostage);
                 }
                 tc_fence_after();
-                const int npad = (si.nk + 15) & ~15;
+                // operand rows dpos .. dpos + nk - 1 hold the block (dpos + nk <= 128 by construction)
+                const int npad = (si.dpos + si.nk + 15) & ~15;
                 const uint32_t d = tmem + (uint32_t)(acc * 256 + si.phase * 128);
-                const uint64_t desc = sw128_desc(smem_u32(tile));
+                const bool mn = si.mode == TILE_MNMAJOR;
+                // K step of 8 TF32: 32 bytes along a K-major row, one 1024-byte row group when MN-major
+                const uint64_t desc = mn ? sw128_atom32_mn_desc(smem_u32(tile), kBoxBytes) : sw128_desc(smem_u32(tile));
+                const uint64_t kstep = mn ? 64ull : 2ull;
+                const uint32_t idesc = idesc_tf32(npad, mn);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    tc_mma_tf32(d, desc + 2ull * kk, desc + 2ull * kk, idesc_tf32(npad), (!si.first || kk > 0) ? 1u : 0u);
-                if (si.strided) {
+                    tc_mma_tf32(d, desc + kstep * kk, desc + kstep * kk, idesc, (!si.first || kk > 0) ? 1u : 0u);
+                if (transposed) {
                     tc_commit(smem_u32(&bar_opempty[ostage]));
                     if (++ostage == kOpStages) { ostage = 0; oph ^= 1u; }
                 } else {
@@ -253,7 +289,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             const StageInfo si = info[stage];
             if (si.block < 0) break;
             const bool mine = STATS && i < si.nk;
-            if (si.strided) {
+            if (si.mode == TILE_MNMAJOR) {
+                // vector i is tile column d + i: sum its squares, the MMA reads the tile in place
+                if (mine) {
+                    const int j = i + si.d;
+                    const uint8_t* src = raw(stage) + (j >> 5) * kBoxBytes;
+                    const int cc = j & 31;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int h = 16 * hh + q;
+                        const float v = *reinterpret_cast<const float*>(src + strided_offset(h, cc));
+                        ff.add_prod(v, v);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
+            } else if (si.mode == TILE_TRANSPOSE) {
                 const int j = i + si.d;  // tile column of vector i
                 const uint8_t* src = raw(stage) + (j >> 5) * kBoxBytes;
                 const int cc = j & 31;
@@ -262,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int h = 16 * hh + q;
-                        v[q] = *reinterpret_cast<const float*>(src + h * 128 + ((((cc >> 2) ^ (h & 7)) << 4) | ((cc & 3) << 2)));
+                        v[q] = *reinterpret_cast<const float*>(src + strided_offset(h, cc));
                     }
                 } else {
 #pragma unroll
@@ -288,10 +339,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (++ostage == kOpStages) { ostage = 0; oph ^= 1u; }
             } else {
                 if (mine) {
-                    const uint8_t* row = raw(stage) + i * 128;
+                    const int r = i + si.d;  // tile row of vector i
+                    const uint8_t* row = raw(stage) + r * 128;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 w4 = *reinterpret_cast<const float4*>(row + (((4 * hh + q) ^ (i & 7)) << 4));
+                        const float4 w4 = *reinterpret_cast<const float4*>(row + (((4 * hh + q) ^ (r & 7)) << 4));
                         ff.add_prod(w4.x, w4.x);
                         ff.add_prod(w4.y, w4.y);
                         ff.add_prod(w4.z, w4.z);
@@ -319,6 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
             // ---- block epilogue
             const long long k = si.block, nk = si.nk;
+            const int dpos = si.dpos;
             const long long lo = off[k];
             conv_sync(cs_bar, cs_uses, &s_abort);
             double sa = 0.0, ss = 0.0, sx = 0.0, sy = 0.0;
@@ -340,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (mbar_wait(smem_u32(&bar_tfull[acc]), (uint32_t)(it >> 1) & 1u, &s_abort)) {
                 tc_fence_after();
                 const int q4 = warp & 3, half = cw >> 2;
-                const int r = 32 * q4 + lane;
+                const int r = 32 * q4 + lane - dpos;  // vector of this TMEM lane
 #pragma unroll 1
                 for (int u = 0; u < 2; ++u) {
                     const int c0 = 64 * half + 32 * u;
@@ -349,11 +402,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     TMEM_LD_32X32B_X32(taddr, gm);
                     TMEM_LD_32X32B_X32(taddr + 128, gn);
                     tmem_ld_wait();
-                    if (r < nk) {
+                    if (r >= 0 && r < nk) {
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
-                            const int jj = c0 + e;
-                            if (jj < nk && jj != r) offf.add_prod(__uint_as_float(gm[e]), __uint_as_float(gn[e]));
+                            const int jj = c0 + e - dpos;
+                            if (jj >= 0 && jj < nk && jj != r)
+                                offf.add_prod(__uint_as_float(gm[e]), __uint_as_float(gn[e]));
                         }
                     }
                 }
@@ -394,7 +448,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && s_abort) set_status(st, BMM_ERR_TIMEOUT, 2);
 }
 
-bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, int64_t ld) {
+// Strided operands (vectors along the storage rows' inner dimension) feed the MMA MN-major, which
+// for TF32 wants 32-byte swizzle atoms; contiguous ones are K-major with the plain 128-byte swizzle.
+bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, int64_t ld, bool strided) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (fn == nullptr) {
         void* q = nullptr;
@@ -409,7 +465,8 @@ bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, 
     cuuint32_t box[2] = {32, 32};
     cuuint32_t es[2] = {1, 1};
     return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, strided ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -433,7 +490,8 @@ cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64
     const int64_t mcols = vM.mode == VEC_STRIDED ? vM.count : vM.len;
     const int64_t nrows = vN.mode == VEC_STRIDED ? vN.len : vN.count;
     const int64_t ncols = vN.mode == VEC_STRIDED ? vN.count : vN.len;
-    if (!make_map_f32(&mM, vM.data, mrows, mcols, vM.ld) || !make_map_f32(&mN, vN.data, nrows, ncols, vN.ld))
+    if (!make_map_f32(&mM, vM.data, mrows, mcols, vM.ld, vM.mode == VEC_STRIDED) ||
+        !make_map_f32(&mN, vN.data, nrows, ncols, vN.ld, vN.mode == VEC_STRIDED))
         return cudaErrorInvalidValue;
     static bool attr[2] = {false, false};
     if (!attr[stats]) {

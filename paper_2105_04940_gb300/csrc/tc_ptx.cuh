@@ -85,6 +85,21 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor: MN-major TF32 tile, 128-byte swizzle with 32-byte atoms
+// (swizzle mode 1; the layout a TMA load with CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B writes: the
+// 32-byte chunk u of 128-byte row r sits at chunk u ^ (r mod 4)).  Each row holds 32 consecutive
+// M/N elements of one K index; one MMA (K = 8) reads two groups of 4 rows, the second 512 bytes
+// after the first (stride byte offset); blocks of 32 M/N elements follow each other every
+// mn_stride_bytes (leading byte offset).  Descriptor version 1 (bit 46).
+__device__ __forceinline__ uint64_t sw128_atom32_mn_desc(uint32_t saddr, uint32_t mn_stride_bytes) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((mn_stride_bytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)1 << 61;
+    return d;
+}
+
 #define TMEM_LD_32X32B_X32(taddr, r)                                                                                  \
     asm volatile(                                                                                                     \
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"  \

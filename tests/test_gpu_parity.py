@@ -146,28 +146,45 @@ def test_fused_statistics_and_tensor_core_f(bmm, layouts, p):
     assert np.all(err <= bound + 1e-12 * f)
 
 
-def test_fused_statistics_low_rank_blocks(bmm):
-    """Rank-one aligned blocks (off-diagonal trace as large as the diagonal) and one full 128 block."""
+@pytest.mark.parametrize("layouts", [("row", "row"), ("col", "col"), ("row", "col"), ("col", "row")])
+def test_fused_statistics_offsets_wide_and_low_rank_blocks(bmm, layouts):
+    """Blocks at every offset mod 4 (strided tiles start at the 16-byte boundary below the block),
+    the widest blocks (127 at offset 3 and 128 at offset 1 exceed the 128 operand rows of an
+    in-place strided tile; 126 at offset 2 fills them exactly), tiny blocks, and one rank-one
+    block (off-diagonal trace as large as the diagonal)."""
     rng = np.random.default_rng(3)
-    sizes = np.array([128, 5, 77, 16, 100, 34])  # n = 360: every leading dimension % 4 == 0
+    sizes = np.array([3, 127, 126, 128, 1, 128, 5, 77, 16, 100, 34, 3])  # n = 748: every ld % 4 == 0
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     n, m, p = int(off[-1]), 96, 152
     M = rng.standard_normal((m, n)).astype(np.float32)
     N = rng.standard_normal((n, p)).astype(np.float32)
     u, v = rng.standard_normal(m), rng.standard_normal(p)
-    w = rng.standard_normal(sizes[2])
-    M[:, off[2]:off[3]] = np.outer(u, w)
-    N[off[2]:off[3], :] = np.outer(w, v)
+    w = rng.standard_normal(sizes[7])
+    M[:, off[7]:off[8]] = np.outer(u, w)
+    N[off[7]:off[8], :] = np.outer(w, v)
     M, N = M.astype(np.float64), N.astype(np.float64)
-    Mt, Nt = to_dev(M.astype(np.float32)), to_dev(N.astype(np.float32))
+    Mt = as_layout(to_dev(M.astype(np.float32)), layouts[0])
+    Nt = as_layout(to_dev(N.astype(np.float32)), layouts[1])
     prob = bmm.prepare(Mt, Nt, off, max_draws=50)
     launches = bmm._abi.bmm_launch_count()
     bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, None, prob.st, prob.ws)
     bmm.check_status(prob)
     assert bmm._abi.bmm_launch_count() - launches == 1  # the fused pass alone (no p requested)
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    assert rel_err(host(prob.st["x"]), x) < 1e-12
+    assert rel_err(host(prob.st["y"]), y) < 1e-12
+    for k in ("a", "s", "mf", "nf"):
+        assert rel_err(host(prob.st[k]), st[k]) < 1e-12, k
     f = oracle.block_frob_sq(M, N, off)
     err = np.abs(host(prob.st["f"]) - f)
     assert np.all(err <= _tf32_gram_bound(M, N, off, m, p) + 1e-12 * f)
+    # the Gram-only form (statistics reused) gives the same f
+    f_fused = host(prob.st["f"]).copy()
+    prob.st["f"].zero_()
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_BLK_PRODNORM, bmm._abi.F_TC | bmm._abi.REUSE_STATS, None, prob.st, prob.ws)
+    bmm.check_status(prob)
+    assert np.array_equal(host(prob.st["f"]), f_fused)
 
 
 # ---------------------------------------------------------------- block sizes (identical inputs)
