@@ -6,26 +6,35 @@
 // off-diagonal part sum_{i != j} G_M[i,j] G_N[i,j] comes from TF32 tensor-core Grams in TMEM.
 //
 // One CTA per SM pulls blocks from a global counter.  For block k it streams the vectors of the
-// block -- columns of M (length m), then rows of N (length p) -- in chunks of 32 coordinates:
-//   warp 0      one lane: TMA loads of 32 x 32 FP32 boxes into an 8-deep ring (128-byte swizzle,
-//               in 32-byte atoms for strided storage);
-//   warp 1      one lane: tcgen05.mma kind::tf32 (M = 128, N = the block's operand rows rounded to
-//               16, K = 8) with the same operand tile as A and B, G_M and G_N in two TMEM
-//               accumulators, double buffered across blocks (512 columns).  A tile whose vectors
-//               are its rows (contiguous storage) is a K-major operand, one whose vectors are its
-//               columns (strided storage: row-major M, column-major N) an MN-major operand; both are
-//               read where TMA put them;
-//   warps 2-9   sum squares of every element they see (exact norms) and, at the end of a block,
-//               fold the norms into a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 and reduce the off-diagonal
-//               Gram products from TMEM.
-// A strided operand's first box starts at the 16-byte boundary at or below the block's first
-// column (TMA needs a 16-byte-aligned inner coordinate), so its vectors are operand rows
+// block -- columns of M (length m), then rows of N (length p) -- in sub-tiles of 32 coordinates,
+// several sub-tiles (up to 40 KB) per pipeline stage:
+//   warp 0      one lane: TMA loads into a 5-stage ring of 40 KB and a record per stage and per
+//               block.  A strided operand stage is nb boxes of 32 columns x 64 rows (two
+//               sub-tiles, 128-byte swizzle in 32-byte atoms); a contiguous operand stage is one
+//               box of 32 coordinates x 32 nb vectors per sub-tile (128-byte swizzle).  Few large
+//               copies keep the TMA unit, which takes about as long for a small box as for a large
+//               one, from limiting the pass;
+//   warp 1      one lane: tcgen05.mma kind::tf32 (M = 128, K = 8) with the same operand tile as A
+//               and B.  A tile whose vectors are its rows (contiguous storage) is a K-major operand,
+//               one whose vectors are its columns (strided storage: row-major M, column-major N)
+//               an MN-major operand; both are read where TMA put them.  G_M and G_N of a block take
+//               two of three 160-column TMEM slots used in turn, so the Grams of the next block
+//               build up while the epilogue of the previous one reads its slots;
+//   warps 2-17  (statistics pass) sum the squares of each stage's elements, every warp a
+//               sixteenth of each sub-tile for all vectors, float-float sums per lane and vector; at
+//               the end of a block they fold the norms into a_k, s_k, ||M^k||_F^2, ||N_k||_F^2, and
+//               (both passes) reduce the off-diagonal Gram products from TMEM.
+// Positions.  A strided operand's first box starts at the 16-byte boundary at or below the block's
+// first column (TMA needs a 16-byte-aligned inner coordinate), so its vectors are operand rows
 // d .. d + n_k - 1 with d = off_k mod 4; the contiguous operand of the same block is loaded d rows
-// early to match.  When d + n_k exceeds the MMA's 128 rows (n_k > 125) the strided tiles are
-// transposed by warps 2-9 into a 2-deep ring of K-major tiles instead, with the block at row 0.
-// Operand rows outside the block hold neighbouring data or zeros and are masked out of every
-// sum.  All waits are bounded; on expiry the CTA records BMM_ERR_TIMEOUT, lets its copies and
-// MMAs in flight land, frees TMEM and returns.
+// early to match.  The MMA takes operand rows 0..127 as its M side and rows 0..npad-1 (npad <= 144)
+// as its N side.  When d + n_k exceeds 128 (a "wide" block, n_k > 125) the missing Gram rows are
+// the transposes of columns >= 128 of the rows below 128, which the epilogue counts twice, except
+// for the products among the <= 3 vectors at rows >= 128: a second MMA (A = rows 32..159, B = rows
+// 128..143, N = 16) computes those into the last 16 columns of the slot.
+// Operand rows outside the block hold neighbouring data or zeros and are masked out of every sum.
+// All waits are bounded; on expiry the CTA records BMM_ERR_TIMEOUT, lets its copies and MMAs in
+// flight land, frees TMEM and returns.
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -34,37 +43,63 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kRawStages = 8;                    // TMA ring: covers DRAM latency
-constexpr int kOpStages = 2;                     // transposed operand tiles for the MMA
-constexpr int kBoxBytes = 32 * 32 * 4;           // one 32 x 32 FP32 box
-constexpr int kRawBoxes = 5;                     // strided operand: 3 leading columns + 128
-constexpr int kRawBytes = kRawBoxes * kBoxBytes;  // 20 KB
-constexpr int kOpBytes = 4 * kBoxBytes;           // 128 vectors x 32 coordinates
-constexpr int kFoldEvery = 8;                    // chunks between FP64 folds of the float-float sums
-constexpr int kConvWarps = 8;
+constexpr int kBoxBytes = 32 * 32 * 4;        // 32 x 32 FP32: one sub-tile of one 32-wide group
+constexpr int kMnRows = 64;                   // rows per strided box: two sub-tiles
+constexpr int kMnBoxBytes = 32 * kMnRows * 4; // 8 KB
+constexpr int kStageBytes = 10 * kBoxBytes;   // 40 KB per pipeline stage
+constexpr int kStages = 5;
+constexpr int kBlockSlots = 4;                // block records in flight
+constexpr int kConvWarps = 16;
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kThreads = 64 + kConvThreads;
-constexpr int kSmem = kRawStages * kRawBytes + kOpStages * kOpBytes + 1024;
+constexpr int kSmem = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
+constexpr int kSlotCols = 160;                // TMEM columns per Gram slot (3 slots)
+constexpr int kCornerCol = 144;               // wide blocks: rows >= 128 x rows >= 128, N = 16
 constexpr int kMaxBlock = 128;
+constexpr int kFoldStages = 4;                // stages between folds into the second-level sums
 
-// How a stage's tile reaches the MMA.
-enum TileMode : int {
-    TILE_KMAJOR = 0,     // vectors are tile rows (contiguous storage): K-major operand in place
-    TILE_MNMAJOR = 1,    // vectors are tile columns (strided storage): MN-major operand in place
-    TILE_TRANSPOSE = 2,  // strided, but the aligned window exceeds 128 vectors: transposed copy
+// Sub-tiles of 32 coordinates per stage of a contiguous operand spanning nb groups of 32 vectors.
+// The MMA reads 128 operand rows (16 KB) from the start of every sub-tile, and a wide block's
+// corner MMA reads up to 20 KB; rows past the block belong to the next sub-tile (masked), but must
+// stay inside the stage: (per - 1) * nb * 4 KB + 16 KB <= 40 KB, and for nb = 5,
+// (per - 1) * 20 KB + 20 KB <= 40 KB.  A strided operand stage always holds kMnRows / 32 = 2
+// sub-tiles: its MN-major operand reads four 8 KB boxes (five for a wide block's corner), at most
+// 4 KB + 4 * 8 KB = 36 KB (40 KB) into the stage.
+__host__ __device__ __forceinline__ int subtiles_per_stage(int nb) { return nb >= 5 ? 2 : 1 + 6 / nb; }
+constexpr int kMaxGroups = 5;                 // 32-wide groups a block spans (d + n_k <= 131)
+
+enum StageFlags : int {
+    ST_PHASE = 1,   // 0: columns of M, 1: rows of N
+    ST_FIRST = 2,   // first stage of the phase
+    ST_LAST = 4,    // last stage of the phase
+    ST_MN = 8,      // vectors are tile columns: MN-major operand
+    ST_WIDE = 16,   // d + n_k > 128: corner MMA
 };
 
-struct StageInfo {
+struct __align__(16) StageInfo {
     int block;  // -1: no more work
-    int phase;  // 0: columns of M, 1: rows of N
+    int flags;  // StageFlags
     int nk;     // block size
-    int d;      // tile row (K-major) or column (strided) of the block's first vector
-    int dpos;   // operand row of the block's first vector, the same in both phases of a block
-    int nb;     // boxes loaded
-    int first;  // first chunk of the phase
-    int last;   // last chunk of the phase
-    int mode;   // TileMode
+    int d;      // tile row (K-major) or column (MN-major) of the block's first vector
+    int dpos;   // operand row of the block's first vector, the same in both phases
+    int nb;     // boxes per sub-tile
+    int nsub;   // sub-tiles in this stage
+    int sub_bytes;  // distance between sub-tiles in the stage
+};
+
+struct __align__(16) BlockInfo {
+    long long lo;  // first column
+    int k;         // block index, -1: no more work
+    int nk;
+    int dpos;
+    int pad[3];
+};
+
+// Tensor maps of one operand: strided storage uses map[0] (32 x kMnRows boxes); contiguous storage
+// uses map[nb - 1] (32 coordinates x 32 nb vectors).
+struct OperandMaps {
+    CUtensorMap map[kMaxGroups];
 };
 
 __device__ __forceinline__ uint32_t idesc_tf32(int npad, bool mn_major) {
@@ -78,64 +113,97 @@ __device__ __forceinline__ uint32_t idesc_tf32(int npad, bool mn_major) {
 // with the 128-byte swizzle of 32-byte atoms: chunk cc / 8 of row h sits at chunk (cc / 8) ^ (h mod 4).
 __device__ __forceinline__ int strided_offset(int h, int cc) { return h * 128 + ((((cc >> 3) ^ (h & 3)) << 5) | ((cc & 7) << 2)); }
 
+// Four K steps (32 coordinates) of one sub-tile, A = B = the operand at descriptor (lo, hi): the
+// start address is in the low word, so a K step is a 32-bit add (32 bytes K-major, 1024 bytes
+// MN-major).  The first MMA overwrites the accumulator when `fresh`.
+template <bool MN>
+__device__ __forceinline__ void mma_sub(uint32_t d, uint32_t lo_a, uint32_t lo_b, uint32_t hi, uint32_t idesc, bool fresh) {
+    constexpr uint32_t ks = MN ? 64u : 2u;
+    const uint64_t h = (uint64_t)hi << 32;
+    tc_mma_tf32(d, h | lo_a, h | lo_b, idesc, fresh ? 0u : 1u);
+    tc_mma_tf32(d, h | (lo_a + ks), h | (lo_b + ks), idesc, 1u);
+    tc_mma_tf32(d, h | (lo_a + 2 * ks), h | (lo_b + 2 * ks), idesc, 1u);
+    tc_mma_tf32(d, h | (lo_a + 3 * ks), h | (lo_b + 3 * ks), idesc, 1u);
+}
+
+template <bool MN>
+__device__ __forceinline__ void mma_stage(uint32_t d_main, uint32_t d_corner, uint32_t addr, uint32_t sub_bytes, int nsub,
+                                          uint32_t idesc, uint32_t idesc16, bool first, bool wide) {
+    // MN-major: 32-row blocks of operand rows are the 8 KB boxes (leading byte offset); K-major:
+    // 32 operand rows are 4 KB
+    constexpr uint32_t group = MN ? (uint32_t)kMnBoxBytes >> 4 : (uint32_t)kBoxBytes >> 4;
+    const uint64_t d0 = MN ? sw128_atom32_mn_desc(addr, kMnBoxBytes) : sw128_desc(addr);
+    const uint32_t hi = (uint32_t)(d0 >> 32);
+    uint32_t lo = (uint32_t)d0;
+    const uint32_t step = sub_bytes >> 4;
+    for (int s = 0; s < nsub; ++s, lo += step) {
+        const bool fresh = first && s == 0;
+        mma_sub<MN>(d_main, lo, lo, hi, idesc, fresh);
+        // operand rows 32..159 (A) against rows 128..143 (B)
+        if (wide) mma_sub<MN>(d_corner, lo + group, lo + 4 * group, hi, idesc16, fresh);
+    }
+}
+
+__device__ __forceinline__ bool wait_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort_flag);
+}
+
 // Barrier over the converter warps built on an mbarrier, so that its wait is bounded like every
 // other wait (a bar.sync could not give up if a warp left the loop after a timeout).
 __device__ __forceinline__ bool conv_sync(uint32_t bar, int& uses, volatile int* abort_flag) {
     __threadfence_block();
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
-    const bool ok = mbar_wait(bar, (uint32_t)(uses & 1), abort_flag);
+    const bool ok = wait_fast(bar, (uint32_t)(uses & 1), abort_flag);
     ++uses;
     return ok;
 }
 
 template <bool STATS>
 __global__ void __launch_bounds__(kThreads, 1)
-    blockstats_tc_kernel(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CUtensorMap tmN,
+    blockstats_tc_kernel(const __grid_constant__ OperandMaps tmM, const __grid_constant__ OperandMaps tmN,
                          int M_strided, int N_strided, long long m, long long p, const int64_t* __restrict__ off,
                          long long K, long long n, int* __restrict__ counter, double* __restrict__ x,
                          double* __restrict__ y, double* __restrict__ a, double* __restrict__ ssum,
                          double* __restrict__ mf, double* __restrict__ nf, double* __restrict__ f, DevStatus* st) {
     extern __shared__ uint8_t dsmem[];
-    __shared__ __align__(8) uint64_t bar_full[kRawStages], bar_empty[kRawStages];
-    __shared__ __align__(8) uint64_t bar_opfull[kOpStages], bar_opempty[kOpStages];
-    __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_drain, bar_cs;
-    __shared__ StageInfo info[kRawStages];
+    __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
+    __shared__ __align__(8) uint64_t bar_bfull[kBlockSlots], bar_bempty[kBlockSlots];
+    __shared__ __align__(8) uint64_t bar_slot_free[3], bar_tfull[2], bar_drain, bar_cs;
+    __shared__ StageInfo info[kStages];
+    __shared__ BlockInfo binfo[kBlockSlots];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
-    __shared__ double part[2][2][kMaxBlock];  // [phase][coordinate half][vector]
+    __shared__ double part[STATS ? kConvWarps : 1][kMaxBlock];  // [warp][vector], one phase at a time
+    __shared__ double xy_sum[STATS ? 2 : 1][kMaxBlock];           // [phase][vector]: x_i, y_i
     __shared__ double red[kConvWarps][5];
 
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
-    auto raw = [&](int s) { return base + s * kRawBytes; };
-    auto opt = [&](int s) { return base + kRawStages * kRawBytes + s * kOpBytes; };
+    auto stage_ptr = [&](int s) { return base + s * kStageBytes; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kRawStages; ++s) {
+        for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
-            // released by the 8 converter warps plus the MMA thread: its commit when the tile is used
-            // in place, a plain arrival once it has read the stage's record when the tile was
-            // transposed.  The MMA thread's arrival is what keeps the producer from overwriting a
-            // record (or advancing bar_full by a whole phase) before the MMA has read it.
-            mbar_init(smem_u32(&bar_empty[s]), kConvWarps + 1);
+            // released by the MMA's commit once its reads are done, and in the statistics pass by
+            // the 16 converter warps once they have read the stage
+            mbar_init(smem_u32(&bar_empty[s]), STATS ? kConvWarps + 1 : 1);
         }
-        for (int s = 0; s < kOpStages; ++s) {
-            mbar_init(smem_u32(&bar_opfull[s]), kConvWarps);
-            mbar_init(smem_u32(&bar_opempty[s]), 1);
+        for (int b = 0; b < kBlockSlots; ++b) {
+            mbar_init(smem_u32(&bar_bfull[b]), 1);
+            mbar_init(smem_u32(&bar_bempty[b]), kConvWarps);
         }
-        for (int q = 0; q < 2; ++q) {
-            mbar_init(smem_u32(&bar_tfull[q]), 1);
-            mbar_init(smem_u32(&bar_tempty[q]), kConvWarps);
-        }
+        for (int q = 0; q < 3; ++q) mbar_init(smem_u32(&bar_slot_free[q]), kConvWarps);
+        for (int q = 0; q < 2; ++q) mbar_init(smem_u32(&bar_tfull[q]), 1);
         mbar_init(smem_u32(&bar_drain), 1);
         mbar_init(smem_u32(&bar_cs), kConvWarps);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // operand tiles start as zeros, so rows no copy ever wrote are finite
-    for (int e = threadIdx.x; e < (kRawStages * kRawBytes + kOpStages * kOpBytes) / 16; e += kThreads)
+    for (int e = threadIdx.x; e < kStages * kStageBytes / 16; e += kThreads)
         reinterpret_cast<uint4*>(base)[e] = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
     if (warp == 1) tmem_alloc(smem_u32(&s_tmem), kTmemCols);
     tc_fence_before();
     __syncthreads();
@@ -145,14 +213,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------ producer
-            int stage = 0;
-            uint32_t ph = 0;
+            int stage = 0, bslot = 0;
+            uint32_t ph = 0, bph = 0;
             uint32_t issued_mask = 0, issued_phase = 0;
             bool aborted = false;
             while (!aborted) {
                 const long long k = atomicAdd(counter, 1);
                 if (k >= K) {
-                    if (!mbar_wait(smem_u32(&bar_empty[stage]), ph ^ 1u, &s_abort)) { aborted = true; break; }
+                    if (!wait_fast(smem_u32(&bar_bempty[bslot]), bph ^ 1u, &s_abort)) { aborted = true; break; }
+                    binfo[bslot].k = -1;
+                    mbar_arrive(smem_u32(&bar_bfull[bslot]));
+                    if (!wait_fast(smem_u32(&bar_empty[stage]), ph ^ 1u, &s_abort)) { aborted = true; break; }
                     info[stage].block = -1;
                     mbar_arrive(smem_u32(&bar_full[stage]));
                     break;
@@ -165,104 +236,106 @@ __global__ void __launch_bounds__(kThreads, 1)
                     f[k] = 0.0;
                     continue;
                 }
-                // A strided tile starts at the 16-byte boundary at or below lo, so the block's vectors
-                // sit at tile columns dlo .. dlo + nk - 1.  Used in place (MN-major) they are operand
-                // rows dlo.., and a contiguous tile of the same block starts dlo rows early so that
-                // both Grams index a vector alike.  A window wider than the MMA's 128 rows (nk > 125)
-                // sends the strided tiles through the transposed copy at operand row 0 instead.
                 const int dlo = (int)(lo & 3);
-                const bool any_strided = M_strided || N_strided;
-                const bool wide = any_strided && dlo + nk > 128;
-                const int dpos = (any_strided && !wide) ? dlo : 0;
+                const int dpos = (M_strided || N_strided) ? dlo : 0;
+                const bool wide = dpos + nk > 128;
+                if (!wait_fast(smem_u32(&bar_bempty[bslot]), bph ^ 1u, &s_abort)) { aborted = true; break; }
+                binfo[bslot].lo = lo;
+                binfo[bslot].k = (int)k;
+                binfo[bslot].nk = (int)nk;
+                binfo[bslot].dpos = dpos;
+                mbar_arrive(smem_u32(&bar_bfull[bslot]));
+                if (++bslot == kBlockSlots) { bslot = 0; bph ^= 1u; }
                 for (int phase = 0; phase < 2 && !aborted; ++phase) {
                     const int strided = phase == 0 ? M_strided : N_strided;
                     const long long len = phase == 0 ? m : p;
-                    const long long nchunks = (len + 31) / 32;
-                    const int mode = !strided ? TILE_KMAJOR : (wide ? TILE_TRANSPOSE : TILE_MNMAJOR);
                     const int d = strided ? dlo : dpos;
                     const int nb = (int)((d + nk + 31) / 32);
-                    const CUtensorMap* map = phase == 0 ? &tmM : &tmN;
-                    for (long long c = 0; c < nchunks; ++c) {
-                        if (!mbar_wait(smem_u32(&bar_empty[stage]), ph ^ 1u, &s_abort)) { aborted = true; break; }
+                    const int per = strided ? kMnRows / 32 : subtiles_per_stage(nb);
+                    const long long nsub_total = (len + 31) / 32;
+                    const OperandMaps& maps = phase == 0 ? tmM : tmN;
+                    const CUtensorMap* map = &maps.map[strided ? 0 : nb - 1];
+                    for (long long c0 = 0; c0 < nsub_total; c0 += per) {
+                        const int nsub = (int)imin(per, nsub_total - c0);
+                        if (!wait_fast(smem_u32(&bar_empty[stage]), ph ^ 1u, &s_abort)) { aborted = true; break; }
                         StageInfo& si = info[stage];
                         si.block = (int)k;
-                        si.phase = phase;
+                        si.flags = phase | (c0 == 0 ? ST_FIRST : 0) | (c0 + per >= nsub_total ? ST_LAST : 0) |
+                                   (strided ? ST_MN : 0) | (wide ? ST_WIDE : 0);
                         si.nk = (int)nk;
                         si.d = d;
                         si.dpos = dpos;
                         si.nb = nb;
-                        si.first = c == 0;
-                        si.last = c == nchunks - 1;
-                        si.mode = mode;
+                        si.nsub = nsub;
+                        si.sub_bytes = strided ? kBoxBytes : nb * kBoxBytes;
                         const uint32_t fb = smem_u32(&bar_full[stage]);
-                        mbar_expect_tx(fb, (uint32_t)(nb * kBoxBytes));
-                        uint8_t* dst = raw(stage);  // every tile lands in the TMA ring
-                        for (int b = 0; b < nb; ++b) {
-                            if (strided)
-                                tma_load_2d(smem_u32(dst + b * kBoxBytes), map, fb, (int32_t)(lo - d + 32 * b),
-                                            (int32_t)(32 * c));
-                            else
-                                tma_load_2d(smem_u32(dst + b * kBoxBytes), map, fb, (int32_t)(32 * c),
-                                            (int32_t)(lo - d + 32 * b));
+                        uint8_t* dst = stage_ptr(stage);
+                        if (strided) {
+                            // nb boxes of 32 columns x kMnRows rows (rows past the operand read as zeros)
+                            mbar_expect_tx(fb, (uint32_t)(nb * kMnBoxBytes));
+                            for (int b = 0; b < nb; ++b)
+                                tma_load_2d(smem_u32(dst + b * kMnBoxBytes), map, fb, (int32_t)(lo - d + 32 * b),
+                                            (int32_t)(32 * c0));
+                        } else {
+                            // one box of 32 coordinates x 32 nb vectors per sub-tile
+                            mbar_expect_tx(fb, (uint32_t)(nsub * nb * kBoxBytes));
+                            for (int s = 0; s < nsub; ++s)
+                                tma_load_2d(smem_u32(dst + s * nb * kBoxBytes), map, fb, (int32_t)(32 * (c0 + s)),
+                                            (int32_t)(lo - d));
                         }
                         issued_mask |= 1u << stage;
                         issued_phase = (issued_phase & ~(1u << stage)) | (ph << stage);
-                        if (++stage == kRawStages) { stage = 0; ph ^= 1u; }
+                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
                     }
                 }
             }
             if (aborted)
-                for (int s = 0; s < kRawStages; ++s)
+                for (int s = 0; s < kStages; ++s)
                     if (issued_mask & (1u << s)) mbar_wait(smem_u32(&bar_full[s]), (issued_phase >> s) & 1u, nullptr);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------ MMA issuer
-            int stage = 0, ostage = 0;
-            uint32_t ph = 0, oph = 0;
-            int it = 0, acc = 0;
+            int stage = 0;
+            uint32_t ph = 0;
+            int it = 0;
+            uint32_t slot_col = 0;
             bool aborted = false;
             while (true) {
-                if (!mbar_wait(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
+                if (!wait_fast(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
                 const StageInfo si = info[stage];
                 if (si.block < 0) break;
-                if (si.first && si.phase == 0) {
-                    acc = it & 1;
-                    if (!mbar_wait(smem_u32(&bar_tempty[acc]), ((uint32_t)(it >> 1) & 1u) ^ 1u, &s_abort)) {
+                const int phase = si.flags & ST_PHASE;
+                const bool first = si.flags & ST_FIRST;
+                if (first) {
+                    // slot of this Gram: the (2 it + phase)-th use of the 3-slot ring
+                    const int u = 2 * it + phase;
+                    const int q = u % 3;
+                    if (!wait_fast(smem_u32(&bar_slot_free[q]), ((uint32_t)(u / 3) & 1u) ^ 1u, &s_abort)) {
                         aborted = true;
                         break;
                     }
-                }
-                const bool transposed = si.mode == TILE_TRANSPOSE;
-                uint8_t* tile = raw(stage);
-                if (transposed) {
-                    mbar_arrive(smem_u32(&bar_empty[stage]));  // record read; the raw tile is not used here
-                    if (!mbar_wait(smem_u32(&bar_opfull[ostage]), oph, &s_abort)) { aborted = true; break; }
-                    tile = opt(ostage);
+                    slot_col = (uint32_t)(q * kSlotCols);
                 }
                 tc_fence_after();
-                // operand rows dpos .. dpos + nk - 1 hold the block (dpos + nk <= 128 by construction)
-                const int npad = (si.dpos + si.nk + 15) & ~15;
-                const uint32_t d = tmem + (uint32_t)(acc * 256 + si.phase * 128);
-                const bool mn = si.mode == TILE_MNMAJOR;
-                // K step of 8 TF32: 32 bytes along a K-major row, one 1024-byte row group when MN-major
-                const uint64_t desc = mn ? sw128_atom32_mn_desc(smem_u32(tile), kBoxBytes) : sw128_desc(smem_u32(tile));
-                const uint64_t kstep = mn ? 64ull : 2ull;
-                const uint32_t idesc = idesc_tf32(npad, mn);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    tc_mma_tf32(d, desc + kstep * kk, desc + kstep * kk, idesc, (!si.first || kk > 0) ? 1u : 0u);
-                if (transposed) {
-                    tc_commit(smem_u32(&bar_opempty[ostage]));
-                    if (++ostage == kOpStages) { ostage = 0; oph ^= 1u; }
-                } else {
-                    tc_commit(smem_u32(&bar_empty[stage]));
-                }
-                if (si.last && si.phase == 1) {
-                    tc_commit(smem_u32(&bar_tfull[acc]));
+                const bool mn = si.flags & ST_MN;
+                const bool wide = si.flags & ST_WIDE;
+                const int npad = (si.dpos + si.nk + 15) & ~15;  // <= 144
+                const uint32_t d_main = tmem + slot_col, d_corner = tmem + slot_col + kCornerCol;
+                const uint32_t addr = smem_u32(stage_ptr(stage));
+                const uint32_t sub_bytes = (uint32_t)si.sub_bytes;
+                if (mn)
+                    mma_stage<true>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_tf32(npad, true), idesc_tf32(16, true),
+                                    first, wide);
+                else
+                    mma_stage<false>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_tf32(npad, false),
+                                     idesc_tf32(16, false), first, wide);
+                tc_commit(smem_u32(&bar_empty[stage]));
+                if ((si.flags & ST_LAST) && phase == 1) {
+                    tc_commit(smem_u32(&bar_tfull[it & 1]));
                     ++it;
                 }
-                if (++stage == kRawStages) { stage = 0; ph ^= 1u; }
+                if (++stage == kStages) { stage = 0; ph ^= 1u; }
             }
             if (aborted) {
                 tc_commit(smem_u32(&bar_drain));
@@ -270,150 +343,181 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // ------------------------------------------------ norms, transpose, block epilogue
+        // ------------------------------------------------ norms, block epilogue
         const int t = threadIdx.x - 64;
-        const int i = t & 127, hh = t >> 7;
         const int cw = warp - 2;  // converter warp 0..7
-        int stage = 0, ostage = 0;
-        uint32_t ph = 0, oph = 0;
+        int stage = 0, bslot = 0;
+        uint32_t ph = 0, bph = 0;
         int it = 0;
-        FF ff;
-        ff.zero();
-        double dacc = 0.0;
-        int since_fold = 0;
         int cs_uses = 0;
         const uint32_t cs_bar = smem_u32(&bar_cs);
         bool aborted = false;
-        while (true) {
-            if (!mbar_wait(smem_u32(&bar_full[stage]), ph, &s_abort)) break;
-            const StageInfo si = info[stage];
-            if (si.block < 0) break;
-            const bool mine = STATS && i < si.nk;
-            if (si.mode == TILE_MNMAJOR) {
-                // vector i is tile column d + i: sum its squares, the MMA reads the tile in place
-                if (mine) {
-                    const int j = i + si.d;
-                    const uint8_t* src = raw(stage) + (j >> 5) * kBoxBytes;
-                    const int cc = j & 31;
+        while (!aborted) {
+            if (!wait_fast(smem_u32(&bar_bfull[bslot]), bph, &s_abort)) break;
+            const BlockInfo bi = binfo[bslot];
+            if (bi.k < 0) break;
+            const int nk = bi.nk, dpos = bi.dpos;
+
+            if (STATS) {
+                // ---- squares of every element, per vector: lane handles vectors lane + 32 v
+                for (int phase = 0; phase < 2 && !aborted; ++phase) {
+                    // two levels of float-float sums: acc over at most kFoldStages stages, folded
+                    // into tot (FP32 operations only: the FP64 pipe is slow on this part); FP64 once
+                    // per phase
+                    FF acc[4], tot[4];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int h = 16 * hh + q;
-                        const float v = *reinterpret_cast<const float*>(src + strided_offset(h, cc));
-                        ff.add_prod(v, v);
+                    for (int v = 0; v < 4; ++v) { acc[v].zero(); tot[v].zero(); }
+                    int since_fold = 0;
+                    bool mn_phase = false;
+                    while (true) {
+                        if (!wait_fast(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
+                        const StageInfo si = info[stage];
+                        mn_phase = si.flags & ST_MN;
+                        const uint8_t* tile = stage_ptr(stage);
+                        const int sub_bytes = si.sub_bytes;
+                        if (si.flags & ST_MN) {
+                            // rows h = cw and cw + 16 of every sub-tile; vector i is tile column d + i
+                            for (int s = 0; s < si.nsub; ++s) {
+                                const uint8_t* sub = tile + s * sub_bytes;
+#pragma unroll
+                                for (int r = 0; r < 2; ++r) {
+                                    const int h = cw + 16 * r;
+#pragma unroll
+                                    for (int v = 0; v < 4; ++v) {
+                                        const int i = lane + 32 * v;
+                                        if (i < si.nk) {
+                                            const int j = i + si.d;
+                                            const float e = *reinterpret_cast<const float*>(
+                                                sub + (j >> 5) * kMnBoxBytes + strided_offset(h, j & 31));
+                                            acc[v].add_prod(e, e);
+                                        }
+                                    }
+                                }
+                            }
+                        } else {
+                            // 16-byte chunk cw / 2 of every sub-tile row, vectors i = lane + 32 v for
+                            // v = cw mod 2 and cw mod 2 + 2; vector i is tile row d + i
+                            const int q = cw >> 1;
+                            for (int s = 0; s < si.nsub; ++s) {
+                                const uint8_t* sub = tile + s * sub_bytes;
+#pragma unroll
+                                for (int vv = 0; vv < 2; ++vv) {
+                                    // acc[vv] holds vector group (cw mod 2) + 2 vv in this layout
+                                    const int i = lane + 32 * ((cw & 1) + 2 * vv);
+                                    if (i < si.nk) {
+                                        const int r = i + si.d;
+                                        const float4 w4 =
+                                            *reinterpret_cast<const float4*>(sub + r * 128 + ((q ^ (r & 7)) << 4));
+                                        acc[vv].add_prod(w4.x, w4.x);
+                                        acc[vv].add_prod(w4.y, w4.y);
+                                        acc[vv].add_prod(w4.z, w4.z);
+                                        acc[vv].add_prod(w4.w, w4.w);
+                                    }
+                                }
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
+                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[v].renorm();
+                        const bool last = si.flags & ST_LAST;
+                        if (++since_fold == kFoldStages || last) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                tot[v].add(acc[v]);
+                                tot[v].renorm();
+                                acc[v].zero();
+                            }
+                            since_fold = 0;
+                        }
+                        if (last) break;
                     }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
-            } else if (si.mode == TILE_TRANSPOSE) {
-                const int j = i + si.d;  // tile column of vector i
-                const uint8_t* src = raw(stage) + (j >> 5) * kBoxBytes;
-                const int cc = j & 31;
-                float v[16];
-                if (j < 32 * si.nb) {
+                    if (mn_phase) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int h = 16 * hh + q;
-                        v[q] = *reinterpret_cast<const float*>(src + strided_offset(h, cc));
+                        for (int v = 0; v < 4; ++v) part[STATS ? cw : 0][lane + 32 * v] = tot[v].value();
+                    } else {
+                        part[STATS ? cw : 0][lane + 32 * (cw & 1)] = tot[0].value();
+                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) + 2)] = tot[1].value();
+                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) ^ 1)] = 0.0;
+                        part[STATS ? cw : 0][lane + 32 * (((cw & 1) ^ 1) + 2)] = 0.0;
                     }
-                } else {
+                    // x_i (phase 0) or y_i (phase 1): the sum over the warps' shares
+                    conv_sync(cs_bar, cs_uses, &s_abort);
+                    if (t < kMaxBlock) {
+                        double sum = 0.0;
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = 0.f;
-                }
-                // the raw tile is read: hand it back to the producer
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
-                if (mine) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) ff.add_prod(v[q], v[q]);
-                }
-                if (!mbar_wait(smem_u32(&bar_opempty[ostage]), oph ^ 1u, &s_abort)) { aborted = true; break; }
-                uint8_t* dst = opt(ostage) + i * 128;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int chunk = (4 * hh + q) ^ (i & 7);
-                    *reinterpret_cast<float4*>(dst + chunk * 16) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                }
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bar_opfull[ostage]));
-                if (++ostage == kOpStages) { ostage = 0; oph ^= 1u; }
-            } else {
-                if (mine) {
-                    const int r = i + si.d;  // tile row of vector i
-                    const uint8_t* row = raw(stage) + r * 128;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 w4 = *reinterpret_cast<const float4*>(row + (((4 * hh + q) ^ (r & 7)) << 4));
-                        ff.add_prod(w4.x, w4.x);
-                        ff.add_prod(w4.y, w4.y);
-                        ff.add_prod(w4.z, w4.z);
-                        ff.add_prod(w4.w, w4.w);
+                        for (int w = 0; w < kConvWarps; ++w) sum += part[STATS ? w : 0][t];
+                        xy_sum[STATS ? phase : 0][t] = sum;
                     }
+                    conv_sync(cs_bar, cs_uses, &s_abort);  // part[] is reused by the next phase
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
+                if (aborted) break;
             }
-            ff.renorm();
-            if (++since_fold == kFoldEvery) {
-                dacc += ff.value();
-                ff.zero();
-                since_fold = 0;
-            }
-            if (si.last) {
-                dacc += ff.value();
-                ff.zero();
-                since_fold = 0;
-                if (STATS) part[si.phase][hh][i] = dacc;
-                dacc = 0.0;
-            }
-            if (++stage == kRawStages) { stage = 0; ph ^= 1u; }
-            if (!(si.last && si.phase == 1)) continue;
 
             // ---- block epilogue
-            const long long k = si.block, nk = si.nk;
-            const int dpos = si.dpos;
-            const long long lo = off[k];
-            conv_sync(cs_bar, cs_uses, &s_abort);
+            const long long k = bi.k;
+            const long long lo = bi.lo;
             double sa = 0.0, ss = 0.0, sx = 0.0, sy = 0.0;
-            if (STATS && t < 128 && i < nk) {
-                const double xi = part[0][0][i] + part[0][1][i];
-                const double yi = part[1][0][i] + part[1][1][i];
-                x[lo + i] = xi;
-                y[lo + i] = yi;
-                const double xy = __dmul_rn(xi, yi);
-                sa = sqrt(xy);
-                ss = xy;
-                sx = xi;
-                sy = yi;
+            if (STATS) {
+                if (t < nk) {
+                    const double xi = xy_sum[0][t], yi = xy_sum[STATS ? 1 : 0][t];
+                    x[lo + t] = xi;
+                    y[lo + t] = yi;
+                    const double xy = __dmul_rn(xi, yi);
+                    sa = sqrt(xy);
+                    ss = xy;
+                    sx = xi;
+                    sy = yi;
+                }
             }
-            // off-diagonal Gram products from TMEM (rows = lanes of this warp's quadrant)
-            const int acc = it & 1;
+            // off-diagonal Gram products from TMEM: rows = lanes of this warp's quadrant (operand
+            // rows 0..127), the five 32-column chunks of a slot split between the quadrant's four warps
             FF offf;
             offf.zero();
-            if (mbar_wait(smem_u32(&bar_tfull[acc]), (uint32_t)(it >> 1) & 1u, &s_abort)) {
+            const int u0 = 2 * it;
+            const int q0 = u0 % 3, q1 = (u0 + 1) % 3;
+            if (wait_fast(smem_u32(&bar_tfull[it & 1]), (uint32_t)(it >> 1) & 1u, &s_abort)) {
                 tc_fence_after();
-                const int q4 = warp & 3, half = cw >> 2;
-                const int r = 32 * q4 + lane - dpos;  // vector of this TMEM lane
+                const int q4 = warp & 3, quarter = cw >> 2;
+                const int r = 32 * q4 + lane;  // operand row
+                const int end = dpos + nk;
+                const bool row_in = r >= dpos && r < end;
+                const bool wide = end > 128;
+                const uint32_t lane_base = tmem + ((uint32_t)(32 * q4) << 16);
 #pragma unroll 1
-                for (int u = 0; u < 2; ++u) {
-                    const int c0 = 64 * half + 32 * u;
+                for (int cchunk = quarter; cchunk < 5; cchunk += 4) {
+                    const int c0 = 32 * cchunk;
                     uint32_t gm[32], gn[32];
-                    const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(acc * 256 + c0);
-                    TMEM_LD_32X32B_X32(taddr, gm);
-                    TMEM_LD_32X32B_X32(taddr + 128, gn);
+                    TMEM_LD_32X32B_X32(lane_base + (uint32_t)(q0 * kSlotCols + c0), gm);
+                    TMEM_LD_32X32B_X32(lane_base + (uint32_t)(q1 * kSlotCols + c0), gn);
                     tmem_ld_wait();
-                    if (r >= 0 && r < nk) {
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const int jj = c0 + e - dpos;
-                            if (jj >= 0 && jj < nk && jj != r)
+                    for (int e = 0; e < 32; ++e) {
+                        const int col = c0 + e;
+                        if (col < kCornerCol) {
+                            // main Gram: operand rows r (< 128) and col; the missing rows >= 128 are
+                            // the transposes of these columns
+                            if (row_in && col >= dpos && col < end && col != r) {
+                                const float g = __uint_as_float(gm[e]);
+                                offf.add_prod(col >= 128 ? 2.0f * g : g, __uint_as_float(gn[e]));
+                            }
+                        } else if (wide) {
+                            // corner: operand rows r + 32 (>= 128) and 128 + (col - 144)
+                            const int rr = r + 32, cc = 128 + (col - kCornerCol);
+                            if (rr >= 128 && rr < end && cc < end && cc != rr)
                                 offf.add_prod(__uint_as_float(gm[e]), __uint_as_float(gn[e]));
                         }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[acc]));
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&bar_slot_free[q0]));
+                    mbar_arrive(smem_u32(&bar_slot_free[q1]));
+                }
+            } else {
+                aborted = true;
             }
             ++it;
             double offd = offf.value();
@@ -434,7 +538,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (STATS) { a[k] = r5[0]; ssum[k] = r5[1]; mf[k] = r5[2]; nf[k] = r5[3]; }
                 f[k] = sk + r5[4];
             }
-            conv_sync(cs_bar, cs_uses, &s_abort);  // part[] and red[] are reused by the next block
+            conv_sync(cs_bar, cs_uses, &s_abort);  // xy_sum[] and red[] are reused by the next block
+            if (lane == 0) mbar_arrive(smem_u32(&bar_bempty[bslot]));
+            if (++bslot == kBlockSlots) { bslot = 0; bph ^= 1u; }
         }
     }
 
@@ -450,7 +556,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Strided operands (vectors along the storage rows' inner dimension) feed the MMA MN-major, which
 // for TF32 wants 32-byte swizzle atoms; contiguous ones are K-major with the plain 128-byte swizzle.
-bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, int64_t ld, bool strided) {
+// Boxes are 32 elements wide and box_rows high.
+bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, int64_t ld, bool strided, int box_rows) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (fn == nullptr) {
         void* q = nullptr;
@@ -462,19 +569,18 @@ bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, 
     }
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
-    cuuint32_t box[2] = {32, 32};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, strided ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
 bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk) {
     if (vM.dtype != BMM_F32 || vN.dtype != BMM_F32 || max_nk > kMaxBlock) return false;
-    if (vM.len < 1 || vN.len < 1) return false;  // every block needs chunks in both phases
+    if (vM.len < 1 || vN.len < 1) return false;  // every block needs stages in both phases
     if ((vM.ld % 4) || (vN.ld % 4)) return false;
     if ((reinterpret_cast<uintptr_t>(vM.data) & 15) || (reinterpret_cast<uintptr_t>(vN.data) & 15)) return false;
     if (vM.len > 0x7fffffffLL || vN.len > 0x7fffffffLL || vM.count > 0x7fffffffLL) return false;
@@ -485,14 +591,20 @@ cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64
                                  bool stats, int* counter, double* x, double* y, double* a, double* ssum, double* mf,
                                  double* nf, double* f, DevStatus* st, cudaStream_t s) {
     // storage of each operand: rows x cols with stride ld (vectors are columns when strided)
-    CUtensorMap mM, mN;
-    const int64_t mrows = vM.mode == VEC_STRIDED ? vM.len : vM.count;
-    const int64_t mcols = vM.mode == VEC_STRIDED ? vM.count : vM.len;
-    const int64_t nrows = vN.mode == VEC_STRIDED ? vN.len : vN.count;
-    const int64_t ncols = vN.mode == VEC_STRIDED ? vN.count : vN.len;
-    if (!make_map_f32(&mM, vM.data, mrows, mcols, vM.ld, vM.mode == VEC_STRIDED) ||
-        !make_map_f32(&mN, vN.data, nrows, ncols, vN.ld, vN.mode == VEC_STRIDED))
-        return cudaErrorInvalidValue;
+    OperandMaps mM, mN;
+    auto maps_of = [](OperandMaps& om, const VecSet& v) {
+        const bool strided = v.mode == VEC_STRIDED;
+        const int64_t rows = strided ? v.len : v.count, cols = strided ? v.count : v.len;
+        if (strided) {
+            for (int g = 0; g < kMaxGroups; ++g)
+                if (!make_map_f32(&om.map[g], v.data, rows, cols, v.ld, true, kMnRows)) return false;
+            return true;
+        }
+        for (int g = 0; g < kMaxGroups; ++g)
+            if (!make_map_f32(&om.map[g], v.data, rows, cols, v.ld, false, 32 * (g + 1))) return false;
+        return true;
+    };
+    if (!maps_of(mM, vM) || !maps_of(mN, vN)) return cudaErrorInvalidValue;
     static bool attr[2] = {false, false};
     if (!attr[stats]) {
         cudaError_t e = stats ? cudaFuncSetAttribute(blockstats_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem)

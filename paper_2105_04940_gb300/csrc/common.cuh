@@ -63,6 +63,14 @@ struct FF {
         lo = __fsub_rn(lo, __fsub_rn(s, hi));
         hi = s;
     }
+    // += another float-float sum (TwoSum of the high parts, low parts added)
+    __device__ __forceinline__ void add(const FF& o) {
+        float t = __fadd_rn(hi, o.hi);
+        float bp = __fsub_rn(t, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(o.hi, bp));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(e, o.lo));
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
