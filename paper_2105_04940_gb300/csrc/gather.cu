@@ -4,6 +4,8 @@
 // rows for the tensor-core GEMM: operand A holds m rows of length L (row h = (C_{h,1..L})),
 // operand B holds p rows of length L (row f = (D_{1..L,f})).  Block sampling first expands
 // every drawn block into its run of contraction indices.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace bmm {
@@ -219,6 +221,100 @@ __global__ void __launch_bounds__(256) gather_contig_kernel(const T* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- BF16 operands, vector stores
+// hi (and, for split BF16, lo) parts of n consecutive values, written as 8- or 16-byte stores
+// (n = 4, 8) into the segments of the operand row: [hi] for BF16; [hi | hi | lo] (A, role 0)
+// or [hi | lo | hi] (B, role 1) for split BF16, whose K-concatenated product is hi hi + hi lo + lo hi.
+template <int NV>
+struct Bf16Pack;
+template <> struct Bf16Pack<4> { using type = uint2; };
+template <> struct Bf16Pack<8> { using type = uint4; };
+
+template <int NV>
+__device__ __forceinline__ void put_bf16(const OpWriter& wr, int64_t r, int64_t j, const float* v) {
+    using P = typename Bf16Pack<NV>::type;
+    __align__(16) __nv_bfloat16 hi[NV], lo[NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+        hi[u] = __float2bfloat16_rn(v[u]);
+        lo[u] = __float2bfloat16_rn(v[u] - __bfloat162float(hi[u]));
+    }
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(wr.out) + r * wr.ldo + j;
+    *reinterpret_cast<P*>(o) = *reinterpret_cast<const P*>(hi);
+    if (wr.mode == BMM_GEMM_SPLIT_BF16) {
+        *reinterpret_cast<P*>(o + wr.kseg) = *reinterpret_cast<const P*>(wr.role == 0 ? hi : lo);
+        *reinterpret_cast<P*>(o + 2 * wr.kseg) = *reinterpret_cast<const P*>(wr.role == 0 ? lo : hi);
+    }
+}
+
+// Vectors are storage rows (row-major N): 64 (contraction index j) x 64 (r) tiles through shared
+// memory; rows are read 16 bytes at a time when aligned and the transposed operand is written 8
+// BF16 (16 bytes) at a time.
+template <typename T>
+__global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
+    const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec, const int32_t* __restrict__ col,
+    const double* __restrict__ w, const int64_t* __restrict__ ext_dev, bool apply_weight, bool vec4, OpWriter wr,
+    DevStatus* st) {
+    __shared__ float tile[64][65];
+    __shared__ int64_t cidx[64];
+    __shared__ float csw[64];
+    const int64_t ext = *ext_dev;
+    const int64_t kseg = round_up(ext, 64);
+    const int64_t j0 = (int64_t)blockIdx.x * 64;
+    if (j0 >= kseg) return;
+    wr.kseg = kseg;
+    const int t = threadIdx.x;
+    if (t < 64) {
+        const int64_t j = j0 + t;
+        int64_t c = -1;
+        float sw = 0.f;
+        if (j < ext) {
+            c = col[j];
+            sw = apply_weight ? (float)sqrt(w[j]) : 1.f;
+            if (c < 0 || c >= nvec) { set_status(st, BMM_ERR_ARG, (int)j); c = -1; }
+        }
+        cidx[t] = c;
+        csw[t] = sw;
+    }
+    __syncthreads();
+    for (int64_t r0 = (int64_t)blockIdx.y * 64; r0 < len; r0 += (int64_t)gridDim.y * 64) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = t + 256 * u;
+            const int jj = idx >> 4, q = idx & 15;
+            const int64_t c = cidx[jj];
+            const int64_t r = r0 + 4 * q;
+            float e[4] = {0.f, 0.f, 0.f, 0.f};
+            if (c >= 0) {
+                const T* src = X + c * ld + r;
+                if (vec4 && r + 4 <= len) {
+                    const float4 f4 = __ldg(reinterpret_cast<const float4*>(src));
+                    e[0] = f4.x; e[1] = f4.y; e[2] = f4.z; e[3] = f4.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (r + k < len) e[k] = ldv<T, float>(src + k);
+                }
+            }
+            const float sw = csw[jj];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tile[jj][4 * q + k] = e[k] * sw;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int rr = (t >> 3) + 32 * u, jj8 = (t & 7) * 8;
+            if (r0 + rr < len) {
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = tile[jj8 + k][rr];
+                put_bf16<8>(wr, r0 + rr, j0 + jj8, v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, typename V>
 static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
                             int64_t ext_max, int mode, int role, bool apply_weight, void* out, int64_t ldo,
@@ -226,6 +322,24 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
     OpWriter wr{out, ldo, 0, mode, role};
     const int64_t kmax = round_up(imax(ext_max, 1), 64);
     const T* X = static_cast<const T*>(v.data);
+    if constexpr (std::is_same<V, float>::value) {
+        // BF16 operand rows: 8- and 16-byte stores need ldo and the output 16-byte aligned
+        if ((ldo % 8) != 0 || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return cudaErrorInvalidValue;
+        if (v.mode == VEC_STRIDED) {
+            // one operand column per lane keeps every warp load one contiguous 128-byte span; wider
+            // per-lane column groups spread a load over several spans and re-fetch sectors
+            dim3 grid((unsigned)ceil_div(kmax, 128), (unsigned)imin(imax(ceil_div(v.len, kGatherRows), 1), 4096));
+            (count_launch(), gather_strided_kernel<T, V><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev,
+                                                                              apply_weight, wr, st));
+        } else {
+            const bool vec4 = sizeof(T) == 4 && std::is_same<T, float>::value && (v.ld % 4) == 0 &&
+                              (reinterpret_cast<uintptr_t>(v.data) & 15) == 0;
+            dim3 grid((unsigned)ceil_div(kmax, 64), (unsigned)imin(imax(ceil_div(v.len, 64), 1), 2048));
+            (count_launch(), gather_contig_bf16_kernel<T><<<grid, 256, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev,
+                                                                               apply_weight, vec4, wr, st));
+        }
+        return cudaGetLastError();
+    } else {
     if (v.mode == VEC_STRIDED) {
         dim3 grid((unsigned)ceil_div(kmax, 128), (unsigned)imin(imax(ceil_div(v.len, kGatherRows), 1), 4096));
         (count_launch(), gather_strided_kernel<T, V><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, apply_weight, wr, st));
@@ -234,6 +348,7 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
         (count_launch(), gather_contig_kernel<T, V><<<grid, 256, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, apply_weight, wr, st));
     }
     return cudaGetLastError();
+    }
 }
 
 template <typename V>
