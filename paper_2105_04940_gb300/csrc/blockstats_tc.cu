@@ -3,35 +3,37 @@
 // f_k = ||M^k N_k||_F^2 = <G_M, G_N>_F with G_M = M^kT M^k and G_N = N_k N_kT (n_k x n_k Grams;
 // eq. 1.2, eq. 3.9).  Its diagonal is s_k = sum_i x_i y_i, which this kernel accumulates exactly
 // (float-float folded into FP64) together with x_i = ||M^(i)||^2 and y_i = ||N_(i)||^2; the
-// off-diagonal part sum_{i != j} G_M[i,j] G_N[i,j] comes from TF32 tensor-core Grams in TMEM.
+// off-diagonal part sum_{i != j} G_M[i,j] G_N[i,j] comes from tensor-core Grams in TMEM: TF32 for
+// FP32 inputs, BF16 (exact products) for BF16 inputs, FP32 accumulation.
 //
 // One CTA per SM pulls blocks from a global counter.  For block k it streams the vectors of the
-// block -- columns of M (length m), then rows of N (length p) -- in sub-tiles of 32 coordinates,
-// several sub-tiles (up to 40 KB) per pipeline stage:
+// block -- columns of M (length m), then rows of N (length p) -- in sub-tiles of E coordinates
+// (E = 128 bytes / element size: 32 FP32 or 64 BF16), several sub-tiles (up to 40 KB) per stage:
 //   warp 0      one lane: TMA loads into a 5-stage ring of 40 KB and a record per stage and per
-//               block.  A strided operand stage is nb boxes of 32 columns x 64 rows (two
-//               sub-tiles, 128-byte swizzle in 32-byte atoms); a contiguous operand stage is one
-//               box of 32 coordinates x 32 nb vectors per sub-tile (128-byte swizzle).  Few large
-//               copies keep the TMA unit, which takes about as long for a small box as for a large
-//               one, from limiting the pass;
-//   warp 1      one lane: tcgen05.mma kind::tf32 (M = 128, K = 8) with the same operand tile as A
-//               and B.  A tile whose vectors are its rows (contiguous storage) is a K-major operand,
-//               one whose vectors are its columns (strided storage: row-major M, column-major N)
-//               an MN-major operand; both are read where TMA put them.  G_M and G_N of a block take
-//               two of three 160-column TMEM slots used in turn, so the Grams of the next block
-//               build up while the epilogue of the previous one reads its slots;
+//               block.  A strided operand stage is nb boxes of E columns x 64 rows (128-byte
+//               swizzle; in 32-byte atoms for FP32); a contiguous operand stage is one box of E
+//               coordinates x 32 nb vectors per sub-tile (128-byte swizzle).  Few large copies keep
+//               the TMA unit, which takes about as long for a small box as for a large one, from
+//               limiting the pass;
+//   warp 1      one lane: tcgen05.mma (M = 128, 32 bytes of K per instruction) with the same operand
+//               tile as A and B.  A tile whose vectors are its rows (contiguous storage) is a K-major
+//               operand, one whose vectors are its columns (strided storage: row-major M,
+//               column-major N) an MN-major operand; both are read where TMA put them.  G_M and G_N
+//               of a block take two of three 160-column TMEM slots used in turn, so the Grams of the
+//               next block build up while the epilogue of the previous one reads its slots;
 //   warps 2-17  (statistics pass) sum the squares of each stage's elements, every warp a
 //               sixteenth of each sub-tile for all vectors, float-float sums per lane and vector; at
 //               the end of a block they fold the norms into a_k, s_k, ||M^k||_F^2, ||N_k||_F^2, and
 //               (both passes) reduce the off-diagonal Gram products from TMEM.
 // Positions.  A strided operand's first box starts at the 16-byte boundary at or below the block's
 // first column (TMA needs a 16-byte-aligned inner coordinate), so its vectors are operand rows
-// d .. d + n_k - 1 with d = off_k mod 4; the contiguous operand of the same block is loaded d rows
-// early to match.  The MMA takes operand rows 0..127 as its M side and rows 0..npad-1 (npad <= 144)
-// as its N side.  When d + n_k exceeds 128 (a "wide" block, n_k > 125) the missing Gram rows are
-// the transposes of columns >= 128 of the rows below 128, which the epilogue counts twice, except
-// for the products among the <= 3 vectors at rows >= 128: a second MMA (A = rows 32..159, B = rows
-// 128..143, N = 16) computes those into the last 16 columns of the slot.
+// d .. d + n_k - 1 with d = off_k mod (16 bytes / element size); the contiguous operand of the same
+// block is loaded d rows early to match.  The MMA takes operand rows 0..127 as its M side and rows
+// 0..npad-1 (npad <= 144) as its N side.  When d + n_k exceeds 128 (a "wide" block) the missing
+// Gram rows are the transposes of columns >= 128 of the rows below 128, which the epilogue counts
+// twice, except for the products among the <= 7 vectors at rows >= 128: a second MMA (A = rows
+// R0..R0+127 with R0 = 32 for FP32, 64 for BF16, B = rows 128..143, N = 16) computes those into the
+// last 16 columns of the slot.
 // Operand rows outside the block hold neighbouring data or zeros and are masked out of every sum.
 // All waits are bounded; on expiry the CTA records BMM_ERR_TIMEOUT, lets its copies and MMAs in
 // flight land, frees TMEM and returns.
@@ -43,10 +45,12 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kBoxBytes = 32 * 32 * 4;        // 32 x 32 FP32: one sub-tile of one 32-wide group
-constexpr int kMnRows = 64;                   // rows per strided box: two sub-tiles
-constexpr int kMnBoxBytes = 32 * kMnRows * 4; // 8 KB
-constexpr int kStageBytes = 10 * kBoxBytes;   // 40 KB per pipeline stage
+constexpr int kRowBytes = 128;                // one swizzled row: E elements
+constexpr int kRowsPerGroup = 32;             // K-major boxes come in multiples of 32 vector rows
+constexpr int kGroupBytes = kRowsPerGroup * kRowBytes;  // 4 KB
+constexpr int kMnRows = 64;                   // rows per strided box
+constexpr int kMnBoxBytes = kMnRows * kRowBytes;        // 8 KB
+constexpr int kStageBytes = 40 * 1024;        // 40 KB per pipeline stage
 constexpr int kStages = 5;
 constexpr int kBlockSlots = 4;                // block records in flight
 constexpr int kConvWarps = 16;
@@ -58,16 +62,59 @@ constexpr int kSlotCols = 160;                // TMEM columns per Gram slot (3 s
 constexpr int kCornerCol = 144;               // wide blocks: rows >= 128 x rows >= 128, N = 16
 constexpr int kMaxBlock = 128;
 constexpr int kFoldStages = 4;                // stages between folds into the second-level sums
+constexpr int kMaxKMaps = 6;                  // K-major box heights 32 .. 192 rows
 
-// Sub-tiles of 32 coordinates per stage of a contiguous operand spanning nb groups of 32 vectors.
-// The MMA reads 128 operand rows (16 KB) from the start of every sub-tile, and a wide block's
-// corner MMA reads up to 20 KB; rows past the block belong to the next sub-tile (masked), but must
-// stay inside the stage: (per - 1) * nb * 4 KB + 16 KB <= 40 KB, and for nb = 5,
-// (per - 1) * 20 KB + 20 KB <= 40 KB.  A strided operand stage always holds kMnRows / 32 = 2
-// sub-tiles: its MN-major operand reads four 8 KB boxes (five for a wide block's corner), at most
-// 4 KB + 4 * 8 KB = 36 KB (40 KB) into the stage.
-__host__ __device__ __forceinline__ int subtiles_per_stage(int nb) { return nb >= 5 ? 2 : 1 + 6 / nb; }
-constexpr int kMaxGroups = 5;                 // 32-wide groups a block spans (d + n_k <= 131)
+// Element-type traits.  E elements fill a 128-byte row; one MMA consumes 32 bytes of K.
+template <typename T> struct Tr;
+template <> struct Tr<float> {
+    static constexpr int E = 32;
+    static constexpr int kAlign = 4;            // elements per 16 bytes
+    static constexpr int kMnSubRows = 32;       // rows of a strided sub-tile (4 MMAs of K = 8)
+    static constexpr int kMnPer = kMnRows / kMnSubRows;
+    static constexpr uint32_t kMnKstep = 64;    // 8 rows x 128 bytes, in descriptor units
+    static constexpr int kCornerRow0 = 32;      // first operand row of the corner MMA's A
+    static constexpr uint32_t kFmt = 2;         // TF32
+    static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    static constexpr CUtensorMapSwizzle kMnSwizzle = CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B;
+    static __device__ __forceinline__ uint64_t mn_desc(uint32_t addr) { return sw128_atom32_mn_desc(addr, kMnBoxBytes); }
+    static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+        tc_mma_tf32(d, a, b, idesc, acc);
+    }
+    // byte offset of (row h, column cc) in a strided box: 32-byte chunk cc / 8 at chunk (cc / 8) ^ (h mod 4)
+    static __device__ __forceinline__ int mn_offset(int h, int cc) {
+        return h * kRowBytes + ((((cc >> 3) ^ (h & 3)) << 5) | ((cc & 7) << 2));
+    }
+    static __device__ __forceinline__ float to_f(float v) { return v; }
+};
+template <> struct Tr<__nv_bfloat16> {
+    static constexpr int E = 64;
+    static constexpr int kAlign = 8;
+    static constexpr int kMnSubRows = 64;       // 4 MMAs of K = 16
+    static constexpr int kMnPer = kMnRows / kMnSubRows;
+    static constexpr uint32_t kMnKstep = 128;   // 16 rows x 128 bytes
+    static constexpr int kCornerRow0 = 64;      // an MN atom is 64 rows wide
+    static constexpr uint32_t kFmt = 1;         // BF16 (kind::f16)
+    static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    static constexpr CUtensorMapSwizzle kMnSwizzle = CU_TENSOR_MAP_SWIZZLE_128B;
+    static __device__ __forceinline__ uint64_t mn_desc(uint32_t addr) { return sw128_mn_desc(addr, kMnBoxBytes); }
+    static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+        tc_mma_bf16(d, a, b, idesc, acc);
+    }
+    // 16-byte chunk (2 cc) / 16 of row h at chunk ^ (h mod 8)
+    static __device__ __forceinline__ int mn_offset(int h, int cc) {
+        return h * kRowBytes + ((((cc >> 3) ^ (h & 7)) << 4) | ((cc & 7) << 1));
+    }
+    static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+
+// Sub-tiles per stage of a contiguous operand whose sub-tiles are nb groups of 32 vector rows.
+// The MMA reads 128 operand rows (16 KB) from the start of every sub-tile and a wide block's
+// corner MMA reads up to R0 + 128 rows; rows past the block belong to the next sub-tile (masked)
+// but must stay inside the 40 KB stage: (per - 1) * nb * 4 KB + 16 KB <= 40 KB for nb <= 4; wide
+// FP32 blocks (nb = 5, corner to 20 KB) take 2 and wide BF16 blocks (nb = 6, corner to 24 KB) 1.
+// A strided operand stage holds kMnPer sub-tiles in nb boxes of 8 KB; its MN-major operand reads
+// the block's boxes, at most 40 KB (FP32, five boxes for a wide block's corner) or 24 KB (BF16).
+__host__ __device__ __forceinline__ int subtiles_per_stage(int nb) { return nb >= 6 ? 1 : (nb == 5 ? 2 : 1 + 6 / nb); }
 
 enum StageFlags : int {
     ST_PHASE = 1,   // 0: columns of M, 1: rows of N
@@ -78,13 +125,13 @@ enum StageFlags : int {
 };
 
 struct __align__(16) StageInfo {
-    int block;  // -1: no more work
-    int flags;  // StageFlags
-    int nk;     // block size
-    int d;      // tile row (K-major) or column (MN-major) of the block's first vector
-    int dpos;   // operand row of the block's first vector, the same in both phases
-    int nb;     // boxes per sub-tile
-    int nsub;   // sub-tiles in this stage
+    int block;      // -1: no more work
+    int flags;      // StageFlags
+    int nk;         // block size
+    int d;          // tile row (K-major) or column (MN-major) of the block's first vector
+    int dpos;       // operand row of the block's first vector, the same in both phases
+    int nb;         // groups per sub-tile: 32-row groups (K-major) or E-column boxes (MN-major)
+    int nsub;       // sub-tiles in this stage
     int sub_bytes;  // distance between sub-tiles in the stage
 };
 
@@ -96,51 +143,50 @@ struct __align__(16) BlockInfo {
     int pad[3];
 };
 
-// Tensor maps of one operand: strided storage uses map[0] (32 x kMnRows boxes); contiguous storage
-// uses map[nb - 1] (32 coordinates x 32 nb vectors).
+// Tensor maps of one operand: strided storage uses map[0] (E x 64 boxes); contiguous storage
+// uses map[nb - 1] (E coordinates x 32 nb vectors).
 struct OperandMaps {
-    CUtensorMap map[kMaxGroups];
+    CUtensorMap map[kMaxKMaps];
 };
 
-__device__ __forceinline__ uint32_t idesc_tf32(int npad, bool mn_major) {
-    // D = F32 (bits 4-5), A = B = TF32 (2 at bits 7-9, 10-12), A and B MN-major (bits 15, 16) or
+template <typename T>
+__device__ __forceinline__ uint32_t idesc_of(int npad, bool mn_major) {
+    // D = F32 (bits 4-5), A and B format (bits 7-9, 10-12), A and B MN-major (bits 15, 16) or
     // K-major, N>>3 at 17, M>>4 at 24
     const uint32_t major = mn_major ? (3u << 15) : 0u;
-    return (1u << 4) | (2u << 7) | (2u << 10) | major | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | (Tr<T>::kFmt << 7) | (Tr<T>::kFmt << 10) | major | ((uint32_t)(npad >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
 }
 
-// Byte offset of element (row h, column cc) in a 32 x 32 FP32 box of a strided operand, loaded
-// with the 128-byte swizzle of 32-byte atoms: chunk cc / 8 of row h sits at chunk (cc / 8) ^ (h mod 4).
-__device__ __forceinline__ int strided_offset(int h, int cc) { return h * 128 + ((((cc >> 3) ^ (h & 3)) << 5) | ((cc & 7) << 2)); }
-
-// Four K steps (32 coordinates) of one sub-tile, A = B = the operand at descriptor (lo, hi): the
-// start address is in the low word, so a K step is a 32-bit add (32 bytes K-major, 1024 bytes
+// Four K steps (128 bytes of K) of one sub-tile, A = B = the operand at descriptor (lo, hi): the
+// start address is in the low word, so a K step is a 32-bit add (32 bytes K-major, 8 or 16 rows
 // MN-major).  The first MMA overwrites the accumulator when `fresh`.
-template <bool MN>
+template <typename T, bool MN>
 __device__ __forceinline__ void mma_sub(uint32_t d, uint32_t lo_a, uint32_t lo_b, uint32_t hi, uint32_t idesc, bool fresh) {
-    constexpr uint32_t ks = MN ? 64u : 2u;
+    constexpr uint32_t ks = MN ? Tr<T>::kMnKstep : 2u;
     const uint64_t h = (uint64_t)hi << 32;
-    tc_mma_tf32(d, h | lo_a, h | lo_b, idesc, fresh ? 0u : 1u);
-    tc_mma_tf32(d, h | (lo_a + ks), h | (lo_b + ks), idesc, 1u);
-    tc_mma_tf32(d, h | (lo_a + 2 * ks), h | (lo_b + 2 * ks), idesc, 1u);
-    tc_mma_tf32(d, h | (lo_a + 3 * ks), h | (lo_b + 3 * ks), idesc, 1u);
+    Tr<T>::mma(d, h | lo_a, h | lo_b, idesc, fresh ? 0u : 1u);
+    Tr<T>::mma(d, h | (lo_a + ks), h | (lo_b + ks), idesc, 1u);
+    Tr<T>::mma(d, h | (lo_a + 2 * ks), h | (lo_b + 2 * ks), idesc, 1u);
+    Tr<T>::mma(d, h | (lo_a + 3 * ks), h | (lo_b + 3 * ks), idesc, 1u);
 }
 
-template <bool MN>
+template <typename T, bool MN>
 __device__ __forceinline__ void mma_stage(uint32_t d_main, uint32_t d_corner, uint32_t addr, uint32_t sub_bytes, int nsub,
                                           uint32_t idesc, uint32_t idesc16, bool first, bool wide) {
-    // MN-major: 32-row blocks of operand rows are the 8 KB boxes (leading byte offset); K-major:
-    // 32 operand rows are 4 KB
-    constexpr uint32_t group = MN ? (uint32_t)kMnBoxBytes >> 4 : (uint32_t)kBoxBytes >> 4;
-    const uint64_t d0 = MN ? sw128_atom32_mn_desc(addr, kMnBoxBytes) : sw128_desc(addr);
+    // corner operands, in descriptor units: A from operand row R0, B from operand row 128.
+    // MN-major: an E-row block of operand rows is one 8 KB box; K-major: a row is 128 bytes.
+    constexpr uint32_t ca = MN ? (uint32_t)(Tr<T>::kCornerRow0 / Tr<T>::E) * (kMnBoxBytes >> 4)
+                               : (uint32_t)(Tr<T>::kCornerRow0 * kRowBytes) >> 4;
+    constexpr uint32_t cb = MN ? (uint32_t)(128 / Tr<T>::E) * (kMnBoxBytes >> 4) : (uint32_t)(128 * kRowBytes) >> 4;
+    const uint64_t d0 = MN ? Tr<T>::mn_desc(addr) : sw128_desc(addr);
     const uint32_t hi = (uint32_t)(d0 >> 32);
     uint32_t lo = (uint32_t)d0;
     const uint32_t step = sub_bytes >> 4;
     for (int s = 0; s < nsub; ++s, lo += step) {
         const bool fresh = first && s == 0;
-        mma_sub<MN>(d_main, lo, lo, hi, idesc, fresh);
-        // operand rows 32..159 (A) against rows 128..143 (B)
-        if (wide) mma_sub<MN>(d_corner, lo + group, lo + 4 * group, hi, idesc16, fresh);
+        mma_sub<T, MN>(d_main, lo, lo, hi, idesc, fresh);
+        if (wide) mma_sub<T, MN>(d_corner, lo + ca, lo + cb, hi, idesc16, fresh);
     }
 }
 
@@ -159,13 +205,14 @@ __device__ __forceinline__ bool conv_sync(uint32_t bar, int& uses, volatile int*
     return ok;
 }
 
-template <bool STATS>
+template <typename T, bool STATS>
 __global__ void __launch_bounds__(kThreads, 1)
     blockstats_tc_kernel(const __grid_constant__ OperandMaps tmM, const __grid_constant__ OperandMaps tmN,
                          int M_strided, int N_strided, long long m, long long p, const int64_t* __restrict__ off,
                          long long K, long long n, int* __restrict__ counter, double* __restrict__ x,
                          double* __restrict__ y, double* __restrict__ a, double* __restrict__ ssum,
                          double* __restrict__ mf, double* __restrict__ nf, double* __restrict__ f, DevStatus* st) {
+    using TR = Tr<T>;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
     __shared__ __align__(8) uint64_t bar_bfull[kBlockSlots], bar_bempty[kBlockSlots];
@@ -236,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     f[k] = 0.0;
                     continue;
                 }
-                const int dlo = (int)(lo & 3);
+                const int dlo = (int)(lo & (TR::kAlign - 1));
                 const int dpos = (M_strided || N_strided) ? dlo : 0;
                 const bool wide = dpos + nk > 128;
                 if (!wait_fast(smem_u32(&bar_bempty[bslot]), bph ^ 1u, &s_abort)) { aborted = true; break; }
@@ -250,9 +297,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int strided = phase == 0 ? M_strided : N_strided;
                     const long long len = phase == 0 ? m : p;
                     const int d = strided ? dlo : dpos;
-                    const int nb = (int)((d + nk + 31) / 32);
-                    const int per = strided ? kMnRows / 32 : subtiles_per_stage(nb);
-                    const long long nsub_total = (len + 31) / 32;
+                    // strided: boxes of E columns; contiguous: groups of 32 vector rows (a wide
+                    // BF16 block takes 6 so that the corner's rows 64..191 are loaded)
+                    int nb = strided ? (int)((d + nk + TR::E - 1) / TR::E) : (int)((d + nk + 31) / 32);
+                    if (!strided && wide && TR::kCornerRow0 + 128 > 32 * nb) nb = (TR::kCornerRow0 + 128) / 32;
+                    const int per = strided ? TR::kMnPer : subtiles_per_stage(nb);
+                    const long long nsub_total = (len + TR::E - 1) / TR::E;
                     const OperandMaps& maps = phase == 0 ? tmM : tmN;
                     const CUtensorMap* map = &maps.map[strided ? 0 : nb - 1];
                     for (long long c0 = 0; c0 < nsub_total; c0 += per) {
@@ -267,20 +317,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         si.dpos = dpos;
                         si.nb = nb;
                         si.nsub = nsub;
-                        si.sub_bytes = strided ? kBoxBytes : nb * kBoxBytes;
+                        si.sub_bytes = strided ? TR::kMnSubRows * kRowBytes : nb * kGroupBytes;
                         const uint32_t fb = smem_u32(&bar_full[stage]);
                         uint8_t* dst = stage_ptr(stage);
                         if (strided) {
-                            // nb boxes of 32 columns x kMnRows rows (rows past the operand read as zeros)
+                            // nb boxes of E columns x 64 rows (rows past the operand read as zeros)
                             mbar_expect_tx(fb, (uint32_t)(nb * kMnBoxBytes));
                             for (int b = 0; b < nb; ++b)
-                                tma_load_2d(smem_u32(dst + b * kMnBoxBytes), map, fb, (int32_t)(lo - d + 32 * b),
-                                            (int32_t)(32 * c0));
+                                tma_load_2d(smem_u32(dst + b * kMnBoxBytes), map, fb, (int32_t)(lo - d + TR::E * b),
+                                            (int32_t)(TR::kMnSubRows * c0));
                         } else {
-                            // one box of 32 coordinates x 32 nb vectors per sub-tile
-                            mbar_expect_tx(fb, (uint32_t)(nsub * nb * kBoxBytes));
+                            // one box of E coordinates x 32 nb vectors per sub-tile
+                            mbar_expect_tx(fb, (uint32_t)(nsub * nb * kGroupBytes));
                             for (int s = 0; s < nsub; ++s)
-                                tma_load_2d(smem_u32(dst + s * nb * kBoxBytes), map, fb, (int32_t)(32 * (c0 + s)),
+                                tma_load_2d(smem_u32(dst + s * nb * kGroupBytes), map, fb, (int32_t)(TR::E * (c0 + s)),
                                             (int32_t)(lo - d));
                         }
                         issued_mask |= 1u << stage;
@@ -325,11 +375,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t addr = smem_u32(stage_ptr(stage));
                 const uint32_t sub_bytes = (uint32_t)si.sub_bytes;
                 if (mn)
-                    mma_stage<true>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_tf32(npad, true), idesc_tf32(16, true),
-                                    first, wide);
+                    mma_stage<T, true>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_of<T>(npad, true),
+                                       idesc_of<T>(16, true), first, wide);
                 else
-                    mma_stage<false>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_tf32(npad, false),
-                                     idesc_tf32(16, false), first, wide);
+                    mma_stage<T, false>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_of<T>(npad, false),
+                                        idesc_of<T>(16, false), first, wide);
                 tc_commit(smem_u32(&bar_empty[stage]));
                 if ((si.flags & ST_LAST) && phase == 1) {
                     tc_commit(smem_u32(&bar_tfull[it & 1]));
@@ -345,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------ norms, block epilogue
         const int t = threadIdx.x - 64;
-        const int cw = warp - 2;  // converter warp 0..7
+        const int cw = warp - 2;  // converter warp 0..15
         int stage = 0, bslot = 0;
         uint32_t ph = 0, bph = 0;
         int it = 0;
@@ -375,20 +425,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mn_phase = si.flags & ST_MN;
                         const uint8_t* tile = stage_ptr(stage);
                         const int sub_bytes = si.sub_bytes;
-                        if (si.flags & ST_MN) {
-                            // rows h = cw and cw + 16 of every sub-tile; vector i is tile column d + i
+                        if (mn_phase) {
+                            // rows h = cw + 16 r of every sub-tile; vector i is tile column d + i
                             for (int s = 0; s < si.nsub; ++s) {
                                 const uint8_t* sub = tile + s * sub_bytes;
 #pragma unroll
-                                for (int r = 0; r < 2; ++r) {
+                                for (int r = 0; r < TR::kMnSubRows / 16; ++r) {
                                     const int h = cw + 16 * r;
 #pragma unroll
                                     for (int v = 0; v < 4; ++v) {
                                         const int i = lane + 32 * v;
                                         if (i < si.nk) {
                                             const int j = i + si.d;
-                                            const float e = *reinterpret_cast<const float*>(
-                                                sub + (j >> 5) * kMnBoxBytes + strided_offset(h, j & 31));
+                                            const float e = TR::to_f(*reinterpret_cast<const T*>(
+                                                sub + (j / TR::E) * kMnBoxBytes + TR::mn_offset(h, j % TR::E)));
                                             acc[v].add_prod(e, e);
                                         }
                                     }
@@ -406,12 +456,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     const int i = lane + 32 * ((cw & 1) + 2 * vv);
                                     if (i < si.nk) {
                                         const int r = i + si.d;
-                                        const float4 w4 =
-                                            *reinterpret_cast<const float4*>(sub + r * 128 + ((q ^ (r & 7)) << 4));
-                                        acc[vv].add_prod(w4.x, w4.x);
-                                        acc[vv].add_prod(w4.y, w4.y);
-                                        acc[vv].add_prod(w4.z, w4.z);
-                                        acc[vv].add_prod(w4.w, w4.w);
+                                        const uint4 w4 =
+                                            *reinterpret_cast<const uint4*>(sub + r * kRowBytes + ((q ^ (r & 7)) << 4));
+                                        const T* e = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+                                        for (int u = 0; u < 16 / (int)sizeof(T); ++u) {
+                                            const float ev = TR::to_f(e[u]);
+                                            acc[vv].add_prod(ev, ev);
+                                        }
                                     }
                                 }
                             }
@@ -503,8 +555,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 offf.add_prod(col >= 128 ? 2.0f * g : g, __uint_as_float(gn[e]));
                             }
                         } else if (wide) {
-                            // corner: operand rows r + 32 (>= 128) and 128 + (col - 144)
-                            const int rr = r + 32, cc = 128 + (col - kCornerCol);
+                            // corner: operand rows R0 + r (>= 128 counted) and 128 + (col - 144)
+                            const int rr = r + TR::kCornerRow0, cc = 128 + (col - kCornerCol);
                             if (rr >= 128 && rr < end && cc < end && cc != rr)
                                 offf.add_prod(__uint_as_float(gm[e]), __uint_as_float(gn[e]));
                         }
@@ -554,10 +606,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && s_abort) set_status(st, BMM_ERR_TIMEOUT, 2);
 }
 
-// Strided operands (vectors along the storage rows' inner dimension) feed the MMA MN-major, which
-// for TF32 wants 32-byte swizzle atoms; contiguous ones are K-major with the plain 128-byte swizzle.
-// Boxes are 32 elements wide and box_rows high.
-bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, int64_t ld, bool strided, int box_rows) {
+// Strided operands (vectors along the storage rows' inner dimension) feed the MMA MN-major: FP32
+// wants 32-byte swizzle atoms, BF16 the plain 128-byte swizzle; contiguous ones are K-major with the
+// plain 128-byte swizzle.  Boxes are 128 bytes wide and box_rows high.
+template <typename T>
+bool make_map(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, int64_t ld, bool strided, int box_rows) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (fn == nullptr) {
         void* q = nullptr;
@@ -568,20 +621,54 @@ bool make_map_f32(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, 
         fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(q);
     }
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
-    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * (int64_t)sizeof(T))};
+    cuuint32_t box[2] = {(cuuint32_t)Tr<T>::E, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, strided ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(mp, Tr<T>::kTmaType, 2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              strided ? Tr<T>::kMnSwizzle : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+bool maps_of(OperandMaps& om, const VecSet& v) {
+    const bool strided = v.mode == VEC_STRIDED;
+    const int64_t rows = strided ? v.len : v.count, cols = strided ? v.count : v.len;
+    for (int g = 0; g < kMaxKMaps; ++g)
+        if (!make_map<T>(&om.map[g], v.data, rows, cols, v.ld, strided, strided ? kMnRows : 32 * (g + 1))) return false;
+    return true;
+}
+
+template <typename T, bool STATS>
+cudaError_t launch_t(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n, int* counter,
+                     double* x, double* y, double* a, double* ssum, double* mf, double* nf, double* f, DevStatus* st,
+                     cudaStream_t s) {
+    OperandMaps mM, mN;
+    if (!maps_of<T>(mM, vM) || !maps_of<T>(mN, vN)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(blockstats_tc_kernel<T, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)imin(K, sms);
+    (count_launch(), blockstats_tc_kernel<T, STATS><<<grid, kThreads, kSmem, s>>>(
+        mM, mN, vM.mode == VEC_STRIDED, vN.mode == VEC_STRIDED, vM.len, vN.len, off, K, n, counter, x, y, a, ssum, mf,
+        nf, f, st));
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk) {
-    if (vM.dtype != BMM_F32 || vN.dtype != BMM_F32 || max_nk > kMaxBlock) return false;
+    if (vM.dtype != vN.dtype || (vM.dtype != BMM_F32 && vM.dtype != BMM_BF16) || max_nk > kMaxBlock) return false;
     if (vM.len < 1 || vN.len < 1) return false;  // every block needs stages in both phases
-    if ((vM.ld % 4) || (vN.ld % 4)) return false;
+    const int align = vM.dtype == BMM_F32 ? 4 : 8;  // elements per 16 bytes
+    if ((vM.ld % align) || (vN.ld % align)) return false;
     if ((reinterpret_cast<uintptr_t>(vM.data) & 15) || (reinterpret_cast<uintptr_t>(vN.data) & 15)) return false;
     if (vM.len > 0x7fffffffLL || vN.len > 0x7fffffffLL || vM.count > 0x7fffffffLL) return false;
     return tc_gemm_supported();
@@ -590,43 +677,11 @@ bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk)
 cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n,
                                  bool stats, int* counter, double* x, double* y, double* a, double* ssum, double* mf,
                                  double* nf, double* f, DevStatus* st, cudaStream_t s) {
-    // storage of each operand: rows x cols with stride ld (vectors are columns when strided)
-    OperandMaps mM, mN;
-    auto maps_of = [](OperandMaps& om, const VecSet& v) {
-        const bool strided = v.mode == VEC_STRIDED;
-        const int64_t rows = strided ? v.len : v.count, cols = strided ? v.count : v.len;
-        if (strided) {
-            for (int g = 0; g < kMaxGroups; ++g)
-                if (!make_map_f32(&om.map[g], v.data, rows, cols, v.ld, true, kMnRows)) return false;
-            return true;
-        }
-        for (int g = 0; g < kMaxGroups; ++g)
-            if (!make_map_f32(&om.map[g], v.data, rows, cols, v.ld, false, 32 * (g + 1))) return false;
-        return true;
-    };
-    if (!maps_of(mM, vM) || !maps_of(mN, vN)) return cudaErrorInvalidValue;
-    static bool attr[2] = {false, false};
-    if (!attr[stats]) {
-        cudaError_t e = stats ? cudaFuncSetAttribute(blockstats_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem)
-                              : cudaFuncSetAttribute(blockstats_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e != cudaSuccess) return e;
-        attr[stats] = true;
-    }
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)imin(K, sms);
-    if (stats)
-        (count_launch(), blockstats_tc_kernel<true><<<grid, kThreads, kSmem, s>>>(
-            mM, mN, vM.mode == VEC_STRIDED, vN.mode == VEC_STRIDED, vM.len, vN.len, off, K, n, counter, x, y, a, ssum,
-            mf, nf, f, st));
-    else
-        (count_launch(), blockstats_tc_kernel<false><<<grid, kThreads, kSmem, s>>>(
-            mM, mN, vM.mode == VEC_STRIDED, vN.mode == VEC_STRIDED, vM.len, vN.len, off, K, n, counter, x, y, a, ssum,
-            mf, nf, f, st));
-    return cudaGetLastError();
+    if (vM.dtype == BMM_F32)
+        return stats ? launch_t<float, true>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s)
+                     : launch_t<float, false>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s);
+    return stats ? launch_t<__nv_bfloat16, true>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s)
+                 : launch_t<__nv_bfloat16, false>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s);
 }
 
 }  // namespace bmm

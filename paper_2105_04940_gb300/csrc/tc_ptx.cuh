@@ -100,6 +100,19 @@ __device__ __forceinline__ uint64_t sw128_atom32_mn_desc(uint32_t saddr, uint32_
     return d;
 }
 
+// Shared-memory matrix descriptor: MN-major 16-bit tile, 128-byte swizzle (swizzle mode 2).  Each
+// 128-byte row holds 64 consecutive M/N elements of one K index; 8 rows form a 1024-byte swizzle
+// atom; one MMA (K = 16) reads two atoms 1024 bytes apart (stride byte offset); blocks of 64 M/N
+// elements follow each other every mn_stride_bytes (leading byte offset).
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr, uint32_t mn_stride_bytes) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((mn_stride_bytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 #define TMEM_LD_32X32B_X32(taddr, r)                                                                                  \
     asm volatile(                                                                                                     \
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"  \

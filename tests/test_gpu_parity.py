@@ -92,15 +92,16 @@ def test_exact_block_frobenius(bmm, dtype):
     assert rel_err(host(pb), oracle.p_blk_prodnorm(f)) < 1e-10
 
 
-def _tf32_gram_bound(M, N, off, m, p):
-    """Error scale of the off-diagonal trace from TF32 Grams: tau * sum_{i != j} (|M|^T|M| |G_N| + |G_M| |N||N|^T)
-    with tau = 2^-9 (both factors truncated to TF32) + len * 2^-23 (FP32 accumulation)."""
+def _tf32_gram_bound(M, N, off, m, p, round_in=2.0 ** -9):
+    """Error scale of the off-diagonal trace from tensor-core Grams: tau * sum_{i != j} (|M|^T|M| |G_N| + |G_M| |N||N|^T)
+    with tau = round_in + len * 2^-23 (FP32 accumulation); round_in = 2^-9 for TF32 (both factors
+    rounded), 0 for BF16 inputs (their products are exact in FP32)."""
     out = []
     for a_, b_ in zip(off[:-1], off[1:]):
         A, B = M[:, a_:b_], N[a_:b_, :]
         GM, GN = A.T @ A, B @ B.T
         AM, AN = np.abs(A).T @ np.abs(A), np.abs(B) @ np.abs(B).T
-        tM, tN = 2.0 ** -9 + m * 2.0 ** -23, 2.0 ** -9 + p * 2.0 ** -23
+        tM, tN = round_in + m * 2.0 ** -23, round_in + p * 2.0 ** -23
         E = tM * AM * np.abs(GN) + tN * np.abs(GM) * AN + tM * tN * AM * AN
         np.fill_diagonal(E, 0.0)
         out.append(E.sum())
@@ -109,13 +110,14 @@ def _tf32_gram_bound(M, N, off, m, p):
 
 @pytest.mark.parametrize("layouts", [("row", "row"), ("col", "col"), ("row", "col"), ("col", "row")])
 @pytest.mark.parametrize("p", [264, 261])
-def test_fused_statistics_and_tensor_core_f(bmm, layouts, p):
-    """One pass for x, y, a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 and f_k = s_k + TF32 off-diagonal trace.
+@pytest.mark.parametrize("dtype", [np.float32, "bf16"])
+def test_fused_statistics_and_tensor_core_f(bmm, layouts, p, dtype):
+    """One pass for x, y, a_k, s_k, ||M^k||_F^2, ||N_k||_F^2 and f_k = s_k + tensor-core off-diagonal trace.
 
-    p = 264 keeps every leading dimension a multiple of 4, so each storage order runs the fused
-    tensor-core pass; p = 261 makes some leading dimensions odd, which takes the exact fallback."""
+    Leading dimensions that are multiples of 16 bytes run the fused tensor-core pass (TF32 Grams for
+    FP32, BF16 for BF16); others (p = 261, m = 300 for BF16) take the exact fallback."""
     m, n = 300, 6000
-    off, M, N, Mt, Nt = _problem(m, n, p, 60, seed=41, dtype=np.float32, lo=16, hi=128)
+    off, M, N, Mt, Nt = _problem(m, n, p, 60, seed=41, dtype=dtype, lo=16, hi=128)
     Mt, Nt = as_layout(Mt, layouts[0]), as_layout(Nt, layouts[1])
     prob = bmm.prepare(Mt, Nt, off, max_draws=100)
     pv = torch.empty(n, dtype=torch.float64, device=Mt.device)
@@ -125,7 +127,8 @@ def test_fused_statistics_and_tensor_core_f(bmm, layouts, p):
     # the fused pass is one kernel (plus the probabilities); odd leading dimensions fall back
     ld_m = n if layouts[0] == "row" else m
     ld_n = p if layouts[1] == "row" else n
-    fused = ld_m % 4 == 0 and ld_n % 4 == 0
+    align = 4 if dtype is np.float32 else 8
+    fused = ld_m % align == 0 and ld_n % align == 0
     assert (bmm._abi.bmm_launch_count() - launches == 2) == fused
     x, y = oracle.col_row_sq_norms(M, N)
     st = oracle.block_stats(x, y, off)
@@ -135,7 +138,7 @@ def test_fused_statistics_and_tensor_core_f(bmm, layouts, p):
         assert rel_err(host(prob.st[k]), st[k]) < 1e-12, k
     assert rel_err(host(pv), oracle.p_col_opt(st["w"], st["a"], off)) < 1e-12
     f = oracle.block_frob_sq(M, N, off)
-    bound = _tf32_gram_bound(M, N, off, m, p)
+    bound = _tf32_gram_bound(M, N, off, m, p, round_in=2.0 ** -9 if dtype is np.float32 else 0.0)
     err = np.abs(host(prob.st["f"]) - f)
     assert np.all(err <= bound + 1e-12 * f), np.max(err / (bound + 1e-300))
     # the statistics-reusing form computes f only, from the given s_k
@@ -147,24 +150,32 @@ def test_fused_statistics_and_tensor_core_f(bmm, layouts, p):
 
 
 @pytest.mark.parametrize("layouts", [("row", "row"), ("col", "col"), ("row", "col"), ("col", "row")])
-def test_fused_statistics_offsets_wide_and_low_rank_blocks(bmm, layouts):
-    """Blocks at every offset mod 4 (strided tiles start at the 16-byte boundary below the block),
-    the widest blocks (127 at offset 3 and 128 at offset 1 exceed the 128 operand rows of an
-    in-place strided tile; 126 at offset 2 fills them exactly), tiny blocks, and one rank-one
-    block (off-diagonal trace as large as the diagonal)."""
+@pytest.mark.parametrize("dtype", [np.float32, "bf16"])
+def test_fused_statistics_offsets_wide_and_low_rank_blocks(bmm, layouts, dtype):
+    """Blocks at every offset mod 4 (FP32) or mod 8 (BF16): strided tiles start at the 16-byte
+    boundary below the block; the widest blocks (FP32: 127 at offset 3 and 128 at offset 1;
+    BF16: 128 at offset 7) exceed the 128 operand rows of an in-place strided tile, 126 at offset 2
+    fills them exactly; tiny blocks; and one rank-one block (off-diagonal trace as large as the
+    diagonal)."""
     rng = np.random.default_rng(3)
-    sizes = np.array([3, 127, 126, 128, 1, 128, 5, 77, 16, 100, 34, 3])  # n = 748: every ld % 4 == 0
+    if dtype is np.float32:
+        sizes = np.array([3, 127, 126, 128, 1, 128, 5, 77, 16, 100, 34, 3])  # n = 748: every ld % 4 == 0
+        low_rank = 7
+    else:
+        sizes = np.array([7, 128, 1, 127, 2, 126, 128, 5, 77, 16, 100, 34, 1])  # n = 752: every ld % 8 == 0
+        low_rank = 8
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     n, m, p = int(off[-1]), 96, 152
     M = rng.standard_normal((m, n)).astype(np.float32)
     N = rng.standard_normal((n, p)).astype(np.float32)
     u, v = rng.standard_normal(m), rng.standard_normal(p)
-    w = rng.standard_normal(sizes[7])
-    M[:, off[7]:off[8]] = np.outer(u, w)
-    N[off[7]:off[8], :] = np.outer(w, v)
-    M, N = M.astype(np.float64), N.astype(np.float64)
-    Mt = as_layout(to_dev(M.astype(np.float32)), layouts[0])
-    Nt = as_layout(to_dev(N.astype(np.float32)), layouts[1])
+    w = rng.standard_normal(sizes[low_rank])
+    M[:, off[low_rank]:off[low_rank + 1]] = np.outer(u, w)
+    N[off[low_rank]:off[low_rank + 1], :] = np.outer(w, v)
+    tdt = torch.float32 if dtype is np.float32 else torch.bfloat16
+    Mt = as_layout(to_dev(M, tdt), layouts[0])
+    Nt = as_layout(to_dev(N, tdt), layouts[1])
+    M, N = host(Mt.double()), host(Nt.double())
     prob = bmm.prepare(Mt, Nt, off, max_draws=50)
     launches = bmm._abi.bmm_launch_count()
     bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, None, prob.st, prob.ws)
@@ -178,7 +189,8 @@ def test_fused_statistics_offsets_wide_and_low_rank_blocks(bmm, layouts):
         assert rel_err(host(prob.st[k]), st[k]) < 1e-12, k
     f = oracle.block_frob_sq(M, N, off)
     err = np.abs(host(prob.st["f"]) - f)
-    assert np.all(err <= _tf32_gram_bound(M, N, off, m, p) + 1e-12 * f)
+    round_in = 2.0 ** -9 if dtype is np.float32 else 0.0
+    assert np.all(err <= _tf32_gram_bound(M, N, off, m, p, round_in) + 1e-12 * f)
     # the Gram-only form (statistics reused) gives the same f
     f_fused = host(prob.st["f"]).copy()
     prob.st["f"].zero_()
