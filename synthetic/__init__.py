@@ -65,6 +65,21 @@ def block_offsets_uneven(n: int, K: int, lo: int, hi: int, seed: int) -> np.ndar
     return off
 
 
+def batched_products(count: int, seed: int):
+    """Shapes of the batched workload: m, p uniform on {128..2048 step 128}, n uniform on
+    {4096..65536 step 4096}, K = n / 64 blocks with sizes in [32, 128] summing to n.
+    Returns a list of dicts (m, n, p, offsets)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.integers(1, 17)) * 128
+        p = int(rng.integers(1, 17)) * 128
+        n = int(rng.integers(1, 17)) * 4096
+        K = n // 64
+        out.append(dict(m=m, n=n, p=p, offsets=block_offsets_uneven(n, K, 32, 128, seed=seed * 100003 + i)))
+    return out
+
+
 def _block_scales(K: int, sigma: float, rng: np.random.Generator) -> np.ndarray:
     return rng.lognormal(mean=0.0, sigma=sigma, size=K)
 
