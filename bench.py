@@ -6,10 +6,11 @@ N(0,1) * s_k with s_k ~ LogNormal(0, 1.5) shared by column block k of M and row 
 K = 1024 blocks with sizes drawn uniformly from {16..128} and adjusted to sum to n; c = K/8 = 128
 blocks, i.e. L = round(c n / K) = 8192 outer products for the Alg. 2 methods.
 
-A step is one approximate product by the A-optimal method (OPL: statistics pass, exact
-||M^k N_k||_F, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
+A step is one approximate product by the A-optimal method (OPL: norm pass, ||M^k N_k||_F^2 from
+TF32 tcgen05 Grams, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
 BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flush is
-needed).  Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+needed).  Prints one JSON line.  --impl reference times the FP64 CPU oracle instead;
+--workload batched runs the 512-product batched workload instead.
 """
 from __future__ import annotations
 
@@ -34,8 +35,10 @@ SMALL = dict(m=256, n=4096, p=256, K=64, nk_lo=64, nk_hi=64, sigma=1.0, c_blocks
 # profiling case: the large workload's n, K and blocks with m = p = 2048 (inputs 1 GB, > L2)
 PROFILE = dict(WORKLOAD, m=2048, p=2048)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
-# committed ncu capture (profiles/); None until a capture of the current kernel exists.
-TRAFFIC = {}
+# committed ncu capture (profiles/ncu_gram_pass_and_gemm_profilecase.md): 1.0786 GB on the
+# profiling case (m = p = 2048), which streams the inputs once; the full workload streams
+# (8192 + 8192) / (2048 + 2048) = 4x those bytes.
+TRAFFIC = {"gram_f": 4 * 1.0786e9}
 
 
 def parse():
