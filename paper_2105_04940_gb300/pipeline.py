@@ -65,6 +65,34 @@ class Problem:
         return int(self.offsets[-1])
 
 
+_UPLOADS: dict = {}
+
+
+def _upload(arr: np.ndarray, dev):
+    """Device copy of a small host int64 array, without making the host wait for the stream (a
+    pageable copy would): pinned staging and a non-blocking copy, cached per content and device so
+    that repeated products with the same blocks (every layer, every step) upload once."""
+    torch = _torch()
+    key = (str(dev), arr.dtype.str, arr.tobytes())
+    hit = _UPLOADS.get(key)
+    if hit is None:
+        if len(_UPLOADS) >= 64:
+            _UPLOADS.pop(next(iter(_UPLOADS)))
+        host_t = torch.from_numpy(np.ascontiguousarray(arr))
+        ev = None
+        if dev.type == "cuda":
+            t = host_t.pin_memory().to(dev, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record()
+        else:
+            t = host_t.to(dev)
+        hit = _UPLOADS[key] = (t, ev)
+    t, ev = hit
+    if ev is not None:
+        torch.cuda.current_stream(dev).wait_event(ev)  # the copy may have been issued on another stream
+    return t
+
+
 def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode: int | None = None,
             ws=None) -> Problem:
     """Upload the offsets, allocate statistics and a workspace large enough for ``gemm_mode``
@@ -75,7 +103,7 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
     n = int(off[-1])
     max_nk = int(np.diff(off).max())
     dev = M.device
-    off_dev = torch.as_tensor(off, device=dev)
+    off_dev = _upload(off, dev)
     B = A.blocks(off_dev, n, max_nk)
     if ws is None:
         need = max(A.bmm_workspace_size(M, N, B, unit, max_draws, md) for md in modes)
@@ -183,7 +211,7 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         per = max(1, c0 // K)
         ck0 = prob.pilot_counts.get(per)
         if ck0 is None:  # uploaded once per problem, outside any timed loop
-            ck0 = torch.as_tensor(np.full(K, per, dtype=np.int64), device=dev)
+            ck0 = _upload(np.full(K, per, dtype=np.int64), dev)
             prob.pilot_counts[per] = ck0
         pidx = torch.empty(K * per, dtype=torch.int32, device=dev)
         pscale = torch.empty(K * per, dtype=torch.float64, device=dev)
