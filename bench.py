@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--method", default="OPL")
-    ap.add_argument("--mode", default="bf16", choices=["bf16", "split_bf16", "f64"])
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "split_bf16", "e4m3", "f64"])
     ap.add_argument("--small", action="store_true", help="256 x 4096 x 256 case (L2-resident)")
     ap.add_argument("--profile-case", action="store_true", help="2048 x 65536 x 2048 case for ncu captures")
     ap.add_argument("--quick", action="store_true", help="skip e2e, methods, error and CPU baseline")

@@ -94,7 +94,12 @@ enum {
 enum {
     BMM_GEMM_F64 = 0,        /* FP64 operands and accumulation on CUDA cores; out is FP64 */
     BMM_GEMM_BF16 = 1,       /* BF16 operands on tcgen05 tensor cores, FP32 accumulation; out is FP32 */
-    BMM_GEMM_SPLIT_BF16 = 2  /* x = hi + lo (both BF16); hi*hi + hi*lo + lo*hi on tcgen05, FP32 accumulation */
+    BMM_GEMM_SPLIT_BF16 = 2, /* x = hi + lo (both BF16); hi*hi + hi*lo + lo*hi on tcgen05, FP32 accumulation */
+    BMM_GEMM_E4M3 = 3        /* FP8 e4m3 operands on tcgen05 (kind::f8f6f4), FP32 accumulation; out is FP32.
+                                Per drawn outer product t, C^(t) is scaled by 2^(e_t) and D_(t) by 2^(-e_t)
+                                (balancing their magnitudes; the product is unchanged), and each operand by
+                                one power of two that brings its largest value to at most 448, restored in
+                                the epilogue.  bmm_apply / bmm_apply_batched only. */
 };
 
 /* Purposes folded into a stream id: stream_id = (replicate << 8) | purpose. */

@@ -21,7 +21,7 @@ CK_OPT, CK_HAT, CK_TILDE, CK_EQUAL = 0, 1, 2, 3
 F_NONE, F_EXACT, F_TC = 0, 1, 2
 REUSE_STATS = 0x100
 UNIT_COLUMN, UNIT_BLOCK = 0, 1
-GEMM_F64, GEMM_BF16, GEMM_SPLIT_BF16 = 0, 1, 2
+GEMM_F64, GEMM_BF16, GEMM_SPLIT_BF16, GEMM_E4M3 = 0, 1, 2, 3
 PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
 
 EXPORTED = (

@@ -145,6 +145,7 @@ struct ApplyPlan {
     void* A;
     void* Bop;
     int64_t lmax, kseg_max, ktot;
+    float *amaxA, *amaxB, *sa, *sb, *oscale;  // e4m3 operand scales
 };
 void plan_apply(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int unit, int64_t count,
                 int mode, ApplyPlan* p) {
@@ -158,9 +159,17 @@ void plan_apply(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks
         p->prefix = cv.take<int64_t>(count);
     }
     p->ext = cv.take<int64_t>(1);
-    p->kseg_max = round_up(imax(p->lmax, 1), 64);
+    p->kseg_max = round_up(imax(p->lmax, 1), mode == BMM_GEMM_E4M3 ? 128 : 64);
     p->ktot = p->kseg_max * (mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1);
-    const size_t es = mode == BMM_GEMM_F64 ? 8 : 2;
+    const size_t es = mode == BMM_GEMM_F64 ? 8 : (mode == BMM_GEMM_E4M3 ? 1 : 2);
+    p->amaxA = p->amaxB = p->sa = p->sb = p->oscale = nullptr;
+    if (mode == BMM_GEMM_E4M3) {
+        p->amaxA = cv.take<float>(p->lmax);
+        p->amaxB = cv.take<float>(p->lmax);
+        p->sa = cv.take<float>(p->lmax);
+        p->sb = cv.take<float>(p->lmax);
+        p->oscale = cv.take<float>(4);
+    }
     p->A = cv.take<char>(M->rows * p->ktot * (int64_t)es);
     p->Bop = cv.take<char>(N->cols * p->ktot * (int64_t)es);
 }
@@ -225,7 +234,7 @@ void plan_backward(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blo
 }
 
 bool valid_gemm_mode(int mode) {
-    return mode == BMM_GEMM_F64 || mode == BMM_GEMM_BF16 || mode == BMM_GEMM_SPLIT_BF16;
+    return mode == BMM_GEMM_F64 || mode == BMM_GEMM_BF16 || mode == BMM_GEMM_SPLIT_BF16 || mode == BMM_GEMM_E4M3;
 }
 
 }  // namespace
@@ -433,17 +442,27 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
         w = plan.w;
     }
     const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
-    BMM_TRY(launch_gather_operand(vM, col, w, plan.ext, plan.lmax, gemm_mode, 0, true, plan.A, plan.ktot, dst, cs));
-    BMM_TRY(launch_gather_operand(vN, col, w, plan.ext, plan.lmax, gemm_mode, 1, true, plan.Bop, plan.ktot, dst, cs));
+    if (gemm_mode == BMM_GEMM_E4M3) {
+        // column maxima of C and row maxima of D, then their power-of-two scales
+        BMM_TRY(cudaMemsetAsync(plan.amaxA, 0, sizeof(float) * plan.lmax, cs));
+        BMM_TRY(cudaMemsetAsync(plan.amaxB, 0, sizeof(float) * plan.lmax, cs));
+        BMM_TRY(launch_vec_absmax(vM, col, w, plan.ext, plan.lmax, plan.amaxA, cs));
+        BMM_TRY(launch_vec_absmax(vN, col, w, plan.ext, plan.lmax, plan.amaxB, cs));
+        BMM_TRY(launch_fp8_scales(plan.amaxA, plan.amaxB, w, plan.ext, plan.sa, plan.sb, plan.oscale, cs));
+    }
+    BMM_TRY(launch_gather_operand(vM, col, w, plan.ext, plan.lmax, gemm_mode, 0, true, plan.A, plan.ktot, dst, cs,
+                                  plan.sa));
+    BMM_TRY(launch_gather_operand(vN, col, w, plan.ext, plan.lmax, gemm_mode, 1, true, plan.Bop, plan.ktot, dst, cs,
+                                  plan.sb));
     if (gemm_mode == BMM_GEMM_F64) {
         BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.A), plan.ktot, static_cast<const double*>(plan.Bop),
                                 plan.ktot, M->rows, N->cols, 0, plan.ext, static_cast<double*>(odata), out->ld,
                                 accumulate, cs));
         return BMM_OK;
     }
-    *g = GemmArgs{static_cast<const __nv_bfloat16*>(plan.A), plan.ktot, static_cast<const __nv_bfloat16*>(plan.Bop),
-                  plan.ktot, M->rows, N->cols, plan.ktot, 0, plan.ext, gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1,
-                  static_cast<float*>(odata), out->ld, accumulate};
+    *g = GemmArgs{plan.A, plan.ktot, plan.Bop, plan.ktot, M->rows, N->cols, plan.ktot, 0, plan.ext,
+                  gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1, static_cast<float*>(odata), out->ld, accumulate,
+                  gemm_mode == BMM_GEMM_E4M3 ? GEMM_ELEM_E4M3 : GEMM_ELEM_BF16, plan.oscale};
     *done = false;
     return BMM_OK;
 }
@@ -459,7 +478,7 @@ BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_block
     bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs, &g, &done);
     if (s != BMM_OK || done) return s;
     BMM_TRY(launch_gemm_bf16_tc(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out, g.ldo,
-                                g.accumulate, status_of(ws), cs));
+                                g.accumulate, status_of(ws), cs, g.elem, g.scale));
     return BMM_OK;
 }
 
@@ -496,7 +515,7 @@ BMM_API bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_ma
     if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
     if (!valid_gemm_mode(gemm_mode) || p == nullptr || c < 0 || (unit == BMM_UNIT_COLUMN && ck == nullptr))
         return BMM_ERR_ARG;
-    if (gemm_mode == BMM_GEMM_SPLIT_BF16) return BMM_ERR_UNSUPPORTED;
+    if (gemm_mode == BMM_GEMM_SPLIT_BF16 || gemm_mode == BMM_GEMM_E4M3) return BMM_ERR_UNSUPPORTED;
     const int gd = gemm_mode == BMM_GEMM_F64 ? BMM_F64 : BMM_F32;
     if ((s = check_mat(G)) != BMM_OK) return s;
     if (G->layout != BMM_ROW_MAJOR || G->rows != M->rows || G->cols != N->cols) return BMM_ERR_SHAPE;

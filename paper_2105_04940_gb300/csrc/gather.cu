@@ -4,6 +4,8 @@
 // rows for the tensor-core GEMM: operand A holds m rows of length L (row h = (C_{h,1..L})),
 // operand B holds p rows of length L (row f = (D_{1..L,f})).  Block sampling first expands
 // every drawn block into its run of contraction indices.
+#include <cuda_fp8.h>
+
 #include <type_traits>
 
 #include "internal.h"
@@ -119,10 +121,16 @@ struct OpWriter {
     void* out;
     int64_t ldo, kseg;
     int mode, role;
+    int kunit;              // padded extent: a multiple of 64 (128 for e4m3)
+    const float* colscale;  // per-column factor replacing sqrt(w_j), or null
     __device__ __forceinline__ void put(int64_t r, int64_t j, double v) const {
         static_cast<double*>(out)[r * ldo + j] = v;
     }
     __device__ __forceinline__ void put(int64_t r, int64_t j, float v) const {
+        if (mode == BMM_GEMM_E4M3) {
+            static_cast<__nv_fp8_storage_t*>(out)[r * ldo + j] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+            return;
+        }
         __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + r * ldo;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         if (mode == BMM_GEMM_BF16) {
@@ -146,7 +154,7 @@ __global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int6
                                       const int64_t* __restrict__ ext_dev, bool apply_weight, OpWriter wr,
                                       DevStatus* st) {
     const int64_t ext = *ext_dev;
-    const int64_t kseg = round_up(ext, 64);
+    const int64_t kseg = round_up(ext, wr.kunit);
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= kseg) return;
     wr.kseg = kseg;
@@ -154,7 +162,7 @@ __global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int6
     V sw = V(0);
     if (j < ext) {
         c = col[j];
-        sw = apply_weight ? (V)sqrt(w[j]) : V(1);
+        sw = wr.colscale != nullptr ? (V)wr.colscale[j] : (apply_weight ? (V)sqrt(w[j]) : V(1));
         if (c < 0 || c >= nvec) { set_status(st, BMM_ERR_ARG, (int)j); c = -1; }
     }
     for (int64_t r0 = (int64_t)blockIdx.y * kGatherRows; r0 < len; r0 += (int64_t)gridDim.y * kGatherRows) {
@@ -186,7 +194,7 @@ __global__ void __launch_bounds__(256) gather_contig_kernel(const T* __restrict_
     __shared__ int64_t cidx[32];
     __shared__ V csw[32];
     const int64_t ext = *ext_dev;
-    const int64_t kseg = round_up(ext, 64);
+    const int64_t kseg = round_up(ext, wr.kunit);
     const int64_t j0 = (int64_t)blockIdx.x * 32;
     if (j0 >= kseg) return;
     wr.kseg = kseg;
@@ -247,6 +255,14 @@ __device__ __forceinline__ void put_bf16(const OpWriter& wr, int64_t r, int64_t 
     }
 }
 
+// 8 consecutive values as e4m3 bytes (saturating), one 8-byte store
+__device__ __forceinline__ void put_fp8x8(const OpWriter& wr, int64_t r, int64_t j, const float* v) {
+    __align__(8) __nv_fp8_storage_t q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) q[u] = __nv_cvt_float_to_fp8(v[u], __NV_SATFINITE, __NV_E4M3);
+    *reinterpret_cast<uint2*>(static_cast<__nv_fp8_storage_t*>(wr.out) + r * wr.ldo + j) = *reinterpret_cast<const uint2*>(q);
+}
+
 // Vectors are storage rows (row-major N): 64 (contraction index j) x 64 (r) tiles through shared
 // memory; rows are read 16 bytes at a time when aligned and the transposed operand is written 8
 // BF16 (16 bytes) at a time.
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
     __shared__ int64_t cidx[64];
     __shared__ float csw[64];
     const int64_t ext = *ext_dev;
-    const int64_t kseg = round_up(ext, 64);
+    const int64_t kseg = round_up(ext, wr.kunit);
     const int64_t j0 = (int64_t)blockIdx.x * 64;
     if (j0 >= kseg) return;
     wr.kseg = kseg;
@@ -270,7 +286,7 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
         float sw = 0.f;
         if (j < ext) {
             c = col[j];
-            sw = apply_weight ? (float)sqrt(w[j]) : 1.f;
+            sw = wr.colscale != nullptr ? wr.colscale[j] : (apply_weight ? (float)sqrt(w[j]) : 1.f);
             if (c < 0 || c >= nvec) { set_status(st, BMM_ERR_ARG, (int)j); c = -1; }
         }
         cidx[t] = c;
@@ -308,7 +324,10 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
                 float v[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) v[k] = tile[jj8 + k][rr];
-                put_bf16<8>(wr, r0 + rr, j0 + jj8, v);
+                if (wr.mode == BMM_GEMM_E4M3)
+                    put_fp8x8(wr, r0 + rr, j0 + jj8, v);
+                else
+                    put_bf16<8>(wr, r0 + rr, j0 + jj8, v);
             }
         }
         __syncthreads();
@@ -318,13 +337,14 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
 template <typename T, typename V>
 static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
                             int64_t ext_max, int mode, int role, bool apply_weight, void* out, int64_t ldo,
-                            DevStatus* st, cudaStream_t s) {
-    OpWriter wr{out, ldo, 0, mode, role};
-    const int64_t kmax = round_up(imax(ext_max, 1), 64);
+                            DevStatus* st, cudaStream_t s, const float* colscale) {
+    const int kunit = mode == BMM_GEMM_E4M3 ? 128 : 64;
+    OpWriter wr{out, ldo, 0, mode, role, kunit, colscale};
+    const int64_t kmax = round_up(imax(ext_max, 1), kunit);
     const T* X = static_cast<const T*>(v.data);
     if constexpr (std::is_same<V, float>::value) {
-        // BF16 operand rows: 8- and 16-byte stores need ldo and the output 16-byte aligned
-        if ((ldo % 8) != 0 || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return cudaErrorInvalidValue;
+        // BF16 / e4m3 operand rows: 8- and 16-byte stores need ldo and the output 16-byte aligned
+        if ((ldo % 16) != 0 || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return cudaErrorInvalidValue;
         if (v.mode == VEC_STRIDED) {
             // one operand column per lane keeps every warp load one contiguous 128-byte span; wider
             // per-lane column groups spread a load over several spans and re-fetch sectors
@@ -354,20 +374,146 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
 template <typename V>
 static cudaError_t gather_v(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
                             int64_t ext_max, int mode, int role, bool apply_weight, void* out, int64_t ldo,
-                            DevStatus* st, cudaStream_t s) {
+                            DevStatus* st, cudaStream_t s, const float* colscale) {
     switch (v.dtype) {
-        case BMM_F64: return gather_t<double, V>(v, col, w, ext_dev, ext_max, mode, role, apply_weight, out, ldo, st, s);
-        case BMM_F32: return gather_t<float, V>(v, col, w, ext_dev, ext_max, mode, role, apply_weight, out, ldo, st, s);
-        default: return gather_t<__nv_bfloat16, V>(v, col, w, ext_dev, ext_max, mode, role, apply_weight, out, ldo, st, s);
+        case BMM_F64: return gather_t<double, V>(v, col, w, ext_dev, ext_max, mode, role, apply_weight, out, ldo, st, s, colscale);
+        case BMM_F32: return gather_t<float, V>(v, col, w, ext_dev, ext_max, mode, role, apply_weight, out, ldo, st, s, colscale);
+        default: return gather_t<__nv_bfloat16, V>(v, col, w, ext_dev, ext_max, mode, role, apply_weight, out, ldo, st, s, colscale);
     }
 }
 
 cudaError_t launch_gather_operand(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
                                   int64_t ext_max, int mode, int split_role, bool apply_weight, void* out, int64_t ldo,
-                                  DevStatus* st, cudaStream_t s) {
+                                  DevStatus* st, cudaStream_t s, const float* colscale) {
     if (mode == BMM_GEMM_F64)
-        return gather_v<double>(v, col, w, ext_dev, ext_max, mode, split_role, apply_weight, out, ldo, st, s);
-    return gather_v<float>(v, col, w, ext_dev, ext_max, mode, split_role, apply_weight, out, ldo, st, s);
+        return gather_v<double>(v, col, w, ext_dev, ext_max, mode, split_role, apply_weight, out, ldo, st, s, colscale);
+    return gather_v<float>(v, col, w, ext_dev, ext_max, mode, split_role, apply_weight, out, ldo, st, s, colscale);
+}
+
+// ---------------------------------------------------------------- FP8 operand scales
+// amax[j] = sqrt(w_j) max_r |vec_{col_j}[r]| as the bit pattern of a non-negative float, so that
+// partial maxima combine with integer atomicMax.  Vectors are storage columns: a thread per j and a
+// run of rows (as the strided gather); storage rows: a warp per j.
+template <typename T>
+__global__ void absmax_strided_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
+                                      const int32_t* __restrict__ col, const double* __restrict__ w,
+                                      const int64_t* __restrict__ ext_dev, float* __restrict__ amax) {
+    const int64_t ext = *ext_dev;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ext) return;
+    const int64_t c = col[j];
+    if (c < 0 || c >= nvec) return;
+    float m = 0.f;
+    const int64_t r1 = imin(len, ((int64_t)blockIdx.y + 1) * kGatherRows * 4);
+    for (int64_t r = (int64_t)blockIdx.y * kGatherRows * 4; r < r1; ++r) m = fmaxf(m, fabsf(ldv<T, float>(X + r * ld + c)));
+    m *= (float)sqrt(w[j]);
+    if (m > 0.f) atomicMax(reinterpret_cast<int*>(amax) + j, __float_as_int(m));
+}
+
+template <typename T>
+__global__ void absmax_contig_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
+                                     const int32_t* __restrict__ col, const double* __restrict__ w,
+                                     const int64_t* __restrict__ ext_dev, float* __restrict__ amax) {
+    const int64_t ext = *ext_dev;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= ext) return;
+    const int64_t c = col[j];
+    if (c < 0 || c >= nvec) return;
+    float m = 0.f;
+    for (int64_t r = lane; r < len; r += 32) m = fmaxf(m, fabsf(ldv<T, float>(X + c * ld + r)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    m *= (float)sqrt(w[j]);
+    if (lane == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(amax) + j, __float_as_int(m));
+}
+
+template <typename T>
+static cudaError_t absmax_t(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
+                            int64_t ext_max, float* amax, cudaStream_t s) {
+    const T* X = static_cast<const T*>(v.data);
+    if (v.mode == VEC_STRIDED) {
+        dim3 grid((unsigned)ceil_div(imax(ext_max, 1), 128), (unsigned)imax(ceil_div(v.len, kGatherRows * 4), 1));
+        (count_launch(), absmax_strided_kernel<T><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev, amax));
+    } else {
+        (count_launch(), absmax_contig_kernel<T><<<(unsigned)ceil_div(imax(ext_max, 1) * 32, 256), 256, 0, s>>>(
+            X, v.len, v.ld, v.count, col, w, ext_dev, amax));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_absmax(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
+                              int64_t ext_max, float* amax, cudaStream_t s) {
+    if (v.len > 0x7fffffffLL / 2) return cudaErrorInvalidValue;  // grid.y of the strided form
+    switch (v.dtype) {
+        case BMM_F64: return absmax_t<double>(v, col, w, ext_dev, ext_max, amax, s);
+        case BMM_F32: return absmax_t<float>(v, col, w, ext_dev, ext_max, amax, s);
+        default: return absmax_t<__nv_bfloat16>(v, col, w, ext_dev, ext_max, amax, s);
+    }
+}
+
+// One CTA.  e_j = round(log2(sqrt(b_j / a_j))) makes a_j 2^(e_j) and b_j 2^(-e_j) about equal (the
+// product a_j b_j is unchanged); gA, gB are the largest exponents keeping every scaled maximum of
+// their operand at most 448.  All factors are powers of two (exact).
+__global__ void __launch_bounds__(1024) fp8_scales_kernel(const float* __restrict__ amaxA, const float* __restrict__ amaxB,
+                                                          const double* __restrict__ w, const int64_t* __restrict__ ext_dev,
+                                                          float* __restrict__ sa, float* __restrict__ sb,
+                                                          float* __restrict__ out_scale) {
+    __shared__ float red[2][32];
+    const int64_t ext = *ext_dev;
+    float ma = 0.f, mb = 0.f;
+    for (int64_t j = threadIdx.x; j < ext; j += blockDim.x) {
+        const float a = amaxA[j], b = amaxB[j];
+        int e = 0;
+        if (a > 0.f && b > 0.f) e = (int)fminf(fmaxf(rintf(0.5f * log2f(b / a)), -60.f), 60.f);
+        ma = fmaxf(ma, ldexpf(a, e));
+        mb = fmaxf(mb, ldexpf(b, -e));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = ma; red[1][threadIdx.x >> 5] = mb; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        ma = threadIdx.x < (blockDim.x >> 5) ? red[0][threadIdx.x] : 0.f;
+        mb = threadIdx.x < (blockDim.x >> 5) ? red[1][threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+            mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        }
+        if (threadIdx.x == 0) { red[0][0] = ma; red[1][0] = mb; }
+    }
+    __syncthreads();
+    // largest g with max * 2^g <= 448: g = floor(log2(448 / max)), corrected for log2f rounding
+    auto gexp = [](float mx) {
+        if (!(mx > 0.f)) return 0;
+        int g = (int)floorf(log2f(448.f / mx));
+        g = max(-100, min(100, g));
+        while (g > -100 && ldexpf(mx, g) > 448.f) --g;
+        while (g < 100 && ldexpf(mx, g + 1) <= 448.f) ++g;
+        return g;
+    };
+    const int gA = gexp(red[0][0]), gB = gexp(red[1][0]);
+    for (int64_t j = threadIdx.x; j < ext; j += blockDim.x) {
+        const float a = amaxA[j], b = amaxB[j];
+        int e = 0;
+        if (a > 0.f && b > 0.f) e = (int)fminf(fmaxf(rintf(0.5f * log2f(b / a)), -60.f), 60.f);
+        // factors stay finite: the largest scaled value is at most 448, so only a column of values
+        // below ~1e-36 could ask for more than 2^100
+        const float r = (float)sqrt(w[j]);
+        sa[j] = ldexpf(r, max(-140, min(100, e + gA)));
+        sb[j] = ldexpf(r, max(-140, min(100, gB - e)));
+    }
+    if (threadIdx.x == 0) *out_scale = ldexpf(1.f, -(gA + gB));
+}
+
+cudaError_t launch_fp8_scales(const float* amaxA, const float* amaxB, const double* w, const int64_t* ext_dev,
+                              float* sa, float* sb, float* out_scale, cudaStream_t s) {
+    (count_launch(), fp8_scales_kernel<<<1, 1024, 0, s>>>(amaxA, amaxB, w, ext_dev, sa, sb, out_scale));
+    return cudaGetLastError();
 }
 
 }  // namespace bmm

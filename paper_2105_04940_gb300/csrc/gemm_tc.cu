@@ -1,11 +1,13 @@
 // gemm_tc.cu -- the sampled product CD = C D on the sm_103a tensor cores (Alg. 2 step 4, eq. 3.3).
 //
-// out[M x N] (+)= A[M x K] * B[N x K]^T with A, B BF16 and K-major (rows of length K).
+// out[M x N] (+)= scale * A[M x K] * B[N x K]^T with A, B K-major (rows of length K), BF16 or FP8
+// e4m3 (scale = 1 for BF16, a device FP32 factor for FP8, whose operands carry power-of-two scales).
 // Persistent kernel, one CTA per SM, 192 threads:
-//   warp 0   one lane issues TMA loads of 128 x 64 (A) and BN x 64 (B) tiles, 128-byte
-//            swizzled, into a ring of shared-memory stages (mbarrier complete_tx);
-//   warp 1   allocates 2*BN TMEM columns; one lane issues tcgen05.mma (kind::f16, M=128,
-//            N=BN, K=16) into one of two TMEM accumulators and commits stages back;
+//   warp 0   one lane issues TMA loads of 128-row (A) and BN-row (B) tiles of 128 bytes of K
+//            (64 BF16 or 128 e4m3), 128-byte swizzled, into a ring of shared-memory stages;
+//   warp 1   allocates 2*BN TMEM columns; one lane issues tcgen05.mma (kind::f16, K = 16, or
+//            kind::f8f6f4, K = 32; M=128, N=BN) into one of two TMEM accumulators and commits stages
+//            back;
 //   warps 2-5 drain the other accumulator with tcgen05.ld (one TMEM lane quadrant per warp)
 //            and store FP32 rows, overlapping the next tile's MMAs.
 // Every wait is bounded (globaltimer); on expiry the CTA records BMM_ERR_TIMEOUT, lets its
@@ -17,18 +19,24 @@ namespace bmm {
 namespace {
 
 using namespace ptx;
-constexpr int BM = 128, BK = 64;
+constexpr int BM = 128;
+constexpr int ROW_BYTES = 128;  // K per stage: one 128-byte swizzled row
 
-template <int BN> struct Cfg {
+// EK: element kind, 0 = BF16 (kind::f16), 1 = FP8 e4m3 (kind::f8f6f4)
+template <int BN, int EK> struct Cfg {
+    static constexpr int ESIZE = EK ? 1 : 2;
+    static constexpr int BK = ROW_BYTES / ESIZE;       // elements of K per stage
+    static constexpr int KMMA = 32 / ESIZE;            // elements of K per MMA (32 bytes)
     static constexpr int STAGES = (BN == 256) ? 4 : 6;
-    static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int A_BYTES = BM * ROW_BYTES;
+    static constexpr int B_BYTES = BN * ROW_BYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-    // instruction descriptor, kind::f16: D=F32 (bits 4-5), A=B=BF16 (bits 7-9, 10-12),
-    // both K-major, N>>3 at bits 17-22, M>>4 at bits 24-28
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+    // instruction descriptor: D=F32 (bits 4-5); A, B format (bits 7-9, 10-12): BF16 = 1 for
+    // kind::f16, E4M3 = 0 for kind::f8f6f4; both K-major, N>>3 at bits 17-22, M>>4 at bits 24-28
+    static constexpr uint32_t FMT = EK ? 0u : 1u;
+    static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(BM >> 4) << 24);
 };
 
@@ -58,6 +66,7 @@ struct GemmProblem {
     int k_mult;
     int accumulate;
     int vec_ok;
+    const float* scale;  // device factor applied to the product (FP8), or null
 };
 template <int G> struct GemmTable {
     int count;
@@ -65,6 +74,7 @@ template <int G> struct GemmTable {
     GemmProblem prob[G];
 };
 constexpr int kMaxGroup = 80;  // 80 x 384-byte entries keep the table under the 32 KB kernel-parameter limit
+static_assert(sizeof(GemmTable<kMaxGroup>) <= 32764, "GEMM table exceeds the kernel-parameter limit");
 
 template <int G>
 __device__ __forceinline__ int find_problem(const GemmTable<G>& tab, int tile) {
@@ -73,14 +83,17 @@ __device__ __forceinline__ int find_problem(const GemmTable<G>& tab, int tile) {
     return pi;
 }
 
+// K blocks of one product: with a device extent, each of the k_mult segments is padded to BK
+template <int BK>
 __device__ __forceinline__ int problem_kb(const GemmProblem& pr) {
-    const long long K = pr.k_dev ? (long long)pr.k_mult * (((*pr.k_dev) + 63) / 64 * 64) : pr.k_host;
+    const long long K = pr.k_dev ? (long long)pr.k_mult * (((*pr.k_dev) + BK - 1) / BK * BK) : pr.k_host;
     return (int)(K / BK);
 }
 
-template <int BN, int G>
+template <int BN, int G, int EK>
 __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_constant__ GemmTable<G> tab, DevStatus* st) {
-    using C = Cfg<BN>;
+    using C = Cfg<BN, EK>;
+    constexpr int BK = C::BK;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t bar_full[C::STAGES];
     __shared__ __align__(8) uint64_t bar_empty[C::STAGES];
@@ -125,7 +138,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             int tm, tn;
             tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, &tm, &tn);
-            const int num_kb = problem_kb(pr);
+            const int num_kb = problem_kb<BK>(pr);
             for (int kb = 0; kb < num_kb; ++kb) {
                 if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
                     aborted = true;
@@ -155,7 +168,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         bool aborted = false;
         for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
-            const int num_kb = problem_kb(pr);
+            const int num_kb = problem_kb<BK>(pr);
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             if (!mbar_wait(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
@@ -173,8 +186,12 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 const uint64_t ad = sw128_desc(smem_u32(sA + stage * C::A_BYTES));
                 const uint64_t bd = sw128_desc(smem_u32(sB + stage * C::B_BYTES));
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k)
-                    tc_mma_bf16(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                for (int k = 0; k < BK / C::KMMA; ++k) {
+                    if (EK)
+                        tc_mma_f8(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                    else
+                        tc_mma_bf16(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                }
                 tc_commit(smem_u32(&bar_empty[stage]));
                 if (++stage == C::STAGES) {
                     stage = 0;
@@ -194,7 +211,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         int it = 0;
         for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
-            const int num_kb = problem_kb(pr);
+            const int num_kb = problem_kb<BK>(pr);
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             if (!mbar_wait(smem_u32(&bar_tfull[acc]), aph, &s_abort)) break;
@@ -203,6 +220,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
             tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, &tm, &tn);
             const int row = tm * BM + q * 32 + lane;
             const int M = pr.M, N = pr.N;
+            const float sc = pr.scale != nullptr ? *pr.scale : 1.0f;
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
                 uint32_t r[32];
@@ -212,6 +230,10 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 if (num_kb == 0) {
 #pragma unroll
                     for (int e = 0; e < 32; ++e) r[e] = 0u;
+                }
+                if (EK) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) r[e] = __float_as_uint(__uint_as_float(r[e]) * sc);
                 }
                 const int col0 = tn * BN + cc * 32;
                 if (row < M && col0 < N) {
@@ -229,7 +251,9 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                         }
                     } else {
                         const int ne = min(32, N - col0);
-                        for (int e = 0; e < ne; ++e) o[e] = (pr.accumulate ? o[e] : 0.0f) + __uint_as_float(r[e]);
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)  // unrolled: r[] stays in registers
+                            if (e < ne) o[e] = (pr.accumulate ? o[e] : 0.0f) + __uint_as_float(r[e]);
                     }
                 }
             }
@@ -262,14 +286,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kdim, int64_t ld, int box_rows) {
+// esize: bytes per element (2 = BF16, 1 = e4m3 bytes); a box is 128 bytes of K by box_rows rows
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kdim, int64_t ld, int box_rows, int esize) {
     auto fn = encode_fn();
     if (fn == nullptr) return false;
     cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+    cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esize), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+    CUresult r = fn(m, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                    const_cast<void*>(ptr), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -283,10 +309,12 @@ int num_sms() {
 }
 
 // Fill one table entry; returns false when a tensor map cannot be made.
-bool fill_problem(GemmProblem* pr, int BN, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
-                  int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
-                  int64_t ldo, int accumulate) {
-    if (!make_map(&pr->mapA, A, M, kdim, lda, BM) || !make_map(&pr->mapB, B, N, kdim, ldb, BN)) return false;
+bool fill_problem(GemmProblem* pr, int BN, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
+                  int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out, int64_t ldo, int accumulate,
+                  int elem, const float* scale) {
+    const int esize = elem == GEMM_ELEM_E4M3 ? 1 : 2;
+    if (!make_map(&pr->mapA, A, M, kdim, lda, BM, esize) || !make_map(&pr->mapB, B, N, kdim, ldb, BN, esize)) return false;
+    pr->scale = scale;
     pr->out = out;
     pr->ldo = ldo;
     pr->k_dev = reinterpret_cast<const long long*>(k_dev);
@@ -301,26 +329,35 @@ bool fill_problem(GemmProblem* pr, int BN, const __nv_bfloat16* A, int64_t lda, 
     return true;
 }
 
-template <int BN, int G>
+template <int BN, int G, int EK>
 cudaError_t launch_table(const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
-    using C = Cfg<BN>;
+    using C = Cfg<BN, EK>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+            cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, G, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (tab.total_tiles == 0) return cudaSuccess;
     const int grid = (int)imin(tab.total_tiles, num_sms());
-    (count_launch(), gemm_bf16_tc_kernel<BN, G><<<grid, 192, C::SMEM, s>>>(tab, st));
+    (count_launch(), gemm_bf16_tc_kernel<BN, G, EK><<<grid, 192, C::SMEM, s>>>(tab, st));
     return cudaGetLastError();
 }
 
-bool gemm_args_ok(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M, int64_t N,
-                  int64_t kdim, int64_t k_host, const int64_t* k_dev) {
-    if (M > 0x7fffffff || N > 0x7fffffff || (lda % 8) != 0 || (ldb % 8) != 0 || kdim <= 0 || kdim > lda ||
-        kdim > ldb || (k_dev == nullptr && (k_host % 64) != 0))
+template <int G>
+cudaError_t launch_any(int BN, int elem, const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
+    if (elem == GEMM_ELEM_E4M3)
+        return BN == 128 ? launch_table<128, G, 1>(tab, st, s) : launch_table<256, G, 1>(tab, st, s);
+    return BN == 128 ? launch_table<128, G, 0>(tab, st, s) : launch_table<256, G, 0>(tab, st, s);
+}
+
+// strides multiples of 16 bytes, K padded to the 128-byte stage with a host extent
+bool gemm_args_ok(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N, int64_t kdim,
+                  int64_t k_host, const int64_t* k_dev, int elem) {
+    const int64_t per16 = elem == GEMM_ELEM_E4M3 ? 16 : 8, bk = elem == GEMM_ELEM_E4M3 ? 128 : 64;
+    if (M > 0x7fffffff || N > 0x7fffffff || (lda % per16) != 0 || (ldb % per16) != 0 || kdim <= 0 || kdim > lda ||
+        kdim > ldb || (k_dev == nullptr && (k_host % bk) != 0))
         return false;
     return !((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15));
 }
@@ -335,32 +372,34 @@ bool tc_gemm_supported() {
     return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-cudaError_t launch_gemm_bf16_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M,
-                                int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
-                                int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s) {
+cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
+                                int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out, int64_t ldo,
+                                int accumulate, DevStatus* st, cudaStream_t s, int elem, const float* scale) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    if (!gemm_args_ok(A, lda, B, ldb, M, N, kdim, k_host, k_dev)) return cudaErrorInvalidValue;
+    if (!gemm_args_ok(A, lda, B, ldb, M, N, kdim, k_host, k_dev, elem)) return cudaErrorInvalidValue;
     const int BN = N <= 128 ? 128 : 256;
     GemmTable<1> tab;
     tab.count = 1;
-    if (!fill_problem(&tab.prob[0], BN, A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate))
+    if (!fill_problem(&tab.prob[0], BN, A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate, elem,
+                      scale))
         return cudaErrorInvalidValue;
     tab.prob[0].tile_begin = 0;
     tab.total_tiles = tab.prob[0].tiles_m * tab.prob[0].tiles_n;
-    return BN == 128 ? launch_table<128, 1>(tab, st, s) : launch_table<256, 1>(tab, st, s);
+    return launch_any<1>(BN, elem, tab, st, s);
 }
 
 cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, DevStatus* st, cudaStream_t s) {
-    // products are grouped by tile width; each launch takes up to kMaxGroup of them
-    for (int pass = 0; pass < 2; ++pass) {
-        const int BN = pass == 0 ? 128 : 256;
+    // products are grouped by tile width and element kind; each launch takes up to kMaxGroup of them
+    for (int pass = 0; pass < 4; ++pass) {
+        const int BN = (pass & 1) ? 256 : 128;
+        const int elem = pass >> 1;
         static GemmTable<kMaxGroup> tab;  // host-side staging of the kernel parameter (30 KB)
         tab.count = 0;
         tab.total_tiles = 0;
         for (int64_t i = 0; i <= count; ++i) {
             const bool flush = (i == count) || tab.count == kMaxGroup;
             if (flush && tab.count > 0) {
-                cudaError_t e = BN == 128 ? launch_table<128, kMaxGroup>(tab, st, s) : launch_table<256, kMaxGroup>(tab, st, s);
+                cudaError_t e = launch_any<kMaxGroup>(BN, elem, tab, st, s);
                 if (e != cudaSuccess) return e;
                 tab.count = 0;
                 tab.total_tiles = 0;
@@ -368,11 +407,12 @@ cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, Dev
             if (i == count) break;
             const GemmArgs& g = args[i];
             if (g.M <= 0 || g.N <= 0) continue;
-            if ((g.N <= 128 ? 128 : 256) != BN) continue;
-            if (!gemm_args_ok(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev)) return cudaErrorInvalidValue;
+            if ((g.N <= 128 ? 128 : 256) != BN || g.elem != elem) continue;
+            if (!gemm_args_ok(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.elem))
+                return cudaErrorInvalidValue;
             GemmProblem& pr = tab.prob[tab.count];
             if (!fill_problem(&pr, BN, g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out,
-                              g.ldo, g.accumulate))
+                              g.ldo, g.accumulate, g.elem, g.scale))
                 return cudaErrorInvalidValue;
             pr.tile_begin = tab.total_tiles;
             tab.total_tiles += pr.tiles_m * pr.tiles_n;

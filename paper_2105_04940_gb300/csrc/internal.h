@@ -77,29 +77,43 @@ cudaError_t launch_expand_blocks(const int32_t* kidx, const double* kscale, int6
                                  const int64_t* off, int64_t K, int64_t n, int64_t max_nk, int32_t* col, double* w,
                                  int64_t* ext_dev, int64_t* prefix_scratch, DevStatus* st, cudaStream_t s);
 cudaError_t launch_set_extent(int64_t* ext_dev, int64_t value, cudaStream_t s);
-// Operand rows: out[r][j] = cvt(sqrt(w_j) * vec_{col_j}[r]) for r < v.len, j < ext, zero up to the padded extent.
+// Operand rows: out[r][j] = cvt(f_j * vec_{col_j}[r]) for r < v.len, j < ext, zero up to the padded
+// extent (a multiple of 64, of 128 for e4m3), with f_j = sqrt(w_j), or colscale[j] when given.
 // mode: BMM_GEMM_BF16 (bf16), BMM_GEMM_SPLIT_BF16 (bf16 segments; `split_role` 0 = [hi|hi|lo], 1 = [hi|lo|hi]),
-//       BMM_GEMM_F64 (double).  ldo = storage row stride of out in elements.
+//       BMM_GEMM_E4M3 (fp8 e4m3 bytes, saturating), BMM_GEMM_F64 (double).  ldo = storage row stride of
+//       out in elements.
 cudaError_t launch_gather_operand(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
                                   int64_t ext_max, int mode, int split_role, bool apply_weight, void* out,
-                                  int64_t ldo, DevStatus* st, cudaStream_t s);
+                                  int64_t ldo, DevStatus* st, cudaStream_t s, const float* colscale = nullptr);
+// FP8 operand scales.  amax[j] = sqrt(w_j) * max_r |vec_{col_j}[r]| (amax must start at zero);
+// then per drawn index j an exponent e_j balancing the two operands and one exponent per operand,
+// gA and gB, that bring each operand's largest value to at most 448 (the e4m3 maximum):
+// sa[j] = sqrt(w_j) 2^(e_j + gA), sb[j] = sqrt(w_j) 2^(gB - e_j), out_scale = 2^-(gA + gB).
+cudaError_t launch_vec_absmax(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
+                              int64_t ext_max, float* amax, cudaStream_t s);
+cudaError_t launch_fp8_scales(const float* amaxA, const float* amaxB, const double* w, const int64_t* ext_dev,
+                              float* sa, float* sb, float* out_scale, cudaStream_t s);
 
 // ---- gemm_tc.cu / gemm_f64.cu
-// out[M x N] (+)= A[M x K] * B[N x K]^T, A and B K-major bf16 with row strides lda/ldb (elements,
-// multiples of 8).  Columns >= kdim of A and B read as zero.  The K loop runs to
-// k_mult * round_up(*k_dev, 64) if k_dev, else to k_host (a multiple of 64).
-cudaError_t launch_gemm_bf16_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
-                                int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult,
-                                float* out, int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s);
+// Element kinds of the tensor-core GEMM.
+enum GemmElem { GEMM_ELEM_BF16 = 0, GEMM_ELEM_E4M3 = 1 };
+// out[M x N] (+)= scale * A[M x K] * B[N x K]^T, A and B K-major, BF16 or e4m3 bytes, with row strides
+// lda/ldb (elements, 16-byte multiples).  Columns >= kdim of A and B read as zero.  The K loop runs
+// to k_mult * round_up(*k_dev, BK) if k_dev, else to k_host (a multiple of BK); BK = 64 (BF16) or
+// 128 (e4m3).  scale (device, e4m3 only) may be null.
+cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
+                                int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
+                                int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s,
+                                int elem = GEMM_ELEM_BF16, const float* scale = nullptr);
 cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,
                             int64_t k_host, const int64_t* k_dev, double* out, int64_t ldo, int accumulate,
                             cudaStream_t s);
 bool tc_gemm_supported();
 // Many independent products in as few persistent launches as the kernel-parameter limit allows.
 struct GemmArgs {
-    const __nv_bfloat16* A;
+    const void* A;
     int64_t lda;
-    const __nv_bfloat16* B;
+    const void* B;
     int64_t ldb;
     int64_t M, N, kdim, k_host;
     const int64_t* k_dev;
@@ -107,6 +121,8 @@ struct GemmArgs {
     float* out;
     int64_t ldo;
     int accumulate;
+    int elem = GEMM_ELEM_BF16;
+    const float* scale = nullptr;
 };
 cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, DevStatus* st, cudaStream_t s);
 

@@ -25,7 +25,7 @@ from . import _abi as A
 COLUMN_METHODS = ("OPL", "ONC", "ONU", "ONMCNR", "UU")
 BLOCK_METHODS = ("SSM", "WU")
 METHODS = COLUMN_METHODS + BLOCK_METHODS
-MODES = {"f64": A.GEMM_F64, "bf16": A.GEMM_BF16, "split_bf16": A.GEMM_SPLIT_BF16}
+MODES = {"f64": A.GEMM_F64, "bf16": A.GEMM_BF16, "split_bf16": A.GEMM_SPLIT_BF16, "e4m3": A.GEMM_E4M3}
 
 
 def _torch():
@@ -98,7 +98,7 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
     """Upload the offsets, allocate statistics and a workspace large enough for ``gemm_mode``
     (all modes when None) and for draws of ``unit`` up to ``max_draws``."""
     torch = _torch()
-    modes = (A.GEMM_F64, A.GEMM_SPLIT_BF16) if gemm_mode is None else (gemm_mode,)
+    modes = (A.GEMM_F64, A.GEMM_SPLIT_BF16, A.GEMM_E4M3) if gemm_mode is None else (gemm_mode,)
     off = np.asarray(offsets, dtype=np.int64)
     n = int(off[-1])
     max_nk = int(np.diff(off).max())

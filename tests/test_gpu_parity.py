@@ -300,6 +300,64 @@ def test_apply_columns(bmm, mode, shape, layouts):
     assert np.all(np.abs(got - want) <= _tol(mode, L) * bound + 1e-300), np.max(np.abs(got - want) / bound)
 
 
+def _e4m3_bound(M, N, cols, w, L):
+    """Element-wise error bound of the e4m3 sampled product.  Per drawn index j (column c_j of M, row
+    c_j of N, weight w_j): a = M[:, c_j] sqrt(w_j), b = N[c_j, :] sqrt(w_j); the kernel scales a by
+    2^(e_j + gA) and b by 2^(gB - e_j) (e_j balances max|a| and max|b|, gA and gB bring each operand's
+    largest value to at most 448) and rounds to e4m3: |q(x) - x| <= 2^-4 |x| in the normal range, or
+    2^-10 in scaled units below it.  The exponents are recomputed here in FP64; the subnormal terms
+    carry a factor 4 for an exponent one off from the kernel's."""
+    u = 2.0 ** -4
+    sw = np.sqrt(np.asarray(w, dtype=np.float64))
+    Aa = np.abs(M[:, cols]) * sw[None, :]
+    Bb = np.abs(N[cols, :]) * sw[:, None]
+    al, be = Aa.max(axis=0), Bb.max(axis=1)
+    e = np.zeros(len(cols))
+    pos = (al > 0) & (be > 0)
+    e[pos] = np.clip(np.rint(0.5 * np.log2(be[pos] / al[pos])), -60, 60)
+    gA = int(np.floor(np.log2(448.0 / np.max(al * 2.0 ** e)))) if np.any(al > 0) else 0
+    gB = int(np.floor(np.log2(448.0 / np.max(be * 2.0 ** -e)))) if np.any(be > 0) else 0
+    da = 4 * 2.0 ** -10 * 2.0 ** -(e + gA)
+    db = 4 * 2.0 ** -10 * 2.0 ** -(gB - e)
+    AB = Aa @ Bb
+    bound = (2 * u + u * u + 1.2 * L * 2.0 ** -23) * AB
+    bound += (1 + u) * ((da @ Bb)[None, :] + (Aa @ db)[:, None]) + np.sum(da * db)
+    return bound
+
+
+@pytest.mark.parametrize("layouts", [("row", "row"), ("col", "row"), ("row", "col")])
+@pytest.mark.parametrize("shape", [(300, 2000, 520), (70, 1200, 100)])
+def test_apply_columns_e4m3(bmm, shape, layouts):
+    """FP8 e4m3 operands with per-outer-product balancing scales and per-operand powers of two."""
+    m, n, p = shape
+    off, M, N, Mt, Nt = _problem(m, n, p, 25, seed=11, dtype=np.float32, lo=20, hi=140)
+    Mt, Nt = as_layout(Mt, layouts[0]), as_layout(Nt, layouts[1])
+    L = 517
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=bmm._abi.GEMM_E4M3)
+    r = bmm.run(prob, "ONC", L, seed=4, gemm_mode=bmm._abi.GEMM_E4M3)
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]), host(r["scale"])
+    want = oracle.sampled_product_columns(M, N, idx, scale)
+    got = host(r["out"]).astype(np.float64)
+    bound = _e4m3_bound(M, N, idx, scale, L)
+    assert np.all(np.abs(got - want) <= bound + 1e-300), np.max(np.abs(got - want) / bound)
+    assert np.linalg.norm(got - want) <= 0.1 * np.linalg.norm(want)
+
+
+def test_apply_blocks_e4m3(bmm):
+    off, M, N, Mt, Nt = _problem(260, 3000, 300, 50, seed=12, dtype=np.float32, lo=10, hi=110)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=9, unit=bmm._abi.UNIT_BLOCK, gemm_mode=bmm._abi.GEMM_E4M3)
+    r = bmm.run(prob, "SSM", 9, seed=2, gemm_mode=bmm._abi.GEMM_E4M3)
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]), host(r["scale"])
+    want = oracle.sampled_product_blocks(M, N, off, idx, scale)
+    cols = np.concatenate([np.arange(off[k], off[k + 1]) for k in idx])
+    w = np.concatenate([np.full(off[k + 1] - off[k], sc) for k, sc in zip(idx, scale)])
+    got = host(r["out"]).astype(np.float64)
+    bound = _e4m3_bound(M, N, cols, w, len(cols))
+    assert np.all(np.abs(got - want) <= bound + 1e-300), np.max(np.abs(got - want) / bound)
+
+
 @pytest.mark.parametrize("mode", ["f64", "bf16"])
 def test_apply_blocks(bmm, mode):
     off, M, N, Mt, Nt = _problem(260, 3000, 300, 50, seed=12, dtype=np.float32, lo=10, hi=110)
