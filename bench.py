@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--fused-stats", action="store_true", help="statistics and f_k in one pass (OPL, WU)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp", "precision"],
                     help="batched: 512 independent BF16 products of uneven shapes in one CUDA graph; "
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
     ap.add_argument("--products", type=int, default=512, help="products in the batched workload")
@@ -532,6 +532,89 @@ def mlp_arm(args, ws, rank, local):
         print(json.dumps(result))
 
 
+def precision_arm(args, ws, rank, local):
+    """Precision workload: inputs rank-32 (Gaussian factors, scaled by 1/sqrt(32)) plus 1e-3 N(0,1)
+    noise, K = n/64 blocks, c = K/8 blocks (L = n/8 outer products), OPL.  For each sampled-GEMM mode
+    (FP64, BF16, split BF16, FP8 e4m3) the same sample is applied and three numbers are reported:
+    the mode error ||CD_mode - CD|| / ||CD|| against the FP64 product of that sample (at the small
+    shape computed by the CPU oracle; at the large shape by the FP64 mode, itself checked on 16 rows
+    against the oracle), the approximation error ||CD_mode - MN|| / ||MN||, and the milliseconds per
+    product."""
+    import torch
+
+    import oracle
+    import paper_2105_04940_gb300 as P
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.build()
+    A = P._abi
+    g = torch.Generator(device=dev)
+    g.manual_seed(4 + 1000 * rank)
+    rep_out = {}
+    for label, (m, n, p) in (("256x4096x256", (256, 4096, 256)), ("4096x262144x4096", (4096, 262144, 4096))):
+        K = n // 64
+        off = np.arange(0, n + 1, 64, dtype=np.int64)
+        L = P.equal_budget(max(K // 8, 1), n, K)
+
+        def low_rank(r_, c_):
+            F = torch.randn(r_, 32, generator=g, device=dev, dtype=torch.float64)
+            G = torch.randn(32, c_, generator=g, device=dev, dtype=torch.float64)
+            return (F @ G / np.sqrt(32.0) + 1e-3 * torch.randn(r_, c_, generator=g, device=dev, dtype=torch.float64))
+
+        small = m * n <= 1 << 24
+        M64, N64 = low_rank(m, n), low_rank(n, p)
+        exact = (M64 @ N64) if small else (M64.float() @ N64.float()).double()
+        M, N = (M64, N64) if small else (M64.float(), N64.float())
+        del M64, N64
+        prob = P.prepare(M, N, off, max_draws=L)
+        # one sample (OPL) for every mode
+        res = P.run(prob, "OPL", L, seed=7, gemm_mode=A.GEMM_F64 if small else A.GEMM_BF16, compute_product=False)
+        idx, scale = res["idx"], res["scale"]
+        ref = None
+        if small:
+            ref = torch.from_numpy(oracle.sampled_product_columns(M.cpu().numpy(), N.cpu().numpy(), idx.cpu().numpy(),
+                                                                  scale.cpu().numpy())).to(dev)
+        out = {}
+        for mode in ("f64", "bf16", "split_bf16", "e4m3"):
+            gm = P.MODES[mode]
+            o = torch.empty(m, p, device=dev, dtype=torch.float64 if mode == "f64" else torch.float32)
+            fn = lambda: A.bmm_apply(M, N, prob.B, res["unit"], idx, scale, L, gm, o, False, prob.ws)
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            P.check_status(prob)
+            if ref is None and mode == "f64":
+                ref = o.clone()
+                rows = torch.randint(0, m, (16,), generator=torch.Generator().manual_seed(5)).to(dev)
+                il = idx.long()
+                # the oracle on the drawn columns only: C_rows = M[rows][:, idx], D = N[idx, :]
+                chk = oracle.sampled_product_columns(M[rows][:, il].double().cpu().numpy(), N[il].double().cpu().numpy(),
+                                                     np.arange(L), scale.cpu().numpy())
+                rows = rows.cpu().numpy()
+                rows_err = float(np.abs(chk - ref.cpu().numpy()[rows]).max() / np.abs(chk).max())
+                out["f64_vs_oracle_rows"] = rows_err
+            od = o.double()
+            out[mode] = {"mode_err": float(torch.linalg.norm(od - ref) / torch.linalg.norm(ref)),
+                         "approx_err": float(torch.linalg.norm(od - exact) / torch.linalg.norm(exact)),
+                         "ms": e0.elapsed_time(e1) / 3}
+        rep_out[label] = dict(L=L, K=K, **out)
+        del prob, M, N, exact, ref
+        torch.cuda.empty_cache()
+    result = {"metric": "relative Frobenius error of the sampled product per GEMM mode (rank-32 + 1e-3 noise inputs)",
+              "value": rep_out["4096x262144x4096"]["e4m3"]["mode_err"], "unit": "relative error (e4m3, large shape)",
+              "n_gpus": ws, "higher_is_better": False, "data": "synthetic",
+              "config": {"workload": "precision: rank-32 + 1e-3 N(0,1) noise, K=n/64, c=K/8, OPL, one sample for all modes"},
+              "shapes": rep_out}
+    if rank == 0:
+        print(json.dumps(result))
+
+
 def error_and_baselines(P, prob, args, w, c, gm, out, dev):
     import torch
     torch.backends.cuda.matmul.allow_tf32 = False
@@ -652,6 +735,8 @@ def main():
             batched_arm(args, ws, rank, local)
         elif args.workload == "mlp":
             mlp_arm(args, ws, rank, local)
+        elif args.workload == "precision":
+            precision_arm(args, ws, rank, local)
         else:
             native_arm(args, ws, rank, local)
     finally:
