@@ -86,13 +86,36 @@ cudaError_t launch_probs(int kind, const double* x, const double* y, const doubl
 
 // ---------------------------------------------------------------- block sizes (one CTA)
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
-constexpr int kActiveCap = 4096;  // blocks tracked in the shared-memory active lists (K above: no pruning)
+constexpr int kActiveCap = 2048;  // blocks tracked in shared memory (K above: no pruning, FP64 counts)
 
 __device__ __forceinline__ long long count_at(double lam, double g, long long nk) {
     if (!(g > 0.0)) return 1;
     // trunc == floor for lam * g >= 0; the conversion saturates, so +inf and huge values clamp to nk
     long long v = __double2ll_rz(__dmul_rn(lam, g));
     return v < 1 ? 1 : (v > nk ? nk : v);
+}
+
+// count_at(lam, g, nk), decided in FP32 when that is certain.  lamf = RN32(lam), gf = RN32(g): with
+// all three in the normal range, t = RN32(lamf * gf) is within 3 * 2^-24 of lam * g, and the FP64
+// product RN64(lam * g) within 2^-53 of it, so RN64(lam * g) lies in [t - 4e-7 t, t + 4e-7 t].
+// When that interval holds one integer floor (or lies below 1, or at or above nk), the FP64 count
+// is known without an FP64 instruction (GB300's FP64 pipe is ~1/64 of FP32); otherwise it is
+// computed exactly.  The result is always count_at's.
+__device__ __forceinline__ long long count_fast(double lam, float lamf, float gf, int nk, double g) {
+    const float t = __fmul_rn(lamf, gf);
+    if (lamf >= 1.17549435e-38f && gf >= 1.17549435e-38f && t >= 1.17549435e-38f && t <= 1.0e30f) {
+        const float mg = __fmul_rn(t, 4.0e-7f);
+        const float th = __fadd_rn(t, mg);
+        if (th < 1.0f) return 1;
+        const float tl = __fsub_rn(t, mg);
+        if (nk < (1 << 24) && tl >= (float)nk) return nk;
+        const float fl = floorf(tl);
+        if (fl == floorf(th)) {
+            const long long v = (long long)fl;
+            return v < 1 ? 1 : (v > nk ? nk : v);
+        }
+    }
+    return count_at(lam, g, nk);
 }
 
 __device__ __forceinline__ double bits_to_lam(unsigned long long u) { return __longlong_as_double((long long)u); }
@@ -149,6 +172,8 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
     __shared__ unsigned long long sLoHi[2];
     __shared__ long long sScan[33];
     __shared__ int sAct[2][kActiveCap];
+    __shared__ float sGf[kActiveCap];  // RN32(g_k), for count_fast
+    __shared__ int sNk[kActiveCap];
     __shared__ int sNact[2];
     __shared__ double sRed[33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -217,14 +242,21 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
         // active list: blocks whose count may still change inside (lo, hi)
         const bool track = K <= kActiveCap;
         if (tid == 0) { sNact[0] = 0; sLoHi[0] = lo; sLoHi[1] = hi; }
+        if (track)
+            for (int64_t k = tid; k < K; k += 1024) {
+                sGf[k] = __double2float_rn(g[k]);
+                sNk[k] = (int)(off[k + 1] - off[k]);
+            }
         __syncthreads();
         int cur = 0;
         long long base = 0;
         if (track) {
             long long mine = 0;
+            const double llo = bits_to_lam(lo), lhi = bits_to_lam(hi);
+            const float flo = __double2float_rn(llo), fhi = __double2float_rn(lhi);
             for (int64_t k = tid; k < K; k += 1024) {
-                const long long nk = off[k + 1] - off[k];
-                const long long clo = count_at(bits_to_lam(lo), g[k], nk), chi = count_at(bits_to_lam(hi), g[k], nk);
+                const int nk = sNk[k];
+                const long long clo = count_fast(llo, flo, sGf[k], nk, g[k]), chi = count_fast(lhi, fhi, sGf[k], nk, g[k]);
                 if (clo == chi) mine += clo;
                 else sAct[0][atomicAdd(&sNact[0], 1)] = (int)k;
             }
@@ -237,11 +269,12 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
                 const unsigned long long w = (unsigned long long)warp;
                 const unsigned long long u = lo + (d >> 5) * w + (((d & 31ull) * w) >> 5);
                 const double lam = bits_to_lam(u);
+                const float lamf = __double2float_rn(lam);
                 long long acc = 0;
                 if (track) {
                     for (int i = lane; i < nact; i += 32) {
                         const int k = sAct[cur][i];
-                        acc += count_at(lam, g[k], off[k + 1] - off[k]);
+                        acc += count_fast(lam, lamf, sGf[k], sNk[k], g[k]);
                     }
                 } else {
                     for (int64_t k = lane; k < K; k += 32) acc += count_at(lam, g[k], off[k + 1] - off[k]);
@@ -270,11 +303,13 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
             hi = sLoHi[1];
             if (track) {  // drop the blocks whose count is now constant on [lo, hi]
                 long long mine = 0;
+                const double llo = bits_to_lam(lo), lhi = bits_to_lam(hi);
+                const float flo = __double2float_rn(llo), fhi = __double2float_rn(lhi);
                 for (int i = tid; i < nact; i += 1024) {
                     const int k = sAct[cur][i];
-                    const long long nk = off[k + 1] - off[k];
-                    const long long clo = count_at(bits_to_lam(lo), g[k], nk);
-                    const long long chi = count_at(bits_to_lam(hi), g[k], nk);
+                    const int nk = sNk[k];
+                    const long long clo = count_fast(llo, flo, sGf[k], nk, g[k]);
+                    const long long chi = count_fast(lhi, fhi, sGf[k], nk, g[k]);
                     if (clo == chi) mine += clo;
                     else sAct[cur ^ 1][atomicAdd(&sNact[cur ^ 1], 1)] = k;
                 }

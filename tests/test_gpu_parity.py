@@ -201,10 +201,12 @@ def test_fused_statistics_offsets_wide_and_low_rank_blocks(bmm, layouts, dtype):
 
 # ---------------------------------------------------------------- block sizes (identical inputs)
 @pytest.mark.parametrize("kind", ["opt", "hat", "equal"])
-def test_blocksizes_bit_exact(bmm, kind):
+@pytest.mark.parametrize("K", [300, 3000])
+def test_blocksizes_bit_exact(bmm, kind, K):
+    """Bit-exact against the oracle given the same FP64 inputs; K = 300 keeps every block in the
+    kernel's shared-memory lists (FP32-decided counts with FP64 fallback), K = 3000 does not."""
     rng = np.random.default_rng(9)
-    K = 300
-    nk = rng.integers(1, 200, size=K)
+    nk = rng.integers(1, 200 if K <= 300 else 40, size=K)
     off = np.concatenate([[0], np.cumsum(nk)]).astype(np.int64)
     n = int(off[-1])
     a = rng.lognormal(0, 2, size=K)
