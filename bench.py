@@ -61,6 +61,7 @@ def parse():
                     help="batched: 512 independent BF16 products of uneven shapes in one CUDA graph; "
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
     ap.add_argument("--products", type=int, default=512, help="products in the batched workload")
+    ap.add_argument("--streams", type=int, default=16, help="side streams of the batched workload")
     return ap.parse_args()
 
 
@@ -399,10 +400,11 @@ def batched_arm(args, ws, rank, local):
         in_bytes += 2 * (m * n + n * p)
         flops += 2.0 * m * p * L
     seeds = [11 + i for i in range(len(probs))]
-    streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(args.streams)]
 
     def batch():
-        return P.run_batched(probs, "OPL", cs, seeds, gemm_mode=P._abi.GEMM_BF16, outs=outs, streams=streams)
+        return P.run_batched(probs, "OPL", cs, seeds, gemm_mode=P._abi.GEMM_BF16, outs=outs, streams=streams,
+                             fused_stats=args.fused_stats)
 
     for _ in range(args.warmup):
         batch()
@@ -446,7 +448,8 @@ def batched_arm(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"batched: {len(probs)} BF16 products, m,p U{{128..2048/128}}, n U{{4096..65536/4096}}, "
-                               "K=n/64 blocks of 32..128, c=K/8, OPL, one CUDA graph per batch",
+                               "K=n/64 blocks of 32..128, c=K/8, OPL, one CUDA graph per batch", "streams": args.streams,
+                   "statistics": "fused, grouped" if args.fused_stats else "norm pass per product, Gram pass grouped",
                    "products": len(probs), "input_gb": in_bytes / 1e9, "gemm_tflop": flops / 1e12,
                    "l2": "inputs larger than the 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "batch_ms": batch_ms, "eager_batch_ms": eager_ms,

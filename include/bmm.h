@@ -159,6 +159,21 @@ bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
                      void* ws, size_t ws_bytes, bmm_stream_t stream);
 
 /*
+ * bmm_probs_batched -- bmm_probs for `count` independent products (arrays of descriptors, one
+ * workspace per product), in as few launches as the kernel-parameter limit allows.  For each i
+ * the results are those of bmm_probs(&Ms[i], &Ns[i], &Bs[i], pkind, fmode, p_outs ? p_outs[i] :
+ * NULL, &sts[i], ws[i], ws_bytes[i], stream).  Products that the tensor-core pass supports
+ * (fmode BMM_F_TC, FP32 or BF16 inputs with 16-byte aligned leading dimensions, n_k <= 128) share
+ * launches of up to ~19 products whose CTAs draw blocks from one work counter (in ws of the first
+ * such product); the others are computed one by one.  All work is on `stream`; nothing is
+ * synchronised or allocated, so the call can be recorded in a CUDA graph.  Errors: as bmm_probs,
+ * the first failing product's status is returned and later products are not started.
+ */
+bmm_status bmm_probs_batched(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns, const bmm_blocks* Bs,
+                             int32_t pkind, int32_t fmode, double* const* p_outs, const bmm_stats* sts,
+                             void* const* ws, const size_t* ws_bytes, bmm_stream_t stream);
+
+/*
  * bmm_probs_static -- bmm_probs without a workspace.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory at call time, such as a plugin whose
  * host program owns all GPU memory through a fixed pool, or a latency-critical loop that cannot

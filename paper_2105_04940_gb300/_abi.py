@@ -27,7 +27,7 @@ PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
 EXPORTED = (
     "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
     "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
-    "bmm_probs_static", "bmm_apply_batched",
+    "bmm_probs_static", "bmm_apply_batched", "bmm_probs_batched",
 )
 
 
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH):
     lib.bmm_apply_batched.argtypes = [i64, P(Mat), P(Mat), P(Blocks), i32, P(vp), P(vp), P(i64), i32, P(Mat), i32,
                                       P(vp), P(sz), vp]
     lib.bmm_apply_batched.restype = i32
+    lib.bmm_probs_batched.argtypes = [i64, P(Mat), P(Mat), P(Blocks), i32, i32, P(vp), P(Stats), P(vp), P(sz), vp]
+    lib.bmm_probs_batched.restype = i32
     lib.bmm_launch_count.argtypes = []
     lib.bmm_launch_count.restype = ctypes.c_uint64
     for name in ("bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
@@ -158,6 +160,17 @@ def bmm_probs(M, N, B: Blocks, pkind: int, fmode: int, p_out, st: dict, ws, stre
     sp = ctypes.byref(stats(st)) if st is not None else None
     _check(load().bmm_probs(Mm, Nm, ctypes.byref(B), pkind, fmode, _ptr(p_out), sp, ws.data_ptr(), ws.numel(),
                             _stream(stream)), "bmm_probs")
+
+
+def bmm_probs_batched(Ms, Ns, Bs, pkind: int, fmode: int, p_outs, sts, wss, stream=None):
+    """bmm_probs over many independent products (lists of equal length; p_outs entries may be None)."""
+    n = len(Ms)
+    MatA, BlkA, VpA = Mat * n, Blocks * n, ctypes.c_void_p * n
+    pp = VpA(*[_ptr(p) for p in p_outs]) if p_outs is not None else None
+    _check(load().bmm_probs_batched(
+        n, MatA(*[mat(m) for m in Ms]), MatA(*[mat(x) for x in Ns]), BlkA(*Bs), pkind, fmode, pp,
+        (Stats * n)(*[stats(st) for st in sts]), VpA(*[w.data_ptr() for w in wss]),
+        (ctypes.c_size_t * n)(*[w.numel() for w in wss]), _stream(stream)), "bmm_probs_batched")
 
 
 def bmm_blocksizes(M, N, B: Blocks, st: dict, ckind: int, c: int, pilot_idx, pilot_scale, pilot_per_block: int,

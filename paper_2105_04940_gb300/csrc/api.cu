@@ -347,6 +347,59 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
     return BMM_OK;
 }
 
+BMM_API bmm_status bmm_probs_batched(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns, const bmm_blocks* Bs,
+                                     int32_t pkind, int32_t fmode, double* const* p_outs, const bmm_stats* sts,
+                                     void* const* ws, const size_t* ws_bytes, bmm_stream_t stream) {
+    if (count < 0 || (count > 0 && (Ms == nullptr || Ns == nullptr || Bs == nullptr || sts == nullptr || ws == nullptr ||
+                                    ws_bytes == nullptr)))
+        return BMM_ERR_ARG;
+    const bool reuse = (fmode & BMM_REUSE_STATS) != 0;
+    const int32_t fbase = fmode & ~BMM_REUSE_STATS;
+    if (pkind < BMM_P_COL_OPT || pkind > BMM_P_BLK_NORMPROD) return BMM_ERR_ARG;
+    if (fbase != BMM_F_NONE && fbase != BMM_F_EXACT && fbase != BMM_F_TC) return BMM_ERR_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<StatsArgs> grouped;
+    std::vector<int64_t> which;
+    int* counter = nullptr;
+    for (int64_t i = 0; i < count; ++i) {
+        const bmm_mat* M = &Ms[i];
+        const bmm_mat* N = &Ns[i];
+        const bmm_blocks* B = &Bs[i];
+        const bmm_stats* st = &sts[i];
+        double* p_out = p_outs ? p_outs[i] : nullptr;
+        bool eligible = fbase == BMM_F_TC && pkind != BMM_P_COL_UNIFORM && check_problem(M, N, B) == BMM_OK &&
+                        st->x && st->y && st->a && st->s && st->mf && st->nf && st->f;
+        if (eligible) eligible = blockstats_tc_supported(vecset_of_M(M), vecset_of_N(N), B->max_nk);
+        if (!eligible) {  // the product on its own, with bmm_probs's rules
+            bmm_status s = bmm_probs(M, N, B, pkind, fmode, p_out, st, ws[i], ws_bytes[i], stream);
+            if (s != BMM_OK) return s;
+            continue;
+        }
+        Carver cnt{nullptr};
+        ProbsPlan plan;
+        plan_probs(cnt, M, N, B, true, &plan);
+        bmm_status s = check_ws(ws[i], ws_bytes[i], cnt.off);
+        if (s != BMM_OK) return s;
+        Carver cv{static_cast<char*>(ws[i]) + kStatusBytes};
+        plan_probs(cv, M, N, B, true, &plan);
+        if (counter == nullptr) counter = plan.counter;
+        grouped.push_back(StatsArgs{vecset_of_M(M), vecset_of_N(N), B->offsets, B->K, B->n, st->x, st->y, st->a, st->s,
+                                    st->mf, st->nf, st->f, status_of(ws[i])});
+        which.push_back(i);
+    }
+    if (!grouped.empty())
+        BMM_TRY(launch_blockstats_tc_grouped(grouped.data(), (int64_t)grouped.size(), !reuse, counter, cs));
+    for (size_t u = 0; u < which.size(); ++u) {
+        const int64_t i = which[u];
+        double* p_out = p_outs ? p_outs[i] : nullptr;
+        if (p_out == nullptr) continue;
+        const bmm_stats* st = &sts[i];
+        BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, Bs[i].offsets, Bs[i].K, Bs[i].n, p_out,
+                             status_of(ws[i]), cs));
+    }
+    return BMM_OK;
+}
+
 BMM_API bmm_status bmm_blocksizes(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, const bmm_stats* st,
                                   int32_t ckind, int64_t c, const int32_t* pilot_idx, const double* pilot_scale,
                                   int64_t pilot_per_block, int64_t* ck_out, double* g_out, double* fhat_out, void* ws,

@@ -6,7 +6,9 @@
 // off-diagonal part sum_{i != j} G_M[i,j] G_N[i,j] comes from tensor-core Grams in TMEM: TF32 for
 // FP32 inputs, BF16 (exact products) for BF16 inputs, FP32 accumulation.
 //
-// One CTA per SM pulls blocks from a global counter.  For block k it streams the vectors of the
+// One CTA per SM pulls blocks from a global counter that runs over the blocks of every product of
+// the launch (a table of products in the kernel parameters: one product for bmm_probs, up to
+// kMaxProducts of them for bmm_probs_batched).  For block k it streams the vectors of the
 // block -- columns of M (length m), then rows of N (length p) -- in sub-tiles of E coordinates
 // (E = 128 bytes / element size: 32 FP32 or 64 BF16), several sub-tiles (up to 40 KB) per stage:
 //   warp 0      one lane: TMA loads into a 5-stage ring of 40 KB and a record per stage and per
@@ -137,10 +139,11 @@ struct __align__(16) StageInfo {
 
 struct __align__(16) BlockInfo {
     long long lo;  // first column
-    int k;         // block index, -1: no more work
+    long long k;   // block index within its product, -1: no more work
+    int q;         // product
     int nk;
     int dpos;
-    int pad[3];
+    int pad;
 };
 
 // Tensor maps of one operand: strided storage uses map[0] (E x 64 boxes); contiguous storage
@@ -148,6 +151,25 @@ struct __align__(16) BlockInfo {
 struct OperandMaps {
     CUtensorMap map[kMaxKMaps];
 };
+
+// One product of a launch.  Outputs x, y [n] and a, s, mf, nf [K] are written in the statistics
+// pass (STATS) and read (s) in the Gram-only pass; f [K] is written by both.
+struct __align__(64) StatsProblem {
+    OperandMaps mM, mN;
+    const int64_t* off;
+    long long K, n, m, p;
+    long long block_begin;  // first block of this product in the launch's block numbering
+    double *x, *y, *a, *s, *mf, *nf, *f;
+    DevStatus* st;
+    int M_strided, N_strided;
+};
+template <int G> struct StatsTable {
+    int count;
+    long long total_blocks;
+    StatsProblem prob[G];
+};
+constexpr int kMaxProducts = (32760 - 64) / (int)sizeof(StatsProblem);  // kernel-parameter limit
+static_assert(sizeof(StatsTable<kMaxProducts>) <= 32764, "statistics table exceeds the kernel-parameter limit");
 
 template <typename T>
 __device__ __forceinline__ uint32_t idesc_of(int npad, bool mn_major) {
@@ -205,13 +227,9 @@ __device__ __forceinline__ bool conv_sync(uint32_t bar, int& uses, volatile int*
     return ok;
 }
 
-template <typename T, bool STATS>
+template <typename T, bool STATS, int G>
 __global__ void __launch_bounds__(kThreads, 1)
-    blockstats_tc_kernel(const __grid_constant__ OperandMaps tmM, const __grid_constant__ OperandMaps tmN,
-                         int M_strided, int N_strided, long long m, long long p, const int64_t* __restrict__ off,
-                         long long K, long long n, int* __restrict__ counter, double* __restrict__ x,
-                         double* __restrict__ y, double* __restrict__ a, double* __restrict__ ssum,
-                         double* __restrict__ mf, double* __restrict__ nf, double* __restrict__ f, DevStatus* st) {
+    blockstats_tc_kernel(const __grid_constant__ StatsTable<G> tab, int* __restrict__ counter) {
     using TR = Tr<T>;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
@@ -221,9 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ BlockInfo binfo[kBlockSlots];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
-    __shared__ double part[STATS ? kConvWarps : 1][kMaxBlock];  // [warp][vector], one phase at a time
+    __shared__ float2 part[STATS ? kConvWarps : 1][kMaxBlock];   // [warp][vector] float-float, one phase
     __shared__ double xy_sum[STATS ? 2 : 1][kMaxBlock];           // [phase][vector]: x_i, y_i
-    __shared__ double red[kConvWarps][5];
+    __shared__ double red[4][4];                                  // statistics sums of the 4 vector warps
+    __shared__ float2 red_off[kConvWarps];                        // off-diagonal sums, float-float
 
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     auto stage_ptr = [&](int s) { return base + s * kStageBytes; };
@@ -260,13 +279,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------ producer
-            int stage = 0, bslot = 0;
+            int stage = 0, bslot = 0, q = 0;
             uint32_t ph = 0, bph = 0;
             uint32_t issued_mask = 0, issued_phase = 0;
             bool aborted = false;
             while (!aborted) {
-                const long long k = atomicAdd(counter, 1);
-                if (k >= K) {
+                const long long kg = atomicAdd(counter, 1);
+                if (kg >= tab.total_blocks) {
                     if (!wait_fast(smem_u32(&bar_bempty[bslot]), bph ^ 1u, &s_abort)) { aborted = true; break; }
                     binfo[bslot].k = -1;
                     mbar_arrive(smem_u32(&bar_bfull[bslot]));
@@ -275,27 +294,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive(smem_u32(&bar_full[stage]));
                     break;
                 }
-                const long long lo = off[k], hi = off[k + 1];
+                // blocks are claimed in increasing order, so this CTA's product index only grows
+                while (q + 1 < tab.count && kg >= tab.prob[q + 1].block_begin) ++q;
+                const StatsProblem& pr = tab.prob[q];
+                const long long k = kg - pr.block_begin;
+                const long long lo = pr.off[k], hi = pr.off[k + 1];
                 const long long nk = hi - lo;
-                if (lo < 0 || hi > n || nk <= 0 || nk > kMaxBlock) {
-                    set_status(st, BMM_ERR_SHAPE, (int)k);
-                    if (STATS) { a[k] = 0.0; ssum[k] = 0.0; mf[k] = 0.0; nf[k] = 0.0; }
-                    f[k] = 0.0;
+                if (lo < 0 || hi > pr.n || nk <= 0 || nk > kMaxBlock) {
+                    set_status(pr.st, BMM_ERR_SHAPE, (int)k);
+                    if (STATS) { pr.a[k] = 0.0; pr.s[k] = 0.0; pr.mf[k] = 0.0; pr.nf[k] = 0.0; }
+                    pr.f[k] = 0.0;
                     continue;
                 }
+                const int M_strided = pr.M_strided, N_strided = pr.N_strided;
                 const int dlo = (int)(lo & (TR::kAlign - 1));
                 const int dpos = (M_strided || N_strided) ? dlo : 0;
                 const bool wide = dpos + nk > 128;
                 if (!wait_fast(smem_u32(&bar_bempty[bslot]), bph ^ 1u, &s_abort)) { aborted = true; break; }
                 binfo[bslot].lo = lo;
-                binfo[bslot].k = (int)k;
+                binfo[bslot].k = k;
+                binfo[bslot].q = q;
                 binfo[bslot].nk = (int)nk;
                 binfo[bslot].dpos = dpos;
                 mbar_arrive(smem_u32(&bar_bfull[bslot]));
                 if (++bslot == kBlockSlots) { bslot = 0; bph ^= 1u; }
                 for (int phase = 0; phase < 2 && !aborted; ++phase) {
                     const int strided = phase == 0 ? M_strided : N_strided;
-                    const long long len = phase == 0 ? m : p;
+                    const long long len = phase == 0 ? pr.m : pr.p;
                     const int d = strided ? dlo : dpos;
                     // strided: boxes of E columns; contiguous: groups of 32 vector rows (a wide
                     // BF16 block takes 6 so that the corner's rows 64..191 are loaded)
@@ -303,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!strided && wide && TR::kCornerRow0 + 128 > 32 * nb) nb = (TR::kCornerRow0 + 128) / 32;
                     const int per = strided ? TR::kMnPer : subtiles_per_stage(nb);
                     const long long nsub_total = (len + TR::E - 1) / TR::E;
-                    const OperandMaps& maps = phase == 0 ? tmM : tmN;
+                    const OperandMaps& maps = phase == 0 ? pr.mM : pr.mN;
                     const CUtensorMap* map = &maps.map[strided ? 0 : nb - 1];
                     for (long long c0 = 0; c0 < nsub_total; c0 += per) {
                         const int nsub = (int)imin(per, nsub_total - c0);
@@ -487,20 +512,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (mn_phase) {
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) part[STATS ? cw : 0][lane + 32 * v] = tot[v].value();
+                        for (int v = 0; v < 4; ++v) part[STATS ? cw : 0][lane + 32 * v] = make_float2(tot[v].hi, tot[v].lo);
                     } else {
-                        part[STATS ? cw : 0][lane + 32 * (cw & 1)] = tot[0].value();
-                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) + 2)] = tot[1].value();
-                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) ^ 1)] = 0.0;
-                        part[STATS ? cw : 0][lane + 32 * (((cw & 1) ^ 1) + 2)] = 0.0;
+                        part[STATS ? cw : 0][lane + 32 * (cw & 1)] = make_float2(tot[0].hi, tot[0].lo);
+                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) + 2)] = make_float2(tot[1].hi, tot[1].lo);
+                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) ^ 1)] = make_float2(0.f, 0.f);
+                        part[STATS ? cw : 0][lane + 32 * (((cw & 1) ^ 1) + 2)] = make_float2(0.f, 0.f);
                     }
-                    // x_i (phase 0) or y_i (phase 1): the sum over the warps' shares
+                    // x_i (phase 0) or y_i (phase 1): the float-float sum of the warps' shares, one
+                    // FP64 conversion per vector
                     conv_sync(cs_bar, cs_uses, &s_abort);
                     if (t < kMaxBlock) {
-                        double sum = 0.0;
+                        FF sum;
+                        sum.zero();
 #pragma unroll
-                        for (int w = 0; w < kConvWarps; ++w) sum += part[STATS ? w : 0][t];
-                        xy_sum[STATS ? phase : 0][t] = sum;
+                        for (int w = 0; w < kConvWarps; ++w) {
+                            const float2 v2 = part[STATS ? w : 0][t];
+                            FF o;
+                            o.hi = v2.x;
+                            o.lo = v2.y;
+                            sum.add(o);
+                            sum.renorm();
+                        }
+                        xy_sum[STATS ? phase : 0][t] = sum.value();
                     }
                     conv_sync(cs_bar, cs_uses, &s_abort);  // part[] is reused by the next phase
                 }
@@ -510,12 +544,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---- block epilogue
             const long long k = bi.k;
             const long long lo = bi.lo;
+            const StatsProblem& pr = tab.prob[bi.q];
             double sa = 0.0, ss = 0.0, sx = 0.0, sy = 0.0;
             if (STATS) {
                 if (t < nk) {
                     const double xi = xy_sum[0][t], yi = xy_sum[STATS ? 1 : 0][t];
-                    x[lo + t] = xi;
-                    y[lo + t] = yi;
+                    pr.x[lo + t] = xi;
+                    pr.y[lo + t] = yi;
                     const double xy = __dmul_rn(xi, yi);
                     sa = sqrt(xy);
                     ss = xy;
@@ -572,23 +607,43 @@ __global__ void __launch_bounds__(kThreads, 1)
                 aborted = true;
             }
             ++it;
-            double offd = offf.value();
-            sa = warp_sum(sa);
-            ss = warp_sum(ss);
-            sx = warp_sum(sx);
-            sy = warp_sum(sy);
-            offd = warp_sum(offd);
-            if (lane == 0) {
-                red[cw][0] = sa; red[cw][1] = ss; red[cw][2] = sx; red[cw][3] = sy; red[cw][4] = offd;
+            // reductions: the off-diagonal sum as float-float (FP32 operations; the FP64 pipe is
+            // slow on this part), the statistics in FP64 over the 4 warps that own vectors only
+            offf.renorm();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                FF other;
+                other.hi = __shfl_xor_sync(0xffffffffu, offf.hi, o);
+                other.lo = __shfl_xor_sync(0xffffffffu, offf.lo, o);
+                offf.add(other);
+                offf.renorm();
+            }
+            if (lane == 0) red_off[cw] = make_float2(offf.hi, offf.lo);
+            if (STATS && cw < 4) {
+                sa = warp_sum(sa);
+                ss = warp_sum(ss);
+                sx = warp_sum(sx);
+                sy = warp_sum(sy);
+                if (lane == 0) { red[cw][0] = sa; red[cw][1] = ss; red[cw][2] = sx; red[cw][3] = sy; }
             }
             conv_sync(cs_bar, cs_uses, &s_abort);
             if (t == 0) {
-                double r5[5] = {0, 0, 0, 0, 0};
-                for (int w = 0; w < kConvWarps; ++w)
-                    for (int q = 0; q < 5; ++q) r5[q] += red[w][q];
-                const double sk = STATS ? r5[1] : ssum[k];
-                if (STATS) { a[k] = r5[0]; ssum[k] = r5[1]; mf[k] = r5[2]; nf[k] = r5[3]; }
-                f[k] = sk + r5[4];
+                FF off_sum;
+                off_sum.zero();
+                for (int w = 0; w < kConvWarps; ++w) {
+                    FF o;
+                    o.hi = red_off[w].x;
+                    o.lo = red_off[w].y;
+                    off_sum.add(o);
+                    off_sum.renorm();
+                }
+                double r4[4] = {0, 0, 0, 0};
+                if (STATS)
+                    for (int w = 0; w < 4; ++w)
+                        for (int c = 0; c < 4; ++c) r4[c] += red[w][c];
+                const double sk = STATS ? r4[1] : pr.s[k];
+                if (STATS) { pr.a[k] = r4[0]; pr.s[k] = r4[1]; pr.mf[k] = r4[2]; pr.nf[k] = r4[3]; }
+                pr.f[k] = sk + off_sum.value();
             }
             conv_sync(cs_bar, cs_uses, &s_abort);  // xy_sum[] and red[] are reused by the next block
             if (lane == 0) mbar_arrive(smem_u32(&bar_bempty[bslot]));
@@ -603,7 +658,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
     }
-    if (threadIdx.x == 0 && s_abort) set_status(st, BMM_ERR_TIMEOUT, 2);
+    if (threadIdx.x == 0 && s_abort)
+        for (int q = 0; q < tab.count; ++q) set_status(tab.prob[q].st, BMM_ERR_TIMEOUT, 2);
 }
 
 // Strided operands (vectors along the storage rows' inner dimension) feed the MMA MN-major: FP32
@@ -638,28 +694,68 @@ bool maps_of(OperandMaps& om, const VecSet& v) {
     return true;
 }
 
-template <typename T, bool STATS>
-cudaError_t launch_t(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n, int* counter,
-                     double* x, double* y, double* a, double* ssum, double* mf, double* nf, double* f, DevStatus* st,
-                     cudaStream_t s) {
-    OperandMaps mM, mN;
-    if (!maps_of<T>(mM, vM) || !maps_of<T>(mN, vN)) return cudaErrorInvalidValue;
+template <typename T>
+bool fill_problem(StatsProblem* pr, const StatsArgs& g) {
+    if (!maps_of<T>(pr->mM, g.vM) || !maps_of<T>(pr->mN, g.vN)) return false;
+    pr->off = g.off;
+    pr->K = g.K;
+    pr->n = g.n;
+    pr->m = g.vM.len;
+    pr->p = g.vN.len;
+    pr->x = g.x; pr->y = g.y; pr->a = g.a; pr->s = g.s; pr->mf = g.mf; pr->nf = g.nf; pr->f = g.f;
+    pr->st = g.st;
+    pr->M_strided = g.vM.mode == VEC_STRIDED;
+    pr->N_strided = g.vN.mode == VEC_STRIDED;
+    return true;
+}
+
+template <typename T, bool STATS, int G>
+cudaError_t launch_table(const StatsTable<G>& tab, int* counter, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(blockstats_tc_kernel<T, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        cudaError_t e = cudaFuncSetAttribute(blockstats_tc_kernel<T, STATS, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    if (tab.total_blocks == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)imin(K, sms);
-    (count_launch(), blockstats_tc_kernel<T, STATS><<<grid, kThreads, kSmem, s>>>(
-        mM, mN, vM.mode == VEC_STRIDED, vN.mode == VEC_STRIDED, vM.len, vN.len, off, K, n, counter, x, y, a, ssum, mf,
-        nf, f, st));
+    const int grid = (int)imin(tab.total_blocks, sms);
+    (count_launch(), blockstats_tc_kernel<T, STATS, G><<<grid, kThreads, kSmem, s>>>(tab, counter));
     return cudaGetLastError();
+}
+
+template <typename T, bool STATS>
+cudaError_t launch_grouped_t(const StatsArgs* args, int64_t count, int* counter, cudaStream_t s) {
+    if (count == 1) {  // a single product: a one-entry table keeps the kernel parameter small
+        StatsTable<1> one;
+        one.count = 1;
+        if (!fill_problem<T>(&one.prob[0], args[0])) return cudaErrorInvalidValue;
+        one.prob[0].block_begin = 0;
+        one.total_blocks = args[0].K;
+        return launch_table<T, STATS, 1>(one, counter, s);
+    }
+    static StatsTable<kMaxProducts> tab;  // host-side staging of the kernel parameter (~32 KB)
+    tab.count = 0;
+    tab.total_blocks = 0;
+    for (int64_t i = 0; i <= count; ++i) {
+        if ((i == count || tab.count == kMaxProducts) && tab.count > 0) {
+            cudaError_t e = launch_table<T, STATS, kMaxProducts>(tab, counter, s);
+            if (e != cudaSuccess) return e;
+            tab.count = 0;
+            tab.total_blocks = 0;
+        }
+        if (i == count) break;
+        StatsProblem& pr = tab.prob[tab.count];
+        if (!fill_problem<T>(&pr, args[i])) return cudaErrorInvalidValue;
+        pr.block_begin = tab.total_blocks;
+        tab.total_blocks += args[i].K;
+        ++tab.count;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -677,11 +773,32 @@ bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk)
 cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n,
                                  bool stats, int* counter, double* x, double* y, double* a, double* ssum, double* mf,
                                  double* nf, double* f, DevStatus* st, cudaStream_t s) {
-    if (vM.dtype == BMM_F32)
-        return stats ? launch_t<float, true>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s)
-                     : launch_t<float, false>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s);
-    return stats ? launch_t<__nv_bfloat16, true>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s)
-                 : launch_t<__nv_bfloat16, false>(vM, vN, off, K, n, counter, x, y, a, ssum, mf, nf, f, st, s);
+    const StatsArgs g{vM, vN, off, K, n, x, y, a, ssum, mf, nf, f, st};
+    return launch_blockstats_tc_grouped(&g, 1, stats, counter, s);
+}
+
+cudaError_t launch_blockstats_tc_grouped(const StatsArgs* args, int64_t count, bool stats, int* counter, cudaStream_t s) {
+    // one launch per element type and kMaxProducts products
+    for (int pass = 0; pass < 2; ++pass) {
+        const int dtype = pass == 0 ? BMM_F32 : BMM_BF16;
+        int64_t i = 0;
+        while (i < count) {
+            // a run of consecutive products of this element type (others are skipped here)
+            if (args[i].vM.dtype != dtype) { ++i; continue; }
+            int64_t j = i;
+            while (j < count && args[j].vM.dtype == dtype) ++j;
+            cudaError_t e;
+            if (dtype == BMM_F32)
+                e = stats ? launch_grouped_t<float, true>(args + i, j - i, counter, s)
+                          : launch_grouped_t<float, false>(args + i, j - i, counter, s);
+            else
+                e = stats ? launch_grouped_t<__nv_bfloat16, true>(args + i, j - i, counter, s)
+                          : launch_grouped_t<__nv_bfloat16, false>(args + i, j - i, counter, s);
+            if (e != cudaSuccess) return e;
+            i = j;
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace bmm

@@ -52,6 +52,17 @@ int64_t gram_frob_partial_elems(int64_t K, int64_t max_len);
 
 // ---- blockstats_tc.cu
 bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk);
+// One product of a grouped statistics launch (outputs as for launch_blockstats_tc).
+struct StatsArgs {
+    VecSet vM, vN;
+    const int64_t* off;
+    int64_t K, n;
+    double *x, *y, *a, *s, *mf, *nf, *f;
+    DevStatus* st;
+};
+// Many products (each supported by blockstats_tc_supported) in launches of up to ~19 products of
+// one element type, every launch's CTAs sharing one work counter over all its blocks.
+cudaError_t launch_blockstats_tc_grouped(const StatsArgs* args, int64_t count, bool stats, int* counter, cudaStream_t s);
 // stats = true: writes x, y, a, ssum, mf, nf and f; stats = false: reads ssum, writes f only
 cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n,
                                  bool stats, int* counter, double* x, double* y, double* a, double* ssum, double* mf,

@@ -123,7 +123,7 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
 
 def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
         gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None,
-        fmode: int = A.F_TC, fused_stats: bool = False) -> dict:
+        fmode: int = A.F_TC, fused_stats: bool = False, p_ready=None) -> dict:
     """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring).
 
     fmode: how OPL and WU compute ||M^k N_k||_F^2 -- A.F_TC (tensor-core Grams when the inputs
@@ -132,6 +132,8 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
 
     events: if a list, (stage name, torch.cuda.Event) pairs are appended at the stage
     boundaries (recorded on the current stream; used for timing only).
+    p_ready (OPL only): probabilities already computed, with prob.st holding the statistics and f
+    (run_batched computes them for many products at once); the statistics calls are skipped.
     """
     torch = _torch()
     M, N, B, ws, st = prob.M, prob.N, prob.B, prob.ws, prob.st
@@ -183,7 +185,9 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         A.bmm_blocksizes(None, None, B, None, A.CK_EQUAL, c, None, None, 0, ck, g, None, ws)
         mark("blocksizes")
     elif method == "OPL":
-        if fmode == A.F_TC and fused_stats:
+        if p_ready is not None:
+            p = p_ready
+        elif fmode == A.F_TC and fused_stats:
             A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_TC, p, st, ws)
             mark("stats_f")
         else:
@@ -290,7 +294,8 @@ SampledMatmul = _Lazy()
 
 
 def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF16, outs=None, streams=None,
-                c0: int | None = None, fmode: int = A.F_TC) -> list:
+                c0: int | None = None, fmode: int = A.F_TC, fused_stats: bool = False,
+                grouped_stats: bool = True) -> list:
     """Many independent products (the batched configuration).
 
     The design and the draws of each product (bmm_probs, bmm_blocksizes, bmm_sample) are spread
@@ -298,6 +303,10 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
     through one bmm_apply_batched call, whose BF16 GEMMs share persistent tensor-core launches.
     Every step is an asynchronous C-ABI call, so the whole sequence can be captured with
     torch.cuda.graph and replayed as one graph launch.  Each Problem needs its own workspace.
+    ``fused_stats`` computes each product's norms and f_k in one tensor-core pass instead of the
+    norm pass plus the Gram pass.  ``grouped_stats`` (OPL with tensor-core f_k): the tensor-core
+    statistics passes of all products share launches of many products (bmm_probs_batched), whose
+    CTAs pull blocks from one work list instead of one small launch per product.
     """
     torch = _torch()
     main = torch.cuda.current_stream()
@@ -307,10 +316,29 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
         if s is not main:
             s.wait_stream(main)
     results = []
+    ready = [None] * len(probs)
+    if grouped_stats and method == "OPL" and fmode == A.F_TC and probs:
+        ready = [torch.empty(pr.n, dtype=torch.float64, device=pr.M.device) for pr in probs]
+        Ms, Ns, Bs = [pr.M for pr in probs], [pr.N for pr in probs], [pr.B for pr in probs]
+        sts, wss = [pr.st for pr in probs], [pr.ws for pr in probs]
+        if fused_stats:
+            A.bmm_probs_batched(Ms, Ns, Bs, A.P_COL_OPT, A.F_TC, ready, sts, wss)
+        else:
+            # norm passes per product on the side streams, then the Gram passes grouped
+            for i, pr in enumerate(probs):
+                with torch.cuda.stream(streams[i % len(streams)]):
+                    A.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_NONE, ready[i], pr.st, pr.ws)
+            for s in streams:
+                if s is not main:
+                    main.wait_stream(s)
+            A.bmm_probs_batched(Ms, Ns, Bs, A.P_COL_OPT, A.F_TC | A.REUSE_STATS, None, sts, wss)
+        for s in streams:
+            if s is not main:
+                s.wait_stream(main)
     for i, prob in enumerate(probs):
         with torch.cuda.stream(streams[i % len(streams)]):
             results.append(run(prob, method, int(cs[i]), int(seeds[i]), c0=c0, gemm_mode=gemm_mode,
-                               compute_product=False, fmode=fmode))
+                               compute_product=False, fmode=fmode, fused_stats=fused_stats, p_ready=ready[i]))
     for s in streams:
         if s is not main:
             main.wait_stream(s)

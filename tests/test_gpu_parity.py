@@ -613,3 +613,53 @@ def test_batched_uneven_products_and_graph_replay(bmm):
         bmm.check_status(pr)
     for a_, b_ in zip(eager, outs):
         np.testing.assert_array_equal(host(b_).astype(np.float64), a_)
+
+
+@pytest.mark.parametrize("reuse", [False, True])
+def test_probs_batched_matches_single_products(bmm, reuse):
+    """bmm_probs_batched over products of both element types, all storage orders and one that the
+    tensor-core pass does not take (odd leading dimension): every output equals bmm_probs's for
+    that product alone, bit for bit (each block is computed the same way in a grouped launch), and
+    a grouped launch spans several tables (25 products > one kernel-parameter table)."""
+    rng = np.random.default_rng(31)
+    A = bmm._abi
+    cases = []
+    for i in range(25):
+        dt = torch.float32 if i % 3 else torch.bfloat16
+        m = int(rng.choice([64, 96, 200])) + (3 if i == 7 else 0)  # product 7: odd ld when column-major
+        p = int(rng.choice([64, 128, 136]))
+        n = int(rng.integers(2, 6)) * 512
+        K = n // 64
+        off = S.block_offsets_uneven(n, K, 16, 128, seed=300 + i)
+        M, N = S.scaled_gaussian(m, n, p, off, 1.0, seed=400 + i, dtype=np.float32)
+        Mt = as_layout(to_dev(M, dt), "col" if i % 4 == 1 else "row")
+        Nt = as_layout(to_dev(N, dt), "col" if i % 4 == 2 else "row")
+        cases.append((Mt, Nt, off))
+
+    def fresh():
+        return [bmm.prepare(Mt, Nt, off, max_draws=64) for Mt, Nt, off in cases]
+
+    single, batch = fresh(), fresh()
+    ps_single = [torch.empty(pr.n, dtype=torch.float64, device=pr.M.device) for pr in single]
+    ps_batch = [torch.empty(pr.n, dtype=torch.float64, device=pr.M.device) for pr in batch]
+    for pr, pv in zip(single, ps_single):
+        if reuse:
+            bmm.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_NONE, pv, pr.st, pr.ws)
+            bmm.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_TC | A.REUSE_STATS, None, pr.st, pr.ws)
+        else:
+            bmm.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_TC, pv, pr.st, pr.ws)
+    if reuse:
+        for pr, pv in zip(batch, ps_batch):
+            bmm.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_NONE, pv, pr.st, pr.ws)
+        A.bmm_probs_batched([pr.M for pr in batch], [pr.N for pr in batch], [pr.B for pr in batch], A.P_COL_OPT,
+                            A.F_TC | A.REUSE_STATS, None, [pr.st for pr in batch], [pr.ws for pr in batch])
+    else:
+        A.bmm_probs_batched([pr.M for pr in batch], [pr.N for pr in batch], [pr.B for pr in batch], A.P_COL_OPT,
+                            A.F_TC, ps_batch, [pr.st for pr in batch], [pr.ws for pr in batch])
+    torch.cuda.synchronize()
+    for a_, b_, pa, pb in zip(single, batch, ps_single, ps_batch):
+        bmm.check_status(a_)
+        bmm.check_status(b_)
+        for key in ("x", "y", "a", "s", "mf", "nf", "f"):
+            np.testing.assert_array_equal(host(a_.st[key]), host(b_.st[key]), err_msg=key)
+        np.testing.assert_array_equal(host(pa), host(pb))
