@@ -104,6 +104,7 @@ struct ProbsPlan {
     double* gpart;
     int64_t gpart_cap;
     int* counter;
+    int* wins;
 };
 void plan_probs(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, bool need_f, ProbsPlan* p) {
     p->partial_cap = imax(vec_sqnorms_partial_elems(vecset_of_M(M)), vec_sqnorms_partial_elems(vecset_of_N(N)));
@@ -111,6 +112,7 @@ void plan_probs(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks
     p->gpart_cap = need_f ? gram_frob_partial_elems(B->K, B->max_nk) : 0;
     p->gpart = need_f ? cv.take<double>(p->gpart_cap) : nullptr;
     p->counter = cv.take<int>(1);
+    p->wins = need_f ? cv.take<int>(stats_windows_ints(B->K)) : nullptr;
 }
 
 struct SizesPlan {
@@ -310,7 +312,7 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
         cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
         const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
         if (fmode == BMM_F_TC && blockstats_tc_supported(vM, vN, B->max_nk))
-            BMM_TRY(launch_blockstats_tc(vM, vN, B->offsets, B->K, B->n, false, plan.counter, st->x, st->y, st->a,
+            BMM_TRY(launch_blockstats_tc(vM, vN, B->offsets, B->K, B->n, false, plan.counter, plan.wins, st->x, st->y, st->a,
                                          st->s, st->mf, st->nf, st->f, status_of(ws), cs));
         else if (fmode != BMM_F_NONE)
             BMM_TRY(launch_gram_frob(vM, vN, B->offsets, B->K, B->max_nk, nullptr, nullptr, 0, st->f, plan.gpart,
@@ -331,7 +333,7 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
     const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
     if (fmode == BMM_F_TC && blockstats_tc_supported(vM, vN, B->max_nk)) {
         // one fused pass: statistics and f_k
-        BMM_TRY(launch_blockstats_tc(vM, vN, B->offsets, B->K, B->n, true, plan.counter, st->x, st->y, st->a, st->s,
+        BMM_TRY(launch_blockstats_tc(vM, vN, B->offsets, B->K, B->n, true, plan.counter, plan.wins, st->x, st->y, st->a, st->s,
                                      st->mf, st->nf, st->f, dst, cs));
     } else {
         BMM_TRY(launch_vec_sqnorms(vM, st->x, plan.partial, plan.partial_cap, cs));
@@ -384,7 +386,7 @@ BMM_API bmm_status bmm_probs_batched(int64_t count, const bmm_mat* Ms, const bmm
         plan_probs(cv, M, N, B, true, &plan);
         if (counter == nullptr) counter = plan.counter;
         grouped.push_back(StatsArgs{vecset_of_M(M), vecset_of_N(N), B->offsets, B->K, B->n, st->x, st->y, st->a, st->s,
-                                    st->mf, st->nf, st->f, status_of(ws[i])});
+                                    st->mf, st->nf, st->f, status_of(ws[i]), plan.wins});
         which.push_back(i);
     }
     if (!grouped.empty())

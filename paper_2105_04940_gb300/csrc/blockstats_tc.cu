@@ -51,7 +51,7 @@ constexpr int kRowBytes = 128;                // one swizzled row: E elements
 constexpr int kRowsPerGroup = 32;             // K-major boxes come in multiples of 32 vector rows
 constexpr int kGroupBytes = kRowsPerGroup * kRowBytes;  // 4 KB
 constexpr int kMnRows = 64;                   // rows per strided box
-constexpr int kMnBoxBytes = kMnRows * kRowBytes;        // 8 KB
+constexpr int kMnBoxBytes = kMnRows * kRowBytes;        // 8 KB (wide blocks; narrower ones use taller boxes)
 constexpr int kStageBytes = 40 * 1024;        // 40 KB per pipeline stage
 constexpr int kStages = 5;
 constexpr int kBlockSlots = 4;                // block records in flight
@@ -78,13 +78,19 @@ template <> struct Tr<float> {
     static constexpr uint32_t kFmt = 2;         // TF32
     static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     static constexpr CUtensorMapSwizzle kMnSwizzle = CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B;
-    static __device__ __forceinline__ uint64_t mn_desc(uint32_t addr) { return sw128_atom32_mn_desc(addr, kMnBoxBytes); }
+    static __device__ __forceinline__ uint64_t mn_desc(uint32_t addr, uint32_t box_bytes) {
+        return sw128_atom32_mn_desc(addr, box_bytes);
+    }
     static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
         tc_mma_tf32(d, a, b, idesc, acc);
     }
     // byte offset of (row h, column cc) in a strided box: 32-byte chunk cc / 8 at chunk (cc / 8) ^ (h mod 4)
     static __device__ __forceinline__ int mn_offset(int h, int cc) {
         return h * kRowBytes + ((((cc >> 3) ^ (h & 3)) << 5) | ((cc & 7) << 2));
+    }
+    // byte offset of 16-byte chunk c16 (columns 4 c16 .. 4 c16 + 3) of row h in a strided box
+    static __device__ __forceinline__ int mn_chunk_offset(int h, int c16) {
+        return h * kRowBytes + ((((c16 >> 1) ^ (h & 3)) << 5) | ((c16 & 1) << 4));
     }
     static __device__ __forceinline__ float to_f(float v) { return v; }
 };
@@ -98,13 +104,19 @@ template <> struct Tr<__nv_bfloat16> {
     static constexpr uint32_t kFmt = 1;         // BF16 (kind::f16)
     static constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     static constexpr CUtensorMapSwizzle kMnSwizzle = CU_TENSOR_MAP_SWIZZLE_128B;
-    static __device__ __forceinline__ uint64_t mn_desc(uint32_t addr) { return sw128_mn_desc(addr, kMnBoxBytes); }
+    static __device__ __forceinline__ uint64_t mn_desc(uint32_t addr, uint32_t box_bytes) {
+        return sw128_mn_desc(addr, box_bytes);
+    }
     static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
         tc_mma_bf16(d, a, b, idesc, acc);
     }
     // 16-byte chunk (2 cc) / 16 of row h at chunk ^ (h mod 8)
     static __device__ __forceinline__ int mn_offset(int h, int cc) {
         return h * kRowBytes + ((((cc >> 3) ^ (h & 7)) << 4) | ((cc & 7) << 1));
+    }
+    // 16-byte chunk c16 (columns 8 c16 .. 8 c16 + 7) of row h
+    static __device__ __forceinline__ int mn_chunk_offset(int h, int c16) {
+        return h * kRowBytes + ((c16 ^ (h & 7)) << 4);
     }
     static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
@@ -114,9 +126,16 @@ template <> struct Tr<__nv_bfloat16> {
 // corner MMA reads up to R0 + 128 rows; rows past the block belong to the next sub-tile (masked)
 // but must stay inside the 40 KB stage: (per - 1) * nb * 4 KB + 16 KB <= 40 KB for nb <= 4; wide
 // FP32 blocks (nb = 5, corner to 20 KB) take 2 and wide BF16 blocks (nb = 6, corner to 24 KB) 1.
-// A strided operand stage holds kMnPer sub-tiles in nb boxes of 8 KB; its MN-major operand reads
-// the block's boxes, at most 40 KB (FP32, five boxes for a wide block's corner) or 24 KB (BF16).
+// A strided operand stage is nb boxes of E columns x mn_rows rows.  The MMA's M side always spans
+// 128 vectors, i.e. 128 / E boxes at the box stride, whatever nb is, and these reads must stay
+// inside the stage: FP32 (four boxes) keeps 64-row boxes (8 KB, 32 KB read); BF16 (two boxes) takes
+// 128-row boxes (16 KB, 32 KB read) for blocks of one or two boxes and 64-row boxes for wide
+// blocks.  A stage holds at most 40 KB (a wide FP32 block's five boxes).
 __host__ __device__ __forceinline__ int subtiles_per_stage(int nb) { return nb >= 6 ? 1 : (nb == 5 ? 2 : 1 + 6 / nb); }
+template <typename T> __host__ __device__ __forceinline__ int mn_map_index(int nb) {
+    return (sizeof(T) == 2 && nb <= 2) ? 1 : 0;
+}
+template <typename T> __host__ __device__ __forceinline__ int mn_rows(int nb) { return kMnRows << mn_map_index<T>(nb); }
 
 enum StageFlags : int {
     ST_PHASE = 1,   // 0: columns of M, 1: rows of N
@@ -135,37 +154,40 @@ struct __align__(16) StageInfo {
     int nb;         // groups per sub-tile: 32-row groups (K-major) or E-column boxes (MN-major)
     int nsub;       // sub-tiles in this stage
     int sub_bytes;  // distance between sub-tiles in the stage
+    int box_bytes;  // MN-major: bytes of one box (E columns x mn_rows rows)
 };
 
+// One window of consecutive blocks: the unit of work of a CTA (see stats_windows_kernel).
 struct __align__(16) BlockInfo {
-    long long lo;  // first column
-    long long k;   // block index within its product, -1: no more work
+    long long lo;  // first column of the window
+    long long kb;  // first block of the window within its product, -1: no more work
     int q;         // product
-    int nk;
-    int dpos;
-    int pad;
+    int nk;        // vectors in the window (the sum of its block sizes)
+    int dpos;      // operand row of the window's first vector
+    int nblk;      // blocks in the window
 };
 
-// Tensor maps of one operand: strided storage uses map[0] (E x 64 boxes); contiguous storage
-// uses map[nb - 1] (E coordinates x 32 nb vectors).
+// Tensor maps of one operand: strided storage uses map[mn_map_index(nb)] (E x 64 or 128 boxes);
+// contiguous storage uses map[nb - 1] (E coordinates x 32 nb vectors).
 struct OperandMaps {
     CUtensorMap map[kMaxKMaps];
 };
 
 // One product of a launch.  Outputs x, y [n] and a, s, mf, nf [K] are written in the statistics
-// pass (STATS) and read (s) in the Gram-only pass; f [K] is written by both.
+// pass (STATS) and read (s) in the Gram-only pass; f [K] is written by both.  wins [K + 2] is
+// workspace: the window starts (wins[0 .. W], wins[W] = K) and wins[K + 1] = W.
 struct __align__(64) StatsProblem {
     OperandMaps mM, mN;
     const int64_t* off;
     long long K, n, m, p;
-    long long block_begin;  // first block of this product in the launch's block numbering
+    int* wins;
     double *x, *y, *a, *s, *mf, *nf, *f;
     DevStatus* st;
     int M_strided, N_strided;
 };
 template <int G> struct StatsTable {
     int count;
-    long long total_blocks;
+    long long total_blocks;  // an upper bound of the launch's windows
     StatsProblem prob[G];
 };
 constexpr int kMaxProducts = (32760 - 64) / (int)sizeof(StatsProblem);  // kernel-parameter limit
@@ -194,14 +216,16 @@ __device__ __forceinline__ void mma_sub(uint32_t d, uint32_t lo_a, uint32_t lo_b
 }
 
 template <typename T, bool MN>
-__device__ __forceinline__ void mma_stage(uint32_t d_main, uint32_t d_corner, uint32_t addr, uint32_t sub_bytes, int nsub,
-                                          uint32_t idesc, uint32_t idesc16, bool first, bool wide) {
+__device__ __forceinline__ void mma_stage(uint32_t d_main, uint32_t d_corner, uint32_t addr, uint32_t sub_bytes,
+                                          uint32_t box_bytes, int nsub, uint32_t idesc, uint32_t idesc16, bool first,
+                                          bool wide) {
     // corner operands, in descriptor units: A from operand row R0, B from operand row 128.
-    // MN-major: an E-row block of operand rows is one 8 KB box; K-major: a row is 128 bytes.
+    // MN-major: an E-row block of operand rows is one box (8 KB for wide blocks); K-major: a row is
+    // 128 bytes.
     constexpr uint32_t ca = MN ? (uint32_t)(Tr<T>::kCornerRow0 / Tr<T>::E) * (kMnBoxBytes >> 4)
                                : (uint32_t)(Tr<T>::kCornerRow0 * kRowBytes) >> 4;
     constexpr uint32_t cb = MN ? (uint32_t)(128 / Tr<T>::E) * (kMnBoxBytes >> 4) : (uint32_t)(128 * kRowBytes) >> 4;
-    const uint64_t d0 = MN ? Tr<T>::mn_desc(addr) : sw128_desc(addr);
+    const uint64_t d0 = MN ? Tr<T>::mn_desc(addr, box_bytes) : sw128_desc(addr);
     const uint32_t hi = (uint32_t)(d0 >> 32);
     uint32_t lo = (uint32_t)d0;
     const uint32_t step = sub_bytes >> 4;
@@ -227,6 +251,359 @@ __device__ __forceinline__ bool conv_sync(uint32_t bar, int& uses, volatile int*
     return ok;
 }
 
+// Sums of squares of one phase of a block with d + n_k <= 128, every vector inside the first 128
+// tile columns (strided) or rows (contiguous).  Each lane reads whole 16-byte chunks and keeps
+// float-float sums per element position of its chunk, so no lane idles on a vector outside the
+// block except at the block's edges.  Return false when a wait expired.
+//
+// Strided (MN) stages: nb boxes of E columns x 64 rows, the block's columns in the first 8 nb
+// 16-byte chunks of each row.  A row is read by lpr = 8 nb lanes (rounded up to 8, 16 or 32), so
+// one warp reads 32 / lpr rows per step: lane chunk cg covers columns kCpc cg .. kCpc cg + kCpc - 1
+// and rows hp + rps (cw + 16 r) (hp = lane / lpr, rps = 32 / lpr).  The swizzle of a chunk depends on
+// the row mod 4 (FP32) or mod 8 (BF16) only, which is fixed per lane.  Partial sums go to
+// part[warp][vector], summed over the warps by the caller.
+template <typename T>
+__device__ __forceinline__ bool squares_strided(const uint8_t* base, const StageInfo* info, uint64_t* bar_full,
+                                                uint64_t* bar_empty, int& stage, uint32_t& ph, volatile int* abort_flag,
+                                                int cw, int lane, int nk, int d, float2 (*part)[kMaxBlock]) {
+    using TR = Tr<T>;
+    constexpr int kCpc = 16 / (int)sizeof(T);
+    const int nb = info[stage].nb, box_bytes = info[stage].box_bytes;  // the same in every stage of the phase
+    const int lpr = nb == 1 ? 8 : (nb == 2 ? 16 : 32);
+    const int rps = 32 / lpr;
+    const int steps = mn_rows<T>(nb) / (16 * rps);  // <= 4
+    const int step_bytes = 16 * rps * kRowBytes;
+    const int cg = lane & (lpr - 1), hp = lane / lpr;
+    const int box = cg >> 3;
+    const int h0 = hp + rps * cw;
+    const int lane_off = box * box_bytes + TR::mn_chunk_offset(h0, cg & 7);
+    FF acc[kCpc], tot[kCpc];
+#pragma unroll
+    for (int u = 0; u < kCpc; ++u) { acc[u].zero(); tot[u].zero(); }
+    int since_fold = 0;
+    while (true) {
+        if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
+        const int rows = info[stage].nsub * TR::kMnSubRows;
+        const bool last = info[stage].flags & ST_LAST;
+        if (box < nb) {
+            const uint8_t* src = base + stage * kStageBytes + lane_off;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r < steps && h0 + 16 * rps * r < rows) {
+                    const uint4 w4 = *reinterpret_cast<const uint4*>(src + r * step_bytes);
+                    const T* e = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+                    for (int u = 0; u < kCpc; ++u) {
+                        const float v = TR::to_f(e[u]);
+                        acc[u].add_prod(v, v);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
+        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+#pragma unroll
+        for (int u = 0; u < kCpc; ++u) acc[u].renorm();
+        if (++since_fold == kFoldStages || last) {
+#pragma unroll
+            for (int u = 0; u < kCpc; ++u) {
+                tot[u].add(acc[u]);
+                tot[u].renorm();
+                acc[u].zero();
+            }
+            since_fold = 0;
+        }
+        if (last) break;
+    }
+    // the rps lanes of a chunk combine their rows
+    for (int o = lpr; o < 32; o <<= 1) {
+#pragma unroll
+        for (int u = 0; u < kCpc; ++u) {
+            FF other;
+            other.hi = __shfl_xor_sync(0xffffffffu, tot[u].hi, o);
+            other.lo = __shfl_xor_sync(0xffffffffu, tot[u].lo, o);
+            tot[u].add(other);
+            tot[u].renorm();
+        }
+    }
+    if (hp == 0) {
+#pragma unroll
+        for (int u = 0; u < kCpc; ++u) {
+            const int i = kCpc * cg + u - d;
+            if (i >= 0 && i < nk) part[cw][i] = make_float2(tot[u].hi, tot[u].lo);
+        }
+    }
+    return true;
+}
+
+// Contiguous (K-major) stages: sub-tiles of 32 nb vector rows x 128 bytes.  Lane t = 32 cw + lane
+// reads chunk t mod 8 of rows t / 8 and t / 8 + 64, every element of a chunk belonging to the same
+// vector; the eight lanes of a row combine their sums and write x_i or y_i to xy[i].
+template <typename T>
+__device__ __forceinline__ bool squares_contig(const uint8_t* base, const StageInfo* info, uint64_t* bar_full,
+                                               uint64_t* bar_empty, int& stage, uint32_t& ph, volatile int* abort_flag,
+                                               int cw, int lane, int nk, int d, double* xy) {
+    using TR = Tr<T>;
+    constexpr int kCpc = 16 / (int)sizeof(T);
+    const int t = 32 * cw + lane;
+    const int q = t & 7, r0 = t >> 3;
+    const int sw = (q ^ (r0 & 7)) << 4;  // (r0 + 64) mod 8 == r0 mod 8
+    const bool in0 = r0 >= d && r0 < d + nk, in1 = r0 + 64 >= d && r0 + 64 < d + nk;
+    FF acc[2], tot[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) { acc[u].zero(); tot[u].zero(); }
+    int since_fold = 0;
+    while (true) {
+        if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
+        const int nsub = info[stage].nsub, sub_bytes = info[stage].sub_bytes;
+        const bool last = info[stage].flags & ST_LAST;
+        const uint8_t* tile = base + stage * kStageBytes + r0 * kRowBytes + sw;
+        for (int s = 0; s < nsub; ++s) {
+            const uint8_t* sub = tile + s * sub_bytes;
+            if (in0) {
+                const uint4 w4 = *reinterpret_cast<const uint4*>(sub);
+                const T* e = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+                for (int u = 0; u < kCpc; ++u) {
+                    const float v = TR::to_f(e[u]);
+                    acc[0].add_prod(v, v);
+                }
+            }
+            if (in1) {
+                const uint4 w4 = *reinterpret_cast<const uint4*>(sub + 64 * kRowBytes);
+                const T* e = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+                for (int u = 0; u < kCpc; ++u) {
+                    const float v = TR::to_f(e[u]);
+                    acc[1].add_prod(v, v);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
+        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) acc[u].renorm();
+        if (++since_fold == kFoldStages || last) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                tot[u].add(acc[u]);
+                tot[u].renorm();
+                acc[u].zero();
+            }
+            since_fold = 0;
+        }
+        if (last) break;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            FF other;
+            other.hi = __shfl_xor_sync(0xffffffffu, tot[u].hi, o);
+            other.lo = __shfl_xor_sync(0xffffffffu, tot[u].lo, o);
+            tot[u].add(other);
+            tot[u].renorm();
+        }
+    if (q == 0) {
+        if (in0) xy[r0 - d] = tot[0].value();
+        if (in1) xy[r0 + 64 - d] = tot[1].value();
+    }
+    return true;
+}
+
+// Sums of squares of one phase of a wide block (d + n_k > 128): lane handles vectors lane + 32 v,
+// every element by itself.  Rare, so kept out of line to spare the kernel's registers.  Returns
+// the next (stage, phase bit) as stage | phase << 8, or -1 when a wait expired.
+template <typename T>
+__device__ __noinline__ int squares_wide(const uint8_t* base, const StageInfo* info, uint64_t* bar_full,
+                                         uint64_t* bar_empty, int stage, uint32_t ph, volatile int* abort_flag,
+                                         int cw, int lane, float2 (*part)[kMaxBlock]) {
+    using TR = Tr<T>;
+    bool aborted = false;
+    // two levels of float-float sums: acc over at most kFoldStages stages, folded
+    // into tot (FP32 operations only: the FP64 pipe is slow on this part); FP64 once
+    // per phase
+    FF acc[4], tot[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { acc[v].zero(); tot[v].zero(); }
+    int since_fold = 0;
+    bool mn_phase = false;
+    while (true) {
+        if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) { aborted = true; break; }
+        const StageInfo si = info[stage];
+        mn_phase = si.flags & ST_MN;
+        const uint8_t* tile = base + stage * kStageBytes;
+        const int sub_bytes = si.sub_bytes;
+        if (mn_phase) {
+            // rows h = cw + 16 r of every sub-tile; vector i is tile column d + i
+            for (int s = 0; s < si.nsub; ++s) {
+                const uint8_t* sub = tile + s * sub_bytes;
+#pragma unroll
+                for (int r = 0; r < TR::kMnSubRows / 16; ++r) {
+                    const int h = cw + 16 * r;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int i = lane + 32 * v;
+                        if (i < si.nk) {
+                            const int j = i + si.d;
+                            const float e = TR::to_f(*reinterpret_cast<const T*>(
+                                sub + (j / TR::E) * kMnBoxBytes + TR::mn_offset(h, j % TR::E)));
+                            acc[v].add_prod(e, e);
+                        }
+                    }
+                }
+            }
+        } else {
+            // 16-byte chunk cw / 2 of every sub-tile row, vectors i = lane + 32 v for
+            // v = cw mod 2 and cw mod 2 + 2; vector i is tile row d + i
+            const int q = cw >> 1;
+            for (int s = 0; s < si.nsub; ++s) {
+                const uint8_t* sub = tile + s * sub_bytes;
+#pragma unroll
+                for (int vv = 0; vv < 2; ++vv) {
+                    // acc[vv] holds vector group (cw mod 2) + 2 vv in this layout
+                    const int i = lane + 32 * ((cw & 1) + 2 * vv);
+                    if (i < si.nk) {
+                        const int r = i + si.d;
+                        const uint4 w4 =
+                            *reinterpret_cast<const uint4*>(sub + r * kRowBytes + ((q ^ (r & 7)) << 4));
+                        const T* e = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+                        for (int u = 0; u < 16 / (int)sizeof(T); ++u) {
+                            const float ev = TR::to_f(e[u]);
+                            acc[vv].add_prod(ev, ev);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
+        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v].renorm();
+        const bool last = si.flags & ST_LAST;
+        if (++since_fold == kFoldStages || last) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                tot[v].add(acc[v]);
+                tot[v].renorm();
+                acc[v].zero();
+            }
+            since_fold = 0;
+        }
+        if (last) break;
+    }
+    if (mn_phase) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) part[cw][lane + 32 * v] = make_float2(tot[v].hi, tot[v].lo);
+    } else {
+        part[cw][lane + 32 * (cw & 1)] = make_float2(tot[0].hi, tot[0].lo);
+        part[cw][lane + 32 * ((cw & 1) + 2)] = make_float2(tot[1].hi, tot[1].lo);
+        part[cw][lane + 32 * ((cw & 1) ^ 1)] = make_float2(0.f, 0.f);
+        part[cw][lane + 32 * (((cw & 1) ^ 1) + 2)] = make_float2(0.f, 0.f);
+    }
+    return aborted ? -1 : (stage | (int)(ph << 8));
+}
+
+constexpr int kWinThreads = 1024;
+constexpr int kWinChunk = 2 * kWinThreads;  // blocks per pass through shared memory
+
+// Windows: runs of consecutive blocks of a product whose vectors, counted from the 16-byte
+// boundary at or below the run's first column (for strided operands), fit the 128 operand rows of
+// one MMA tile.  They are taken greedily from block 0: a window ends before the first block that
+// would overflow it, and a block that fills the tile by itself (a wide block) is a window alone.
+// Packing small blocks this way gives the MMA, the TMA and the norm warps fuller tiles.  One CTA
+// per product, in passes of kWinChunk blocks (no window crosses a pass).  With next[k] = the end
+// of the window that starts at block k, the windows are the orbit of the pass's first block under
+// next, found by pointer doubling: after the round with jump J = next^(2^r), every next^i(0) with
+// i < 2^(r+1) is marked.  Writes wins[0 .. W] (window starts, wins[W] = K) and wins[K + 1] = W;
+// CTA 0 also zeroes the work counter of the statistics launch that follows.
+template <typename T, int G>
+__global__ void __launch_bounds__(kWinThreads)
+    stats_windows_kernel(const __grid_constant__ StatsTable<G> tab, int* __restrict__ counter) {
+    __shared__ long long s_off[kWinChunk + 1];
+    __shared__ int s_next[kWinChunk + 1];
+    __shared__ unsigned char s_mark[kWinChunk];
+    __shared__ int s_scan[kWinThreads / 32];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    if ((int)blockIdx.x >= tab.count) return;
+    const StatsProblem& pr = tab.prob[blockIdx.x];
+    const long long K = pr.K;
+    const long long align_mask = (pr.M_strided || pr.N_strided) ? Tr<T>::kAlign - 1 : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int base = 0;
+    for (long long c0 = 0; c0 < K; c0 += kWinChunk) {
+        const int L = (int)imin(kWinChunk, K - c0);
+        __syncthreads();  // the previous pass is done with shared memory
+        for (int i = threadIdx.x; i <= L; i += kWinThreads) s_off[i] = pr.off[c0 + i];
+        __syncthreads();
+        for (int k = threadIdx.x; k < L; k += kWinThreads) {
+            // largest e in [k + 1, min(L, k + 128)] with off[e] - (off[k] rounded down to 16 bytes) <= 128
+            const long long lim = s_off[k] - (s_off[k] & align_mask) + 128;
+            int lo = k + 1, hi = (int)imin(L, k + 128);
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= lim) lo = mid;
+                else hi = mid - 1;
+            }
+            s_next[k] = lo;
+            s_mark[k] = k == 0;
+        }
+        if (threadIdx.x == 0) s_next[L] = L;
+        __syncthreads();
+        for (int jump = 1; jump < L; jump <<= 1) {
+            for (int k = threadIdx.x; k < L; k += kWinThreads)
+                if (s_mark[k] && s_next[k] < L) s_mark[s_next[k]] = 1;
+            __syncthreads();
+            int jn[kWinChunk / kWinThreads];
+#pragma unroll
+            for (int u = 0; u < kWinChunk / kWinThreads; ++u) {
+                const int k = threadIdx.x + u * kWinThreads;
+                jn[u] = k < L ? s_next[s_next[k]] : L;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kWinChunk / kWinThreads; ++u) {
+                const int k = threadIdx.x + u * kWinThreads;
+                if (k < L) s_next[k] = jn[u];
+            }
+            __syncthreads();
+        }
+        // compaction in block order: thread t owns blocks 2t and 2t + 1
+        const int k0 = 2 * threadIdx.x;
+        const int m0 = k0 < L ? s_mark[k0] : 0, m1 = k0 + 1 < L ? s_mark[k0 + 1] : 0;
+        int v = m0 + m1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += x;
+        }
+        if (lane == 31) s_scan[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int w = s_scan[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += x;
+            }
+            s_scan[lane] = w;
+        }
+        __syncthreads();
+        const int excl = base + (warp ? s_scan[warp - 1] : 0) + v - m0 - m1;
+        if (m0) pr.wins[excl] = (int)(c0 + k0);
+        if (m1) pr.wins[excl + m0] = (int)(c0 + k0 + 1);
+        base += s_scan[kWinThreads / 32 - 1];
+    }
+    if (threadIdx.x == 0) {
+        pr.wins[base] = (int)K;
+        pr.wins[K + 1] = base;
+    }
+}
+
 template <typename T, bool STATS, int G>
 __global__ void __launch_bounds__(kThreads, 1)
     blockstats_tc_kernel(const __grid_constant__ StatsTable<G> tab, int* __restrict__ counter) {
@@ -237,12 +614,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) uint64_t bar_slot_free[3], bar_tfull[2], bar_drain, bar_cs;
     __shared__ StageInfo info[kStages];
     __shared__ BlockInfo binfo[kBlockSlots];
+    __shared__ long long s_wb[G + 1];                               // first window of each product
+    __shared__ int s_seg[kMaxBlock + 1];                            // block starts in the window
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ float2 part[STATS ? kConvWarps : 1][kMaxBlock];   // [warp][vector] float-float, one phase
     __shared__ double xy_sum[STATS ? 2 : 1][kMaxBlock];           // [phase][vector]: x_i, y_i
-    __shared__ double red[4][4];                                  // statistics sums of the 4 vector warps
-    __shared__ float2 red_off[kConvWarps];                        // off-diagonal sums, float-float
+    __shared__ float2 rowpart[4][kMaxBlock];                      // off-diagonal sums per [quarter][row]
 
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     auto stage_ptr = [&](int s) { return base + s * kStageBytes; };
@@ -283,39 +661,52 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t ph = 0, bph = 0;
             uint32_t issued_mask = 0, issued_phase = 0;
             bool aborted = false;
+            // the launch numbers the windows of its products one after another
+            long long total = 0;
+            for (int u = 0; u < tab.count; ++u) {
+                s_wb[u] = total;
+                total += tab.prob[u].wins[tab.prob[u].K + 1];
+            }
+            s_wb[tab.count] = total;
             while (!aborted) {
                 const long long kg = atomicAdd(counter, 1);
-                if (kg >= tab.total_blocks) {
+                if (kg >= total) {
                     if (!wait_fast(smem_u32(&bar_bempty[bslot]), bph ^ 1u, &s_abort)) { aborted = true; break; }
-                    binfo[bslot].k = -1;
+                    binfo[bslot].kb = -1;
                     mbar_arrive(smem_u32(&bar_bfull[bslot]));
                     if (!wait_fast(smem_u32(&bar_empty[stage]), ph ^ 1u, &s_abort)) { aborted = true; break; }
                     info[stage].block = -1;
                     mbar_arrive(smem_u32(&bar_full[stage]));
                     break;
                 }
-                // blocks are claimed in increasing order, so this CTA's product index only grows
-                while (q + 1 < tab.count && kg >= tab.prob[q + 1].block_begin) ++q;
+                // windows are claimed in increasing order, so this CTA's product index only grows
+                while (q + 1 < tab.count && kg >= s_wb[q + 1]) ++q;
                 const StatsProblem& pr = tab.prob[q];
-                const long long k = kg - pr.block_begin;
-                const long long lo = pr.off[k], hi = pr.off[k + 1];
+                const long long w = kg - s_wb[q];
+                const long long k = pr.wins[w], ke = pr.wins[w + 1];  // blocks k .. ke - 1
+                const bool range_ok = k >= 0 && ke > k && ke <= pr.K && ke - k <= kMaxBlock;
+                const long long lo = range_ok ? pr.off[k] : 0, hi = range_ok ? pr.off[ke] : 0;
                 const long long nk = hi - lo;
-                if (lo < 0 || hi > pr.n || nk <= 0 || nk > kMaxBlock) {
-                    set_status(pr.st, BMM_ERR_SHAPE, (int)k);
-                    if (STATS) { pr.a[k] = 0.0; pr.s[k] = 0.0; pr.mf[k] = 0.0; pr.nf[k] = 0.0; }
-                    pr.f[k] = 0.0;
-                    continue;
-                }
                 const int M_strided = pr.M_strided, N_strided = pr.N_strided;
                 const int dlo = (int)(lo & (TR::kAlign - 1));
                 const int dpos = (M_strided || N_strided) ? dlo : 0;
-                const bool wide = dpos + nk > 128;
+                if (!range_ok || lo < 0 || hi > pr.n || nk <= 0 || (ke - k == 1 ? nk > kMaxBlock : dpos + nk > 128)) {
+                    set_status(pr.st, BMM_ERR_SHAPE, (int)k);
+                    if (range_ok)
+                        for (long long kk = k; kk < ke; ++kk) {
+                            if (STATS) { pr.a[kk] = 0.0; pr.s[kk] = 0.0; pr.mf[kk] = 0.0; pr.nf[kk] = 0.0; }
+                            pr.f[kk] = 0.0;
+                        }
+                    continue;
+                }
+                const bool wide = dpos + nk > 128;  // a window of one block only
                 if (!wait_fast(smem_u32(&bar_bempty[bslot]), bph ^ 1u, &s_abort)) { aborted = true; break; }
                 binfo[bslot].lo = lo;
-                binfo[bslot].k = k;
+                binfo[bslot].kb = k;
                 binfo[bslot].q = q;
                 binfo[bslot].nk = (int)nk;
                 binfo[bslot].dpos = dpos;
+                binfo[bslot].nblk = (int)(ke - k);
                 mbar_arrive(smem_u32(&bar_bfull[bslot]));
                 if (++bslot == kBlockSlots) { bslot = 0; bph ^= 1u; }
                 for (int phase = 0; phase < 2 && !aborted; ++phase) {
@@ -326,10 +717,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // BF16 block takes 6 so that the corner's rows 64..191 are loaded)
                     int nb = strided ? (int)((d + nk + TR::E - 1) / TR::E) : (int)((d + nk + 31) / 32);
                     if (!strided && wide && TR::kCornerRow0 + 128 > 32 * nb) nb = (TR::kCornerRow0 + 128) / 32;
-                    const int per = strided ? TR::kMnPer : subtiles_per_stage(nb);
+                    const int box_bytes = strided ? mn_rows<T>(nb) * kRowBytes : 0;
+                    const int per = strided ? mn_rows<T>(nb) / TR::kMnSubRows : subtiles_per_stage(nb);
                     const long long nsub_total = (len + TR::E - 1) / TR::E;
                     const OperandMaps& maps = phase == 0 ? pr.mM : pr.mN;
-                    const CUtensorMap* map = &maps.map[strided ? 0 : nb - 1];
+                    const CUtensorMap* map = &maps.map[strided ? mn_map_index<T>(nb) : nb - 1];
                     for (long long c0 = 0; c0 < nsub_total; c0 += per) {
                         const int nsub = (int)imin(per, nsub_total - c0);
                         if (!wait_fast(smem_u32(&bar_empty[stage]), ph ^ 1u, &s_abort)) { aborted = true; break; }
@@ -343,13 +735,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         si.nb = nb;
                         si.nsub = nsub;
                         si.sub_bytes = strided ? TR::kMnSubRows * kRowBytes : nb * kGroupBytes;
+                        si.box_bytes = box_bytes;
                         const uint32_t fb = smem_u32(&bar_full[stage]);
                         uint8_t* dst = stage_ptr(stage);
                         if (strided) {
-                            // nb boxes of E columns x 64 rows (rows past the operand read as zeros)
-                            mbar_expect_tx(fb, (uint32_t)(nb * kMnBoxBytes));
+                            // nb boxes of E columns x mn_rows rows (rows past the operand read as zeros)
+                            mbar_expect_tx(fb, (uint32_t)(nb * box_bytes));
                             for (int b = 0; b < nb; ++b)
-                                tma_load_2d(smem_u32(dst + b * kMnBoxBytes), map, fb, (int32_t)(lo - d + TR::E * b),
+                                tma_load_2d(smem_u32(dst + b * box_bytes), map, fb, (int32_t)(lo - d + TR::E * b),
                                             (int32_t)(TR::kMnSubRows * c0));
                         } else {
                             // one box of E coordinates x 32 nb vectors per sub-tile
@@ -400,10 +793,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t addr = smem_u32(stage_ptr(stage));
                 const uint32_t sub_bytes = (uint32_t)si.sub_bytes;
                 if (mn)
-                    mma_stage<T, true>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_of<T>(npad, true),
-                                       idesc_of<T>(16, true), first, wide);
+                    mma_stage<T, true>(d_main, d_corner, addr, sub_bytes, (uint32_t)si.box_bytes, si.nsub,
+                                       idesc_of<T>(npad, true), idesc_of<T>(16, true), first, wide);
                 else
-                    mma_stage<T, false>(d_main, d_corner, addr, sub_bytes, si.nsub, idesc_of<T>(npad, false),
+                    mma_stage<T, false>(d_main, d_corner, addr, sub_bytes, 0u, si.nsub, idesc_of<T>(npad, false),
                                         idesc_of<T>(16, false), first, wide);
                 tc_commit(smem_u32(&bar_empty[stage]));
                 if ((si.flags & ST_LAST) && phase == 1) {
@@ -430,99 +823,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         while (!aborted) {
             if (!wait_fast(smem_u32(&bar_bfull[bslot]), bph, &s_abort)) break;
             const BlockInfo bi = binfo[bslot];
-            if (bi.k < 0) break;
+            if (bi.kb < 0) break;
             const int nk = bi.nk, dpos = bi.dpos;
+            // block starts relative to the window (read in the epilogue, after the converter syncs)
+            if (t <= bi.nblk) s_seg[t] = (int)(tab.prob[bi.q].off[bi.kb + t] - bi.lo);
 
-            if (STATS) {
-                // ---- squares of every element, per vector: lane handles vectors lane + 32 v
+            if constexpr (STATS) {
+                // ---- squares of every element, per vector
                 for (int phase = 0; phase < 2 && !aborted; ++phase) {
-                    // two levels of float-float sums: acc over at most kFoldStages stages, folded
-                    // into tot (FP32 operations only: the FP64 pipe is slow on this part); FP64 once
-                    // per phase
-                    FF acc[4], tot[4];
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) { acc[v].zero(); tot[v].zero(); }
-                    int since_fold = 0;
-                    bool mn_phase = false;
-                    while (true) {
+                    bool reduce_parts = true;
+                    if (dpos + nk <= 128) {
+                        // every lane on whole 16-byte chunks (strided: partial sums per warp in
+                        // part[]; contiguous: x_i or y_i written directly)
                         if (!wait_fast(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
-                        const StageInfo si = info[stage];
-                        mn_phase = si.flags & ST_MN;
-                        const uint8_t* tile = stage_ptr(stage);
-                        const int sub_bytes = si.sub_bytes;
-                        if (mn_phase) {
-                            // rows h = cw + 16 r of every sub-tile; vector i is tile column d + i
-                            for (int s = 0; s < si.nsub; ++s) {
-                                const uint8_t* sub = tile + s * sub_bytes;
-#pragma unroll
-                                for (int r = 0; r < TR::kMnSubRows / 16; ++r) {
-                                    const int h = cw + 16 * r;
-#pragma unroll
-                                    for (int v = 0; v < 4; ++v) {
-                                        const int i = lane + 32 * v;
-                                        if (i < si.nk) {
-                                            const int j = i + si.d;
-                                            const float e = TR::to_f(*reinterpret_cast<const T*>(
-                                                sub + (j / TR::E) * kMnBoxBytes + TR::mn_offset(h, j % TR::E)));
-                                            acc[v].add_prod(e, e);
-                                        }
-                                    }
-                                }
-                            }
-                        } else {
-                            // 16-byte chunk cw / 2 of every sub-tile row, vectors i = lane + 32 v for
-                            // v = cw mod 2 and cw mod 2 + 2; vector i is tile row d + i
-                            const int q = cw >> 1;
-                            for (int s = 0; s < si.nsub; ++s) {
-                                const uint8_t* sub = tile + s * sub_bytes;
-#pragma unroll
-                                for (int vv = 0; vv < 2; ++vv) {
-                                    // acc[vv] holds vector group (cw mod 2) + 2 vv in this layout
-                                    const int i = lane + 32 * ((cw & 1) + 2 * vv);
-                                    if (i < si.nk) {
-                                        const int r = i + si.d;
-                                        const uint4 w4 =
-                                            *reinterpret_cast<const uint4*>(sub + r * kRowBytes + ((q ^ (r & 7)) << 4));
-                                        const T* e = reinterpret_cast<const T*>(&w4);
-#pragma unroll
-                                        for (int u = 0; u < 16 / (int)sizeof(T); ++u) {
-                                            const float ev = TR::to_f(e[u]);
-                                            acc[vv].add_prod(ev, ev);
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
-                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) acc[v].renorm();
-                        const bool last = si.flags & ST_LAST;
-                        if (++since_fold == kFoldStages || last) {
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) {
-                                tot[v].add(acc[v]);
-                                tot[v].renorm();
-                                acc[v].zero();
-                            }
-                            since_fold = 0;
-                        }
-                        if (last) break;
-                    }
-                    if (mn_phase) {
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) part[STATS ? cw : 0][lane + 32 * v] = make_float2(tot[v].hi, tot[v].lo);
+                        const bool mn = info[stage].flags & ST_MN;
+                        const bool ok = mn ? squares_strided<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw,
+                                                                lane, nk, dpos, part)
+                                           : squares_contig<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw,
+                                                               lane, nk, dpos, xy_sum[phase]);
+                        if (!ok) { aborted = true; break; }
+                        reduce_parts = mn;
                     } else {
-                        part[STATS ? cw : 0][lane + 32 * (cw & 1)] = make_float2(tot[0].hi, tot[0].lo);
-                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) + 2)] = make_float2(tot[1].hi, tot[1].lo);
-                        part[STATS ? cw : 0][lane + 32 * ((cw & 1) ^ 1)] = make_float2(0.f, 0.f);
-                        part[STATS ? cw : 0][lane + 32 * (((cw & 1) ^ 1) + 2)] = make_float2(0.f, 0.f);
+                        const int r = squares_wide<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane,
+                                                      part);
+                        if (r < 0) { aborted = true; break; }
+                        stage = r & 0xff;
+                        ph = (uint32_t)(r >> 8);
                     }
                     // x_i (phase 0) or y_i (phase 1): the float-float sum of the warps' shares, one
                     // FP64 conversion per vector
                     conv_sync(cs_bar, cs_uses, &s_abort);
-                    if (t < kMaxBlock) {
+                    if (reduce_parts && t < kMaxBlock) {
                         FF sum;
                         sum.zero();
 #pragma unroll
@@ -541,51 +872,62 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (aborted) break;
             }
 
-            // ---- block epilogue
-            const long long k = bi.k;
+            // ---- window epilogue
+            const long long kb = bi.kb;
             const long long lo = bi.lo;
+            const int nblk = bi.nblk;
             const StatsProblem& pr = tab.prob[bi.q];
-            double sa = 0.0, ss = 0.0, sx = 0.0, sy = 0.0;
-            if (STATS) {
-                if (t < nk) {
-                    const double xi = xy_sum[0][t], yi = xy_sum[STATS ? 1 : 0][t];
-                    pr.x[lo + t] = xi;
-                    pr.y[lo + t] = yi;
-                    const double xy = __dmul_rn(xi, yi);
-                    sa = sqrt(xy);
-                    ss = xy;
-                    sx = xi;
-                    sy = yi;
-                }
+            if constexpr (!STATS) conv_sync(cs_bar, cs_uses, &s_abort);  // s_seg[] is visible
+            if (STATS && t < nk) {
+                pr.x[lo + t] = xy_sum[0][t];
+                pr.y[lo + t] = xy_sum[STATS ? 1 : 0][t];
             }
             // off-diagonal Gram products from TMEM: rows = lanes of this warp's quadrant (operand
-            // rows 0..127), the five 32-column chunks of a slot split between the quadrant's four warps
+            // rows 0..127), the ten 16-column chunks of a slot split between the quadrant's four
+            // warps; a product counts when both vectors belong to the same block of the window
             FF offf;
             offf.zero();
             const int u0 = 2 * it;
             const int q0 = u0 % 3, q1 = (u0 + 1) % 3;
+            const int q4 = warp & 3, quarter = cw >> 2;
+            const int r = 32 * q4 + lane;  // operand row
             if (wait_fast(smem_u32(&bar_tfull[it & 1]), (uint32_t)(it >> 1) & 1u, &s_abort)) {
                 tc_fence_after();
-                const int q4 = warp & 3, quarter = cw >> 2;
-                const int r = 32 * q4 + lane;  // operand row
                 const int end = dpos + nk;
-                const bool row_in = r >= dpos && r < end;
-                const bool wide = end > 128;
+                const bool wide = end > 128;  // a window of one block
+                // the block of operand row r spans operand rows blo .. bhi - 1
+                int blo = 0, bhi = 0;
+                const int v = r - dpos;
+                if (v >= 0 && v < nk) {
+                    int ja = 0, jb = nblk - 1;  // the last block starting at or before v
+                    while (ja < jb) {
+                        const int mid = (ja + jb + 1) >> 1;
+                        if (s_seg[mid] <= v) ja = mid;
+                        else jb = mid - 1;
+                    }
+                    blo = dpos + s_seg[ja];
+                    bhi = dpos + s_seg[ja + 1];
+                }
+                // chunks holding no column of any of the warp's rows' blocks are skipped (the TMEM
+                // loads are warp-wide, so the test is too)
+                const int w_hi = __reduce_max_sync(0xffffffffu, bhi);
+                const int w_lo = __reduce_min_sync(0xffffffffu, bhi > blo ? blo : 1 << 20);
                 const uint32_t lane_base = tmem + ((uint32_t)(32 * q4) << 16);
 #pragma unroll 1
-                for (int cchunk = quarter; cchunk < 5; cchunk += 4) {
-                    const int c0 = 32 * cchunk;
-                    uint32_t gm[32], gn[32];
-                    TMEM_LD_32X32B_X32(lane_base + (uint32_t)(q0 * kSlotCols + c0), gm);
-                    TMEM_LD_32X32B_X32(lane_base + (uint32_t)(q1 * kSlotCols + c0), gn);
+                for (int cchunk = quarter; cchunk < kSlotCols / 16; cchunk += 4) {
+                    const int c0 = 16 * cchunk;
+                    if ((c0 >= w_hi || c0 + 16 <= w_lo) && !(wide && c0 >= kCornerCol)) continue;
+                    uint32_t gm[16], gn[16];
+                    TMEM_LD_32X32B_X16(lane_base + (uint32_t)(q0 * kSlotCols + c0), gm);
+                    TMEM_LD_32X32B_X16(lane_base + (uint32_t)(q1 * kSlotCols + c0), gn);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
+                    for (int e = 0; e < 16; ++e) {
                         const int col = c0 + e;
                         if (col < kCornerCol) {
-                            // main Gram: operand rows r (< 128) and col; the missing rows >= 128 are
-                            // the transposes of these columns
-                            if (row_in && col >= dpos && col < end && col != r) {
+                            // main Gram: operand rows r (< 128) and col; the missing rows >= 128 of a
+                            // wide block are the transposes of these columns
+                            if (col >= blo && col < bhi && col != r) {
                                 const float g = __uint_as_float(gm[e]);
                                 offf.add_prod(col >= 128 ? 2.0f * g : g, __uint_as_float(gn[e]));
                             }
@@ -607,45 +949,70 @@ __global__ void __launch_bounds__(kThreads, 1)
                 aborted = true;
             }
             ++it;
-            // reductions: the off-diagonal sum as float-float (FP32 operations; the FP64 pipe is
-            // slow on this part), the statistics in FP64 over the 4 warps that own vectors only
             offf.renorm();
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                FF other;
-                other.hi = __shfl_xor_sync(0xffffffffu, offf.hi, o);
-                other.lo = __shfl_xor_sync(0xffffffffu, offf.lo, o);
-                offf.add(other);
-                offf.renorm();
-            }
-            if (lane == 0) red_off[cw] = make_float2(offf.hi, offf.lo);
-            if (STATS && cw < 4) {
-                sa = warp_sum(sa);
-                ss = warp_sum(ss);
-                sx = warp_sum(sx);
-                sy = warp_sum(sy);
-                if (lane == 0) { red[cw][0] = sa; red[cw][1] = ss; red[cw][2] = sx; red[cw][3] = sy; }
-            }
+            rowpart[quarter][r] = make_float2(offf.hi, offf.lo);
             conv_sync(cs_bar, cs_uses, &s_abort);
-            if (t == 0) {
-                FF off_sum;
-                off_sum.zero();
-                for (int w = 0; w < kConvWarps; ++w) {
-                    FF o;
-                    o.hi = red_off[w].x;
-                    o.lo = red_off[w].y;
-                    off_sum.add(o);
-                    off_sum.renorm();
+            // per block of the window: warp cw takes blocks cw, cw + 16, ...; its lanes run over the
+            // block's vectors from the block's first, so the sums do not depend on where the block
+            // sits in its window.  Off-diagonal sums as float-float (FP32 operations: the FP64 pipe
+            // is slow on this part), the statistics in FP64.
+            for (int j = cw; j < nblk; j += kConvWarps) {
+                const int b0 = s_seg[j], b1 = s_seg[j + 1];
+                const long long k = kb + j;
+                const bool ok = b0 >= 0 && b1 > b0 && b1 <= nk;
+                FF off;
+                off.zero();
+                double sa = 0.0, ss = 0.0, sx = 0.0, sy = 0.0;
+                if (ok) {
+                    for (int i = b0 + lane; i < b1; i += 32) {
+                        const int rr = dpos + i;
+                        if (rr < 128) {
+#pragma unroll
+                            for (int qq = 0; qq < 4; ++qq) {
+                                FF o;
+                                o.hi = rowpart[qq][rr].x;
+                                o.lo = rowpart[qq][rr].y;
+                                off.add(o);
+                                off.renorm();
+                            }
+                        }
+                        if (STATS) {
+                            const double xi = xy_sum[0][i], yi = xy_sum[STATS ? 1 : 0][i];
+                            const double xy = __dmul_rn(xi, yi);
+                            sa += sqrt(xy);
+                            ss += xy;
+                            sx += xi;
+                            sy += yi;
+                        }
+                    }
                 }
-                double r4[4] = {0, 0, 0, 0};
-                if (STATS)
-                    for (int w = 0; w < 4; ++w)
-                        for (int c = 0; c < 4; ++c) r4[c] += red[w][c];
-                const double sk = STATS ? r4[1] : pr.s[k];
-                if (STATS) { pr.a[k] = r4[0]; pr.s[k] = r4[1]; pr.mf[k] = r4[2]; pr.nf[k] = r4[3]; }
-                pr.f[k] = sk + off_sum.value();
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    FF other;
+                    other.hi = __shfl_xor_sync(0xffffffffu, off.hi, o);
+                    other.lo = __shfl_xor_sync(0xffffffffu, off.lo, o);
+                    off.add(other);
+                    off.renorm();
+                }
+                if (STATS) {
+                    sa = warp_sum(sa);
+                    ss = warp_sum(ss);
+                    sx = warp_sum(sx);
+                    sy = warp_sum(sy);
+                }
+                if (lane == 0) {
+                    if (!ok) {
+                        set_status(pr.st, BMM_ERR_SHAPE, (int)k);
+                        if (STATS) { pr.a[k] = 0.0; pr.s[k] = 0.0; pr.mf[k] = 0.0; pr.nf[k] = 0.0; }
+                        pr.f[k] = 0.0;
+                    } else {
+                        const double sk = STATS ? ss : pr.s[k];
+                        if (STATS) { pr.a[k] = sa; pr.s[k] = ss; pr.mf[k] = sx; pr.nf[k] = sy; }
+                        pr.f[k] = sk + off.value();
+                    }
+                }
             }
-            conv_sync(cs_bar, cs_uses, &s_abort);  // xy_sum[] and red[] are reused by the next block
+            conv_sync(cs_bar, cs_uses, &s_abort);  // xy_sum[], rowpart[] and s_seg[] are reused by the next window
             if (lane == 0) mbar_arrive(smem_u32(&bar_bempty[bslot]));
             if (++bslot == kBlockSlots) { bslot = 0; bph ^= 1u; }
         }
@@ -689,8 +1056,9 @@ template <typename T>
 bool maps_of(OperandMaps& om, const VecSet& v) {
     const bool strided = v.mode == VEC_STRIDED;
     const int64_t rows = strided ? v.len : v.count, cols = strided ? v.count : v.len;
-    for (int g = 0; g < kMaxKMaps; ++g)
-        if (!make_map<T>(&om.map[g], v.data, rows, cols, v.ld, strided, strided ? kMnRows : 32 * (g + 1))) return false;
+    for (int g = 0; g < (strided ? 2 : kMaxKMaps); ++g)
+        if (!make_map<T>(&om.map[g], v.data, rows, cols, v.ld, strided, strided ? kMnRows << g : 32 * (g + 1)))
+            return false;
     return true;
 }
 
@@ -704,6 +1072,7 @@ bool fill_problem(StatsProblem* pr, const StatsArgs& g) {
     pr->p = g.vN.len;
     pr->x = g.x; pr->y = g.y; pr->a = g.a; pr->s = g.s; pr->mf = g.mf; pr->nf = g.nf; pr->f = g.f;
     pr->st = g.st;
+    pr->wins = g.wins;
     pr->M_strided = g.vM.mode == VEC_STRIDED;
     pr->N_strided = g.vN.mode == VEC_STRIDED;
     return true;
@@ -718,7 +1087,9 @@ cudaError_t launch_table(const StatsTable<G>& tab, int* counter, cudaStream_t s)
         attr = true;
     }
     if (tab.total_blocks == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    // the windows of every product (and the zeroed work counter), then the pass over them
+    (count_launch(), stats_windows_kernel<T, G><<<tab.count, kWinThreads, 0, s>>>(tab, counter));
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
@@ -734,7 +1105,6 @@ cudaError_t launch_grouped_t(const StatsArgs* args, int64_t count, int* counter,
         StatsTable<1> one;
         one.count = 1;
         if (!fill_problem<T>(&one.prob[0], args[0])) return cudaErrorInvalidValue;
-        one.prob[0].block_begin = 0;
         one.total_blocks = args[0].K;
         return launch_table<T, STATS, 1>(one, counter, s);
     }
@@ -751,7 +1121,6 @@ cudaError_t launch_grouped_t(const StatsArgs* args, int64_t count, int* counter,
         if (i == count) break;
         StatsProblem& pr = tab.prob[tab.count];
         if (!fill_problem<T>(&pr, args[i])) return cudaErrorInvalidValue;
-        pr.block_begin = tab.total_blocks;
         tab.total_blocks += args[i].K;
         ++tab.count;
     }
@@ -771,9 +1140,9 @@ bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk)
 }
 
 cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n,
-                                 bool stats, int* counter, double* x, double* y, double* a, double* ssum, double* mf,
-                                 double* nf, double* f, DevStatus* st, cudaStream_t s) {
-    const StatsArgs g{vM, vN, off, K, n, x, y, a, ssum, mf, nf, f, st};
+                                 bool stats, int* counter, int* wins, double* x, double* y, double* a, double* ssum,
+                                 double* mf, double* nf, double* f, DevStatus* st, cudaStream_t s) {
+    const StatsArgs g{vM, vN, off, K, n, x, y, a, ssum, mf, nf, f, st, wins};
     return launch_blockstats_tc_grouped(&g, 1, stats, counter, s);
 }
 

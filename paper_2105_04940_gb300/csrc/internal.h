@@ -59,14 +59,16 @@ struct StatsArgs {
     int64_t K, n;
     double *x, *y, *a, *s, *mf, *nf, *f;
     DevStatus* st;
+    int* wins;  // workspace, stats_windows_ints(K) ints
 };
+inline int64_t stats_windows_ints(int64_t K) { return K + 2; }
 // Many products (each supported by blockstats_tc_supported) in launches of up to ~19 products of
 // one element type, every launch's CTAs sharing one work counter over all its blocks.
 cudaError_t launch_blockstats_tc_grouped(const StatsArgs* args, int64_t count, bool stats, int* counter, cudaStream_t s);
 // stats = true: writes x, y, a, ssum, mf, nf and f; stats = false: reads ssum, writes f only
 cudaError_t launch_blockstats_tc(const VecSet& vM, const VecSet& vN, const int64_t* off, int64_t K, int64_t n,
-                                 bool stats, int* counter, double* x, double* y, double* a, double* ssum, double* mf,
-                                 double* nf, double* f, DevStatus* st, cudaStream_t s);
+                                 bool stats, int* counter, int* wins, double* x, double* y, double* a, double* ssum,
+                                 double* mf, double* nf, double* f, DevStatus* st, cudaStream_t s);
 
 // ---- design.cu
 cudaError_t launch_probs(int kind, const double* x, const double* y, const double* a, const double* mf,

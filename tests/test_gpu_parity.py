@@ -124,12 +124,13 @@ def test_fused_statistics_and_tensor_core_f(bmm, layouts, p, dtype):
     launches = bmm._abi.bmm_launch_count()
     bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, pv, prob.st, prob.ws)
     bmm.check_status(prob)
-    # the fused pass is one kernel (plus the probabilities); odd leading dimensions fall back
+    # the fused pass is one kernel after the window pass (plus the probabilities); odd leading
+    # dimensions fall back
     ld_m = n if layouts[0] == "row" else m
     ld_n = p if layouts[1] == "row" else n
     align = 4 if dtype is np.float32 else 8
     fused = ld_m % align == 0 and ld_n % align == 0
-    assert (bmm._abi.bmm_launch_count() - launches == 2) == fused
+    assert (bmm._abi.bmm_launch_count() - launches == 3) == fused
     x, y = oracle.col_row_sq_norms(M, N)
     st = oracle.block_stats(x, y, off)
     assert rel_err(host(prob.st["x"]), x) < 1e-12
@@ -180,7 +181,7 @@ def test_fused_statistics_offsets_wide_and_low_rank_blocks(bmm, layouts, dtype):
     launches = bmm._abi.bmm_launch_count()
     bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, None, prob.st, prob.ws)
     bmm.check_status(prob)
-    assert bmm._abi.bmm_launch_count() - launches == 1  # the fused pass alone (no p requested)
+    assert bmm._abi.bmm_launch_count() - launches == 2  # the window pass and the fused pass (no p requested)
     x, y = oracle.col_row_sq_norms(M, N)
     st = oracle.block_stats(x, y, off)
     assert rel_err(host(prob.st["x"]), x) < 1e-12
@@ -192,6 +193,45 @@ def test_fused_statistics_offsets_wide_and_low_rank_blocks(bmm, layouts, dtype):
     round_in = 2.0 ** -9 if dtype is np.float32 else 0.0
     assert np.all(err <= _tf32_gram_bound(M, N, off, m, p, round_in) + 1e-12 * f)
     # the Gram-only form (statistics reused) gives the same f
+    f_fused = host(prob.st["f"]).copy()
+    prob.st["f"].zero_()
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_BLK_PRODNORM, bmm._abi.F_TC | bmm._abi.REUSE_STATS, None, prob.st, prob.ws)
+    bmm.check_status(prob)
+    assert np.array_equal(host(prob.st["f"]), f_fused)
+
+
+@pytest.mark.parametrize("layouts", [("row", "row"), ("col", "row")])
+@pytest.mark.parametrize("dtype", [np.float32, "bf16"])
+def test_fused_statistics_packed_small_blocks(bmm, layouts, dtype):
+    """Consecutive small blocks share one 128-vector MMA tile (a window): 5000 blocks of 1..8
+    vectors, more than two passes of the window search, with wide blocks (121..128 vectors) that
+    stay alone.  Per-block statistics and f_k as the oracle, in the fused and Gram-only forms."""
+    rng = np.random.default_rng(11)
+    sizes = rng.integers(1, 9, size=5000)
+    sizes[rng.choice(5000, size=12, replace=False)] = rng.integers(121, 129, size=12)
+    align = 4 if dtype is np.float32 else 8
+    sizes[-1] += (-int(sizes.sum())) % align  # row-major M needs ld = n aligned to 16 bytes
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n, m, p = int(off[-1]), 40, 72
+    M = rng.standard_normal((m, n)).astype(np.float32)
+    N = rng.standard_normal((n, p)).astype(np.float32)
+    tdt = torch.float32 if dtype is np.float32 else torch.bfloat16
+    Mt = as_layout(to_dev(M, tdt), layouts[0])
+    Nt = as_layout(to_dev(N, tdt), layouts[1])
+    M, N = host(Mt.double()), host(Nt.double())
+    prob = bmm.prepare(Mt, Nt, off, max_draws=50)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_TC, None, prob.st, prob.ws)
+    bmm.check_status(prob)
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    assert rel_err(host(prob.st["x"]), x) < 1e-12
+    assert rel_err(host(prob.st["y"]), y) < 1e-12
+    for k in ("a", "s", "mf", "nf"):
+        assert rel_err(host(prob.st[k]), st[k]) < 1e-12, k
+    f = oracle.block_frob_sq(M, N, off)
+    round_in = 2.0 ** -9 if dtype is np.float32 else 0.0
+    bound = _tf32_gram_bound(M, N, off, m, p, round_in)
+    assert np.all(np.abs(host(prob.st["f"]) - f) <= bound + 1e-12 * f)
     f_fused = host(prob.st["f"]).copy()
     prob.st["f"].zero_()
     bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_BLK_PRODNORM, bmm._abi.F_TC | bmm._abi.REUSE_STATS, None, prob.st, prob.ws)
