@@ -6,8 +6,9 @@ N(0,1) * s_k with s_k ~ LogNormal(0, 1.5) shared by column block k of M and row 
 K = 1024 blocks with sizes drawn uniformly from {16..128} and adjusted to sum to n; c = K/8 = 128
 blocks, i.e. L = round(c n / K) = 8192 outer products for the Alg. 2 methods.
 
-A step is one approximate product by the A-optimal method (OPL: norm pass, ||M^k N_k||_F^2 from
-TF32 tcgen05 Grams, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
+A step is one approximate product by the A-optimal method (OPL: one statistics pass giving the
+column and row norms and ||M^k N_k||_F^2 -- exact float-float squares plus the off-diagonal terms of
+TF32 tcgen05 Grams --, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
 BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flush is
 needed).  Prints one JSON line.  --impl reference times the FP64 CPU oracle instead;
 --workload batched runs the 512-product batched workload instead.
@@ -35,16 +36,16 @@ SMALL = dict(m=256, n=4096, p=256, K=64, nk_lo=64, nk_hi=64, sigma=1.0, c_blocks
 # profiling case: the large workload's n, K and blocks with m = p = 2048 (inputs 1 GB, > L2)
 PROFILE = dict(WORKLOAD, m=2048, p=2048)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
-# committed ncu capture (profiles/ncu_gram_pass_and_gemm_profilecase.md): 1.0786 GB on the
-# profiling case (m = p = 2048), which streams the inputs once; the full workload streams
-# (8192 + 8192) / (2048 + 2048) = 4x those bytes.
-TRAFFIC = {"gram_f": 4 * 1.0786e9}
+# committed ncu capture (profiles/ncu_fused_stats_and_gemm_profilecase.md) of the fused statistics
+# pass: 1.0775 GB read + 12.0 MB written on the profiling case (m = p = 2048), which streams the
+# inputs once; the full workload reads (8192 + 8192) / (2048 + 2048) = 4x those bytes.
+TRAFFIC = {"stats_f": 4 * 1.0775e9 + 12.0e6}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--method", default="OPL")
@@ -56,7 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-error", action="store_true")
-    ap.add_argument("--fused-stats", action="store_true", help="statistics and f_k in one pass (OPL, WU)")
+    ap.add_argument("--split-stats", action="store_true",
+                    help="single product: norm pass, then the Gram-only f_k pass (default: one fused pass)")
+    ap.add_argument("--fused-stats", action="store_true",
+                    help="batched workload: statistics and f_k in one grouped pass per table of products")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp", "precision"],
                     help="batched: 512 independent BF16 products of uneven shapes in one CUDA graph; "
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
@@ -277,7 +281,7 @@ def native_arm(args, ws, rank, local):
 
     def step(s, events=None):
         return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events,
-                     fused_stats=args.fused_stats)
+                     fused_stats=not args.split_stats)
 
     for s in range(args.warmup):
         step(10_000 + s)

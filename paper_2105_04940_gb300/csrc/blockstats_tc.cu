@@ -277,9 +277,10 @@ __device__ __forceinline__ bool squares_strided(const uint8_t* base, const Stage
     const int box = cg >> 3;
     const int h0 = hp + rps * cw;
     const int lane_off = box * box_bytes + TR::mn_chunk_offset(h0, cg & 7);
-    FF acc[kCpc], tot[kCpc];
+    // element u of the chunk goes to half u & 1 of pair u / 2 (two vectors per paired sum)
+    FF2 acc[kCpc / 2], tot[kCpc / 2];
 #pragma unroll
-    for (int u = 0; u < kCpc; ++u) { acc[u].zero(); tot[u].zero(); }
+    for (int u = 0; u < kCpc / 2; ++u) { acc[u].zero(); tot[u].zero(); }
     int since_fold = 0;
     while (true) {
         if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
@@ -293,10 +294,8 @@ __device__ __forceinline__ bool squares_strided(const uint8_t* base, const Stage
                     const uint4 w4 = *reinterpret_cast<const uint4*>(src + r * step_bytes);
                     const T* e = reinterpret_cast<const T*>(&w4);
 #pragma unroll
-                    for (int u = 0; u < kCpc; ++u) {
-                        const float v = TR::to_f(e[u]);
-                        acc[u].add_prod(v, v);
-                    }
+                    for (int u = 0; u < kCpc / 2; ++u)
+                        acc[u].add_sq(make_float2(TR::to_f(e[2 * u]), TR::to_f(e[2 * u + 1])));
                 }
             }
         }
@@ -304,10 +303,10 @@ __device__ __forceinline__ bool squares_strided(const uint8_t* base, const Stage
         if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
         if (++stage == kStages) { stage = 0; ph ^= 1u; }
 #pragma unroll
-        for (int u = 0; u < kCpc; ++u) acc[u].renorm();
+        for (int u = 0; u < kCpc / 2; ++u) acc[u].renorm();
         if (++since_fold == kFoldStages || last) {
 #pragma unroll
-            for (int u = 0; u < kCpc; ++u) {
+            for (int u = 0; u < kCpc / 2; ++u) {
                 tot[u].add(acc[u]);
                 tot[u].renorm();
                 acc[u].zero();
@@ -319,10 +318,12 @@ __device__ __forceinline__ bool squares_strided(const uint8_t* base, const Stage
     // the rps lanes of a chunk combine their rows
     for (int o = lpr; o < 32; o <<= 1) {
 #pragma unroll
-        for (int u = 0; u < kCpc; ++u) {
-            FF other;
-            other.hi = __shfl_xor_sync(0xffffffffu, tot[u].hi, o);
-            other.lo = __shfl_xor_sync(0xffffffffu, tot[u].lo, o);
+        for (int u = 0; u < kCpc / 2; ++u) {
+            FF2 other;
+            other.hi.x = __shfl_xor_sync(0xffffffffu, tot[u].hi.x, o);
+            other.hi.y = __shfl_xor_sync(0xffffffffu, tot[u].hi.y, o);
+            other.lo.x = __shfl_xor_sync(0xffffffffu, tot[u].lo.x, o);
+            other.lo.y = __shfl_xor_sync(0xffffffffu, tot[u].lo.y, o);
             tot[u].add(other);
             tot[u].renorm();
         }
@@ -331,7 +332,8 @@ __device__ __forceinline__ bool squares_strided(const uint8_t* base, const Stage
 #pragma unroll
         for (int u = 0; u < kCpc; ++u) {
             const int i = kCpc * cg + u - d;
-            if (i >= 0 && i < nk) part[cw][i] = make_float2(tot[u].hi, tot[u].lo);
+            const FF h = tot[u >> 1].half(u & 1);
+            if (i >= 0 && i < nk) part[cw][i] = make_float2(h.hi, h.lo);
         }
     }
     return true;
@@ -350,65 +352,54 @@ __device__ __forceinline__ bool squares_contig(const uint8_t* base, const StageI
     const int q = t & 7, r0 = t >> 3;
     const int sw = (q ^ (r0 & 7)) << 4;  // (r0 + 64) mod 8 == r0 mod 8
     const bool in0 = r0 >= d && r0 < d + nk, in1 = r0 + 64 >= d && r0 + 64 < d + nk;
-    FF acc[2], tot[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) { acc[u].zero(); tot[u].zero(); }
+    // half 0: row r0, half 1: row r0 + 64; a row outside the block adds zeros, which leave its
+    // half unchanged, so each half equals the sum it would have been alone
+    FF2 acc, tot;
+    acc.zero();
+    tot.zero();
     int since_fold = 0;
     while (true) {
         if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
         const int nsub = info[stage].nsub, sub_bytes = info[stage].sub_bytes;
         const bool last = info[stage].flags & ST_LAST;
         const uint8_t* tile = base + stage * kStageBytes + r0 * kRowBytes + sw;
-        for (int s = 0; s < nsub; ++s) {
-            const uint8_t* sub = tile + s * sub_bytes;
-            if (in0) {
-                const uint4 w4 = *reinterpret_cast<const uint4*>(sub);
-                const T* e = reinterpret_cast<const T*>(&w4);
+        if (in0 || in1) {
+            for (int s = 0; s < nsub; ++s) {
+                const uint8_t* sub = tile + s * sub_bytes;
+                const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+                const uint4 a4 = in0 ? *reinterpret_cast<const uint4*>(sub) : z4;
+                const uint4 b4 = in1 ? *reinterpret_cast<const uint4*>(sub + 64 * kRowBytes) : z4;
+                const T* ea = reinterpret_cast<const T*>(&a4);
+                const T* eb = reinterpret_cast<const T*>(&b4);
 #pragma unroll
-                for (int u = 0; u < kCpc; ++u) {
-                    const float v = TR::to_f(e[u]);
-                    acc[0].add_prod(v, v);
-                }
-            }
-            if (in1) {
-                const uint4 w4 = *reinterpret_cast<const uint4*>(sub + 64 * kRowBytes);
-                const T* e = reinterpret_cast<const T*>(&w4);
-#pragma unroll
-                for (int u = 0; u < kCpc; ++u) {
-                    const float v = TR::to_f(e[u]);
-                    acc[1].add_prod(v, v);
-                }
+                for (int u = 0; u < kCpc; ++u) acc.add_sq(make_float2(TR::to_f(ea[u]), TR::to_f(eb[u])));
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
         if (++stage == kStages) { stage = 0; ph ^= 1u; }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) acc[u].renorm();
+        acc.renorm();
         if (++since_fold == kFoldStages || last) {
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                tot[u].add(acc[u]);
-                tot[u].renorm();
-                acc[u].zero();
-            }
+            tot.add(acc);
+            tot.renorm();
+            acc.zero();
             since_fold = 0;
         }
         if (last) break;
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            FF other;
-            other.hi = __shfl_xor_sync(0xffffffffu, tot[u].hi, o);
-            other.lo = __shfl_xor_sync(0xffffffffu, tot[u].lo, o);
-            tot[u].add(other);
-            tot[u].renorm();
-        }
+    for (int o = 1; o < 8; o <<= 1) {
+        FF2 other;
+        other.hi.x = __shfl_xor_sync(0xffffffffu, tot.hi.x, o);
+        other.hi.y = __shfl_xor_sync(0xffffffffu, tot.hi.y, o);
+        other.lo.x = __shfl_xor_sync(0xffffffffu, tot.lo.x, o);
+        other.lo.y = __shfl_xor_sync(0xffffffffu, tot.lo.y, o);
+        tot.add(other);
+        tot.renorm();
+    }
     if (q == 0) {
-        if (in0) xy[r0 - d] = tot[0].value();
-        if (in1) xy[r0 + 64 - d] = tot[1].value();
+        if (in0) xy[r0 - d] = tot.half(0).value();
+        if (in1) xy[r0 + 64 - d] = tot.half(1).value();
     }
     return true;
 }

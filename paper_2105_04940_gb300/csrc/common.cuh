@@ -74,6 +74,42 @@ struct FF {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Two independent float-float sums in paired FP32 registers: every operation is the one of FF
+// applied to both halves with the sm_100+ two-wide FP32 instructions (one issue slot for two
+// rounded operations), so each half is bit-identical to an FF that saw the same terms.
+struct FF2 {
+    float2 hi, lo;
+    static __device__ __forceinline__ float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
+    __device__ __forceinline__ void zero() { hi = make_float2(0.f, 0.f); lo = hi; }
+    __device__ __forceinline__ void add_sq(float2 v) {
+        const float2 pr = __fmul2_rn(v, v);
+        const float2 pe = __ffma2_rn(v, v, neg(pr));
+        const float2 t = __fadd2_rn(hi, pr);
+        const float2 bp = __fadd2_rn(t, neg(hi));
+        const float2 e = __fadd2_rn(__fadd2_rn(hi, neg(__fadd2_rn(t, neg(bp)))), __fadd2_rn(pr, neg(bp)));
+        hi = t;
+        lo = __fadd2_rn(lo, __fadd2_rn(e, pe));
+    }
+    __device__ __forceinline__ void renorm() {
+        const float2 s = __fadd2_rn(hi, lo);
+        lo = __fadd2_rn(lo, neg(__fadd2_rn(s, neg(hi))));
+        hi = s;
+    }
+    __device__ __forceinline__ void add(const FF2& o) {
+        const float2 t = __fadd2_rn(hi, o.hi);
+        const float2 bp = __fadd2_rn(t, neg(hi));
+        const float2 e = __fadd2_rn(__fadd2_rn(hi, neg(__fadd2_rn(t, neg(bp)))), __fadd2_rn(o.hi, neg(bp)));
+        hi = t;
+        lo = __fadd2_rn(lo, __fadd2_rn(e, o.lo));
+    }
+    __device__ __forceinline__ FF half(int i) const {
+        FF r;
+        r.hi = i ? hi.y : hi.x;
+        r.lo = i ? lo.y : lo.x;
+        return r;
+    }
+};
+
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
 struct U4 { uint32_t x, y, z, w; };

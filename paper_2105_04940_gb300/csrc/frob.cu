@@ -181,10 +181,123 @@ static cudaError_t gram_frob_t(const VecSet& U, const VecSet& V, const int64_t* 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- small pilots
+// The Alg. 3 pilot with few draws per block (per <= kPilotMax, e.g. c0 = 4 K): one CTA per block
+// k keeps every pair product <u_a, u_b>, <v_a, v_b> (a <= b < P) of its drawn vectors in registers,
+// each thread summing a strided share of the coordinates in float-float (FP64 for FP64 data) and
+// folding into FP64 every kPilotFold coordinates; the shares are summed in FP64 across the CTA and
+// thread 0 forms f^_k = sum_{a,b} w_a w_b <u_a, u_b> <v_a, v_b>.  Rounding per up to P, so draws
+// past per are empty vectors of weight 0.  Reads only the drawn vectors, once.
+constexpr int kPilotMax = 8;
+constexpr int kPilotThreads = 256;
+constexpr int kPilotFold = 64;
+
+template <int P> struct PilotPairs { static constexpr int n = P * (P + 1) / 2; };
+
+template <typename T, int P>
+__device__ __forceinline__ void pilot_gram(const T* __restrict__ X, int64_t len, int64_t ld, int mode,
+                                           const int64_t* idx, double (*red)[kPilotThreads / 32], double* out) {
+    constexpr int NP = PilotPairs<P>::n;
+    DotAcc32 acc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc[q].init();
+    int since = 0;
+    for (int64_t h = threadIdx.x; h < len; h += kPilotThreads) {
+        typename AccT<T>::type v[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            v[a] = 0;
+            if (idx[a] >= 0) v[a] = ld_as(mode == VEC_CONTIG ? X + idx[a] * ld + h : X + h * ld + idx[a]);
+        }
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a)
+#pragma unroll
+            for (int b = a; b < P; ++b) acc[q++].add(v[a], v[b]);
+        if (++since == kPilotFold) {
+#pragma unroll
+            for (int qq = 0; qq < NP; ++qq) acc[qq].fold();
+            since = 0;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const double w = warp_sum(acc[q].value());
+        if (lane == 0) red[q][warp] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < NP) {
+        double s = 0.0;
+        for (int w = 0; w < kPilotThreads / 32; ++w) s += red[threadIdx.x][w];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kPilotThreads)
+    pilot_frob_kernel(const T* __restrict__ U, int64_t lenU, int64_t ldU, int modeU, const T* __restrict__ V,
+                      int64_t lenV, int64_t ldV, int modeV, int64_t n_vec, const int32_t* __restrict__ cols,
+                      const double* __restrict__ wts, int per, double* __restrict__ f, DevStatus* st) {
+    constexpr int NP = PilotPairs<P>::n;
+    __shared__ int64_t s_idx[P];
+    __shared__ double s_w[P];
+    __shared__ double red[NP][kPilotThreads / 32];
+    __shared__ double gu[NP], gv[NP];
+    const int64_t k = blockIdx.x;
+    if (threadIdx.x < P) {
+        int64_t id = -1;
+        double w = 0.0;
+        if ((int)threadIdx.x < per) {
+            id = cols[k * per + threadIdx.x];
+            w = wts[k * per + threadIdx.x];
+            if (id < 0 || id >= n_vec) { set_status(st, BMM_ERR_ARG, (int)k); id = -1; w = 0.0; }
+        }
+        s_idx[threadIdx.x] = id;
+        s_w[threadIdx.x] = w;
+    }
+    __syncthreads();
+    pilot_gram<T, P>(U, lenU, ldU, modeU, s_idx, red, gu);
+    pilot_gram<T, P>(V, lenV, ldV, modeV, s_idx, red, gv);
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        int q = 0;
+        for (int a = 0; a < P; ++a)
+            for (int b = a; b < P; ++b, ++q) s += (a == b ? 1.0 : 2.0) * s_w[a] * s_w[b] * gu[q] * gv[q];
+        f[k] = s;
+    }
+}
+
+template <typename T, int P>
+static cudaError_t pilot_frob_t(const VecSet& U, const VecSet& V, int64_t K, const int32_t* cols, const double* wts,
+                                int per, double* f, DevStatus* st, cudaStream_t s) {
+    (count_launch(), pilot_frob_kernel<T, P><<<(unsigned)K, kPilotThreads, 0, s>>>(
+                         static_cast<const T*>(U.data), U.len, U.ld, U.mode, static_cast<const T*>(V.data), V.len, V.ld,
+                         V.mode, U.count, cols, wts, per, f, st));
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t pilot_frob_any(const VecSet& U, const VecSet& V, int64_t K, const int32_t* cols, const double* wts,
+                                  int per, double* f, DevStatus* st, cudaStream_t s) {
+    if (per <= 1) return pilot_frob_t<T, 1>(U, V, K, cols, wts, per, f, st, s);
+    if (per <= 2) return pilot_frob_t<T, 2>(U, V, K, cols, wts, per, f, st, s);
+    if (per <= 4) return pilot_frob_t<T, 4>(U, V, K, cols, wts, per, f, st, s);
+    return pilot_frob_t<T, kPilotMax>(U, V, K, cols, wts, per, f, st, s);
+}
+
 cudaError_t launch_gram_frob(const VecSet& U, const VecSet& V, const int64_t* off, int64_t K, int64_t max_len,
                              const int32_t* cols, const double* wts, int64_t per, double* f, double* partial,
                              int64_t partial_cap, DevStatus* st, cudaStream_t s) {
     if (K <= 0) return cudaSuccess;
+    if (cols != nullptr && per >= 1 && per <= kPilotMax && K <= 2147483647LL) {
+        switch (U.dtype) {
+            case BMM_F64: return pilot_frob_any<double>(U, V, K, cols, wts, (int)per, f, st, s);
+            case BMM_F32: return pilot_frob_any<float>(U, V, K, cols, wts, (int)per, f, st, s);
+            default: return pilot_frob_any<__nv_bfloat16>(U, V, K, cols, wts, (int)per, f, st, s);
+        }
+    }
     if (partial_cap < gram_frob_partial_elems(K, cols ? per : max_len)) return cudaErrorInvalidValue;
     if (K > 2147483647LL || tiles_for(cols ? per : max_len) > 362) return cudaErrorInvalidValue;
     switch (U.dtype) {

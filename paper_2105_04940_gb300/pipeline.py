@@ -123,12 +123,13 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
 
 def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
         gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None,
-        fmode: int = A.F_TC, fused_stats: bool = False, p_ready=None) -> dict:
+        fmode: int = A.F_TC, fused_stats: bool = True, p_ready=None) -> dict:
     """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring).
 
     fmode: how OPL and WU compute ||M^k N_k||_F^2 -- A.F_TC (tensor-core Grams when the inputs
-    allow it, else exact) or A.F_EXACT.  fused_stats: with F_TC, one pass computes the statistics
-    and f together; otherwise the norm pass runs first and the Gram pass reuses its statistics.
+    allow it, else exact) or A.F_EXACT.  fused_stats (default): with F_TC, one pass computes the
+    statistics and f together; otherwise the norm pass runs first and the Gram pass reuses its
+    statistics (two reads of M and N, slower on one large product).
 
     events: if a list, (stage name, torch.cuda.Event) pairs are appended at the stage
     boundaries (recorded on the current stream; used for timing only).

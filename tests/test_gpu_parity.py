@@ -477,6 +477,24 @@ def test_tilde_block_sizes_from_pilot(bmm):
     np.testing.assert_array_equal(host(r["ck"]), oracle.apportion(oracle.g_with_fallback(g, st["a"], np.diff(off)), np.diff(off), 600))
 
 
+@pytest.mark.parametrize("per", [1, 3, 4, 8, 9])
+@pytest.mark.parametrize("dtype,layout", [(np.float32, "row"), (np.float32, "col"), ("bf16", "row"), (np.float64, "row")])
+def test_pilot_fhat_small_and_tiled(bmm, per, dtype, layout):
+    """Alg. 3 pilot f^_k with 1..8 draws per block (the one-CTA-per-block kernel, rounded up to
+    1, 2, 4 or 8 vectors) and 9 (the tiled kernel), every storage order of M and element type."""
+    off, M, N, Mt, Nt = _problem(300, 2200, 170, 20, seed=31, dtype=dtype, lo=40, hi=180)
+    Mt = as_layout(Mt, layout)
+    K = len(off) - 1
+    prob = bmm.prepare(Mt, Nt, off, max_draws=800)
+    r = bmm.run(prob, "ONU", 400, seed=5, c0=per * K, gemm_mode=bmm._abi.GEMM_F64)
+    bmm.check_status(prob)
+    fh_or, idx_or, sc_or = oracle.pilot_frob_sq(M, N, off, oracle.p_col_uniform(off), per, seed=5,
+                                                sid=oracle.stream_id(0, oracle.PURPOSE_PILOT))
+    np.testing.assert_array_equal(host(r["pilot_idx"]), idx_or)
+    np.testing.assert_array_equal(host(r["pilot_scale"]), sc_or)
+    assert rel_err(host(r["fhat"]), fh_or) < 1e-10
+
+
 # ---------------------------------------------------------------- adjoint
 @pytest.mark.parametrize("mode", ["f64", "bf16"])
 @pytest.mark.parametrize("unit", ["column", "block"])
