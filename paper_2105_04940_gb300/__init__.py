@@ -7,13 +7,13 @@ torch.autograd.Function (``pipeline``).  There is no CPU path: without a CUDA de
 without the built library every call raises.
 """
 from . import _abi
-from ._abi import (BmmError, bmm_apply, bmm_backward, bmm_blocksizes, bmm_clear_device_status, bmm_probs,
+from ._abi import (BmmError, bmm_apply, bmm_apply_batched, bmm_backward, bmm_blocksizes, bmm_clear_device_status, bmm_probs,
                    bmm_probs_batched, bmm_read_device_status, bmm_sample, bmm_workspace_size)
 from .pipeline import (METHODS, MODES, Problem, SampledMatmul, check_status, equal_budget, prepare, run, run_batched,
                        sampled_matmul, stream_id)
 
 __all__ = [
-    "BmmError", "bmm_apply", "bmm_backward", "bmm_blocksizes", "bmm_clear_device_status", "bmm_probs", "bmm_probs_batched",
+    "BmmError", "bmm_apply", "bmm_apply_batched", "bmm_backward", "bmm_blocksizes", "bmm_clear_device_status", "bmm_probs", "bmm_probs_batched",
     "bmm_read_device_status", "bmm_sample", "bmm_workspace_size", "METHODS", "MODES", "Problem",
     "SampledMatmul", "check_status", "equal_budget", "prepare", "run", "run_batched", "sampled_matmul",
     "stream_id",

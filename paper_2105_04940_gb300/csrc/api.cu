@@ -460,9 +460,12 @@ namespace bmm {
 namespace {
 // Checks and gathers of one product of bmm_apply / bmm_apply_batched.  On BMM_OK either *done
 // (nothing left to compute) or *g describes the product's GEMM (BF16 modes; FP64 is launched here).
+// With `defer` (bmm_apply_batched), a column-unit BF16 or split-BF16 product launches nothing: its
+// two gathers are appended to *defer for one grouped launch and its GEMM uses the host extent.
 bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit, const int32_t* idx,
                          const double* scale, int64_t count, int32_t gemm_mode, const bmm_mat* out,
-                         int32_t accumulate, void* ws, size_t ws_bytes, cudaStream_t cs, GemmArgs* g, bool* done) {
+                         int32_t accumulate, void* ws, size_t ws_bytes, cudaStream_t cs, GemmArgs* g, bool* done,
+                         std::vector<GatherJob>* defer = nullptr) {
     *done = true;
     bmm_status s = check_problem(M, N, B);
     if (s != BMM_OK) return s;
@@ -488,6 +491,18 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
     DevStatus* dst = status_of(ws);
     const int32_t* col = idx;
     const double* w = scale;
+    const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
+    if (defer != nullptr && unit == BMM_UNIT_COLUMN &&
+        (gemm_mode == BMM_GEMM_BF16 || gemm_mode == BMM_GEMM_SPLIT_BF16)) {
+        defer->push_back(GatherJob{vM, idx, scale, count, gemm_mode, 0, plan.A, plan.ktot, dst});
+        defer->push_back(GatherJob{vN, idx, scale, count, gemm_mode, 1, plan.Bop, plan.ktot, dst});
+        const int k_mult = gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1;
+        *g = GemmArgs{plan.A, plan.ktot, plan.Bop, plan.ktot, M->rows, N->cols, plan.ktot,
+                      k_mult * round_up(count, 64), nullptr, k_mult, static_cast<float*>(odata), out->ld, accumulate,
+                      GEMM_ELEM_BF16, nullptr};
+        *done = false;
+        return BMM_OK;
+    }
     if (unit == BMM_UNIT_COLUMN) {
         BMM_TRY(launch_set_extent(plan.ext, count, cs));
     } else {
@@ -496,7 +511,6 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
         col = plan.col;
         w = plan.w;
     }
-    const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
     if (gemm_mode == BMM_GEMM_E4M3) {
         // column maxima of C and row maxima of D, then their power-of-two scales
         BMM_TRY(cudaMemsetAsync(plan.amaxA, 0, sizeof(float) * plan.lmax, cs));
@@ -547,15 +561,18 @@ BMM_API bmm_status bmm_apply_batched(int64_t count, const bmm_mat* Ms, const bmm
     if (!Ms || !Ns || !Bs || !idx || !scale || !draws || !outs || !ws || !ws_bytes) return BMM_ERR_ARG;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     std::vector<GemmArgs> gemms;
+    std::vector<GatherJob> gathers;
     gemms.reserve((size_t)count);
+    gathers.reserve(2 * (size_t)count);
     for (int64_t i = 0; i < count; ++i) {
         GemmArgs g;
         bool done = true;
         const bmm_status s = apply_prepare(&Ms[i], &Ns[i], &Bs[i], unit, idx[i], scale[i], draws[i], gemm_mode, &outs[i],
-                                           accumulate, ws[i], ws_bytes[i], cs, &g, &done);
+                                           accumulate, ws[i], ws_bytes[i], cs, &g, &done, &gathers);
         if (s != BMM_OK) return s;
         if (!done) gemms.push_back(g);
     }
+    if (!gathers.empty()) BMM_TRY(launch_gather_grouped(gathers.data(), (int64_t)gathers.size(), cs));
     if (!gemms.empty())
         BMM_TRY(launch_gemm_bf16_tc_grouped(gemms.data(), (int64_t)gemms.size(), status_of(ws[0]), cs));
     return BMM_OK;

@@ -93,6 +93,7 @@ template <> struct Tr<float> {
         return h * kRowBytes + ((((c16 >> 1) ^ (h & 3)) << 5) | ((c16 & 1) << 4));
     }
     static __device__ __forceinline__ float to_f(float v) { return v; }
+    static __device__ __forceinline__ void add_sq(FF2& acc, float2 v) { acc.add_sq(v); }
 };
 template <> struct Tr<__nv_bfloat16> {
     static constexpr int E = 64;
@@ -119,6 +120,8 @@ template <> struct Tr<__nv_bfloat16> {
         return h * kRowBytes + ((c16 ^ (h & 7)) << 4);
     }
     static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    // a BF16 value has 8 significant bits, so its square is exact in FP32
+    static __device__ __forceinline__ void add_sq(FF2& acc, float2 v) { acc.add_sq_exact(v); }
 };
 
 // Sub-tiles per stage of a contiguous operand whose sub-tiles are nb groups of 32 vector rows.
@@ -237,7 +240,7 @@ __device__ __forceinline__ void mma_stage(uint32_t d_main, uint32_t d_corner, ui
 }
 
 __device__ __forceinline__ bool wait_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort_flag);
+    return mbar_try_wait_sleep(bar, parity) || mbar_wait<true>(bar, parity, abort_flag);
 }
 
 // Barrier over the converter warps built on an mbarrier, so that its wait is bounded like every
@@ -295,7 +298,7 @@ __device__ __forceinline__ bool squares_strided(const uint8_t* base, const Stage
                     const T* e = reinterpret_cast<const T*>(&w4);
 #pragma unroll
                     for (int u = 0; u < kCpc / 2; ++u)
-                        acc[u].add_sq(make_float2(TR::to_f(e[2 * u]), TR::to_f(e[2 * u + 1])));
+                        TR::add_sq(acc[u], make_float2(TR::to_f(e[2 * u]), TR::to_f(e[2 * u + 1])));
                 }
             }
         }
@@ -352,54 +355,64 @@ __device__ __forceinline__ bool squares_contig(const uint8_t* base, const StageI
     const int q = t & 7, r0 = t >> 3;
     const int sw = (q ^ (r0 & 7)) << 4;  // (r0 + 64) mod 8 == r0 mod 8
     const bool in0 = r0 >= d && r0 < d + nk, in1 = r0 + 64 >= d && r0 + 64 < d + nk;
-    // half 0: row r0, half 1: row r0 + 64; a row outside the block adds zeros, which leave its
-    // half unchanged, so each half equals the sum it would have been alone
-    FF2 acc, tot;
-    acc.zero();
-    tot.zero();
+    // acc[j]: row r0 + 64 j, elements 2u and 2u + 1 of the chunk in the two halves (added at the end)
+    FF2 acc[2], tot[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) { acc[u].zero(); tot[u].zero(); }
     int since_fold = 0;
     while (true) {
         if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
         const int nsub = info[stage].nsub, sub_bytes = info[stage].sub_bytes;
         const bool last = info[stage].flags & ST_LAST;
         const uint8_t* tile = base + stage * kStageBytes + r0 * kRowBytes + sw;
-        if (in0 || in1) {
-            for (int s = 0; s < nsub; ++s) {
-                const uint8_t* sub = tile + s * sub_bytes;
-                const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-                const uint4 a4 = in0 ? *reinterpret_cast<const uint4*>(sub) : z4;
-                const uint4 b4 = in1 ? *reinterpret_cast<const uint4*>(sub + 64 * kRowBytes) : z4;
-                const T* ea = reinterpret_cast<const T*>(&a4);
-                const T* eb = reinterpret_cast<const T*>(&b4);
+        for (int s = 0; s < nsub; ++s) {
+            const uint8_t* sub = tile + s * sub_bytes;
+            if (in0) {
+                const uint4 w4 = *reinterpret_cast<const uint4*>(sub);
+                const T* e = reinterpret_cast<const T*>(&w4);
 #pragma unroll
-                for (int u = 0; u < kCpc; ++u) acc.add_sq(make_float2(TR::to_f(ea[u]), TR::to_f(eb[u])));
+                for (int u = 0; u < kCpc / 2; ++u)
+                    TR::add_sq(acc[0], make_float2(TR::to_f(e[2 * u]), TR::to_f(e[2 * u + 1])));
+            }
+            if (in1) {
+                const uint4 w4 = *reinterpret_cast<const uint4*>(sub + 64 * kRowBytes);
+                const T* e = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+                for (int u = 0; u < kCpc / 2; ++u)
+                    TR::add_sq(acc[1], make_float2(TR::to_f(e[2 * u]), TR::to_f(e[2 * u + 1])));
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
         if (++stage == kStages) { stage = 0; ph ^= 1u; }
-        acc.renorm();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) acc[u].renorm();
         if (++since_fold == kFoldStages || last) {
-            tot.add(acc);
-            tot.renorm();
-            acc.zero();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                tot[u].add(acc[u]);
+                tot[u].renorm();
+                acc[u].zero();
+            }
             since_fold = 0;
         }
         if (last) break;
     }
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        FF2 other;
-        other.hi.x = __shfl_xor_sync(0xffffffffu, tot.hi.x, o);
-        other.hi.y = __shfl_xor_sync(0xffffffffu, tot.hi.y, o);
-        other.lo.x = __shfl_xor_sync(0xffffffffu, tot.lo.x, o);
-        other.lo.y = __shfl_xor_sync(0xffffffffu, tot.lo.y, o);
-        tot.add(other);
-        tot.renorm();
-    }
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            FF2 other;
+            other.hi.x = __shfl_xor_sync(0xffffffffu, tot[u].hi.x, o);
+            other.hi.y = __shfl_xor_sync(0xffffffffu, tot[u].hi.y, o);
+            other.lo.x = __shfl_xor_sync(0xffffffffu, tot[u].lo.x, o);
+            other.lo.y = __shfl_xor_sync(0xffffffffu, tot[u].lo.y, o);
+            tot[u].add(other);
+            tot[u].renorm();
+        }
     if (q == 0) {
-        if (in0) xy[r0 - d] = tot.half(0).value();
-        if (in1) xy[r0 + 64 - d] = tot.half(1).value();
+        if (in0) xy[r0 - d] = tot[0].both().value();
+        if (in1) xy[r0 + 64 - d] = tot[1].both().value();
     }
     return true;
 }

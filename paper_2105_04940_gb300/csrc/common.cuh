@@ -90,6 +90,16 @@ struct FF2 {
         hi = t;
         lo = __fadd2_rn(lo, __fadd2_rn(e, pe));
     }
+    // += v * v when the squares are exact in FP32 (v has at most 12 significant bits, e.g. BF16,
+    // and v * v is a normal number): the TwoProd residual is zero and is left out
+    __device__ __forceinline__ void add_sq_exact(float2 v) {
+        const float2 pr = __fmul2_rn(v, v);
+        const float2 t = __fadd2_rn(hi, pr);
+        const float2 bp = __fadd2_rn(t, neg(hi));
+        const float2 e = __fadd2_rn(__fadd2_rn(hi, neg(__fadd2_rn(t, neg(bp)))), __fadd2_rn(pr, neg(bp)));
+        hi = t;
+        lo = __fadd2_rn(lo, e);
+    }
     __device__ __forceinline__ void renorm() {
         const float2 s = __fadd2_rn(hi, lo);
         lo = __fadd2_rn(lo, neg(__fadd2_rn(s, neg(hi))));
@@ -106,6 +116,13 @@ struct FF2 {
         FF r;
         r.hi = i ? hi.y : hi.x;
         r.lo = i ? lo.y : lo.x;
+        return r;
+    }
+    // the two halves added into one sum
+    __device__ __forceinline__ FF both() const {
+        FF r = half(0);
+        r.add(half(1));
+        r.renorm();
         return r;
     }
 };

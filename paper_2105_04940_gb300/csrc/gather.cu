@@ -148,14 +148,15 @@ struct OpWriter {
 // a run of kGatherRows rows, so the weight's square root is taken once per run.
 constexpr int kGatherRows = 64;
 
+// One CTA's share of a strided gather: operand columns j = 128 bx + thread, rows from 64 by in
+// steps of 64 gy (bx, by, gy: the CTA's place in a (gx, gy) grid of this gather).
 template <typename T, typename V>
-__global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
-                                      const int32_t* __restrict__ col, const double* __restrict__ w,
-                                      const int64_t* __restrict__ ext_dev, bool apply_weight, OpWriter wr,
-                                      DevStatus* st) {
-    const int64_t ext = *ext_dev;
+__device__ __forceinline__ void gather_strided_body(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
+                                                    const int32_t* __restrict__ col, const double* __restrict__ w,
+                                                    int64_t ext, bool apply_weight, OpWriter wr, DevStatus* st,
+                                                    int64_t bx, int64_t by, int64_t gy) {
     const int64_t kseg = round_up(ext, wr.kunit);
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = bx * blockDim.x + threadIdx.x;
     if (j >= kseg) return;
     wr.kseg = kseg;
     int64_t c = -1;
@@ -165,7 +166,7 @@ __global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int6
         sw = wr.colscale != nullptr ? (V)wr.colscale[j] : (apply_weight ? (V)sqrt(w[j]) : V(1));
         if (c < 0 || c >= nvec) { set_status(st, BMM_ERR_ARG, (int)j); c = -1; }
     }
-    for (int64_t r0 = (int64_t)blockIdx.y * kGatherRows; r0 < len; r0 += (int64_t)gridDim.y * kGatherRows) {
+    for (int64_t r0 = by * kGatherRows; r0 < len; r0 += gy * kGatherRows) {
         const int64_t r1 = imin(len, r0 + kGatherRows);
         if (c < 0) {
             for (int64_t r = r0; r < r1; ++r) wr.put(r, j, V(0));
@@ -181,6 +182,15 @@ __global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int6
         }
         for (; r < r1; ++r) wr.put(r, j, ldv<T, V>(X + r * ld + c) * sw);
     }
+}
+
+template <typename T, typename V>
+__global__ void gather_strided_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
+                                      const int32_t* __restrict__ col, const double* __restrict__ w,
+                                      const int64_t* __restrict__ ext_dev, bool apply_weight, OpWriter wr,
+                                      DevStatus* st) {
+    gather_strided_body<T, V>(X, len, ld, nvec, col, w, *ext_dev, apply_weight, wr, st, blockIdx.x, blockIdx.y,
+                              gridDim.y);
 }
 
 // vectors are storage rows: element r of vector i at X[i*ld + r]; 32(j) x 64(r) transpose tiles
@@ -265,18 +275,18 @@ __device__ __forceinline__ void put_fp8x8(const OpWriter& wr, int64_t r, int64_t
 
 // Vectors are storage rows (row-major N): 64 (contraction index j) x 64 (r) tiles through shared
 // memory; rows are read 16 bytes at a time when aligned and the transposed operand is written 8
-// BF16 (16 bytes) at a time.
+// BF16 (16 bytes) at a time.  One CTA (256 threads) handles operand columns 64 bx .. 64 bx + 63
+// and rows from 64 by in steps of 64 gy.
 template <typename T>
-__global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
-    const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec, const int32_t* __restrict__ col,
-    const double* __restrict__ w, const int64_t* __restrict__ ext_dev, bool apply_weight, bool vec4, OpWriter wr,
-    DevStatus* st) {
+__device__ __forceinline__ void gather_contig_bf16_body(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
+                                                        const int32_t* __restrict__ col, const double* __restrict__ w,
+                                                        int64_t ext, bool apply_weight, bool vec4, OpWriter wr,
+                                                        DevStatus* st, int64_t bx, int64_t by, int64_t gy) {
     __shared__ float tile[64][65];
     __shared__ int64_t cidx[64];
     __shared__ float csw[64];
-    const int64_t ext = *ext_dev;
     const int64_t kseg = round_up(ext, wr.kunit);
-    const int64_t j0 = (int64_t)blockIdx.x * 64;
+    const int64_t j0 = bx * 64;
     if (j0 >= kseg) return;
     wr.kseg = kseg;
     const int t = threadIdx.x;
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
         csw[t] = sw;
     }
     __syncthreads();
-    for (int64_t r0 = (int64_t)blockIdx.y * 64; r0 < len; r0 += (int64_t)gridDim.y * 64) {
+    for (int64_t r0 = by * 64; r0 < len; r0 += gy * 64) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int idx = t + 256 * u;
@@ -304,8 +314,15 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
             if (c >= 0) {
                 const T* src = X + c * ld + r;
                 if (vec4 && r + 4 <= len) {
-                    const float4 f4 = __ldg(reinterpret_cast<const float4*>(src));
-                    e[0] = f4.x; e[1] = f4.y; e[2] = f4.z; e[3] = f4.w;
+                    // four consecutive elements in one aligned load (16 bytes FP32, 8 bytes BF16)
+                    if constexpr (std::is_same<T, float>::value) {
+                        const float4 f4 = __ldg(reinterpret_cast<const float4*>(src));
+                        e[0] = f4.x; e[1] = f4.y; e[2] = f4.z; e[3] = f4.w;
+                    } else {
+                        const uint2 u2 = __ldg(reinterpret_cast<const uint2*>(src));
+                        e[0] = __uint_as_float(u2.x << 16); e[1] = __uint_as_float(u2.x & 0xffff0000u);
+                        e[2] = __uint_as_float(u2.y << 16); e[3] = __uint_as_float(u2.y & 0xffff0000u);
+                    }
                 } else {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -334,6 +351,28 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
     }
 }
 
+
+template <typename T>
+__global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
+    const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec, const int32_t* __restrict__ col,
+    const double* __restrict__ w, const int64_t* __restrict__ ext_dev, bool apply_weight, bool vec4, OpWriter wr,
+    DevStatus* st) {
+    gather_contig_bf16_body<T>(X, len, ld, nvec, col, w, *ext_dev, apply_weight, vec4, wr, st, blockIdx.x, blockIdx.y,
+                               gridDim.y);
+}
+
+template <typename T> constexpr int dtype_of();
+template <> constexpr int dtype_of<float>() { return BMM_F32; }
+template <> constexpr int dtype_of<__nv_bfloat16>() { return BMM_BF16; }
+template <> constexpr int dtype_of<double>() { return BMM_F64; }
+
+// rows of X can be read four elements at a time (FP32: 16-byte loads, BF16: 8-byte loads)
+template <typename T>
+static bool contig_vec4(const VecSet& v) {
+    if (!std::is_same<T, float>::value && !std::is_same<T, __nv_bfloat16>::value) return false;
+    return (v.ld % 4) == 0 && (reinterpret_cast<uintptr_t>(v.data) % (4 * sizeof(T))) == 0;
+}
+
 template <typename T, typename V>
 static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
                             int64_t ext_max, int mode, int role, bool apply_weight, void* out, int64_t ldo,
@@ -352,8 +391,7 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
             (count_launch(), gather_strided_kernel<T, V><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev,
                                                                               apply_weight, wr, st));
         } else {
-            const bool vec4 = sizeof(T) == 4 && std::is_same<T, float>::value && (v.ld % 4) == 0 &&
-                              (reinterpret_cast<uintptr_t>(v.data) & 15) == 0;
+            const bool vec4 = contig_vec4<T>(v);
             dim3 grid((unsigned)ceil_div(kmax, 64), (unsigned)imin(imax(ceil_div(v.len, 64), 1), 2048));
             (count_launch(), gather_contig_bf16_kernel<T><<<grid, 256, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev,
                                                                                apply_weight, vec4, wr, st));
@@ -388,6 +426,121 @@ cudaError_t launch_gather_operand(const VecSet& v, const int32_t* col, const dou
     if (mode == BMM_GEMM_F64)
         return gather_v<double>(v, col, w, ext_dev, ext_max, mode, split_role, apply_weight, out, ldo, st, s, colscale);
     return gather_v<float>(v, col, w, ext_dev, ext_max, mode, split_role, apply_weight, out, ldo, st, s, colscale);
+}
+
+// ---------------------------------------------------------------- grouped gathers
+// The gathers of many products in one launch (bmm_apply_batched): a table of jobs travels as a
+// __grid_constant__ kernel parameter, each job a (gx, gy) grid of the single-product kernel laid out
+// one after another along blockIdx.x; a CTA finds its job by binary search over the jobs' first CTAs
+// and runs the same body as the single-product kernel.  Extents are host values here.
+struct GatherJobDev {
+    const void* X;
+    int64_t len, ld, nvec;
+    const int32_t* col;
+    const double* w;
+    int64_t ext;
+    OpWriter wr;
+    DevStatus* st;
+    int gx, gy;
+    int cta_begin;
+    int vec4;
+};
+constexpr int kMaxGatherJobs = 224;  // 136-byte jobs: the table stays under the 32 KB parameter limit
+struct GatherTable {
+    int count;
+    int total;
+    GatherJobDev job[kMaxGatherJobs];
+};
+static_assert(sizeof(GatherTable) <= 32764, "gather table exceeds the kernel-parameter limit");
+
+template <typename T, bool STRIDED>
+__global__ void __launch_bounds__(STRIDED ? 128 : 256) gather_grouped_kernel(const __grid_constant__ GatherTable tab) {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = tab.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab.job[mid].cta_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const GatherJobDev& jb = tab.job[lo];
+    const int local = b - jb.cta_begin;
+    const int64_t bx = local % jb.gx, by = local / jb.gx;
+    const T* X = static_cast<const T*>(jb.X);
+    if constexpr (STRIDED)
+        gather_strided_body<T, float>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, jb.ext, true, jb.wr, jb.st, bx, by, jb.gy);
+    else
+        gather_contig_bf16_body<T>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, jb.ext, true, jb.vec4 != 0, jb.wr, jb.st, bx,
+                                   by, jb.gy);
+}
+
+template <typename T, bool STRIDED>
+static cudaError_t launch_gather_table(const GatherTable& tab, cudaStream_t s) {
+    if (tab.count == 0 || tab.total == 0) return cudaSuccess;
+    (count_launch(), gather_grouped_kernel<T, STRIDED><<<(unsigned)tab.total, STRIDED ? 128 : 256, 0, s>>>(tab));
+    return cudaGetLastError();
+}
+
+template <typename T, bool STRIDED>
+static cudaError_t gather_grouped_t(const GatherJob* jobs, int64_t count, cudaStream_t s) {
+    static GatherTable tab;  // host-side staging of the kernel parameter (~31 KB)
+    tab.count = 0;
+    tab.total = 0;
+    for (int64_t i = 0; i <= count; ++i) {
+        const bool flush = i == count || tab.count == kMaxGatherJobs;
+        if (flush) {
+            cudaError_t e = launch_gather_table<T, STRIDED>(tab, s);
+            if (e != cudaSuccess) return e;
+            tab.count = 0;
+            tab.total = 0;
+        }
+        if (i == count) break;
+        const GatherJob& g = jobs[i];
+        const bool strided = g.v.mode == VEC_STRIDED;
+        if (strided != STRIDED || g.v.dtype != dtype_of<T>()) continue;
+        const int kunit = g.mode == BMM_GEMM_E4M3 ? 128 : 64;
+        const int64_t kmax = round_up(imax(g.ext, 1), kunit);
+        const int64_t gx = ceil_div(kmax, STRIDED ? 128 : 64);
+        const int64_t gy = imin(imax(ceil_div(g.v.len, STRIDED ? kGatherRows : 64), 1), STRIDED ? 4096 : 2048);
+        if ((int64_t)tab.total + gx * gy > 0x7fffffffLL) {  // keep every launch's grid within 2^31 CTAs
+            cudaError_t e = launch_gather_table<T, STRIDED>(tab, s);
+            if (e != cudaSuccess) return e;
+            tab.count = 0;
+            tab.total = 0;
+        }
+        GatherJobDev& d = tab.job[tab.count++];
+        d.X = g.v.data;
+        d.len = g.v.len;
+        d.ld = g.v.ld;
+        d.nvec = g.v.count;
+        d.col = g.col;
+        d.w = g.w;
+        d.ext = g.ext;
+        d.wr = OpWriter{g.out, g.ldo, 0, g.mode, g.role, kunit, nullptr};
+        d.st = g.st;
+        d.gx = (int)gx;
+        d.gy = (int)gy;
+        d.cta_begin = tab.total;
+        d.vec4 = contig_vec4<T>(g.v) ? 1 : 0;
+        tab.total += (int)(gx * gy);
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_gather_grouped(const GatherJob* jobs, int64_t count, cudaStream_t s) {
+    for (int64_t i = 0; i < count; ++i) {
+        const GatherJob& g = jobs[i];
+        if (g.mode == BMM_GEMM_F64 || g.ext < 0 || (g.v.dtype != BMM_F32 && g.v.dtype != BMM_BF16 && g.v.dtype != BMM_F64))
+            return cudaErrorInvalidValue;
+        // BF16 / e4m3 operand rows: 8- and 16-byte stores need ldo and the output 16-byte aligned
+        if ((g.ldo % 16) != 0 || (reinterpret_cast<uintptr_t>(g.out) & 15) != 0) return cudaErrorInvalidValue;
+    }
+    cudaError_t e;
+    if ((e = gather_grouped_t<float, true>(jobs, count, s)) != cudaSuccess) return e;
+    if ((e = gather_grouped_t<float, false>(jobs, count, s)) != cudaSuccess) return e;
+    if ((e = gather_grouped_t<__nv_bfloat16, true>(jobs, count, s)) != cudaSuccess) return e;
+    if ((e = gather_grouped_t<__nv_bfloat16, false>(jobs, count, s)) != cudaSuccess) return e;
+    if ((e = gather_grouped_t<double, true>(jobs, count, s)) != cudaSuccess) return e;
+    return gather_grouped_t<double, false>(jobs, count, s);
 }
 
 // ---------------------------------------------------------------- FP8 operand scales

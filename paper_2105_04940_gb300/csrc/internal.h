@@ -98,6 +98,19 @@ cudaError_t launch_set_extent(int64_t* ext_dev, int64_t value, cudaStream_t s);
 cudaError_t launch_gather_operand(const VecSet& v, const int32_t* col, const double* w, const int64_t* ext_dev,
                                   int64_t ext_max, int mode, int split_role, bool apply_weight, void* out,
                                   int64_t ldo, DevStatus* st, cudaStream_t s, const float* colscale = nullptr);
+// One operand gather of a grouped launch (bmm_apply_batched): the extent is a host value and
+// the weight's square root scales every gathered vector (BF16, split-BF16 or e4m3 operands).
+struct GatherJob {
+    VecSet v;
+    const int32_t* col;
+    const double* w;
+    int64_t ext;
+    int mode, role;
+    void* out;
+    int64_t ldo;
+    DevStatus* st;
+};
+cudaError_t launch_gather_grouped(const GatherJob* jobs, int64_t count, cudaStream_t s);
 // FP8 operand scales.  amax[j] = sqrt(w_j) * max_r |vec_{col_j}[r]| (amax must start at zero);
 // then per drawn index j an exponent e_j balancing the two operands and one exponent per operand,
 // gA and gB, that bring each operand's largest value to at most 448 (the e4m3 maximum):

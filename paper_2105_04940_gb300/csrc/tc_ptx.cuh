@@ -38,13 +38,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait.  abort_flag != nullptr: give up when another role aborted, and raise the flag on expiry.
+// As mbar_try_wait, but the waiting thread may be suspended for up to 20 us until the phase
+// completes (a suspend-time hint), so that warps waiting on a stage leave the issue slots to the
+// warps of the same scheduler that have work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait.  abort_flag != nullptr: give up when another role aborted, and raise the flag on
+// expiry.  SLEEP: poll with mbar_try_wait_sleep.
+template <bool SLEEP = false>
 static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (SLEEP ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
+            if (SLEEP ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
         if (abort_flag != nullptr && *abort_flag) return false;
         if (globaltimer() - t0 > kTimeoutNs) {
             if (abort_flag != nullptr) *abort_flag = 1;

@@ -673,6 +673,46 @@ def test_batched_uneven_products_and_graph_replay(bmm):
         np.testing.assert_array_equal(host(b_).astype(np.float64), a_)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, "bf16"])
+@pytest.mark.parametrize("mode", ["bf16", "split_bf16"])
+@pytest.mark.parametrize("layout", ["row", "col"])
+def test_apply_batched_equals_single_products(bmm, dtype, mode, layout):
+    """bmm_apply_batched gathers the operands of all its column-sampled products in grouped
+    launches (one grid over a table of products): every product must equal bmm_apply's for that
+    product alone, bit for bit, for FP32 and BF16 inputs, both storage orders of M and ragged m, p, L."""
+    rng = np.random.default_rng(29)
+    gm = bmm.MODES[mode]
+    probs, cs, samples = [], [], []
+    for i in range(5):
+        m = int(rng.integers(40, 300))
+        p = int(rng.choice([64, 136, 300]))
+        n = int(rng.integers(2, 4)) * 1024
+        K = n // 64
+        off, M, N, Mt, Nt = _problem(m, n, p, K, seed=300 + i, dtype=dtype, lo=32, hi=100)
+        Mt = as_layout(Mt, layout)
+        c = bmm.equal_budget(max(1, K // 8), n, K) + (17 if i % 2 else 0)
+        pr = bmm.prepare(Mt, Nt, off, max_draws=c, gemm_mode=gm)
+        r = bmm.run(pr, "ONC", c, seed=70 + i, compute_product=False)
+        probs.append(pr)
+        cs.append(c)
+        samples.append((r["idx"], r["scale"]))
+    single = []
+    for pr, c, (idx, scale) in zip(probs, cs, samples):
+        out = torch.empty(pr.M.shape[0], pr.N.shape[1], dtype=torch.float32, device=pr.M.device)
+        bmm.bmm_apply(pr.M, pr.N, pr.B, bmm._abi.UNIT_COLUMN, idx, scale, c, gm, out, False, pr.ws)
+        bmm.check_status(pr)
+        single.append(host(out))
+    outs = [torch.full((pr.M.shape[0], pr.N.shape[1]), float("nan"), dtype=torch.float32, device=pr.M.device)
+            for pr in probs]
+    bmm.bmm_apply_batched([pr.M for pr in probs], [pr.N for pr in probs], [pr.B for pr in probs],
+                          bmm._abi.UNIT_COLUMN, [s_[0] for s_ in samples], [s_[1] for s_ in samples], cs, gm, outs,
+                          False, [pr.ws for pr in probs])
+    for pr in probs:
+        bmm.check_status(pr)
+    for a_, b_ in zip(single, outs):
+        np.testing.assert_array_equal(host(b_), a_)
+
+
 @pytest.mark.parametrize("reuse", [False, True])
 def test_probs_batched_matches_single_products(bmm, reuse):
     """bmm_probs_batched over products of both element types, all storage orders and one that the
