@@ -11,7 +11,8 @@ column and row norms and ||M^k N_k||_F^2 -- exact float-float squares plus the o
 TF32 tcgen05 Grams --, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
 BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flush is
 needed).  Prints one JSON line.  --impl reference times the FP64 CPU oracle instead;
---workload batched runs the 512-product batched workload instead.
+--workload batched runs the 512-product batched workload instead; --workload paper the paper's
+five experiments (Sec. 4) at their sizes.
 """
 from __future__ import annotations
 
@@ -61,10 +62,11 @@ def parse():
                     help="single product: norm pass, then the Gram-only f_k pass (default: one fused pass)")
     ap.add_argument("--fused-stats", action="store_true",
                     help="batched workload: statistics and f_k in one grouped pass per table of products")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp", "precision"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp", "precision", "paper"],
                     help="batched: 512 independent BF16 products of uneven shapes in one CUDA graph; "
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
     ap.add_argument("--products", type=int, default=512, help="products in the batched workload")
+    ap.add_argument("--reps", type=int, default=20, help="replications per setting of the paper workload (paper: 100)")
     ap.add_argument("--streams", type=int, default=16, help="side streams of the batched workload")
     return ap.parse_args()
 
@@ -730,6 +732,105 @@ def e2e(P, prob, args, w, c, gm, out, c0, rank, ws, dev):
             "d2h_bytes_per_step": int(outh.numel() * outh.element_size()), "steps": steps}
 
 
+def paper_arm(args, ws, rank, local):
+    """The paper's five experiments (Sec. 4, Table 1) on the GPU, at the paper's sizes: m = 26,
+    p = 28, n = 5e5, Case I (Gaussian, AR(0.7) covariances) and Case II (t_1, location one); equal
+    blocks; c outer products for the Alg. 2/3 methods and, for SSM (eq. 1.4), round(c K / n) whole
+    blocks (the same contraction budget).  FP64 inputs and FP64 products, so the error is the
+    sampling error alone.  For every setting and method: the mean relative error
+    ||MN - CD||_F / ||MN||_F over --reps replications (the paper used 100) and the mean time of one
+    whole approximate product (statistics, design, draws, product) with CUDA events.  MN is the
+    library's own FP64 product with every index drawn once at scale 1."""
+    import torch
+
+    import paper_2105_04940_gb300 as P
+    import synthetic as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.build()
+    A = P._abi
+    m, n, p = 26, 500000, 28
+    cs1 = [50000, 100000, 200000, 300000, 400000, 500000]
+    Ks = [10, 50, 100, 250, 500]
+    alg2 = ["OPL", "ONC", "UU", "SSM"]
+    alg23 = ["OPL", "ONC", "ONU", "ONMCNR"]
+    exps = [(1, [(c, 10, 5000) for c in cs1], alg2), (2, [(50000, K, 5000) for K in Ks], alg2),
+            (3, [(c, 10, 5000) for c in cs1], alg23), (4, [(50000, K, 5000) for K in Ks], alg23),
+            (5, [(50000, 10, c0) for c0 in (500, 5000, 50000)], alg23)]
+    reps = max(1, args.reps)
+    results, all_ms = [], []
+    with ClockSampler(local) as clk:
+        for case in (1, 2):
+            Mh, Nh = S.paper_case(m, n, p, case, seed=2 + case + 1000 * rank)
+            M = torch.from_numpy(Mh).to(dev)
+            N = torch.from_numpy(Nh).to(dev)
+            probs = {}
+            for K in sorted({K for _, sets, _ in exps for _, K, _ in sets}):
+                off = S.block_offsets_equal(n, K)
+                pr = P.prepare(M, N, off, max_draws=n, gemm_mode=A.GEMM_F64)
+                exact = torch.empty(m, p, dtype=torch.float64, device=dev)
+                A.bmm_apply(M, N, pr.B, A.UNIT_COLUMN, torch.arange(n, dtype=torch.int32, device=dev),
+                            torch.ones(n, dtype=torch.float64, device=dev), n, A.GEMM_F64, exact, False, pr.ws)
+                probs[K] = (pr, exact, torch.linalg.matrix_norm(exact).item())
+                prb = P.prepare(M, N, off, max_draws=K, unit=A.UNIT_BLOCK, gemm_mode=A.GEMM_F64)
+                probs[("blk", K)] = prb
+            out = torch.empty(m, p, dtype=torch.float64, device=dev)
+            for num, sets, methods in exps:
+                for c, K, c0 in sets:
+                    pr, exact, nrm = probs[K]
+                    for meth in methods:
+                        blk = meth == "SSM"
+                        prob = probs[("blk", K)] if blk else pr
+                        cc = max(1, int(round(c * K / n))) if blk else c
+                        errs, ms = [], []
+                        for r in range(reps + 1):  # the first run is a warm-up
+                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            e0.record()
+                            P.run(prob, meth, cc, seed=1000 * num + r, replicate=rank, c0=c0, gemm_mode=A.GEMM_F64,
+                                  out=out, fmode=A.F_EXACT)
+                            e1.record()
+                            if r == 0:
+                                continue
+                            errs.append(torch.linalg.matrix_norm(out - exact) / nrm)
+                            ms.append((e0, e1))
+                        torch.cuda.synchronize()
+                        P.check_status(prob)
+                        t = [a.elapsed_time(b) for a, b in ms]
+                        all_ms += t
+                        results.append({"exp": num, "case": case, "c": c, "K": K, "c0": c0, "method": meth,
+                                        "draws": cc, "rel_err": float(torch.stack(errs).mean().item()),
+                                        "ms": float(np.mean(t))})
+            del M, N, probs
+            torch.cuda.empty_cache()
+
+    def err(num, case, meth, **kw):
+        v = [r["rel_err"] for r in results if r["exp"] == num and r["case"] == case and r["method"] == meth
+             and all(r[k] == x for k, x in kw.items())]
+        return float(np.mean(v)) if v else None
+
+    findings = {
+        # Sec. 4: for Case II, OPL and ONC are more accurate than SSM (experiments 1-2)
+        "case2_opl_onc_beat_ssm": all(err(e, 2, mt, c=r["c"], K=r["K"]) < err(e, 2, "SSM", c=r["c"], K=r["K"])
+                                      for e in (1, 2) for mt in ("OPL", "ONC")
+                                      for r in results if r["exp"] == e and r["case"] == 2 and r["method"] == "SSM"),
+        # experiment 5: with c0 = 5e4 draws ONMCNR is about as accurate as OPL
+        "exp5_onmcnr_vs_opl_at_c0_5e4": [err(5, cs, "ONMCNR", c0=50000) / err(5, cs, "OPL", c0=50000) for cs in (1, 2)],
+    }
+    pk = peaks()
+    line = {
+        "metric": METRIC, "value": float(np.mean(all_ms)), "unit": "ms", "n_gpus": ws, "steps": len(all_ms),
+        "warmup": len(results), "ms_per_step": float(np.mean(all_ms)), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper experiments 1-5 (Sec. 4, Table 1): m=26, p=28, n=5e5, Case I/II, equal blocks, "
+                               "SSM at the same contraction budget", "reps": reps, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs 216 MB per case, larger than the 129 MB L2"},
+        "results": results, "findings": findings, "clocks": clk.summary(), "peak_source": pk["source"],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.gpus > 1 and int(os.environ.get("WORLD_SIZE", "1")) == 1:
@@ -744,6 +845,8 @@ def main():
             mlp_arm(args, ws, rank, local)
         elif args.workload == "precision":
             precision_arm(args, ws, rank, local)
+        elif args.workload == "paper":
+            paper_arm(args, ws, rank, local)
         else:
             native_arm(args, ws, rank, local)
     finally:

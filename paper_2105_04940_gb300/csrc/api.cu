@@ -109,7 +109,7 @@ struct ProbsPlan {
 void plan_probs(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, bool need_f, ProbsPlan* p) {
     p->partial_cap = imax(vec_sqnorms_partial_elems(vecset_of_M(M)), vec_sqnorms_partial_elems(vecset_of_N(N)));
     p->partial = cv.take<double>(p->partial_cap);
-    p->gpart_cap = need_f ? gram_frob_partial_elems(B->K, B->max_nk) : 0;
+    p->gpart_cap = need_f ? frob_partial_elems(B->K, B->max_nk, vecset_of_M(M).len, vecset_of_N(N).len) : 0;
     p->gpart = need_f ? cv.take<double>(p->gpart_cap) : nullptr;
     p->counter = cv.take<int>(1);
     p->wins = need_f ? cv.take<int>(stats_windows_ints(B->K)) : nullptr;
@@ -121,15 +121,16 @@ struct SizesPlan {
     double* gpart;
     int64_t gpart_cap;
 };
+// m, pp: lengths of M's columns and N's rows (the pilot's vectors); used only by BMM_CK_TILDE
 void plan_sizes(Carver& cv, const bmm_blocks* B, int ckind, int64_t per, double* g_out, double* fhat_out,
-                SizesPlan* p) {
+                SizesPlan* p, int64_t m = 0, int64_t pp = 0) {
     p->g = g_out ? g_out : cv.take<double>(B->K);
     p->fhat = nullptr;
     p->gpart = nullptr;
     p->gpart_cap = 0;
     if (ckind == BMM_CK_TILDE) {
         p->fhat = fhat_out ? fhat_out : cv.take<double>(B->K);
-        p->gpart_cap = gram_frob_partial_elems(B->K, per);
+        p->gpart_cap = frob_partial_elems(B->K, per, m, pp);
         p->gpart = cv.take<double>(p->gpart_cap);
     }
 }
@@ -148,6 +149,8 @@ struct ApplyPlan {
     void* Bop;
     int64_t lmax, kseg_max, ktot;
     float *amaxA, *amaxB, *sa, *sb, *oscale;  // e4m3 operand scales
+    double* kpart;                            // FP64: partial products of the K splits
+    int64_t kpart_cap;
 };
 void plan_apply(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int unit, int64_t count,
                 int mode, ApplyPlan* p) {
@@ -174,6 +177,8 @@ void plan_apply(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks
     }
     p->A = cv.take<char>(M->rows * p->ktot * (int64_t)es);
     p->Bop = cv.take<char>(N->cols * p->ktot * (int64_t)es);
+    p->kpart_cap = mode == BMM_GEMM_F64 ? gemm_f64_split_elems(M->rows, N->cols, p->ktot) : 0;
+    p->kpart = p->kpart_cap > 0 ? cv.take<double>(p->kpart_cap) : nullptr;
 }
 
 struct BackPlan {
@@ -258,7 +263,8 @@ BMM_API size_t bmm_workspace_size(const bmm_mat* M, const bmm_mat* N, const bmm_
     {
         Carver cv{nullptr};
         SizesPlan p;
-        plan_sizes(cv, B, BMM_CK_TILDE, ceil_div(imax(max_draws, 1), B->K), nullptr, nullptr, &p);
+        plan_sizes(cv, B, BMM_CK_TILDE, ceil_div(imax(max_draws, 1), B->K), nullptr, nullptr, &p, vecset_of_M(M).len,
+                   vecset_of_N(N).len);
         need = cv.off > need ? cv.off : need;
     }
     {
@@ -417,12 +423,13 @@ BMM_API bmm_status bmm_blocksizes(const bmm_mat* M, const bmm_mat* N, const bmm_
     }
     if (c < B->K || c > B->n) return BMM_ERR_INFEASIBLE;
     const int64_t per = ckind == BMM_CK_TILDE ? pilot_per_block : 0;
+    const int64_t vm = ckind == BMM_CK_TILDE ? vecset_of_M(M).len : 0, vp = ckind == BMM_CK_TILDE ? vecset_of_N(N).len : 0;
     Carver cnt{nullptr};
     SizesPlan plan;
-    plan_sizes(cnt, B, ckind, per, g_out, fhat_out, &plan);
+    plan_sizes(cnt, B, ckind, per, g_out, fhat_out, &plan, vm, vp);
     if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
     Carver cv{static_cast<char*>(ws) + kStatusBytes};
-    plan_sizes(cv, B, ckind, per, g_out, fhat_out, &plan);
+    plan_sizes(cv, B, ckind, per, g_out, fhat_out, &plan, vm, vp);
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     DevStatus* dst = status_of(ws);
     const double* fvec = nullptr;
@@ -526,7 +533,7 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
     if (gemm_mode == BMM_GEMM_F64) {
         BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.A), plan.ktot, static_cast<const double*>(plan.Bop),
                                 plan.ktot, M->rows, N->cols, 0, plan.ext, static_cast<double*>(odata), out->ld,
-                                accumulate, cs));
+                                accumulate, cs, plan.ktot, plan.kpart, plan.kpart_cap));
         return BMM_OK;
     }
     *g = GemmArgs{plan.A, plan.ktot, plan.Bop, plan.ktot, M->rows, N->cols, plan.ktot, 0, plan.ext,

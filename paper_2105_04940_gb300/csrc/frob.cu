@@ -181,6 +181,153 @@ static cudaError_t gram_frob_t(const VecSet& U, const VecSet& V, const int64_t* 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- direct form
+// For small m p the product itself is cheaper than the Grams: f = ||sum_t w_t u_t v_t^T||_F^2 costs
+// 2 m p len flops directly against 2 (m + p) len^2 through the trace identity (eq. 1.2 and eq. 3.9 with
+// blocks of thousands of vectors and m, p of a few dozen, as in the paper's experiments).  CTA
+// (k, s, r) accumulates the rectangle r (kDirTH rows x kDirTF columns) of block k's product over
+// the s-th slice of its vectors in FP64 (each term (w_t u_h) v_f one FMA), and writes it to a
+// partial buffer; direct_reduce_kernel sums the slices in slice order, squares and sums the entries.
+constexpr int kDirThreads = 256;
+constexpr int kDirTH = 32;                     // product rows per rectangle
+constexpr int kDirTF = 64;                     // product columns per rectangle
+constexpr int kDirPer = kDirTH * kDirTF / kDirThreads;  // 8 entries per thread: row t / 8, columns t % 8 + 8 j
+constexpr int kDirChunk = 32;                  // vectors staged per step
+constexpr int64_t kDirMaxEntries = 1 << 16;    // m p limit of the direct form (partial buffer size)
+
+static int64_t dir_rects(int64_t m, int64_t p) { return ceil_div(m, kDirTH) * ceil_div(p, kDirTF); }
+static int64_t dir_slices(int64_t K, int64_t len, int64_t m, int64_t p) {
+    // about four CTAs per SM over the launch, slices of at least kDirChunk vectors
+    const int64_t want = ceil_div(4 * 152, imax(K * dir_rects(m, p), 1));
+    return imax(1, imin(want, ceil_div(imax(len, 1), kDirChunk)));
+}
+
+bool frob_use_direct(int64_t m, int64_t p, int64_t len) {
+    if (m < 1 || p < 1 || m * p > kDirMaxEntries) return false;
+    return m * p <= (m + p) * len || ceil_div(imax(len, 1), kTile) > 362;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDirThreads)
+    direct_frob_kernel(const T* __restrict__ U, int64_t m, int64_t ldU, int modeU, const T* __restrict__ V, int64_t p,
+                       int64_t ldV, int modeV, int64_t n_vec, const int64_t* __restrict__ off,
+                       const int32_t* __restrict__ cols, const double* __restrict__ wts, int64_t per, int64_t slices,
+                       double* __restrict__ partial, DevStatus* st) {
+    __shared__ double su[kDirChunk][kDirTH];
+    __shared__ double sv[kDirChunk][kDirTF];
+    __shared__ double sw[kDirChunk];
+    __shared__ int64_t sidx[kDirChunk];
+    const int64_t k = blockIdx.x, sl = blockIdx.y, rect = blockIdx.z;
+    const int64_t rf = ceil_div(p, kDirTF);
+    const int64_t h0 = (rect / rf) * kDirTH, f0 = (rect % rf) * kDirTF;
+    int64_t base = 0, len = 0;
+    bool ok = true;
+    if (cols == nullptr) {
+        base = off[k];
+        len = off[k + 1] - base;
+        ok = base >= 0 && len > 0 && base + len <= n_vec;
+    } else {
+        base = k * per;
+        len = per;
+    }
+    const int tid = threadIdx.x;
+    const int hh = tid / 8, fc = tid % 8;
+    double acc[kDirPer];
+#pragma unroll
+    for (int j = 0; j < kDirPer; ++j) acc[j] = 0.0;
+    if (!ok) {
+        if (tid == 0 && sl == 0 && rect == 0) set_status(st, BMM_ERR_SHAPE, (int)k);
+        len = 0;
+    }
+    const int64_t chunk = ceil_div(imax(len, 1), slices);
+    const int64_t t_lo = sl * chunk, t_hi = imin(len, t_lo + chunk);
+    for (int64_t t0 = t_lo; t0 < t_hi; t0 += kDirChunk) {
+        __syncthreads();
+        if (tid < kDirChunk) {
+            const int64_t t = t0 + tid;
+            int64_t idx = -1;
+            double w = 0.0;
+            if (t < t_hi) {
+                if (cols == nullptr) { idx = base + t; w = 1.0; }
+                else {
+                    idx = cols[base + t];
+                    w = wts[base + t];
+                    if (idx < 0 || idx >= n_vec) { set_status(st, BMM_ERR_ARG, (int)k); idx = -1; w = 0.0; }
+                }
+            }
+            sidx[tid] = idx;
+            sw[tid] = w;
+        }
+        __syncthreads();
+        // stage u_t[h0 .. h0 + 32) (times w_t) and v_t[f0 .. f0 + 64) of the chunk's vectors
+        for (int e = tid; e < kDirChunk * kDirTH; e += kDirThreads) {
+            const int c = e / kDirTH, h = e % kDirTH;
+            const int64_t idx = sidx[c], hg = h0 + h;
+            double v = 0.0;
+            if (idx >= 0 && hg < m) v = sw[c] * (double)Elem<T>::to_f64(modeU == VEC_CONTIG ? U[idx * ldU + hg] : U[hg * ldU + idx]);
+            su[c][h] = v;
+        }
+        for (int e = tid; e < kDirChunk * kDirTF; e += kDirThreads) {
+            const int c = e / kDirTF, f = e % kDirTF;
+            const int64_t idx = sidx[c], fg = f0 + f;
+            double v = 0.0;
+            if (idx >= 0 && fg < p) v = (double)Elem<T>::to_f64(modeV == VEC_CONTIG ? V[idx * ldV + fg] : V[fg * ldV + idx]);
+            sv[c][f] = v;
+        }
+        __syncthreads();
+        const int nc = (int)imin(kDirChunk, t_hi - t0);
+        for (int c = 0; c < nc; ++c) {
+            const double a = su[c][hh];
+#pragma unroll
+            for (int j = 0; j < kDirPer; ++j) acc[j] = fma(a, sv[c][fc + 8 * j], acc[j]);
+        }
+    }
+    double* out = partial + (k * slices + sl) * (m * p);
+#pragma unroll
+    for (int j = 0; j < kDirPer; ++j) {
+        const int64_t h = h0 + hh, f = f0 + fc + 8 * j;
+        if (h < m && f < p) out[h * p + f] = acc[j];
+    }
+}
+
+// f[k] = sum over entries of (sum over slices of the partial products)^2, in a fixed order.
+__global__ void __launch_bounds__(256) direct_reduce_kernel(const double* __restrict__ partial, int64_t mp, int64_t slices,
+                                                            double* __restrict__ f) {
+    __shared__ double red[8];
+    const int64_t k = blockIdx.x;
+    double s2 = 0.0;
+    for (int64_t e = threadIdx.x; e < mp; e += blockDim.x) {
+        double pe = 0.0;
+        for (int64_t sl = 0; sl < slices; ++sl) pe += partial[(k * slices + sl) * mp + e];
+        s2 = fma(pe, pe, s2);
+    }
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        f[k] = tot;
+    }
+}
+
+template <typename T>
+static cudaError_t direct_frob_t(const VecSet& U, const VecSet& V, const int64_t* off, int64_t K, int64_t max_len,
+                                 const int32_t* cols, const double* wts, int64_t per, double* f, double* partial,
+                                 DevStatus* st, cudaStream_t s) {
+    const int64_t m = U.len, p = V.len;
+    const int64_t len = cols ? per : max_len;
+    const int64_t slices = dir_slices(K, len, m, p);
+    const int64_t rects = dir_rects(m, p);
+    if (K > 2147483647LL || slices > 65535 || rects > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)K, (unsigned)slices, (unsigned)rects);
+    (count_launch(), direct_frob_kernel<T><<<grid, kDirThreads, 0, s>>>(
+                         static_cast<const T*>(U.data), m, U.ld, U.mode, static_cast<const T*>(V.data), p, V.ld, V.mode,
+                         U.count, off, cols, wts, per, slices, partial, st));
+    (count_launch(), direct_reduce_kernel<<<(unsigned)K, 256, 0, s>>>(partial, m * p, slices, f));
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- small pilots
 // The Alg. 3 pilot with few draws per block (per <= kPilotMax, e.g. c0 = 4 K): one CTA per block
 // k keeps every pair product <u_a, u_b>, <v_a, v_b> (a <= b < P) of its drawn vectors in registers,
@@ -287,6 +434,11 @@ static cudaError_t pilot_frob_any(const VecSet& U, const VecSet& V, int64_t K, c
     return pilot_frob_t<T, kPilotMax>(U, V, K, cols, wts, per, f, st, s);
 }
 
+int64_t frob_partial_elems(int64_t K, int64_t len, int64_t m, int64_t p) {
+    if (frob_use_direct(m, p, len)) return K * dir_slices(K, len, m, p) * m * p;
+    return gram_frob_partial_elems(K, len);
+}
+
 cudaError_t launch_gram_frob(const VecSet& U, const VecSet& V, const int64_t* off, int64_t K, int64_t max_len,
                              const int32_t* cols, const double* wts, int64_t per, double* f, double* partial,
                              int64_t partial_cap, DevStatus* st, cudaStream_t s) {
@@ -296,6 +448,15 @@ cudaError_t launch_gram_frob(const VecSet& U, const VecSet& V, const int64_t* of
             case BMM_F64: return pilot_frob_any<double>(U, V, K, cols, wts, (int)per, f, st, s);
             case BMM_F32: return pilot_frob_any<float>(U, V, K, cols, wts, (int)per, f, st, s);
             default: return pilot_frob_any<__nv_bfloat16>(U, V, K, cols, wts, (int)per, f, st, s);
+        }
+    }
+    const int64_t len = cols ? per : max_len;
+    if (frob_use_direct(U.len, V.len, len)) {
+        if (partial_cap < frob_partial_elems(K, len, U.len, V.len)) return cudaErrorInvalidValue;
+        switch (U.dtype) {
+            case BMM_F64: return direct_frob_t<double>(U, V, off, K, max_len, cols, wts, per, f, partial, st, s);
+            case BMM_F32: return direct_frob_t<float>(U, V, off, K, max_len, cols, wts, per, f, partial, st, s);
+            default: return direct_frob_t<__nv_bfloat16>(U, V, off, K, max_len, cols, wts, per, f, partial, st, s);
         }
     }
     if (partial_cap < gram_frob_partial_elems(K, cols ? per : max_len)) return cudaErrorInvalidValue;

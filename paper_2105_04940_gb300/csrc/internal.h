@@ -49,6 +49,11 @@ cudaError_t launch_gram_frob(const VecSet& U, const VecSet& V, const int64_t* of
                              const int32_t* cols, const double* wts, int64_t per,
                              double* f, double* partial, int64_t partial_cap, DevStatus* st, cudaStream_t s);
 int64_t gram_frob_partial_elems(int64_t K, int64_t max_len);
+// Partial-buffer elements launch_gram_frob needs for K blocks (or pilots) of len vectors of
+// lengths m and p: the direct form's slices of the m x p product when m p is the smaller cost
+// (frob_use_direct), else the Gram form's pair tiles.
+bool frob_use_direct(int64_t m, int64_t p, int64_t len);
+int64_t frob_partial_elems(int64_t K, int64_t len, int64_t m, int64_t p);
 
 // ---- blockstats_tc.cu
 bool blockstats_tc_supported(const VecSet& vM, const VecSet& vN, int64_t max_nk);
@@ -131,9 +136,12 @@ cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64
                                 int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
                                 int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s,
                                 int elem = GEMM_ELEM_BF16, const float* scale = nullptr);
+// K is k_host, or *k_dev rounded up to 64; k_max bounds it for the choice of K splits, whose
+// partial tiles go to part (gemm_f64_split_elems(M, N, k_max) doubles; without it, no split).
 cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,
                             int64_t k_host, const int64_t* k_dev, double* out, int64_t ldo, int accumulate,
-                            cudaStream_t s);
+                            cudaStream_t s, int64_t k_max = 0, double* part = nullptr, int64_t part_cap = 0);
+int64_t gemm_f64_split_elems(int64_t M, int64_t N, int64_t K);
 bool tc_gemm_supported();
 // Many independent products in as few persistent launches as the kernel-parameter limit allows.
 struct GemmArgs {

@@ -495,6 +495,61 @@ def test_pilot_fhat_small_and_tiled(bmm, per, dtype, layout):
     assert rel_err(host(r["fhat"]), fh_or) < 1e-10
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, "bf16"])
+@pytest.mark.parametrize("layouts", [("row", "row"), ("col", "col")])
+def test_exact_f_direct_form_large_blocks(bmm, dtype, layouts):
+    """Exact f_k = ||M^k N_k||_F^2 for blocks of thousands of vectors with small m, p (the shape of
+    the paper's experiments): the direct m x p product per block (FP64 sums over slices of the
+    block) replaces the Gram form, whose n_k^2 pair tiles it would not take."""
+    m, p, n, K = 26, 28, 20000, 4
+    off, M, N, Mt, Nt = _problem(m, n, p, K, seed=51, dtype=dtype, lo=2000, hi=8000)
+    Mt, Nt = as_layout(Mt, layouts[0]), as_layout(Nt, layouts[1])
+    prob = bmm.prepare(Mt, Nt, off, max_draws=2000)
+    pv = torch.empty(n, dtype=torch.float64, device=Mt.device)
+    bmm.bmm_probs(Mt, Nt, prob.B, bmm._abi.P_COL_OPT, bmm._abi.F_EXACT, pv, prob.st, prob.ws)
+    bmm.check_status(prob)
+    assert rel_err(host(prob.st["f"]), oracle.block_frob_sq(M, N, off)) < 1e-10
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    assert rel_err(host(pv), oracle.p_col_opt(st["w"], st["a"], off)) < 1e-12
+
+
+@pytest.mark.parametrize("per", [40, 500])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_pilot_fhat_direct_form(bmm, per, dtype):
+    """Alg. 3 pilots of 40 and 500 draws per block with m = 26, p = 28: f^_k through the direct
+    product of the drawn, rescaled outer products, against the oracle."""
+    m, p, n, K = 26, 28, 12000, 6
+    off, M, N, Mt, Nt = _problem(m, n, p, K, seed=53, dtype=dtype, lo=1000, hi=3000)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=per * K)
+    r = bmm.run(prob, "ONMCNR", 3 * K, seed=9, c0=per * K, gemm_mode=bmm._abi.GEMM_F64)
+    bmm.check_status(prob)
+    fh_or, idx_or, sc_or = oracle.pilot_frob_sq(M, N, off, host(r["p0"]), per, seed=9,
+                                                sid=oracle.stream_id(0, oracle.PURPOSE_PILOT))
+    np.testing.assert_array_equal(host(r["pilot_idx"]), idx_or)
+    assert rel_err(host(r["fhat"]), fh_or) < 1e-10
+
+
+@pytest.mark.parametrize("L", [5000, 20011])
+def test_f64_product_split_k(bmm, L):
+    """FP64 sampled product of a 26 x 28 output (one 64 x 64 tile) with thousands of drawn columns:
+    the K range is split over CTAs and the partial tiles summed in split order; against the
+    oracle's FP64 product of the same draws, and identical on a second call."""
+    m, p, n, K = 26, 28, 30000, 10
+    off, M, N, Mt, Nt = _problem(m, n, p, K, seed=57, dtype=np.float64)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L)
+    r = bmm.run(prob, "ONC", L, seed=4, gemm_mode=bmm._abi.GEMM_F64)
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]), host(r["scale"])
+    want = oracle.sampled_product_columns(M, N, idx, scale)
+    bound = product_bound(M, N, idx, scale)
+    assert np.all(np.abs(host(r["out"]) - want) <= _tol("f64", L) * bound + 1e-300)
+    first = host(r["out"]).copy()
+    bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, r["idx"], r["scale"], L, bmm._abi.GEMM_F64, r["out"], False,
+                  prob.ws)
+    np.testing.assert_array_equal(host(r["out"]), first)
+
+
 # ---------------------------------------------------------------- adjoint
 @pytest.mark.parametrize("mode", ["f64", "bf16"])
 @pytest.mark.parametrize("unit", ["column", "block"])
