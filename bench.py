@@ -67,6 +67,7 @@ def parse():
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
     ap.add_argument("--products", type=int, default=512, help="products in the batched workload")
     ap.add_argument("--reps", type=int, default=20, help="replications per setting of the paper workload (paper: 100)")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: default GEMM tiles")
     ap.add_argument("--streams", type=int, default=16, help="side streams of the batched workload")
     return ap.parse_args()
 
@@ -280,6 +281,9 @@ def native_arm(args, ws, rank, local):
     prob = P.prepare(M, N, off, max_draws=max(c, L), unit=unit, gemm_mode=gm)
     out = torch.empty(w["m"], w["p"], device=dev, dtype=torch.float64 if args.mode == "f64" else torch.float32)
     c0 = 4 * K
+    tuned = {}
+    if args.mode != "f64" and not args.no_autotune:  # GEMM tiles for this product's shape
+        tuned = P.autotune([(w["m"], w["p"], L)], gm, dev)
 
     def step(s, events=None):
         return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events,
@@ -359,6 +363,7 @@ def native_arm(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline, "stages_ms": stages, "stage_rooflines": roof_all,
         "clocks": clk.summary(), "gpu_launches": int(launches),
+        "autotune": {f"{k[0]}x{k[1]}xL{k[2]}": v for k, v in tuned.items()},
     }
 
     if rank == 0 and not args.quick:
@@ -407,16 +412,25 @@ def batched_arm(args, ws, rank, local):
         flops += 2.0 * m * p * L
     seeds = [11 + i for i in range(len(probs))]
     streams = [torch.cuda.Stream(device=dev) for _ in range(args.streams)]
+    tune, tune_s = None, 0.0
 
     def batch():
         return P.run_batched(probs, "OPL", cs, seeds, gemm_mode=P._abi.GEMM_BF16, outs=outs, streams=streams,
                              fused_stats=args.fused_stats)
 
+    res = None
     for _ in range(args.warmup):
-        batch()
+        res = batch()
     torch.cuda.synchronize()
     for pr in probs:
         P.check_status(pr)
+    if not args.no_autotune:
+        if res is None:
+            res = batch()
+        # GEMM tiles for the grouped launch of this batch, timed on its own sampled products
+        t0 = time.perf_counter()
+        tune = P.autotune_batched(probs, res, cs, P._abi.GEMM_BF16, outs)
+        tune_s = time.perf_counter() - t0
     # eager batch time (host launch overhead included)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -454,11 +468,14 @@ def batched_arm(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"batched: {len(probs)} BF16 products, m,p U{{128..2048/128}}, n U{{4096..65536/4096}}, "
-                               "K=n/64 blocks of 32..128, c=K/8, OPL, one CUDA graph per batch", "streams": args.streams,
+                               "K=n/64 blocks of 32..128, c=K/8, OPL, one CUDA graph per batch, GEMM tiles autotuned",
+                   "streams": args.streams,
                    "statistics": "fused, grouped" if args.fused_stats else "norm pass per product, Gram pass grouped",
                    "products": len(probs), "input_gb": in_bytes / 1e9, "gemm_tflop": flops / 1e12,
                    "l2": "inputs larger than the 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "batch_ms": batch_ms, "eager_batch_ms": eager_ms,
+        "autotune": None if tune is None else {"choice": tune["choice"], "seconds": tune_s,
+                                                "apply_ms_by_policy": tune["ms"]},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s", "frac": ach / pk["hbm"],
                      "kernel": "whole batch (one read of every input per product)", "traffic": None,
                      "peak_source": pk["source"]},
@@ -536,6 +553,7 @@ def mlp_arm(args, ws, rank, local):
                                "c=64 blocks (L=4096), forward + backward", "parallelism": f"replicas x{ws}"},
         "exact_bf16_mlp_ms": exact_ms, "sampled_gemm_tflop_per_step": gemm_flops / 1e12,
         "clocks": clk.summary(), "gpu_launches": int(launches),
+        "autotune": {f"{k[0]}x{k[1]}xL{k[2]}": v for k, v in tuned.items()},
     }
     if rank == 0:
         print(json.dumps(result))

@@ -280,6 +280,35 @@ const char* bmm_status_string(bmm_status s);
  * enqueued since it was loaded, summed over all threads and calls. */
 uint64_t bmm_launch_count(void);
 
+/* ---- GEMM tile autotuner (no counterpart in the paper: a tuning aid for the batched
+ * configuration, whose products have uneven m, p and L).
+ * The sampled product of an m x n by n x p problem with L drawn outer products is, on the tensor
+ * cores, a GEMM of M = m rows, N = p columns and depth K = L rounded up to 64 (BF16), 128 (e4m3)
+ * or three times 64-rounded L (split BF16).  Its tile width (BN = 128 or 256 output columns) and
+ * raster group (4, 8 or 16 row tiles walked together for L2 reuse) come from a process-wide
+ * table keyed by the element kind and the base-2 logarithms (rounded up) of M, N and K; shapes
+ * not in the table use BN = 128 when N <= 128, else 256, and a raster group of 8.  No choice
+ * changes any result bit: each output element is the same dot product in the same order.
+ * gemm_mode: BMM_GEMM_BF16, BMM_GEMM_SPLIT_BF16 or BMM_GEMM_E4M3 (else BMM_ERR_ARG). */
+
+/* Workspace bytes bmm_autotune_gemm needs for this shape (0 for an invalid one). */
+size_t bmm_autotune_workspace_size(int64_t m, int64_t p, int64_t L, int32_t gemm_mode);
+/* Times every (BN, raster group) candidate on constant scratch operands carved from ws (device,
+ * 256-byte aligned, caller-owned; contents overwritten) on the stream: one warm-up and three timed
+ * launches each, CUDA events.  Records the fastest for the shape's bucket and returns it in
+ * *bn_out, *raster_out and *ms_out (any may be NULL).  Synchronises the stream: call it before
+ * timing or graph capture.  Errors: BMM_ERR_ARG, BMM_ERR_WORKSPACE, BMM_ERR_UNSUPPORTED (no
+ * sm_103 device), BMM_ERR_CUDA. */
+bmm_status bmm_autotune_gemm(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, void* ws, size_t ws_bytes,
+                             bmm_stream_t stream, int32_t* bn_out, int32_t* raster_out, float* ms_out);
+/* The choice the next launch of this shape will use (host only, no device access). */
+bmm_status bmm_autotune_get(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, int32_t* bn_out,
+                            int32_t* raster_out);
+/* Records a choice for the shape's bucket (bn 128 or 256, raster 4, 8 or 16; else BMM_ERR_ARG). */
+bmm_status bmm_autotune_set(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, int32_t bn, int32_t raster);
+/* Forgets every recorded choice. */
+void bmm_autotune_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,13 +9,13 @@ without the built library every call raises.
 from . import _abi
 from ._abi import (BmmError, bmm_apply, bmm_apply_batched, bmm_backward, bmm_blocksizes, bmm_clear_device_status, bmm_probs,
                    bmm_probs_batched, bmm_read_device_status, bmm_sample, bmm_workspace_size)
-from .pipeline import (METHODS, MODES, Problem, SampledMatmul, check_status, equal_budget, prepare, run, run_batched,
+from .pipeline import (METHODS, MODES, Problem, SampledMatmul, autotune, autotune_batched, check_status, equal_budget, prepare, run, run_batched,
                        sampled_matmul, stream_id)
 
 __all__ = [
     "BmmError", "bmm_apply", "bmm_apply_batched", "bmm_backward", "bmm_blocksizes", "bmm_clear_device_status", "bmm_probs", "bmm_probs_batched",
     "bmm_read_device_status", "bmm_sample", "bmm_workspace_size", "METHODS", "MODES", "Problem",
-    "SampledMatmul", "check_status", "equal_budget", "prepare", "run", "run_batched", "sampled_matmul",
+    "SampledMatmul", "autotune", "autotune_batched", "check_status", "equal_budget", "prepare", "run", "run_batched", "sampled_matmul",
     "stream_id",
 ]
 

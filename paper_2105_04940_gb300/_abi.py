@@ -28,6 +28,7 @@ EXPORTED = (
     "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
     "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
     "bmm_probs_static", "bmm_apply_batched", "bmm_probs_batched",
+    "bmm_autotune_workspace_size", "bmm_autotune_gemm", "bmm_autotune_get", "bmm_autotune_set", "bmm_autotune_clear",
 )
 
 
@@ -85,6 +86,16 @@ def load(path: str = LIB_PATH):
     lib.bmm_probs_batched.restype = i32
     lib.bmm_launch_count.argtypes = []
     lib.bmm_launch_count.restype = ctypes.c_uint64
+    lib.bmm_autotune_workspace_size.argtypes = [i64, i64, i64, i32]
+    lib.bmm_autotune_workspace_size.restype = sz
+    lib.bmm_autotune_gemm.argtypes = [i64, i64, i64, i32, vp, sz, vp, P(i32), P(i32), P(ctypes.c_float)]
+    lib.bmm_autotune_gemm.restype = i32
+    lib.bmm_autotune_get.argtypes = [i64, i64, i64, i32, P(i32), P(i32)]
+    lib.bmm_autotune_get.restype = i32
+    lib.bmm_autotune_set.argtypes = [i64, i64, i64, i32, i32, i32]
+    lib.bmm_autotune_set.restype = i32
+    lib.bmm_autotune_clear.argtypes = []
+    lib.bmm_autotune_clear.restype = None
     for name in ("bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
                  "bmm_read_device_status", "bmm_clear_device_status"):
         getattr(lib, name).restype = i32
@@ -217,6 +228,34 @@ def bmm_clear_device_status(ws, stream=None):
 def bmm_launch_count() -> int:
     """Kernels launched by libbmm.so since it was loaded (diagnostic)."""
     return int(load().bmm_launch_count())
+
+
+def bmm_autotune_workspace_size(m: int, p: int, L: int, gemm_mode: int) -> int:
+    """Workspace bytes bmm_autotune_gemm needs for an m x p product of L outer products."""
+    return int(load().bmm_autotune_workspace_size(m, p, L, gemm_mode))
+
+
+def bmm_autotune_gemm(m: int, p: int, L: int, gemm_mode: int, ws, stream=None) -> dict:
+    """Time the GEMM tile candidates for this shape and record the fastest (see include/bmm.h)."""
+    bn, ra, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().bmm_autotune_gemm(m, p, L, gemm_mode, ws.data_ptr(), ws.numel(), _stream(stream), ctypes.byref(bn),
+                                    ctypes.byref(ra), ctypes.byref(ms)), "bmm_autotune_gemm")
+    return {"bn": bn.value, "raster": ra.value, "ms": ms.value}
+
+
+def bmm_autotune_get(m: int, p: int, L: int, gemm_mode: int) -> dict:
+    """The tile choice the next GEMM of this shape will use."""
+    bn, ra = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().bmm_autotune_get(m, p, L, gemm_mode, ctypes.byref(bn), ctypes.byref(ra)), "bmm_autotune_get")
+    return {"bn": bn.value, "raster": ra.value}
+
+
+def bmm_autotune_set(m: int, p: int, L: int, gemm_mode: int, bn: int, raster: int):
+    _check(load().bmm_autotune_set(m, p, L, gemm_mode, bn, raster), "bmm_autotune_set")
+
+
+def bmm_autotune_clear():
+    load().bmm_autotune_clear()
 
 
 def bmm_probs_static(M, N, B: Blocks, pkind: int, p_out, st: dict, status_out, stream=None):

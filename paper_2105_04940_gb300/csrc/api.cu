@@ -707,3 +707,63 @@ BMM_API const char* bmm_status_string(bmm_status s) {
 }
 
 BMM_API uint64_t bmm_launch_count(void) { return launch_counter().load(std::memory_order_relaxed); }
+
+// ---- GEMM tile autotuner
+namespace {
+// element kind and GEMM depth of a sampled product with L outer products in gemm_mode
+bool tune_shape(int64_t m, int64_t p, int64_t L, int32_t mode, int* elem, int64_t* K) {
+    if (m < 1 || p < 1 || L < 1 || m > 0x7fffffff || p > 0x7fffffff || L > (int64_t(1) << 40)) return false;
+    if (mode != BMM_GEMM_BF16 && mode != BMM_GEMM_SPLIT_BF16 && mode != BMM_GEMM_E4M3) return false;
+    *elem = mode == BMM_GEMM_E4M3 ? bmm::GEMM_ELEM_E4M3 : bmm::GEMM_ELEM_BF16;
+    *K = bmm::round_up(L, mode == BMM_GEMM_E4M3 ? 128 : 64) * (mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1);
+    return true;
+}
+}  // namespace
+
+BMM_API size_t bmm_autotune_workspace_size(int64_t m, int64_t p, int64_t L, int32_t gemm_mode) {
+    int elem;
+    int64_t K;
+    if (!tune_shape(m, p, L, gemm_mode, &elem, &K)) return 0;
+    return (size_t)(kStatusBytes + gemm_autotune_bytes(m, p, K, elem));
+}
+
+BMM_API bmm_status bmm_autotune_gemm(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, void* ws, size_t ws_bytes,
+                                     bmm_stream_t stream, int32_t* bn_out, int32_t* raster_out, float* ms_out) {
+    int elem;
+    int64_t K;
+    if (!tune_shape(m, p, L, gemm_mode, &elem, &K)) return BMM_ERR_ARG;
+    if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255) ||
+        ws_bytes < (size_t)(kStatusBytes + gemm_autotune_bytes(m, p, K, elem)))
+        return BMM_ERR_WORKSPACE;
+    if (!tc_gemm_supported()) return BMM_ERR_UNSUPPORTED;
+    TileChoice best{0, 0};
+    float ms = 0.f;
+    BMM_TRY(gemm_autotune(m, p, K, elem, static_cast<char*>(ws) + kStatusBytes, ws_bytes - kStatusBytes, status_of(ws),
+                          reinterpret_cast<cudaStream_t>(stream), &best, &ms));
+    if (bn_out) *bn_out = best.bn;
+    if (raster_out) *raster_out = best.raster;
+    if (ms_out) *ms_out = ms;
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_autotune_get(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, int32_t* bn_out,
+                                    int32_t* raster_out) {
+    int elem;
+    int64_t K;
+    if (!tune_shape(m, p, L, gemm_mode, &elem, &K)) return BMM_ERR_ARG;
+    const TileChoice c = gemm_tile_choice(elem, m, p, K);
+    if (bn_out) *bn_out = c.bn;
+    if (raster_out) *raster_out = c.raster;
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_autotune_set(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, int32_t bn, int32_t raster) {
+    int elem;
+    int64_t K;
+    const TileChoice c{bn, raster};
+    if (!tune_shape(m, p, L, gemm_mode, &elem, &K) || !gemm_tile_valid(c)) return BMM_ERR_ARG;
+    gemm_tile_set(elem, m, p, K, c);
+    return BMM_OK;
+}
+
+BMM_API void bmm_autotune_clear(void) { gemm_tile_clear(); }

@@ -12,6 +12,10 @@
 //            and store FP32 rows, overlapping the next tile's MMAs.
 // Every wait is bounded (globaltimer); on expiry the CTA records BMM_ERR_TIMEOUT, lets its
 // copies and MMAs in flight finish (again bounded), frees TMEM and returns.
+#include <map>
+#include <mutex>
+#include <vector>
+
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -40,8 +44,9 @@ template <int BN, int EK> struct Cfg {
                                       ((uint32_t)(BM >> 4) << 24);
 };
 
-__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int* tm, int* tn) {
-    constexpr int G = 8;  // M-tiles per raster group, so concurrent CTAs share A and B panels in L2
+// G M-tiles per raster group (4, 8 or 16, chosen per product by the autotuner), so that concurrent
+// CTAs share A and B panels in L2
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int G, int* tm, int* tn) {
     const int span = G * tiles_n;
     const int group = tile / span;
     const int first = group * G;
@@ -66,6 +71,7 @@ struct GemmProblem {
     int k_mult;
     int accumulate;
     int vec_ok;
+    int raster;
     const float* scale;  // device factor applied to the product (FP8), or null
 };
 template <int G> struct GemmTable {
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             int tm, tn;
-            tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, &tm, &tn);
+            tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, pr.raster, &tm, &tn);
             const int num_kb = problem_kb<BK>(pr);
             for (int kb = 0; kb < num_kb; ++kb) {
                 if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
             if (!mbar_wait(smem_u32(&bar_tfull[acc]), aph, &s_abort)) break;
             tc_fence_after();
             int tm, tn;
-            tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, &tm, &tn);
+            tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, pr.raster, &tm, &tn);
             const int row = tm * BM + q * 32 + lane;
             const int M = pr.M, N = pr.N;
             const float sc = pr.scale != nullptr ? *pr.scale : 1.0f;
@@ -309,9 +315,9 @@ int num_sms() {
 }
 
 // Fill one table entry; returns false when a tensor map cannot be made.
-bool fill_problem(GemmProblem* pr, int BN, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
-                  int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out, int64_t ldo, int accumulate,
-                  int elem, const float* scale) {
+bool fill_problem(GemmProblem* pr, int BN, int raster, const void* A, int64_t lda, const void* B, int64_t ldb,
+                  int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
+                  int64_t ldo, int accumulate, int elem, const float* scale) {
     const int esize = elem == GEMM_ELEM_E4M3 ? 1 : 2;
     if (!make_map(&pr->mapA, A, M, kdim, lda, BM, esize) || !make_map(&pr->mapB, B, N, kdim, ldb, BN, esize)) return false;
     pr->scale = scale;
@@ -326,6 +332,7 @@ bool fill_problem(GemmProblem* pr, int BN, const void* A, int64_t lda, const voi
     pr->k_mult = k_mult;
     pr->accumulate = accumulate;
     pr->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (ldo % 4 == 0);
+    pr->raster = raster;
     return true;
 }
 
@@ -362,7 +369,50 @@ bool gemm_args_ok(const void* A, int64_t lda, const void* B, int64_t ldb, int64_
     return !((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15));
 }
 
+// ---------------------------------------------------------------- tile choices
+// The tile width (BN) and raster group of each product come from a process-wide table filled by
+// the autotuner (bmm_autotune_gemm), keyed by element kind and the rounded-up base-2 logarithms of
+// M, N and K; shapes never tuned take BN = 128 for N <= 128, else 256, and raster group 8.  Neither
+// choice changes a result: every output element is the same dot product in the same K order.
+std::mutex& tune_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+std::map<uint64_t, TileChoice>& tune_table() {
+    static std::map<uint64_t, TileChoice> t;
+    return t;
+}
+uint64_t tune_key(int elem, int64_t M, int64_t N, int64_t K) {
+    auto lg = [](int64_t v) {
+        uint64_t b = 0;
+        while (b < 62 && (int64_t(1) << b) < v) ++b;
+        return b;
+    };
+    return ((uint64_t)elem << 24) | (lg(M) << 16) | (lg(N) << 8) | lg(K);
+}
+
 }  // namespace
+
+TileChoice gemm_tile_choice(int elem, int64_t M, int64_t N, int64_t K) {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    const auto it = tune_table().find(tune_key(elem, M, N, K));
+    if (it != tune_table().end()) return it->second;
+    return TileChoice{N <= 128 ? 128 : 256, 8};
+}
+
+bool gemm_tile_valid(const TileChoice& c) {
+    return (c.bn == 128 || c.bn == 256) && (c.raster == 4 || c.raster == 8 || c.raster == 16);
+}
+
+void gemm_tile_set(int elem, int64_t M, int64_t N, int64_t K, const TileChoice& c) {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    tune_table()[tune_key(elem, M, N, K)] = c;
+}
+
+void gemm_tile_clear() {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    tune_table().clear();
+}
 
 bool tc_gemm_supported() {
     int dev = 0, major = 0, minor = 0;
@@ -377,11 +427,12 @@ cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64
                                 int accumulate, DevStatus* st, cudaStream_t s, int elem, const float* scale) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (!gemm_args_ok(A, lda, B, ldb, M, N, kdim, k_host, k_dev, elem)) return cudaErrorInvalidValue;
-    const int BN = N <= 128 ? 128 : 256;
+    const TileChoice tc = gemm_tile_choice(elem, M, N, kdim);
+    const int BN = tc.bn;
     GemmTable<1> tab;
     tab.count = 1;
-    if (!fill_problem(&tab.prob[0], BN, A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo, accumulate, elem,
-                      scale))
+    if (!fill_problem(&tab.prob[0], BN, tc.raster, A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo,
+                      accumulate, elem, scale))
         return cudaErrorInvalidValue;
     tab.prob[0].tile_begin = 0;
     tab.total_tiles = tab.prob[0].tiles_m * tab.prob[0].tiles_n;
@@ -390,6 +441,8 @@ cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64
 
 cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, DevStatus* st, cudaStream_t s) {
     // products are grouped by tile width and element kind; each launch takes up to kMaxGroup of them
+    std::vector<TileChoice> choice((size_t)count);
+    for (int64_t i = 0; i < count; ++i) choice[i] = gemm_tile_choice(args[i].elem, args[i].M, args[i].N, args[i].kdim);
     for (int pass = 0; pass < 4; ++pass) {
         const int BN = (pass & 1) ? 256 : 128;
         const int elem = pass >> 1;
@@ -407,18 +460,88 @@ cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, Dev
             if (i == count) break;
             const GemmArgs& g = args[i];
             if (g.M <= 0 || g.N <= 0) continue;
-            if ((g.N <= 128 ? 128 : 256) != BN || g.elem != elem) continue;
+            if (choice[i].bn != BN || g.elem != elem) continue;
             if (!gemm_args_ok(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.elem))
                 return cudaErrorInvalidValue;
             GemmProblem& pr = tab.prob[tab.count];
-            if (!fill_problem(&pr, BN, g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out,
-                              g.ldo, g.accumulate, g.elem, g.scale))
+            if (!fill_problem(&pr, BN, choice[i].raster, g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev,
+                              g.k_mult, g.out, g.ldo, g.accumulate, g.elem, g.scale))
                 return cudaErrorInvalidValue;
             pr.tile_begin = tab.total_tiles;
             tab.total_tiles += pr.tiles_m * pr.tiles_n;
             ++tab.count;
         }
     }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- autotuner
+static int64_t align256(int64_t b) { return round_up(b, 256); }
+
+int64_t gemm_autotune_bytes(int64_t M, int64_t N, int64_t K, int elem) {
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    const int64_t es = elem == GEMM_ELEM_E4M3 ? 1 : 2, bk = elem == GEMM_ELEM_E4M3 ? 128 : 64;
+    const int64_t Kp = round_up(K, bk);
+    return align256(M * Kp * es) + align256(N * Kp * es) + align256(M * N * 4);
+}
+
+// Times every (BN, raster group) candidate on scratch operands of shape M x K and N x K (the
+// contents do not affect the result's timing in a way that matters: constant operands), one
+// warm-up launch and three timed launches each on stream s, and records the fastest in the table.
+// Synchronises s.  scratch: gemm_autotune_bytes(M, N, K, elem) bytes, 256-byte aligned.
+cudaError_t gemm_autotune(int64_t M, int64_t N, int64_t K, int elem, void* scratch, size_t bytes, DevStatus* st,
+                          cudaStream_t s, TileChoice* best_out, float* best_ms) {
+    if (M <= 0 || N <= 0 || K <= 0 || M > 0x7fffffff || N > 0x7fffffff) return cudaErrorInvalidValue;
+    if ((int64_t)bytes < gemm_autotune_bytes(M, N, K, elem) || (reinterpret_cast<uintptr_t>(scratch) & 255))
+        return cudaErrorInvalidValue;
+    const int64_t es = elem == GEMM_ELEM_E4M3 ? 1 : 2, bk = elem == GEMM_ELEM_E4M3 ? 128 : 64;
+    const int64_t Kp = round_up(K, bk);
+    char* base = static_cast<char*>(scratch);
+    void* A = base;
+    void* B = base + align256(M * Kp * es);
+    float* out = reinterpret_cast<float*>(base + align256(M * Kp * es) + align256(N * Kp * es));
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(A, 0x3c, (size_t)(M * Kp * es), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(B, 0x3c, (size_t)(N * Kp * es), s)) != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+    TileChoice best{0, 0};
+    float best_t = 0.f;
+    for (int bn : {128, 256}) {
+        for (int raster : {4, 8, 16}) {
+            GemmTable<1> tab;
+            tab.count = 1;
+            if (!fill_problem(&tab.prob[0], bn, raster, A, Kp, B, Kp, M, N, Kp, Kp, nullptr, 1, out, N, 0, elem, nullptr)) {
+                e = cudaErrorInvalidValue;
+                break;
+            }
+            tab.prob[0].tile_begin = 0;
+            tab.total_tiles = tab.prob[0].tiles_m * tab.prob[0].tiles_n;
+            float t_min = 0.f;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                cudaEventRecord(e0, s);
+                e = launch_any<1>(bn, elem, tab, st, s);
+                cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (rep == 1 || (rep > 1 && t < t_min)) t_min = t;  // launch 0 is the warm-up
+            }
+            if (e != cudaSuccess) break;
+            if (best.bn == 0 || t_min < best_t) {
+                best = TileChoice{bn, raster};
+                best_t = t_min;
+            }
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    gemm_tile_set(elem, M, N, Kp, best);
+    if (best_out) *best_out = best;
+    if (best_ms) *best_ms = best_t;
     return cudaSuccess;
 }
 

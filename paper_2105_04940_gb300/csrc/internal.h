@@ -159,6 +159,18 @@ struct GemmArgs {
     const float* scale = nullptr;
 };
 cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, DevStatus* st, cudaStream_t s);
+// Tile width (BN, 128 or 256) and raster group (4, 8 or 16 M-tiles) of a tensor-core GEMM: from the
+// autotuner's table when the shape's bucket was tuned, else BN = 128 for N <= 128 (else 256) and 8.
+struct TileChoice {
+    int bn, raster;
+};
+TileChoice gemm_tile_choice(int elem, int64_t M, int64_t N, int64_t K);
+bool gemm_tile_valid(const TileChoice& c);
+void gemm_tile_set(int elem, int64_t M, int64_t N, int64_t K, const TileChoice& c);
+void gemm_tile_clear();
+int64_t gemm_autotune_bytes(int64_t M, int64_t N, int64_t K, int elem);
+cudaError_t gemm_autotune(int64_t M, int64_t N, int64_t K, int elem, void* scratch, size_t bytes, DevStatus* st,
+                          cudaStream_t s, TileChoice* best_out, float* best_ms);
 
 // ---- backward.cu
 int64_t unique_scratch_bytes(int64_t space, int64_t count);

@@ -294,6 +294,84 @@ class _Lazy:
 SampledMatmul = _Lazy()
 
 
+def autotune(shapes, gemm_mode: int = A.GEMM_BF16, device=None) -> dict:
+    """Tune the tensor-core GEMM tiles for the sampled products of ``shapes`` ((m, p, L) triples):
+    one bmm_autotune_gemm call per distinct (log2 m, log2 p, log2 K) bucket, on a scratch tensor
+    allocated here.  Synchronises; call it before timing or capturing a graph.  Returns
+    {(m, p, L): {"bn", "raster", "ms"}} for the shapes that were timed (one per bucket)."""
+    torch = _torch()
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    done, out, ws = set(), {}, None
+
+    def lg(v):
+        return int(np.ceil(np.log2(max(int(v), 1))))
+
+    unit = 128 if gemm_mode == A.GEMM_E4M3 else 64
+    mult = 3 if gemm_mode == A.GEMM_SPLIT_BF16 else 1
+    for m, p, L in shapes:
+        key = (lg(m), lg(p), lg(mult * ((int(L) + unit - 1) // unit) * unit))
+        if key in done:
+            continue
+        done.add(key)
+        need = A.bmm_autotune_workspace_size(int(m), int(p), int(L), gemm_mode)
+        if need == 0:
+            raise ValueError(f"cannot tune shape {(m, p, L)} in mode {gemm_mode}")
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        out[(int(m), int(p), int(L))] = A.bmm_autotune_gemm(int(m), int(p), int(L), gemm_mode, ws)
+    return out
+
+
+def autotune_batched(probs: list, results: list, cs, gemm_mode: int = A.GEMM_BF16, outs=None, reps: int = 3) -> dict:
+    """Tune the GEMM tiles of a batch for its grouped launch, whose best tiles differ from those of
+    each product alone (many products share the GPU).  Times the batch's own bmm_apply_batched
+    (the draws of ``results``, eager, CUDA events, best of ``reps``) under each policy: the default
+    rule, every uniform (tile width, raster group), and the per-shape choices of autotune(); keeps
+    the fastest in the library's table.  Synchronises; call it before capturing a graph.  The
+    outputs are overwritten.  Returns {"choice": name, "ms": {policy: ms}}."""
+    torch = _torch()
+    shapes = [(int(p.M.shape[0]), int(p.N.shape[1]), int(c)) for p, c in zip(probs, cs)]
+    if outs is None:
+        outs = [r["out"] for r in results]
+    unit = results[0]["unit"] if results else A.UNIT_COLUMN
+
+    def apply():
+        A.bmm_apply_batched([p.M for p in probs], [p.N for p in probs], [p.B for p in probs], unit,
+                            [r["idx"] for r in results], [r["scale"] for r in results], [c for *_, c in shapes],
+                            gemm_mode, outs, False, [p.ws for p in probs])
+
+    def timed():
+        apply()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(max(1, reps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            apply()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def uniform(bn, ra):
+        A.bmm_autotune_clear()
+        for m, p, L in shapes:
+            A.bmm_autotune_set(m, p, L, gemm_mode, bn, ra)
+
+    policies = {"default": A.bmm_autotune_clear}
+    for bn in (128, 256):
+        for ra in (4, 8, 16):
+            policies[f"bn{bn}/r{ra}"] = (lambda bn=bn, ra=ra: uniform(bn, ra))
+    policies["per_shape"] = lambda: (A.bmm_autotune_clear(), autotune(shapes, gemm_mode, probs[0].M.device))
+    ms = {}
+    for name, setp in policies.items():
+        setp()
+        ms[name] = timed()
+    best = min(ms, key=ms.get)
+    policies[best]()
+    return {"choice": best, "ms": ms}
+
+
 def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF16, outs=None, streams=None,
                 c0: int | None = None, fmode: int = A.F_TC, fused_stats: bool = False,
                 grouped_stats: bool = True) -> list:

@@ -64,3 +64,27 @@ def test_product_path_fails_loudly_without_a_gpu():
     import paper_2105_04940_gb300 as P
     with pytest.raises(RuntimeError):
         P.prepare(torch.zeros(4, 4), torch.zeros(4, 4), np.array([0, 2, 4]), max_draws=2)
+
+
+def test_autotune_table_host_side():
+    """The GEMM tile table (no device access): untuned shapes take the default rule, a recorded
+    choice covers its whole bucket (rounded-up log2 of m, p and the GEMM depth), invalid choices and
+    modes are refused, and clear forgets everything."""
+    import paper_2105_04940_gb300 as P
+    A = P._abi
+    A.load()
+    A.bmm_autotune_clear()
+    assert A.bmm_autotune_get(300, 100, 517, A.GEMM_BF16) == {"bn": 128, "raster": 8}
+    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": 256, "raster": 8}
+    A.bmm_autotune_set(300, 520, 517, A.GEMM_BF16, 128, 16)
+    assert A.bmm_autotune_get(300, 520, 600, A.GEMM_BF16) == {"bn": 128, "raster": 16}  # same bucket
+    assert A.bmm_autotune_get(300, 520, 2000, A.GEMM_BF16) == {"bn": 256, "raster": 8}  # depth bucket differs
+    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_E4M3) == {"bn": 256, "raster": 8}  # element kind differs
+    for bad in ((300, 520, 517, A.GEMM_BF16, 192, 8), (300, 520, 517, A.GEMM_BF16, 128, 5),
+                (300, 520, 517, A.GEMM_F64, 128, 8), (0, 520, 517, A.GEMM_BF16, 128, 8)):
+        with pytest.raises(A.BmmError):
+            A.bmm_autotune_set(*bad)
+    assert A.bmm_autotune_workspace_size(300, 520, 517, A.GEMM_F64) == 0
+    assert A.bmm_autotune_workspace_size(300, 520, 517, A.GEMM_BF16) > 256 + 2 * (300 + 520) * 576
+    A.bmm_autotune_clear()
+    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": 256, "raster": 8}

@@ -1,0 +1,105 @@
+"""GEMM tile autotuner on the GPU: every (tile width, raster group) choice gives the same sampled
+product bit for bit (single and grouped launches), and the tuner records one of the candidates."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from tests._gpu_util import host, to_dev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CHOICES = [(bn, r) for bn in (128, 256) for r in (4, 8, 16)]
+
+
+@pytest.fixture(scope="module")
+def bmm():
+    import paper_2105_04940_gb300 as P
+    P.build()
+    P._abi.load()
+    return P
+
+
+@pytest.mark.parametrize("mode", ["bf16", "split_bf16", "e4m3"])
+def test_tile_choices_do_not_change_results(bmm, mode):
+    A = bmm._abi
+    gm = bmm.MODES[mode]
+    off = S.block_offsets_uneven(6000, 60, 40, 160, seed=61)
+    M, N = S.scaled_gaussian(700, 6000, 520, off, 1.0, seed=62, dtype=np.float32)
+    Mt, Nt = to_dev(M), to_dev(N)
+    L = 1100
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=gm)
+    r = bmm.run(prob, "ONC", L, seed=3, compute_product=False)
+    A.bmm_autotune_clear()
+    outs = []
+    for bn, ra in CHOICES:
+        A.bmm_autotune_set(700, 520, L, gm, bn, ra)
+        out = torch.full((700, 520), float("nan"), dtype=torch.float32, device=Mt.device)
+        A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, gm, out, False, prob.ws)
+        bmm.check_status(prob)
+        outs.append(host(out))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    assert np.all(np.isfinite(outs[0]))
+    # the tuner picks one candidate and records it for the shape
+    ws = torch.empty(A.bmm_autotune_workspace_size(700, 520, L, gm), dtype=torch.uint8, device=Mt.device)
+    res = A.bmm_autotune_gemm(700, 520, L, gm, ws)
+    assert (res["bn"], res["raster"]) in CHOICES and res["ms"] > 0
+    assert A.bmm_autotune_get(700, 520, L, gm) == {"bn": res["bn"], "raster": res["raster"]}
+    out = torch.empty(700, 520, dtype=torch.float32, device=Mt.device)
+    A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, gm, out, False, prob.ws)
+    np.testing.assert_array_equal(host(out), outs[0])
+    A.bmm_autotune_clear()
+
+
+def test_grouped_launch_mixed_choices(bmm):
+    """bmm_apply_batched with products whose recorded tile widths differ: each product lands in the
+    launch of its own width and equals its single-product result."""
+    A = bmm._abi
+    gm = A.GEMM_BF16
+    A.bmm_autotune_clear()
+    probs, samples, cs, shapes = [], [], [], [(300, 200), (520, 136), (128, 520), (700, 300)]
+    for i, (m, p) in enumerate(shapes):
+        off = S.block_offsets_uneven(3000, 30, 40, 160, seed=70 + i)
+        M, N = S.scaled_gaussian(m, 3000, p, off, 1.0, seed=80 + i, dtype=np.float32)
+        pr = bmm.prepare(to_dev(M), to_dev(N), off, max_draws=600, gemm_mode=gm)
+        r = bmm.run(pr, "ONC", 600, seed=i, compute_product=False)
+        probs.append(pr)
+        samples.append(r)
+        cs.append(600)
+        A.bmm_autotune_set(m, p, 600, gm, (128, 256)[i % 2], (4, 8, 16)[i % 3])
+    single = []
+    for pr, r in zip(probs, samples):
+        out = torch.empty(pr.M.shape[0], pr.N.shape[1], dtype=torch.float32, device=pr.M.device)
+        A.bmm_apply(pr.M, pr.N, pr.B, A.UNIT_COLUMN, r["idx"], r["scale"], 600, gm, out, False, pr.ws)
+        single.append(host(out))
+    outs = [torch.empty(pr.M.shape[0], pr.N.shape[1], dtype=torch.float32, device=pr.M.device) for pr in probs]
+    A.bmm_apply_batched([pr.M for pr in probs], [pr.N for pr in probs], [pr.B for pr in probs], A.UNIT_COLUMN,
+                        [r["idx"] for r in samples], [r["scale"] for r in samples], cs, gm, outs, False,
+                        [pr.ws for pr in probs])
+    for pr in probs:
+        bmm.check_status(pr)
+    for a_, b_ in zip(single, outs):
+        np.testing.assert_array_equal(host(b_), a_)
+    A.bmm_autotune_clear()
+
+
+def test_batch_level_tuning_keeps_results(bmm):
+    """autotune_batched times the batch's own grouped launch under each tile policy and keeps the
+    fastest; the products are unchanged bit for bit."""
+    A = bmm._abi
+    A.bmm_autotune_clear()
+    probs, cs = [], []
+    for i, (m, p) in enumerate([(256, 384), (640, 128), (384, 512)]):
+        off = S.block_offsets_uneven(4096, 64, 32, 100, seed=90 + i)
+        M, N = S.scaled_gaussian(m, 4096, p, off, 1.0, seed=95 + i, dtype=np.float32)
+        probs.append(bmm.prepare(to_dev(M), to_dev(N), off, max_draws=512, gemm_mode=A.GEMM_BF16))
+        cs.append(512)
+    res = bmm.run_batched(probs, "ONC", cs, [1, 2, 3], gemm_mode=A.GEMM_BF16)
+    before = [host(r["out"]).copy() for r in res]
+    tune = bmm.autotune_batched(probs, res, cs, A.GEMM_BF16)
+    assert tune["choice"] in tune["ms"] and len(tune["ms"]) == 8
+    res2 = bmm.run_batched(probs, "ONC", cs, [1, 2, 3], gemm_mode=A.GEMM_BF16)
+    for a_, r in zip(before, res2):
+        np.testing.assert_array_equal(host(r["out"]), a_)
+    A.bmm_autotune_clear()
