@@ -59,9 +59,7 @@ def parse():
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--split-stats", action="store_true",
-                    help="single product: norm pass, then the Gram-only f_k pass (default: one fused pass)")
-    ap.add_argument("--fused-stats", action="store_true",
-                    help="batched workload: statistics and f_k in one grouped pass per table of products")
+                    help="norm pass, then the Gram-only f_k pass (default: one fused statistics pass)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp", "precision", "paper"],
                     help="batched: 512 independent BF16 products of uneven shapes in one CUDA graph; "
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
@@ -416,7 +414,7 @@ def batched_arm(args, ws, rank, local):
 
     def batch():
         return P.run_batched(probs, "OPL", cs, seeds, gemm_mode=P._abi.GEMM_BF16, outs=outs, streams=streams,
-                             fused_stats=args.fused_stats)
+                             fused_stats=not args.split_stats)
 
     res = None
     for _ in range(args.warmup):
@@ -470,7 +468,7 @@ def batched_arm(args, ws, rank, local):
         "config": {"workload": f"batched: {len(probs)} BF16 products, m,p U{{128..2048/128}}, n U{{4096..65536/4096}}, "
                                "K=n/64 blocks of 32..128, c=K/8, OPL, one CUDA graph per batch, GEMM tiles autotuned",
                    "streams": args.streams,
-                   "statistics": "fused, grouped" if args.fused_stats else "norm pass per product, Gram pass grouped",
+                   "statistics": "norm pass per product, Gram pass grouped" if args.split_stats else "fused, grouped",
                    "products": len(probs), "input_gb": in_bytes / 1e9, "gemm_tflop": flops / 1e12,
                    "l2": "inputs larger than the 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "batch_ms": batch_ms, "eager_batch_ms": eager_ms,

@@ -141,7 +141,12 @@ def mat(t) -> Mat:
 
 
 def blocks(offsets_dev, n: int, max_nk: int) -> Blocks:
-    return Blocks(len(offsets_dev) - 1, n, max_nk, offsets_dev.data_ptr())
+    """bmm_blocks of a device int64 offsets tensor.  The struct keeps a reference to the tensor:
+    it holds only the raw device address, and a temporary tensor freed after this call would
+    hand that memory to the next allocation."""
+    b = Blocks(len(offsets_dev) - 1, n, max_nk, offsets_dev.data_ptr())
+    b._offsets_ref = offsets_dev
+    return b
 
 
 def stats(d: dict) -> Stats:

@@ -348,7 +348,7 @@ __device__ __forceinline__ bool squares_strided(const uint8_t* base, const Stage
 template <typename T>
 __device__ __forceinline__ bool squares_contig(const uint8_t* base, const StageInfo* info, uint64_t* bar_full,
                                                uint64_t* bar_empty, int& stage, uint32_t& ph, volatile int* abort_flag,
-                                               int cw, int lane, int nk, int d, double* xy) {
+                                               int cw, int lane, int nk, int d, float2* xy) {
     using TR = Tr<T>;
     constexpr int kCpc = 16 / (int)sizeof(T);
     const int t = 32 * cw + lane;
@@ -411,8 +411,14 @@ __device__ __forceinline__ bool squares_contig(const uint8_t* base, const StageI
             tot[u].renorm();
         }
     if (q == 0) {
-        if (in0) xy[r0 - d] = tot[0].both().value();
-        if (in1) xy[r0 + 64 - d] = tot[1].both().value();
+        if (in0) {
+            const FF f = tot[0].both();
+            xy[r0 - d] = make_float2(f.hi, f.lo);
+        }
+        if (in1) {
+            const FF f = tot[1].both();
+            xy[r0 + 64 - d] = make_float2(f.hi, f.lo);
+        }
     }
     return true;
 }
@@ -623,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ float2 part[STATS ? kConvWarps : 1][kMaxBlock];   // [warp][vector] float-float, one phase
-    __shared__ double xy_sum[STATS ? 2 : 1][kMaxBlock];           // [phase][vector]: x_i, y_i
+    __shared__ float2 xy_ff[STATS ? 2 : 1][kMaxBlock];            // [phase][vector]: x_i, y_i (float-float)
     __shared__ float2 rowpart[4][kMaxBlock];                      // off-diagonal sums per [quarter][row]
 
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
@@ -844,7 +850,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const bool ok = mn ? squares_strided<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw,
                                                                 lane, nk, dpos, part)
                                            : squares_contig<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw,
-                                                               lane, nk, dpos, xy_sum[phase]);
+                                                               lane, nk, dpos, xy_ff[phase]);
                         if (!ok) { aborted = true; break; }
                         reduce_parts = mn;
                     } else {
@@ -869,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             sum.add(o);
                             sum.renorm();
                         }
-                        xy_sum[STATS ? phase : 0][t] = sum.value();
+                        xy_ff[STATS ? phase : 0][t] = make_float2(sum.hi, sum.lo);
                     }
                     conv_sync(cs_bar, cs_uses, &s_abort);  // part[] is reused by the next phase
                 }
@@ -883,14 +889,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const StatsProblem& pr = tab.prob[bi.q];
             if constexpr (!STATS) conv_sync(cs_bar, cs_uses, &s_abort);  // s_seg[] is visible
             if (STATS && t < nk) {
-                pr.x[lo + t] = xy_sum[0][t];
-                pr.y[lo + t] = xy_sum[STATS ? 1 : 0][t];
+                const float2 xf = xy_ff[0][t], yf = xy_ff[STATS ? 1 : 0][t];
+                pr.x[lo + t] = (double)xf.x + (double)xf.y;
+                pr.y[lo + t] = (double)yf.x + (double)yf.y;
             }
             // off-diagonal Gram products from TMEM: rows = lanes of this warp's quadrant (operand
             // rows 0..127), the ten 16-column chunks of a slot split between the quadrant's four
             // warps; a product counts when both vectors belong to the same block of the window
             FF offf;
             offf.zero();
+            FF2 offp;  // main-Gram products, two columns at a time
+            offp.zero();
             const int u0 = 2 * it;
             const int q0 = u0 % 3, q1 = (u0 + 1) % 3;
             const int q4 = warp & 3, quarter = cw >> 2;
@@ -925,22 +934,38 @@ __global__ void __launch_bounds__(kThreads, 1)
                     TMEM_LD_32X32B_X16(lane_base + (uint32_t)(q0 * kSlotCols + c0), gm);
                     TMEM_LD_32X32B_X16(lane_base + (uint32_t)(q1 * kSlotCols + c0), gn);
                     tmem_ld_wait();
+                    if (c0 < kCornerCol) {
+                        // main Gram: operand rows r (< 128) and col; the missing rows >= 128 of a
+                        // wide block are the transposes of these columns.  Two columns per paired
+                        // instruction; a column outside the row's block adds an exact zero.
+#pragma unroll
+                        for (int e = 0; e < 16; e += 2) {
+                            float2 a2, b2;
+                            {
+                                const int col = c0 + e;
+                                const bool in = col >= blo && col < bhi && col != r;
+                                const float g = __uint_as_float(gm[e]);
+                                a2.x = in ? (col >= 128 ? 2.0f * g : g) : 0.f;
+                                b2.x = in ? __uint_as_float(gn[e]) : 0.f;
+                            }
+                            {
+                                const int col = c0 + e + 1;
+                                const bool in = col >= blo && col < bhi && col != r;
+                                const float g = __uint_as_float(gm[e + 1]);
+                                a2.y = in ? (col >= 128 ? 2.0f * g : g) : 0.f;
+                                b2.y = in ? __uint_as_float(gn[e + 1]) : 0.f;
+                            }
+                            offp.add_prod(a2, b2);
+                        }
+                        continue;
+                    }
+                    // the corner chunk of a wide block: operand rows R0 + r (>= 128 counted) and
+                    // 128 + (col - 144)
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
-                        const int col = c0 + e;
-                        if (col < kCornerCol) {
-                            // main Gram: operand rows r (< 128) and col; the missing rows >= 128 of a
-                            // wide block are the transposes of these columns
-                            if (col >= blo && col < bhi && col != r) {
-                                const float g = __uint_as_float(gm[e]);
-                                offf.add_prod(col >= 128 ? 2.0f * g : g, __uint_as_float(gn[e]));
-                            }
-                        } else if (wide) {
-                            // corner: operand rows R0 + r (>= 128 counted) and 128 + (col - 144)
-                            const int rr = r + TR::kCornerRow0, cc = 128 + (col - kCornerCol);
-                            if (rr >= 128 && rr < end && cc < end && cc != rr)
-                                offf.add_prod(__uint_as_float(gm[e]), __uint_as_float(gn[e]));
-                        }
+                        const int rr = r + TR::kCornerRow0, cc = 128 + e;
+                        if (rr >= 128 && rr < end && cc < end && cc != rr)
+                            offf.add_prod(__uint_as_float(gm[e]), __uint_as_float(gn[e]));
                     }
                 }
                 tc_fence_before();
@@ -953,20 +978,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 aborted = true;
             }
             ++it;
+            offf.add(offp.both());
             offf.renorm();
             rowpart[quarter][r] = make_float2(offf.hi, offf.lo);
             conv_sync(cs_bar, cs_uses, &s_abort);
             // per block of the window: warp cw takes blocks cw, cw + 16, ...; its lanes run over the
             // block's vectors from the block's first, so the sums do not depend on where the block
-            // sits in its window.  Off-diagonal sums as float-float (FP32 operations: the FP64 pipe
-            // is slow on this part), the statistics in FP64.
+            // sits in its window.  Every sum is float-float on the FP32 pipe (GB300's FP64 pipe is
+            // slow: FP64 square roots and sums took half of this epilogue): w_i = sqrt(x_i y_i) from
+            // a float-float product and square root, converted to FP64 once per block.  A warp
+            // whose x_i, y_i or x_i y_i leave [2^-100, 2^120] (where float-float loses digits or
+            // overflows) takes the FP64 path for its block instead.
             for (int j = cw; j < nblk; j += kConvWarps) {
                 const int b0 = s_seg[j], b1 = s_seg[j + 1];
                 const long long k = kb + j;
                 const bool ok = b0 >= 0 && b1 > b0 && b1 <= nk;
-                FF off;
+                FF off, fa, fs, fx, fy;
                 off.zero();
-                double sa = 0.0, ss = 0.0, sx = 0.0, sy = 0.0;
+                fa.zero(); fs.zero(); fx.zero(); fy.zero();
+                bool in_range = true;
                 if (ok) {
                     for (int i = b0 + lane; i < b1; i += 32) {
                         const int rr = dpos + i;
@@ -981,28 +1011,62 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                         if (STATS) {
-                            const double xi = xy_sum[0][i], yi = xy_sum[STATS ? 1 : 0][i];
+                            FF xi, yi;
+                            xi.hi = xy_ff[0][i].x; xi.lo = xy_ff[0][i].y;
+                            yi.hi = xy_ff[STATS ? 1 : 0][i].x; yi.lo = xy_ff[STATS ? 1 : 0][i].y;
+                            const FF xy = ff_mul(xi, yi);
+                            auto ok_range = [](float v) { return v == 0.f || (v >= 0x1p-100f && v <= 0x1p120f); };
+                            in_range = in_range && ok_range(xi.hi) && ok_range(yi.hi) && ok_range(xy.hi);
+                            fa.add(ff_sqrt(xy));
+                            fa.renorm();
+                            fs.add(xy);
+                            fs.renorm();
+                            fx.add(xi);
+                            fx.renorm();
+                            fy.add(yi);
+                            fy.renorm();
+                        }
+                    }
+                }
+                auto warp_ff = [&](FF& v) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        FF other;
+                        other.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+                        other.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+                        v.add(other);
+                        v.renorm();
+                    }
+                };
+                warp_ff(off);
+                double sa = 0.0, ss = 0.0, sx = 0.0, sy = 0.0;
+                if (STATS) {
+                    if (__all_sync(0xffffffffu, in_range)) {
+                        warp_ff(fa);
+                        warp_ff(fs);
+                        warp_ff(fx);
+                        warp_ff(fy);
+                        if (lane == 0) {  // FP64 once per block
+                            sa = fa.value();
+                            ss = fs.value();
+                            sx = fx.value();
+                            sy = fy.value();
+                        }
+                    } else if (ok) {
+                        for (int i = b0 + lane; i < b1; i += 32) {
+                            const double xi = (double)xy_ff[0][i].x + (double)xy_ff[0][i].y;
+                            const double yi = (double)xy_ff[STATS ? 1 : 0][i].x + (double)xy_ff[STATS ? 1 : 0][i].y;
                             const double xy = __dmul_rn(xi, yi);
                             sa += sqrt(xy);
                             ss += xy;
                             sx += xi;
                             sy += yi;
                         }
+                        sa = warp_sum(sa);
+                        ss = warp_sum(ss);
+                        sx = warp_sum(sx);
+                        sy = warp_sum(sy);
                     }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    FF other;
-                    other.hi = __shfl_xor_sync(0xffffffffu, off.hi, o);
-                    other.lo = __shfl_xor_sync(0xffffffffu, off.lo, o);
-                    off.add(other);
-                    off.renorm();
-                }
-                if (STATS) {
-                    sa = warp_sum(sa);
-                    ss = warp_sum(ss);
-                    sx = warp_sum(sx);
-                    sy = warp_sum(sy);
                 }
                 if (lane == 0) {
                     if (!ok) {

@@ -74,6 +74,28 @@ struct FF {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Float-float product and square root (about 2^-44 relative; inputs and results normal FP32
+// numbers): a b = a.hi b.hi (exact TwoProd) + the cross terms; sqrt(a) = s + (a - s^2) / (2 s) with
+// s = sqrt(a.hi) and the residual a.hi - s^2 exact through an FMA.
+__device__ __forceinline__ FF ff_mul(const FF& a, const FF& b) {
+    const float ph = __fmul_rn(a.hi, b.hi);
+    const float pl = __fadd_rn(__fmaf_rn(a.hi, b.hi, -ph), __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi)));
+    FF r;
+    r.hi = __fadd_rn(ph, pl);
+    r.lo = __fsub_rn(pl, __fsub_rn(r.hi, ph));
+    return r;
+}
+__device__ __forceinline__ FF ff_sqrt(const FF& a) {
+    FF r;
+    if (!(a.hi > 0.f)) { r.hi = 0.f; r.lo = 0.f; return r; }
+    const float sh = __fsqrt_rn(a.hi);
+    const float e = __fadd_rn(__fmaf_rn(-sh, sh, a.hi), a.lo);
+    const float sl = __fmul_rn(e, __frcp_rn(__fmul_rn(2.f, sh)));
+    r.hi = __fadd_rn(sh, sl);
+    r.lo = __fsub_rn(sl, __fsub_rn(r.hi, sh));
+    return r;
+}
+
 // Two independent float-float sums in paired FP32 registers: every operation is the one of FF
 // applied to both halves with the sm_100+ two-wide FP32 instructions (one issue slot for two
 // rounded operations), so each half is bit-identical to an FF that saw the same terms.
@@ -117,6 +139,16 @@ struct FF2 {
         r.hi = i ? hi.y : hi.x;
         r.lo = i ? lo.y : lo.x;
         return r;
+    }
+    // += a * b in each half (exact TwoProd residual)
+    __device__ __forceinline__ void add_prod(float2 a, float2 b) {
+        const float2 pr = __fmul2_rn(a, b);
+        const float2 pe = __ffma2_rn(a, b, neg(pr));
+        const float2 t = __fadd2_rn(hi, pr);
+        const float2 bp = __fadd2_rn(t, neg(hi));
+        const float2 e = __fadd2_rn(__fadd2_rn(hi, neg(__fadd2_rn(t, neg(bp)))), __fadd2_rn(pr, neg(bp)));
+        hi = t;
+        lo = __fadd2_rn(lo, __fadd2_rn(e, pe));
     }
     // the two halves added into one sum
     __device__ __forceinline__ FF both() const {

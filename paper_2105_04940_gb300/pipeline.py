@@ -373,7 +373,7 @@ def autotune_batched(probs: list, results: list, cs, gemm_mode: int = A.GEMM_BF1
 
 
 def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF16, outs=None, streams=None,
-                c0: int | None = None, fmode: int = A.F_TC, fused_stats: bool = False,
+                c0: int | None = None, fmode: int = A.F_TC, fused_stats: bool = True,
                 grouped_stats: bool = True) -> list:
     """Many independent products (the batched configuration).
 
@@ -382,8 +382,8 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
     through one bmm_apply_batched call, whose BF16 GEMMs share persistent tensor-core launches.
     Every step is an asynchronous C-ABI call, so the whole sequence can be captured with
     torch.cuda.graph and replayed as one graph launch.  Each Problem needs its own workspace.
-    ``fused_stats`` computes each product's norms and f_k in one tensor-core pass instead of the
-    norm pass plus the Gram pass.  ``grouped_stats`` (OPL with tensor-core f_k): the tensor-core
+    ``fused_stats`` (default) computes each product's norms and f_k in one tensor-core pass instead
+    of the norm pass plus the Gram pass.  ``grouped_stats`` (OPL with tensor-core f_k): the tensor-core
     statistics passes of all products share launches of many products (bmm_probs_batched), whose
     CTAs pull blocks from one work list instead of one small launch per product.
     """

@@ -303,7 +303,8 @@ def test_sampler_bit_exact_blocks_and_long_segment(bmm):
     n = 70000
     off = np.array([0, n])
     p = S.random_probabilities(off, seed=4, zero_frac=0.5)
-    B = bmm._abi.blocks(torch.as_tensor(off, device=dev), n, n)
+    off_dev = torch.as_tensor(off, device=dev)  # kept alive: the struct holds only its address
+    B = bmm._abi.blocks(off_dev, n, n)
     idx = torch.empty(3000, dtype=torch.int32, device=dev)
     scale = torch.empty(3000, dtype=torch.float64, device=dev)
     bmm.bmm_sample(to_dev(p), bmm._abi.UNIT_COLUMN, B, to_dev(np.array([3000])), 3000, 77, 0, idx, scale, ws)
@@ -313,7 +314,8 @@ def test_sampler_bit_exact_blocks_and_long_segment(bmm):
     # block sampling over K blocks
     off = S.block_offsets_uneven(20000, 2500, 4, 12, seed=1)
     pb = S.random_probabilities(np.array([0, 2500]), seed=2, zero_frac=0.3)
-    B = bmm._abi.blocks(torch.as_tensor(off, device=dev), 20000, 12)
+    off_dev = torch.as_tensor(off, device=dev)
+    B = bmm._abi.blocks(off_dev, 20000, 12)
     idx = torch.empty(700, dtype=torch.int32, device=dev)
     scale = torch.empty(700, dtype=torch.float64, device=dev)
     bmm.bmm_sample(to_dev(pb), bmm._abi.UNIT_BLOCK, B, None, 700, 5, 1, idx, scale, ws)

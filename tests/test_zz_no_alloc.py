@@ -59,7 +59,8 @@ def test_static_scratch_matches_workspace_entry_point():
     big_off = S.block_offsets_equal(nbig, kbig)
     Mb = torch.zeros((mbig, nbig), dtype=torch.bfloat16, device=dev)
     Nb = torch.zeros((nbig, 8), dtype=torch.bfloat16, device=dev)
-    Bb = A.blocks(torch.as_tensor(big_off, device=dev), nbig, int(np.diff(big_off).max()))
+    big_off_dev = torch.as_tensor(big_off, device=dev)  # kept alive: the struct holds only its address
+    Bb = A.blocks(big_off_dev, nbig, int(np.diff(big_off).max()))
     st_big = {k: torch.zeros(nbig if k in ("x", "y") else kbig, **f64) for k in ("x", "y", "a", "s", "mf", "nf")}
     status = torch.zeros(2, dtype=torch.int32, device=dev)
     with pytest.raises(A.BmmError) as err:
