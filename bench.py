@@ -551,7 +551,6 @@ def mlp_arm(args, ws, rank, local):
                                "c=64 blocks (L=4096), forward + backward", "parallelism": f"replicas x{ws}"},
         "exact_bf16_mlp_ms": exact_ms, "sampled_gemm_tflop_per_step": gemm_flops / 1e12,
         "clocks": clk.summary(), "gpu_launches": int(launches),
-        "autotune": {f"{k[0]}x{k[1]}xL{k[2]}": v for k, v in tuned.items()},
     }
     if rank == 0:
         print(json.dumps(result))

@@ -262,7 +262,9 @@ bmm_status bmm_apply_batched(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns
  *     dM^{(i)} += w_i G N_{(i)}^T,   dN_{(i)} += w_i M^{(i)T} G
  * (whole blocks for BMM_UNIT_BLOCK).  Columns/rows never drawn are left unchanged
  * (accumulate = 1) or set to zero (accumulate = 0).  Either of dM, dN may be NULL.
- *   G, dM, dN: row-major, dtype FP32 for the BF16 modes, FP64 for BMM_GEMM_F64.
+ *   G: row-major, FP32 for the BF16 mode, FP64 for BMM_GEMM_F64.  dM, dN: either storage order,
+ *   the dtype of G, or BF16 for the BF16 mode (each touched element is its FP32 value rounded to
+ *   BF16 once, after adding the stored value when accumulate = 1).
  */
 bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B,
                         int32_t unit, const double* p, const int64_t* ck, int64_t c,

@@ -599,23 +599,25 @@ BMM_API bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_ma
     if ((s = check_mat(G)) != BMM_OK) return s;
     if (G->layout != BMM_ROW_MAJOR || G->rows != M->rows || G->cols != N->cols) return BMM_ERR_SHAPE;
     if (G->dtype != gd) return BMM_ERR_DTYPE;
+    // gradients in the product's precision (FP64 / FP32), or BF16 for the BF16 mode
+    auto grad_dtype_ok = [&](int dt) { return dt == gd || (gd == BMM_F32 && dt == BMM_BF16); };
     if (dM) {
         if ((s = check_mat(dM)) != BMM_OK) return s;
         if (dM->rows != M->rows || dM->cols != M->cols) return BMM_ERR_SHAPE;
-        if (dM->dtype != gd) return BMM_ERR_DTYPE;
+        if (!grad_dtype_ok(dM->dtype)) return BMM_ERR_DTYPE;
     }
     if (dN) {
         if ((s = check_mat(dN)) != BMM_OK) return s;
         if (dN->rows != N->rows || dN->cols != N->cols) return BMM_ERR_SHAPE;
-        if (dN->dtype != gd) return BMM_ERR_DTYPE;
+        if (!grad_dtype_ok(dN->dtype)) return BMM_ERR_DTYPE;
     }
     if (gemm_mode != BMM_GEMM_F64 && !tc_gemm_supported()) return BMM_ERR_UNSUPPORTED;
     if (c > 0x7fffffffLL) return BMM_ERR_UNSUPPORTED;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     if (!accumulate) {
-        if (dM) BMM_TRY(launch_zero_matrix(const_cast<void*>(dM->data), gd, dM->layout == BMM_ROW_MAJOR ? dM->rows : dM->cols,
+        if (dM) BMM_TRY(launch_zero_matrix(const_cast<void*>(dM->data), dM->dtype, dM->layout == BMM_ROW_MAJOR ? dM->rows : dM->cols,
                                            dM->layout == BMM_ROW_MAJOR ? dM->cols : dM->rows, dM->ld, cs));
-        if (dN) BMM_TRY(launch_zero_matrix(const_cast<void*>(dN->data), gd, dN->layout == BMM_ROW_MAJOR ? dN->rows : dN->cols,
+        if (dN) BMM_TRY(launch_zero_matrix(const_cast<void*>(dN->data), dN->dtype, dN->layout == BMM_ROW_MAJOR ? dN->rows : dN->cols,
                                            dN->layout == BMM_ROW_MAJOR ? dN->cols : dN->rows, dN->ld, cs));
     }
     if (c == 0 || (!dM && !dN)) return BMM_OK;
@@ -651,7 +653,7 @@ BMM_API bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_ma
                                         round_up(pp, 64), nullptr, 1, static_cast<float*>(plan.outM), plan.ldOM, 0,
                                         dst, cs));
         const int mode = dM->layout == BMM_ROW_MAJOR ? VEC_STRIDED : VEC_CONTIG;
-        BMM_TRY(launch_scatter_grad(const_cast<void*>(dM->data), gd, dM->ld, mode, m, plan.outM, gd, plan.ldOM, false,
+        BMM_TRY(launch_scatter_grad(const_cast<void*>(dM->data), dM->dtype, dM->ld, mode, m, plan.outM, gd, plan.ldOM, false,
                                     plan.col, plan.w, plan.ext, plan.lmax, cs));
     }
     if (dN) {
@@ -669,7 +671,7 @@ BMM_API bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_ma
                                         round_up(m, 64), nullptr, 1, static_cast<float*>(plan.outN), plan.ldON, 0,
                                         dst, cs));
         const int mode = dN->layout == BMM_ROW_MAJOR ? VEC_CONTIG : VEC_STRIDED;
-        BMM_TRY(launch_scatter_grad(const_cast<void*>(dN->data), gd, dN->ld, mode, pp, plan.outN, gd, plan.ldON, true,
+        BMM_TRY(launch_scatter_grad(const_cast<void*>(dN->data), dN->dtype, dN->ld, mode, pp, plan.outN, gd, plan.ldON, true,
                                     plan.col, plan.w, plan.ext, plan.lmax, cs));
     }
     return BMM_OK;

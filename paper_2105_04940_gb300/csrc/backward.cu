@@ -299,6 +299,31 @@ __global__ void scatter_kernel<float, float>(float* __restrict__ dst, int64_t ds
     }
 }
 
+// BF16 gradient from FP32 products: each touched element is w_j * src rounded to FP32, added to the
+// stored value in FP32 and rounded to BF16 once (with a zeroed gradient: the FP32 value rounded)
+template <>
+__global__ void scatter_kernel<__nv_bfloat16, float>(__nv_bfloat16* __restrict__ dst, int64_t dst_ld, int dst_mode,
+                                                     int64_t len, const float* __restrict__ src, int64_t src_ld,
+                                                     bool src_rows, const int32_t* __restrict__ col,
+                                                     const double* __restrict__ w,
+                                                     const int64_t* __restrict__ ext_dev) {
+    const int64_t ext = *ext_dev;
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    if (j0 >= ext) return;
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int q = ty; q < 32; q += blockDim.y) {
+        int64_t j, r;
+        if (dst_mode == VEC_CONTIG) { j = j0 + q; r = r0 + tx; }
+        else { j = j0 + tx; r = r0 + q; }
+        if (j >= ext || r >= len) continue;
+        const int64_t c = col[j];
+        const float sv = src_rows ? src[j * src_ld + r] : src[r * src_ld + j];
+        __nv_bfloat16* d = (dst_mode == VEC_CONTIG) ? dst + c * dst_ld + r : dst + r * dst_ld + c;
+        *d = __float2bfloat16_rn(__fmaf_rn((float)w[j], sv, __bfloat162float(*d)));
+    }
+}
+
 cudaError_t launch_scatter_grad(void* dst, int dst_dtype, int64_t dst_ld, int dst_mode, int64_t len, const void* src,
                                 int src_dtype, int64_t src_ld, bool src_rows, const int32_t* col, const double* w,
                                 const int64_t* ext_dev, int64_t ext_max, cudaStream_t s) {
@@ -314,6 +339,10 @@ cudaError_t launch_scatter_grad(void* dst, int dst_dtype, int64_t dst_ld, int ds
         (count_launch(), scatter_kernel<float, float><<<grid, block, 0, s>>>(static_cast<float*>(dst), dst_ld, dst_mode, len,
                                                            static_cast<const float*>(src), src_ld, src_rows, col, w,
                                                            ext_dev));
+    else if (dst_dtype == BMM_BF16 && src_dtype == BMM_F32)
+        (count_launch(), scatter_kernel<__nv_bfloat16, float><<<grid, block, 0, s>>>(
+                             static_cast<__nv_bfloat16*>(dst), dst_ld, dst_mode, len, static_cast<const float*>(src),
+                             src_ld, src_rows, col, w, ext_dev));
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -269,8 +269,12 @@ def _autograd_function():
             gm = MODES[cfg["mode"]]
             gdt = torch.float64 if gm == A.GEMM_F64 else torch.float32
             G = G.to(gdt).contiguous()
-            dM = torch.empty(prob.M.shape, dtype=gdt, device=G.device) if ctx.needs_input_grad[0] else None
-            dN = torch.empty(prob.N.shape, dtype=gdt, device=G.device) if ctx.needs_input_grad[1] else None
+
+            def grad_dtype(t):  # BF16 inputs get BF16 gradients written by the library (one rounding)
+                return torch.bfloat16 if gm == A.GEMM_BF16 and t.dtype == torch.bfloat16 else gdt
+
+            dM = torch.empty(prob.M.shape, dtype=grad_dtype(prob.M), device=G.device) if ctx.needs_input_grad[0] else None
+            dN = torch.empty(prob.N.shape, dtype=grad_dtype(prob.N), device=G.device) if ctx.needs_input_grad[1] else None
             A.bmm_backward(G, prob.M, prob.N, prob.B, res["unit"], res["p"], res["ck"], cfg["c"], cfg["seed"],
                            res["sid"], gm, dM, dN, False, prob.ws)
             if dM is not None and dM.dtype != prob.M.dtype:

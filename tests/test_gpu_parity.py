@@ -590,6 +590,30 @@ def test_backward(bmm, mode, unit):
                                atol=1e-6 * np.abs(host(dM)).max())
 
 
+@pytest.mark.parametrize("unit", ["column", "block"])
+@pytest.mark.parametrize("layout", ["row", "col"])
+def test_backward_bf16_gradients(bmm, unit, layout):
+    """BF16 inputs, BF16 mode: gradients written as BF16 equal the FP32 gradients rounded to BF16,
+    bit for bit (every touched element is rounded once); untouched ones are zero; both storage
+    orders of the gradient."""
+    off, M, N, Mt, Nt = _problem(136, 1500, 200, 15, seed=23, dtype="bf16", lo=40, hi=160)
+    method, c = ("ONC", 400) if unit == "column" else ("SSM", 6)
+    gm = bmm._abi.GEMM_BF16
+    prob = bmm.prepare(Mt, Nt, off, max_draws=c, unit=bmm._abi.UNIT_BLOCK if unit == "block" else 0)
+    r = bmm.run(prob, method, c, seed=8, gemm_mode=gm)
+    Gt = to_dev(np.random.default_rng(6).standard_normal((136, 200)).astype(np.float32))
+    args = (Gt, Mt, Nt, prob.B, r["unit"], r["p"], r["ck"], c, 8, r["sid"], gm)
+    dM32 = torch.empty(Mt.shape, dtype=torch.float32, device=Mt.device)
+    dN32 = torch.empty(Nt.shape, dtype=torch.float32, device=Mt.device)
+    bmm.bmm_backward(*args, dM32, dN32, False, prob.ws)
+    dM16 = as_layout(torch.full(Mt.shape, 3.0, dtype=torch.bfloat16, device=Mt.device), layout)
+    dN16 = as_layout(torch.full(Nt.shape, 3.0, dtype=torch.bfloat16, device=Mt.device), layout)
+    bmm.bmm_backward(*args, dM16, dN16, False, prob.ws)
+    bmm.check_status(prob)
+    np.testing.assert_array_equal(host(dM16.float()), host(dM32.to(torch.bfloat16).float()))
+    np.testing.assert_array_equal(host(dN16.float()), host(dN32.to(torch.bfloat16).float()))
+
+
 def test_autograd_function(bmm):
     off = S.block_offsets_equal(512, 8)
     M, N = S.scaled_gaussian(64, 512, 64, off, 1.0, seed=11)
