@@ -1,6 +1,8 @@
 // api.cu -- the exported C ABI (include/bmm.h): argument checks, workspace carving, launch order.
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -249,8 +251,17 @@ bool valid_gemm_mode(int mode) {
 
 using namespace bmm;
 
+namespace bmm {
+namespace {
+struct SideStream;
+SideStream* side_stream();
+}  // namespace
+}  // namespace bmm
+
 BMM_API size_t bmm_workspace_size(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
                                   int64_t max_draws, int32_t gemm_mode) {
+    // the overlapped apply's side stream, created here, outside any graph capture (no error if no device)
+    if (side_stream() == nullptr) cudaGetLastError();
     if (check_problem(M, N, B) != BMM_OK || max_draws < 0 || !valid_gemm_mode(gemm_mode)) return 0;
     if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return 0;
     size_t need = 0;
@@ -545,12 +556,108 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
 }  // namespace
 }  // namespace bmm
 
+namespace bmm {
+namespace {
+// ---- overlapped apply: the GEMM of K-chunk c runs on a highest-priority side stream while the
+// gathers of chunk c + 1 run on the caller's stream (gathers are memory-bound, the GEMM
+// tensor-bound); the priority makes the block scheduler place the GEMM's persistent CTAs ahead of
+// the remaining gather CTAs, so the two share the SMs instead of running one after the other.
+// Ordering is by events only; the side stream forks from and joins back into the caller's stream
+// inside the call, so the call stays stream-ordered and can be captured in a CUDA graph.
+constexpr int kApplyChunks = 2;
+constexpr int64_t kChunkMinDraws = 4096;             // and m p >= 2^24: large products only
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join = nullptr;
+    cudaEvent_t done[kApplyChunks] = {};
+};
+// One side stream and its events per device, created on first use (before any graph capture
+// that uses them) and kept until exit; nullptr when they cannot be created.
+SideStream* side_stream() {
+    static std::mutex mu;
+    static std::map<int, SideStream*> per_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = per_dev.find(dev);
+    if (it != per_dev.end()) return it->second;
+    SideStream* ss = new SideStream;
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&ss->s, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; c < kApplyChunks && ok; ++c)
+        ok = cudaEventCreateWithFlags(&ss->done[c], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();  // the failure is not the caller's error
+        per_dev[dev] = nullptr;
+        return nullptr;
+    }
+    per_dev[dev] = ss;
+    return ss;
+}
+
+// Runs the deferred gathers and the GEMM of a column-sampled BF16 product in kApplyChunks
+// K-chunks (multiples of 64 draws).  Each chunk's GEMM adds its partial product to the output
+// (the first one overwrites unless accumulate), so the sum is over the chunks' FP32 partials.
+bmm_status apply_overlapped(const std::vector<GatherJob>& jobs, const GemmArgs& g, int64_t count, DevStatus* st,
+                            SideStream* ss, cudaStream_t cs) {
+    // the events are shared by every caller on this device: a record and the waits on it are
+    // enqueued under one lock, so no other caller's record can come in between
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    const int64_t chunk = round_up(ceil_div(count, kApplyChunks), 64);
+    BMM_TRY(cudaEventRecord(ss->fork, cs));
+    BMM_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+    int nchunks = 0;
+    for (int c = 0; c < kApplyChunks; ++c) {  // gathers, in order, on the caller's stream
+        const int64_t lo = c * chunk, ext = imin(count, lo + chunk) - lo;
+        if (ext <= 0) break;
+        std::vector<GatherJob> part(jobs);
+        for (GatherJob& j : part) {
+            j.col += lo;
+            j.w += lo;
+            j.ext = ext;
+            j.out = static_cast<__nv_bfloat16*>(j.out) + lo;
+        }
+        BMM_TRY(launch_gather_grouped(part.data(), (int64_t)part.size(), cs));
+        BMM_TRY(cudaEventRecord(ss->done[c], cs));
+        ++nchunks;
+    }
+    for (int c = 0; c < nchunks; ++c) {  // GEMMs, each after its chunk's gathers, on the side stream
+        const int64_t lo = c * chunk, ext = imin(count, lo + chunk) - lo, kseg = round_up(ext, 64);
+        BMM_TRY(cudaStreamWaitEvent(ss->s, ss->done[c], 0));
+        BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(g.A) + lo, g.lda,
+                                    static_cast<const __nv_bfloat16*>(g.B) + lo, g.ldb, g.M, g.N, kseg, kseg, nullptr,
+                                    1, g.out, g.ldo, c == 0 ? g.accumulate : 1, st, ss->s, GEMM_ELEM_BF16, nullptr,
+                                    g.kdim));
+    }
+    BMM_TRY(cudaEventRecord(ss->join, ss->s));
+    BMM_TRY(cudaStreamWaitEvent(cs, ss->join, 0));
+    return BMM_OK;
+}
+}  // namespace
+}  // namespace bmm
+
 BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
                              const int32_t* idx, const double* scale, int64_t count, int32_t gemm_mode,
                              const bmm_mat* out, int32_t accumulate, void* ws, size_t ws_bytes, bmm_stream_t stream) {
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     GemmArgs g;
     bool done = true;
+    if (gemm_mode == BMM_GEMM_BF16 && unit == BMM_UNIT_COLUMN && count >= kChunkMinDraws && M && N &&
+        M->rows * N->cols >= (int64_t(1) << 24)) {
+        SideStream* ss = side_stream();
+        if (ss != nullptr) {
+            std::vector<GatherJob> jobs;
+            bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs,
+                                         &g, &done, &jobs);
+            if (s != BMM_OK || done) return s;
+            return apply_overlapped(jobs, g, count, status_of(ws), ss, cs);
+        }
+    }
     bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs, &g, &done);
     if (s != BMM_OK || done) return s;
     BMM_TRY(launch_gemm_bf16_tc(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out, g.ldo,

@@ -424,10 +424,11 @@ bool tc_gemm_supported() {
 
 cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
                                 int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out, int64_t ldo,
-                                int accumulate, DevStatus* st, cudaStream_t s, int elem, const float* scale) {
+                                int accumulate, DevStatus* st, cudaStream_t s, int elem, const float* scale,
+                                int64_t tune_k) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (!gemm_args_ok(A, lda, B, ldb, M, N, kdim, k_host, k_dev, elem)) return cudaErrorInvalidValue;
-    const TileChoice tc = gemm_tile_choice(elem, M, N, kdim);
+    const TileChoice tc = gemm_tile_choice(elem, M, N, tune_k > 0 ? tune_k : kdim);
     const int BN = tc.bn;
     GemmTable<1> tab;
     tab.count = 1;

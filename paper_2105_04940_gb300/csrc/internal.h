@@ -131,11 +131,12 @@ enum GemmElem { GEMM_ELEM_BF16 = 0, GEMM_ELEM_E4M3 = 1 };
 // out[M x N] (+)= scale * A[M x K] * B[N x K]^T, A and B K-major, BF16 or e4m3 bytes, with row strides
 // lda/ldb (elements, 16-byte multiples).  Columns >= kdim of A and B read as zero.  The K loop runs
 // to k_mult * round_up(*k_dev, BK) if k_dev, else to k_host (a multiple of BK); BK = 64 (BF16) or
-// 128 (e4m3).  scale (device, e4m3 only) may be null.
+// 128 (e4m3).  scale (device, e4m3 only) may be null.  tune_k: the depth whose tile choice to use
+// (a K-chunk of a longer product takes the whole product's), kdim if 0.
 cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
                                 int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
                                 int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s,
-                                int elem = GEMM_ELEM_BF16, const float* scale = nullptr);
+                                int elem = GEMM_ELEM_BF16, const float* scale = nullptr, int64_t tune_k = 0);
 // K is k_host, or *k_dev rounded up to 64; k_max bounds it for the choice of K splits, whose
 // partial tiles go to part (gemm_f64_split_elems(M, N, k_max) doubles; without it, no split).
 cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,

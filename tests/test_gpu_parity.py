@@ -754,6 +754,35 @@ def test_batched_uneven_products_and_graph_replay(bmm):
         np.testing.assert_array_equal(host(b_).astype(np.float64), a_)
 
 
+@pytest.mark.parametrize("layout", ["row", "col"])
+def test_overlapped_apply_large_product(bmm, layout):
+    """A column-sampled BF16 product with m p >= 2^24 and >= 4096 draws runs in two K-chunks, the
+    second chunk's gathers overlapping the first chunk's GEMM on a side stream: within the BF16
+    bound of the oracle's product of the same draws (5000 draws: a ragged second chunk),
+    repeatable bit for bit, and accumulate adds onto the output."""
+    m, n, p, K = 4096, 8192, 4096, 128
+    off, M, N, Mt, Nt = _problem(m, n, p, K, seed=73, dtype=np.float32, lo=32, hi=96)
+    Mt = as_layout(Mt, layout)
+    L = 5000
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L)
+    r = bmm.run(prob, "ONC", L, seed=2, gemm_mode=bmm._abi.GEMM_BF16)
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]), host(r["scale"])
+    got = host(r["out"]).astype(np.float64)
+    rows = np.random.default_rng(1).choice(m, size=96, replace=False)  # oracle rows (a full product is slow)
+    want = oracle.sampled_product_columns(M[rows], N, idx, scale)
+    bound = product_bound(M[rows], N, idx, scale)
+    assert np.all(np.abs(got[rows] - want) <= _tol("bf16", L) * bound + 1e-300)
+    out2 = torch.empty_like(r["out"])
+    bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, r["idx"], r["scale"], L, bmm._abi.GEMM_BF16, out2, False,
+                  prob.ws)
+    np.testing.assert_array_equal(host(out2), host(r["out"]))
+    bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, r["idx"], r["scale"], L, bmm._abi.GEMM_BF16, out2, True,
+                  prob.ws)
+    bmm.check_status(prob)
+    np.testing.assert_allclose(host(out2)[rows], 2 * got[rows], rtol=2e-6, atol=1e-6 * np.abs(got).max())
+
+
 @pytest.mark.parametrize("dtype", [np.float32, "bf16"])
 @pytest.mark.parametrize("mode", ["bf16", "split_bf16"])
 @pytest.mark.parametrize("layout", ["row", "col"])
