@@ -558,14 +558,15 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
 
 namespace bmm {
 namespace {
-// ---- overlapped apply: the GEMM of K-chunk c runs on a highest-priority side stream while the
-// gathers of chunk c + 1 run on the caller's stream (gathers are memory-bound, the GEMM
-// tensor-bound); the priority makes the block scheduler place the GEMM's persistent CTAs ahead of
-// the remaining gather CTAs, so the two share the SMs instead of running one after the other.
-// Ordering is by events only; the side stream forks from and joins back into the caller's stream
-// inside the call, so the call stays stream-ordered and can be captured in a CUDA graph.
+// ---- overlapped apply: the product's rows are split in two; the GEMM of row half h runs on a
+// highest-priority side stream while the gathers of half h + 1 run on the caller's stream (the
+// strided gather of M is memory-bound, the GEMM tensor-bound; the priority makes the block
+// scheduler place the GEMM's persistent CTAs ahead of the remaining gather CTAs, so the two share
+// the SMs).  Each output element is the same full-depth dot product as in one launch, so the result
+// is bit-identical.  Ordering is by events only; the side stream forks from and joins back into the
+// caller's stream inside the call, so the call stays stream-ordered and can be captured in a graph.
 constexpr int kApplyChunks = 2;
-constexpr int64_t kChunkMinDraws = 4096;             // and m p >= 2^24: large products only
+constexpr int64_t kChunkMinDraws = 4096;             // and m >= 256, m p >= 2^24: large products only
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr;
@@ -599,40 +600,39 @@ SideStream* side_stream() {
     return ss;
 }
 
-// Runs the deferred gathers and the GEMM of a column-sampled BF16 product in kApplyChunks
-// K-chunks (multiples of 64 draws).  Each chunk's GEMM adds its partial product to the output
-// (the first one overwrites unless accumulate), so the sum is over the chunks' FP32 partials.
-bmm_status apply_overlapped(const std::vector<GatherJob>& jobs, const GemmArgs& g, int64_t count, DevStatus* st,
-                            SideStream* ss, cudaStream_t cs) {
+// Runs the deferred gathers (jobs[0]: columns of M into A, jobs[1]: rows of N into B) and the GEMM
+// of a column-sampled BF16 product in kApplyChunks row ranges of M (multiples of 128 rows).
+bmm_status apply_overlapped(const std::vector<GatherJob>& jobs, const GemmArgs& g, DevStatus* st, SideStream* ss,
+                            cudaStream_t cs) {
     // the events are shared by every caller on this device: a record and the waits on it are
     // enqueued under one lock, so no other caller's record can come in between
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    const int64_t chunk = round_up(ceil_div(count, kApplyChunks), 64);
+    const GatherJob& jM = jobs[0];
+    const int64_t rows = g.M, half = round_up(ceil_div(rows, kApplyChunks), 128);
+    const size_t esM = jM.v.dtype == BMM_F64 ? 8 : (jM.v.dtype == BMM_F32 ? 4 : 2);
     BMM_TRY(cudaEventRecord(ss->fork, cs));
     BMM_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+    BMM_TRY(launch_gather_grouped(&jobs[1], 1, cs));  // all of B first
     int nchunks = 0;
-    for (int c = 0; c < kApplyChunks; ++c) {  // gathers, in order, on the caller's stream
-        const int64_t lo = c * chunk, ext = imin(count, lo + chunk) - lo;
-        if (ext <= 0) break;
-        std::vector<GatherJob> part(jobs);
-        for (GatherJob& j : part) {
-            j.col += lo;
-            j.w += lo;
-            j.ext = ext;
-            j.out = static_cast<__nv_bfloat16*>(j.out) + lo;
-        }
-        BMM_TRY(launch_gather_grouped(part.data(), (int64_t)part.size(), cs));
+    for (int c = 0; c < kApplyChunks; ++c) {  // rows [lo, hi) of A, in order, on the caller's stream
+        const int64_t lo = c * half, hi = imin(rows, lo + half);
+        if (hi <= lo) break;
+        GatherJob part = jM;
+        // element r of a column of M: at data[r * ld + i] (strided) or data[i * ld + r] (contiguous)
+        part.v.data = static_cast<const char*>(jM.v.data) + (jM.v.mode == VEC_STRIDED ? lo * jM.v.ld : lo) * esM;
+        part.v.len = hi - lo;
+        part.out = static_cast<__nv_bfloat16*>(jM.out) + lo * jM.ldo;
+        BMM_TRY(launch_gather_grouped(&part, 1, cs));
         BMM_TRY(cudaEventRecord(ss->done[c], cs));
         ++nchunks;
     }
-    for (int c = 0; c < nchunks; ++c) {  // GEMMs, each after its chunk's gathers, on the side stream
-        const int64_t lo = c * chunk, ext = imin(count, lo + chunk) - lo, kseg = round_up(ext, 64);
+    for (int c = 0; c < nchunks; ++c) {  // GEMMs of the row ranges, each after its gathers
+        const int64_t lo = c * half, hi = imin(rows, lo + half);
         BMM_TRY(cudaStreamWaitEvent(ss->s, ss->done[c], 0));
-        BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(g.A) + lo, g.lda,
-                                    static_cast<const __nv_bfloat16*>(g.B) + lo, g.ldb, g.M, g.N, kseg, kseg, nullptr,
-                                    1, g.out, g.ldo, c == 0 ? g.accumulate : 1, st, ss->s, GEMM_ELEM_BF16, nullptr,
-                                    g.kdim));
+        BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(g.A) + lo * g.lda, g.lda, g.B, g.ldb, hi - lo,
+                                    g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out + lo * g.ldo, g.ldo, g.accumulate,
+                                    st, ss->s, GEMM_ELEM_BF16, nullptr, g.kdim));
     }
     BMM_TRY(cudaEventRecord(ss->join, ss->s));
     BMM_TRY(cudaStreamWaitEvent(cs, ss->join, 0));
@@ -648,14 +648,14 @@ BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_block
     GemmArgs g;
     bool done = true;
     if (gemm_mode == BMM_GEMM_BF16 && unit == BMM_UNIT_COLUMN && count >= kChunkMinDraws && M && N &&
-        M->rows * N->cols >= (int64_t(1) << 24)) {
+        M->rows >= 256 && M->rows * N->cols >= (int64_t(1) << 24)) {
         SideStream* ss = side_stream();
         if (ss != nullptr) {
             std::vector<GatherJob> jobs;
             bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs,
                                          &g, &done, &jobs);
             if (s != BMM_OK || done) return s;
-            return apply_overlapped(jobs, g, count, status_of(ws), ss, cs);
+            return apply_overlapped(jobs, g, status_of(ws), ss, cs);
         }
     }
     bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs, &g, &done);

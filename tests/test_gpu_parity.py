@@ -756,10 +756,10 @@ def test_batched_uneven_products_and_graph_replay(bmm):
 
 @pytest.mark.parametrize("layout", ["row", "col"])
 def test_overlapped_apply_large_product(bmm, layout):
-    """A column-sampled BF16 product with m p >= 2^24 and >= 4096 draws runs in two K-chunks, the
-    second chunk's gathers overlapping the first chunk's GEMM on a side stream: within the BF16
-    bound of the oracle's product of the same draws (5000 draws: a ragged second chunk),
-    repeatable bit for bit, and accumulate adds onto the output."""
+    """A column-sampled BF16 product with m p >= 2^24 and >= 4096 draws runs in two row halves, the
+    second half's gathers overlapping the first half's GEMM on a side stream: within the BF16
+    bound of the oracle's product of the same draws, bit-identical to the unsplit grouped path
+    (bmm_apply_batched) and repeatable, and accumulate adds onto the output."""
     m, n, p, K = 4096, 8192, 4096, 128
     off, M, N, Mt, Nt = _problem(m, n, p, K, seed=73, dtype=np.float32, lo=32, hi=96)
     Mt = as_layout(Mt, layout)
@@ -777,6 +777,10 @@ def test_overlapped_apply_large_product(bmm, layout):
     bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, r["idx"], r["scale"], L, bmm._abi.GEMM_BF16, out2, False,
                   prob.ws)
     np.testing.assert_array_equal(host(out2), host(r["out"]))
+    out3 = torch.empty_like(r["out"])
+    bmm.bmm_apply_batched([Mt], [Nt], [prob.B], bmm._abi.UNIT_COLUMN, [r["idx"]], [r["scale"]], [L],
+                          bmm._abi.GEMM_BF16, [out3], False, [prob.ws])
+    np.testing.assert_array_equal(host(out3), host(r["out"]))
     bmm.bmm_apply(Mt, Nt, prob.B, bmm._abi.UNIT_COLUMN, r["idx"], r["scale"], L, bmm._abi.GEMM_BF16, out2, True,
                   prob.ws)
     bmm.check_status(prob)
