@@ -38,9 +38,9 @@ SMALL = dict(m=256, n=4096, p=256, K=64, nk_lo=64, nk_hi=64, sigma=1.0, c_blocks
 PROFILE = dict(WORKLOAD, m=2048, p=2048)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
 # committed ncu capture (profiles/ncu_fused_stats_and_gemm_profilecase.md) of the fused statistics
-# pass: 1.0775 GB read + 12.0 MB written on the profiling case (m = p = 2048), which streams the
+# pass: 1.0762 GB read + 10.0 MB written on the profiling case (m = p = 2048), which streams the
 # inputs once; the full workload reads (8192 + 8192) / (2048 + 2048) = 4x those bytes.
-TRAFFIC = {"stats_f": 4 * 1.0775e9 + 12.0e6}
+TRAFFIC = {"stats_f": 4 * 1.0762e9 + 10.0e6}
 
 
 def parse():
