@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-error", action="store_true")
-    ap.add_argument("--split-stats", action="store_true",
-                    help="norm pass, then the Gram-only f_k pass (default: one fused statistics pass)")
+    ap.add_argument("--stats", default="auto", choices=["auto", "fused", "split"],
+                    help="fused: one statistics pass computes the norms and f_k; split: the norm pass, then the "
+                         "Gram-only f_k pass; auto: fused for one product, split for the batched workload")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp", "precision", "paper"],
                     help="batched: 512 independent BF16 products of uneven shapes in one CUDA graph; "
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
@@ -285,7 +286,7 @@ def native_arm(args, ws, rank, local):
 
     def step(s, events=None):
         return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events,
-                     fused_stats=not args.split_stats)
+                     fused_stats=args.stats != "split")
 
     for s in range(args.warmup):
         step(10_000 + s)
@@ -414,7 +415,7 @@ def batched_arm(args, ws, rank, local):
 
     def batch():
         return P.run_batched(probs, "OPL", cs, seeds, gemm_mode=P._abi.GEMM_BF16, outs=outs, streams=streams,
-                             fused_stats=not args.split_stats)
+                             fused_stats=args.stats == "fused")
 
     res = None
     for _ in range(args.warmup):
@@ -468,7 +469,7 @@ def batched_arm(args, ws, rank, local):
         "config": {"workload": f"batched: {len(probs)} BF16 products, m,p U{{128..2048/128}}, n U{{4096..65536/4096}}, "
                                "K=n/64 blocks of 32..128, c=K/8, OPL, one CUDA graph per batch, GEMM tiles autotuned",
                    "streams": args.streams,
-                   "statistics": "norm pass per product, Gram pass grouped" if args.split_stats else "fused, grouped",
+                   "statistics": "fused, grouped" if args.stats == "fused" else "norm pass grouped, Gram pass grouped",
                    "products": len(probs), "input_gb": in_bytes / 1e9, "gemm_tflop": flops / 1e12,
                    "l2": "inputs larger than the 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "batch_ms": batch_ms, "eager_batch_ms": eager_ms,

@@ -366,6 +366,63 @@ BMM_API bmm_status bmm_probs(const bmm_mat* M, const bmm_mat* N, const bmm_block
     return BMM_OK;
 }
 
+namespace bmm {
+namespace {
+// bmm_probs_batched without f_k: the norm pass of every FP32 / BF16 product in grouped launches
+// (x_i, y_i of all products, then a_k, s_k, ||M^k||_F^2, ||N_k||_F^2), then each product's
+// probabilities; other products take bmm_probs's path on their own.
+bmm_status probs_batched_norms(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns, const bmm_blocks* Bs,
+                               int32_t pkind, double* const* p_outs, const bmm_stats* sts, void* const* ws,
+                               const size_t* ws_bytes, bmm_stream_t stream) {
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<NormJobArgs> norms;
+    std::vector<BlockStatsArgs> blocks;
+    std::vector<int64_t> which;
+    for (int64_t i = 0; i < count; ++i) {
+        const bmm_mat* M = &Ms[i];
+        const bmm_mat* N = &Ns[i];
+        const bmm_blocks* B = &Bs[i];
+        const bmm_stats* st = &sts[i];
+        const bool eligible = check_problem(M, N, B) == BMM_OK && st->x && st->y && st->a && st->s && st->mf &&
+                              st->nf && (M->dtype == BMM_F32 || M->dtype == BMM_BF16) && N->dtype == M->dtype &&
+                              ws[i] != nullptr && (reinterpret_cast<uintptr_t>(ws[i]) & 255) == 0 &&
+                              ws_bytes[i] >= kStatusBytes;
+        if (!eligible) {
+            bmm_status s = bmm_probs(M, N, B, pkind, BMM_F_NONE, p_outs ? p_outs[i] : nullptr, st, ws[i], ws_bytes[i],
+                                     stream);
+            if (s != BMM_OK) return s;
+            continue;
+        }
+        // the row-slice buffer of the product's workspace serves its first strided set (M's columns
+        // when M is row-major); a second strided set in the same launch goes without slices
+        Carver cnt{nullptr};
+        ProbsPlan plan;
+        plan_probs(cnt, M, N, B, false, &plan);
+        if (check_ws(ws[i], ws_bytes[i], cnt.off) != BMM_OK) return BMM_ERR_WORKSPACE;
+        Carver cv{static_cast<char*>(ws[i]) + kStatusBytes};
+        plan_probs(cv, M, N, B, false, &plan);
+        const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
+        const bool m_slices = vM.mode == VEC_STRIDED;
+        norms.push_back(NormJobArgs{vM, st->x, m_slices ? plan.partial : nullptr, m_slices ? plan.partial_cap : 0});
+        norms.push_back(NormJobArgs{vN, st->y, m_slices ? nullptr : plan.partial, m_slices ? 0 : plan.partial_cap});
+        blocks.push_back(BlockStatsArgs{st->x, st->y, B->offsets, B->K, B->n, st->a, st->s, st->mf, st->nf,
+                                        status_of(ws[i])});
+        which.push_back(i);
+    }
+    if (!norms.empty()) BMM_TRY(launch_vec_sqnorms_grouped(norms.data(), (int64_t)norms.size(), cs));
+    if (!blocks.empty()) BMM_TRY(launch_block_stats_grouped(blocks.data(), (int64_t)blocks.size(), cs));
+    for (const int64_t i : which) {
+        double* p_out = p_outs ? p_outs[i] : nullptr;
+        if (p_out == nullptr) continue;
+        const bmm_stats* st = &sts[i];
+        BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, Bs[i].offsets, Bs[i].K, Bs[i].n, p_out,
+                             status_of(ws[i]), cs));
+    }
+    return BMM_OK;
+}
+}  // namespace
+}  // namespace bmm
+
 BMM_API bmm_status bmm_probs_batched(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns, const bmm_blocks* Bs,
                                      int32_t pkind, int32_t fmode, double* const* p_outs, const bmm_stats* sts,
                                      void* const* ws, const size_t* ws_bytes, bmm_stream_t stream) {
@@ -377,6 +434,8 @@ BMM_API bmm_status bmm_probs_batched(int64_t count, const bmm_mat* Ms, const bmm
     if (pkind < BMM_P_COL_OPT || pkind > BMM_P_BLK_NORMPROD) return BMM_ERR_ARG;
     if (fbase != BMM_F_NONE && fbase != BMM_F_EXACT && fbase != BMM_F_TC) return BMM_ERR_ARG;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (fbase == BMM_F_NONE && !reuse && pkind != BMM_P_COL_UNIFORM && pkind != BMM_P_BLK_PRODNORM)
+        return probs_batched_norms(count, Ms, Ns, Bs, pkind, p_outs, sts, ws, ws_bytes, stream);
     std::vector<StatsArgs> grouped;
     std::vector<int64_t> which;
     int* counter = nullptr;

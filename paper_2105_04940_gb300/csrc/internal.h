@@ -39,6 +39,22 @@ cudaError_t launch_vec_sqnorms(const VecSet& v, double* out, double* partial, in
 int64_t vec_sqnorms_partial_elems(const VecSet& v);
 cudaError_t launch_block_stats(const double* x, const double* y, const int64_t* off, int64_t K, int64_t n,
                                double* a, double* ssum, double* mf, double* nf, DevStatus* st, cudaStream_t s);
+// The same for many vector sets / products in one launch per kernel kind (FP32 and BF16 sets).
+struct NormJobArgs {
+    VecSet v;
+    double* out;
+    double* partial;      // strided sets: row-slice sums, vec_sqnorms_partial_elems(v) doubles (or null)
+    int64_t partial_cap;
+};
+cudaError_t launch_vec_sqnorms_grouped(const NormJobArgs* jobs, int64_t count, cudaStream_t s);
+struct BlockStatsArgs {
+    const double *x, *y;
+    const int64_t* off;
+    int64_t K, n;
+    double *a, *s, *mf, *nf;
+    DevStatus* st;
+};
+cudaError_t launch_block_stats_grouped(const BlockStatsArgs* args, int64_t count, cudaStream_t s);
 
 // ---- frob.cu
 // Per segment k: f[k] = || sum_t w_t u_t v_t^T ||_F^2 over the listed vectors of the segment,

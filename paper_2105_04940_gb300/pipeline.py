@@ -377,7 +377,7 @@ def autotune_batched(probs: list, results: list, cs, gemm_mode: int = A.GEMM_BF1
 
 
 def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF16, outs=None, streams=None,
-                c0: int | None = None, fmode: int = A.F_TC, fused_stats: bool = True,
+                c0: int | None = None, fmode: int = A.F_TC, fused_stats: bool = False,
                 grouped_stats: bool = True) -> list:
     """Many independent products (the batched configuration).
 
@@ -386,10 +386,12 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
     through one bmm_apply_batched call, whose BF16 GEMMs share persistent tensor-core launches.
     Every step is an asynchronous C-ABI call, so the whole sequence can be captured with
     torch.cuda.graph and replayed as one graph launch.  Each Problem needs its own workspace.
-    ``fused_stats`` (default) computes each product's norms and f_k in one tensor-core pass instead
-    of the norm pass plus the Gram pass.  ``grouped_stats`` (OPL with tensor-core f_k): the tensor-core
-    statistics passes of all products share launches of many products (bmm_probs_batched), whose
-    CTAs pull blocks from one work list instead of one small launch per product.
+    ``grouped_stats`` (OPL with tensor-core f_k): the statistics passes of all products share
+    launches of many products (bmm_probs_batched): the norm pass of every product, then the Gram
+    pass, whose CTAs pull blocks from one work list instead of one small launch per product.
+    ``fused_stats`` computes each product's norms and f_k in one tensor-core pass instead; with
+    many products in flight the two separate grouped passes are faster (each runs closer to its
+    own limit), so the split form is the default here, unlike run() for one product.
     """
     torch = _torch()
     main = torch.cuda.current_stream()
@@ -407,13 +409,8 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
         if fused_stats:
             A.bmm_probs_batched(Ms, Ns, Bs, A.P_COL_OPT, A.F_TC, ready, sts, wss)
         else:
-            # norm passes per product on the side streams, then the Gram passes grouped
-            for i, pr in enumerate(probs):
-                with torch.cuda.stream(streams[i % len(streams)]):
-                    A.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_NONE, ready[i], pr.st, pr.ws)
-            for s in streams:
-                if s is not main:
-                    main.wait_stream(s)
+            # the norm passes of all products grouped, then the Gram passes grouped
+            A.bmm_probs_batched(Ms, Ns, Bs, A.P_COL_OPT, A.F_NONE, ready, sts, wss)
             A.bmm_probs_batched(Ms, Ns, Bs, A.P_COL_OPT, A.F_TC | A.REUSE_STATS, None, sts, wss)
         for s in streams:
             if s is not main:

@@ -827,6 +827,42 @@ def test_apply_batched_equals_single_products(bmm, dtype, mode, layout):
         np.testing.assert_array_equal(host(b_), a_)
 
 
+def test_probs_batched_grouped_norm_pass(bmm):
+    """bmm_probs_batched without f_k runs the norm pass of all FP32 / BF16 products in grouped
+    launches (vector sets of every product in one grid, then the per-block sums): x_i, y_i, a_k,
+    s_k, ||M^k||_F^2, ||N_k||_F^2 and p within 1e-12 of the oracle, for both element types, all
+    storage orders, ragged and odd sizes, more products than one table holds, and an FP64 product
+    that takes the single-product path."""
+    rng = np.random.default_rng(37)
+    A = bmm._abi
+    cases = []
+    for i in range(600):  # more jobs than one table of the grouped launch holds
+        dt = torch.float64 if i == 5 else (torch.float32 if i % 3 else torch.bfloat16)
+        m = int(rng.choice([1, 7, 64, 200, 301]))
+        p = int(rng.choice([1, 24, 128, 136]))
+        n = int(rng.integers(1, 6)) * 128 + (int(rng.integers(0, 8)) if i % 5 == 0 else 0)
+        K = max(1, n // 64)
+        off = S.block_offsets_uneven(n, K, 1, 2 * n // K + 1, seed=500 + i)
+        M, N = S.scaled_gaussian(m, n, p, off, 1.5, seed=600 + i, dtype=np.float64)
+        Mt = as_layout(to_dev(M, dt), "col" if i % 4 == 1 else "row")
+        Nt = as_layout(to_dev(N, dt), "col" if i % 4 == 2 else "row")
+        cases.append((Mt, Nt, off, host(Mt.double()), host(Nt.double())))
+    probs = [bmm.prepare(Mt, Nt, off, max_draws=16) for Mt, Nt, off, _, _ in cases]
+    ps = [torch.empty(pr.n, dtype=torch.float64, device=pr.M.device) for pr in probs]
+    A.bmm_probs_batched([pr.M for pr in probs], [pr.N for pr in probs], [pr.B for pr in probs], A.P_COL_OPT,
+                        A.F_NONE, ps, [pr.st for pr in probs], [pr.ws for pr in probs])
+    for pr in probs:
+        bmm.check_status(pr)
+    for (Mt, Nt, off, M, N), pr, pv in zip(cases, probs, ps):
+        x, y = oracle.col_row_sq_norms(M, N)
+        st = oracle.block_stats(x, y, off)
+        assert rel_err(host(pr.st["x"]), x) < 1e-12
+        assert rel_err(host(pr.st["y"]), y) < 1e-12
+        for k in ("a", "s", "mf", "nf"):
+            assert rel_err(host(pr.st[k]), st[k]) < 1e-12, k
+        assert rel_err(host(pv), oracle.p_col_opt(st["w"], st["a"], off)) < 1e-12
+
+
 @pytest.mark.parametrize("reuse", [False, True])
 def test_probs_batched_matches_single_products(bmm, reuse):
     """bmm_probs_batched over products of both element types, all storage orders and one that the
