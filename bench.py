@@ -258,6 +258,33 @@ def stage_work(w, L, nk, method):
     }
 
 
+def time_norm_pass(P, prob, w, pk, reps=20):
+    """The statistics pass without f_k (x_i, y_i and the block sums: one read of M and N), timed
+    alone with CUDA events outside the timed region, so that its HBM fraction can be read apart
+    from the fused pass that the step runs."""
+    import torch
+
+    A = P._abi
+    p = torch.empty(w["n"], dtype=torch.float64, device=prob.M.device)
+    for _ in range(3):
+        A.bmm_probs(prob.M, prob.N, prob.B, A.P_COL_OPT, A.F_NONE, p, prob.st, prob.ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        A.bmm_probs(prob.M, prob.N, prob.B, A.P_COL_OPT, A.F_NONE, p, prob.st, prob.ws)
+    e1.record()
+    torch.cuda.synchronize()
+    P.check_status(prob)
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = (w["m"] * w["n"] + w["n"] * w["p"]) * 4 + 8 * (3 * w["n"] + 4 * w["K"])
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s", "frac": ach / pk["hbm"],
+            "ms": ms, "bytes": nbytes, "reps": reps,
+            "note": "norm pass and eq. 3.8 probabilities (BMM_F_NONE), inputs larger than L2, back to back"}
+
+
 def native_arm(args, ws, rank, local):
     import torch
 
@@ -353,10 +380,15 @@ def native_arm(args, ws, rank, local):
         r["peak_source"] = pk["source"] + (" (sustained bf16)" if r["bound"] == "tensor" else "")
         roofline = r
 
+    norm_alone = None
+    if args.method in ("OPL", "ONC", "ONU", "ONMCNR") and args.mode != "f64":
+        norm_alone = time_norm_pass(P, prob, w, pk)
+
     result = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": args.mode, "data": "synthetic",
+        "norm_pass_alone": norm_alone,
         "config": {"workload": workload_name(args), "method": args.method, "gemm": args.mode, "c": c,
                    "l2": "small case, L2-resident" if args.small else "inputs larger than the 129 MB L2, no flush",
                    "parallelism": f"replicas x{ws}"},

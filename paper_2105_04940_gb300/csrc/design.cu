@@ -100,25 +100,50 @@ __device__ __forceinline__ long long count_at(double lam, double g, long long nk
 // product RN64(lam * g) within 2^-53 of it, so RN64(lam * g) lies in [t - 4e-7 t, t + 4e-7 t].
 // When that interval holds one integer floor (or lies below 1, or at or above nk), the FP64 count
 // is known without an FP64 instruction (GB300's FP64 pipe is ~1/64 of FP32); otherwise it is
-// computed exactly.  The result is always count_at's.
-__device__ __forceinline__ long long count_fast(double lam, float lamf, float gf, int nk, double g) {
+// computed exactly.  The result is always count_at's.  Floors are taken by adding 2^23 rounding
+// down (exact for 0 <= x < 2^23, and >= 2^23 for larger x, which only the clamp at nk < 2^23
+// sees), so that no conversion instruction is needed.
+__device__ __forceinline__ long long count_fast(double lam, float lamf, float gf, int nk, const double* g) {
     const float t = __fmul_rn(lamf, gf);
-    if (lamf >= 1.17549435e-38f && gf >= 1.17549435e-38f && t >= 1.17549435e-38f && t <= 1.0e30f) {
+    if (lamf >= 1.17549435e-38f && gf >= 1.17549435e-38f && t >= 1.17549435e-38f && t <= 1.0e30f &&
+        nk < (1 << 23)) {
         const float mg = __fmul_rn(t, 4.0e-7f);
         const float th = __fadd_rn(t, mg);
         if (th < 1.0f) return 1;
         const float tl = __fsub_rn(t, mg);
-        if (nk < (1 << 24) && tl >= (float)nk) return nk;
-        const float fl = floorf(tl);
-        if (fl == floorf(th)) {
-            const long long v = (long long)fl;
-            return v < 1 ? 1 : (v > nk ? nk : v);
-        }
+        const int il = __float_as_int(__fadd_rd(tl, 8388608.0f)) - 0x4B000000;  // floor(tl)
+        if (il >= nk) return nk;
+        const int ih = __float_as_int(__fadd_rd(th, 8388608.0f)) - 0x4B000000;  // floor(th)
+        if (il == ih) return il < 1 ? 1 : il;
     }
-    return count_at(lam, g, nk);
+    return count_at(lam, *g, nk);
 }
 
 __device__ __forceinline__ double bits_to_lam(unsigned long long u) { return __longlong_as_double((long long)u); }
+
+// The smallest lam (as a bit pattern) with count_at(lam, g, nk) >= j, for 2 <= j <= nk and g > 0:
+// there trunc(RN(lam g)) >= j iff RN(lam g) >= j, which is monotone in lam.  RN(j / g) puts
+// RN(lam g) within a few units in the last place of j, so single bit-pattern steps from it end
+// within two; more than eight (or an overflow) report failure and the caller keeps bisecting.
+__device__ __forceinline__ bool breakpoint_of(double g, long long j, unsigned long long* out) {
+    const double jd = (double)j;
+    unsigned long long u = (unsigned long long)__double_as_longlong(__ddiv_rn(jd, g));
+    if (u >= kInfBits) return false;
+    int steps = 0;
+    if (__dmul_rn(bits_to_lam(u), g) >= jd) {
+        while (u > 0ull && __dmul_rn(bits_to_lam(u - 1ull), g) >= jd) {
+            --u;
+            if (++steps > 8) return false;
+        }
+    } else {
+        do {
+            ++u;
+            if (++steps > 8 || u >= kInfBits) return false;
+        } while (!(__dmul_rn(bits_to_lam(u), g) >= jd));
+    }
+    *out = u;
+    return true;
+}
 
 // exclusive scan of one value per thread over a 1024-thread block (exact)
 __device__ long long block_exclusive_scan(long long v, long long* sm, long long* total) {
@@ -155,6 +180,32 @@ __device__ long long block_sum_ll(long long v, long long* sm) {
     return t;
 }
 
+// two block-wide sums at once (exact), returned in place to every thread; sm holds 64 values
+__device__ void block_sum2_ll(long long* a, long long* b, long long* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    long long x = *a, y = *b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) {
+        sm[warp] = x;
+        sm[32 + warp] = y;
+    }
+    __syncthreads();
+    x = lane < nw ? sm[lane] : 0;
+    y = lane < nw ? sm[32 + lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    __syncthreads();  // every read done before sm is written again
+    *a = x;
+    *b = y;
+}
+
 // F(u) = sum_k count(u, k) over all blocks, by the whole CTA (exact)
 __device__ long long block_F(unsigned long long u, const double* g, const int64_t* off, int64_t K, long long* sm) {
     const double lam = bits_to_lam(u);
@@ -162,6 +213,31 @@ __device__ long long block_F(unsigned long long u, const double* g, const int64_
     for (int64_t k = threadIdx.x; k < K; k += 1024) acc += count_at(lam, g[k], off[k + 1] - off[k]);
     return block_sum_ll(acc, sm);
 }
+
+// candidate w of n = 32 or 1024 evenly spaced bit patterns in [lo, lo + d): lo + floor(w d / n)
+__device__ __forceinline__ unsigned long long cand_32(unsigned long long lo, unsigned long long d, unsigned long long w) {
+    return lo + (d >> 5) * w + (((d & 31ull) * w) >> 5);
+}
+__device__ __forceinline__ unsigned long long cand_1024(unsigned long long lo, unsigned long long d, unsigned long long w) {
+    return lo + (d >> 10) * w + (((d & 1023ull) * w) >> 10);
+}
+
+// appends k to an active list for the lanes with keep set: one shared atomic per warp
+__device__ __forceinline__ void push_active(bool keep, int k, int* list, int* count, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    int pos = 0;
+    if (lane == 0 && m != 0u) pos = atomicAdd(count, __popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (keep) list[pos + __popc(m & ((1u << lane) - 1u))] = k;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int kEndgameSteps = 256;  // steps of F left in (lo, hi] at or below which they are found directly
 
 __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double* __restrict__ a,
                                                           const double* __restrict__ f,
@@ -171,11 +247,15 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
     __shared__ long long sF[32];
     __shared__ unsigned long long sLoHi[2];
     __shared__ long long sScan[33];
+    __shared__ long long sSum2[64];
     __shared__ int sAct[2][kActiveCap];
     __shared__ float sGf[kActiveCap];  // RN32(g_k), for count_fast
     __shared__ int sNk[kActiveCap];
     __shared__ int sNact[2];
-    __shared__ double sRed[33];
+    __shared__ float sRedF[32];
+    __shared__ double sLam0;
+    __shared__ int sEgLo[kEndgameSteps], sEgN[kEndgameSteps], sEgPre[kEndgameSteps];
+    __shared__ unsigned long long sEgStep[kEndgameSteps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // 1. weights g_k
@@ -221,60 +301,155 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
     const bool inf_case = Finf <= c;
     unsigned long long lo = 0ull, hi = kInfBits;
     if (!inf_case) {
-        // a guess lam0 = c / sum g narrows the bracket when it verifies
-        double gs = 0.0;
-        for (int64_t k = tid; k < K; k += 1024) gs += g[k];
-        gs = warp_sum(gs);
-        if (lane == 0) sRed[warp] = gs;
-        __syncthreads();
-        if (warp == 0) {
-            double t = warp_sum(sRed[lane]);
-            if (lane == 0) sRed[32] = t;
-        }
-        __syncthreads();
-        const double lam0 = (double)c / sRed[32];
-        if (isfinite(lam0) && lam0 > 0.0) {
-            const unsigned long long ulo = (unsigned long long)__double_as_longlong(lam0 * 0.25);
-            const unsigned long long uhi = (unsigned long long)__double_as_longlong(lam0 * 4.0);
-            if (uhi < kInfBits && block_F(ulo, g, off, K, sScan) <= c) lo = ulo;
-            if (uhi < kInfBits && block_F(uhi, g, off, K, sScan) > c) hi = uhi;
-        }
-        // active list: blocks whose count may still change inside (lo, hi)
+        // a guess lam0 = c / sum g (an FP32 sum is enough: it only places the candidates below)
+        float gs = 0.f;
+        for (int64_t k = tid; k < K; k += 1024) gs += __double2float_rn(g[k]);
+        gs = warp_sum_f(gs);
+        if (lane == 0) sRedF[warp] = gs;
         const bool track = K <= kActiveCap;
-        if (tid == 0) { sNact[0] = 0; sLoHi[0] = lo; sLoHi[1] = hi; }
+        if (tid == 0) sNact[0] = 0;
         if (track)
             for (int64_t k = tid; k < K; k += 1024) {
                 sGf[k] = __double2float_rn(g[k]);
                 sNk[k] = (int)(off[k + 1] - off[k]);
             }
         __syncthreads();
+        if (warp == 0) {
+            const float t = warp_sum_f(sRedF[lane]);
+            if (lane == 0) sLam0 = (double)c / (double)t;
+        }
+        __syncthreads();
+        // 32 candidates lam0 2^(w - 8), w = 0..31, one per warp, its lanes splitting the blocks; F is
+        // monotone, so the candidates with F <= c form a prefix and the bracket becomes the pair
+        // around its end (an exponent step: exact).  Candidates past the largest double are +inf
+        // (F(inf) > c), those below the normal range 0 (F(0) = K <= c).  Without a usable lam0
+        // the bracket stays [0, inf).
+        const double lam0 = sLam0;
+        const unsigned long long b0 = (unsigned long long)__double_as_longlong(lam0);
+        const long long e0 = (long long)((b0 >> 52) & 0x7FFull);
+        const bool usable = isfinite(lam0) && lam0 > 0.0 && e0 >= 1;
+        auto geo = [&](int w) -> unsigned long long {
+            const long long e = e0 + (w - 8);
+            return e >= 2047 ? kInfBits : (e <= 0 ? 0ull : b0 + ((unsigned long long)(long long)(w - 8) << 52));
+        };
+        if (usable) {
+            const unsigned long long u = geo(warp);
+            const double lam = bits_to_lam(u);
+            const float lamf = __double2float_rn(lam);
+            long long acc = 0;
+            if (track) {
+                for (int k = lane; k < (int)K; k += 32) acc += count_fast(lam, lamf, sGf[k], sNk[k], g + k);
+            } else {
+                for (int64_t k = lane; k < K; k += 32) acc += count_at(lam, g[k], off[k + 1] - off[k]);
+            }
+            acc = warp_sum_ll(acc);
+            if (lane == 0) sF[warp] = acc;
+        }
+        __syncthreads();
+        if (usable) {
+            if (warp == 0) {
+                const int t = __popc(__ballot_sync(0xffffffffu, sF[lane] <= c)) - 1;
+                if (lane == 0) {
+                    sLoHi[0] = t >= 0 ? geo(t) : 0ull;
+                    sLoHi[1] = t < 31 ? geo(t + 1) : kInfBits;
+                }
+            }
+            __syncthreads();
+            lo = sLoHi[0];
+            hi = sLoHi[1];
+        }
+        // active list: blocks whose count may still change inside (lo, hi); counts of the others
+        // are summed into base, and nbrk = F(hi) - F(lo) counts the steps of F inside (lo, hi]
         int cur = 0;
-        long long base = 0;
+        long long base = 0, nbrk = 0;
         if (track) {
-            long long mine = 0;
+            long long mine = 0, steps = 0;
             const double llo = bits_to_lam(lo), lhi = bits_to_lam(hi);
             const float flo = __double2float_rn(llo), fhi = __double2float_rn(lhi);
-            for (int64_t k = tid; k < K; k += 1024) {
-                const int nk = sNk[k];
-                const long long clo = count_fast(llo, flo, sGf[k], nk, g[k]), chi = count_fast(lhi, fhi, sGf[k], nk, g[k]);
-                if (clo == chi) mine += clo;
-                else sAct[0][atomicAdd(&sNact[0], 1)] = (int)k;
+            for (int k0 = warp * 32; k0 < (int)K; k0 += 1024) {  // warp-uniform trips
+                const int k = k0 + lane;
+                bool keep = false;
+                if (k < (int)K) {
+                    const long long clo = count_fast(llo, flo, sGf[k], sNk[k], g + k);
+                    const long long chi = count_fast(lhi, fhi, sGf[k], sNk[k], g + k);
+                    if (clo == chi) mine += clo;
+                    else keep = true;
+                    steps += chi - clo;
+                }
+                push_active(keep, k, sAct[0], &sNact[0], lane);
             }
-            base = block_sum_ll(mine, sScan);
+            block_sum2_ll(&mine, &steps, sSum2);
+            base = mine;
+            nbrk = steps;
         }
+        bool endgame = true;
         while (hi - lo > 1ull) {
             const unsigned long long d = hi - lo;
             const int nact = track ? sNact[cur] : 0;
+            if (track && endgame && nbrk <= kEndgameSteps && nbrk > 0 && nact <= kEndgameSteps) {
+                // Few steps of F are left in (lo, hi]: find each one exactly (the bit pattern where an
+                // active block's count reaches j), then lam* sits just below the (c - F(lo) + 1)-th
+                // smallest of them.  F(lam) = F(lo) + #{steps <= lam} on [lo, hi].
+                long long clo = 0, dlt = 0;
+                if (tid < nact) {
+                    const int k = sAct[cur][tid];
+                    clo = count_at(bits_to_lam(lo), g[k], sNk[k]);
+                    dlt = count_at(bits_to_lam(hi), g[k], sNk[k]) - clo;
+                    sEgLo[tid] = (int)clo;
+                    sEgN[tid] = (int)dlt;
+                }
+                long long total_lo = clo, total_dlt = dlt;
+                block_sum2_ll(&total_lo, &total_dlt, sSum2);
+                long long nsteps;
+                const long long pre = block_exclusive_scan(tid < nact ? dlt : 0, sScan, &nsteps);
+                if (tid < nact) sEgPre[tid] = (int)pre;
+                __syncthreads();
+                bool fail = nsteps != nbrk || nsteps > kEndgameSteps;
+                if (!fail && tid < nsteps) {
+                    int a = 0, b = nact - 1;  // the active block whose steps hold step number tid
+                    while (a < b) {
+                        const int mid = (a + b + 1) >> 1;
+                        if (sEgPre[mid] <= tid) a = mid;
+                        else b = mid - 1;
+                    }
+                    const int k = sAct[cur][a];
+                    const long long jj = (long long)sEgLo[a] + 1 + (tid - sEgPre[a]);
+                    unsigned long long u = 0ull;
+                    fail = !breakpoint_of(g[k], jj, &u);
+                    sEgStep[tid] = u;
+                }
+                fail = __syncthreads_or(fail);
+                if (!fail) {
+                    const long long r = c - (base + total_lo);  // 0 <= r < nsteps
+                    if (tid < nsteps) {
+                        const unsigned long long v = sEgStep[tid];
+                        int less = 0, eq = 0;
+                        for (int q = 0; q < (int)nsteps; ++q) {
+                            const unsigned long long w = sEgStep[q];
+                            less += w < v;
+                            eq += w == v;
+                        }
+                        if (less <= r && r < less + eq) sLoHi[0] = v - 1ull;
+                    }
+                    __syncthreads();
+                    lo = sLoHi[0];
+                    hi = lo + 1ull;
+                    break;
+                }
+                endgame = false;  // not expected; bisection below stays exact
+            }
+            if (tid == 0) sNact[cur ^ 1] = 0;
+            // 32 candidates u_w = lo + floor(w d / 32), warp w >= 1 evaluating u_w with its lanes
+            // splitting the blocks; warp 0 picks the last candidate with F <= c by a ballot
             if (warp >= 1) {
-                const unsigned long long w = (unsigned long long)warp;
-                const unsigned long long u = lo + (d >> 5) * w + (((d & 31ull) * w) >> 5);
+                const unsigned long long u = cand_32(lo, d, (unsigned long long)warp);
                 const double lam = bits_to_lam(u);
                 const float lamf = __double2float_rn(lam);
                 long long acc = 0;
                 if (track) {
                     for (int i = lane; i < nact; i += 32) {
                         const int k = sAct[cur][i];
-                        acc += count_fast(lam, lamf, sGf[k], sNk[k], g[k]);
+                        acc += count_fast(lam, lamf, sGf[k], sNk[k], g + k);
                     }
                 } else {
                     for (int64_t k = lane; k < K; k += 32) acc += count_at(lam, g[k], off[k + 1] - off[k]);
@@ -283,37 +458,40 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
                 if (lane == 0) sF[warp] = base + acc;
             }
             __syncthreads();
-            if (tid == 0) {
-                unsigned long long nlo = lo, nhi = hi;
-                for (int w = 1; w < 32; ++w) {
-                    const unsigned long long u =
-                        lo + (d >> 5) * (unsigned long long)w + (((d & 31ull) * (unsigned long long)w) >> 5);
-                    if (sF[w] <= c) {
-                        if (u > nlo) nlo = u;
-                    } else if (u < nhi) {
-                        nhi = u;
-                    }
+            if (warp == 0) {
+                const bool ok = lane == 0 || sF[lane] <= c;
+                const int t = __popc(__ballot_sync(0xffffffffu, ok)) - 1;  // a prefix: F is monotone
+                if (lane == 0) {
+                    sLoHi[0] = cand_32(lo, d, (unsigned long long)t);
+                    sLoHi[1] = t < 31 ? cand_32(lo, d, (unsigned long long)(t + 1)) : hi;
                 }
-                sLoHi[0] = nlo;
-                sLoHi[1] = nhi;
-                sNact[cur ^ 1] = 0;
             }
             __syncthreads();
             lo = sLoHi[0];
             hi = sLoHi[1];
             if (track) {  // drop the blocks whose count is now constant on [lo, hi]
-                long long mine = 0;
-                const double llo = bits_to_lam(lo), lhi = bits_to_lam(hi);
-                const float flo = __double2float_rn(llo), fhi = __double2float_rn(lhi);
-                for (int i = tid; i < nact; i += 1024) {
-                    const int k = sAct[cur][i];
-                    const int nk = sNk[k];
-                    const long long clo = count_fast(llo, flo, sGf[k], nk, g[k]);
-                    const long long chi = count_fast(lhi, fhi, sGf[k], nk, g[k]);
-                    if (clo == chi) mine += clo;
-                    else sAct[cur ^ 1][atomicAdd(&sNact[cur ^ 1], 1)] = k;
+                long long mine = 0, steps = 0;
+                if (warp * 32 < nact) {
+                    const double llo = bits_to_lam(lo), lhi = bits_to_lam(hi);
+                    const float flo = __double2float_rn(llo), fhi = __double2float_rn(lhi);
+                    for (int i0 = warp * 32; i0 < nact; i0 += 1024) {  // warp-uniform trips
+                        const int i = i0 + lane;
+                        bool keep = false;
+                        int k = 0;
+                        if (i < nact) {
+                            k = sAct[cur][i];
+                            const long long clo = count_fast(llo, flo, sGf[k], sNk[k], g + k);
+                            const long long chi = count_fast(lhi, fhi, sGf[k], sNk[k], g + k);
+                            if (clo == chi) mine += clo;
+                            else keep = true;
+                            steps += chi - clo;
+                        }
+                        push_active(keep, k, sAct[cur ^ 1], &sNact[cur ^ 1], lane);
+                    }
                 }
-                base += block_sum_ll(mine, sScan);
+                block_sum2_ll(&mine, &steps, sSum2);
+                base += mine;
+                nbrk = steps;
                 cur ^= 1;
             }
             __syncthreads();
