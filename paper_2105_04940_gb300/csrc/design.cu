@@ -3,8 +3,10 @@
 //
 // The block-size search is exact and order-free: F(lam) = sum_k clamp(floor(lam g_k), 1, n_k)
 // is an integer sum of element-wise IEEE operations, so the largest FP64 lam with F(lam) <= c
-// is one number whatever the reduction order.  One CTA finds it by a 32-way search over
-// the IEEE bit patterns of the non-negative doubles (13 rounds instead of 63 bisections).
+// is one number whatever the reduction order.  One CTA finds it: 32 candidates lam0 2^j around
+// lam0 = c / sum g give a bracket one binade wide, 32-way rounds over the IEEE bit patterns in the
+// bracket narrow it (blocks whose count is constant on it leave an active list), and once at most
+// 256 steps of F are left each step is located exactly and lam* read off by rank.
 #include "internal.h"
 
 namespace bmm {
