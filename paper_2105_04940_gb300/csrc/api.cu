@@ -405,15 +405,18 @@ bmm_status probs_batched_norms(int64_t count, const bmm_mat* Ms, const bmm_mat* 
         const bool m_slices = vM.mode == VEC_STRIDED;
         norms.push_back(NormJobArgs{vM, st->x, m_slices ? plan.partial : nullptr, m_slices ? plan.partial_cap : 0});
         norms.push_back(NormJobArgs{vN, st->y, m_slices ? nullptr : plan.partial, m_slices ? 0 : plan.partial_cap});
+        // eq. 3.8 probabilities come out of the grouped block-statistics kernel; the block kind
+        // (eq. 1.4) needs all K block sums first and keeps its own launch below
+        double* p_col = (p_outs && pkind == BMM_P_COL_OPT) ? p_outs[i] : nullptr;
         blocks.push_back(BlockStatsArgs{st->x, st->y, B->offsets, B->K, B->n, st->a, st->s, st->mf, st->nf,
-                                        status_of(ws[i])});
+                                        status_of(ws[i]), p_col});
         which.push_back(i);
     }
     if (!norms.empty()) BMM_TRY(launch_vec_sqnorms_grouped(norms.data(), (int64_t)norms.size(), cs));
     if (!blocks.empty()) BMM_TRY(launch_block_stats_grouped(blocks.data(), (int64_t)blocks.size(), cs));
     for (const int64_t i : which) {
         double* p_out = p_outs ? p_outs[i] : nullptr;
-        if (p_out == nullptr) continue;
+        if (p_out == nullptr || pkind == BMM_P_COL_OPT) continue;
         const bmm_stats* st = &sts[i];
         BMM_TRY(launch_probs(pkind, st->x, st->y, st->a, st->mf, st->nf, st->f, Bs[i].offsets, Bs[i].K, Bs[i].n, p_out,
                              status_of(ws[i]), cs));

@@ -53,6 +53,7 @@ struct BlockStatsArgs {
     int64_t K, n;
     double *a, *s, *mf, *nf;
     DevStatus* st;
+    double* p;  // optional [n]: eq. 3.8 probabilities, written with a_k (nullptr: none)
 };
 cudaError_t launch_block_stats_grouped(const BlockStatsArgs* args, int64_t count, cudaStream_t s);
 

@@ -6,7 +6,9 @@
 // FP64-accurate sums built from FP32 float-float pairs (GB300's FP64 rate is too
 // low to square every element in FP64 at HBM speed), renormalised every 32 terms and folded
 // into FP64 every 128 (one warp-wide FP64 instruction costs about 64 FP32 ones on GB300).
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "internal.h"
 
@@ -244,6 +246,7 @@ struct NormJob {
     int slices;
 };
 constexpr int kMaxNormJobs = 384;  // 80-byte jobs: under the 32 KB kernel-parameter limit
+constexpr int64_t kGroupedSliceRows = 512;  // strided sets in grouped launches: rows per slice, at least
 struct NormTable {
     int count;
     int total;
@@ -506,18 +509,48 @@ static cudaError_t norm_grouped_t(const NormJobArgs* jobs, int64_t count, cudaSt
         sums.count = sums.total = 0;
         return cudaGetLastError();
     };
+    // the longest CTAs first (rows per CTA for strided sets, vector length for contiguous ones), so
+    // that short ones fill the tail of the launch
+    std::vector<int64_t> order;
+    std::vector<int64_t> work;
     for (int64_t i = 0; i < count; ++i) {
         const VecSet& v = jobs[i].v;
         if (v.dtype != dt || (v.mode == VEC_STRIDED) != STRIDED || v.count <= 0) continue;
-        int64_t gx = ceil_div(v.count, 256), S = 1, rps = imax(v.len, 1);  // contiguous: 256 vectors per CTA
+        order.push_back(i);
+    }
+    auto geometry = [&](int64_t i, int64_t* gx, int64_t* S, int64_t* rps) {
+        const VecSet& v = jobs[i].v;
+        *gx = ceil_div(v.count, 256);  // contiguous: 256 vectors per CTA
+        *S = 1;
+        *rps = imax(v.len, 1);
         if (STRIDED) {
-            // the single-product kernel's slices of rows, when the product's partial buffer holds them
-            col_geometry(v, &gx, &S, &rps);
-            if (S > 1 && (jobs[i].partial == nullptr || jobs[i].partial_cap < S * v.count)) {
-                S = 1;
-                rps = imax(v.len, 1);
+            // slices of rows where the product's partial buffer holds them; with many products in the
+            // launch there is no need for the single-product kernel's thin slices: at least
+            // kGroupedSliceRows rows each keeps the partial sums' traffic under 1% of the input
+            col_geometry(v, gx, S, rps);
+            if (*rps < kGroupedSliceRows) {
+                *rps = round_up(imin(imax(v.len, 1), kGroupedSliceRows), 32);
+                *S = ceil_div(v.len, *rps);
+            }
+            if (*S > 1 && (jobs[i].partial == nullptr || jobs[i].partial_cap < *S * v.count)) {
+                *S = 1;
+                *rps = imax(v.len, 1);
             }
         }
+    };
+    for (const int64_t i : order) {
+        int64_t gx, S, rps;
+        geometry(i, &gx, &S, &rps);
+        work.push_back(rps);
+    }
+    std::vector<int64_t> perm(order.size());
+    for (size_t q = 0; q < perm.size(); ++q) perm[q] = (int64_t)q;
+    std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return work[a] > work[b]; });
+    for (const int64_t pi : perm) {
+        const int64_t i = order[pi];
+        const VecSet& v = jobs[i].v;
+        int64_t gx, S, rps;
+        geometry(i, &gx, &S, &rps);
         const int64_t ctas = gx * S;
         if (tab.count == kMaxNormJobs || sums.count == kMaxNormJobs || (int64_t)tab.total + ctas > 0x7fffffffLL) {
             cudaError_t e = flush();
@@ -601,16 +634,20 @@ cudaError_t launch_block_stats(const double* x, const double* y, const int64_t* 
 }
 
 // block_stats_kernel for many products in one launch (one warp per block, the CTAs of product j after
-// those of product j - 1)
+// those of product j - 1), and, where p is given, the eq. 3.8 probabilities p_i = sqrt(x_i y_i) / a_k
+// of the block's columns with the same FP64 operations as probs_col_kernel (uniform 1/n_k when
+// a_k = 0), reusing the square roots of the block sum: one kernel over all products' blocks instead
+// of a probability launch per product.
 struct BlockStatsJob {
     const double *x, *y;
     const int64_t* off;
     int64_t K, n;
     double *a, *s, *mf, *nf;
     DevStatus* st;
+    double* p;
     int cta_begin;
 };
-constexpr int kMaxBlockStatsJobs = 360;
+constexpr int kMaxBlockStatsJobs = 336;
 struct BlockStatsTable {
     int count;
     int total;
@@ -638,13 +675,18 @@ __global__ void __launch_bounds__(256) block_stats_grouped_kernel(const __grid_c
         }
         return;
     }
+    constexpr int kKeep = 4;  // square roots kept in registers for the probabilities (blocks <= 128)
+    double root[kKeep];
     double sa = 0, ss = 0, sx = 0, sy = 0;
     bool bad = false;
-    for (int64_t i = a0 + lane; i < a1; i += 32) {
+    int q = 0;
+    for (int64_t i = a0 + lane; i < a1; i += 32, ++q) {
         const double xi = jb.x[i], yi = jb.y[i];
         const double xy = __dmul_rn(xi, yi);
         bad |= !isfinite(xi) || !isfinite(yi);
-        sa += sqrt(xy);
+        const double r = sqrt(xy);
+        if (q < kKeep) root[q] = r;
+        sa += r;
         ss += xy;
         sx += xi;
         sy += yi;
@@ -660,6 +702,15 @@ __global__ void __launch_bounds__(256) block_stats_grouped_kernel(const __grid_c
         jb.mf[k] = sx;
         jb.nf[k] = sy;
         if (bad) set_status(jb.st, BMM_ERR_NONFINITE, (int)k);
+    }
+    if (jb.p != nullptr) {
+        const double uni = __ddiv_rn(1.0, (double)(a1 - a0));
+        q = 0;
+        for (int64_t i = a0 + lane; i < a1; i += 32, ++q) {
+            double v = uni;
+            if (sa > 0.0) v = __ddiv_rn(q < kKeep ? root[q] : sqrt(__dmul_rn(jb.x[i], jb.y[i])), sa);
+            jb.p[i] = v;
+        }
     }
 }
 
@@ -684,7 +735,7 @@ cudaError_t launch_block_stats_grouped(const BlockStatsArgs* args, int64_t count
         }
         BlockStatsJob& j = tab.job[tab.count++];
         j.x = g.x; j.y = g.y; j.off = g.off; j.K = g.K; j.n = g.n;
-        j.a = g.a; j.s = g.s; j.mf = g.mf; j.nf = g.nf; j.st = g.st;
+        j.a = g.a; j.s = g.s; j.mf = g.mf; j.nf = g.nf; j.st = g.st; j.p = g.p;
         j.cta_begin = tab.total;
         tab.total += (int)ctas;
     }
