@@ -17,6 +17,9 @@ Modules
   estimator  -- Alg. 1/2/3 estimators, block sampling, closed-form expected
                 errors (Lemma 2.1, Remark 2.2, eq. 3.10), bounds (eq. 3.11,
                 4.3) and the adjoint of the sampled product
+  errors     -- error bars: per-entry variance (eq. 3.7, Thm 3.1), its
+                one-sample estimate from the draws, and the whole-matrix
+                report (Remark 2.2, eq. 3.10-3.12, 4.3-4.4, 4.8-4.9)
 
 Pins (see tests/test_oracle_*.py): library norms and products, brute-force
 enumeration of every sampling outcome on tiny inputs (exact expectation and
@@ -30,8 +33,9 @@ convention of the sampler are conventions of this implementation (the paper
 states neither); they are pinned only through invariants and equivalences,
 not against numbers printed in the paper (it prints none).
 """
-from . import stats, design, sampler, estimator  # noqa: F401
+from . import stats, design, sampler, estimator, errors  # noqa: F401
 from .stats import *  # noqa: F401,F403
 from .design import *  # noqa: F401,F403
 from .sampler import *  # noqa: F401,F403
 from .estimator import *  # noqa: F401,F403
+from .errors import *  # noqa: F401,F403
