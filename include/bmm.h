@@ -272,6 +272,81 @@ bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_mat* N, co
                         const bmm_mat* dM, const bmm_mat* dN, int32_t accumulate,
                         void* ws, size_t ws_bytes, bmm_stream_t stream);
 
+/* ---- Error bars of the sampled product (Lemma 3.1, Thm 3.1, Remark 2.2, Thm 3.3, Thm 4.2, Thm 4.4).
+ * Reports beside the product, not part of it; FP64 throughout; all arrays are device memory and
+ * every call only enqueues work on the stream. */
+
+/* Fields of the bmm_error_report output (FP64 [BMM_REPORT_LEN]); NaN where an input is missing. */
+enum {
+    BMM_REPORT_EXPECTED_SQ_ERROR = 0, /* E||MN - CD||_F^2 = sum_k (1/c_k)(sum_{i in k} x_i y_i / p_i - f_k)
+                                         (Remark 2.2: eq. 3.7 summed over all entries); needs f */
+    BMM_REPORT_EQ310 = 1,             /* (1/c) [sum_k (a_k^2 - f_k)^{1/2}]^2 (eq. 3.10); needs f */
+    BMM_REPORT_THETA1 = 2,            /* min_k 1 - v_k^2, v_k^2 = f_k / a_k^2 (Thm 3.3), a_k > 0; needs f */
+    BMM_REPORT_THETA2 = 3,            /* max_k 1 - v_k^2; needs f */
+    BMM_REPORT_BETA = 4,              /* min(1, min_i p_i / p*_i), p* the eq. 3.8 probabilities */
+    BMM_REPORT_M_FRO2 = 5,            /* ||M||_F^2 = sum_k mf_k */
+    BMM_REPORT_N_FRO2 = 6,            /* ||N||_F^2 = sum_k nf_k */
+    BMM_REPORT_PHI = 7,               /* phi of Thm 3.3 */
+    BMM_REPORT_EQ311 = 8,             /* phi^2 / (beta c) ||M||_F^2 ||N||_F^2 (eq. 3.11) */
+    BMM_REPORT_ETA312 = 9,            /* eta = phi + (theta2/theta1)^{1/2} (8/beta log(1/delta))^{1/2} */
+    BMM_REPORT_EQ312 = 10,            /* eta^2 / (beta c) ||M||_F^2 ||N||_F^2: eq. 3.12, probability >= 1 - delta */
+    BMM_REPORT_PHIHAT = 11,           /* (1 - beta (1 - theta2))^{1/2} (Thm 4.2) */
+    BMM_REPORT_EQ43 = 12,             /* eq. 4.3 */
+    BMM_REPORT_ETA44 = 13,            /* phihat + (8/beta log(1/delta))^{1/2} */
+    BMM_REPORT_EQ44 = 14,             /* eq. 4.4 */
+    BMM_REPORT_THETA1HAT = 15,        /* min_k |1 - fhat_k / a_k^2| (Thm 4.3); needs f and fhat */
+    BMM_REPORT_THETA2HAT = 16,        /* max_k |1 - fhat_k / a_k^2| */
+    BMM_REPORT_PHITILDE = 17,         /* phi-tilde of Thm 4.4 */
+    BMM_REPORT_EQ48 = 18,             /* eq. 4.8 */
+    BMM_REPORT_ETA49 = 19,
+    BMM_REPORT_EQ49 = 20,             /* eq. 4.9, probability >= 1 - delta */
+    BMM_REPORT_LEN = 21
+};
+
+/*
+ * bmm_error_report -- the whole-matrix error quantities of Alg. 2 (fields above) from the
+ * statistics (st->x, y, a, mf, nf required; st->f optional), the probabilities p [n], the block
+ * sizes ck [K] (device int64; the expected error is exact for these integers, while the bounds of
+ * Thm 3.3 / 4.2 are stated for the real-valued eq. 3.9 / 4.2 sizes) and their total c.  fhat
+ * (optional, device FP64 [K]): the Alg. 3 pilot estimates of ||M^k N_k||_F^2.  delta in (0, 1).
+ * report_out: device FP64 [BMM_REPORT_LEN].  One CTA; no workspace.
+ */
+bmm_status bmm_error_report(const bmm_blocks* B, const bmm_stats* st, const double* p, const int64_t* ck, int64_t c,
+                            const double* fhat, double delta, double* report_out, bmm_stream_t stream);
+
+/*
+ * bmm_entry_variance -- Var[(CD)_hf] for each listed entry (Lemma 3.1, eq. 3.7: the sigma^2 of
+ * Thm 3.1) for the design (p, ck) before any draw:
+ *   BMM_UNIT_COLUMN: sum_k (1/c_k) [sum_{i in k, p_i > 0} M_hi^2 N_if^2 / p_i - (sum_{i in k, p_i > 0} M_hi N_if)^2],
+ *                    p [n], ck [K];
+ *   BMM_UNIT_BLOCK:  (1/c) [sum_{k: p_k > 0} ((M^k N_k)_hf)^2 / p_k - (sum_{k: p_k > 0} (M^k N_k)_hf)^2],
+ *                    p [K], ck ignored, c draws.
+ * Terms with zero probability are never drawn and are left out (the variance of the estimator as
+ * run).  entries: device int64 [count][2] = (h, f); an entry outside the m x p product gets NaN.
+ * sigma2_out: device FP64 [count].  Reads O(n) elements of M and N per entry; no workspace.
+ */
+bmm_status bmm_entry_variance(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                              const double* p, const int64_t* ck, int64_t c, const int64_t* entries, int64_t count,
+                              double* sigma2_out, bmm_stream_t stream);
+
+/*
+ * bmm_entry_estimate -- from one sample (the idx, scale of bmm_sample, `draws` of them): each listed
+ * entry's value (CD)_hf = sum_t Z_t, Z_t = scale_t M_{h,i_t} N_{i_t,f} in FP64, and the one-sample
+ * estimate of its variance:
+ *   BMM_UNIT_COLUMN: sum over blocks with c_k >= 2 of c_k/(c_k - 1) sum_{t in k} (Z_t - Zbar_k)^2
+ *                    (the draws of block k are consecutive, c_k of them; blocks with c_k = 1 add their
+ *                    value but no variance -- one draw carries no spread);
+ *   BMM_UNIT_BLOCK:  c/(c - 1) sum_t (Z_t - Zbar)^2 with Z_t = scale_t (M^{k_t} N_{k_t})_hf.
+ * Unbiased for the variance of the blocks it covers, so (CD)_hf +- z sqrt(s2) is the normal interval
+ * of Thm 3.1.  ck: device int64 [K] (column unit; sum must equal draws, else BMM_ERR_SHAPE in the
+ * workspace status).  cd_out, s2_out: device FP64 [count]; NaN for an entry outside the product.
+ * ws: at least 256 + 8 (K + 1) bytes (any bmm_workspace_size of the problem holds them).
+ */
+bmm_status bmm_entry_estimate(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                              const int64_t* ck, const int32_t* idx, const double* scale, int64_t draws,
+                              const int64_t* entries, int64_t count, double* cd_out, double* s2_out, void* ws,
+                              size_t ws_bytes, bmm_stream_t stream);
+
 /* Synchronises the stream, then returns the first device-recorded error (BMM_OK if none). */
 bmm_status bmm_read_device_status(const void* ws, bmm_stream_t stream);
 /* Enqueues a reset of the device status word. */

@@ -29,7 +29,15 @@ EXPORTED = (
     "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
     "bmm_probs_static", "bmm_apply_batched", "bmm_probs_batched",
     "bmm_autotune_workspace_size", "bmm_autotune_gemm", "bmm_autotune_get", "bmm_autotune_set", "bmm_autotune_clear",
+    "bmm_error_report", "bmm_entry_variance", "bmm_entry_estimate",
 )
+
+# fields of the bmm_error_report output, in order (BMM_REPORT_* of include/bmm.h)
+REPORT_FIELDS = (
+    "expected_sq_error", "eq310", "theta1", "theta2", "beta", "m_fro2", "n_fro2", "phi", "eq311", "eta312", "eq312",
+    "phihat", "eq43", "eta44", "eq44", "theta1hat", "theta2hat", "phitilde", "eq48", "eta49", "eq49",
+)
+REPORT_LEN = len(REPORT_FIELDS)
 
 
 class BmmError(RuntimeError):
@@ -96,6 +104,12 @@ def load(path: str = LIB_PATH):
     lib.bmm_autotune_set.restype = i32
     lib.bmm_autotune_clear.argtypes = []
     lib.bmm_autotune_clear.restype = None
+    lib.bmm_error_report.argtypes = [P(Blocks), P(Stats), vp, vp, i64, vp, ctypes.c_double, vp, vp]
+    lib.bmm_error_report.restype = i32
+    lib.bmm_entry_variance.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, vp, i64, vp, vp]
+    lib.bmm_entry_variance.restype = i32
+    lib.bmm_entry_estimate.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, vp, vp, i64, vp, i64, vp, vp, vp, sz, vp]
+    lib.bmm_entry_estimate.restype = i32
     for name in ("bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
                  "bmm_read_device_status", "bmm_clear_device_status"):
         getattr(lib, name).restype = i32
@@ -220,6 +234,29 @@ def bmm_backward(G, M, N, B: Blocks, unit: int, p, ck, c: int, seed: int, stream
                                unit, _ptr(p), _ptr(ck), c, seed & 0xFFFFFFFFFFFFFFFF, stream_id & 0xFFFFFFFFFFFFFFFF,
                                gemm_mode, dMm, dNm, int(bool(accumulate)), ws.data_ptr(), ws.numel(),
                                _stream(stream)), "bmm_backward")
+
+
+def bmm_error_report(B: Blocks, st: dict, p, ck, c: int, fhat, delta: float, report_out, stream=None):
+    """report_out: device FP64 [REPORT_LEN] (fields REPORT_FIELDS)."""
+    _check(load().bmm_error_report(ctypes.byref(B), ctypes.byref(stats(st)), _ptr(p), _ptr(ck), c, _ptr(fhat),
+                                   float(delta), _ptr(report_out), _stream(stream)), "bmm_error_report")
+
+
+def bmm_entry_variance(M, N, B: Blocks, unit: int, p, ck, c: int, entries, sigma2_out, stream=None):
+    """entries: device int64 [count, 2] of (h, f); sigma2_out: device FP64 [count]."""
+    count = 0 if entries is None else int(entries.shape[0])
+    _check(load().bmm_entry_variance(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), unit, _ptr(p),
+                                     _ptr(ck), c, _ptr(entries), count, _ptr(sigma2_out), _stream(stream)),
+           "bmm_entry_variance")
+
+
+def bmm_entry_estimate(M, N, B: Blocks, unit: int, ck, idx, scale, draws: int, entries, cd_out, s2_out, ws,
+                       stream=None):
+    """entries: device int64 [count, 2]; cd_out, s2_out: device FP64 [count]."""
+    count = 0 if entries is None else int(entries.shape[0])
+    _check(load().bmm_entry_estimate(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), unit, _ptr(ck),
+                                     _ptr(idx), _ptr(scale), draws, _ptr(entries), count, _ptr(cd_out), _ptr(s2_out),
+                                     ws.data_ptr(), ws.numel(), _stream(stream)), "bmm_entry_estimate")
 
 
 def bmm_read_device_status(ws, stream=None) -> int:

@@ -938,3 +938,61 @@ BMM_API bmm_status bmm_autotune_set(int64_t m, int64_t p, int64_t L, int32_t gem
 }
 
 BMM_API void bmm_autotune_clear(void) { gemm_tile_clear(); }
+
+// ------------------------------------------------------------------ error bars
+namespace bmm {
+namespace {
+MatView view_of(const bmm_mat* A) {
+    return MatView{A->data, A->rows, A->cols, A->ld, A->dtype, A->layout == BMM_ROW_MAJOR ? 1 : 0};
+}
+}  // namespace
+}  // namespace bmm
+
+BMM_API bmm_status bmm_error_report(const bmm_blocks* B, const bmm_stats* st, const double* p, const int64_t* ck,
+                                    int64_t c, const double* fhat, double delta, double* report_out,
+                                    bmm_stream_t stream) {
+    bmm_status s = check_blocks(B);
+    if (s != BMM_OK) return s;
+    if (st == nullptr || st->x == nullptr || st->y == nullptr || st->a == nullptr || st->mf == nullptr ||
+        st->nf == nullptr || p == nullptr || ck == nullptr || report_out == nullptr)
+        return BMM_ERR_ARG;
+    if (!(delta > 0.0 && delta < 1.0) || c < 1) return BMM_ERR_ARG;
+    BMM_TRY(launch_error_report(st->x, st->y, p, B->offsets, B->K, ck, st->a, st->f, st->mf, st->nf,
+                                st->f != nullptr ? fhat : nullptr, c, delta, report_out,
+                                reinterpret_cast<cudaStream_t>(stream)));
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_entry_variance(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                                      const double* p, const int64_t* ck, int64_t c, const int64_t* entries,
+                                      int64_t count, double* sigma2_out, bmm_stream_t stream) {
+    bmm_status s = check_problem(M, N, B);
+    if (s != BMM_OK) return s;
+    if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
+    if (count < 0 || p == nullptr || (count > 0 && (entries == nullptr || sigma2_out == nullptr))) return BMM_ERR_ARG;
+    if (unit == BMM_UNIT_COLUMN && ck == nullptr) return BMM_ERR_ARG;
+    if (unit == BMM_UNIT_BLOCK && c < 1) return BMM_ERR_ARG;
+    BMM_TRY(launch_entry_variance(view_of(M), view_of(N), B->offsets, B->K, unit, p, ck, c, entries, count, sigma2_out,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+    return BMM_OK;
+}
+
+BMM_API bmm_status bmm_entry_estimate(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
+                                      const int64_t* ck, const int32_t* idx, const double* scale, int64_t draws,
+                                      const int64_t* entries, int64_t count, double* cd_out, double* s2_out, void* ws,
+                                      size_t ws_bytes, bmm_stream_t stream) {
+    bmm_status s = check_problem(M, N, B);
+    if (s != BMM_OK) return s;
+    if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
+    if (count < 0 || draws < 0 || (draws > 0 && (idx == nullptr || scale == nullptr))) return BMM_ERR_ARG;
+    if (count > 0 && (entries == nullptr || cd_out == nullptr || s2_out == nullptr)) return BMM_ERR_ARG;
+    if (unit == BMM_UNIT_COLUMN && ck == nullptr) return BMM_ERR_ARG;
+    Carver cnt{nullptr};
+    cnt.take<int64_t>(B->K + 1);
+    if ((s = check_ws(ws, ws_bytes, cnt.off)) != BMM_OK) return s;
+    Carver cv{static_cast<char*>(ws) + kStatusBytes};
+    int64_t* start = cv.take<int64_t>(B->K + 1);
+    BMM_TRY(launch_entry_estimate(view_of(M), view_of(N), B->offsets, B->K, unit, ck, idx, scale, draws, entries, count,
+                                  cd_out, s2_out, start, status_of(ws), reinterpret_cast<cudaStream_t>(stream)));
+    return BMM_OK;
+}

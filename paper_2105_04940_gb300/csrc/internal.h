@@ -57,6 +57,26 @@ struct BlockStatsArgs {
 };
 cudaError_t launch_block_stats_grouped(const BlockStatsArgs* args, int64_t count, cudaStream_t s);
 
+// ---- errors.cu
+// A matrix for element access by (row, column): either storage order, F64 / F32 / BF16.
+struct MatView {
+    const void* data;
+    int64_t rows, cols, ld;
+    int dtype;
+    int row_major;
+};
+cudaError_t launch_entry_variance(const MatView& M, const MatView& N, const int64_t* off, int64_t K, int unit,
+                                  const double* p, const int64_t* ck, int64_t c, const int64_t* entries, int64_t count,
+                                  double* out, cudaStream_t s);
+cudaError_t launch_entry_estimate(const MatView& M, const MatView& N, const int64_t* off, int64_t K, int unit,
+                                  const int64_t* ck, const int32_t* idx, const double* scale, int64_t draws,
+                                  const int64_t* entries, int64_t count, double* cd, double* s2, int64_t* start,
+                                  DevStatus* st, cudaStream_t s);
+cudaError_t launch_error_report(const double* x, const double* y, const double* p, const int64_t* off, int64_t K,
+                                const int64_t* ck, const double* a, const double* f, const double* mf,
+                                const double* nf, const double* fhat, int64_t c, double delta, double* out,
+                                cudaStream_t s);
+
 // ---- frob.cu
 // Per segment k: f[k] = || sum_t w_t u_t v_t^T ||_F^2 over the listed vectors of the segment,
 // computed as sum_{t,t'} w_t w_t' <u_t,u_t'> <v_t,v_t'> with FP64-accurate dot products.

@@ -236,6 +236,48 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
     return res
 
 
+def error_report(prob: Problem, res: dict, delta: float = 0.05, stream=None) -> dict:
+    """Whole-matrix error quantities of one Alg. 2 run (a run() result with res["unit"] column):
+    E||MN - CD||_F^2 (Remark 2.2), eq. 3.10, theta_1, theta_2, beta and the bounds of eq. 3.11 / 3.12,
+    eq. 4.3 / 4.4 and, for the two-step methods, eq. 4.8 / 4.9, as a dict keyed by _abi.REPORT_FIELDS
+    (NaN where ||M^k N_k||_F^2 was not computed by the method).  Synchronises to read the values."""
+    torch = _torch()
+    if res["unit"] != A.UNIT_COLUMN:
+        raise ValueError("the error report covers Alg. 2 (column sampling)")
+    out = torch.empty(A.REPORT_LEN, dtype=torch.float64, device=prob.M.device)
+    st = dict(prob.st)
+    if res["method"] != "OPL":  # f_k of this run exists only where the method computed it
+        st["f"] = None
+    A.bmm_error_report(prob.B, st, res["p"], res["ck"], int(res["c"]), res.get("fhat") if st["f"] is not None else None,
+                       delta, out, stream)
+    return dict(zip(A.REPORT_FIELDS, out.cpu().tolist()))
+
+
+def error_bars(prob: Problem, res: dict, entries, z: float = 1.96, exact: bool = False, stream=None) -> dict:
+    """Normal intervals (Thm 3.1) for chosen entries of one sampled product: for entries (int64
+    [count, 2] of (h, f), any device) the value (CD)_hf and the one-sample variance estimate from
+    the run's own draws (bmm_entry_estimate), the interval value +- z sqrt(estimate), and with
+    exact=True also the variance of eq. 3.7 (bmm_entry_variance; reads O(n) elements per entry).
+    Tensors stay on the device."""
+    torch = _torch()
+    dev = prob.M.device
+    ent = torch.as_tensor(entries, dtype=torch.int64).to(dev).reshape(-1, 2).contiguous()
+    cnt = ent.shape[0]
+    cd = torch.empty(cnt, dtype=torch.float64, device=dev)
+    s2 = torch.empty(cnt, dtype=torch.float64, device=dev)
+    unit = res["unit"]
+    A.bmm_entry_estimate(prob.M, prob.N, prob.B, unit, res.get("ck"), res["idx"], res["scale"], int(res["idx"].numel()),
+                         ent, cd, s2, prob.ws, stream)
+    half = z * torch.sqrt(torch.clamp(s2, min=0.0))
+    out = {"entries": ent, "value": cd, "var_est": s2, "lo": cd - half, "hi": cd + half}
+    if exact:
+        var = torch.empty(cnt, dtype=torch.float64, device=dev)
+        A.bmm_entry_variance(prob.M, prob.N, prob.B, unit, res["p"], res.get("ck"), int(res["idx"].numel()), ent, var,
+                             stream)
+        out["var"] = var
+    return out
+
+
 def check_status(prob: Problem):
     code = A.bmm_read_device_status(prob.ws)
     if code != A.OK:

@@ -88,3 +88,31 @@ def test_autotune_table_host_side():
     assert A.bmm_autotune_workspace_size(300, 520, 517, A.GEMM_BF16) > 256 + 2 * (300 + 520) * 576
     A.bmm_autotune_clear()
     assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": 256, "raster": 8}
+
+
+def test_error_bar_calls_validate_arguments_on_host(lib):
+    """The error-bar entry points reject bad arguments before any device work (no GPU needed), and
+    the report's field names match the BMM_REPORT_* indices of include/bmm.h."""
+    from paper_2105_04940_gb300 import _abi
+    fake = 1 << 20  # never dereferenced
+    M = _abi.Mat(fake, 8, 64, 64, _abi.F64, _abi.ROW_MAJOR)
+    N = _abi.Mat(fake, 64, 8, 8, _abi.F64, _abi.ROW_MAJOR)
+    B = _abi.Blocks(4, 64, 16, fake)
+    st = _abi.Stats(fake, fake, fake, fake, fake, fake, None)
+    ok = dict(p=fake, ck=fake, out=fake)
+    assert lib.bmm_error_report(ctypes.byref(B), ctypes.byref(st), fake, fake, 16, None, 1.5, fake, None) == _abi.ERR_ARG
+    assert lib.bmm_error_report(ctypes.byref(B), ctypes.byref(st), fake, fake, 0, None, 0.1, fake, None) == _abi.ERR_ARG
+    assert lib.bmm_error_report(ctypes.byref(B), None, fake, fake, 16, None, 0.1, fake, None) == _abi.ERR_ARG
+    assert lib.bmm_entry_variance(ctypes.byref(M), ctypes.byref(N), ctypes.byref(B), 7, ok["p"], ok["ck"], 16, fake,
+                                  3, fake, None) == _abi.ERR_ARG
+    assert lib.bmm_entry_variance(ctypes.byref(M), ctypes.byref(N), ctypes.byref(B), _abi.UNIT_COLUMN, ok["p"], None,
+                                  16, fake, 3, fake, None) == _abi.ERR_ARG
+    badN = _abi.Mat(fake, 63, 8, 8, _abi.F64, _abi.ROW_MAJOR)
+    assert lib.bmm_entry_variance(ctypes.byref(M), ctypes.byref(badN), ctypes.byref(B), _abi.UNIT_COLUMN, ok["p"],
+                                  ok["ck"], 16, fake, 3, fake, None) == _abi.ERR_SHAPE
+    assert lib.bmm_entry_estimate(ctypes.byref(M), ctypes.byref(N), ctypes.byref(B), _abi.UNIT_COLUMN, fake, fake,
+                                  fake, 16, fake, 3, fake, fake, None, 0, None) == _abi.ERR_WORKSPACE
+    text = open(os.path.join(ROOT, "include", "bmm.h")).read()
+    idx = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"BMM_REPORT_([A-Z0-9_]+) = (\d+)", text)}
+    assert idx.pop("len") == _abi.REPORT_LEN
+    assert [k for k, _ in sorted(idx.items(), key=lambda kv: kv[1])] == list(_abi.REPORT_FIELDS)
