@@ -721,10 +721,45 @@ def error_and_baselines(P, prob, args, w, c, gm, out, dev):
     rms = float(np.sqrt(np.mean(np.square(errs))))
     res = {"exact_fp32_gemm_ms": t_fp32, "exact_tf32_gemm_ms": t_tf32, "exact_bf16_gemm_ms": t_bf16,
            "rel_err_rms": rms, "rel_err_seeds": len(errs)}
+    if args.method == "OPL":
+        res["error_bars"] = error_bars_check(P, prob, c, w, gm, out, ex, timeit)
     if exps:
         res["rel_err_expected"] = float(np.mean(exps))
         res["rel_err_ratio"] = rms / float(np.mean(exps))
     return res
+
+
+def error_bars_check(P, prob, c, w, gm, out, ex, timeit, count=4096, exact_count=256):
+    """The error-bar calls on one OPL product of the workload (outside the timed region): their
+    times, and how often the one-sample 95% interval of Thm 3.1 holds the exact FP32 product's
+    entry over `count` seeded random entries."""
+    import torch
+    A = P._abi
+    dev = prob.M.device
+    r = P.run(prob, "OPL", c, seed=60_000, gemm_mode=gm, out=out)
+    rng = np.random.default_rng(7)
+    ent = torch.as_tensor(np.stack([rng.integers(0, w["m"], count), rng.integers(0, w["p"], count)], 1),
+                          dtype=torch.int64, device=dev)
+    cd = torch.empty(count, dtype=torch.float64, device=dev)
+    s2 = torch.empty_like(cd)
+    var = torch.empty(exact_count, dtype=torch.float64, device=dev)
+    rep = torch.empty(A.REPORT_LEN, dtype=torch.float64, device=dev)
+    draws = int(r["idx"].numel())
+    t_est = timeit(lambda: A.bmm_entry_estimate(prob.M, prob.N, prob.B, A.UNIT_COLUMN, r["ck"], r["idx"], r["scale"],
+                                                draws, ent, cd, s2, prob.ws), reps=3)
+    t_var = timeit(lambda: A.bmm_entry_variance(prob.M, prob.N, prob.B, A.UNIT_COLUMN, r["p"], r["ck"], draws,
+                                                ent[:exact_count], var), reps=3)
+    t_rep = timeit(lambda: A.bmm_error_report(prob.B, prob.st, r["p"], r["ck"], draws, None, 0.05, rep), reps=3)
+    P.check_status(prob)
+    exact = ex[ent[:, 0], ent[:, 1]].double()
+    half = 1.96 * torch.sqrt(torch.clamp(s2, min=0.0))
+    cover = ((exact - cd).abs() <= half).double().mean().item()
+    ratio = (s2[:exact_count] / var).median().item()
+    fields = dict(zip(A.REPORT_FIELDS, rep.cpu().tolist()))
+    return {"entries": count, "coverage_95": cover, "estimate_ms": t_est, "exact_entries": exact_count,
+            "exact_variance_ms": t_var, "report_ms": t_rep, "median_estimate_over_exact": ratio,
+            "expected_sq_error": fields["expected_sq_error"], "eq311": fields["eq311"], "eq312_delta_0.05": fields["eq312"],
+            "beta": fields["beta"]}
 
 
 def time_methods(P, prob, args, w, L, gm, out, c0, rank):
