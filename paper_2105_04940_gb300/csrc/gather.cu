@@ -303,37 +303,51 @@ __device__ __forceinline__ void gather_contig_bf16_body(const T* __restrict__ X,
         csw[t] = sw;
     }
     __syncthreads();
-    for (int64_t r0 = by * 64; r0 < len; r0 += gy * 64) {
+    // 64 vectors x 64 coordinates per step; the next step's loads are issued before this step's
+    // transposed stores, so each CTA keeps a tile of loads in flight while it writes
+    float e[4][4];
+    auto load_tile = [&](int64_t r0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int idx = t + 256 * u;
             const int jj = idx >> 4, q = idx & 15;
             const int64_t c = cidx[jj];
             const int64_t r = r0 + 4 * q;
-            float e[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[u][k] = 0.f;
             if (c >= 0) {
                 const T* src = X + c * ld + r;
                 if (vec4 && r + 4 <= len) {
                     // four consecutive elements in one aligned load (16 bytes FP32, 8 bytes BF16)
                     if constexpr (std::is_same<T, float>::value) {
                         const float4 f4 = __ldg(reinterpret_cast<const float4*>(src));
-                        e[0] = f4.x; e[1] = f4.y; e[2] = f4.z; e[3] = f4.w;
+                        e[u][0] = f4.x; e[u][1] = f4.y; e[u][2] = f4.z; e[u][3] = f4.w;
                     } else {
                         const uint2 u2 = __ldg(reinterpret_cast<const uint2*>(src));
-                        e[0] = __uint_as_float(u2.x << 16); e[1] = __uint_as_float(u2.x & 0xffff0000u);
-                        e[2] = __uint_as_float(u2.y << 16); e[3] = __uint_as_float(u2.y & 0xffff0000u);
+                        e[u][0] = __uint_as_float(u2.x << 16); e[u][1] = __uint_as_float(u2.x & 0xffff0000u);
+                        e[u][2] = __uint_as_float(u2.y << 16); e[u][3] = __uint_as_float(u2.y & 0xffff0000u);
                     }
                 } else {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (r + k < len) e[k] = ldv<T, float>(src + k);
+                        if (r + k < len) e[u][k] = ldv<T, float>(src + k);
                 }
             }
+        }
+    };
+    int64_t r0 = by * 64;
+    if (r0 < len) load_tile(r0);
+    for (; r0 < len; r0 += gy * 64) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = t + 256 * u;
+            const int jj = idx >> 4, q = idx & 15;
             const float sw = csw[jj];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) tile[jj][4 * q + k] = e[k] * sw;
+            for (int k = 0; k < 4; ++k) tile[jj][4 * q + k] = e[u][k] * sw;
         }
         __syncthreads();
+        if (r0 + gy * 64 < len) load_tile(r0 + gy * 64);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int rr = (t >> 3) + 32 * u, jj8 = (t & 7) * 8;
@@ -360,6 +374,10 @@ __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
     gather_contig_bf16_body<T>(X, len, ld, nvec, col, w, *ext_dev, apply_weight, vec4, wr, st, blockIdx.x, blockIdx.y,
                                gridDim.y);
 }
+
+// CTAs along the coordinates of a contiguous BF16 / e4m3 gather: each takes up to four 64-coordinate
+// steps, so that its loads for one step overlap its stores of the previous one
+static int64_t contig_gy(int64_t len) { return imin(imax(ceil_div(ceil_div(len, 64), 4), 1), 2048); }
 
 template <typename T> constexpr int dtype_of();
 template <> constexpr int dtype_of<float>() { return BMM_F32; }
@@ -392,7 +410,7 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
                                                                               apply_weight, wr, st));
         } else {
             const bool vec4 = contig_vec4<T>(v);
-            dim3 grid((unsigned)ceil_div(kmax, 64), (unsigned)imin(imax(ceil_div(v.len, 64), 1), 2048));
+            dim3 grid((unsigned)ceil_div(kmax, 64), (unsigned)contig_gy(v.len));
             (count_launch(), gather_contig_bf16_kernel<T><<<grid, 256, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev,
                                                                                apply_weight, vec4, wr, st));
         }
@@ -500,7 +518,7 @@ static cudaError_t gather_grouped_t(const GatherJob* jobs, int64_t count, cudaSt
         const int kunit = g.mode == BMM_GEMM_E4M3 ? 128 : 64;
         const int64_t kmax = round_up(imax(g.ext, 1), kunit);
         const int64_t gx = ceil_div(kmax, STRIDED ? 128 : 64);
-        const int64_t gy = imin(imax(ceil_div(g.v.len, STRIDED ? kGatherRows : 64), 1), STRIDED ? 4096 : 2048);
+        const int64_t gy = STRIDED ? imin(imax(ceil_div(g.v.len, kGatherRows), 1), 4096) : contig_gy(g.v.len);
         if ((int64_t)tab.total + gx * gy > 0x7fffffffLL) {  // keep every launch's grid within 2^31 CTAs
             cudaError_t e = launch_gather_table<T, STRIDED>(tab, s);
             if (e != cudaSuccess) return e;
