@@ -210,6 +210,19 @@ bmm_status bmm_blocksizes(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* 
                           void* ws, size_t ws_bytes, bmm_stream_t stream);
 
 /*
+ * bmm_blocksizes_batched -- bmm_blocksizes for `count` independent products in one launch (one CTA
+ * per product, up to 400 per launch), for ckind BMM_CK_OPT, BMM_CK_HAT or BMM_CK_EQUAL (the Alg. 3
+ * pilot form takes bmm_blocksizes).  For each i the results are those of
+ * bmm_blocksizes(NULL, NULL, &Bs[i], &sts[i], ckind, cs[i], NULL, NULL, 0, ck_outs[i],
+ * g_outs ? g_outs[i] : NULL, NULL, ws[i], ws_bytes[i], stream), bit for bit.  sts may be NULL for
+ * BMM_CK_EQUAL.  Host-side checks of every product come before any launch; nothing is synchronised
+ * or allocated (graph-capturable).
+ */
+bmm_status bmm_blocksizes_batched(int64_t count, const bmm_blocks* Bs, const bmm_stats* sts, int32_t ckind,
+                                  const int64_t* cs, int64_t* const* ck_outs, double* const* g_outs,
+                                  void* const* ws, const size_t* ws_bytes, bmm_stream_t stream);
+
+/*
  * bmm_sample -- i.i.d. draws with replacement (Alg. 1 step 1(a), Alg. 2 step 1).
  * Philox4x32-10 with key (seed_lo, seed_hi) and counter (t_lo, t_hi, sid_lo, sid_hi) for
  * global draw number t gives r = (x1 << 32) | x0; W_j = floor(p_j 2^62); the draw is the

@@ -29,7 +29,7 @@ EXPORTED = (
     "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
     "bmm_probs_static", "bmm_apply_batched", "bmm_probs_batched",
     "bmm_autotune_workspace_size", "bmm_autotune_gemm", "bmm_autotune_get", "bmm_autotune_set", "bmm_autotune_clear",
-    "bmm_error_report", "bmm_entry_variance", "bmm_entry_estimate",
+    "bmm_error_report", "bmm_entry_variance", "bmm_entry_estimate", "bmm_blocksizes_batched",
 )
 
 # fields of the bmm_error_report output, in order (BMM_REPORT_* of include/bmm.h)
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
     lib.bmm_autotune_set.restype = i32
     lib.bmm_autotune_clear.argtypes = []
     lib.bmm_autotune_clear.restype = None
+    lib.bmm_blocksizes_batched.argtypes = [i64, P(Blocks), P(Stats), i32, P(i64), P(vp), P(vp), P(vp), P(sz), vp]
+    lib.bmm_blocksizes_batched.restype = i32
     lib.bmm_error_report.argtypes = [P(Blocks), P(Stats), vp, vp, i64, vp, ctypes.c_double, vp, vp]
     lib.bmm_error_report.restype = i32
     lib.bmm_entry_variance.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, vp, i64, vp, vp]
@@ -234,6 +236,19 @@ def bmm_backward(G, M, N, B: Blocks, unit: int, p, ck, c: int, seed: int, stream
                                unit, _ptr(p), _ptr(ck), c, seed & 0xFFFFFFFFFFFFFFFF, stream_id & 0xFFFFFFFFFFFFFFFF,
                                gemm_mode, dMm, dNm, int(bool(accumulate)), ws.data_ptr(), ws.numel(),
                                _stream(stream)), "bmm_backward")
+
+
+def bmm_blocksizes_batched(Bs, sts, ckind: int, cs, ck_outs, g_outs, wss, stream=None):
+    """bmm_blocksizes for many products in one launch (lists of equal length; sts may be None for
+    CK_EQUAL, g_outs None or a list with None entries)."""
+    n = len(Bs)
+    BlkA, VpA = Blocks * n, ctypes.c_void_p * n
+    st = (Stats * n)(*[stats(d) for d in sts]) if sts is not None else None
+    gp = VpA(*[_ptr(g) for g in g_outs]) if g_outs is not None else None
+    _check(load().bmm_blocksizes_batched(n, BlkA(*Bs), st, ckind, (ctypes.c_int64 * n)(*[int(c) for c in cs]),
+                                         VpA(*[_ptr(c) for c in ck_outs]), gp, VpA(*[w.data_ptr() for w in wss]),
+                                         (ctypes.c_size_t * n)(*[w.numel() for w in wss]), _stream(stream)),
+           "bmm_blocksizes_batched")
 
 
 def bmm_error_report(B: Blocks, st: dict, p, ck, c: int, fhat, delta: float, report_out, stream=None):

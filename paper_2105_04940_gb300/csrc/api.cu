@@ -517,6 +517,39 @@ BMM_API bmm_status bmm_blocksizes(const bmm_mat* M, const bmm_mat* N, const bmm_
     return BMM_OK;
 }
 
+BMM_API bmm_status bmm_blocksizes_batched(int64_t count, const bmm_blocks* Bs, const bmm_stats* sts, int32_t ckind,
+                                          const int64_t* cs, int64_t* const* ck_outs, double* const* g_outs,
+                                          void* const* ws, const size_t* ws_bytes, bmm_stream_t stream) {
+    if (count < 0 || (count > 0 && (Bs == nullptr || cs == nullptr || ck_outs == nullptr || ws == nullptr ||
+                                    ws_bytes == nullptr)))
+        return BMM_ERR_ARG;
+    if (ckind != BMM_CK_OPT && ckind != BMM_CK_HAT && ckind != BMM_CK_EQUAL) return BMM_ERR_ARG;
+    if (ckind != BMM_CK_EQUAL && sts == nullptr) return BMM_ERR_ARG;
+    std::vector<SizesJob> jobs;
+    jobs.reserve((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        const bmm_blocks* B = &Bs[i];
+        bmm_status s = check_blocks(B);
+        if (s != BMM_OK) return s;
+        if (ck_outs[i] == nullptr) return BMM_ERR_ARG;
+        const bmm_stats* st = ckind == BMM_CK_EQUAL ? nullptr : &sts[i];
+        if (st != nullptr && (st->a == nullptr || (ckind == BMM_CK_OPT && st->f == nullptr))) return BMM_ERR_ARG;
+        if (cs[i] < B->K || cs[i] > B->n) return BMM_ERR_INFEASIBLE;
+        double* g_out = g_outs ? g_outs[i] : nullptr;
+        Carver cnt{nullptr};
+        SizesPlan plan;
+        plan_sizes(cnt, B, ckind, 0, g_out, nullptr, &plan);
+        if ((s = check_ws(ws[i], ws_bytes[i], cnt.off)) != BMM_OK) return s;
+        Carver cv{static_cast<char*>(ws[i]) + kStatusBytes};
+        plan_sizes(cv, B, ckind, 0, g_out, nullptr, &plan);
+        jobs.push_back(SizesJob{ckind, st ? st->a : nullptr, ckind == BMM_CK_OPT ? st->f : nullptr, B->offsets, B->K,
+                                B->n, cs[i], ck_outs[i], plan.g, status_of(ws[i])});
+    }
+    if (!jobs.empty())
+        BMM_TRY(launch_blocksizes_grouped(jobs.data(), (int64_t)jobs.size(), reinterpret_cast<cudaStream_t>(stream)));
+    return BMM_OK;
+}
+
 BMM_API bmm_status bmm_sample(const double* p, int32_t unit, const bmm_blocks* B, const int64_t* ck, int64_t c,
                               uint64_t seed, uint64_t stream_id, int32_t* idx_out, double* scale_out, void* ws,
                               size_t ws_bytes, bmm_stream_t stream) {

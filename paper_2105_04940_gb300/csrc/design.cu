@@ -241,11 +241,10 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 constexpr int kEndgameSteps = 256;  // steps of F left in (lo, hi] at or below which they are found directly
 
-__global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double* __restrict__ a,
-                                                          const double* __restrict__ f,
-                                                          const int64_t* __restrict__ off, int64_t K, int64_t n,
-                                                          int64_t c, int64_t* __restrict__ ck, double* __restrict__ g,
-                                                          DevStatus* st) {
+// The block sizes of one product by the whole (1024-thread) CTA.
+__device__ __forceinline__ void blocksizes_body(int kind, const double* __restrict__ a, const double* __restrict__ f,
+                                                const int64_t* __restrict__ off, int64_t K, int64_t n, int64_t c,
+                                                int64_t* __restrict__ ck, double* __restrict__ g, DevStatus* st) {
     __shared__ long long sF[32];
     __shared__ unsigned long long sLoHi[2];
     __shared__ long long sScan[33];
@@ -545,10 +544,43 @@ __global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double
     }
 }
 
+__global__ void __launch_bounds__(1024) blocksizes_kernel(int kind, const double* __restrict__ a,
+                                                          const double* __restrict__ f,
+                                                          const int64_t* __restrict__ off, int64_t K, int64_t n,
+                                                          int64_t c, int64_t* __restrict__ ck, double* __restrict__ g,
+                                                          DevStatus* st) {
+    blocksizes_body(kind, a, f, off, K, n, c, ck, g, st);
+}
+
 cudaError_t launch_blocksizes(int kind, const double* a, const double* f, const int64_t* off, int64_t K, int64_t n,
                               int64_t c, int64_t* ck, double* g, DevStatus* st, cudaStream_t s) {
     (count_launch(), blocksizes_kernel<<<1, 1024, 0, s>>>(kind, a, f, off, K, n, c, ck, g, st));
     return cudaGetLastError();
+}
+
+// Many products' block sizes in one launch: CTA i computes job i (the same body, so every c_k is
+// the one bmm_blocksizes gives for that product alone).
+struct SizesTable {
+    int count;
+    SizesJob job[kMaxSizesJobs];
+};
+static_assert(sizeof(SizesTable) <= 32764, "block-size table exceeds the kernel-parameter limit");
+
+__global__ void __launch_bounds__(1024) blocksizes_grouped_kernel(const __grid_constant__ SizesTable tab) {
+    const SizesJob& j = tab.job[blockIdx.x];
+    blocksizes_body(j.kind, j.a, j.f, j.off, j.K, j.n, j.c, j.ck, j.g, j.st);
+}
+
+cudaError_t launch_blocksizes_grouped(const SizesJob* jobs, int64_t count, cudaStream_t s) {
+    static SizesTable tab;  // host-side staging of the kernel parameter
+    for (int64_t i0 = 0; i0 < count; i0 += kMaxSizesJobs) {
+        tab.count = (int)imin(count - i0, kMaxSizesJobs);
+        for (int q = 0; q < tab.count; ++q) tab.job[q] = jobs[i0 + q];
+        (count_launch(), blocksizes_grouped_kernel<<<(unsigned)tab.count, 1024, 0, s>>>(tab));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace bmm

@@ -118,6 +118,18 @@ cudaError_t launch_probs(int kind, const double* x, const double* y, const doubl
                          double* p, DevStatus* st, cudaStream_t s);
 cudaError_t launch_blocksizes(int kind, const double* a, const double* f, const int64_t* off, int64_t K, int64_t n,
                               int64_t c, int64_t* ck, double* g, DevStatus* st, cudaStream_t s);
+// One product's block-size job (bmm_blocksizes without the pilot), for the grouped launch.
+struct SizesJob {
+    int kind;
+    const double *a, *f;
+    const int64_t* off;
+    int64_t K, n, c;
+    int64_t* ck;
+    double* g;
+    DevStatus* st;
+};
+constexpr int kMaxSizesJobs = 400;  // 80-byte jobs under the kernel-parameter limit
+cudaError_t launch_blocksizes_grouped(const SizesJob* jobs, int64_t count, cudaStream_t s);
 
 // ---- sampler.cu
 int64_t sampler_scratch_bytes(int64_t len, int64_t K);

@@ -123,7 +123,7 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
 
 def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
         gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None,
-        fmode: int = A.F_TC, fused_stats: bool = True, p_ready=None) -> dict:
+        fmode: int = A.F_TC, fused_stats: bool = True, p_ready=None, sizes_ready=None) -> dict:
     """One approximate product CD of prob.M @ prob.N by ``method`` (see module docstring).
 
     fmode: how OPL and WU compute ||M^k N_k||_F^2 -- A.F_TC (tensor-core Grams when the inputs
@@ -133,6 +133,7 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
 
     events: if a list, (stage name, torch.cuda.Event) pairs are appended at the stage
     boundaries (recorded on the current stream; used for timing only).
+    sizes_ready (OPL only): a (c_k, g_k) pair already computed for this product and this c.
     p_ready (OPL only): probabilities already computed, with prob.st holding the statistics and f
     (run_batched computes them for many products at once); the statistics calls are skipped.
     """
@@ -196,7 +197,10 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
             mark("stats")
             A.bmm_probs(M, N, B, A.P_COL_OPT, fmode | A.REUSE_STATS, None, st, ws)
             mark("exact_f" if fmode == A.F_EXACT else "gram_f")
-        A.bmm_blocksizes(M, N, B, st, A.CK_OPT, c, None, None, 0, ck, g, None, ws)
+        if sizes_ready is not None:  # (c_k, g_k) already computed for this product (run_batched)
+            ck, g = sizes_ready
+        else:
+            A.bmm_blocksizes(M, N, B, st, A.CK_OPT, c, None, None, 0, ck, g, None, ws)
         mark("blocksizes")
     elif method == "ONC":
         A.bmm_probs(M, N, B, A.P_COL_OPT, A.F_NONE, p, st, ws)
@@ -444,6 +448,7 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
             s.wait_stream(main)
     results = []
     ready = [None] * len(probs)
+    sizes = [None] * len(probs)
     if grouped_stats and method == "OPL" and fmode == A.F_TC and probs:
         ready = [torch.empty(pr.n, dtype=torch.float64, device=pr.M.device) for pr in probs]
         Ms, Ns, Bs = [pr.M for pr in probs], [pr.N for pr in probs], [pr.B for pr in probs]
@@ -454,13 +459,19 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
             # the norm passes of all products grouped, then the Gram passes grouped
             A.bmm_probs_batched(Ms, Ns, Bs, A.P_COL_OPT, A.F_NONE, ready, sts, wss)
             A.bmm_probs_batched(Ms, Ns, Bs, A.P_COL_OPT, A.F_TC | A.REUSE_STATS, None, sts, wss)
+        # every product's eq. 3.9 block sizes in one launch
+        cks = [torch.empty(pr.K, dtype=torch.int64, device=pr.M.device) for pr in probs]
+        gs = [torch.empty(pr.K, dtype=torch.float64, device=pr.M.device) for pr in probs]
+        A.bmm_blocksizes_batched(Bs, sts, A.CK_OPT, [int(x) for x in cs], cks, gs, wss)
+        sizes = list(zip(cks, gs))
         for s in streams:
             if s is not main:
                 s.wait_stream(main)
     for i, prob in enumerate(probs):
         with torch.cuda.stream(streams[i % len(streams)]):
             results.append(run(prob, method, int(cs[i]), int(seeds[i]), c0=c0, gemm_mode=gemm_mode,
-                               compute_product=False, fmode=fmode, fused_stats=fused_stats, p_ready=ready[i]))
+                               compute_product=False, fmode=fmode, fused_stats=fused_stats, p_ready=ready[i],
+                               sizes_ready=sizes[i]))
     for s in streams:
         if s is not main:
             main.wait_stream(s)

@@ -911,3 +911,49 @@ def test_probs_batched_matches_single_products(bmm, reuse):
         for key in ("x", "y", "a", "s", "mf", "nf", "f"):
             np.testing.assert_array_equal(host(a_.st[key]), host(b_.st[key]), err_msg=key)
         np.testing.assert_array_equal(host(pa), host(pb))
+
+
+@pytest.mark.parametrize("ckind", ["opt", "hat", "equal"])
+def test_blocksizes_batched_equals_single_products(bmm, ckind):
+    """bmm_blocksizes_batched over 430 products (two launches of the grouped kernel) gives every
+    product's c_k and g_k bit for bit as bmm_blocksizes alone, and the c_k equal the oracle's
+    apportionment of the same weights."""
+    A = bmm._abi
+    kind = {"opt": A.CK_OPT, "hat": A.CK_HAT, "equal": A.CK_EQUAL}[ckind]
+    rng = np.random.default_rng(211)
+    dev = torch.device("cuda", 0)
+    Bs, sts, cs, wss, offs, hosts = [], [], [], [], [], []
+    for i in range(430):
+        K = int(rng.integers(1, 40))
+        n = K * int(rng.integers(2, 30)) + int(rng.integers(0, 5))
+        off = S.block_offsets_uneven(n, K, 1, 2 * n // K + 1, seed=300 + i)
+        a = np.exp(rng.normal(0, 1.5, K)) * 10
+        f = a * a * rng.uniform(0, 0.9, K)
+        c = int(rng.integers(K, n + 1))
+        off_dev = to_dev(off.astype(np.int64))
+        offs.append(off_dev)
+        Bs.append(A.Blocks(K, n, int(np.max(np.diff(off))), off_dev.data_ptr()))
+        st = {k: None for k in ("x", "y", "s", "mf", "nf")}
+        st["a"], st["f"] = to_dev(a), to_dev(f)
+        sts.append(st)
+        cs.append(c)
+        wss.append(torch.zeros(1 << 16, dtype=torch.uint8, device=dev))
+        hosts.append((off, a, f, c))
+    cks = [torch.empty(B.K, dtype=torch.int64, device=dev) for B in Bs]
+    gs = [torch.empty(B.K, dtype=torch.float64, device=dev) for B in Bs]
+    A.bmm_blocksizes_batched(Bs, sts if kind != A.CK_EQUAL else None, kind, cs, cks, gs, wss)
+    for i in (0, 1, 199, 399, 400, 429):
+        ck1 = torch.empty_like(cks[i])
+        g1 = torch.empty_like(gs[i])
+        A.bmm_blocksizes(None, None, Bs[i], sts[i], kind, cs[i], None, None, 0, ck1, g1, None, wss[i])
+        assert torch.equal(ck1, cks[i]) and torch.equal(g1, gs[i]), i
+    for i in range(0, 430, 37):
+        off, a, f, c = hosts[i]
+        nk = np.diff(off)
+        g = {"opt": oracle.g_opt(a, f), "hat": oracle.g_hat(a), "equal": oracle.g_equal(len(nk))}[ckind]
+        np.testing.assert_array_equal(host(cks[i]), oracle.apportion(oracle.g_with_fallback(g, a, nk), nk, c))
+    for w in wss:
+        assert A.bmm_read_device_status(w) == A.OK
+    with pytest.raises(bmm.BmmError):  # c below K is refused on the host, before any launch
+        A.bmm_blocksizes_batched(Bs[:2], sts[:2], A.CK_HAT, [Bs[0].K - 1 if Bs[0].K > 1 else 0, cs[1]], cks[:2],
+                                 None, wss[:2])
