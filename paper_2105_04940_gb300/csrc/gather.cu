@@ -273,16 +273,23 @@ __device__ __forceinline__ void put_fp8x8(const OpWriter& wr, int64_t r, int64_t
     *reinterpret_cast<uint2*>(static_cast<__nv_fp8_storage_t*>(wr.out) + r * wr.ldo + j) = *reinterpret_cast<const uint2*>(q);
 }
 
-// Vectors are storage rows (row-major N): 64 (contraction index j) x 64 (r) tiles through shared
-// memory; rows are read 16 bytes at a time when aligned and the transposed operand is written 8
-// BF16 (16 bytes) at a time.  One CTA (256 threads) handles operand columns 64 bx .. 64 bx + 63
-// and rows from 64 by in steps of 64 gy.
+// Vectors are storage rows (row-major N): 64 (contraction index j) x S (coordinate r) tiles through
+// shared memory, S = 16 elements of 16 bytes (64 FP32, 128 BF16, 32 FP64 coordinates); rows are read
+// 16 bytes at a time when aligned and the transposed operand is written 8 BF16 (16 bytes) or 8 e4m3
+// at a time.  One CTA (256 threads) handles operand columns 64 bx .. 64 bx + 63 and coordinates from
+// S by in steps of S gy; the next step's loads are issued before this step's transposed stores, so
+// each CTA keeps a tile of loads (16 KB) in flight while it writes.
+template <typename T> constexpr int contig_step() { return 16 * (16 / (int)sizeof(T)); }
 template <typename T>
 __device__ __forceinline__ void gather_contig_bf16_body(const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec,
                                                         const int32_t* __restrict__ col, const double* __restrict__ w,
-                                                        int64_t ext, bool apply_weight, bool vec4, OpWriter wr,
+                                                        int64_t ext, bool apply_weight, bool vec16, OpWriter wr,
                                                         DevStatus* st, int64_t bx, int64_t by, int64_t gy) {
-    __shared__ float tile[64][65];
+    constexpr int EPL = 16 / (int)sizeof(T);    // elements per 16-byte load
+    constexpr int kStep = contig_step<T>();     // coordinates per step
+    constexpr int LPR = kStep / EPL;            // loads per draw per step (16)
+    constexpr int NL = 64 * LPR / 256;          // loads per thread per step (4)
+    __shared__ float tile[64][kStep + 1];
     __shared__ int64_t cidx[64];
     __shared__ float csw[64];
     const int64_t kseg = round_up(ext, wr.kunit);
@@ -303,53 +310,57 @@ __device__ __forceinline__ void gather_contig_bf16_body(const T* __restrict__ X,
         csw[t] = sw;
     }
     __syncthreads();
-    // 64 vectors x 64 coordinates per step; the next step's loads are issued before this step's
-    // transposed stores, so each CTA keeps a tile of loads in flight while it writes
-    float e[4][4];
+    float e[NL][EPL];
     auto load_tile = [&](int64_t r0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < NL; ++u) {
             const int idx = t + 256 * u;
-            const int jj = idx >> 4, q = idx & 15;
+            const int jj = idx / LPR, q = idx % LPR;
             const int64_t c = cidx[jj];
-            const int64_t r = r0 + 4 * q;
+            const int64_t r = r0 + EPL * q;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) e[u][k] = 0.f;
+            for (int k = 0; k < EPL; ++k) e[u][k] = 0.f;
             if (c >= 0) {
                 const T* src = X + c * ld + r;
-                if (vec4 && r + 4 <= len) {
-                    // four consecutive elements in one aligned load (16 bytes FP32, 8 bytes BF16)
+                if (vec16 && r + EPL <= len) {
+                    const uint4 raw = __ldg(reinterpret_cast<const uint4*>(src));
                     if constexpr (std::is_same<T, float>::value) {
-                        const float4 f4 = __ldg(reinterpret_cast<const float4*>(src));
-                        e[u][0] = f4.x; e[u][1] = f4.y; e[u][2] = f4.z; e[u][3] = f4.w;
+                        e[u][0] = __uint_as_float(raw.x); e[u][1] = __uint_as_float(raw.y);
+                        e[u][2] = __uint_as_float(raw.z); e[u][3] = __uint_as_float(raw.w);
+                    } else if constexpr (std::is_same<T, double>::value) {
+                        e[u][0] = (float)__hiloint2double((int)raw.y, (int)raw.x);
+                        e[u][1] = (float)__hiloint2double((int)raw.w, (int)raw.z);
                     } else {
-                        const uint2 u2 = __ldg(reinterpret_cast<const uint2*>(src));
-                        e[u][0] = __uint_as_float(u2.x << 16); e[u][1] = __uint_as_float(u2.x & 0xffff0000u);
-                        e[u][2] = __uint_as_float(u2.y << 16); e[u][3] = __uint_as_float(u2.y & 0xffff0000u);
+                        const uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            e[u][2 * k] = __uint_as_float(wd[k] << 16);
+                            e[u][2 * k + 1] = __uint_as_float(wd[k] & 0xffff0000u);
+                        }
                     }
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
+                    for (int k = 0; k < EPL; ++k)
                         if (r + k < len) e[u][k] = ldv<T, float>(src + k);
                 }
             }
         }
     };
-    int64_t r0 = by * 64;
+    int64_t r0 = by * kStep;
     if (r0 < len) load_tile(r0);
-    for (; r0 < len; r0 += gy * 64) {
+    for (; r0 < len; r0 += gy * kStep) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < NL; ++u) {
             const int idx = t + 256 * u;
-            const int jj = idx >> 4, q = idx & 15;
+            const int jj = idx / LPR, q = idx % LPR;
             const float sw = csw[jj];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) tile[jj][4 * q + k] = e[u][k] * sw;
+            for (int k = 0; k < EPL; ++k) tile[jj][EPL * q + k] = e[u][k] * sw;
         }
         __syncthreads();
-        if (r0 + gy * 64 < len) load_tile(r0 + gy * 64);
+        if (r0 + gy * kStep < len) load_tile(r0 + gy * kStep);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kStep / 32; ++u) {
             const int rr = (t >> 3) + 32 * u, jj8 = (t & 7) * 8;
             if (r0 + rr < len) {
                 float v[8];
@@ -369,26 +380,26 @@ __device__ __forceinline__ void gather_contig_bf16_body(const T* __restrict__ X,
 template <typename T>
 __global__ void __launch_bounds__(256) gather_contig_bf16_kernel(
     const T* __restrict__ X, int64_t len, int64_t ld, int64_t nvec, const int32_t* __restrict__ col,
-    const double* __restrict__ w, const int64_t* __restrict__ ext_dev, bool apply_weight, bool vec4, OpWriter wr,
+    const double* __restrict__ w, const int64_t* __restrict__ ext_dev, bool apply_weight, bool vec16, OpWriter wr,
     DevStatus* st) {
-    gather_contig_bf16_body<T>(X, len, ld, nvec, col, w, *ext_dev, apply_weight, vec4, wr, st, blockIdx.x, blockIdx.y,
+    gather_contig_bf16_body<T>(X, len, ld, nvec, col, w, *ext_dev, apply_weight, vec16, wr, st, blockIdx.x, blockIdx.y,
                                gridDim.y);
 }
 
-// CTAs along the coordinates of a contiguous BF16 / e4m3 gather: each takes up to four 64-coordinate
-// steps, so that its loads for one step overlap its stores of the previous one
-static int64_t contig_gy(int64_t len) { return imin(imax(ceil_div(ceil_div(len, 64), 4), 1), 2048); }
+// CTAs along the coordinates of a contiguous BF16 / e4m3 gather: each takes up to four steps of
+// contig_step<T>() coordinates, so that its loads for one step overlap its stores of the previous one
+template <typename T>
+static int64_t contig_gy(int64_t len) { return imin(imax(ceil_div(ceil_div(len, contig_step<T>()), 4), 1), 2048); }
 
 template <typename T> constexpr int dtype_of();
 template <> constexpr int dtype_of<float>() { return BMM_F32; }
 template <> constexpr int dtype_of<__nv_bfloat16>() { return BMM_BF16; }
 template <> constexpr int dtype_of<double>() { return BMM_F64; }
 
-// rows of X can be read four elements at a time (FP32: 16-byte loads, BF16: 8-byte loads)
+// rows of X can be read 16 bytes at a time: every row starts on a 16-byte boundary
 template <typename T>
-static bool contig_vec4(const VecSet& v) {
-    if (!std::is_same<T, float>::value && !std::is_same<T, __nv_bfloat16>::value) return false;
-    return (v.ld % 4) == 0 && (reinterpret_cast<uintptr_t>(v.data) % (4 * sizeof(T))) == 0;
+static bool contig_vec16(const VecSet& v) {
+    return (v.ld % (int64_t)(16 / sizeof(T))) == 0 && (reinterpret_cast<uintptr_t>(v.data) % 16) == 0;
 }
 
 template <typename T, typename V>
@@ -409,10 +420,10 @@ static cudaError_t gather_t(const VecSet& v, const int32_t* col, const double* w
             (count_launch(), gather_strided_kernel<T, V><<<grid, 128, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev,
                                                                               apply_weight, wr, st));
         } else {
-            const bool vec4 = contig_vec4<T>(v);
-            dim3 grid((unsigned)ceil_div(kmax, 64), (unsigned)contig_gy(v.len));
+            const bool vec16 = contig_vec16<T>(v);
+            dim3 grid((unsigned)ceil_div(kmax, 64), (unsigned)contig_gy<T>(v.len));
             (count_launch(), gather_contig_bf16_kernel<T><<<grid, 256, 0, s>>>(X, v.len, v.ld, v.count, col, w, ext_dev,
-                                                                               apply_weight, vec4, wr, st));
+                                                                               apply_weight, vec16, wr, st));
         }
         return cudaGetLastError();
     } else {
@@ -461,7 +472,7 @@ struct GatherJobDev {
     DevStatus* st;
     int gx, gy;
     int cta_begin;
-    int vec4;
+    int vec16;  // rows readable 16 bytes at a time
 };
 constexpr int kMaxGatherJobs = 224;  // 136-byte jobs: the table stays under the 32 KB parameter limit
 struct GatherTable {
@@ -487,7 +498,7 @@ __global__ void __launch_bounds__(STRIDED ? 128 : 256) gather_grouped_kernel(con
     if constexpr (STRIDED)
         gather_strided_body<T, float>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, jb.ext, true, jb.wr, jb.st, bx, by, jb.gy);
     else
-        gather_contig_bf16_body<T>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, jb.ext, true, jb.vec4 != 0, jb.wr, jb.st, bx,
+        gather_contig_bf16_body<T>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, jb.ext, true, jb.vec16 != 0, jb.wr, jb.st, bx,
                                    by, jb.gy);
 }
 
@@ -518,7 +529,7 @@ static cudaError_t gather_grouped_t(const GatherJob* jobs, int64_t count, cudaSt
         const int kunit = g.mode == BMM_GEMM_E4M3 ? 128 : 64;
         const int64_t kmax = round_up(imax(g.ext, 1), kunit);
         const int64_t gx = ceil_div(kmax, STRIDED ? 128 : 64);
-        const int64_t gy = STRIDED ? imin(imax(ceil_div(g.v.len, kGatherRows), 1), 4096) : contig_gy(g.v.len);
+        const int64_t gy = STRIDED ? imin(imax(ceil_div(g.v.len, kGatherRows), 1), 4096) : contig_gy<T>(g.v.len);
         if ((int64_t)tab.total + gx * gy > 0x7fffffffLL) {  // keep every launch's grid within 2^31 CTAs
             cudaError_t e = launch_gather_table<T, STRIDED>(tab, s);
             if (e != cudaSuccess) return e;
@@ -538,7 +549,7 @@ static cudaError_t gather_grouped_t(const GatherJob* jobs, int64_t count, cudaSt
         d.gx = (int)gx;
         d.gy = (int)gy;
         d.cta_begin = tab.total;
-        d.vec4 = contig_vec4<T>(g.v) ? 1 : 0;
+        d.vec16 = contig_vec16<T>(g.v) ? 1 : 0;
         tab.total += (int)(gx * gy);
     }
     return cudaSuccess;
