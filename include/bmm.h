@@ -47,7 +47,7 @@ typedef enum {
     BMM_ERR_WORKSPACE = 6,   /* workspace too small or misaligned */
     BMM_ERR_CUDA = 7,        /* a CUDA runtime call failed */
     BMM_ERR_TIMEOUT = 8,     /* a bounded device-side wait expired; the kernel returned early */
-    BMM_ERR_UNSUPPORTED = 9  /* valid request this build or device does not support */
+    BMM_ERR_UNSUPPORTED = 9  /* valid request this library or device does not support */
 } bmm_status;
 
 /* Element types. */

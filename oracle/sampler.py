@@ -1,7 +1,7 @@
 """I.i.d. sampling with replacement (oracle; test infrastructure only).
 
 Alg. 1 step 1(a) draws i_t with Pr(i_t = s) = p_s, independently and with
-replacement.  The paper does not say how; this build fixes a reproducible
+replacement.  The paper does not say how; this implementation fixes a reproducible
 convention so the CPU and GPU samplers can be compared index for index:
 
 * Random bits: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random

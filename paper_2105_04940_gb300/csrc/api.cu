@@ -905,7 +905,7 @@ BMM_API const char* bmm_status_string(bmm_status s) {
         case BMM_ERR_WORKSPACE: return "workspace too small or misaligned";
         case BMM_ERR_CUDA: return "CUDA runtime error";
         case BMM_ERR_TIMEOUT: return "bounded device wait expired";
-        case BMM_ERR_UNSUPPORTED: return "not supported by this build or device";
+        case BMM_ERR_UNSUPPORTED: return "not supported by this library or device";
     }
     return "unknown status";
 }
