@@ -73,6 +73,12 @@ constexpr int kMaxKMaps = 6;                  // K-major box heights 32 .. 192 r
 // tests pass with it on) but is slower, because the converter warps, now on the MMA's critical path
 // with one handshake per sub-tile and 4-byte reads of strided tiles, run out of issue slots.
 constexpr bool kTmemOperandA = false;
+// The same for contiguous tiles only (rows of the operand are vectors: the converters already read
+// 16 bytes per lane there), handed over one stage at a time: two groups of three chunks, stages of
+// at most three sub-tiles.  Strided tiles keep A in shared memory.  Off: also correct, also slower
+// (1.09 ms against 0.985 for the bench product's statistics pass).
+constexpr bool kTmemOperandAContig = false;
+constexpr int kAGroupChunks = 3;
 constexpr int kAChunks = 6;
 constexpr uint32_t kAChunkCols = 32;
 constexpr uint32_t kARingCol = 2 * 160;
@@ -522,6 +528,83 @@ __device__ __forceinline__ bool squares_ta(const uint8_t* base, const StageInfo*
     return true;
 }
 
+// Contiguous tiles with A in TMEM, windows with dpos + n_k <= 128, one hand-over per stage: the
+// lanes and K rows of squares_ta, the stage's (at most three) sub-tiles stored into A-chunk group g
+// (chunks 3 g .. 3 g + 2), then one tcgen05.wait::st and one arrive on bar_afull[g]; the MMA warp
+// frees the group with one commit on bar_aempty[g].  Partial sums as squares_ta.
+template <typename T>
+__device__ __forceinline__ bool squares_tc(const uint8_t* base, const StageInfo* info, uint64_t* bar_full,
+                                           uint64_t* bar_empty, uint64_t* bar_afull, uint64_t* bar_aempty, int& stage,
+                                           uint32_t& ph, int& grp, uint32_t& gph, volatile int* abort_flag, int cw,
+                                           int lane, int nk, int d, uint32_t tmem, float2 (*part)[kMaxBlock]) {
+    static_assert(std::is_same<T, float>::value, "TMEM operands are built for FP32 inputs");
+    const int q = (cw + 2) & 3, ks = cw >> 2;
+    const int v = 32 * q + lane;  // operand row
+    const int i = v - d;
+    const bool in = i >= 0 && i < nk;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16) + kARingCol + 8u * (uint32_t)ks;
+    const int sw = v & 7;
+    FF2 acc, tot;
+    acc.zero();
+    tot.zero();
+    int since_fold = 0;
+    while (true) {
+        if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
+        const StageInfo& si = info[stage];
+        const bool last = si.flags & ST_LAST;
+        const int nsub = si.nsub, sub_bytes = si.sub_bytes;
+        const bool loaded = v < 32 * si.nb;
+        const uint8_t* row = base + stage * kStageBytes + v * kRowBytes;
+        if (!wait_fast(smem_u32(&bar_aempty[grp]), gph ^ 1u, abort_flag)) return false;
+        for (int s = 0; s < nsub; ++s) {
+            uint32_t r[8];
+            if (loaded) {
+                const uint8_t* rs = row + s * sub_bytes;
+                const uint4 a0 = *reinterpret_cast<const uint4*>(rs + (((2 * ks) ^ sw) << 4));
+                const uint4 a1 = *reinterpret_cast<const uint4*>(rs + (((2 * ks + 1) ^ sw) << 4));
+                r[0] = a0.x; r[1] = a0.y; r[2] = a0.z; r[3] = a0.w;
+                r[4] = a1.x; r[5] = a1.y; r[6] = a1.z; r[7] = a1.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) r[e] = 0u;
+            }
+            if (in) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    acc.add_sq(make_float2(__uint_as_float(r[2 * u]), __uint_as_float(r[2 * u + 1])));
+            }
+            tmem_st_32x32b_x8(lane_base + (uint32_t)(grp * kAGroupChunks + s) * kAChunkCols, r);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(smem_u32(&bar_afull[grp]));
+            mbar_arrive(smem_u32(&bar_empty[stage]));
+        }
+        if (++grp == 2) { grp = 0; gph ^= 1u; }
+        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+        acc.renorm();
+        if (++since_fold == kFoldStages || last) {
+            tot.add(acc);
+            tot.renorm();
+            acc.zero();
+            since_fold = 0;
+        }
+        if (last) break;
+    }
+    const FF f = tot.both();
+#pragma unroll
+    for (int j = 0; j < kMaxBlock / 32; ++j) {
+        const int t = 32 * j + lane;
+        const int src = (t + d) & 31;
+        const float hi = __shfl_sync(0xffffffffu, f.hi, src), lo = __shfl_sync(0xffffffffu, f.lo, src);
+        const bool mine = ((t + d) >> 5) == q && t < nk;
+        part[cw][t] = mine ? make_float2(hi, lo) : make_float2(0.f, 0.f);
+    }
+    return true;
+}
+
 // Sums of squares of one phase of a wide block (d + n_k > 128): lane handles vectors lane + 32 v,
 // every element by itself.  Rare, so kept out of line to spare the kernel's registers.  Returns
 // the next (stage, phase bit) as stage | phase << 8, or -1 when a wait expired.
@@ -724,6 +807,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) uint64_t bar_afull[kAChunks], bar_aempty[kAChunks];
     // FP32 statistics pass: A from TMEM (two Gram slots and the A ring), else three Gram slots
     constexpr bool TA = kTmemOperandA && STATS && std::is_same<T, float>::value;
+    constexpr bool TC = !TA && kTmemOperandAContig && STATS && std::is_same<T, float>::value;
+    constexpr bool TWO = TA || TC;  // two Gram slots (the rest of TMEM holds A chunks)
     __shared__ StageInfo info[kStages];
     __shared__ BlockInfo binfo[kBlockSlots];
     __shared__ long long s_wb[G + 1];                               // first window of each product
@@ -834,7 +919,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     int nb = strided ? (int)((d + nk + TR::E - 1) / TR::E) : (int)((d + nk + 31) / 32);
                     if (!strided && wide && TR::kCornerRow0 + 128 > 32 * nb) nb = (TR::kCornerRow0 + 128) / 32;
                     const int box_bytes = strided ? mn_rows<T>(nb) * kRowBytes : 0;
-                    const int per = strided ? mn_rows<T>(nb) / TR::kMnSubRows : subtiles_per_stage(nb);
+                    int per = strided ? mn_rows<T>(nb) / TR::kMnSubRows : subtiles_per_stage(nb);
+                    if (TC && !strided && !wide && per > kAGroupChunks) per = kAGroupChunks;  // one A group
                     const long long nsub_total = (len + TR::E - 1) / TR::E;
                     const OperandMaps& maps = phase == 0 ? pr.mM : pr.mN;
                     const CUtensorMap* map = &maps.map[strided ? mn_map_index<T>(nb) : nb - 1];
@@ -884,8 +970,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t ph = 0;
             int it = 0;
             uint32_t slot_col = 0;
-            int aring = 0;
-            uint32_t aph = 0;
+            int aring = 0, grp = 0;
+            uint32_t aph = 0, gph = 0;
             bool aborted = false;
             while (true) {
                 if (!wait_fast(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
@@ -896,9 +982,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (first) {
                     // slot of this Gram: the (2 it + phase)-th use of the 3-slot ring, or with A in
                     // TMEM slot `phase`, used once per window
-                    const int u = TA ? it : 2 * it + phase;
-                    const int q = TA ? phase : u % 3;
-                    const uint32_t par = ((uint32_t)(TA ? u : u / 3) & 1u) ^ 1u;
+                    const int u = TWO ? it : 2 * it + phase;
+                    const int q = TWO ? phase : u % 3;
+                    const uint32_t par = ((uint32_t)(TWO ? u : u / 3) & 1u) ^ 1u;
                     if (!wait_fast(smem_u32(&bar_slot_free[q]), par, &s_abort)) {
                         aborted = true;
                         break;
@@ -912,7 +998,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d_main = tmem + slot_col, d_corner = tmem + slot_col + kCornerCol;
                 const uint32_t addr = smem_u32(stage_ptr(stage));
                 const uint32_t sub_bytes = (uint32_t)si.sub_bytes;
-                if (TA && !wide) {
+                if (TC && !mn && !wide) {
+                    // contiguous tile: A from the stage's TMEM chunk group, B from shared memory
+                    if (!wait_fast(smem_u32(&bar_afull[grp]), gph, &s_abort)) { aborted = true; break; }
+                    tc_fence_after();
+                    const uint64_t d0 = sw128_desc(addr);
+                    const uint64_t h = d0 & 0xFFFFFFFF00000000ull;
+                    const uint32_t lo0 = (uint32_t)d0, step = sub_bytes >> 4;
+                    const uint32_t idesc = (1u << 4) | (TR::kFmt << 7) | (TR::kFmt << 10) |
+                                           ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+                    for (int sb = 0; sb < si.nsub; ++sb) {
+                        const uint32_t a0 = tmem + kARingCol + (uint32_t)(grp * kAGroupChunks + sb) * kAChunkCols;
+                        const uint32_t lo = lo0 + (uint32_t)sb * step;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            tc_mma_tf32_ts(d_main, a0 + 8u * (uint32_t)kk, h | (uint64_t)(lo + 2u * (uint32_t)kk), idesc,
+                                           (first && sb == 0 && kk == 0) ? 0u : 1u);
+                    }
+                    tc_commit(smem_u32(&bar_aempty[grp]));
+                    if (++grp == 2) { grp = 0; gph ^= 1u; }
+                } else if (TA && !wide) {
                     // A: the sub-tile's chunk in TMEM (K-major there); B: the tile in shared memory
                     const uint64_t d0 = mn ? TR::mn_desc(addr, (uint32_t)si.box_bytes) : sw128_desc(addr);
                     const uint64_t h = d0 & 0xFFFFFFFF00000000ull;
@@ -960,8 +1065,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t ph = 0, bph = 0;
         int it = 0;
         int cs_uses = 0;
-        int aring = 0;
-        uint32_t aph = 0;
+        int aring = 0, grp = 0;
+        uint32_t aph = 0, gph = 0;
         const uint32_t cs_bar = smem_u32(&bar_cs);
         bool aborted = false;
         while (!aborted) {
@@ -990,15 +1095,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (done) {
                     } else if (dpos + nk <= 128) {
                         // every lane on whole 16-byte chunks (strided: partial sums per warp in
-                        // part[]; contiguous: x_i or y_i written directly)
+                        // part[]; contiguous: x_i or y_i written directly, or with A in TMEM partial
+                        // sums as strided)
                         if (!wait_fast(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
                         const bool mn = info[stage].flags & ST_MN;
-                        const bool ok = mn ? squares_strided<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw,
-                                                                lane, nk, dpos, part)
-                                           : squares_contig<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw,
-                                                               lane, nk, dpos, xy_ff[phase]);
-                        if (!ok) { aborted = true; break; }
-                        reduce_parts = mn;
+                        bool handled = false;
+                        if constexpr (TC) {
+                            if (!mn) {
+                                if (!squares_tc<T>(base, info, bar_full, bar_empty, bar_afull, bar_aempty, stage, ph,
+                                                   grp, gph, &s_abort, cw, lane, nk, dpos, tmem, part)) {
+                                    aborted = true;
+                                    break;
+                                }
+                                handled = true;
+                            }
+                        }
+                        if (!handled) {
+                            const bool ok =
+                                mn ? squares_strided<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane, nk,
+                                                        dpos, part)
+                                   : squares_contig<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane, nk,
+                                                       dpos, xy_ff[phase]);
+                            if (!ok) { aborted = true; break; }
+                            reduce_parts = mn;
+                        }
                     } else {
                         const int r = squares_wide<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane,
                                                       part);
@@ -1047,7 +1167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             FF2 offp;  // main-Gram products, two columns at a time
             offp.zero();
             const int u0 = 2 * it;
-            const int q0 = TA ? 0 : u0 % 3, q1 = TA ? 1 : (u0 + 1) % 3;
+            const int q0 = TWO ? 0 : u0 % 3, q1 = TWO ? 1 : (u0 + 1) % 3;
             const int q4 = warp & 3, quarter = cw >> 2;
             const int r = 32 * q4 + lane;  // operand row
             if (wait_fast(smem_u32(&bar_tfull[it & 1]), (uint32_t)(it >> 1) & 1u, &s_abort)) {
