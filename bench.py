@@ -10,9 +10,13 @@ A step is one approximate product by the A-optimal method (OPL: one statistics p
 column and row norms and ||M^k N_k||_F^2 -- exact float-float squares plus the off-diagonal terms of
 TF32 tcgen05 Grams --, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
 BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flush is
-needed).  Prints one JSON line.  --impl reference times the FP64 CPU oracle instead;
---workload batched runs the 512-product batched workload instead; --workload paper the paper's
-five experiments (Sec. 4) at their sizes.
+needed).  Prints one JSON line.  Besides the contract's keys it carries the stage times and their
+rooflines, `norm_pass_alone` (the statistics pass without f_k, timed apart), the exact GEMM
+baselines and the measured error against the closed form, `error_bars` (the error-bar calls on one
+product and the coverage of their 95% intervals), the other methods' times, e2e through host
+buffers and the CPU oracle's time on a bounded sample.  --impl reference times the FP64 CPU oracle
+instead; --workload batched runs the 512-product batched workload instead; --workload paper the
+paper's five experiments (Sec. 4) at their sizes.
 """
 from __future__ import annotations
 
