@@ -524,6 +524,7 @@ BMM_API bmm_status bmm_blocksizes_batched(int64_t count, const bmm_blocks* Bs, c
                                     ws_bytes == nullptr)))
         return BMM_ERR_ARG;
     if (ckind != BMM_CK_OPT && ckind != BMM_CK_HAT && ckind != BMM_CK_EQUAL) return BMM_ERR_ARG;
+    if (count == 0) return BMM_OK;
     if (ckind != BMM_CK_EQUAL && sts == nullptr) return BMM_ERR_ARG;
     std::vector<SizesJob> jobs;
     jobs.reserve((size_t)count);

@@ -116,3 +116,27 @@ def test_error_bar_calls_validate_arguments_on_host(lib):
     idx = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"BMM_REPORT_([A-Z0-9_]+) = (\d+)", text)}
     assert idx.pop("len") == _abi.REPORT_LEN
     assert [k for k, _ in sorted(idx.items(), key=lambda kv: kv[1])] == list(_abi.REPORT_FIELDS)
+
+
+def test_blocksizes_batched_validates_on_host(lib):
+    """bmm_blocksizes_batched refuses bad arguments before any device work: a negative count, the
+    pilot kind (which needs bmm_blocksizes), missing statistics, an infeasible c, a short workspace."""
+    from paper_2105_04940_gb300 import _abi
+    fake = 1 << 20  # never dereferenced
+    B = (_abi.Blocks * 1)(_abi.Blocks(4, 64, 16, fake))
+    st = (_abi.Stats * 1)(_abi.Stats(None, None, fake, None, None, None, fake))
+    cs = (ctypes.c_int64 * 1)(16)
+    ck = (ctypes.c_void_p * 1)(fake)
+    ws = (ctypes.c_void_p * 1)(1 << 21)  # 256-byte aligned
+    big = (ctypes.c_size_t * 1)(1 << 20)
+    small = (ctypes.c_size_t * 1)(64)
+    call = lib.bmm_blocksizes_batched
+    assert call(-1, B, st, _abi.CK_OPT, cs, ck, None, ws, big, None) == _abi.ERR_ARG
+    assert call(0, None, None, _abi.CK_OPT, None, None, None, None, None, None) == _abi.OK
+    assert call(1, B, st, _abi.CK_TILDE, cs, ck, None, ws, big, None) == _abi.ERR_ARG
+    assert call(1, B, None, _abi.CK_OPT, cs, ck, None, ws, big, None) == _abi.ERR_ARG
+    no_f = (_abi.Stats * 1)(_abi.Stats(None, None, fake, None, None, None, None))
+    assert call(1, B, no_f, _abi.CK_OPT, cs, ck, None, ws, big, None) == _abi.ERR_ARG
+    bad_c = (ctypes.c_int64 * 1)(3)  # below K
+    assert call(1, B, st, _abi.CK_OPT, bad_c, ck, None, ws, big, None) == _abi.ERR_INFEASIBLE
+    assert call(1, B, st, _abi.CK_OPT, cs, ck, None, ws, small, None) == _abi.ERR_WORKSPACE
