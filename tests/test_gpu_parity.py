@@ -957,3 +957,41 @@ def test_blocksizes_batched_equals_single_products(bmm, ckind):
     with pytest.raises(bmm.BmmError):  # c below K is refused on the host, before any launch
         A.bmm_blocksizes_batched(Bs[:2], sts[:2], A.CK_HAT, [Bs[0].K - 1 if Bs[0].K > 1 else 0, cs[1]], cks[:2],
                                  None, wss[:2])
+
+
+@pytest.mark.parametrize("case", ["all_aligned", "all_zero", "one_heavy"])
+def test_blocksizes_degenerate_weights(bmm, case):
+    """Block sizes when every eq. 3.9 weight is zero (every block rank-one aligned: fall back to
+    a_k), when every statistic is zero (fall back to n_k), and when one block's weight dwarfs the
+    rest by 2^80 (the geometric bracket and the exact endgame at the ends of the FP64 range):
+    bit-exact against the oracle for c from K to n."""
+    rng = np.random.default_rng(17)
+    K = 257
+    nk = rng.integers(1, 60, size=K)
+    off = np.concatenate([[0], np.cumsum(nk)]).astype(np.int64)
+    n = int(off[-1])
+    a = rng.lognormal(0, 1, size=K)
+    if case == "all_aligned":
+        f = a * a
+    elif case == "all_zero":
+        a = np.zeros(K)
+        f = np.zeros(K)
+    else:
+        f = a * a * 0.5
+        a[100] *= 2.0 ** 80
+        f[100] = a[100] ** 2 * 0.5
+    dev = torch.device("cuda:0")
+    st = {k: torch.zeros(K if k not in ("x", "y") else n, dtype=torch.float64, device=dev)
+          for k in ("x", "y", "a", "s", "mf", "nf", "f")}
+    st["a"].copy_(torch.from_numpy(a))
+    st["f"].copy_(torch.from_numpy(f))
+    off_dev = torch.as_tensor(off, device=dev)
+    B = bmm._abi.blocks(off_dev, n, int(nk.max()))
+    ws = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+    ck = torch.empty(K, dtype=torch.int64, device=dev)
+    g = torch.empty(K, dtype=torch.float64, device=dev)
+    gw = oracle.g_with_fallback(oracle.g_opt(a, f), a, nk)
+    for c in (K, K + 3, n // 2, n - 1, n):
+        bmm.bmm_blocksizes(None, None, B, st, bmm._abi.CK_OPT, c, None, None, 0, ck, g, None, ws)
+        assert bmm.bmm_read_device_status(ws) == 0
+        np.testing.assert_array_equal(host(ck), oracle.apportion(gw, nk, c), err_msg=f"c={c}")
