@@ -991,7 +991,7 @@ BMM_API bmm_status bmm_error_report(const bmm_blocks* B, const bmm_stats* st, co
         st->nf == nullptr || p == nullptr || ck == nullptr || report_out == nullptr)
         return BMM_ERR_ARG;
     if (!(delta > 0.0 && delta < 1.0) || c < 1) return BMM_ERR_ARG;
-    BMM_TRY(launch_error_report(st->x, st->y, p, B->offsets, B->K, ck, st->a, st->f, st->mf, st->nf,
+    BMM_TRY(launch_error_report(st->x, st->y, p, B->offsets, B->K, B->n, ck, st->a, st->f, st->mf, st->nf,
                                 st->f != nullptr ? fhat : nullptr, c, delta, report_out,
                                 reinterpret_cast<cudaStream_t>(stream)));
     return BMM_OK;

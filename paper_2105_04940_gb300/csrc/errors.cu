@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(256) entry_variance_kernel(MatView M, MatView 
     }
     double acc = 0.0, mean = 0.0;
     for (int64_t k = lane; k < K; k += 32) {
-        const int64_t a = off[k], b = off[k + 1];
+        // block ranges clamped to [0, n): a malformed offsets array cannot send a read outside M or N
+        const int64_t a = imax(off[k], 0), b = imin(off[k + 1], M.cols);
         if (unit == BMM_UNIT_COLUMN) {
             double s = 0.0, dot = 0.0;
             for (int64_t i = a; i < b; ++i) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256) entry_estimate_kernel(MatView M, MatView 
             double d = kNaN;
             if ((uint64_t)k < (uint64_t)K) {
                 d = 0.0;
-                for (int64_t i = off[k]; i < off[k + 1]; ++i) d += mat_at(M, h, i) * mat_at(N, i, f);
+                for (int64_t i = imax(off[k], 0); i < imin(off[k + 1], M.cols); ++i) d += mat_at(M, h, i) * mat_at(N, i, f);
             }
             cd += scale[t] * d;
         }
@@ -197,7 +198,8 @@ __global__ void __launch_bounds__(256) entry_estimate_kernel(MatView M, MatView 
                 double d = kNaN;
                 if ((uint64_t)k < (uint64_t)K) {
                     d = 0.0;
-                    for (int64_t i = off[k]; i < off[k + 1]; ++i) d += mat_at(M, h, i) * mat_at(N, i, f);
+                    for (int64_t i = imax(off[k], 0); i < imin(off[k + 1], M.cols); ++i)
+                        d += mat_at(M, h, i) * mat_at(N, i, f);
                 }
                 const double dz = scale[t] * d - zbar;
                 q += dz * dz;
@@ -245,7 +247,7 @@ __device__ double block_reduce(double v, int op, double* sm) {  // op 0 sum, 1 m
 
 __global__ void __launch_bounds__(1024) error_report_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                                             const double* __restrict__ p,
-                                                            const int64_t* __restrict__ off, int64_t K,
+                                                            const int64_t* __restrict__ off, int64_t K, int64_t n,
                                                             const int64_t* __restrict__ ck,
                                                             const double* __restrict__ a,
                                                             const double* __restrict__ f,
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(1024) error_report_kernel(const double* __rest
         ms += mf[k];
         ns += nf[k];
         double q = 0.0;
-        for (int64_t i = off[k]; i < off[k + 1]; ++i) {
+        for (int64_t i = imax(off[k], 0); i < imin(off[k + 1], n); ++i) {  // clamped to [0, n)
             const double xy = x[i] * y[i];
             const double pi = p[i];
             if (pi > 0.0) q += xy / pi;
@@ -333,10 +335,10 @@ __global__ void __launch_bounds__(1024) error_report_kernel(const double* __rest
 }
 
 cudaError_t launch_error_report(const double* x, const double* y, const double* p, const int64_t* off, int64_t K,
-                                const int64_t* ck, const double* a, const double* f, const double* mf,
+                                int64_t n, const int64_t* ck, const double* a, const double* f, const double* mf,
                                 const double* nf, const double* fhat, int64_t c, double delta, double* out,
                                 cudaStream_t s) {
-    (count_launch(), error_report_kernel<<<1, 1024, 0, s>>>(x, y, p, off, K, ck, a, f, mf, nf, fhat, c, delta, out));
+    (count_launch(), error_report_kernel<<<1, 1024, 0, s>>>(x, y, p, off, K, n, ck, a, f, mf, nf, fhat, c, delta, out));
     return cudaGetLastError();
 }
 

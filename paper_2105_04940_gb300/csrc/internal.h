@@ -73,7 +73,7 @@ cudaError_t launch_entry_estimate(const MatView& M, const MatView& N, const int6
                                   const int64_t* entries, int64_t count, double* cd, double* s2, int64_t* start,
                                   DevStatus* st, cudaStream_t s);
 cudaError_t launch_error_report(const double* x, const double* y, const double* p, const int64_t* off, int64_t K,
-                                const int64_t* ck, const double* a, const double* f, const double* mf,
+                                int64_t n, const int64_t* ck, const double* a, const double* f, const double* mf,
                                 const double* nf, const double* fhat, int64_t c, double delta, double* out,
                                 cudaStream_t s);
 
