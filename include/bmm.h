@@ -353,7 +353,8 @@ bmm_status bmm_entry_variance(const bmm_mat* M, const bmm_mat* N, const bmm_bloc
  * Unbiased for the variance of the blocks it covers, so (CD)_hf +- z sqrt(s2) is the normal interval
  * of Thm 3.1.  ck: device int64 [K] (column unit; sum must equal draws, else BMM_ERR_SHAPE in the
  * workspace status).  cd_out, s2_out: device FP64 [count]; NaN for an entry outside the product.
- * ws: at least 256 + 8 (K + 1) bytes (any bmm_workspace_size of the problem holds them).
+ * ws: 256-byte aligned, at least 256 + 8 (K + 1) bytes rounded up to a multiple of 256 (any
+ * bmm_workspace_size of the problem holds them); its status word records a draw-count mismatch.
  */
 bmm_status bmm_entry_estimate(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
                               const int64_t* ck, const int32_t* idx, const double* scale, int64_t draws,
