@@ -1,6 +1,6 @@
 """Pins for oracle.errors: the per-entry variance of eq. 3.7 and its one-sample estimate against
 exact enumeration of every sampling outcome, the whole-matrix report against Remark 2.2, the
-bounds of Thm 3.3 / Thm 4.2, and the special case of Remark 4.4."""
+bounds of Thm 3.3 / Thm 4.2, the special case of Remark 4.4 and the ordering of Remark 4.6."""
 import itertools
 import math
 
@@ -212,3 +212,27 @@ def test_interval_coverage_monte_carlo():
         hits += int(np.sum(np.abs(cd - MN) <= 1.96 * np.sqrt(s2)))
         total += len(ent)
     assert 0.90 <= hits / total <= 0.98, hits / total
+
+
+def test_report_probability_bounds_orderings():
+    # Thm 3.3: eta = phi + (theta2/theta1)^{1/2} (8/beta log 1/delta)^{1/2} with theta1 <= theta2, so the
+    # second term is at least the bare (8/beta log 1/delta)^{1/2} of Thm 4.2, with equality only when
+    # theta1 = theta2.  Remark 4.6: with pilot values theta2hat > 1 >= theta1hat and 1 - theta2 small,
+    # the Thm 4.4 bound (eq. 4.9) is weaker than the Thm 4.2 one (eq. 4.4).
+    off = S.block_offsets_equal(320, 8)
+    M, N = S.scaled_gaussian(16, 320, 12, off, 1.0, seed=41)
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    f = oracle.block_frob_sq(M, N, off)
+    p = oracle.p_col_opt(st["w"], st["a"], off)
+    ck = np.full(8, 10)
+    delta = 0.05
+    fhat = f.copy()
+    fhat[0] = 2.5 * st["a"][0] ** 2  # |1 - fhat/a^2| = 1.5 > 1
+    r = oracle.error_report(x, y, p, off, ck, st["a"], f, st["mf"], st["nf"], 80, delta, fhat=fhat)
+    bare = math.sqrt(8.0 / r["beta"] * math.log(1.0 / delta))
+    assert r["theta1"] < r["theta2"] <= 1.0
+    assert r["eta312"] - r["phi"] > bare * (1 + 1e-12)
+    assert r["eta44"] - r["phihat"] == pytest.approx(bare, rel=1e-14)
+    assert 1.0 - r["theta2"] < 0.2 and r["theta2hat"] > 1.0 >= r["theta1hat"]
+    assert r["eq49"] > r["eq44"]
