@@ -13,10 +13,11 @@ BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flu
 needed).  Prints one JSON line.  Besides the contract's keys it carries the stage times and their
 rooflines, `norm_pass_alone` (the statistics pass without f_k, timed apart), the exact GEMM
 baselines and the measured error against the closed form, `error_bars` (the error-bar calls on one
-product and the coverage of their 95% intervals), the other methods' times, e2e through host
-buffers and the CPU oracle's time on a bounded sample.  --impl reference times the FP64 CPU oracle
-instead; --workload batched runs the 512-product batched workload instead; --workload paper the
-paper's five experiments (Sec. 4) at their sizes.
+product and the coverage of their 95% intervals), `targets` (the workload's stated targets against
+these measurements), the other methods' times, e2e through host buffers and the CPU oracle's time
+on a bounded sample.  --impl reference times the FP64 CPU oracle instead; --workload batched runs
+the 512-product batched workload instead; --workload paper the paper's five experiments (Sec. 4)
+at their sizes.
 """
 from __future__ import annotations
 
@@ -413,8 +414,39 @@ def native_arm(args, ws, rank, local):
         v, t, sample = cpu_oracle_sample(w, args.method)
         result["cpu_baseline"] = {"value": v, "unit": "ms", "cores": oracle_cores(), "kind": "oracle",
                                   "sample": sample, "stage_seconds": t}
+    targets = target_checks(result, pk, w, L)
+    if targets:
+        result["targets"] = targets
     if rank == 0:
         print(json.dumps(result))
+
+
+def target_checks(result, pk, w, L):
+    """The workload's stated targets against this line's measurements (where they were taken):
+    the norm pass at >= 80% of HBM, the sampled GEMM at >= 60% of the tensor peak (the tuned GEMM's
+    own time), the product >= 5x faster than the exact FP32 GEMM, and the RMS relative error within
+    1.05x of the closed form."""
+    out = {}
+    try:
+        na = result.get("norm_pass_alone")
+        if na:
+            out["norm_pass_hbm_frac"] = {"value": na["frac"], "target": 0.8, "met": na["frac"] >= 0.8}
+        tuned = result.get("autotune") or {}
+        if tuned:
+            ms = min(v["ms"] for v in tuned.values())
+            peak = pk["bf16_sustained"] or pk["bf16"]
+            frac = 2.0 * w["m"] * w["p"] * L / (ms * 1e-3) / 1e12 / peak
+            out["gemm_tensor_frac"] = {"value": frac, "target": 0.6, "met": frac >= 0.6,
+                                       "note": "the tuned GEMM timed alone, of the sustained BF16 peak"}
+        if result.get("exact_fp32_gemm_ms"):
+            sp = result["exact_fp32_gemm_ms"] / result["value"]
+            out["speedup_vs_exact_fp32"] = {"value": sp, "target": 5.0, "met": sp >= 5.0}
+        if result.get("rel_err_ratio"):
+            r = result["rel_err_ratio"]
+            out["rel_err_over_closed_form"] = {"value": r, "target": 1.05, "met": r <= 1.05}
+    except (KeyError, TypeError, ValueError, ZeroDivisionError):
+        return {}
+    return out
 
 
 def batched_arm(args, ws, rank, local):
