@@ -181,11 +181,14 @@ bmm_status bmm_probs_batched(int64_t count, const bmm_mat* Ms, const bmm_mat* Ns
  * in a 16 MiB array compiled into the library (held on every GPU that loads it until exit);
  * problems needing more are rejected with BMM_ERR_WORKSPACE before any launch.
  *   pkind:      BMM_P_COL_OPT, BMM_P_COL_UNIFORM or BMM_P_BLK_NORMPROD (no ||M^k N_k||_F).
- *   status_out: device int32[2], zeroed by the caller; receives what bmm_probs records in the
- *               workspace status block (first error code, detail).
- *   M, N, B, p_out, st: as for bmm_probs (st->f unused).
+ *   status_out: device int32[2], 4-byte aligned, zeroed by the caller; receives what bmm_probs
+ *               records in the workspace status block (first error code, detail).
+ *   M, N, B, p_out, st: as for bmm_probs (st->f unused), checked by the same tests in the same order
+ *               with the same codes; a null or misaligned status_out is BMM_ERR_ARG.
  * The first call on each device looks up the array's address with that device current; make it
- * before any stream capture starts.  Calls share the array: calls that overlap on the GPU race.
+ * before any stream capture starts.  The address is kept for the life of the process, so resetting
+ * a device after its first call (cudaDeviceReset) is not supported.  Calls share the array: calls
+ * that overlap on the GPU race.
  */
 bmm_status bmm_probs_static(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t pkind,
                             double* p_out, const bmm_stats* st, int32_t* status_out, bmm_stream_t stream);

@@ -33,36 +33,9 @@ VecSet vecset_of_N(const bmm_mat* N) {
     return v;
 }
 
-namespace {
-
-constexpr size_t kStatusBytes = 256;
-
-// bump allocator over the workspace scratch; with base == nullptr it only counts
-struct Carver {
-    char* base;
-    size_t off = 0;
-    template <typename T> T* take(int64_t n) {
-        const size_t b = (size_t)round_up(imax(n, 1) * (int64_t)sizeof(T), 256);
-        T* r = base ? reinterpret_cast<T*>(base + off) : nullptr;
-        off += b;
-        return r;
-    }
-};
-
 size_t esize(int dtype) { return dtype == BMM_F64 ? 8 : (dtype == BMM_F32 ? 4 : 2); }
 
-bmm_status from_cuda(cudaError_t e) {
-    if (e == cudaSuccess) return BMM_OK;
-    if (e == cudaErrorInvalidValue) return BMM_ERR_UNSUPPORTED;
-    return BMM_ERR_CUDA;
-}
-
-#define BMM_TRY(expr)                                   \
-    do {                                                \
-        const bmm_status _s = from_cuda(expr);          \
-        if (_s != BMM_OK) return _s;                    \
-    } while (0)
-
+// ---- argument checks shared by the entry points (bmm_probs_static included)
 bmm_status check_mat(const bmm_mat* A) {
     if (A == nullptr || A->data == nullptr) return BMM_ERR_ARG;
     if (A->dtype != BMM_F64 && A->dtype != BMM_F32 && A->dtype != BMM_BF16) return BMM_ERR_DTYPE;
@@ -90,6 +63,34 @@ bmm_status check_problem(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
     if (M->dtype != N->dtype) return BMM_ERR_DTYPE;
     return BMM_OK;
 }
+
+namespace {
+
+constexpr size_t kStatusBytes = 256;
+
+// bump allocator over the workspace scratch; with base == nullptr it only counts
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T> T* take(int64_t n) {
+        const size_t b = (size_t)round_up(imax(n, 1) * (int64_t)sizeof(T), 256);
+        T* r = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += b;
+        return r;
+    }
+};
+
+bmm_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return BMM_OK;
+    if (e == cudaErrorInvalidValue) return BMM_ERR_UNSUPPORTED;
+    return BMM_ERR_CUDA;
+}
+
+#define BMM_TRY(expr)                                   \
+    do {                                                \
+        const bmm_status _s = from_cuda(expr);          \
+        if (_s != BMM_OK) return _s;                    \
+    } while (0)
 
 bmm_status check_ws(const void* ws, size_t ws_bytes, size_t need) {
     if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255)) return BMM_ERR_WORKSPACE;

@@ -32,6 +32,16 @@ struct VecSet {
 VecSet vecset_of_M(const bmm_mat* M);  // columns of M
 VecSet vecset_of_N(const bmm_mat* N);  // rows of N
 
+// ---- api.cu: host-side argument checks, identical for every entry point that takes them
+size_t esize(int dtype);  // bytes per element of BMM_F64 / BMM_F32 / BMM_BF16
+// null data, unknown dtype (BMM_ERR_DTYPE) or layout, negative sizes or short ld (BMM_ERR_SHAPE),
+// data not aligned to its element size (BMM_ERR_ARG)
+bmm_status check_mat(const bmm_mat* A);
+// null offsets, K < 1, n < K, max_nk outside [1, n] (BMM_ERR_SHAPE), n above INT32_MAX (BMM_ERR_UNSUPPORTED)
+bmm_status check_blocks(const bmm_blocks* B);
+// both matrices and the blocks, then n = cols(M) = rows(N) (BMM_ERR_SHAPE) and one dtype (BMM_ERR_DTYPE)
+bmm_status check_problem(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B);
+
 // ---- norms.cu
 // out[i] = ||vector i||^2 for i < count (FP64-accurate)
 cudaError_t launch_vec_sqnorms(const VecSet& v, double* out, double* partial, int64_t partial_cap,

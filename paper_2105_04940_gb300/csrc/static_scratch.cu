@@ -16,6 +16,11 @@
 //    calls whose work overlaps on the GPU (different streams, no ordering) race on the array.
 //  - Problems whose partial sums need more than kStaticScratchBytes are rejected with
 //    BMM_ERR_WORKSPACE before anything is launched; use bmm_probs with a workspace instead.
+//  - The address is cached per device for the life of the process.  Resetting a device after the
+//    first call (cudaDeviceReset, or anything else that tears its primary context down) leaves a
+//    stale address behind, so it is not supported; every other use of the device is unaffected.
+//  - Arguments are checked exactly as bmm_probs checks them (same tests, same order, same codes),
+//    plus the status word: non-null and 4-byte aligned (it is updated with 32-bit atomics).
 #include <mutex>
 
 #include "internal.h"
@@ -50,14 +55,6 @@ cudaError_t static_scratch_address(void** out) {
     return cudaSuccess;
 }
 
-bool mat_ok(const bmm_mat* A) {
-    if (A == nullptr || A->data == nullptr || A->rows < 0 || A->cols < 0) return false;
-    if (A->dtype != BMM_F64 && A->dtype != BMM_F32 && A->dtype != BMM_BF16) return false;
-    if (A->layout != BMM_ROW_MAJOR && A->layout != BMM_COL_MAJOR) return false;
-    const int64_t inner = (A->layout == BMM_ROW_MAJOR) ? A->cols : A->rows;
-    return A->ld >= imax(inner, 1);
-}
-
 }  // namespace
 }  // namespace bmm
 
@@ -65,13 +62,12 @@ using namespace bmm;
 
 BMM_API bmm_status bmm_probs_static(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t pkind,
                                     double* p_out, const bmm_stats* st, int32_t* status_out, bmm_stream_t stream) {
-    if (!mat_ok(M) || !mat_ok(N) || B == nullptr || B->offsets == nullptr || status_out == nullptr)
-        return BMM_ERR_ARG;
-    if (M->dtype != N->dtype) return BMM_ERR_DTYPE;
-    if (B->K < 1 || B->n < B->K || B->max_nk < 1 || B->max_nk > B->n || M->cols != N->rows || M->cols != B->n)
-        return BMM_ERR_SHAPE;
+    // the order of bmm_probs: the kind, then the problem, then the statistics
     if (pkind != BMM_P_COL_OPT && pkind != BMM_P_COL_UNIFORM && pkind != BMM_P_BLK_NORMPROD) return BMM_ERR_ARG;
+    bmm_status s = check_problem(M, N, B);
+    if (s != BMM_OK) return s;
     if (st == nullptr || !st->x || !st->y || !st->a || !st->s || !st->mf || !st->nf) return BMM_ERR_ARG;
+    if (status_out == nullptr || (reinterpret_cast<uintptr_t>(status_out) & 3)) return BMM_ERR_ARG;
     const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
     const int64_t partial_elems = imax(vec_sqnorms_partial_elems(vM), vec_sqnorms_partial_elems(vN));
     if ((size_t)partial_elems * sizeof(double) > kStaticScratchBytes) return BMM_ERR_WORKSPACE;

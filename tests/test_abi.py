@@ -140,3 +140,64 @@ def test_blocksizes_batched_validates_on_host(lib):
     bad_c = (ctypes.c_int64 * 1)(3)  # below K
     assert call(1, B, st, _abi.CK_OPT, bad_c, ck, None, ws, big, None) == _abi.ERR_INFEASIBLE
     assert call(1, B, st, _abi.CK_OPT, cs, ck, None, ws, small, None) == _abi.ERR_WORKSPACE
+
+
+def test_static_entry_point_checks_arguments_like_bmm_probs(lib):
+    """bmm_probs_static and bmm_probs refuse the same bad descriptors with the same status codes,
+    before anything is launched (host only: no pointer below is ever dereferenced).  bmm_probs is
+    called first with no workspace, so a case that slipped past the descriptor checks would fail
+    there (BMM_ERR_WORKSPACE) before bmm_probs_static could launch anything on the fake pointers."""
+    from paper_2105_04940_gb300 import _abi
+    fake = 1 << 20
+    n, K = 4096, 64
+
+    def M_(**kw):
+        d = dict(data=fake, rows=256, cols=n, ld=n, dtype=_abi.F32, layout=_abi.ROW_MAJOR)
+        d.update(kw)
+        return _abi.Mat(d["data"], d["rows"], d["cols"], d["ld"], d["dtype"], d["layout"])
+
+    def N_(**kw):
+        d = dict(data=fake, rows=n, cols=256, ld=256, dtype=_abi.F32, layout=_abi.ROW_MAJOR)
+        d.update(kw)
+        return _abi.Mat(d["data"], d["rows"], d["cols"], d["ld"], d["dtype"], d["layout"])
+
+    def B_(**kw):
+        d = dict(K=K, n=n, max_nk=64, offsets=fake)
+        d.update(kw)
+        return _abi.Blocks(d["K"], d["n"], d["max_nk"], d["offsets"])
+
+    good_st = _abi.Stats(*([fake] * 6 + [None]))
+    big = 1 << 31
+    cases = {
+        "M null": (M_(data=None), N_(), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_ARG),
+        "M dtype": (M_(dtype=7), N_(), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_DTYPE),
+        "M misaligned for F32": (M_(data=fake + 2), N_(), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_ARG),
+        "F64 N misaligned": (M_(dtype=_abi.F64), N_(dtype=_abi.F64, data=fake + 4), B_(), _abi.P_COL_OPT, good_st,
+                             _abi.ERR_ARG),
+        "N layout": (M_(), N_(layout=5), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_ARG),
+        "M negative rows": (M_(rows=-1), N_(), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_SHAPE),
+        "M short ld": (M_(ld=n - 1), N_(), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_SHAPE),
+        "K = 0": (M_(), N_(), B_(K=0), _abi.P_COL_OPT, good_st, _abi.ERR_SHAPE),
+        "offsets null": (M_(), N_(), B_(offsets=None), _abi.P_COL_OPT, good_st, _abi.ERR_ARG),
+        "n above INT32_MAX": (M_(cols=big, ld=big), N_(rows=big), B_(n=big), _abi.P_COL_OPT, good_st,
+                              _abi.ERR_UNSUPPORTED),
+        "cols(M) != rows(N)": (M_(), N_(rows=n - 1), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_SHAPE),
+        "dtype mismatch": (M_(), N_(dtype=_abi.BF16, ld=256), B_(), _abi.P_COL_OPT, good_st, _abi.ERR_DTYPE),
+        "unknown pkind": (M_(), N_(), B_(), 9, good_st, _abi.ERR_ARG),
+        "stats without x": (M_(), N_(), B_(), _abi.P_COL_OPT, _abi.Stats(*([None] + [fake] * 5 + [None])),
+                            _abi.ERR_ARG),
+    }
+    by = ctypes.byref
+    for name, (M, N, B, pk, st, want) in cases.items():
+        got = lib.bmm_probs(by(M), by(N), by(B), pk, _abi.F_NONE, None, by(st), None, 0, None)
+        assert got == want, (name, got)
+        status = ctypes.c_void_p(fake)
+        got_static = lib.bmm_probs_static(by(M), by(N), by(B), pk, None, by(st), status, None)
+        assert got_static == want, (name, got_static)
+    # the status word of the static form is updated with 32-bit atomics: null or misaligned is refused
+    Mg, Ng, Bg = M_(), N_(), B_()
+    assert lib.bmm_probs(by(Mg), by(Ng), by(Bg), _abi.P_COL_OPT, _abi.F_NONE, None, by(good_st), None, 0,
+                         None) == _abi.ERR_WORKSPACE
+    for bad in (None, ctypes.c_void_p(fake + 2)):
+        assert lib.bmm_probs_static(by(Mg), by(Ng), by(Bg), _abi.P_COL_OPT, None, by(good_st), bad,
+                                    None) == _abi.ERR_ARG
