@@ -199,3 +199,26 @@ def test_error_bars_on_a_run(bmm):
     cover = np.mean((MN.ravel() >= lo) & (MN.ravel() <= hi))
     assert 0.90 <= cover <= 0.985, cover
     np.testing.assert_allclose(host(eb["value"]), host(res["out"]).ravel(), rtol=1e-9, atol=1e-9 * np.abs(MN).max())
+
+
+def test_error_report_hand_worked_example(bmm):
+    """bmm_error_report on the hand-worked example of tests/golden/error_report_thm33_thm44.json
+    (theta_1 != theta_2, beta < 1, theta-hat_1 != theta-hat_2): every field against the values
+    simplified by hand from Remark 2.2, eq. 3.10 and Thms 3.3, 4.2 and 4.4."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "error_report_thm33_thm44.json")
+    with open(path) as fh:
+        fx = json.load(fh)
+    i = fx["inputs"]
+    off = np.asarray(i["offsets"], dtype=np.int64)
+    off_dev = to_dev(off)
+    B = bmm._abi.blocks(off_dev, int(off[-1]), int(np.diff(off).max()))
+    dst = {k: to_dev(np.asarray(i[k], dtype=np.float64)) for k in ("x", "y", "a", "mf", "nf", "f")}
+    out = torch.empty(bmm._abi.REPORT_LEN, dtype=torch.float64, device=off_dev.device)
+    bmm._abi.bmm_error_report(B, dst, to_dev(np.asarray(i["p"], dtype=np.float64)),
+                              to_dev(np.asarray(i["ck"], dtype=np.int64)), int(i["c"]),
+                              to_dev(np.asarray(i["fhat"], dtype=np.float64)), math.exp(-1.0), out)
+    got = dict(zip(bmm._abi.REPORT_FIELDS, host(out).tolist()))
+    for name, e in fx["expected"].items():
+        assert got[name] == pytest.approx(e["value"], rel=1e-13, abs=0.0), name

@@ -2,7 +2,9 @@
 exact enumeration of every sampling outcome, the whole-matrix report against Remark 2.2, the
 bounds of Thm 3.3 / Thm 4.2, the special case of Remark 4.4 and the ordering of Remark 4.6."""
 import itertools
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -236,3 +238,35 @@ def test_report_probability_bounds_orderings():
     assert r["eta44"] - r["phihat"] == pytest.approx(bare, rel=1e-14)
     assert 1.0 - r["theta2"] < 0.2 and r["theta2hat"] > 1.0 >= r["theta1hat"]
     assert r["eq49"] > r["eq44"]
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "error_report_thm33_thm44.json")
+
+
+def _golden():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+def test_report_hand_worked_example_theta1_ne_theta2_beta_below_one():
+    """Every report field against values simplified by hand from Remark 2.2, eq. 3.10, Thm 3.3,
+    Thm 4.2 and Thm 4.4 (tests/golden/error_report_thm33_thm44.json): theta_1 = 0.25 != theta_2 = 0.64,
+    beta = 0.5 and theta-hat = (0.5, 0.6), so every term of phi and phi-tilde carries weight.  A
+    slip such as swapping theta_1 beta and theta_2 theta_1 beta in phi (phi^2 = 1.7125 instead of
+    1.4875), or theta-hat_2 for theta_2 in phi-tilde, moves a field far outside the tolerance."""
+    fx = _golden()
+    i = fx["inputs"]
+    r = oracle.error_report(i["x"], i["y"], i["p"], i["offsets"], i["ck"], i["a"], i["f"], i["mf"], i["nf"], i["c"],
+                            math.exp(-1.0), fhat=i["fhat"])
+    for name, e in fx["expected"].items():
+        assert r[name] == pytest.approx(e["value"], rel=1e-13, abs=0.0), name
+
+
+def test_report_hand_worked_example_discriminates():
+    """The example separates the readings a slip would produce: the pinned phi^2 and phi-tilde^2
+    differ from the swapped-term and hatted-theta_2 variants by far more than the tolerance."""
+    ex = _golden()["expected"]
+    assert abs(ex["phi"]["value"] ** 2 - 1.4875) < 1e-14
+    assert abs(1.7125 - 1.4875) > 0.2  # theta_1 beta and theta_2 theta_1 beta swapped
+    assert abs(ex["phitilde"]["value"] ** 2 * math.sqrt(0.3) - 0.51) < 1e-14
+    assert abs(0.50 - 0.51) > 1e-3  # theta-hat_2 in place of theta_2

@@ -141,3 +141,17 @@ def test_alg2_scales_and_streams():
     np.testing.assert_array_equal(idx, idx3)
     with pytest.raises(ValueError):
         oracle.sample_segments(np.zeros(3), [0, 3], [1], seed=0, sid=0)
+
+
+@pytest.mark.parametrize("counter,key,want", [
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+])
+def test_philox_known_answers(counter, key, want):
+    """Philox4x32-10 against the known-answer vectors published with the generator (Salmon et al.,
+    SC'11, and its reference distribution): all-zero, all-ones and pi-digit counter and key.  No
+    other implementation is needed, so this pin holds wherever the test runs."""
+    got = oracle.philox4x32_10(*counter, *key)
+    assert tuple(int(v) for v in got) == want
