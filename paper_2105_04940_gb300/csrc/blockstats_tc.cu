@@ -67,22 +67,6 @@ constexpr int kCornerCol = 144;               // wide blocks: rows >= 128 x rows
 constexpr int kMaxBlock = 128;
 constexpr int kFoldStages = 4;                // stages between folds into the second-level sums
 constexpr int kMaxKMaps = 6;                  // K-major box heights 32 .. 192 rows
-// FP32 statistics pass with the MMA's A operand in TMEM (written there by the converter warps, which
-// read every element anyway) instead of shared memory: two Gram slots, then a ring of A chunks of 32
-// columns (one sub-tile's K), 512 = 2 * 160 + 6 * 32.  Off: it gives the same results (the parity
-// tests pass with it on) but is slower, because the converter warps, now on the MMA's critical path
-// with one handshake per sub-tile and 4-byte reads of strided tiles, run out of issue slots.
-constexpr bool kTmemOperandA = false;
-// The same for contiguous tiles only (rows of the operand are vectors: the converters already read
-// 16 bytes per lane there), handed over one stage at a time: two groups of three chunks, stages of
-// at most three sub-tiles.  Strided tiles keep A in shared memory.  Off: also correct, also slower
-// (1.09 ms against 0.985 for the bench product's statistics pass).
-constexpr bool kTmemOperandAContig = false;
-constexpr int kAGroupChunks = 3;
-constexpr int kAChunks = 6;
-constexpr uint32_t kAChunkCols = 32;
-constexpr uint32_t kARingCol = 2 * 160;
-
 // Element-type traits.  E elements fill a 128-byte row; one MMA consumes 32 bytes of K.
 template <typename T> struct Tr;
 template <> struct Tr<float> {
@@ -440,171 +424,6 @@ __device__ __forceinline__ bool squares_contig(const uint8_t* base, const StageI
     return true;
 }
 
-// FP32 statistics pass with A in TMEM, windows with dpos + n_k <= 128.  The 16 converter warps read
-// every sub-tile once: warp cw serves the TMEM lane quarter q = (cw + 2) mod 4 that its CTA warp
-// index may access (operand rows 32 q .. 32 q + 31, one per lane) and K rows 8 (cw / 4) .. + 7 of
-// the sub-tile.  A lane adds the squares of its vector's elements and stores the eight values into
-// its TMEM lane, columns 8 (cw / 4) .. + 7 of the sub-tile's A chunk (a ring of kAChunks chunks);
-// the MMA warp then reads only B from shared memory.  bar_afull[c]: the 16 warps' stores of chunk c
-// are done; bar_aempty[c]: the MMAs that read chunk c are done (tcgen05.commit).  Operand rows the
-// stage did not load are stored as zeros.  Sums per [warp][window-relative vector] go to part[]
-// (zero where the warp holds none).  Return false when a wait expired.
-template <typename T>
-__device__ __forceinline__ bool squares_ta(const uint8_t* base, const StageInfo* info, uint64_t* bar_full,
-                                           uint64_t* bar_empty, uint64_t* bar_afull, uint64_t* bar_aempty, int& stage,
-                                           uint32_t& ph, int& aring, uint32_t& aph, volatile int* abort_flag, int cw,
-                                           int lane, int nk, int d, uint32_t tmem, float2 (*part)[kMaxBlock]) {
-    static_assert(std::is_same<T, float>::value, "TMEM operands are built for FP32 inputs");
-    const int q = (cw + 2) & 3, ks = cw >> 2;
-    const int v = 32 * q + lane;  // operand row
-    const int i = v - d;          // vector of the window
-    const bool in = i >= 0 && i < nk;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16) + kARingCol + 8u * (uint32_t)ks;
-    FF2 acc, tot;
-    acc.zero();
-    tot.zero();
-    int since_fold = 0;
-    while (true) {
-        if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
-        const StageInfo& si = info[stage];
-        const bool mn = si.flags & ST_MN;
-        const bool last = si.flags & ST_LAST;
-        const int nsub = si.nsub, sub_bytes = si.sub_bytes, box_bytes = si.box_bytes;
-        const bool loaded = v < 32 * si.nb;  // the stage holds this operand row
-        const uint8_t* st_base = base + stage * kStageBytes;
-        for (int s = 0; s < nsub; ++s) {
-            if (!wait_fast(smem_u32(&bar_aempty[aring]), aph ^ 1u, abort_flag)) return false;
-            uint32_t r[8];
-            if (loaded && mn) {
-                // column v & 31 of box v / 32, rows 8 ks .. 8 ks + 7 of sub-tile s
-                const uint8_t* src = st_base + (v >> 5) * box_bytes + s * sub_bytes;
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    r[e] = *reinterpret_cast<const uint32_t*>(src + Tr<T>::mn_offset(8 * ks + e, v & 31));
-            } else if (loaded) {
-                // row v of sub-tile s, 16-byte chunks 2 ks and 2 ks + 1 (chunk u at u ^ (v mod 8))
-                const uint8_t* row = st_base + s * sub_bytes + v * kRowBytes;
-                const uint4 a0 = *reinterpret_cast<const uint4*>(row + (((2 * ks) ^ (v & 7)) << 4));
-                const uint4 a1 = *reinterpret_cast<const uint4*>(row + (((2 * ks + 1) ^ (v & 7)) << 4));
-                r[0] = a0.x; r[1] = a0.y; r[2] = a0.z; r[3] = a0.w;
-                r[4] = a1.x; r[5] = a1.y; r[6] = a1.z; r[7] = a1.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) r[e] = 0u;
-            }
-            if (in) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    acc.add_sq(make_float2(__uint_as_float(r[2 * u]), __uint_as_float(r[2 * u + 1])));
-            }
-            tmem_st_32x32b_x8(lane_base + (uint32_t)aring * kAChunkCols, r);
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bar_afull[aring]));
-            if (++aring == kAChunks) { aring = 0; aph ^= 1u; }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
-        if (++stage == kStages) { stage = 0; ph ^= 1u; }
-        acc.renorm();
-        if (++since_fold == kFoldStages || last) {
-            tot.add(acc);
-            tot.renorm();
-            acc.zero();
-            since_fold = 0;
-        }
-        if (last) break;
-    }
-    const FF f = tot.both();
-#pragma unroll
-    for (int j = 0; j < kMaxBlock / 32; ++j) {
-        const int t = 32 * j + lane;
-        const int src = (t + d) & 31;
-        const float hi = __shfl_sync(0xffffffffu, f.hi, src), lo = __shfl_sync(0xffffffffu, f.lo, src);
-        const bool mine = ((t + d) >> 5) == q && t < nk;
-        part[cw][t] = mine ? make_float2(hi, lo) : make_float2(0.f, 0.f);
-    }
-    return true;
-}
-
-// Contiguous tiles with A in TMEM, windows with dpos + n_k <= 128, one hand-over per stage: the
-// lanes and K rows of squares_ta, the stage's (at most three) sub-tiles stored into A-chunk group g
-// (chunks 3 g .. 3 g + 2), then one tcgen05.wait::st and one arrive on bar_afull[g]; the MMA warp
-// frees the group with one commit on bar_aempty[g].  Partial sums as squares_ta.
-template <typename T>
-__device__ __forceinline__ bool squares_tc(const uint8_t* base, const StageInfo* info, uint64_t* bar_full,
-                                           uint64_t* bar_empty, uint64_t* bar_afull, uint64_t* bar_aempty, int& stage,
-                                           uint32_t& ph, int& grp, uint32_t& gph, volatile int* abort_flag, int cw,
-                                           int lane, int nk, int d, uint32_t tmem, float2 (*part)[kMaxBlock]) {
-    static_assert(std::is_same<T, float>::value, "TMEM operands are built for FP32 inputs");
-    const int q = (cw + 2) & 3, ks = cw >> 2;
-    const int v = 32 * q + lane;  // operand row
-    const int i = v - d;
-    const bool in = i >= 0 && i < nk;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16) + kARingCol + 8u * (uint32_t)ks;
-    const int sw = v & 7;
-    FF2 acc, tot;
-    acc.zero();
-    tot.zero();
-    int since_fold = 0;
-    while (true) {
-        if (!wait_fast(smem_u32(&bar_full[stage]), ph, abort_flag)) return false;
-        const StageInfo& si = info[stage];
-        const bool last = si.flags & ST_LAST;
-        const int nsub = si.nsub, sub_bytes = si.sub_bytes;
-        const bool loaded = v < 32 * si.nb;
-        const uint8_t* row = base + stage * kStageBytes + v * kRowBytes;
-        if (!wait_fast(smem_u32(&bar_aempty[grp]), gph ^ 1u, abort_flag)) return false;
-        for (int s = 0; s < nsub; ++s) {
-            uint32_t r[8];
-            if (loaded) {
-                const uint8_t* rs = row + s * sub_bytes;
-                const uint4 a0 = *reinterpret_cast<const uint4*>(rs + (((2 * ks) ^ sw) << 4));
-                const uint4 a1 = *reinterpret_cast<const uint4*>(rs + (((2 * ks + 1) ^ sw) << 4));
-                r[0] = a0.x; r[1] = a0.y; r[2] = a0.z; r[3] = a0.w;
-                r[4] = a1.x; r[5] = a1.y; r[6] = a1.z; r[7] = a1.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) r[e] = 0u;
-            }
-            if (in) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    acc.add_sq(make_float2(__uint_as_float(r[2 * u]), __uint_as_float(r[2 * u + 1])));
-            }
-            tmem_st_32x32b_x8(lane_base + (uint32_t)(grp * kAGroupChunks + s) * kAChunkCols, r);
-        }
-        tmem_st_wait();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-            mbar_arrive(smem_u32(&bar_afull[grp]));
-            mbar_arrive(smem_u32(&bar_empty[stage]));
-        }
-        if (++grp == 2) { grp = 0; gph ^= 1u; }
-        if (++stage == kStages) { stage = 0; ph ^= 1u; }
-        acc.renorm();
-        if (++since_fold == kFoldStages || last) {
-            tot.add(acc);
-            tot.renorm();
-            acc.zero();
-            since_fold = 0;
-        }
-        if (last) break;
-    }
-    const FF f = tot.both();
-#pragma unroll
-    for (int j = 0; j < kMaxBlock / 32; ++j) {
-        const int t = 32 * j + lane;
-        const int src = (t + d) & 31;
-        const float hi = __shfl_sync(0xffffffffu, f.hi, src), lo = __shfl_sync(0xffffffffu, f.lo, src);
-        const bool mine = ((t + d) >> 5) == q && t < nk;
-        part[cw][t] = mine ? make_float2(hi, lo) : make_float2(0.f, 0.f);
-    }
-    return true;
-}
-
 // Sums of squares of one phase of a wide block (d + n_k > 128): lane handles vectors lane + 32 v,
 // every element by itself.  Rare, so kept out of line to spare the kernel's registers.  Returns
 // the next (stage, phase bit) as stage | phase << 8, or -1 when a wait expired.
@@ -804,11 +623,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
     __shared__ __align__(8) uint64_t bar_bfull[kBlockSlots], bar_bempty[kBlockSlots];
     __shared__ __align__(8) uint64_t bar_slot_free[3], bar_tfull[2], bar_drain, bar_cs;
-    __shared__ __align__(8) uint64_t bar_afull[kAChunks], bar_aempty[kAChunks];
-    // FP32 statistics pass: A from TMEM (two Gram slots and the A ring), else three Gram slots
-    constexpr bool TA = kTmemOperandA && STATS && std::is_same<T, float>::value;
-    constexpr bool TC = !TA && kTmemOperandAContig && STATS && std::is_same<T, float>::value;
-    constexpr bool TWO = TA || TC;  // two Gram slots (the rest of TMEM holds A chunks)
     __shared__ StageInfo info[kStages];
     __shared__ BlockInfo binfo[kBlockSlots];
     __shared__ long long s_wb[G + 1];                               // first window of each product
@@ -838,10 +652,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int q = 0; q < 2; ++q) mbar_init(smem_u32(&bar_tfull[q]), 1);
         mbar_init(smem_u32(&bar_drain), 1);
         mbar_init(smem_u32(&bar_cs), kConvWarps);
-        for (int c = 0; c < kAChunks; ++c) {
-            mbar_init(smem_u32(&bar_afull[c]), kConvWarps);
-            mbar_init(smem_u32(&bar_aempty[c]), 1);
-        }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -919,8 +729,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     int nb = strided ? (int)((d + nk + TR::E - 1) / TR::E) : (int)((d + nk + 31) / 32);
                     if (!strided && wide && TR::kCornerRow0 + 128 > 32 * nb) nb = (TR::kCornerRow0 + 128) / 32;
                     const int box_bytes = strided ? mn_rows<T>(nb) * kRowBytes : 0;
-                    int per = strided ? mn_rows<T>(nb) / TR::kMnSubRows : subtiles_per_stage(nb);
-                    if (TC && !strided && !wide && per > kAGroupChunks) per = kAGroupChunks;  // one A group
+                    const int per = strided ? mn_rows<T>(nb) / TR::kMnSubRows : subtiles_per_stage(nb);
                     const long long nsub_total = (len + TR::E - 1) / TR::E;
                     const OperandMaps& maps = phase == 0 ? pr.mM : pr.mN;
                     const CUtensorMap* map = &maps.map[strided ? mn_map_index<T>(nb) : nb - 1];
@@ -970,8 +779,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t ph = 0;
             int it = 0;
             uint32_t slot_col = 0;
-            int aring = 0, grp = 0;
-            uint32_t aph = 0, gph = 0;
             bool aborted = false;
             while (true) {
                 if (!wait_fast(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
@@ -980,11 +787,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int phase = si.flags & ST_PHASE;
                 const bool first = si.flags & ST_FIRST;
                 if (first) {
-                    // slot of this Gram: the (2 it + phase)-th use of the 3-slot ring, or with A in
-                    // TMEM slot `phase`, used once per window
-                    const int u = TWO ? it : 2 * it + phase;
-                    const int q = TWO ? phase : u % 3;
-                    const uint32_t par = ((uint32_t)(TWO ? u : u / 3) & 1u) ^ 1u;
+                    // slot of this Gram: the (2 it + phase)-th use of the 3-slot ring
+                    const int u = 2 * it + phase;
+                    const int q = u % 3;
+                    const uint32_t par = ((uint32_t)(u / 3) & 1u) ^ 1u;
                     if (!wait_fast(smem_u32(&bar_slot_free[q]), par, &s_abort)) {
                         aborted = true;
                         break;
@@ -998,47 +804,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d_main = tmem + slot_col, d_corner = tmem + slot_col + kCornerCol;
                 const uint32_t addr = smem_u32(stage_ptr(stage));
                 const uint32_t sub_bytes = (uint32_t)si.sub_bytes;
-                if (TC && !mn && !wide) {
-                    // contiguous tile: A from the stage's TMEM chunk group, B from shared memory
-                    if (!wait_fast(smem_u32(&bar_afull[grp]), gph, &s_abort)) { aborted = true; break; }
-                    tc_fence_after();
-                    const uint64_t d0 = sw128_desc(addr);
-                    const uint64_t h = d0 & 0xFFFFFFFF00000000ull;
-                    const uint32_t lo0 = (uint32_t)d0, step = sub_bytes >> 4;
-                    const uint32_t idesc = (1u << 4) | (TR::kFmt << 7) | (TR::kFmt << 10) |
-                                           ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-                    for (int sb = 0; sb < si.nsub; ++sb) {
-                        const uint32_t a0 = tmem + kARingCol + (uint32_t)(grp * kAGroupChunks + sb) * kAChunkCols;
-                        const uint32_t lo = lo0 + (uint32_t)sb * step;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_tf32_ts(d_main, a0 + 8u * (uint32_t)kk, h | (uint64_t)(lo + 2u * (uint32_t)kk), idesc,
-                                           (first && sb == 0 && kk == 0) ? 0u : 1u);
-                    }
-                    tc_commit(smem_u32(&bar_aempty[grp]));
-                    if (++grp == 2) { grp = 0; gph ^= 1u; }
-                } else if (TA && !wide) {
-                    // A: the sub-tile's chunk in TMEM (K-major there); B: the tile in shared memory
-                    const uint64_t d0 = mn ? TR::mn_desc(addr, (uint32_t)si.box_bytes) : sw128_desc(addr);
-                    const uint64_t h = d0 & 0xFFFFFFFF00000000ull;
-                    const uint32_t lo0 = (uint32_t)d0, step = sub_bytes >> 4;
-                    const uint32_t kstep = mn ? TR::kMnKstep : 2u;
-                    const uint32_t idesc = (1u << 4) | (TR::kFmt << 7) | (TR::kFmt << 10) | (mn ? (1u << 16) : 0u) |
-                                           ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-                    for (int sb = 0; sb < si.nsub; ++sb) {
-                        if (!wait_fast(smem_u32(&bar_afull[aring]), aph, &s_abort)) { aborted = true; break; }
-                        tc_fence_after();
-                        const uint32_t a0 = tmem + kARingCol + (uint32_t)aring * kAChunkCols;
-                        const uint32_t lo = lo0 + (uint32_t)sb * step;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_tf32_ts(d_main, a0 + 8u * (uint32_t)kk, h | (uint64_t)(lo + (uint32_t)kk * kstep),
-                                           idesc, (first && sb == 0 && kk == 0) ? 0u : 1u);
-                        tc_commit(smem_u32(&bar_aempty[aring]));
-                        if (++aring == kAChunks) { aring = 0; aph ^= 1u; }
-                    }
-                    if (aborted) break;
-                } else if (mn) {
+                if (mn) {
                     mma_stage<T, true>(d_main, d_corner, addr, sub_bytes, (uint32_t)si.box_bytes, si.nsub,
                                        idesc_of<T>(npad, true), idesc_of<T>(16, true), first, wide);
                 } else {
@@ -1065,8 +831,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t ph = 0, bph = 0;
         int it = 0;
         int cs_uses = 0;
-        int aring = 0, grp = 0;
-        uint32_t aph = 0, gph = 0;
         const uint32_t cs_bar = smem_u32(&bar_cs);
         bool aborted = false;
         while (!aborted) {
@@ -1081,44 +845,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // ---- squares of every element, per vector
                 for (int phase = 0; phase < 2 && !aborted; ++phase) {
                     bool reduce_parts = true;
-                    bool done = false;
-                    if constexpr (TA) {
-                        if (dpos + nk <= 128) {
-                            if (!squares_ta<T>(base, info, bar_full, bar_empty, bar_afull, bar_aempty, stage, ph,
-                                               aring, aph, &s_abort, cw, lane, nk, dpos, tmem, part)) {
-                                aborted = true;
-                                break;
-                            }
-                            done = true;
-                        }
-                    }
-                    if (done) {
-                    } else if (dpos + nk <= 128) {
+                    if (dpos + nk <= 128) {
                         // every lane on whole 16-byte chunks (strided: partial sums per warp in
-                        // part[]; contiguous: x_i or y_i written directly, or with A in TMEM partial
-                        // sums as strided)
+                        // part[]; contiguous: x_i or y_i written directly)
                         if (!wait_fast(smem_u32(&bar_full[stage]), ph, &s_abort)) { aborted = true; break; }
                         const bool mn = info[stage].flags & ST_MN;
-                        bool handled = false;
-                        if constexpr (TC) {
-                            if (!mn) {
-                                if (!squares_tc<T>(base, info, bar_full, bar_empty, bar_afull, bar_aempty, stage, ph,
-                                                   grp, gph, &s_abort, cw, lane, nk, dpos, tmem, part)) {
-                                    aborted = true;
-                                    break;
-                                }
-                                handled = true;
-                            }
-                        }
-                        if (!handled) {
-                            const bool ok =
-                                mn ? squares_strided<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane, nk,
-                                                        dpos, part)
-                                   : squares_contig<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane, nk,
-                                                       dpos, xy_ff[phase]);
-                            if (!ok) { aborted = true; break; }
-                            reduce_parts = mn;
-                        }
+                        const bool ok =
+                            mn ? squares_strided<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane, nk,
+                                                    dpos, part)
+                               : squares_contig<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane, nk,
+                                                   dpos, xy_ff[phase]);
+                        if (!ok) { aborted = true; break; }
+                        reduce_parts = mn;
                     } else {
                         const int r = squares_wide<T>(base, info, bar_full, bar_empty, stage, ph, &s_abort, cw, lane,
                                                       part);
@@ -1167,7 +905,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             FF2 offp;  // main-Gram products, two columns at a time
             offp.zero();
             const int u0 = 2 * it;
-            const int q0 = TWO ? 0 : u0 % 3, q1 = TWO ? 1 : (u0 + 1) % 3;
+            const int q0 = u0 % 3, q1 = (u0 + 1) % 3;
             const int q4 = warp & 3, quarter = cw >> 2;
             const int r = 32 * q4 + lane;  // operand row
             if (wait_fast(smem_u32(&bar_tfull[it & 1]), (uint32_t)(it >> 1) & 1u, &s_abort)) {

@@ -1,0 +1,142 @@
+"""The product path as the benchmark runs it, end to end in one run, against the FP64 oracle.
+
+pipeline.run with OPL composes: the fused statistics pass (x_i, y_i, a_k, s_k, ||M^k||_F^2,
+||N_k||_F^2 and f_k = s_k + the off-diagonal trace of tensor-core Grams, F_TC), eq. 3.8
+probabilities, eq. 3.9 block sizes from that f, Philox draws, and the BF16 apply (for m p >= 2^24
+and >= 4096 draws the row-split, overlapped form).  Each stage is checked against the oracle on
+the inputs the stage actually received, so one run pins the whole composition:
+  statistics and p            1e-12 relative (FP64-accurate on both sides)
+  f_k                         within the TF32 (FP32 inputs) or exact-product (BF16 inputs) Gram
+                              bound of the off-diagonal trace
+  c_k                         bit for bit: oracle.apportion of eq. 3.9 on the GPU's a_k and f_k
+  idx, scale                  bit for bit: oracle.sample_alg2 on the GPU's p and c_k
+  CD                          within the BF16 element bound on 64 sampled rows
+The block-sampling baseline of eq. 1.2 (WU) under F_TC is checked the same way, with p_k's
+tolerance propagated from the f_k bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from tests._gpu_util import host, product_bound, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bmm():
+    import paper_2105_04940_gb300 as P
+    P.build()
+    P._abi.load()
+    assert torch.cuda.is_available()
+    return P
+
+
+def _gram_bound(M, N, off, round_in):
+    """Per block: tau_M sum_{i != j} |M|^T|M| |G_N| + tau_N |G_M| |N||N|^T + tau_M tau_N (...), with
+    tau = round_in + len 2^-23 (operand rounding, FP32 accumulation over len = m or p)."""
+    m, p = M.shape[0], N.shape[1]
+    out = np.empty(len(off) - 1)
+    for k, (a_, b_) in enumerate(zip(off[:-1], off[1:])):
+        A, B = M[:, a_:b_], N[a_:b_, :]
+        GM, GN = A.T @ A, B @ B.T
+        AM, AN = np.abs(A).T @ np.abs(A), np.abs(B) @ np.abs(B).T
+        tM, tN = round_in + m * 2.0 ** -23, round_in + p * 2.0 ** -23
+        E = tM * AM * np.abs(GN) + tN * np.abs(GM) * AN + tM * tN * AM * AN
+        np.fill_diagonal(E, 0.0)
+        out[k] = E.sum()
+    return out
+
+
+def _inputs(dtype, m, n, p, K, seed):
+    off = S.block_offsets_uneven(n, K, 16, 128, seed=seed)
+    M, N = S.scaled_gaussian(m, n, p, off, 1.5, seed=seed + 1, dtype=np.float64)
+    if dtype == "bf16":
+        Mt, Nt = to_dev(M, torch.bfloat16), to_dev(N, torch.bfloat16)
+    else:
+        Mt, Nt = to_dev(M.astype(np.float32)), to_dev(N.astype(np.float32))
+    return off, host(Mt.double()), host(Nt.double()), Mt, Nt
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_benched_opl_path_end_to_end(bmm, dtype):
+    A = bmm._abi
+    m, n, p, K = 4096, 16384, 4096, 228
+    off, M, N, Mt, Nt = _inputs(dtype, m, n, p, K, seed=301 if dtype == "f32" else 311)
+    nk = np.diff(off)
+    assert len(nk) == K and nk.min() >= 16 and nk.max() <= 128
+    L = bmm.equal_budget(K // 8, n, K)
+    assert L >= 4096 and m * p >= 1 << 24  # the overlapped, row-split apply runs
+    seed = 7
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    r = bmm.run(prob, "OPL", L, seed=seed, gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+    bmm.check_status(prob)
+    st = {k: host(v) for k, v in prob.st.items()}
+    # statistics and eq. 3.8 probabilities
+    x, y = oracle.col_row_sq_norms(M, N)
+    ost = oracle.block_stats(x, y, off)
+    assert rel_err(st["x"], x) < 1e-12 and rel_err(st["y"], y) < 1e-12
+    for k in ("a", "s", "mf", "nf"):
+        assert rel_err(st[k], ost[k]) < 1e-12, k
+    p_gpu = host(r["p"])
+    assert rel_err(p_gpu, oracle.p_col_opt(ost["w"], ost["a"], off)) < 1e-12
+    # f_k from the tensor-core Grams, within the bound of their rounding
+    f = oracle.block_frob_sq_gram(M, N, off)
+    bound = _gram_bound(M, N, off, 2.0 ** -9 if dtype == "f32" else 0.0)
+    err = np.abs(st["f"] - f)
+    assert np.all(err <= bound + 1e-12 * f), float(np.max(err / (bound + 1e-12 * f)))
+    # eq. 3.9 block sizes from the GPU's own a_k and f_k, bit for bit
+    ck = host(r["ck"])
+    want_ck = oracle.apportion(oracle.g_with_fallback(oracle.g_opt(st["a"], st["f"]), st["a"], nk), nk, L)
+    np.testing.assert_array_equal(ck, want_ck)
+    # the draws from the GPU's p and c_k, bit for bit
+    idx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+    want_idx, want_scale = oracle.sample_alg2(p_gpu, off, ck, seed, bmm.stream_id(0, A.PURPOSE_MAIN))
+    np.testing.assert_array_equal(idx, want_idx)
+    np.testing.assert_array_equal(scale, want_scale)
+    # the product on 64 sampled rows, within the BF16 element bound
+    rows = np.random.default_rng(5).choice(m, size=64, replace=False)
+    want = oracle.sampled_product_columns(M[rows], N, idx, scale)
+    got = host(r["out"]).astype(np.float64)[rows]
+    tol = 2.0 ** -7 + L * 2.0 ** -22
+    assert np.all(np.abs(got - want) <= tol * product_bound(M[rows], N, idx, scale) + 1e-300)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_wu_block_sampling_with_tensor_core_f(bmm, dtype):
+    """eq. 1.2 (WU) under F_TC: p_k = sqrt(f_k) / sum_j sqrt(f_j) with f_k from the fused pass.  If
+    |f_k - f*_k| <= e_k f*_k, then sqrt(f_k) is within e_k/2 and the normaliser within max_j e_j/2, so
+    |p_k - p*_k| <= (e_k + max_j e_j)/2 p*_k to first order (slack 1% plus 1e-12).  The draws are
+    then bit-exact given p_k, and the product within the BF16 bound."""
+    A = bmm._abi
+    m, n, p, K = 1536, 12288, 1280, 170
+    off, M, N, Mt, Nt = _inputs(dtype, m, n, p, K, seed=321 if dtype == "f32" else 331)
+    c = K // 8
+    seed = 11
+    prob = bmm.prepare(Mt, Nt, off, max_draws=c, unit=A.UNIT_BLOCK, gemm_mode=A.GEMM_BF16)
+    r = bmm.run(prob, "WU", c, seed=seed, gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+    bmm.check_status(prob)
+    f = oracle.block_frob_sq_gram(M, N, off)
+    bound = _gram_bound(M, N, off, 2.0 ** -9 if dtype == "f32" else 0.0) + 1e-12 * f
+    f_gpu = host(prob.st["f"])
+    assert np.all(np.abs(f_gpu - f) <= bound)
+    e = bound / f
+    pk = host(r["p"])
+    p_star = oracle.p_blk_prodnorm(f)
+    tol = 0.5 * (e + e.max()) * 1.01 + 1e-12
+    assert np.all(np.abs(pk - p_star) <= tol * p_star), float(np.max(np.abs(pk - p_star) / (tol * p_star)))
+    assert rel_err(pk, oracle.p_blk_prodnorm(f_gpu)) < 1e-12  # eq. 1.2 on the GPU's own f_k
+    kidx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+    want_idx, want_scale = oracle.sample_blocks(pk, c, seed, bmm.stream_id(0, A.PURPOSE_MAIN))
+    np.testing.assert_array_equal(kidx, want_idx)
+    np.testing.assert_array_equal(scale, want_scale)
+    rows = np.random.default_rng(6).choice(m, size=64, replace=False)
+    want = oracle.sampled_product_blocks(M[rows], N, off, kidx, scale)
+    got = host(r["out"]).astype(np.float64)[rows]
+    Lcols = int(sum(off[k + 1] - off[k] for k in kidx))
+    tolp = 2.0 ** -7 + Lcols * 2.0 ** -22
+    bnd = product_bound(M[rows], N, kidx, scale, offsets=off, unit="block")
+    assert np.all(np.abs(got - want) <= tolp * bnd + 1e-300)
