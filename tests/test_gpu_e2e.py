@@ -64,11 +64,11 @@ def _inputs(dtype, m, n, p, K, seed):
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_benched_opl_path_end_to_end(bmm, dtype):
     A = bmm._abi
-    m, n, p, K = 4096, 16384, 4096, 228
+    m, n, p, K = 4096, 32768, 4096, 455
     off, M, N, Mt, Nt = _inputs(dtype, m, n, p, K, seed=301 if dtype == "f32" else 311)
     nk = np.diff(off)
     assert len(nk) == K and nk.min() >= 16 and nk.max() <= 128
-    L = bmm.equal_budget(K // 8, n, K)
+    L = 4608  # outer products (about c = K/7 blocks' worth)
     assert L >= 4096 and m * p >= 1 << 24  # the overlapped, row-split apply runs
     seed = 7
     prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
