@@ -10,10 +10,12 @@
  *
  * Conventions shared by every call
  *   - Every pointer inside the descriptors and every array argument is DEVICE memory
- *     owned by the caller, unless marked "host".  The library allocates nothing and
- *     keeps no state between calls (beyond a diagnostic launch counter and the cached
- *     driver entry point of the tensor-map encoder); all work is enqueued on the caller's stream and
- *     the calls return without synchronising (except bmm_read_device_status).
+ *     owned by the caller, unless marked "host".  The library allocates nothing, creates no
+ *     stream and keeps no state between calls beyond a diagnostic launch counter, the cached
+ *     driver entry point of the tensor-map encoder, the GEMM tile table (bmm_autotune_*) and the
+ *     device address of bmm_probs_static's array; all work is enqueued on the caller's stream and
+ *     the calls return without synchronising (except bmm_read_device_status and
+ *     bmm_autotune_gemm, which times with two events it creates and destroys itself).
  *   - Argument, shape and feasibility errors are returned before anything is launched.
  *     Conditions only the GPU can see (non-finite data, bad offsets, a probability
  *     segment with zero mass, a bounded wait that expired) are recorded in a sticky
@@ -253,6 +255,28 @@ bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, in
                      const int32_t* idx, const double* scale, int64_t count, int32_t gemm_mode,
                      const bmm_mat* out, int32_t accumulate,
                      void* ws, size_t ws_bytes, bmm_stream_t stream);
+
+/* Parts of a column-sampled BF16 product for bmm_apply_part. */
+enum {
+    BMM_APPLY_GATHER_B = 0, /* gather N's drawn rows (rows row0, row1 ignored) */
+    BMM_APPLY_GATHER_A = 1, /* gather M's drawn columns for output rows [row0, row1) */
+    BMM_APPLY_GEMM = 2      /* the GEMM of output rows [row0, row1) */
+};
+
+/*
+ * bmm_apply_part -- one part of bmm_apply(M, N, B, BMM_UNIT_COLUMN, idx, scale, count, BMM_GEMM_BF16,
+ * out, accumulate, ws, ws_bytes, stream), so that the caller can overlap the memory-bound gathers with
+ * the tensor-core GEMM on streams of its own (eq. 3.3, Alg. 1 step 1(b)); the library creates no
+ * stream or event.  The operands live in ws, laid out as bmm_apply lays them out, so all parts of one
+ * product take the same ws and arguments.  The GEMM of rows [row0, row1) needs GATHER_B and the
+ * GATHER_A of those rows to be complete (same stream, or ordered by the caller's events).  Every
+ * output element is the full-depth dot product of a single bmm_apply, so any split of the rows gives
+ * the same bits.  row0 and row1: multiples of 128 (row1 may be m), 0 <= row0 <= row1 <= m;
+ * count >= 1.  Errors as bmm_apply; a bad part is BMM_ERR_ARG, a bad row range BMM_ERR_SHAPE.
+ */
+bmm_status bmm_apply_part(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, const int32_t* idx,
+                          const double* scale, int64_t count, const bmm_mat* out, int32_t accumulate, int32_t part,
+                          int64_t row0, int64_t row1, void* ws, size_t ws_bytes, bmm_stream_t stream);
 
 /*
  * bmm_apply_batched -- bmm_apply for `count` independent products of any shapes (the batched

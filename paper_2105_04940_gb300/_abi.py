@@ -23,13 +23,14 @@ REUSE_STATS = 0x100
 UNIT_COLUMN, UNIT_BLOCK = 0, 1
 GEMM_F64, GEMM_BF16, GEMM_SPLIT_BF16, GEMM_E4M3 = 0, 1, 2, 3
 PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
+APPLY_GATHER_B, APPLY_GATHER_A, APPLY_GEMM = 0, 1, 2
 
 EXPORTED = (
     "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",
     "bmm_read_device_status", "bmm_clear_device_status", "bmm_status_string", "bmm_launch_count",
     "bmm_probs_static", "bmm_apply_batched", "bmm_probs_batched",
     "bmm_autotune_workspace_size", "bmm_autotune_gemm", "bmm_autotune_get", "bmm_autotune_set", "bmm_autotune_clear",
-    "bmm_error_report", "bmm_entry_variance", "bmm_entry_estimate", "bmm_blocksizes_batched",
+    "bmm_error_report", "bmm_entry_variance", "bmm_entry_estimate", "bmm_blocksizes_batched", "bmm_apply_part",
 )
 
 # fields of the bmm_error_report output, in order (BMM_REPORT_* of include/bmm.h)
@@ -79,6 +80,8 @@ def load(path: str = LIB_PATH):
     lib.bmm_blocksizes.argtypes = [P(Mat), P(Mat), P(Blocks), P(Stats), i32, i64, vp, vp, i64, vp, vp, vp, vp, sz, vp]
     lib.bmm_sample.argtypes = [vp, i32, P(Blocks), vp, i64, u64, u64, vp, vp, vp, sz, vp]
     lib.bmm_apply.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, i32, P(Mat), i32, vp, sz, vp]
+    lib.bmm_apply_part.argtypes = [P(Mat), P(Mat), P(Blocks), vp, vp, i64, P(Mat), i32, i32, i64, i64, vp, sz, vp]
+    lib.bmm_apply_part.restype = i32
     lib.bmm_backward.argtypes = [P(Mat), P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, u64, u64, i32,
                                  P(Mat), P(Mat), i32, vp, sz, vp]
     lib.bmm_read_device_status.argtypes = [vp, vp]
@@ -226,6 +229,14 @@ def bmm_apply(M, N, B: Blocks, unit: int, idx, scale, count: int, gemm_mode: int
     _check(load().bmm_apply(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), unit, _ptr(idx),
                             _ptr(scale), count, gemm_mode, ctypes.byref(mat(out)), int(bool(accumulate)),
                             ws.data_ptr(), ws.numel(), _stream(stream)), "bmm_apply")
+
+
+def bmm_apply_part(M, N, B: Blocks, idx, scale, count: int, out, accumulate: bool, part: int, row0: int, row1: int,
+                   ws, stream=None):
+    """One part (APPLY_GATHER_B, APPLY_GATHER_A, APPLY_GEMM) of a column-sampled BF16 bmm_apply."""
+    _check(load().bmm_apply_part(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), _ptr(idx), _ptr(scale),
+                                 count, ctypes.byref(mat(out)), int(bool(accumulate)), part, row0, row1, ws.data_ptr(),
+                                 ws.numel(), _stream(stream)), "bmm_apply_part")
 
 
 def bmm_backward(G, M, N, B: Blocks, unit: int, p, ck, c: int, seed: int, stream_id: int, gemm_mode: int, dM, dN,

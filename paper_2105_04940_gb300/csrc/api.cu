@@ -1,8 +1,6 @@
 // api.cu -- the exported C ABI (include/bmm.h): argument checks, workspace carving, launch order.
 #include <string.h>
 
-#include <map>
-#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -252,17 +250,8 @@ bool valid_gemm_mode(int mode) {
 
 using namespace bmm;
 
-namespace bmm {
-namespace {
-struct SideStream;
-SideStream* side_stream();
-}  // namespace
-}  // namespace bmm
-
 BMM_API size_t bmm_workspace_size(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
                                   int64_t max_draws, int32_t gemm_mode) {
-    // the overlapped apply's side stream, created here, outside any graph capture (no error if no device)
-    if (side_stream() == nullptr) cudaGetLastError();
     if (check_problem(M, N, B) != BMM_OK || max_draws < 0 || !valid_gemm_mode(gemm_mode)) return 0;
     if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return 0;
     size_t need = 0;
@@ -653,112 +642,59 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
 }  // namespace
 }  // namespace bmm
 
-namespace bmm {
-namespace {
-// ---- overlapped apply: the product's rows are split in two; the GEMM of row half h runs on a
-// highest-priority side stream while the gathers of half h + 1 run on the caller's stream (the
-// strided gather of M is memory-bound, the GEMM tensor-bound; the priority makes the block
-// scheduler place the GEMM's persistent CTAs ahead of the remaining gather CTAs, so the two share
-// the SMs).  Each output element is the same full-depth dot product as in one launch, so the result
-// is bit-identical.  Ordering is by events only; the side stream forks from and joins back into the
-// caller's stream inside the call, so the call stays stream-ordered and can be captured in a graph.
-constexpr int kApplyChunks = 2;
-constexpr int64_t kChunkMinDraws = 4096;             // and m >= 256, m p >= 2^24: large products only
-struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr;
-    cudaEvent_t join = nullptr;
-    cudaEvent_t done[kApplyChunks] = {};
-};
-// One side stream and its events per device, created on first use (before any graph capture
-// that uses them) and kept until exit; nullptr when they cannot be created.
-SideStream* side_stream() {
-    static std::mutex mu;
-    static std::map<int, SideStream*> per_dev;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lock(mu);
-    const auto it = per_dev.find(dev);
-    if (it != per_dev.end()) return it->second;
-    SideStream* ss = new SideStream;
-    int least = 0, greatest = 0;
-    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
-              cudaStreamCreateWithPriority(&ss->s, cudaStreamNonBlocking, greatest) == cudaSuccess &&
-              cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming) == cudaSuccess;
-    for (int c = 0; c < kApplyChunks && ok; ++c)
-        ok = cudaEventCreateWithFlags(&ss->done[c], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
-        cudaGetLastError();  // the failure is not the caller's error
-        per_dev[dev] = nullptr;
-        return nullptr;
-    }
-    per_dev[dev] = ss;
-    return ss;
-}
-
-// Runs the deferred gathers (jobs[0]: columns of M into A, jobs[1]: rows of N into B) and the GEMM
-// of a column-sampled BF16 product in kApplyChunks row ranges of M (multiples of 128 rows).
-bmm_status apply_overlapped(const std::vector<GatherJob>& jobs, const GemmArgs& g, DevStatus* st, SideStream* ss,
-                            cudaStream_t cs) {
-    // the events are shared by every caller on this device: a record and the waits on it are
-    // enqueued under one lock, so no other caller's record can come in between
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
-    const GatherJob& jM = jobs[0];
-    const int64_t rows = g.M, half = round_up(ceil_div(rows, kApplyChunks), 128);
-    const size_t esM = jM.v.dtype == BMM_F64 ? 8 : (jM.v.dtype == BMM_F32 ? 4 : 2);
-    BMM_TRY(cudaEventRecord(ss->fork, cs));
-    BMM_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
-    BMM_TRY(launch_gather_grouped(&jobs[1], 1, cs));  // all of B first
-    int nchunks = 0;
-    for (int c = 0; c < kApplyChunks; ++c) {  // rows [lo, hi) of A, in order, on the caller's stream
-        const int64_t lo = c * half, hi = imin(rows, lo + half);
-        if (hi <= lo) break;
-        GatherJob part = jM;
-        // element r of a column of M: at data[r * ld + i] (strided) or data[i * ld + r] (contiguous)
-        part.v.data = static_cast<const char*>(jM.v.data) + (jM.v.mode == VEC_STRIDED ? lo * jM.v.ld : lo) * esM;
-        part.v.len = hi - lo;
-        part.out = static_cast<__nv_bfloat16*>(jM.out) + lo * jM.ldo;
-        BMM_TRY(launch_gather_grouped(&part, 1, cs));
-        BMM_TRY(cudaEventRecord(ss->done[c], cs));
-        ++nchunks;
-    }
-    for (int c = 0; c < nchunks; ++c) {  // GEMMs of the row ranges, each after its gathers
-        const int64_t lo = c * half, hi = imin(rows, lo + half);
-        BMM_TRY(cudaStreamWaitEvent(ss->s, ss->done[c], 0));
-        BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(g.A) + lo * g.lda, g.lda, g.B, g.ldb, hi - lo,
-                                    g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out + lo * g.ldo, g.ldo, g.accumulate,
-                                    st, ss->s, GEMM_ELEM_BF16, nullptr, g.kdim));
-    }
-    BMM_TRY(cudaEventRecord(ss->join, ss->s));
-    BMM_TRY(cudaStreamWaitEvent(cs, ss->join, 0));
-    return BMM_OK;
-}
-}  // namespace
-}  // namespace bmm
-
 BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit,
                              const int32_t* idx, const double* scale, int64_t count, int32_t gemm_mode,
                              const bmm_mat* out, int32_t accumulate, void* ws, size_t ws_bytes, bmm_stream_t stream) {
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     GemmArgs g;
     bool done = true;
-    if (gemm_mode == BMM_GEMM_BF16 && unit == BMM_UNIT_COLUMN && count >= kChunkMinDraws && M && N &&
-        M->rows >= 256 && M->rows * N->cols >= (int64_t(1) << 24)) {
-        SideStream* ss = side_stream();
-        if (ss != nullptr) {
-            std::vector<GatherJob> jobs;
-            bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs,
-                                         &g, &done, &jobs);
-            if (s != BMM_OK || done) return s;
-            return apply_overlapped(jobs, g, status_of(ws), ss, cs);
-        }
-    }
     bmm_status s = apply_prepare(M, N, B, unit, idx, scale, count, gemm_mode, out, accumulate, ws, ws_bytes, cs, &g, &done);
     if (s != BMM_OK || done) return s;
     BMM_TRY(launch_gemm_bf16_tc(g.A, g.lda, g.B, g.ldb, g.M, g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out, g.ldo,
                                 g.accumulate, status_of(ws), cs, g.elem, g.scale));
+    return BMM_OK;
+}
+
+// One part of a column-sampled BF16 bmm_apply, so that a caller can overlap the parts on streams of
+// its own: the gather of N's drawn rows (operand B), the gather of M's drawn columns for a range of
+// output rows (operand A), and the GEMM of a range of output rows.  The operands live in the
+// workspace, as bmm_apply lays them out; every output element is the full-depth dot product of a
+// single bmm_apply, so any split gives the same bits.
+BMM_API bmm_status bmm_apply_part(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, const int32_t* idx,
+                                  const double* scale, int64_t count, const bmm_mat* out, int32_t accumulate,
+                                  int32_t part, int64_t row0, int64_t row1, void* ws, size_t ws_bytes,
+                                  bmm_stream_t stream) {
+    if (part != BMM_APPLY_GATHER_B && part != BMM_APPLY_GATHER_A && part != BMM_APPLY_GEMM) return BMM_ERR_ARG;
+    if (count < 1 || M == nullptr || N == nullptr || M->rows < 1 || N->cols < 1) return BMM_ERR_ARG;
+    if (part != BMM_APPLY_GATHER_B &&
+        (row0 < 0 || row1 < row0 || row1 > M->rows || row0 % 128 || (row1 % 128 && row1 != M->rows)))
+        return BMM_ERR_SHAPE;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    GemmArgs g;
+    bool done = true;
+    std::vector<GatherJob> jobs;
+    bmm_status s = apply_prepare(M, N, B, BMM_UNIT_COLUMN, idx, scale, count, BMM_GEMM_BF16, out, accumulate, ws,
+                                 ws_bytes, cs, &g, &done, &jobs);
+    if (s != BMM_OK || done) return s;
+    if (part == BMM_APPLY_GATHER_B) {
+        BMM_TRY(launch_gather_grouped(&jobs[1], 1, cs));
+        return BMM_OK;
+    }
+    if (row1 == row0) return BMM_OK;
+    if (part == BMM_APPLY_GATHER_A) {
+        const GatherJob& jM = jobs[0];
+        GatherJob sub = jM;
+        // element r of a column of M: at data[r * ld + i] (strided) or data[i * ld + r] (contiguous)
+        sub.v.data = static_cast<const char*>(jM.v.data) + (jM.v.mode == VEC_STRIDED ? row0 * jM.v.ld : row0) *
+                                                             (int64_t)esize(jM.v.dtype);
+        sub.v.len = row1 - row0;
+        sub.out = static_cast<__nv_bfloat16*>(jM.out) + row0 * jM.ldo;
+        BMM_TRY(launch_gather_grouped(&sub, 1, cs));
+        return BMM_OK;
+    }
+    BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(g.A) + row0 * g.lda, g.lda, g.B, g.ldb, row1 - row0,
+                                g.N, g.kdim, g.k_host, g.k_dev, g.k_mult, g.out + row0 * g.ldo, g.ldo, g.accumulate,
+                                status_of(ws), cs, GEMM_ELEM_BF16, nullptr, g.kdim));
     return BMM_OK;
 }
 

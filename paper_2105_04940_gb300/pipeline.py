@@ -121,6 +121,57 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
     return Problem(M, N, off, off_dev, B, ws, st)
 
 
+_SIDE: dict = {}
+
+
+def _side_stream(dev):
+    """A high-priority stream per device for the GEMM halves of the overlapped apply (created once,
+    outside any graph capture that uses it)."""
+    torch = _torch()
+    s = _SIDE.get(str(dev))
+    if s is None:
+        s = _SIDE[str(dev)] = torch.cuda.Stream(device=dev, priority=-1)
+    return s
+
+
+def overlapped_apply_wanted(M, N, count: int, gemm_mode: int, unit: int) -> bool:
+    """Large column-sampled BF16 products (>= 4096 draws, m >= 256, m p >= 2^24) gain from overlapping
+    the gather of M's columns (memory-bound) with the GEMM (tensor-bound)."""
+    m, p = int(M.shape[0]), int(N.shape[1])
+    return gemm_mode == A.GEMM_BF16 and unit == A.UNIT_COLUMN and count >= 4096 and m >= 256 and m * p >= 1 << 24
+
+
+def apply_columns(prob: Problem, idx, scale, count: int, gemm_mode: int, out, accumulate: bool = False):
+    """CD of Alg. 2's draws (bmm_apply).  For large BF16 products the output rows are split in two:
+    N's rows and the first half's columns of M are gathered on the current stream, the first half's
+    GEMM runs on a high-priority side stream while the second half's columns are gathered, then the
+    second half's GEMM -- all through bmm_apply_part, ordered by events (a fork and a join of the
+    current stream, so the sequence can be captured in a graph).  The result is bit-identical to one
+    bmm_apply: every output element is the same full-depth dot product."""
+    torch = _torch()
+    M, N, B, ws = prob.M, prob.N, prob.B, prob.ws
+    if not overlapped_apply_wanted(M, N, count, gemm_mode, A.UNIT_COLUMN):
+        A.bmm_apply(M, N, B, A.UNIT_COLUMN, idx, scale, count, gemm_mode, out, accumulate, ws)
+        return out
+    main = torch.cuda.current_stream(M.device)
+    side = _side_stream(M.device)
+    m = int(M.shape[0])
+    half = min(m, ((m + 1) // 2 + 127) // 128 * 128)
+    side.wait_stream(main)
+    A.bmm_apply_part(M, N, B, idx, scale, count, out, accumulate, A.APPLY_GATHER_B, 0, 0, ws, main)
+    done = []
+    for lo, hi in ((0, half), (half, m)):
+        A.bmm_apply_part(M, N, B, idx, scale, count, out, accumulate, A.APPLY_GATHER_A, lo, hi, ws, main)
+        ev = torch.cuda.Event()
+        ev.record(main)
+        done.append((lo, hi, ev))
+    for lo, hi, ev in done:
+        side.wait_event(ev)
+        A.bmm_apply_part(M, N, B, idx, scale, count, out, accumulate, A.APPLY_GEMM, lo, hi, ws, side)
+    main.wait_stream(side)
+    return out
+
+
 def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: int | None = None,
         gemm_mode: int = A.GEMM_BF16, out=None, compute_product: bool = True, events: list | None = None,
         fmode: int = A.F_TC, fused_stats: bool = True, p_ready=None, sizes_ready=None) -> dict:
@@ -234,7 +285,7 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
     A.bmm_sample(p, A.UNIT_COLUMN, B, ck, c, seed, sid, idx, scale, ws)
     mark("sample")
     if compute_product:
-        A.bmm_apply(M, N, B, A.UNIT_COLUMN, idx, scale, c, gemm_mode, out, False, ws)
+        apply_columns(prob, idx, scale, c, gemm_mode, out)
         mark("apply")
     res.update(p=p, ck=ck, g=g, idx=idx, scale=scale, unit=A.UNIT_COLUMN, out=out)
     return res

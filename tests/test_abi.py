@@ -201,3 +201,26 @@ def test_static_entry_point_checks_arguments_like_bmm_probs(lib):
     for bad in (None, ctypes.c_void_p(fake + 2)):
         assert lib.bmm_probs_static(by(Mg), by(Ng), by(Bg), _abi.P_COL_OPT, None, by(good_st), bad,
                                     None) == _abi.ERR_ARG
+
+
+def test_apply_part_refuses_bad_parts_and_row_ranges(lib):
+    """bmm_apply_part checks its part and row range on the host, before anything is launched (the
+    fake pointers below are never dereferenced)."""
+    from paper_2105_04940_gb300 import _abi
+    fake = 1 << 20
+    M = _abi.Mat(fake, 512, 4096, 4096, _abi.F32, _abi.ROW_MAJOR)
+    N = _abi.Mat(fake, 4096, 256, 256, _abi.F32, _abi.ROW_MAJOR)
+    out = _abi.Mat(fake, 512, 256, 256, _abi.F32, _abi.ROW_MAJOR)
+    B = _abi.Blocks(64, 4096, 64, fake)
+    by = ctypes.byref
+    call = lambda part, r0, r1, count=100: lib.bmm_apply_part(by(M), by(N), by(B), fake, fake, count, by(out), 0, part,
+                                                             r0, r1, None, 0, None)
+    assert call(3, 0, 128) == _abi.ERR_ARG
+    assert call(-1, 0, 128) == _abi.ERR_ARG
+    assert call(_abi.APPLY_GEMM, 0, 128, count=0) == _abi.ERR_ARG
+    assert call(_abi.APPLY_GATHER_A, 64, 128) == _abi.ERR_SHAPE   # row0 not a multiple of 128
+    assert call(_abi.APPLY_GEMM, 0, 100) == _abi.ERR_SHAPE        # row1 neither a multiple of 128 nor m
+    assert call(_abi.APPLY_GEMM, 256, 128) == _abi.ERR_SHAPE      # row1 < row0
+    assert call(_abi.APPLY_GEMM, 0, 640) == _abi.ERR_SHAPE        # row1 > m
+    # a well-formed request passes these checks and stops at the device (none here) or workspace check
+    assert call(_abi.APPLY_GEMM, 0, 512) in (_abi.ERR_UNSUPPORTED, _abi.ERR_WORKSPACE)

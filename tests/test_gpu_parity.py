@@ -787,6 +787,43 @@ def test_overlapped_apply_large_product(bmm, layout):
     np.testing.assert_allclose(host(out2)[rows], 2 * got[rows], rtol=2e-6, atol=1e-6 * np.abs(got).max())
 
 
+@pytest.mark.parametrize("layout", ["row", "col"])
+def test_apply_parts_equal_one_apply(bmm, layout):
+    """bmm_apply_part's three parts, in any row split (multiples of 128, the last ending at m) and on
+    one or two streams, give bmm_apply's product bit for bit, with and without accumulate."""
+    m, n, p, K, L = 700, 3000, 300, 40, 900
+    off, M, N, Mt, Nt = _problem(m, n, p, K, seed=81, dtype=np.float32, lo=40, hi=110)
+    Mt = as_layout(Mt, layout)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=bmm._abi.GEMM_BF16)
+    r = bmm.run(prob, "ONC", L, seed=4, gemm_mode=bmm._abi.GEMM_BF16, compute_product=False)
+    A = bmm._abi
+    want = torch.empty(m, p, dtype=torch.float32, device=Mt.device)
+    A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, A.GEMM_BF16, want, False, prob.ws)
+    for split in ([0, m], [0, 128, m], [0, 384, 512, m]):
+        got = torch.full((m, p), float("nan"), dtype=torch.float32, device=Mt.device)
+        A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GATHER_B, 0, 0, prob.ws)
+        for lo, hi in zip(split[:-1], split[1:]):
+            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GATHER_A, lo, hi, prob.ws)
+        for lo, hi in zip(split[:-1], split[1:]):
+            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GEMM, lo, hi, prob.ws)
+        bmm.check_status(prob)
+        np.testing.assert_array_equal(host(got), host(want), err_msg=str(split))
+    # accumulate: out += CD, rows split across a second stream
+    acc = want.clone()
+    side = torch.cuda.Stream()
+    A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, acc, True, A.APPLY_GATHER_B, 0, 0, prob.ws)
+    A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, acc, True, A.APPLY_GATHER_A, 0, m, prob.ws)
+    side.wait_stream(torch.cuda.current_stream())
+    A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, acc, True, A.APPLY_GEMM, 0, 256, prob.ws, side)
+    A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, acc, True, A.APPLY_GEMM, 256, m, prob.ws)
+    torch.cuda.current_stream().wait_stream(side)
+    bmm.check_status(prob)
+    twice = torch.empty_like(want)
+    A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, A.GEMM_BF16, twice, False, prob.ws)
+    A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, A.GEMM_BF16, twice, True, prob.ws)
+    np.testing.assert_array_equal(host(acc), host(twice))
+
+
 @pytest.mark.parametrize("dtype", [np.float32, "bf16"])
 @pytest.mark.parametrize("mode", ["bf16", "split_bf16"])
 @pytest.mark.parametrize("layout", ["row", "col"])
