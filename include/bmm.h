@@ -388,6 +388,26 @@ bmm_status bmm_entry_estimate(const bmm_mat* M, const bmm_mat* N, const bmm_bloc
                               const int64_t* entries, int64_t count, double* cd_out, double* s2_out, void* ws,
                               size_t ws_bytes, bmm_stream_t stream);
 
+/*
+ * bmm_f_tc_supported -- whether bmm_probs with BMM_F_TC computes ||M^k N_k||_F^2 of this problem on the
+ * tensor cores (*uses_tc = 1: FP32 or BF16 data, 16-byte aligned base pointers and leading dimensions,
+ * blocks of at most 128, an sm_103 device) or falls back to BMM_F_EXACT (*uses_tc = 0).  Host only,
+ * no launch.  No counterpart in the paper (the path is this library's choice, eq. 1.2 / eq. 3.9 only
+ * fix the value).  Errors: as the descriptor checks of bmm_probs; uses_tc NULL is BMM_ERR_ARG.
+ */
+bmm_status bmm_f_tc_supported(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t* uses_tc);
+
+/*
+ * bmm_wait_selftest -- diagnostic, no counterpart in the paper.  Every pipelined kernel of the library
+ * waits on barriers with a bound: past it the kernel gives up, records BMM_ERR_TIMEOUT in the status
+ * word and returns, instead of hanging.  This call exercises that path on purpose: one CTA waits, with
+ * the library's wait routine, on barriers that nothing completes (nothing else is in flight), gives up
+ * after the bound (2 s) and records BMM_ERR_TIMEOUT with detail = the number of waits that gave up (2:
+ * one on the time bound, one through the CTA's abort flag).  ws: 256-byte aligned, >= 256 bytes, its
+ * status block zeroed by the caller; read it with bmm_read_device_status.
+ */
+bmm_status bmm_wait_selftest(void* ws, size_t ws_bytes, bmm_stream_t stream);
+
 /* Synchronises the stream, then returns the first device-recorded error (BMM_OK if none). */
 bmm_status bmm_read_device_status(const void* ws, bmm_stream_t stream);
 /* Enqueues a reset of the device status word. */

@@ -31,6 +31,7 @@ EXPORTED = (
     "bmm_probs_static", "bmm_apply_batched", "bmm_probs_batched",
     "bmm_autotune_workspace_size", "bmm_autotune_gemm", "bmm_autotune_get", "bmm_autotune_set", "bmm_autotune_clear",
     "bmm_error_report", "bmm_entry_variance", "bmm_entry_estimate", "bmm_blocksizes_batched", "bmm_apply_part",
+    "bmm_f_tc_supported", "bmm_wait_selftest",
 )
 
 # fields of the bmm_error_report output, in order (BMM_REPORT_* of include/bmm.h)
@@ -82,6 +83,10 @@ def load(path: str = LIB_PATH):
     lib.bmm_apply.argtypes = [P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, i32, P(Mat), i32, vp, sz, vp]
     lib.bmm_apply_part.argtypes = [P(Mat), P(Mat), P(Blocks), vp, vp, i64, P(Mat), i32, i32, i64, i64, vp, sz, vp]
     lib.bmm_apply_part.restype = i32
+    lib.bmm_f_tc_supported.argtypes = [P(Mat), P(Mat), P(Blocks), P(i32)]
+    lib.bmm_f_tc_supported.restype = i32
+    lib.bmm_wait_selftest.argtypes = [vp, sz, vp]
+    lib.bmm_wait_selftest.restype = i32
     lib.bmm_backward.argtypes = [P(Mat), P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, u64, u64, i32,
                                  P(Mat), P(Mat), i32, vp, sz, vp]
     lib.bmm_read_device_status.argtypes = [vp, vp]
@@ -283,6 +288,19 @@ def bmm_entry_estimate(M, N, B: Blocks, unit: int, ck, idx, scale, draws: int, e
     _check(load().bmm_entry_estimate(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), unit, _ptr(ck),
                                      _ptr(idx), _ptr(scale), draws, _ptr(entries), count, _ptr(cd_out), _ptr(s2_out),
                                      ws.data_ptr(), ws.numel(), _stream(stream)), "bmm_entry_estimate")
+
+
+def bmm_f_tc_supported(M, N, B: Blocks) -> bool:
+    """Whether bmm_probs with F_TC computes f_k of this problem on the tensor cores (else exactly)."""
+    r = ctypes.c_int32(-1)
+    _check(load().bmm_f_tc_supported(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), ctypes.byref(r)),
+           "bmm_f_tc_supported")
+    return r.value == 1
+
+
+def bmm_wait_selftest(ws, stream=None):
+    """Launch the bounded-wait self-test (gives up after the library's wait bound, about 2 s)."""
+    _check(load().bmm_wait_selftest(ws.data_ptr(), ws.numel(), _stream(stream)), "bmm_wait_selftest")
 
 
 def bmm_read_device_status(ws, stream=None) -> int:

@@ -224,3 +224,22 @@ def test_apply_part_refuses_bad_parts_and_row_ranges(lib):
     assert call(_abi.APPLY_GEMM, 0, 640) == _abi.ERR_SHAPE        # row1 > m
     # a well-formed request passes these checks and stops at the device (none here) or workspace check
     assert call(_abi.APPLY_GEMM, 0, 512) in (_abi.ERR_UNSUPPORTED, _abi.ERR_WORKSPACE)
+
+
+def test_f_tc_query_on_the_host(lib):
+    """bmm_f_tc_supported answers from the descriptors alone (no launch): without an sm_103 device it
+    reports the exact fallback; bad descriptors get bmm_probs's codes; a null answer pointer is refused."""
+    from paper_2105_04940_gb300 import _abi
+    import torch
+    fake = 1 << 20
+    M = _abi.Mat(fake, 256, 4096, 4096, _abi.F32, _abi.ROW_MAJOR)
+    N = _abi.Mat(fake, 4096, 256, 256, _abi.F32, _abi.ROW_MAJOR)
+    B = _abi.Blocks(64, 4096, 64, fake)
+    r = ctypes.c_int32(-1)
+    by = ctypes.byref
+    assert lib.bmm_f_tc_supported(by(M), by(N), by(B), by(r)) == _abi.OK
+    if not torch.cuda.is_available():
+        assert r.value == 0
+    bad = _abi.Mat(fake, 256, 4000, 4096, _abi.F32, _abi.ROW_MAJOR)
+    assert lib.bmm_f_tc_supported(by(bad), by(N), by(B), by(r)) == _abi.ERR_SHAPE
+    assert lib.bmm_f_tc_supported(by(M), by(N), by(B), None) == _abi.ERR_ARG

@@ -131,6 +131,7 @@ def test_fused_statistics_and_tensor_core_f(bmm, layouts, p, dtype):
     align = 4 if dtype is np.float32 else 8
     fused = ld_m % align == 0 and ld_n % align == 0
     assert (bmm._abi.bmm_launch_count() - launches == 3) == fused
+    assert bmm._abi.bmm_f_tc_supported(Mt, Nt, prob.B) == fused  # the query names the path that ran
     x, y = oracle.col_row_sq_norms(M, N)
     st = oracle.block_stats(x, y, off)
     assert rel_err(host(prob.st["x"]), x) < 1e-12
@@ -1032,3 +1033,26 @@ def test_blocksizes_degenerate_weights(bmm, case):
         bmm.bmm_blocksizes(None, None, B, st, bmm._abi.CK_OPT, c, None, None, 0, ck, g, None, ws)
         assert bmm.bmm_read_device_status(ws) == 0
         np.testing.assert_array_equal(host(ck), oracle.apportion(gw, nk, c), err_msg=f"c={c}")
+
+
+def test_bounded_wait_gives_up_and_reports(bmm):
+    """The bounded-wait path of the pipelined kernels, reached on purpose (bmm_wait_selftest): a wait on
+    a barrier nothing completes gives up after the bound, a second wait gives up through the abort
+    flag, the status word says BMM_ERR_TIMEOUT with both counted, and the context stays usable."""
+    import ctypes
+    import time
+    A = bmm._abi
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda:0")
+    t0 = time.perf_counter()
+    A.bmm_wait_selftest(ws)
+    assert A.bmm_read_device_status(ws) == A.ERR_TIMEOUT
+    elapsed = time.perf_counter() - t0
+    assert 1.0 < elapsed < 30.0, elapsed
+    detail = ctypes.c_int32.from_buffer_copy(bytes(ws[4:8].cpu().numpy())).value
+    assert detail == 2
+    # the device still answers: a small product runs and its status is clean
+    off, M, N, Mt, Nt = _problem(64, 256, 64, 4, seed=13, dtype=np.float64)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=16)
+    r = bmm.run(prob, "ONC", 16, seed=1, gemm_mode=A.GEMM_F64)
+    bmm.check_status(prob)
+    assert np.isfinite(host(r["out"])).all()
