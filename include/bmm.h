@@ -244,6 +244,20 @@ bmm_status bmm_sample(const double* p, int32_t unit, const bmm_blocks* B, const 
                       void* ws, size_t ws_bytes, bmm_stream_t stream);
 
 /*
+ * bmm_sample_batched -- bmm_sample for `count` independent products (host arrays of length count:
+ * p[i], Bs[i], ck[i] (column unit), cs[i] draws, seeds[i], stream_ids[i], idx_out[i], scale_out[i],
+ * ws[i] / ws_bytes[i]) in three launches per up to 200 products.  For each i the draws are those of
+ * bmm_sample(p[i], unit, &Bs[i], ck[i], cs[i], seeds[i], stream_ids[i], idx_out[i], scale_out[i], ws[i],
+ * ws_bytes[i], stream), bit for bit (the same exact integer prefix sums).  Every product is checked on
+ * the host before anything is launched; device-detected errors go to each product's status block.
+ * Nothing is synchronised or allocated (graph-capturable).
+ */
+bmm_status bmm_sample_batched(int64_t count, const double* const* p, int32_t unit, const bmm_blocks* Bs,
+                              const int64_t* const* ck, const int64_t* cs, const uint64_t* seeds,
+                              const uint64_t* stream_ids, int32_t* const* idx_out, double* const* scale_out,
+                              void* const* ws, const size_t* ws_bytes, bmm_stream_t stream);
+
+/*
  * bmm_apply -- the sampled product CD = sum_t scale_t M^{(i_t)} N_{(i_t)} (eq. 3.3,
  * Alg. 2 step 4), or sum_t scale_t M^{k_t} N_{k_t} for BMM_UNIT_BLOCK.
  * The chosen columns/rows are gathered, multiplied by sqrt(scale_t) (Alg. 1 step 1(b)),

@@ -31,7 +31,7 @@ EXPORTED = (
     "bmm_probs_static", "bmm_apply_batched", "bmm_probs_batched",
     "bmm_autotune_workspace_size", "bmm_autotune_gemm", "bmm_autotune_get", "bmm_autotune_set", "bmm_autotune_clear",
     "bmm_error_report", "bmm_entry_variance", "bmm_entry_estimate", "bmm_blocksizes_batched", "bmm_apply_part",
-    "bmm_f_tc_supported", "bmm_wait_selftest",
+    "bmm_f_tc_supported", "bmm_wait_selftest", "bmm_sample_batched",
 )
 
 # fields of the bmm_error_report output, in order (BMM_REPORT_* of include/bmm.h)
@@ -87,6 +87,9 @@ def load(path: str = LIB_PATH):
     lib.bmm_f_tc_supported.restype = i32
     lib.bmm_wait_selftest.argtypes = [vp, sz, vp]
     lib.bmm_wait_selftest.restype = i32
+    lib.bmm_sample_batched.argtypes = [i64, P(vp), i32, P(Blocks), P(vp), P(i64), P(u64), P(u64), P(vp), P(vp), P(vp),
+                                       P(sz), vp]
+    lib.bmm_sample_batched.restype = i32
     lib.bmm_backward.argtypes = [P(Mat), P(Mat), P(Mat), P(Blocks), i32, vp, vp, i64, u64, u64, i32,
                                  P(Mat), P(Mat), i32, vp, sz, vp]
     lib.bmm_read_device_status.argtypes = [vp, vp]
@@ -227,6 +230,18 @@ def bmm_sample(p, unit: int, B: Blocks, ck, c: int, seed: int, stream_id: int, i
     _check(load().bmm_sample(_ptr(p), unit, ctypes.byref(B), _ptr(ck), c, seed & 0xFFFFFFFFFFFFFFFF,
                              stream_id & 0xFFFFFFFFFFFFFFFF, _ptr(idx_out), _ptr(scale_out), ws.data_ptr(),
                              ws.numel(), _stream(stream)), "bmm_sample")
+
+
+def bmm_sample_batched(ps, unit: int, Bs, cks, cs, seeds, stream_ids, idx_outs, scale_outs, wss, stream=None):
+    """bmm_sample over many independent products (lists of equal length; cks None for the block unit)."""
+    n = len(ps)
+    VpA, I64A, U64A = ctypes.c_void_p * n, ctypes.c_int64 * n, ctypes.c_uint64 * n
+    ckp = VpA(*[_ptr(c) for c in cks]) if cks is not None else None
+    _check(load().bmm_sample_batched(
+        n, VpA(*[_ptr(x) for x in ps]), unit, (Blocks * n)(*Bs), ckp, I64A(*[int(c) for c in cs]),
+        U64A(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in seeds]), U64A(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in stream_ids]),
+        VpA(*[_ptr(x) for x in idx_outs]), VpA(*[_ptr(x) for x in scale_outs]), VpA(*[w.data_ptr() for w in wss]),
+        (ctypes.c_size_t * n)(*[w.numel() for w in wss]), _stream(stream)), "bmm_sample_batched")
 
 
 def bmm_apply(M, N, B: Blocks, unit: int, idx, scale, count: int, gemm_mode: int, out, accumulate: bool, ws,

@@ -560,6 +560,36 @@ BMM_API bmm_status bmm_sample(const double* p, int32_t unit, const bmm_blocks* B
     return BMM_OK;
 }
 
+BMM_API bmm_status bmm_sample_batched(int64_t count, const double* const* p, int32_t unit, const bmm_blocks* Bs,
+                                      const int64_t* const* ck, const int64_t* cs, const uint64_t* seeds,
+                                      const uint64_t* stream_ids, int32_t* const* idx_out, double* const* scale_out,
+                                      void* const* ws, const size_t* ws_bytes, bmm_stream_t stream) {
+    if (count < 0) return BMM_ERR_ARG;
+    if (count == 0) return BMM_OK;
+    if (!p || !Bs || !cs || !seeds || !stream_ids || !idx_out || !scale_out || !ws || !ws_bytes) return BMM_ERR_ARG;
+    if (unit != BMM_UNIT_COLUMN && unit != BMM_UNIT_BLOCK) return BMM_ERR_ARG;
+    if (unit == BMM_UNIT_COLUMN && ck == nullptr) return BMM_ERR_ARG;
+    std::vector<SampleArgs> jobs;
+    jobs.reserve((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {  // every product checked as bmm_sample checks it, before any launch
+        const bmm_blocks* B = &Bs[i];
+        bmm_status s = check_blocks(B);
+        if (s != BMM_OK) return s;
+        if (p[i] == nullptr || idx_out[i] == nullptr || scale_out[i] == nullptr || cs[i] < 0) return BMM_ERR_ARG;
+        if (unit == BMM_UNIT_COLUMN && ck[i] == nullptr) return BMM_ERR_ARG;
+        if (cs[i] > 0x7fffffffLL) return BMM_ERR_UNSUPPORTED;
+        Carver cnt{nullptr};
+        plan_sample(cnt, unit, B);
+        if ((s = check_ws(ws[i], ws_bytes[i], cnt.off)) != BMM_OK) return s;
+        Carver cv{static_cast<char*>(ws[i]) + kStatusBytes};
+        void* scr = plan_sample(cv, unit, B);
+        jobs.push_back(SampleArgs{p[i], unit, B->offsets, B->K, B->n, unit == BMM_UNIT_COLUMN ? ck[i] : nullptr, cs[i],
+                                  seeds[i], stream_ids[i], idx_out[i], scale_out[i], scr, status_of(ws[i])});
+    }
+    BMM_TRY(launch_sample_grouped(jobs.data(), (int64_t)jobs.size(), reinterpret_cast<cudaStream_t>(stream)));
+    return BMM_OK;
+}
+
 namespace bmm {
 namespace {
 // Checks and gathers of one product of bmm_apply / bmm_apply_batched.  On BMM_OK either *done

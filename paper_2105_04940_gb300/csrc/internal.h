@@ -143,6 +143,22 @@ cudaError_t launch_blocksizes_grouped(const SizesJob* jobs, int64_t count, cudaS
 
 // ---- sampler.cu
 int64_t sampler_scratch_bytes(int64_t len, int64_t K);
+// One product of a grouped sampler launch: the arguments of launch_sample.
+struct SampleArgs {
+    const double* p;
+    int unit;
+    const int64_t* off;
+    int64_t K, n;
+    const int64_t* ck;
+    int64_t c;
+    uint64_t seed, sid;
+    int32_t* idx;
+    double* scale;
+    void* scratch;
+    DevStatus* st;
+};
+// Many products' draws in three launches per up to 200 products, identical to launch_sample's.
+cudaError_t launch_sample_grouped(const SampleArgs* args, int64_t count, cudaStream_t s);
 cudaError_t launch_sample(const double* p, int unit, const int64_t* off, int64_t K, int64_t n, const int64_t* ck,
                           int64_t c, uint64_t seed, uint64_t sid, int32_t* idx, double* scale,
                           void* scratch, DevStatus* st, cudaStream_t s);

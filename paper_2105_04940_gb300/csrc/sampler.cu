@@ -152,6 +152,190 @@ __global__ void draw_kernel(const double* __restrict__ p, int unit, const int64_
     scale[t] = __ddiv_rn(1.0, __dmul_rn((double)cnt, p[lo]));
 }
 
+// ---- many products per launch (bmm_sample_batched): the same integers, hence the same draws, as
+// one launch sequence per product.  Three launches for up to kMaxSampleJobs products: the weights
+// and per-tile scans of every product's tiles, one CTA per product for its tile prefix and draw
+// offsets, and one thread per draw (the tile prefix added inside the binary search).
+namespace {
+
+struct SampleJob {
+    const double* p;
+    const int64_t* off;
+    const int64_t* ck;
+    int32_t* idx;
+    double* scale;
+    unsigned long long* G;    // [len] tile-local inclusive prefix of W
+    unsigned long long* tot;  // [ntiles] tile totals, then their exclusive prefix
+    int64_t* D;               // [K + 1] draw offsets (column unit)
+    DevStatus* st;
+    long long K, len, c;
+    unsigned long long seed, sid;
+    int unit;
+    int tiles_before;   // tiles of the launch's earlier jobs
+    int blocks_before;  // 128-draw blocks of the launch's earlier jobs
+};
+constexpr int kMaxSampleJobs = 200;  // 152-byte jobs under the kernel-parameter limit
+template <int G> struct SampleTable {
+    int count;
+    SampleJob job[G];
+};
+static_assert(sizeof(SampleTable<kMaxSampleJobs>) <= 32760, "sampler table exceeds the kernel-parameter limit");
+
+// the job whose range [before[j], before[j + 1]) holds x (before is non-decreasing over jobs)
+template <int G, typename F>
+__device__ __forceinline__ int job_of(const SampleTable<G>& tab, long long x, F before) {
+    int lo = 0, hi = tab.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (before(tab.job[mid]) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kScanTile) weights_scan_grouped_kernel(const __grid_constant__ SampleTable<G> tab) {
+    __shared__ unsigned long long sm[32];
+    const int q = job_of(tab, blockIdx.x, [](const SampleJob& j) { return (long long)j.tiles_before; });
+    const SampleJob& jb = tab.job[q];
+    const long long tile = (long long)blockIdx.x - jb.tiles_before;
+    const long long j = tile * kScanTile + threadIdx.x;
+    unsigned long long W = 0;
+    if (j < jb.len) {
+        const double pj = jb.p[j];
+        if (!(pj >= 0.0 && pj <= 1.0)) set_status(jb.st, BMM_ERR_ARG, (int)(j & 0x7fffffff));
+        else W = __double2ull_rz(floor(ldexp(pj, 62)));
+    }
+    const unsigned long long inc = block_incl_scan_u64(W, sm);
+    if (j < jb.len) jb.G[j] = inc;
+    if (threadIdx.x == kScanTile - 1) jb.tot[tile] = inc;
+}
+
+// one CTA per job: exclusive prefix of its tile totals, and its draw offsets (column unit)
+template <int G>
+__global__ void __launch_bounds__(kScanTile) prefix_grouped_kernel(const __grid_constant__ SampleTable<G> tab) {
+    __shared__ unsigned long long sm[32];
+    __shared__ unsigned long long carry;
+    const SampleJob& jb = tab.job[blockIdx.x];
+    const long long ntiles = (jb.len + kScanTile - 1) / kScanTile;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b = 0; b < ntiles; b += kScanTile) {
+        const long long i = b + threadIdx.x;
+        const unsigned long long v = i < ntiles ? jb.tot[i] : 0ull;
+        const unsigned long long inc = block_incl_scan_u64(v, sm);
+        const unsigned long long c0 = carry;
+        if (i < ntiles) jb.tot[i] = c0 + inc - v;
+        __syncthreads();
+        if (threadIdx.x == kScanTile - 1) carry = c0 + inc;
+        __syncthreads();
+    }
+    if (jb.unit != BMM_UNIT_COLUMN) return;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b = 0; b < jb.K; b += kScanTile) {
+        const long long i = b + threadIdx.x;
+        long long v = i < jb.K ? jb.ck[i] : 0;
+        if (v < 0) { set_status(jb.st, BMM_ERR_ARG, (int)i); v = 0; }
+        const unsigned long long inc = block_incl_scan_u64((unsigned long long)v, sm);
+        const long long c0 = (long long)carry;
+        if (i < jb.K) jb.D[i] = c0 + (long long)inc - v;
+        __syncthreads();
+        if (threadIdx.x == kScanTile - 1) carry = (unsigned long long)(c0 + (long long)inc);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        jb.D[jb.K] = (long long)carry;
+        if ((long long)carry != jb.c) set_status(jb.st, BMM_ERR_INFEASIBLE, 3);
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(128) draw_grouped_kernel(const __grid_constant__ SampleTable<G> tab) {
+    const int q = job_of(tab, blockIdx.x, [](const SampleJob& j) { return (long long)j.blocks_before; });
+    const SampleJob& jb = tab.job[q];
+    const long long t = ((long long)blockIdx.x - jb.blocks_before) * 128 + threadIdx.x;
+    if (t >= jb.c) return;
+    const unsigned long long* pre = jb.G;
+    const unsigned long long* tot = jb.tot;
+    auto S = [&](long long j) { return pre[j] + tot[j / kScanTile]; };  // the full inclusive prefix
+    long long a = 0, b = jb.len, cnt = jb.c;
+    if (jb.unit == BMM_UNIT_COLUMN) {
+        long long lo = 0, hi = jb.K;  // invariant: D[lo] <= t < D[hi]
+        if (!(jb.D[jb.K] > t)) {
+            set_status(jb.st, BMM_ERR_INFEASIBLE, 4);
+            jb.idx[t] = 0; jb.scale[t] = 0.0;
+            return;
+        }
+        while (hi - lo > 1) {
+            const long long mid = (lo + hi) >> 1;
+            if (jb.D[mid] <= t) lo = mid; else hi = mid;
+        }
+        a = jb.off[lo];
+        b = jb.off[lo + 1];
+        cnt = jb.ck[lo];
+        if (a < 0 || b <= a || b > jb.len) {
+            set_status(jb.st, BMM_ERR_SHAPE, (int)lo);
+            jb.idx[t] = 0; jb.scale[t] = 0.0;
+            return;
+        }
+    }
+    const unsigned long long base = (a == 0) ? 0ull : S(a - 1);
+    const unsigned long long T = S(b - 1) - base;
+    if (T == 0ull) {
+        set_status(jb.st, BMM_ERR_ARG, (int)(a & 0x7fffffff));
+        jb.idx[t] = (int32_t)a; jb.scale[t] = 0.0;
+        return;
+    }
+    const uint64_t r = draw_bits(jb.seed, jb.sid, (uint64_t)t);
+    const unsigned long long target = __umul64hi(r, T);
+    long long lo = a, hi = b - 1;  // smallest j in [a, b) with S(j) - base > target
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (S(mid) - base > target) hi = mid; else lo = mid + 1;
+    }
+    jb.idx[t] = (int32_t)lo;
+    jb.scale[t] = __ddiv_rn(1.0, __dmul_rn((double)cnt, jb.p[lo]));
+}
+
+}  // namespace
+
+cudaError_t launch_sample_grouped(const SampleArgs* args, int64_t count, cudaStream_t s) {
+    static SampleTable<kMaxSampleJobs> tab;  // host-side staging of the kernel parameter
+    int64_t i = 0;
+    while (i < count) {
+        tab.count = 0;
+        long long tiles = 0, blocks = 0;
+        for (; i < count && tab.count < kMaxSampleJobs; ++i) {
+            const SampleArgs& a = args[i];
+            if (a.c == 0) continue;
+            const int64_t len = a.unit == BMM_UNIT_COLUMN ? a.n : a.K;
+            const int64_t ntiles = ceil_div(len, kScanTile);
+            char* w = static_cast<char*>(a.scratch);
+            SampleJob& jb = tab.job[tab.count++];
+            jb.p = a.p; jb.off = a.off; jb.ck = a.ck; jb.idx = a.idx; jb.scale = a.scale;
+            jb.G = reinterpret_cast<unsigned long long*>(w);
+            w += round_up(len * 8, 256);
+            jb.tot = reinterpret_cast<unsigned long long*>(w);
+            w += round_up(ntiles * 8, 256);
+            jb.D = reinterpret_cast<int64_t*>(w);
+            jb.st = a.st;
+            jb.K = a.K; jb.len = len; jb.c = a.c; jb.seed = a.seed; jb.sid = a.sid; jb.unit = a.unit;
+            jb.tiles_before = (int)tiles;
+            jb.blocks_before = (int)blocks;
+            tiles += ntiles;
+            blocks += ceil_div(a.c, 128);
+        }
+        if (tab.count == 0) continue;
+        if (tiles > 0x7fffffffLL || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        (count_launch(), weights_scan_grouped_kernel<kMaxSampleJobs><<<(unsigned)tiles, kScanTile, 0, s>>>(tab));
+        (count_launch(), prefix_grouped_kernel<kMaxSampleJobs><<<(unsigned)tab.count, kScanTile, 0, s>>>(tab));
+        (count_launch(), draw_grouped_kernel<kMaxSampleJobs><<<(unsigned)blocks, 128, 0, s>>>(tab));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 int64_t sampler_scratch_bytes(int64_t len, int64_t K) {
     const int64_t ntiles = ceil_div(imax(len, 1), kScanTile);
     return round_up(len * 8, 256) + round_up(ntiles * 8, 256) + round_up((K + 1) * 8, 256);

@@ -478,9 +478,12 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
                 grouped_stats: bool = True) -> list:
     """Many independent products (the batched configuration).
 
-    The design and the draws of each product (bmm_probs, bmm_blocksizes, bmm_sample) are spread
-    round-robin over ``streams`` so that small products overlap; the products themselves run
-    through one bmm_apply_batched call, whose BF16 GEMMs share persistent tensor-core launches.
+    With OPL and tensor-core f_k (``grouped_stats``) every stage runs as grouped launches over all the
+    products: statistics (bmm_probs_batched), block sizes (bmm_blocksizes_batched), draws
+    (bmm_sample_batched) and the products (bmm_apply_batched, whose BF16 GEMMs share persistent
+    tensor-core launches), so the number of launches does not grow with the number of products.
+    Other methods run each product's design and draws on its own, spread round-robin over
+    ``streams`` so that small products overlap, and then the grouped products.
     Every step is an asynchronous C-ABI call, so the whole sequence can be captured with
     torch.cuda.graph and replayed as one graph launch.  Each Problem needs its own workspace.
     ``grouped_stats`` (OPL with tensor-core f_k): the statistics passes of all products share
@@ -518,11 +521,24 @@ def run_batched(probs: list, method: str, cs, seeds, gemm_mode: int = A.GEMM_BF1
         for s in streams:
             if s is not main:
                 s.wait_stream(main)
-    for i, prob in enumerate(probs):
-        with torch.cuda.stream(streams[i % len(streams)]):
-            results.append(run(prob, method, int(cs[i]), int(seeds[i]), c0=c0, gemm_mode=gemm_mode,
-                               compute_product=False, fmode=fmode, fused_stats=fused_stats, p_ready=ready[i],
-                               sizes_ready=sizes[i]))
+    if probs and sizes[0] is not None:
+        # every product's draws in grouped launches (bmm_sample_batched) on the current stream
+        sid = stream_id(0, A.PURPOSE_MAIN)
+        idxs = [torch.empty(int(c), dtype=torch.int32, device=pr.M.device) for pr, c in zip(probs, cs)]
+        scales = [torch.empty(int(c), dtype=torch.float64, device=pr.M.device) for pr, c in zip(probs, cs)]
+        A.bmm_sample_batched(ready, A.UNIT_COLUMN, [pr.B for pr in probs], [ck for ck, _ in sizes],
+                             [int(c) for c in cs], [int(sd) for sd in seeds], [sid] * len(probs), idxs, scales,
+                             [pr.ws for pr in probs])
+        for i, pr in enumerate(probs):
+            results.append({"method": method, "c": int(cs[i]), "seed": int(seeds[i]), "sid": sid, "p": ready[i],
+                            "ck": sizes[i][0], "g": sizes[i][1], "idx": idxs[i], "scale": scales[i],
+                            "unit": A.UNIT_COLUMN, "out": None})
+    else:
+        for i, prob in enumerate(probs):
+            with torch.cuda.stream(streams[i % len(streams)]):
+                results.append(run(prob, method, int(cs[i]), int(seeds[i]), c0=c0, gemm_mode=gemm_mode,
+                                   compute_product=False, fmode=fmode, fused_stats=fused_stats, p_ready=ready[i],
+                                   sizes_ready=sizes[i]))
     for s in streams:
         if s is not main:
             main.wait_stream(s)

@@ -1056,3 +1056,56 @@ def test_bounded_wait_gives_up_and_reports(bmm):
     r = bmm.run(prob, "ONC", 16, seed=1, gemm_mode=A.GEMM_F64)
     bmm.check_status(prob)
     assert np.isfinite(host(r["out"])).all()
+
+
+@pytest.mark.parametrize("unit", ["column", "block"])
+def test_sample_batched_equals_single_products(bmm, unit):
+    """bmm_sample_batched over 230 products of mixed lengths (one crosses the 200-product launch
+    split; some segments longer than one 1024-element scan tile; zero-probability entries; one
+    product with no draws) gives each product's bmm_sample draws bit for bit, and the first product
+    also equals the oracle's draws."""
+    A = bmm._abi
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(91)
+    col = unit == "column"
+    ps, Bs, cks, cs, seeds, sids, wss, keep = [], [], [], [], [], [], [], []
+    for i in range(230):
+        n = int(rng.integers(40, 3000)) if i % 7 else int(rng.integers(2100, 5000))
+        K = int(rng.integers(1, min(n, 60) + 1))
+        off = np.sort(rng.choice(np.arange(1, n), size=K - 1, replace=False)) if K > 1 else np.array([], dtype=np.int64)
+        off = np.concatenate([[0], off, [n]]).astype(np.int64)
+        p = S.random_probabilities(off if col else np.array([0, K]), seed=1000 + i, zero_frac=0.1)
+        c = 0 if i == 17 else (int(rng.integers(K, min(n, 4 * K) + 1)) if col else int(rng.integers(1, 200)))
+        ck = oracle.apportion(np.ones(K), np.diff(off), c) if col and c > 0 else np.zeros(K, dtype=np.int64)
+        off_dev = to_dev(off)
+        keep.append(off_dev)
+        B = A.blocks(off_dev, n, int(np.diff(off).max()))
+        ps.append(to_dev(p))
+        Bs.append(B)
+        cks.append(to_dev(ck))
+        cs.append(c)
+        seeds.append(int(rng.integers(0, 2 ** 62)))
+        sids.append(int(rng.integers(0, 2 ** 20)))
+        need = 256 + 8 * (n + 64 + K + 1) + 4096
+        wss.append(torch.zeros(need, dtype=torch.uint8, device=dev))
+    idx_b = [torch.full((max(c, 1),), -1, dtype=torch.int32, device=dev) for c in cs]
+    sc_b = [torch.full((max(c, 1),), float("nan"), dtype=torch.float64, device=dev) for c in cs]
+    ut = A.UNIT_COLUMN if col else A.UNIT_BLOCK
+    A.bmm_sample_batched(ps, ut, Bs, cks if col else None, cs, seeds, sids, idx_b, sc_b, wss)
+    for i in range(230):
+        assert A.bmm_read_device_status(wss[i]) == A.OK, i
+        if cs[i] == 0:
+            assert int(idx_b[i][0]) == -1
+            continue
+        idx1 = torch.empty(cs[i], dtype=torch.int32, device=dev)
+        sc1 = torch.empty(cs[i], dtype=torch.float64, device=dev)
+        A.bmm_sample(ps[i], ut, Bs[i], cks[i] if col else None, cs[i], seeds[i], sids[i], idx1, sc1, wss[i])
+        np.testing.assert_array_equal(host(idx_b[i]), host(idx1), err_msg=str(i))
+        np.testing.assert_array_equal(host(sc_b[i]), host(sc1), err_msg=str(i))
+    off0 = host(keep[0])
+    if col:
+        wi, wsc = oracle.sample_alg2(host(ps[0]), off0, host(cks[0]), seeds[0], sids[0])
+    else:
+        wi, wsc = oracle.sample_blocks(host(ps[0]), cs[0], seeds[0], sids[0])
+    np.testing.assert_array_equal(host(idx_b[0]), wi)
+    np.testing.assert_array_equal(host(sc_b[0]), wsc)
