@@ -11,7 +11,8 @@ column and row norms and ||M^k N_k||_F^2 -- exact float-float squares plus the o
 TF32 tcgen05 Grams --, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
 BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flush is
 needed).  Prints one JSON line.  Besides the contract's keys it carries the stage times and their
-rooflines, `norm_pass_alone` (the statistics pass without f_k, timed apart), the exact GEMM
+rooflines, `norm_pass_alone` (the statistics pass without f_k, timed apart), `gemm_part_alone`
+(the apply's GEMM on the step's gathered operands, timed apart), the exact GEMM
 baselines and the measured error against the closed form, `error_bars` (the error-bar calls on one
 product and the coverage of their 95% intervals), `targets` (the workload's stated targets against
 these measurements), the other methods' times, e2e through host buffers and the CPU oracle's time
@@ -356,6 +357,38 @@ def time_norm_pass(P, prob, w, pk, reps=20):
             "note": "norm pass and eq. 3.8 probabilities (BMM_F_NONE), inputs larger than L2, back to back"}
 
 
+def time_gemm_part(P, prob, w, L, r, pk, reps=20):
+    """The sampled GEMM of the column-sampled BF16 product (its part of bmm_apply, on the gathered
+    BF16 operands of the step's own draws r) timed alone with CUDA events outside the timed region,
+    back to back: its tensor fraction on real operands, beside the autotuner's figure on constant
+    ones (which draw less power and hold higher clocks)."""
+    import torch
+
+    A = P._abi
+    m, p = w["m"], w["p"]
+    out = torch.empty(m, p, dtype=torch.float32, device=prob.M.device)
+    part = lambda pt: A.bmm_apply_part(prob.M, prob.N, prob.B, r["idx"], r["scale"], L, out, False, pt, 0, m, prob.ws)
+    part(A.APPLY_GATHER_B)
+    part(A.APPLY_GATHER_A)
+    for _ in range(3):
+        part(A.APPLY_GEMM)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        part(A.APPLY_GEMM)
+    e1.record()
+    torch.cuda.synchronize()
+    P.check_status(prob)
+    ms = e0.elapsed_time(e1) / reps
+    tflops = 2.0 * m * p * L / (ms * 1e-3) / 1e12
+    tile = A.bmm_autotune_get(m, p, L, A.GEMM_BF16)
+    return {"bound": "tensor", "achieved": tflops, "peak": pk["bf16"], "unit": "TFLOP/s", "frac": tflops / pk["bf16"],
+            "ms": ms, "reps": reps, "tile": tile,
+            "note": "GEMM part of the BF16 apply on the step's gathered operands, back to back, of the burst peak"}
+
+
 def native_arm(args, ws, rank, local):
     import torch
 
@@ -386,8 +419,9 @@ def native_arm(args, ws, rank, local):
         return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events,
                      fused_stats=args.stats != "split")
 
+    last = None
     for s in range(args.warmup):
-        step(10_000 + s)
+        last = step(10_000 + s)
     torch.cuda.synchronize()
     P.check_status(prob)
 
@@ -451,15 +485,17 @@ def native_arm(args, ws, rank, local):
         r["peak_source"] = pk["source"] + (" (burst bf16)" if r["bound"] == "tensor" else "")
         roofline = r
 
-    norm_alone = None
+    norm_alone = gemm_alone = None
     if args.method in ("OPL", "ONC", "ONU", "ONMCNR") and args.mode != "f64":
         norm_alone = time_norm_pass(P, prob, w, pk)
+    if args.method in ("OPL", "ONC", "ONU", "ONMCNR") and args.mode == "bf16" and last is not None:
+        gemm_alone = time_gemm_part(P, prob, w, L, last, pk)
 
     result = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": args.mode, "data": "synthetic",
-        "norm_pass_alone": norm_alone,
+        "norm_pass_alone": norm_alone, "gemm_part_alone": gemm_alone,
         "config": {"workload": workload_name(args), "method": args.method, "gemm": args.mode, "c": c,
                    "l2": "small case, L2-resident" if args.small else "inputs larger than the 129 MB L2, no flush",
                    "parallelism": f"replicas x{ws}"},
@@ -510,7 +546,11 @@ def target_checks(result, pk, w, L):
             peak = pk["bf16"]
             frac = 2.0 * w["m"] * w["p"] * L / (ms * 1e-3) / 1e12 / peak
             out["gemm_tensor_frac"] = {"value": frac, "target": 0.6, "met": frac >= 0.6,
-                                       "note": "the tuned GEMM timed alone (0.7 ms), of the burst BF16 peak"}
+                                       "note": f"the tuned GEMM timed alone by the autotuner on constant operands "
+                                               f"({ms:.3f} ms), of the burst BF16 peak"}
+        ga = result.get("gemm_part_alone")
+        if ga:
+            out["gemm_tensor_frac_real_operands"] = {"value": ga["frac"], "target": 0.6, "met": ga["frac"] >= 0.6}
         if result.get("exact_fp32_gemm_ms"):
             sp = result["exact_fp32_gemm_ms"] / result["value"]
             out["speedup_vs_exact_fp32"] = {"value": sp, "target": 5.0, "met": sp >= 5.0}
@@ -1016,7 +1056,8 @@ def e2e(P, prob, args, w, c, gm, out, c0, rank, ws, dev):
     from pinned host memory to the device and reads its product back to pinned host memory, all
     inside the timed region.  As a serving loop would, the steps are pipelined over two device input
     sets: step s + 1's upload (its own stream) overlaps step s's product, and step s's download (a
-    third stream) overlaps both; a set is overwritten only after its previous product is done.
+    third stream) overlaps both; a set's inputs are overwritten only after its previous product is
+    done, and its output only after that product has been downloaded.
     `serial` is the same without the pipelining (upload, product, download, one after the other)."""
     import torch
     Mh = prob.M.cpu().pin_memory()
@@ -1030,7 +1071,8 @@ def e2e(P, prob, args, w, c, gm, out, c0, rank, ws, dev):
     sets = [(prob, out), (prob1, torch.empty_like(out))]
     outh = [torch.empty(out.shape, dtype=out.dtype).pin_memory() for _ in range(2)]
     done = [torch.cuda.Event(), torch.cuda.Event()]
-    for e in done:
+    read = [torch.cuda.Event(), torch.cuda.Event()]  # a set's product has been downloaded
+    for e in done + read:
         e.record(main)
 
     def step(s):
@@ -1041,11 +1083,13 @@ def e2e(P, prob, args, w, c, gm, out, c0, rank, ws, dev):
             pr.M.copy_(Mh, non_blocking=True)
             pr.N.copy_(Nh, non_blocking=True)
         main.wait_stream(up)
+        main.wait_event(read[k])  # and its previous product has left the device
         P.run(pr, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=o)
         done[k].record(main)
         down.wait_event(done[k])
         with torch.cuda.stream(down):
             outh[k].copy_(o, non_blocking=True)
+        read[k].record(down)
 
     def serial(s):
         prob.M.copy_(Mh, non_blocking=True)

@@ -10,6 +10,14 @@
 //            back;
 //   warps 2-5 drain the other accumulator with tcgen05.ld (one TMEM lane quadrant per warp)
 //            and store FP32 rows, overlapping the next tile's MMAs.
+// CTA-pair form (PAIR, tile choice bn = 512): clusters of two CTAs on two SMs compute 256 x 256
+// tiles with cta_group::2 MMAs (M = 256, N = 256).  Each CTA loads its own 128 rows of A and 128 of
+// the tile's 256 rows of B per stage (32 KB instead of the single-CTA 48 KB for 128 x 256), both
+// copies completing on the even CTA's stage barrier; that CTA's MMA lane issues for the pair and
+// multicasts its commits to both CTAs' stage and accumulator barriers; each CTA's epilogue drains
+// its own 128 rows and releases the accumulator on the even CTA's barrier.  Per SM the shared-memory
+// traffic of one 64-deep BF16 stage drops from 96 KB (copy writes and MMA operand reads) to about
+// 80 KB for the same 128 x 256 x 64 of math, and the L2 traffic per tile element halves.
 // Every wait is bounded (globaltimer); on expiry the CTA records BMM_ERR_TIMEOUT, lets its
 // copies and MMAs in flight finish (again bounded), frees TMEM and returns.
 #include <map>
@@ -26,22 +34,27 @@ using namespace ptx;
 constexpr int BM = 128;
 constexpr int ROW_BYTES = 128;  // K per stage: one 128-byte swizzled row
 
-// EK: element kind, 0 = BF16 (kind::f16), 1 = FP8 e4m3 (kind::f8f6f4)
-template <int BN, int EK> struct Cfg {
+// EK: element kind, 0 = BF16 (kind::f16), 1 = FP8 e4m3 (kind::f8f6f4).  PAIR: CTA-pair tiles
+// (BN = 256 only): TILE_M = 256 output rows per tile, 128 per CTA, and B_ROWS = 128 rows of B per CTA.
+template <int BN, int EK, bool PAIR = false> struct Cfg {
+    static_assert(!PAIR || BN == 256, "CTA-pair tiles are 256 x 256");
     static constexpr int ESIZE = EK ? 1 : 2;
     static constexpr int BK = ROW_BYTES / ESIZE;       // elements of K per stage
     static constexpr int KMMA = 32 / ESIZE;            // elements of K per MMA (32 bytes)
-    static constexpr int STAGES = (BN == 256) ? 4 : 6;
+    static constexpr int TILE_M = PAIR ? 2 * BM : BM;
+    static constexpr int B_ROWS = PAIR ? BN / 2 : BN;
+    static constexpr int STAGES = PAIR ? 7 : ((BN == 256) ? 4 : 6);
     static constexpr int A_BYTES = BM * ROW_BYTES;
-    static constexpr int B_BYTES = BN * ROW_BYTES;
+    static constexpr int B_BYTES = B_ROWS * ROW_BYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t STAGE_TX = (PAIR ? 2u : 1u) * (uint32_t)STAGE_BYTES;  // bytes a full barrier awaits
     static constexpr int TMEM_COLS = 2 * BN;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
     // instruction descriptor: D=F32 (bits 4-5); A, B format (bits 7-9, 10-12): BF16 = 1 for
     // kind::f16, E4M3 = 0 for kind::f8f6f4; both K-major, N>>3 at bits 17-22, M>>4 at bits 24-28
     static constexpr uint32_t FMT = EK ? 0u : 1u;
     static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                      ((uint32_t)(BM >> 4) << 24);
+                                      ((uint32_t)(TILE_M >> 4) << 24);
 };
 
 // G M-tiles per raster group (4, 8 or 16, chosen per product by the autotuner), so that concurrent
@@ -96,9 +109,15 @@ __device__ __forceinline__ int problem_kb(const GemmProblem& pr) {
     return (int)(K / BK);
 }
 
-template <int BN, int G, int EK>
+__device__ __forceinline__ int ld_cluster_s32(uint32_t cluster_addr) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
+    return v;
+}
+
+template <int BN, int G, int EK, bool PAIR>
 __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_constant__ GemmTable<G> tab, DevStatus* st) {
-    using C = Cfg<BN, EK>;
+    using C = Cfg<BN, EK, PAIR>;
     constexpr int BK = C::BK;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t bar_full[C::STAGES];
@@ -114,6 +133,11 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
     uint8_t* sB = base + C::STAGES * C::A_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_tiles = tab.total_tiles;
+    // tiles are dealt to CTAs, or in PAIR form to CTA pairs (clusters), round-robin
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const bool leader = rank == 0;
+    const int first_tile = PAIR ? (int)cluster_id() : (int)blockIdx.x;
+    const int tile_step = PAIR ? (int)cluster_count() : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -122,15 +146,23 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&bar_tfull[a]), 1);
-            mbar_init(smem_u32(&bar_tempty[a]), 4);
+            mbar_init(smem_u32(&bar_tempty[a]), PAIR ? 8 : 4);  // the epilogue warps of the CTA (pair)
         }
         mbar_init(smem_u32(&bar_drain), 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(&s_tmem), (uint32_t)C::TMEM_COLS);
+    if (warp == 1) {
+        if constexpr (PAIR)
+            tmem_alloc_pair(smem_u32(&s_tmem), (uint32_t)C::TMEM_COLS);
+        else
+            tmem_alloc(smem_u32(&s_tmem), (uint32_t)C::TMEM_COLS);
+    }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR)
+        cluster_sync();  // the peer's barriers are initialised before any copy or arrive targets them
+    else
+        __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
@@ -140,7 +172,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         uint32_t phase = 0;
         uint32_t issued_mask = 0, issued_phase = 0;
         bool aborted = false;
-        for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x) {
+        for (int tile = first_tile; tile < num_tiles && !aborted; tile += tile_step) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             int tm, tn;
             tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, pr.raster, &tm, &tn);
@@ -151,9 +183,21 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                     break;
                 }
                 const uint32_t fb = smem_u32(&bar_full[stage]);
-                mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
-                tma_load_2d(smem_u32(sA + stage * C::A_BYTES), &pr.mapA, fb, kb * BK, tm * BM);
-                tma_load_2d(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb, kb * BK, tn * BN);
+                if constexpr (PAIR) {
+                    // both CTAs' copies complete on the even CTA's barrier, which awaits all 64 KB;
+                    // a peer copy may land before that CTA's expect_tx (the phase cannot complete
+                    // while its one arrival is pending)
+                    const uint32_t fb0 = smem_peer(fb, 0);
+                    if (leader) mbar_expect_tx(fb, C::STAGE_TX);
+                    tma_load_2d_pair(smem_u32(sA + stage * C::A_BYTES), &pr.mapA, fb0, kb * BK,
+                                     tm * C::TILE_M + BM * (int)rank);
+                    tma_load_2d_pair(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb0, kb * BK,
+                                     tn * BN + C::B_ROWS * (int)rank);
+                } else {
+                    mbar_expect_tx(fb, C::STAGE_TX);
+                    tma_load_2d(smem_u32(sA + stage * C::A_BYTES), &pr.mapA, fb, kb * BK, tm * BM);
+                    tma_load_2d(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb, kb * BK, tn * BN);
+                }
                 issued_mask |= 1u << stage;
                 issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                 if (++stage == C::STAGES) {
@@ -162,17 +206,20 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 }
             }
         }
-        if (aborted) {  // let the copies in flight land before the CTA's shared memory goes away
+        // let the copies in flight land before the CTA's shared memory goes away (in PAIR form
+        // the peer's bytes count on the even CTA's barriers: both CTAs wait out a grace period
+        // at the end instead)
+        if (aborted && !PAIR) {
             for (int s = 0; s < C::STAGES; ++s)
                 if (issued_mask & (1u << s)) mbar_wait(smem_u32(&bar_full[s]), (issued_phase >> s) & 1u, nullptr);
         }
-    } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------------ MMA issuer
+    } else if (warp == 1 && lane == 0 && leader) {
+        // ------------------------------------------------ MMA issuer (the even CTA of a pair)
         int stage = 0;
         uint32_t phase = 0;
         int it = 0;
         bool aborted = false;
-        for (int tile = blockIdx.x; tile < num_tiles && !aborted; tile += gridDim.x, ++it) {
+        for (int tile = first_tile; tile < num_tiles && !aborted; tile += tile_step, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             const int num_kb = problem_kb<BK>(pr);
             const int acc = it & 1;
@@ -193,29 +240,46 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 const uint64_t bd = sw128_desc(smem_u32(sB + stage * C::B_BYTES));
 #pragma unroll
                 for (int k = 0; k < BK / C::KMMA; ++k) {
-                    if (EK)
-                        tc_mma_f8(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
-                    else
-                        tc_mma_bf16(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                    const uint32_t acc_in = (kb > 0 || k > 0) ? 1u : 0u;
+                    if constexpr (PAIR) {
+                        if (EK)
+                            tc_mma_f8_pair(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
+                        else
+                            tc_mma_bf16_pair(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
+                    } else {
+                        if (EK)
+                            tc_mma_f8(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
+                        else
+                            tc_mma_bf16(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
+                    }
                 }
-                tc_commit(smem_u32(&bar_empty[stage]));
+                if constexpr (PAIR)
+                    tc_commit_pair_mc(smem_u32(&bar_empty[stage]), (uint16_t)3);
+                else
+                    tc_commit(smem_u32(&bar_empty[stage]));
                 if (++stage == C::STAGES) {
                     stage = 0;
                     phase ^= 1u;
                 }
             }
             if (aborted) break;
-            tc_commit(smem_u32(&bar_tfull[acc]));
+            if constexpr (PAIR)
+                tc_commit_pair_mc(smem_u32(&bar_tfull[acc]), (uint16_t)3);
+            else
+                tc_commit(smem_u32(&bar_tfull[acc]));
         }
         if (aborted) {  // wait for the MMAs already issued before TMEM is freed
-            tc_commit(smem_u32(&bar_drain));
+            if constexpr (PAIR)
+                tc_commit_pair_mc(smem_u32(&bar_drain), (uint16_t)1);
+            else
+                tc_commit(smem_u32(&bar_drain));
             mbar_wait(smem_u32(&bar_drain), 0u, nullptr);
         }
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;
         int it = 0;
-        for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+        for (int tile = first_tile; tile < num_tiles; tile += tile_step, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             const int num_kb = problem_kb<BK>(pr);
             const int acc = it & 1;
@@ -224,7 +288,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
             tc_fence_after();
             int tm, tn;
             tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, pr.raster, &tm, &tn);
-            const int row = tm * BM + q * 32 + lane;
+            const int row = tm * C::TILE_M + BM * (int)rank + q * 32 + lane;
             const int M = pr.M, N = pr.N;
             const float sc = pr.scale != nullptr ? *pr.scale : 1.0f;
 #pragma unroll 1
@@ -265,16 +329,37 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[acc]));
+            if (lane == 0) {
+                if constexpr (PAIR)
+                    mbar_arrive_cluster(smem_peer(smem_u32(&bar_tempty[acc]), 0));
+                else
+                    mbar_arrive(smem_u32(&bar_tempty[acc]));
+            }
         }
     }
 
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) {
+        // all roles of both CTAs are done (every wait above is bounded); if either CTA gave up,
+        // copies it or its peer issued may still be landing: wait 1 ms before shared memory goes away
+        cluster_sync();
+        const int any_abort = s_abort | ld_cluster_s32(smem_peer(smem_u32((const void*)&s_abort), rank ^ 1u));
+        cluster_sync();
+        if (any_abort) {
+            const uint64_t t0 = globaltimer();
+            while (globaltimer() - t0 < 1000000ull) {
+            }
+        }
+    } else {
+        __syncthreads();
+    }
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, (uint32_t)C::TMEM_COLS);
+        if constexpr (PAIR)
+            tmem_dealloc_pair(tmem, (uint32_t)C::TMEM_COLS);
+        else
+            tmem_dealloc(tmem, (uint32_t)C::TMEM_COLS);
     }
     if (threadIdx.x == 0 && s_abort) set_status(st, BMM_ERR_TIMEOUT, 1);
 }
@@ -314,12 +399,17 @@ int num_sms() {
     return n > 0 ? n : 1;
 }
 
-// Fill one table entry; returns false when a tensor map cannot be made.
-bool fill_problem(GemmProblem* pr, int BN, int raster, const void* A, int64_t lda, const void* B, int64_t ldb,
+// Fill one table entry for tile choice bn (128 or 256: one CTA, 128 x bn tiles; kPairTile: a CTA
+// pair, 256 x 256 tiles with 128-row boxes of A and B per CTA); returns false when a tensor map
+// cannot be made.
+bool fill_problem(GemmProblem* pr, int bn, int raster, const void* A, int64_t lda, const void* B, int64_t ldb,
                   int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
                   int64_t ldo, int accumulate, int elem, const float* scale) {
     const int esize = elem == GEMM_ELEM_E4M3 ? 1 : 2;
-    if (!make_map(&pr->mapA, A, M, kdim, lda, BM, esize) || !make_map(&pr->mapB, B, N, kdim, ldb, BN, esize)) return false;
+    const bool pair = bn == kPairTile;
+    const int tile_m = pair ? 2 * BM : BM, tile_n = pair ? 256 : bn, b_rows = pair ? 128 : bn;
+    if (!make_map(&pr->mapA, A, M, kdim, lda, BM, esize) || !make_map(&pr->mapB, B, N, kdim, ldb, b_rows, esize))
+        return false;
     pr->scale = scale;
     pr->out = out;
     pr->ldo = ldo;
@@ -327,8 +417,8 @@ bool fill_problem(GemmProblem* pr, int BN, int raster, const void* A, int64_t ld
     pr->k_host = k_host;
     pr->M = (int)M;
     pr->N = (int)N;
-    pr->tiles_m = (int)ceil_div(M, BM);
-    pr->tiles_n = (int)ceil_div(N, BN);
+    pr->tiles_m = (int)ceil_div(M, tile_m);
+    pr->tiles_n = (int)ceil_div(N, tile_n);
     pr->k_mult = k_mult;
     pr->accumulate = accumulate;
     pr->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (ldo % 4 == 0);
@@ -336,27 +426,65 @@ bool fill_problem(GemmProblem* pr, int BN, int raster, const void* A, int64_t ld
     return true;
 }
 
-template <int BN, int G, int EK>
+template <int BN, int G, int EK, bool PAIR>
 cudaError_t launch_table(const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
-    using C = Cfg<BN, EK>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, G, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    using C = Cfg<BN, EK, PAIR>;
+    auto kern = gemm_bf16_tc_kernel<BN, G, EK, PAIR>;
+    static int units = 0;  // CTAs, or CTA pairs, that are resident at once
+    if (units == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int n = num_sms();
+        if (PAIR) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)(n & ~1));
+            cfg.blockDim = dim3(192);
+            cfg.dynamicSmemBytes = C::SMEM;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+            if (e != cudaSuccess) return e;
+            n = clusters > 0 ? clusters : 1;
+        }
+        units = n;
     }
     if (tab.total_tiles == 0) return cudaSuccess;
-    const int grid = (int)imin(tab.total_tiles, num_sms());
-    (count_launch(), gemm_bf16_tc_kernel<BN, G, EK><<<grid, 192, C::SMEM, s>>>(tab, st));
-    return cudaGetLastError();
+    const int grid = (int)imin(tab.total_tiles, units);
+    count_launch();
+    if constexpr (PAIR) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(2 * grid));
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = C::SMEM;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, tab, st);
+    } else {
+        kern<<<grid, 192, C::SMEM, s>>>(tab, st);
+        return cudaGetLastError();
+    }
 }
 
 template <int G>
-cudaError_t launch_any(int BN, int elem, const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
-    if (elem == GEMM_ELEM_E4M3)
-        return BN == 128 ? launch_table<128, G, 1>(tab, st, s) : launch_table<256, G, 1>(tab, st, s);
-    return BN == 128 ? launch_table<128, G, 0>(tab, st, s) : launch_table<256, G, 0>(tab, st, s);
+cudaError_t launch_any(int bn, int elem, const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
+    if (elem == GEMM_ELEM_E4M3) {
+        if (bn == kPairTile) return launch_table<256, G, 1, true>(tab, st, s);
+        return bn == 128 ? launch_table<128, G, 1, false>(tab, st, s) : launch_table<256, G, 1, false>(tab, st, s);
+    }
+    if (bn == kPairTile) return launch_table<256, G, 0, true>(tab, st, s);
+    return bn == 128 ? launch_table<128, G, 0, false>(tab, st, s) : launch_table<256, G, 0, false>(tab, st, s);
 }
 
 // strides multiples of 16 bytes, K padded to the 128-byte stage with a host extent
@@ -372,8 +500,9 @@ bool gemm_args_ok(const void* A, int64_t lda, const void* B, int64_t ldb, int64_
 // ---------------------------------------------------------------- tile choices
 // The tile width (BN) and raster group of each product come from a process-wide table filled by
 // the autotuner (bmm_autotune_gemm), keyed by element kind and the rounded-up base-2 logarithms of
-// M, N and K; shapes never tuned take BN = 128 for N <= 128, else 256, and raster group 8.  Neither
-// choice changes a result: every output element is the same dot product in the same K order.
+// M, N and K; shapes never tuned take BN = 128 for N <= 128, else 256 for M <= 128 (a CTA pair's
+// second 128 rows would be empty), else the CTA-pair tile, and raster group 8.  Neither choice
+// changes a result: every output element is the same dot product in the same K order.
 std::mutex& tune_mutex() {
     static std::mutex mu;
     return mu;
@@ -397,11 +526,11 @@ TileChoice gemm_tile_choice(int elem, int64_t M, int64_t N, int64_t K) {
     std::lock_guard<std::mutex> lock(tune_mutex());
     const auto it = tune_table().find(tune_key(elem, M, N, K));
     if (it != tune_table().end()) return it->second;
-    return TileChoice{N <= 128 ? 128 : 256, 8};
+    return TileChoice{N <= 128 ? 128 : (M <= 128 ? 256 : kPairTile), 8};
 }
 
 bool gemm_tile_valid(const TileChoice& c) {
-    return (c.bn == 128 || c.bn == 256) && (c.raster == 4 || c.raster == 8 || c.raster == 16);
+    return (c.bn == 128 || c.bn == 256 || c.bn == kPairTile) && (c.raster == 4 || c.raster == 8 || c.raster == 16);
 }
 
 void gemm_tile_set(int elem, int64_t M, int64_t N, int64_t K, const TileChoice& c) {
@@ -444,9 +573,9 @@ cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, Dev
     // products are grouped by tile width and element kind; each launch takes up to kMaxGroup of them
     std::vector<TileChoice> choice((size_t)count);
     for (int64_t i = 0; i < count; ++i) choice[i] = gemm_tile_choice(args[i].elem, args[i].M, args[i].N, args[i].kdim);
-    for (int pass = 0; pass < 4; ++pass) {
-        const int BN = (pass & 1) ? 256 : 128;
-        const int elem = pass >> 1;
+    for (int pass = 0; pass < 6; ++pass) {
+        const int BN = pass % 3 == 0 ? 128 : (pass % 3 == 1 ? 256 : kPairTile);
+        const int elem = pass / 3;
         static GemmTable<kMaxGroup> tab;  // host-side staging of the kernel parameter (30 KB)
         tab.count = 0;
         tab.total_tiles = 0;
@@ -509,7 +638,7 @@ cudaError_t gemm_autotune(int64_t M, int64_t N, int64_t K, int elem, void* scrat
     if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
     TileChoice best{0, 0};
     float best_t = 0.f;
-    for (int bn : {128, 256}) {
+    for (int bn : {128, 256, kPairTile}) {
         for (int raster : {4, 8, 16}) {
             GemmTable<1> tab;
             tab.count = 1;

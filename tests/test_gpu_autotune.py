@@ -9,7 +9,7 @@ from tests._gpu_util import host, to_dev
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-CHOICES = [(bn, r) for bn in (128, 256) for r in (4, 8, 16)]
+CHOICES = [(bn, r) for bn in (128, 256, 512) for r in (4, 8, 16)]  # 512: the CTA-pair tile
 
 
 @pytest.fixture(scope="module")
@@ -52,6 +52,34 @@ def test_tile_choices_do_not_change_results(bmm, mode):
     A.bmm_autotune_clear()
 
 
+@pytest.mark.parametrize("mode", ["bf16", "e4m3"])
+@pytest.mark.parametrize("m,p", [(64, 40), (130, 260), (256, 256), (390, 129)])
+def test_pair_tile_edges_accumulate(bmm, mode, m, p):
+    """The CTA-pair tile against the single-CTA 128 x 128 tile, bit for bit, on shapes where the odd
+    CTA's rows of A or of B lie wholly or partly past the matrix (m < 128, ragged m and p), adding
+    into a prefilled output."""
+    A = bmm._abi
+    gm = bmm.MODES[mode]
+    off = S.block_offsets_uneven(2000, 25, 40, 120, seed=m + p)
+    M, N = S.scaled_gaussian(m, 2000, p, off, 1.0, seed=m * p, dtype=np.float32)
+    Mt, Nt = to_dev(M), to_dev(N)
+    L = 300
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=gm)
+    r = bmm.run(prob, "ONC", L, seed=5, compute_product=False)
+    base = torch.from_numpy(np.random.default_rng(m).standard_normal((m, p)).astype(np.float32)).to(Mt.device)
+    outs = []
+    for bn in (128, A.TILE_PAIR):
+        A.bmm_autotune_clear()
+        A.bmm_autotune_set(m, p, L, gm, bn, 8)
+        out = base.clone()
+        A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, gm, out, True, prob.ws)
+        bmm.check_status(prob)
+        outs.append(host(out))
+    A.bmm_autotune_clear()
+    np.testing.assert_array_equal(outs[1], outs[0])
+    assert not np.array_equal(outs[0], host(base))
+
+
 def test_grouped_launch_mixed_choices(bmm):
     """bmm_apply_batched with products whose recorded tile widths differ: each product lands in the
     launch of its own width and equals its single-product result."""
@@ -67,7 +95,7 @@ def test_grouped_launch_mixed_choices(bmm):
         probs.append(pr)
         samples.append(r)
         cs.append(600)
-        A.bmm_autotune_set(m, p, 600, gm, (128, 256)[i % 2], (4, 8, 16)[i % 3])
+        A.bmm_autotune_set(m, p, 600, gm, (128, 256, A.TILE_PAIR)[i % 3], (4, 8, 16)[(i + 1) % 3])
     single = []
     for pr, r in zip(probs, samples):
         out = torch.empty(pr.M.shape[0], pr.N.shape[1], dtype=torch.float32, device=pr.M.device)
@@ -98,7 +126,7 @@ def test_batch_level_tuning_keeps_results(bmm):
     res = bmm.run_batched(probs, "ONC", cs, [1, 2, 3], gemm_mode=A.GEMM_BF16)
     before = [host(r["out"]).copy() for r in res]
     tune = bmm.autotune_batched(probs, res, cs, A.GEMM_BF16)
-    assert tune["choice"] in tune["ms"] and len(tune["ms"]) == 8
+    assert tune["choice"] in tune["ms"] and len(tune["ms"]) == 11
     res2 = bmm.run_batched(probs, "ONC", cs, [1, 2, 3], gemm_mode=A.GEMM_BF16)
     for a_, r in zip(before, res2):
         np.testing.assert_array_equal(host(r["out"]), a_)
