@@ -75,19 +75,22 @@ def test_autotune_table_host_side():
     A.load()
     A.bmm_autotune_clear()
     assert A.bmm_autotune_get(300, 100, 517, A.GEMM_BF16) == {"bn": 128, "raster": 8}
-    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": 256, "raster": 8}
+    assert A.bmm_autotune_get(100, 520, 517, A.GEMM_BF16) == {"bn": 256, "raster": 8}  # m <= 128: one CTA
+    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": A.TILE_PAIR, "raster": 8}
     A.bmm_autotune_set(300, 520, 517, A.GEMM_BF16, 128, 16)
     assert A.bmm_autotune_get(300, 520, 600, A.GEMM_BF16) == {"bn": 128, "raster": 16}  # same bucket
-    assert A.bmm_autotune_get(300, 520, 2000, A.GEMM_BF16) == {"bn": 256, "raster": 8}  # depth bucket differs
-    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_E4M3) == {"bn": 256, "raster": 8}  # element kind differs
-    for bad in ((300, 520, 517, A.GEMM_BF16, 192, 8), (300, 520, 517, A.GEMM_BF16, 128, 5),
+    assert A.bmm_autotune_get(300, 520, 2000, A.GEMM_BF16) == {"bn": A.TILE_PAIR, "raster": 8}  # depth bucket differs
+    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_E4M3) == {"bn": A.TILE_PAIR, "raster": 8}  # element kind differs
+    A.bmm_autotune_set(300, 520, 517, A.GEMM_BF16, A.TILE_PAIR, 4)
+    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": A.TILE_PAIR, "raster": 4}
+    for bad in ((300, 520, 517, A.GEMM_BF16, 192, 8), (300, 520, 517, A.GEMM_BF16, 128, 5), (300, 520, 517, A.GEMM_BF16, 1024, 8),
                 (300, 520, 517, A.GEMM_F64, 128, 8), (0, 520, 517, A.GEMM_BF16, 128, 8)):
         with pytest.raises(A.BmmError):
             A.bmm_autotune_set(*bad)
     assert A.bmm_autotune_workspace_size(300, 520, 517, A.GEMM_F64) == 0
     assert A.bmm_autotune_workspace_size(300, 520, 517, A.GEMM_BF16) > 256 + 2 * (300 + 520) * 576
     A.bmm_autotune_clear()
-    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": 256, "raster": 8}
+    assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": A.TILE_PAIR, "raster": 8}
 
 
 def test_error_bar_calls_validate_arguments_on_host(lib):
