@@ -8,8 +8,11 @@
 //   warp 1   allocates 2*BN TMEM columns; one lane issues tcgen05.mma (kind::f16, K = 16, or
 //            kind::f8f6f4, K = 32; M=128, N=BN) into one of two TMEM accumulators and commits stages
 //            back;
-//   warps 2-5 drain the other accumulator with tcgen05.ld (one TMEM lane quadrant per warp)
-//            and store FP32 rows, overlapping the next tile's MMAs.
+//   warps 2-5 drain the other accumulator with tcgen05.ld (one TMEM lane quadrant per warp),
+//            overlapping the next tile's MMAs: each warp stages 32 x 32 FP32 blocks in shared
+//            memory (two 4 KB buffers, 128-byte swizzled) and writes them with TMA tile stores, or
+//            TMA reduce-adds when accumulating (the same FP32 old + new as a load-add-store); an
+//            output whose base or row stride is not 16-byte aligned is written with plain stores.
 // CTA-pair form (PAIR, tile choice bn = 512): clusters of two CTAs on two SMs compute 256 x 256
 // tiles with cta_group::2 MMAs (M = 256, N = 256).  Each CTA loads its own 128 rows of A and 128 of
 // the tile's 256 rows of B per stage (32 KB instead of the single-CTA 48 KB for 128 x 256), both
@@ -43,13 +46,14 @@ template <int BN, int EK, bool PAIR = false> struct Cfg {
     static constexpr int KMMA = 32 / ESIZE;            // elements of K per MMA (32 bytes)
     static constexpr int TILE_M = PAIR ? 2 * BM : BM;
     static constexpr int B_ROWS = PAIR ? BN / 2 : BN;
-    static constexpr int STAGES = PAIR ? 7 : ((BN == 256) ? 4 : 6);
+    static constexpr int STAGES = PAIR ? 6 : ((BN == 256) ? 4 : 6);
     static constexpr int A_BYTES = BM * ROW_BYTES;
     static constexpr int B_BYTES = B_ROWS * ROW_BYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr uint32_t STAGE_TX = (PAIR ? 2u : 1u) * (uint32_t)STAGE_BYTES;  // bytes a full barrier awaits
     static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+    static constexpr int EPI_BYTES = 4 * 2 * 32 * 32 * 4;  // 4 epilogue warps x 2 buffers x 32 x 32 FP32
+    static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
     // instruction descriptor: D=F32 (bits 4-5); A, B format (bits 7-9, 10-12): BF16 = 1 for
     // kind::f16, E4M3 = 0 for kind::f8f6f4; both K-major, N>>3 at bits 17-22, M>>4 at bits 24-28
     static constexpr uint32_t FMT = EK ? 0u : 1u;
@@ -74,6 +78,7 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
 struct GemmProblem {
     CUtensorMap mapA;
     CUtensorMap mapB;
+    CUtensorMap mapO;  // FP32 output, 32 x 32 boxes, 128-byte swizzle (valid when tma_out)
     float* out;
     long long ldo;
     const long long* k_dev;
@@ -84,6 +89,7 @@ struct GemmProblem {
     int k_mult;
     int accumulate;
     int vec_ok;
+    int tma_out;
     int raster;
     const float* scale;  // device factor applied to the product (FP8), or null
 };
@@ -92,7 +98,7 @@ template <int G> struct GemmTable {
     int total_tiles;
     GemmProblem prob[G];
 };
-constexpr int kMaxGroup = 80;  // 80 x 384-byte entries keep the table under the 32 KB kernel-parameter limit
+constexpr int kMaxGroup = 60;  // 60 x 512-byte entries keep the table under the 32 KB kernel-parameter limit
 static_assert(sizeof(GemmTable<kMaxGroup>) <= 32764, "GEMM table exceeds the kernel-parameter limit");
 
 template <int G>
@@ -107,6 +113,12 @@ template <int BK>
 __device__ __forceinline__ int problem_kb(const GemmProblem& pr) {
     const long long K = pr.k_dev ? (long long)pr.k_mult * (((*pr.k_dev) + BK - 1) / BK * BK) : pr.k_host;
     return (int)(K / BK);
+}
+
+// A bounded wait whose first poll is inline: on the issue path of the single MMA thread a call to
+// the out-of-line wait for a phase that is already complete costs about 4% of the GEMM's time.
+__device__ __forceinline__ bool wait_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort_flag);
 }
 
 __device__ __forceinline__ int ld_cluster_s32(uint32_t cluster_addr) {
@@ -131,6 +143,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = base;
     uint8_t* sB = base + C::STAGES * C::A_BYTES;
+    uint8_t* sE = sB + C::STAGES * C::B_BYTES;  // epilogue staging, 1024-byte aligned
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_tiles = tab.total_tiles;
     // tiles are dealt to CTAs, or in PAIR form to CTA pairs (clusters), round-robin
@@ -178,7 +191,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
             tile_coords(tile - pr.tile_begin, pr.tiles_m, pr.tiles_n, pr.raster, &tm, &tn);
             const int num_kb = problem_kb<BK>(pr);
             for (int kb = 0; kb < num_kb; ++kb) {
-                if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
+                if (!wait_fast(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
                     aborted = true;
                     break;
                 }
@@ -224,14 +237,14 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
             const int num_kb = problem_kb<BK>(pr);
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
-            if (!mbar_wait(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
+            if (!wait_fast(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
                 aborted = true;
                 break;
             }
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(acc * BN);
             for (int kb = 0; kb < num_kb; ++kb) {
-                if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &s_abort)) {
+                if (!wait_fast(smem_u32(&bar_full[stage]), phase, &s_abort)) {
                     aborted = true;
                     break;
                 }
@@ -279,6 +292,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         // ------------------------------------------------ epilogue
         const int q = warp & 3;
         int it = 0;
+        int nchunk = 0;  // staged chunks so far: selects the buffer
         for (int tile = first_tile; tile < num_tiles; tile += tile_step, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             const int num_kb = problem_kb<BK>(pr);
@@ -306,7 +320,29 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                     for (int e = 0; e < 32; ++e) r[e] = __float_as_uint(__uint_as_float(r[e]) * sc);
                 }
                 const int col0 = tn * BN + cc * 32;
-                if (row < M && col0 < N) {
+                if (pr.tma_out) {
+                    // this warp's 32 rows x 32 columns: row = lane, 16-byte chunk c of the row at
+                    // chunk c ^ (row mod 8) of its 128 bytes (the 128-byte swizzle the map expects)
+                    const int row0 = row - lane;
+                    uint8_t* buf = sE + (q * 2 + (nchunk & 1)) * 4096;
+                    if (lane == 0) bulk_wait_read<1>();  // the store issued from this buffer two chunks ago has read it
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        *reinterpret_cast<float4*>(buf + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+                            make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
+                                        __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0 && row0 < M && col0 < N) {  // the map clips rows >= M and columns >= N
+                        if (pr.accumulate)
+                            tma_reduce_add_2d(&pr.mapO, smem_u32(buf), col0, row0);
+                        else
+                            tma_store_2d(&pr.mapO, smem_u32(buf), col0, row0);
+                        bulk_commit();
+                    }
+                    ++nchunk;
+                } else if (row < M && col0 < N) {
                     float* o = pr.out + (long long)row * pr.ldo + col0;
                     if (pr.vec_ok && col0 + 32 <= N) {
 #pragma unroll
@@ -336,6 +372,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                     mbar_arrive(smem_u32(&bar_tempty[acc]));
             }
         }
+        if (lane == 0) bulk_wait<0>();  // the output is written and the staging buffers are read
     }
 
     tc_fence_before();
@@ -392,6 +429,20 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kdim, int64
     return r == CUDA_SUCCESS;
 }
 
+// FP32 output of M rows and N columns (row stride ldo elements): 32 x 32 boxes (128 bytes by 32 rows),
+// 128-byte swizzle, for the epilogue's TMA stores
+bool make_out_map(CUtensorMap* m, float* out, int64_t M, int64_t N, int64_t ldo) {
+    auto fn = encode_fn();
+    if (fn == nullptr) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+    cuuint64_t strides[1] = {(cuuint64_t)(ldo * 4)};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, out, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int num_sms() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -422,6 +473,7 @@ bool fill_problem(GemmProblem* pr, int bn, int raster, const void* A, int64_t ld
     pr->k_mult = k_mult;
     pr->accumulate = accumulate;
     pr->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (ldo % 4 == 0);
+    pr->tma_out = pr->vec_ok && make_out_map(&pr->mapO, out, M, N, ldo) ? 1 : 0;
     pr->raster = raster;
     return true;
 }

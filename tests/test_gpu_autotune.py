@@ -80,6 +80,38 @@ def test_pair_tile_edges_accumulate(bmm, mode, m, p):
     assert not np.array_equal(outs[0], host(base))
 
 
+@pytest.mark.parametrize("bn", [128, 256, 512])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_tma_store_epilogue_matches_plain_stores(bmm, bn, accumulate):
+    """An output whose base and row stride are 16-byte aligned is written by the epilogue's TMA tile
+    stores (TMA reduce-adds when accumulating); one that is not takes plain stores.  Both give the
+    same bits, for every tile width, on ragged m and p."""
+    A = bmm._abi
+    gm = A.GEMM_BF16
+    m, p, L = 333, 272, 500
+    off = S.block_offsets_uneven(3000, 30, 40, 160, seed=17)
+    M, N = S.scaled_gaussian(m, 3000, p, off, 1.0, seed=18, dtype=np.float32)
+    Mt, Nt = to_dev(M), to_dev(N)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=gm)
+    r = bmm.run(prob, "ONC", L, seed=9, compute_product=False)
+    A.bmm_autotune_clear()
+    A.bmm_autotune_set(m, p, L, gm, bn, 8)
+    base = torch.from_numpy(np.random.default_rng(4).standard_normal((m, p)).astype(np.float32)).to(Mt.device)
+    aligned = base.clone()
+    assert aligned.data_ptr() % 16 == 0 and aligned.stride(0) % 4 == 0
+    offset = torch.empty(m * p + 1, dtype=torch.float32, device=Mt.device)[1:].view(m, p)  # base 4 bytes off
+    padded = torch.empty(m, p + 1, dtype=torch.float32, device=Mt.device)[:, :p]  # row stride p + 1
+    outs = []
+    for out in (aligned, offset, padded):
+        out.copy_(base)
+        A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, gm, out, accumulate, prob.ws)
+        bmm.check_status(prob)
+        outs.append(host(out))
+    A.bmm_autotune_clear()
+    np.testing.assert_array_equal(outs[1], outs[0])
+    np.testing.assert_array_equal(outs[2], outs[0])
+
+
 def test_grouped_launch_mixed_choices(bmm):
     """bmm_apply_batched with products whose recorded tile widths differ: each product lands in the
     launch of its own width and equals its single-product result."""
