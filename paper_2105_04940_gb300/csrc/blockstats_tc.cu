@@ -178,8 +178,9 @@ struct OperandMaps {
 };
 
 // One product of a launch.  Outputs x, y [n] and a, s, mf, nf [K] are written in the statistics
-// pass (STATS) and read (s) in the Gram-only pass; f [K] is written by both.  wins [K + 2] is
-// workspace: the window starts (wins[0 .. W], wins[W] = K) and wins[K + 1] = W.
+// pass (STATS) and read (s) in the Gram-only pass; f [K] is written by both.  wins
+// [stats_windows_ints(K)] is workspace: the window starts (wins[0 .. W], wins[W] = K), wins[K + 1] = W,
+// wins[K + 2] = T and wins[K + 3 .. K + 3 + T) the order in which the last T windows are handed out.
 struct __align__(64) StatsProblem {
     OperandMaps mM, mN;
     const int64_t* off;
@@ -532,9 +533,15 @@ constexpr int kWinChunk = 2 * kWinThreads;  // blocks per pass through shared me
 // next, found by pointer doubling: after the round with jump J = next^(2^r), every next^i(0) with
 // i < 2^(r+1) is marked.  Writes wins[0 .. W] (window starts, wins[W] = K) and wins[K + 1] = W;
 // CTA 0 also zeroes the work counter of the statistics launch that follows.
+// The statistics kernel's CTAs claim windows in order, which lets neighbouring windows share their
+// edge boxes through L2, but leaves a tail: with about 4.5 windows of 1 to 4 boxes per CTA, the last
+// CTA to finish carries about 17% more than the mean.  So the launch's last product also gets a
+// hand-out order for its last T = min(W, tail) windows, largest first (by vector span, ties in block
+// order): wins[K + 2] = T and wins[K + 3 + r] = the window handed out r-th among them (T = 0 for
+// the other products).  Tail lengths of 3/4 of the CTAs cut the simulated excess to about 6%.
 template <typename T, int G>
 __global__ void __launch_bounds__(kWinThreads)
-    stats_windows_kernel(const __grid_constant__ StatsTable<G> tab, int* __restrict__ counter) {
+    stats_windows_kernel(const __grid_constant__ StatsTable<G> tab, int* __restrict__ counter, int tail) {
     __shared__ long long s_off[kWinChunk + 1];
     __shared__ int s_next[kWinChunk + 1];
     __shared__ unsigned char s_mark[kWinChunk];
@@ -613,6 +620,21 @@ __global__ void __launch_bounds__(kWinThreads)
         pr.wins[base] = (int)K;
         pr.wins[K + 1] = base;
     }
+    const int W = base;
+    const int nt = (int)blockIdx.x == tab.count - 1 ? (int)imin(imin(W, tail), kWinTailMax) : 0;
+    __syncthreads();  // every window start written above is visible to the block
+    for (int i = threadIdx.x; i < nt; i += kWinThreads) {
+        const int w = W - nt + i;
+        const long long lo = pr.off[pr.wins[w]], hi = pr.off[pr.wins[w + 1]];
+        s_off[i] = hi - lo + (lo & 31);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += kWinThreads) {
+        int rank = 0;
+        for (int j = 0; j < nt; ++j) rank += (s_off[j] > s_off[i]) || (s_off[j] == s_off[i] && j < i);
+        pr.wins[K + 3 + rank] = W - nt + i;
+    }
+    if (threadIdx.x == 0) pr.wins[K + 2] = nt;
 }
 
 template <typename T, bool STATS, int G>
@@ -693,7 +715,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // windows are claimed in increasing order, so this CTA's product index only grows
                 while (q + 1 < tab.count && kg >= s_wb[q + 1]) ++q;
                 const StatsProblem& pr = tab.prob[q];
-                const long long w = kg - s_wb[q];
+                long long w = kg - s_wb[q];
+                {  // the last windows of the launch's last product go out in the precomputed order
+                    const long long W = s_wb[q + 1] - s_wb[q];
+                    const int nt = pr.wins[pr.K + 2];
+                    if (nt > 0 && nt <= kWinTailMax && nt <= W && w >= W - nt) {
+                        const long long wt = pr.wins[pr.K + 3 + (w - (W - nt))];
+                        if (wt >= W - nt && wt < W) w = wt;
+                    }
+                }
                 const long long k = pr.wins[w], ke = pr.wins[w + 1];  // blocks k .. ke - 1
                 const bool range_ok = k >= 0 && ke > k && ke <= pr.K && ke - k <= kMaxBlock;
                 const long long lo = range_ok ? pr.off[k] : 0, hi = range_ok ? pr.off[ke] : 0;
@@ -1159,14 +1189,14 @@ cudaError_t launch_table(const StatsTable<G>& tab, int* counter, cudaStream_t s)
         attr = true;
     }
     if (tab.total_blocks == 0) return cudaSuccess;
-    // the windows of every product (and the zeroed work counter), then the pass over them
-    (count_launch(), stats_windows_kernel<T, G><<<tab.count, kWinThreads, 0, s>>>(tab, counter));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)imin(tab.total_blocks, sms);
+    // the windows of every product (and the zeroed work counter), then the pass over them
+    (count_launch(), stats_windows_kernel<T, G><<<tab.count, kWinThreads, 0, s>>>(tab, counter, 3 * grid / 4));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     (count_launch(), blockstats_tc_kernel<T, STATS, G><<<grid, kThreads, kSmem, s>>>(tab, counter));
     return cudaGetLastError();
 }

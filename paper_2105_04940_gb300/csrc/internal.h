@@ -113,7 +113,9 @@ struct StatsArgs {
     DevStatus* st;
     int* wins;  // workspace, stats_windows_ints(K) ints
 };
-inline int64_t stats_windows_ints(int64_t K) { return K + 2; }
+// window starts [K + 1], the window count, and the hand-out order of up to kWinTailMax last windows
+constexpr int kWinTailMax = 256;
+inline int64_t stats_windows_ints(int64_t K) { return K + 3 + kWinTailMax; }
 // Many products (each supported by blockstats_tc_supported) in launches of up to ~19 products of
 // one element type, every launch's CTAs sharing one work counter over all its blocks.
 cudaError_t launch_blockstats_tc_grouped(const StatsArgs* args, int64_t count, bool stats, int* counter, cudaStream_t s);
