@@ -80,14 +80,16 @@ def test_pair_tile_edges_accumulate(bmm, mode, m, p):
     assert not np.array_equal(outs[0], host(base))
 
 
+@pytest.mark.parametrize("mode", ["bf16", "e4m3"])
 @pytest.mark.parametrize("bn", [128, 256, 512])
 @pytest.mark.parametrize("accumulate", [False, True])
-def test_tma_store_epilogue_matches_plain_stores(bmm, bn, accumulate):
+def test_tma_store_epilogue_matches_plain_stores(bmm, mode, bn, accumulate):
     """An output whose base and row stride are 16-byte aligned is written by the epilogue's TMA tile
     stores (TMA reduce-adds when accumulating); one that is not takes plain stores.  Both give the
-    same bits, for every tile width, on ragged m and p."""
+    same bits, for every tile width and element kind (e4m3 scales its product in the epilogue), on
+    ragged m and p."""
     A = bmm._abi
-    gm = A.GEMM_BF16
+    gm = bmm.MODES[mode]
     m, p, L = 333, 272, 500
     off = S.block_offsets_uneven(3000, 30, 40, 160, seed=17)
     M, N = S.scaled_gaussian(m, 3000, p, off, 1.0, seed=18, dtype=np.float32)
