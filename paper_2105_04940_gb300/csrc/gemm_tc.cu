@@ -322,26 +322,31 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 const int col0 = tn * BN + cc * 32;
                 if (pr.tma_out) {
                     // this warp's 32 rows x 32 columns: row = lane, 16-byte chunk c of the row at
-                    // chunk c ^ (row mod 8) of its 128 bytes (the 128-byte swizzle the map expects)
+                    // chunk c ^ (row mod 8) of its 128 bytes (the 128-byte swizzle the map expects).
+                    // A block wholly past the matrix is neither staged nor stored, so that every
+                    // staged block is one bulk group and the wait below covers the store that last
+                    // read this buffer (the map clips rows >= M and columns >= N of the others).
                     const int row0 = row - lane;
-                    uint8_t* buf = sE + (q * 2 + (nchunk & 1)) * 4096;
-                    if (lane == 0) bulk_wait_read<1>();  // the store issued from this buffer two chunks ago has read it
-                    __syncwarp();
+                    if (row0 < M && col0 < N) {  // the same for every lane of the warp
+                        uint8_t* buf = sE + (q * 2 + (nchunk & 1)) * 4096;
+                        if (lane == 0) bulk_wait_read<1>();  // the store issued from this buffer before has read it
+                        __syncwarp();
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        *reinterpret_cast<float4*>(buf + lane * 128 + ((c ^ (lane & 7)) << 4)) =
-                            make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
-                                        __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0 && row0 < M && col0 < N) {  // the map clips rows >= M and columns >= N
-                        if (pr.accumulate)
-                            tma_reduce_add_2d(&pr.mapO, smem_u32(buf), col0, row0);
-                        else
-                            tma_store_2d(&pr.mapO, smem_u32(buf), col0, row0);
-                        bulk_commit();
+                        for (int c = 0; c < 8; ++c)
+                            *reinterpret_cast<float4*>(buf + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+                                make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
+                                            __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            if (pr.accumulate)
+                                tma_reduce_add_2d(&pr.mapO, smem_u32(buf), col0, row0);
+                            else
+                                tma_store_2d(&pr.mapO, smem_u32(buf), col0, row0);
+                            bulk_commit();
+                        }
+                        ++nchunk;
                     }
-                    ++nchunk;
                 } else if (row < M && col0 < N) {
                     float* o = pr.out + (long long)row * pr.ldo + col0;
                     if (pr.vec_ok && col0 + 32 <= N) {

@@ -114,6 +114,36 @@ def test_tma_store_epilogue_matches_plain_stores(bmm, mode, bn, accumulate):
     np.testing.assert_array_equal(outs[2], outs[0])
 
 
+@pytest.mark.parametrize("bn", [128, 256, 512])
+@pytest.mark.parametrize("p", [272, 300])
+def test_tma_epilogue_repeatable_at_ragged_edges(bmm, bn, p):
+    """Where the last column tile holds chunks wholly past the matrix (p = 272, 300), the epilogue
+    stages and stores only the others, so a staging buffer is never refilled while a store that
+    reads it is in flight: twelve repetitions of the TMA-store product (plain and accumulating)
+    equal the plain-store product bit for bit every time."""
+    A = bmm._abi
+    gm = A.GEMM_BF16
+    m, L = 700, 900
+    off = S.block_offsets_uneven(3000, 40, 40, 110, seed=81)
+    M, N = S.scaled_gaussian(m, 3000, p, off, 1.0, seed=82, dtype=np.float32)
+    Mt, Nt = to_dev(M), to_dev(N)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=gm)
+    r = bmm.run(prob, "ONC", L, seed=4, compute_product=False)
+    A.bmm_autotune_clear()
+    A.bmm_autotune_set(m, p, L, gm, bn, 8)
+    plain = torch.empty(m * p + 1, dtype=torch.float32, device=Mt.device)[1:].view(m, p)  # no TMA: base 4 bytes off
+    A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, gm, plain, False, prob.ws)
+    want = host(plain).copy()
+    out = torch.empty(m, p, dtype=torch.float32, device=Mt.device)
+    for rep in range(12):
+        out.fill_(float("nan"))
+        A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, gm, out, False, prob.ws)
+        A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, gm, out, True, prob.ws)
+        bmm.check_status(prob)
+        np.testing.assert_array_equal(host(out), 2 * want, err_msg=f"repetition {rep}")
+    A.bmm_autotune_clear()
+
+
 def test_grouped_launch_mixed_choices(bmm):
     """bmm_apply_batched with products whose recorded tile widths differ: each product lands in the
     launch of its own width and equals its single-product result."""

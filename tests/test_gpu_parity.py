@@ -788,6 +788,57 @@ def test_overlapped_apply_large_product(bmm, layout):
     np.testing.assert_allclose(host(out2)[rows], 2 * got[rows], rtol=2e-6, atol=1e-6 * np.abs(got).max())
 
 
+@pytest.mark.parametrize("bn", [128, 256, 512])
+@pytest.mark.parametrize("m,L", [(64, 37), (333, 700), (1000, 130)])
+def test_apply_equals_grouped_apply(bmm, bn, m, L):
+    """bmm_apply against the grouped path (bmm_apply_batched, whose gathers and GEMM are table-driven
+    launches over products): the same product bit for bit for every tile width, with fewer rows
+    than one 128-row tile, ragged tiles, fewer draws than one 64-column unit, and with
+    accumulate."""
+    A = bmm._abi
+    n, p, K = 2400, 270, 30
+    off, M, N, Mt, Nt = _problem(m, n, p, K, seed=m + L, dtype=np.float32, lo=40, hi=120)
+    assert Mt.stride(1) == 1 and Mt.dtype == torch.float32
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    r = bmm.run(prob, "ONC", L, seed=6, gemm_mode=A.GEMM_BF16, compute_product=False)
+    A.bmm_autotune_clear()
+    A.bmm_autotune_set(m, p, L, A.GEMM_BF16, bn, 8)
+    base = torch.from_numpy(np.random.default_rng(m).standard_normal((m, p)).astype(np.float32)).to(Mt.device)
+    for accumulate in (False, True):
+        fused, sep = base.clone(), base.clone()
+        A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, A.GEMM_BF16, fused, accumulate, prob.ws)
+        A.bmm_apply_batched([Mt], [Nt], [prob.B], A.UNIT_COLUMN, [r["idx"]], [r["scale"]], [L], A.GEMM_BF16, [sep],
+                            accumulate, [prob.ws])
+        bmm.check_status(prob)
+        np.testing.assert_array_equal(host(fused), host(sep), err_msg=f"accumulate={accumulate}")
+    A.bmm_autotune_clear()
+
+
+def test_apply_reports_a_bad_index(bmm):
+    """A draw index outside M's columns: bmm_apply and the grouped path both record BMM_ERR_ARG on the
+    device and use zeros for that column, so their outputs still agree."""
+    A = bmm._abi
+    m, n, p, K, L = 300, 2000, 200, 25, 400
+    off, M, N, Mt, Nt = _problem(m, n, p, K, seed=91, dtype=np.float32, lo=40, hi=120)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    r = bmm.run(prob, "ONC", L, seed=3, gemm_mode=A.GEMM_BF16, compute_product=False)
+    idx = r["idx"].clone()
+    idx[17] = n + 5
+    outs = []
+    for single in (True, False):
+        out = torch.empty(m, p, dtype=torch.float32, device=Mt.device)
+        A.bmm_clear_device_status(prob.ws)
+        if single:
+            A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, idx, r["scale"], L, A.GEMM_BF16, out, False, prob.ws)
+        else:
+            A.bmm_apply_batched([Mt], [Nt], [prob.B], A.UNIT_COLUMN, [idx], [r["scale"]], [L], A.GEMM_BF16, [out],
+                                False, [prob.ws])
+        assert A.bmm_read_device_status(prob.ws) == A.ERR_ARG
+        outs.append(host(out))
+    A.bmm_clear_device_status(prob.ws)
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("layout", ["row", "col"])
 def test_apply_parts_equal_one_apply(bmm, layout):
     """bmm_apply_part's three parts, in any row split (multiples of 128, the last ending at m) and on
