@@ -439,8 +439,10 @@ uint64_t bmm_launch_count(void);
  * or three times 64-rounded L (split BF16).  Its tile width and raster group (4, 8 or 16 row tiles
  * walked together for L2 reuse) come from a process-wide table keyed by the element kind and the
  * base-2 logarithms (rounded up) of M, N and K.  Tile widths: BN = 128 or 256 (one SM per 128 x BN
- * output tile) or BMM_TILE_PAIR (two SMs of a thread-block cluster per 256 x 256 tile, cta_group::2
- * MMAs, each SM loading half of the tile's A and B rows).  Shapes not in the table use BN = 128
+ * output tile), BMM_TILE_PAIR (two SMs of a thread-block cluster per 256 x 256 tile, cta_group::2
+ * MMAs, each SM loading half of the tile's A and B rows) or BMM_TILE_PAIR_WIDE (the same per
+ * 256 x 512 tile: fewer operand bytes per MMA, one accumulator, so its epilogue does not overlap
+ * the next tile's MMAs).  Shapes not in the table use BN = 128
  * when N <= 128, else 256 when M <= 128, else BMM_TILE_PAIR, and a raster group of 8.  No choice changes any result bit: each output
  * element is the same dot product in the same order.
  * gemm_mode: BMM_GEMM_BF16, BMM_GEMM_SPLIT_BF16 or BMM_GEMM_E4M3 (else BMM_ERR_ARG). */
@@ -459,8 +461,9 @@ bmm_status bmm_autotune_gemm(int64_t m, int64_t p, int64_t L, int32_t gemm_mode,
 bmm_status bmm_autotune_get(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, int32_t* bn_out,
                             int32_t* raster_out);
 #define BMM_TILE_PAIR 512
-/* Records a choice for the shape's bucket (bn 128, 256 or BMM_TILE_PAIR, raster 4, 8 or 16; else
- * BMM_ERR_ARG). */
+#define BMM_TILE_PAIR_WIDE 1024
+/* Records a choice for the shape's bucket (bn 128, 256, BMM_TILE_PAIR or BMM_TILE_PAIR_WIDE, raster
+ * 4, 8 or 16; else BMM_ERR_ARG). */
 bmm_status bmm_autotune_set(int64_t m, int64_t p, int64_t L, int32_t gemm_mode, int32_t bn, int32_t raster);
 /* Forgets every recorded choice. */
 void bmm_autotune_clear(void);

@@ -25,6 +25,7 @@ GEMM_F64, GEMM_BF16, GEMM_SPLIT_BF16, GEMM_E4M3 = 0, 1, 2, 3
 PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
 APPLY_GATHER_B, APPLY_GATHER_A, APPLY_GEMM = 0, 1, 2
 TILE_PAIR = 512  # GEMM tile choice: a CTA pair per 256 x 256 tile
+TILE_PAIR_WIDE = 1024  # a CTA pair per 256 x 512 tile
 
 EXPORTED = (
     "bmm_workspace_size", "bmm_probs", "bmm_blocksizes", "bmm_sample", "bmm_apply", "bmm_backward",

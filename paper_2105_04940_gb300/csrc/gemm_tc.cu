@@ -37,27 +37,33 @@ using namespace ptx;
 constexpr int BM = 128;
 constexpr int ROW_BYTES = 128;  // K per stage: one 128-byte swizzled row
 
-// EK: element kind, 0 = BF16 (kind::f16), 1 = FP8 e4m3 (kind::f8f6f4).  PAIR: CTA-pair tiles
-// (BN = 256 only): TILE_M = 256 output rows per tile, 128 per CTA, and B_ROWS = 128 rows of B per CTA.
+// EK: element kind, 0 = BF16 (kind::f16), 1 = FP8 e4m3 (kind::f8f6f4).  PAIR: CTA-pair tiles of
+// TILE_M = 256 output rows (128 per CTA) by BN = 256 or 512 columns, B_ROWS = BN / 2 rows of B per
+// CTA; each K step is BN / 256 pair MMAs of N = 256.  The 256 x 512 tile keeps one 512-column
+// accumulator (its epilogue does not overlap the next tile's MMAs) and needs 47 B of copies per
+// cycle per SM at the math rate against the 256 x 256 tile's 64.
 template <int BN, int EK, bool PAIR = false> struct Cfg {
-    static_assert(!PAIR || BN == 256, "CTA-pair tiles are 256 x 256");
+    static_assert(!PAIR || BN == 256 || BN == 512, "CTA-pair tiles are 256 x 256 or 256 x 512");
     static constexpr int ESIZE = EK ? 1 : 2;
     static constexpr int BK = ROW_BYTES / ESIZE;       // elements of K per stage
     static constexpr int KMMA = 32 / ESIZE;            // elements of K per MMA (32 bytes)
     static constexpr int TILE_M = PAIR ? 2 * BM : BM;
     static constexpr int B_ROWS = PAIR ? BN / 2 : BN;
-    static constexpr int STAGES = PAIR ? 6 : ((BN == 256) ? 4 : 6);
+    static constexpr int NMMA = PAIR ? BN / 256 : 1;  // MMAs per K step
+    static constexpr int MMA_N = PAIR ? 256 : BN;
+    static constexpr int ACCS = (PAIR && BN == 512) ? 1 : 2;  // accumulators in TMEM
+    static constexpr int STAGES = PAIR ? (BN == 512 ? 4 : 6) : ((BN == 256) ? 4 : 6);
     static constexpr int A_BYTES = BM * ROW_BYTES;
     static constexpr int B_BYTES = B_ROWS * ROW_BYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr uint32_t STAGE_TX = (PAIR ? 2u : 1u) * (uint32_t)STAGE_BYTES;  // bytes a full barrier awaits
-    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr int TMEM_COLS = ACCS * BN;
     static constexpr int EPI_BYTES = 4 * 2 * 32 * 32 * 4;  // 4 epilogue warps x 2 buffers x 32 x 32 FP32
     static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
     // instruction descriptor: D=F32 (bits 4-5); A, B format (bits 7-9, 10-12): BF16 = 1 for
     // kind::f16, E4M3 = 0 for kind::f8f6f4; both K-major, N>>3 at bits 17-22, M>>4 at bits 24-28
     static constexpr uint32_t FMT = EK ? 0u : 1u;
-    static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) |
+    static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
                                       ((uint32_t)(TILE_M >> 4) << 24);
 };
 
@@ -235,8 +241,8 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         for (int tile = first_tile; tile < num_tiles && !aborted; tile += tile_step, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             const int num_kb = problem_kb<BK>(pr);
-            const int acc = it & 1;
-            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            const int acc = C::ACCS == 2 ? (it & 1) : 0;
+            const uint32_t aph = C::ACCS == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
             if (!wait_fast(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
                 aborted = true;
                 break;
@@ -255,10 +261,16 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 for (int k = 0; k < BK / C::KMMA; ++k) {
                     const uint32_t acc_in = (kb > 0 || k > 0) ? 1u : 0u;
                     if constexpr (PAIR) {
-                        if (EK)
-                            tc_mma_f8_pair(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
-                        else
-                            tc_mma_bf16_pair(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
+                        // MMA h: B rows 128 h .. 128 h + 127 of each CTA into accumulator columns 256 h ..
+#pragma unroll
+                        for (int h = 0; h < C::NMMA; ++h) {
+                            const uint32_t dh = d + (uint32_t)(256 * h);
+                            const uint64_t bh = bd + (uint64_t)((h * 128 * ROW_BYTES) >> 4) + 2ull * k;
+                            if (EK)
+                                tc_mma_f8_pair(dh, ad + 2ull * k, bh, C::IDESC, acc_in);
+                            else
+                                tc_mma_bf16_pair(dh, ad + 2ull * k, bh, C::IDESC, acc_in);
+                        }
                     } else {
                         if (EK)
                             tc_mma_f8(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
@@ -296,8 +308,8 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         for (int tile = first_tile; tile < num_tiles; tile += tile_step, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             const int num_kb = problem_kb<BK>(pr);
-            const int acc = it & 1;
-            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            const int acc = C::ACCS == 2 ? (it & 1) : 0;
+            const uint32_t aph = C::ACCS == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
             if (!mbar_wait(smem_u32(&bar_tfull[acc]), aph, &s_abort)) break;
             tc_fence_after();
             int tm, tn;
@@ -319,7 +331,15 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
 #pragma unroll
                     for (int e = 0; e < 32; ++e) r[e] = __float_as_uint(__uint_as_float(r[e]) * sc);
                 }
-                const int col0 = tn * BN + cc * 32;
+                // accumulator column c: MMA h = c / 256; its columns w = c mod 256 below 128 are the
+                // even CTA's B rows 128 h + w, the others the odd CTA's, which holds tile columns
+                // B_ROWS .. 2 B_ROWS - 1
+                int tcol = cc * 32;
+                if constexpr (PAIR) {
+                    const int h = tcol / 256, w = tcol % 256;
+                    tcol = w < 128 ? 128 * h + w : C::B_ROWS + 128 * h + (w - 128);
+                }
+                const int col0 = tn * BN + tcol;
                 if (pr.tma_out) {
                     // this warp's 32 rows x 32 columns: row = lane, 16-byte chunk c of the row at
                     // chunk c ^ (row mod 8) of its 128 bytes (the 128-byte swizzle the map expects).
@@ -462,8 +482,9 @@ bool fill_problem(GemmProblem* pr, int bn, int raster, const void* A, int64_t ld
                   int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
                   int64_t ldo, int accumulate, int elem, const float* scale) {
     const int esize = elem == GEMM_ELEM_E4M3 ? 1 : 2;
-    const bool pair = bn == kPairTile;
-    const int tile_m = pair ? 2 * BM : BM, tile_n = pair ? 256 : bn, b_rows = pair ? 128 : bn;
+    const bool pair = bn == kPairTile || bn == kPairTileWide;
+    const int tile_m = pair ? 2 * BM : BM, tile_n = bn == kPairTileWide ? 512 : (pair ? 256 : bn);
+    const int b_rows = pair ? tile_n / 2 : bn;
     if (!make_map(&pr->mapA, A, M, kdim, lda, BM, esize) || !make_map(&pr->mapB, B, N, kdim, ldb, b_rows, esize))
         return false;
     pr->scale = scale;
@@ -537,9 +558,11 @@ cudaError_t launch_table(const GemmTable<G>& tab, DevStatus* st, cudaStream_t s)
 template <int G>
 cudaError_t launch_any(int bn, int elem, const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
     if (elem == GEMM_ELEM_E4M3) {
+        if (bn == kPairTileWide) return launch_table<512, G, 1, true>(tab, st, s);
         if (bn == kPairTile) return launch_table<256, G, 1, true>(tab, st, s);
         return bn == 128 ? launch_table<128, G, 1, false>(tab, st, s) : launch_table<256, G, 1, false>(tab, st, s);
     }
+    if (bn == kPairTileWide) return launch_table<512, G, 0, true>(tab, st, s);
     if (bn == kPairTile) return launch_table<256, G, 0, true>(tab, st, s);
     return bn == 128 ? launch_table<128, G, 0, false>(tab, st, s) : launch_table<256, G, 0, false>(tab, st, s);
 }
@@ -587,7 +610,8 @@ TileChoice gemm_tile_choice(int elem, int64_t M, int64_t N, int64_t K) {
 }
 
 bool gemm_tile_valid(const TileChoice& c) {
-    return (c.bn == 128 || c.bn == 256 || c.bn == kPairTile) && (c.raster == 4 || c.raster == 8 || c.raster == 16);
+    return (c.bn == 128 || c.bn == 256 || c.bn == kPairTile || c.bn == kPairTileWide) &&
+           (c.raster == 4 || c.raster == 8 || c.raster == 16);
 }
 
 void gemm_tile_set(int elem, int64_t M, int64_t N, int64_t K, const TileChoice& c) {
@@ -630,9 +654,9 @@ cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, Dev
     // products are grouped by tile width and element kind; each launch takes up to kMaxGroup of them
     std::vector<TileChoice> choice((size_t)count);
     for (int64_t i = 0; i < count; ++i) choice[i] = gemm_tile_choice(args[i].elem, args[i].M, args[i].N, args[i].kdim);
-    for (int pass = 0; pass < 6; ++pass) {
-        const int BN = pass % 3 == 0 ? 128 : (pass % 3 == 1 ? 256 : kPairTile);
-        const int elem = pass / 3;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int BN = pass % 4 == 0 ? 128 : (pass % 4 == 1 ? 256 : (pass % 4 == 2 ? kPairTile : kPairTileWide));
+        const int elem = pass / 4;
         static GemmTable<kMaxGroup> tab;  // host-side staging of the kernel parameter (30 KB)
         tab.count = 0;
         tab.total_tiles = 0;
@@ -695,7 +719,7 @@ cudaError_t gemm_autotune(int64_t M, int64_t N, int64_t K, int elem, void* scrat
     if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
     TileChoice best{0, 0};
     float best_t = 0.f;
-    for (int bn : {128, 256, kPairTile}) {
+    for (int bn : {128, 256, kPairTile, kPairTileWide}) {
         for (int raster : {4, 8, 16}) {
             GemmTable<1> tab;
             tab.count = 1;

@@ -240,7 +240,8 @@ cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, Dev
 // Tile width (BN, 128 or 256: one CTA per 128 x BN tile; kPairTile: a CTA pair per 256 x 256 tile)
 // and raster group (4, 8 or 16 M-tiles) of a tensor-core GEMM: from the autotuner's table when the
 // shape's bucket was tuned, else BN = 128 for N <= 128, 256 for M <= 128, else kPairTile; group 8.
-constexpr int kPairTile = 512;
+constexpr int kPairTile = 512;       // a CTA pair per 256 x 256 tile
+constexpr int kPairTileWide = 1024;  // a CTA pair per 256 x 512 tile
 struct TileChoice {
     int bn, raster;
 };

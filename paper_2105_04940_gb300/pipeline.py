@@ -460,7 +460,7 @@ def autotune_batched(probs: list, results: list, cs, gemm_mode: int = A.GEMM_BF1
             A.bmm_autotune_set(m, p, L, gemm_mode, bn, ra)
 
     policies = {"default": A.bmm_autotune_clear}
-    for bn in (128, 256, A.TILE_PAIR):
+    for bn in (128, 256, A.TILE_PAIR, A.TILE_PAIR_WIDE):
         for ra in (4, 8, 16):
             policies[f"bn{bn}/r{ra}"] = (lambda bn=bn, ra=ra: uniform(bn, ra))
     policies["per_shape"] = lambda: (A.bmm_autotune_clear(), autotune(shapes, gemm_mode, probs[0].M.device))

@@ -83,7 +83,7 @@ def test_autotune_table_host_side():
     assert A.bmm_autotune_get(300, 520, 517, A.GEMM_E4M3) == {"bn": A.TILE_PAIR, "raster": 8}  # element kind differs
     A.bmm_autotune_set(300, 520, 517, A.GEMM_BF16, A.TILE_PAIR, 4)
     assert A.bmm_autotune_get(300, 520, 517, A.GEMM_BF16) == {"bn": A.TILE_PAIR, "raster": 4}
-    for bad in ((300, 520, 517, A.GEMM_BF16, 192, 8), (300, 520, 517, A.GEMM_BF16, 128, 5), (300, 520, 517, A.GEMM_BF16, 1024, 8),
+    for bad in ((300, 520, 517, A.GEMM_BF16, 192, 8), (300, 520, 517, A.GEMM_BF16, 128, 5), (300, 520, 517, A.GEMM_BF16, 2048, 8),
                 (300, 520, 517, A.GEMM_F64, 128, 8), (0, 520, 517, A.GEMM_BF16, 128, 8)):
         with pytest.raises(A.BmmError):
             A.bmm_autotune_set(*bad)

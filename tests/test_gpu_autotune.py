@@ -9,7 +9,7 @@ from tests._gpu_util import host, to_dev
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-CHOICES = [(bn, r) for bn in (128, 256, 512) for r in (4, 8, 16)]  # 512: the CTA-pair tile
+CHOICES = [(bn, r) for bn in (128, 256, 512, 1024) for r in (4, 8, 16)]  # 512, 1024: CTA-pair tiles
 
 
 @pytest.fixture(scope="module")
@@ -55,9 +55,9 @@ def test_tile_choices_do_not_change_results(bmm, mode):
 @pytest.mark.parametrize("mode", ["bf16", "e4m3"])
 @pytest.mark.parametrize("m,p", [(64, 40), (130, 260), (256, 256), (390, 129)])
 def test_pair_tile_edges_accumulate(bmm, mode, m, p):
-    """The CTA-pair tile against the single-CTA 128 x 128 tile, bit for bit, on shapes where the odd
-    CTA's rows of A or of B lie wholly or partly past the matrix (m < 128, ragged m and p), adding
-    into a prefilled output."""
+    """The CTA-pair tiles (256 x 256 and 256 x 512) against the single-CTA 128 x 128 tile, bit for bit,
+    on shapes where the odd CTA's rows of A or of B lie wholly or partly past the matrix (m < 128,
+    ragged m and p), adding into a prefilled output."""
     A = bmm._abi
     gm = bmm.MODES[mode]
     off = S.block_offsets_uneven(2000, 25, 40, 120, seed=m + p)
@@ -68,7 +68,7 @@ def test_pair_tile_edges_accumulate(bmm, mode, m, p):
     r = bmm.run(prob, "ONC", L, seed=5, compute_product=False)
     base = torch.from_numpy(np.random.default_rng(m).standard_normal((m, p)).astype(np.float32)).to(Mt.device)
     outs = []
-    for bn in (128, A.TILE_PAIR):
+    for bn in (128, A.TILE_PAIR, A.TILE_PAIR_WIDE):
         A.bmm_autotune_clear()
         A.bmm_autotune_set(m, p, L, gm, bn, 8)
         out = base.clone()
@@ -77,11 +77,12 @@ def test_pair_tile_edges_accumulate(bmm, mode, m, p):
         outs.append(host(out))
     A.bmm_autotune_clear()
     np.testing.assert_array_equal(outs[1], outs[0])
+    np.testing.assert_array_equal(outs[2], outs[0])
     assert not np.array_equal(outs[0], host(base))
 
 
 @pytest.mark.parametrize("mode", ["bf16", "e4m3"])
-@pytest.mark.parametrize("bn", [128, 256, 512])
+@pytest.mark.parametrize("bn", [128, 256, 512, 1024])
 @pytest.mark.parametrize("accumulate", [False, True])
 def test_tma_store_epilogue_matches_plain_stores(bmm, mode, bn, accumulate):
     """An output whose base and row stride are 16-byte aligned is written by the epilogue's TMA tile
@@ -114,7 +115,7 @@ def test_tma_store_epilogue_matches_plain_stores(bmm, mode, bn, accumulate):
     np.testing.assert_array_equal(outs[2], outs[0])
 
 
-@pytest.mark.parametrize("bn", [128, 256, 512])
+@pytest.mark.parametrize("bn", [128, 256, 512, 1024])
 @pytest.mark.parametrize("p", [272, 300])
 def test_tma_epilogue_repeatable_at_ragged_edges(bmm, bn, p):
     """Where the last column tile holds chunks wholly past the matrix (p = 272, 300), the epilogue
@@ -159,7 +160,7 @@ def test_grouped_launch_mixed_choices(bmm):
         probs.append(pr)
         samples.append(r)
         cs.append(600)
-        A.bmm_autotune_set(m, p, 600, gm, (128, 256, A.TILE_PAIR)[i % 3], (4, 8, 16)[(i + 1) % 3])
+        A.bmm_autotune_set(m, p, 600, gm, (128, 256, A.TILE_PAIR, A.TILE_PAIR_WIDE)[i % 4], (4, 8, 16)[(i + 1) % 3])
     single = []
     for pr, r in zip(probs, samples):
         out = torch.empty(pr.M.shape[0], pr.N.shape[1], dtype=torch.float32, device=pr.M.device)
@@ -190,7 +191,7 @@ def test_batch_level_tuning_keeps_results(bmm):
     res = bmm.run_batched(probs, "ONC", cs, [1, 2, 3], gemm_mode=A.GEMM_BF16)
     before = [host(r["out"]).copy() for r in res]
     tune = bmm.autotune_batched(probs, res, cs, A.GEMM_BF16)
-    assert tune["choice"] in tune["ms"] and len(tune["ms"]) == 11
+    assert tune["choice"] in tune["ms"] and len(tune["ms"]) == 14
     res2 = bmm.run_batched(probs, "ONC", cs, [1, 2, 3], gemm_mode=A.GEMM_BF16)
     for a_, r in zip(before, res2):
         np.testing.assert_array_equal(host(r["out"]), a_)

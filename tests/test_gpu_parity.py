@@ -788,7 +788,7 @@ def test_overlapped_apply_large_product(bmm, layout):
     np.testing.assert_allclose(host(out2)[rows], 2 * got[rows], rtol=2e-6, atol=1e-6 * np.abs(got).max())
 
 
-@pytest.mark.parametrize("bn", [128, 256, 512])
+@pytest.mark.parametrize("bn", [128, 256, 512, 1024])
 @pytest.mark.parametrize("m,L", [(64, 37), (333, 700), (1000, 130)])
 def test_apply_equals_grouped_apply(bmm, bn, m, L):
     """bmm_apply against the grouped path (bmm_apply_batched, whose gathers and GEMM are table-driven
