@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--stats", default="auto", choices=["auto", "fused", "split"],
                     help="fused: one statistics pass computes the norms and f_k; split: the norm pass, then the "
                          "Gram-only f_k pass; auto: fused for one product, split for the batched workload")
+    ap.add_argument("--schedule", default="pipelined", choices=["pipelined", "sequential"],
+                    help="pipelined: the timed products run two in flight (run_pipelined; OPL, BF16, fused "
+                         "statistics pass), the per-stage times come from a sequential pass; sequential: one "
+                         "product after another")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "mlp", "precision", "paper"],
                     help="batched: 512 independent BF16 products of uneven shapes in one CUDA graph; "
                          "mlp: 4-layer GELU MLP with sampled products, forward and backward")
@@ -419,36 +423,59 @@ def native_arm(args, ws, rank, local):
         return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events,
                      fused_stats=args.stats != "split")
 
+    pipelined = (args.schedule == "pipelined" and args.method == "OPL" and args.mode == "bf16"
+                 and args.stats != "split")
+    if pipelined:
+        # a second problem state and output for the product in flight beside the current one
+        probs = [prob, P.prepare(M, N, off, max_draws=L, gemm_mode=gm)]
+        outs = [out, torch.empty_like(out)]
+
     last = None
     for s in range(args.warmup):
         last = step(10_000 + s)
+    if pipelined:
+        P.run_pipelined(probs, c, range(20_000, 20_000 + args.warmup), outs, replicate=rank)
     torch.cuda.synchronize()
     P.check_status(prob)
 
-    # ---- timed region: K steps, per-stage events on the launching (current) stream
+    def timed(fn):
+        barrier(ws)
+        torch.cuda.synchronize()
+        n0 = P._abi.bmm_launch_count()
+        with ClockSampler(local) as clk:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            fn()
+            t1.record()
+            torch.cuda.synchronize()
+        barrier(ws)
+        return max_over_ranks(t0.elapsed_time(t1), ws, dev), P._abi.bmm_launch_count() - n0, clk.summary()
+
+    # ---- sequential pass: K steps, per-stage events on the launching (current) stream
     stage_ev = []
-    barrier(ws)
-    torch.cuda.synchronize()
-    n_launch0 = P._abi.bmm_launch_count()
-    with ClockSampler(local) as clk:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record()
+
+    def sequential():
         for s in range(args.steps):
             ev = []
             step(s, ev)
             stage_ev.append(ev)
-        t_end.record()
-        torch.cuda.synchronize()
-    barrier(ws)
-    launches = P._abi.bmm_launch_count() - n_launch0
-    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), ws, dev)
+
+    seq_ms, launches, clocks = timed(sequential)
     P.check_status(prob)
     stages = {}
     for ev in stage_ev:
         for (a, ea), (b, eb) in zip(ev[:-1], ev[1:]):
             stages[b] = stages.get(b, 0.0) + ea.elapsed_time(eb)
     stages = {k: v / args.steps for k, v in stages.items()}
+    elapsed_ms = seq_ms
+    if pipelined:
+        # ---- timed region: the same K products (same seeds), two in flight
+        elapsed_ms, launches, clocks = timed(lambda: P.run_pipelined(probs, c, range(args.steps), outs,
+                                                                      replicate=rank))
+        for pr in probs:
+            P.check_status(pr)
+        del probs[1], outs[1]
     ms_step = elapsed_ms / args.steps
     value = elapsed_ms / (args.steps * ws)
 
@@ -496,11 +523,14 @@ def native_arm(args, ws, rank, local):
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": args.mode, "data": "synthetic",
         "norm_pass_alone": norm_alone, "gemm_part_alone": gemm_alone,
+        "sequential_ms_per_step": seq_ms / args.steps,
         "config": {"workload": workload_name(args), "method": args.method, "gemm": args.mode, "c": c,
+                   "schedule": ("two products in flight (run_pipelined: the next product's statistics pass "
+                                "beside this product's design and gathers)") if pipelined else "sequential",
                    "l2": "small case, L2-resident" if args.small else "inputs larger than the 129 MB L2, no flush",
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline, "stages_ms": stages, "stage_rooflines": roof_all,
-        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "clocks": clocks, "gpu_launches": int(launches),
         "autotune": {f"{k[0]}x{k[1]}xL{k[2]}": v for k, v in tuned.items()},
     }
 
@@ -741,7 +771,7 @@ def mlp_run(args, ws, rank, local):
         "config": {"workload": "MLP: X 4096x16384 BF16, 4 layers W 16384x16384, GELU, OPL K=256 blocks of 64, "
                                "c=64 blocks (L=4096), forward + backward", "parallelism": f"replicas x{ws}"},
         "exact_bf16_mlp_ms": exact_ms, "sampled_gemm_tflop_per_step": gemm_flops / 1e12,
-        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "clocks": clocks, "gpu_launches": int(launches),
     }
     del X, Ws, R
     torch.cuda.empty_cache()

@@ -12,7 +12,8 @@ from ._abi import (BmmError, bmm_apply, bmm_apply_batched, bmm_backward, bmm_blo
                    bmm_entry_estimate, bmm_entry_variance, bmm_error_report, bmm_probs, bmm_probs_batched,
                    bmm_read_device_status, bmm_sample, bmm_workspace_size)
 from .pipeline import (METHODS, MODES, Problem, SampledMatmul, autotune, autotune_batched, check_status, equal_budget,
-                       error_bars, error_report, prepare, run, run_batched, sampled_matmul, stream_id)
+                       error_bars, error_report, prepare, run, run_batched, run_pipelined, sampled_matmul,
+                       stream_id)
 
 __all__ = [
     "BmmError", "bmm_apply", "bmm_apply_batched", "bmm_backward", "bmm_blocksizes", "bmm_blocksizes_batched",

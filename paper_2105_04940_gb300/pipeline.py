@@ -125,8 +125,8 @@ _SIDE: dict = {}
 
 
 def _side_stream(dev):
-    """A high-priority stream per device for the GEMM halves of the overlapped apply (created once,
-    outside any graph capture that uses it)."""
+    """A high-priority stream per device for the GEMM halves of the overlapped apply and for the
+    design and gathers of run_pipelined (created once, outside any graph capture that uses it)."""
     torch = _torch()
     s = _SIDE.get(str(dev))
     if s is None:
@@ -289,6 +289,67 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
         mark("apply")
     res.update(p=p, ck=ck, g=g, idx=idx, scale=scale, unit=A.UNIT_COLUMN, out=out)
     return res
+
+
+def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEMM_BF16, replicate: int = 0) -> None:
+    """Alg. 2 with eq. 3.8 / 3.9 (OPL, tensor-core f_k, fused statistics pass, column sampling) on a
+    sequence of independent products, two in flight: product i + 1's statistics pass (bound by
+    shared-memory traffic, leaving HBM bandwidth free) runs beside product i's block sizes, draws and
+    gathers (on a high-priority side stream), and product i's GEMM follows, so a long sequence takes
+    about a statistics pass plus a GEMM per product instead of the whole chain.  Every product is the
+    same computation as run() with its seed, bit for bit.
+
+    probs: two or more Problem states (prepared with max_draws >= c) over the inputs, used round-robin
+    (product i works in probs[i % len(probs)]); seeds: one per product; outs: output matrices used
+    round-robin (product i writes outs[i % len(outs)], which keeps it until product i + len(outs)
+    overwrites it); replicate: as in run().  Enqueues everything on the current stream and the side
+    stream and returns; the current stream has joined the side stream when it returns.  Device status
+    is read with check_status() on each state, as after run()."""
+    torch = _torch()
+    if len(probs) < 2 or not outs:
+        raise ValueError("run_pipelined needs two or more problem states and an output")
+    if gemm_mode != A.GEMM_BF16:
+        raise ValueError("run_pipelined runs the BF16 sampled GEMM")
+    seeds = list(seeds)
+    dev = probs[0].M.device
+    main = torch.cuda.current_stream(dev)
+    side = _side_stream(dev)
+    sid = stream_id(replicate, A.PURPOSE_MAIN)
+    bufs = []
+    for pr in probs:
+        K, n = pr.B.K, pr.B.n
+        bufs.append(dict(p=torch.empty(n, dtype=torch.float64, device=dev), ck=torch.empty(K, dtype=torch.int64, device=dev),
+                         g=torch.empty(K, dtype=torch.float64, device=dev), idx=torch.empty(c, dtype=torch.int32, device=dev),
+                         scale=torch.empty(c, dtype=torch.float64, device=dev)))
+
+    def stats(i):
+        pr, b = probs[i % len(probs)], bufs[i % len(probs)]
+        A.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_TC, b["p"], pr.st, pr.ws, main)
+        ev = torch.cuda.Event()
+        ev.record(main)
+        return ev
+
+    if not seeds:
+        return
+    side.wait_stream(main)
+    ev_stats = stats(0)
+    for i, seed in enumerate(seeds):
+        pr, b, out = probs[i % len(probs)], bufs[i % len(probs)], outs[i % len(outs)]
+        m = int(pr.M.shape[0])
+        side.wait_event(ev_stats)
+        A.bmm_blocksizes(pr.M, pr.N, pr.B, pr.st, A.CK_OPT, c, None, None, 0, b["ck"], b["g"], None, pr.ws, side)
+        A.bmm_sample(b["p"], A.UNIT_COLUMN, pr.B, b["ck"], c, seed, sid, b["idx"], b["scale"], pr.ws, side)
+        A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GATHER_B, 0, 0, pr.ws, side)
+        A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GATHER_A, 0, m, pr.ws, side)
+        ev_g = torch.cuda.Event()
+        ev_g.record(side)
+        if i + 1 < len(seeds):
+            # the next product's state is free: its previous user (product i + 1 - len(probs)) finished
+            # its GEMM on this stream, and its side work before that GEMM started
+            ev_stats = stats(i + 1)
+        main.wait_event(ev_g)
+        A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GEMM, 0, m, pr.ws, main)
+    main.wait_stream(side)
 
 
 def error_report(prob: Problem, res: dict, delta: float = 0.05, stream=None) -> dict:

@@ -140,3 +140,39 @@ def test_wu_block_sampling_with_tensor_core_f(bmm, dtype):
     tolp = 2.0 ** -7 + Lcols * 2.0 ** -22
     bnd = product_bound(M[rows], N, kidx, scale, offsets=off, unit="block")
     assert np.all(np.abs(got - want) <= tolp * bnd + 1e-300)
+
+
+@pytest.mark.parametrize("dtype,states,nouts", [("f32", 2, 1), ("f32", 3, 5), ("bf16", 2, 2)])
+def test_pipelined_products_equal_run(bmm, dtype, states, nouts):
+    """run_pipelined (two products in flight over two streams) gives each product exactly what run()
+    gives for its seed: same statistics, block sizes, draws and GEMM, only reordered in time."""
+    A = bmm._abi
+    m, n, p, K = 1000, 16384, 520, 229
+    off, _, _, Mt, Nt = _inputs(dtype, m, n, p, K, seed=331)
+    L = 2048
+    seeds = [41, 42, 43, 44, 45]
+    probs = [bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16) for _ in range(states)]
+    outs = [torch.full((m, p), float("nan"), device="cuda") for _ in range(nouts)]
+    bmm.run_pipelined(probs, L, seeds, outs)
+    torch.cuda.synchronize()
+    for pr in probs:
+        bmm.check_status(pr)
+    ref = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    # product i lives in outs[i % nouts] until product i + nouts overwrites it
+    for i in range(max(0, len(seeds) - nouts), len(seeds)):
+        r = bmm.run(ref, "OPL", L, seed=seeds[i], gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+        bmm.check_status(ref)
+        assert torch.equal(outs[i % nouts], r["out"]), i
+
+
+def test_pipelined_rejects_what_it_does_not_run(bmm):
+    A = bmm._abi
+    off, _, _, Mt, Nt = _inputs("f32", 256, 2048, 128, 32, seed=5)
+    pr = bmm.prepare(Mt, Nt, off, max_draws=256, gemm_mode=A.GEMM_BF16)
+    out = torch.empty(256, 128, device="cuda")
+    with pytest.raises(ValueError):
+        bmm.run_pipelined([pr], 256, [1], [out])
+    with pytest.raises(ValueError):
+        bmm.run_pipelined([pr, pr], 256, [1], [])
+    with pytest.raises(ValueError):
+        bmm.run_pipelined([pr, pr], 256, [1], [out], gemm_mode=A.GEMM_F64)
