@@ -771,7 +771,7 @@ def mlp_run(args, ws, rank, local):
         "config": {"workload": "MLP: X 4096x16384 BF16, 4 layers W 16384x16384, GELU, OPL K=256 blocks of 64, "
                                "c=64 blocks (L=4096), forward + backward", "parallelism": f"replicas x{ws}"},
         "exact_bf16_mlp_ms": exact_ms, "sampled_gemm_tflop_per_step": gemm_flops / 1e12,
-        "clocks": clocks, "gpu_launches": int(launches),
+        "clocks": clk.summary(), "gpu_launches": int(launches),
     }
     del X, Ws, R
     torch.cuda.empty_cache()
