@@ -10,7 +10,11 @@ A step is one approximate product by the A-optimal method (OPL: one statistics p
 column and row norms and ||M^k N_k||_F^2 -- exact float-float squares plus the off-diagonal terms of
 TF32 tcgen05 Grams --, probabilities eq. 3.8, block sizes eq. 3.9, Philox sampling, gather and the
 BF16 tcgen05 product), inputs resident in HBM (4.3 GB, larger than L2, so no flush is
-needed).  Prints one JSON line.  Besides the contract's keys it carries the stage times and their
+needed).  The timed products run two in flight (pipeline.run_pipelined: the next product's
+statistics pass beside this product's design and gathers; `config.schedule`); a sequential pass of
+the same products gives `sequential_ms_per_step` and the per-stage times, and `pipeline_timeline`
+shows where a product's time goes in the pipelined schedule (--schedule sequential times the
+sequential pass instead).  Prints one JSON line.  Besides the contract's keys it carries the stage times and their
 rooflines, `norm_pass_alone` (the statistics pass without f_k, timed apart), `gemm_part_alone`
 (the apply's GEMM on the step's gathered operands, timed apart), the exact GEMM
 baselines and the measured error against the closed form, `error_bars` (the error-bar calls on one
@@ -393,6 +397,34 @@ def time_gemm_part(P, prob, w, L, r, pk, reps=20):
             "note": "GEMM part of the BF16 apply on the step's gathered operands, back to back, of the burst peak"}
 
 
+def pipeline_timeline(P, probs, c, outs, rank, nprod=12):
+    """Where a product's time goes when two are in flight: run_pipelined over nprod products with
+    events on both streams (outside the timed region), averaged over the middle products.  cycle: GEMM
+    end to GEMM end; stats: the next product's statistics pass as it runs beside this product's side
+    work; design: block sizes and draws from the end of this product's statistics pass (they wait
+    behind the previous product's GEMM); gathers: C and D; gemm: the sampled GEMM."""
+    import torch
+
+    ev = []
+    P.run_pipelined(probs, c, range(30_000, 30_000 + nprod), outs, replicate=rank, events=ev)
+    torch.cuda.synchronize()
+    at = {(name, i): e for name, i, e in ev}
+
+    def span(a, b):
+        return at[a].elapsed_time(at[b])
+
+    mid = range(2, nprod - 2)
+    avg = lambda xs: sum(xs) / len(xs)
+    return {
+        "products": nprod, "averaged_over": f"products 2..{nprod - 3}",
+        "cycle_ms": avg([span(("gemm_end", i - 1), ("gemm_end", i)) for i in mid]),
+        "stats_ms": avg([span(("stats_start", i + 1), ("stats_end", i + 1)) for i in mid]),
+        "design_ms": avg([span(("side_start", i), ("design_end", i)) for i in mid]),
+        "gathers_ms": avg([span(("design_end", i), ("gathers_end", i)) for i in mid]),
+        "gemm_ms": avg([span(("gemm_start", i), ("gemm_end", i)) for i in mid]),
+    }
+
+
 def native_arm(args, ws, rank, local):
     import torch
 
@@ -475,7 +507,10 @@ def native_arm(args, ws, rank, local):
                                                                       replicate=rank))
         for pr in probs:
             P.check_status(pr)
+        timeline = pipeline_timeline(P, probs, c, outs, rank)
         del probs[1], outs[1]
+    else:
+        timeline = None
     ms_step = elapsed_ms / args.steps
     value = elapsed_ms / (args.steps * ws)
 
@@ -523,7 +558,7 @@ def native_arm(args, ws, rank, local):
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": args.mode, "data": "synthetic",
         "norm_pass_alone": norm_alone, "gemm_part_alone": gemm_alone,
-        "sequential_ms_per_step": seq_ms / args.steps,
+        "sequential_ms_per_step": seq_ms / args.steps, "pipeline_timeline": timeline,
         "config": {"workload": workload_name(args), "method": args.method, "gemm": args.mode, "c": c,
                    "schedule": ("two products in flight (run_pipelined: the next product's statistics pass "
                                 "beside this product's design and gathers)") if pipelined else "sequential",
@@ -899,7 +934,8 @@ def config1_summary(P, dev, seeds=1000):
             r = P.run(prob, meth, c, seed=sd, c0=4 * K, gemm_mode=A.GEMM_F64, out=out, fmode=A.F_EXACT)
             errs.append(torch.linalg.norm(out - MN) ** 2)
             if sd < 8 or meth in ("ONU", "ONMCNR"):  # the design is the same for every seed except the two-step ones
-                A.bmm_probs(M, N, prob.B, A.P_COL_OPT, A.F_EXACT | A.REUSE_STATS, None, prob.st, prob.ws)
+                # the statistics and exact f_k for the closed form (UU's own pass computes neither)
+                A.bmm_probs(M, N, prob.B, A.P_COL_OPT, A.F_EXACT, None, prob.st, prob.ws)
                 f = prob.st["f"]
                 if blk:
                     E = (torch.sum(f / r["p"]) - mn2) / c

@@ -291,7 +291,8 @@ def run(prob: Problem, method: str, c: int, seed: int, replicate: int = 0, c0: i
     return res
 
 
-def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEMM_BF16, replicate: int = 0) -> None:
+def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEMM_BF16, replicate: int = 0,
+                  events: list | None = None) -> None:
     """Alg. 2 with eq. 3.8 / 3.9 (OPL, tensor-core f_k, fused statistics pass, column sampling) on a
     sequence of independent products, two in flight: product i + 1's statistics pass (bound by
     shared-memory traffic, leaving HBM bandwidth free) runs beside product i's block sizes, draws and
@@ -304,7 +305,11 @@ def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEM
     round-robin (product i writes outs[i % len(outs)], which keeps it until product i + len(outs)
     overwrites it); replicate: as in run().  Enqueues everything on the current stream and the side
     stream and returns; the current stream has joined the side stream when it returns.  Device status
-    is read with check_status() on each state, as after run()."""
+    is read with check_status() on each state, as after run().
+
+    events: if a list, (name, product, torch.cuda.Event) triples are appended for a timeline (timing
+    only): stats_start / stats_end and gemm_start / gemm_end on the current stream, side_start /
+    design_end / gathers_end on the side stream."""
     torch = _torch()
     if len(probs) < 2 or not outs:
         raise ValueError("run_pipelined needs two or more problem states and an output")
@@ -322,12 +327,19 @@ def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEM
                          g=torch.empty(K, dtype=torch.float64, device=dev), idx=torch.empty(c, dtype=torch.int32, device=dev),
                          scale=torch.empty(c, dtype=torch.float64, device=dev)))
 
+    def mark(name, i, stream):
+        ev = torch.cuda.Event(enable_timing=events is not None)
+        ev.record(stream)
+        if events is not None:
+            events.append((name, i, ev))
+        return ev
+
     def stats(i):
         pr, b = probs[i % len(probs)], bufs[i % len(probs)]
+        if events is not None:
+            mark("stats_start", i, main)
         A.bmm_probs(pr.M, pr.N, pr.B, A.P_COL_OPT, A.F_TC, b["p"], pr.st, pr.ws, main)
-        ev = torch.cuda.Event()
-        ev.record(main)
-        return ev
+        return mark("stats_end", i, main)
 
     if not seeds:
         return
@@ -337,18 +349,25 @@ def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEM
         pr, b, out = probs[i % len(probs)], bufs[i % len(probs)], outs[i % len(outs)]
         m = int(pr.M.shape[0])
         side.wait_event(ev_stats)
+        if events is not None:
+            mark("side_start", i, side)
         A.bmm_blocksizes(pr.M, pr.N, pr.B, pr.st, A.CK_OPT, c, None, None, 0, b["ck"], b["g"], None, pr.ws, side)
         A.bmm_sample(b["p"], A.UNIT_COLUMN, pr.B, b["ck"], c, seed, sid, b["idx"], b["scale"], pr.ws, side)
+        if events is not None:
+            mark("design_end", i, side)
         A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GATHER_B, 0, 0, pr.ws, side)
         A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GATHER_A, 0, m, pr.ws, side)
-        ev_g = torch.cuda.Event()
-        ev_g.record(side)
+        ev_g = mark("gathers_end", i, side)
         if i + 1 < len(seeds):
             # the next product's state is free: its previous user (product i + 1 - len(probs)) finished
             # its GEMM on this stream, and its side work before that GEMM started
             ev_stats = stats(i + 1)
         main.wait_event(ev_g)
+        if events is not None:
+            mark("gemm_start", i, main)
         A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GEMM, 0, m, pr.ws, main)
+        if events is not None:
+            mark("gemm_end", i, main)
     main.wait_stream(side)
 
 

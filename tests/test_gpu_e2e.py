@@ -153,8 +153,16 @@ def test_pipelined_products_equal_run(bmm, dtype, states, nouts):
     seeds = [41, 42, 43, 44, 45]
     probs = [bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16) for _ in range(states)]
     outs = [torch.full((m, p), float("nan"), device="cuda") for _ in range(nouts)]
-    bmm.run_pipelined(probs, L, seeds, outs)
+    ev = []
+    bmm.run_pipelined(probs, L, seeds, outs, events=ev)
     torch.cuda.synchronize()
+    names = ("stats_start", "stats_end", "side_start", "design_end", "gathers_end", "gemm_start", "gemm_end")
+    assert sorted((n, i) for n, i, _ in ev) == sorted((n, i) for n in names for i in range(len(seeds)))
+    at = {(n, i): e for n, i, e in ev}
+    for i in range(len(seeds)):  # each product's events in schedule order
+        chain = [("stats_start", i), ("stats_end", i), ("side_start", i), ("design_end", i), ("gathers_end", i),
+                 ("gemm_start", i), ("gemm_end", i)]
+        assert all(at[a].elapsed_time(at[b]) >= 0.0 for a, b in zip(chain[:-1], chain[1:])), i
     for pr in probs:
         bmm.check_status(pr)
     ref = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
