@@ -184,3 +184,28 @@ def test_pipelined_rejects_what_it_does_not_run(bmm):
         bmm.run_pipelined([pr, pr], 256, [1], [])
     with pytest.raises(ValueError):
         bmm.run_pipelined([pr, pr], 256, [1], [out], gemm_mode=A.GEMM_F64)
+
+
+def test_pipelined_products_of_different_inputs(bmm):
+    """Two states over different matrices (and different block partitions): product i works on
+    state i mod 2, so the stream alternates between the two products, each equal to run() on its own
+    inputs with the same seed."""
+    A = bmm._abi
+    L = 1536
+    sets = []
+    for seed, (m, n, p, K) in ((341, (520, 12288, 776, 170)), (351, (1000, 8192, 264, 120))):
+        off, _, _, Mt, Nt = _inputs("f32", m, n, p, K, seed=seed)
+        sets.append((off, Mt, Nt))
+    probs = [bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16) for off, Mt, Nt in sets]
+    outs = [torch.full((int(s[1].shape[0]), int(s[2].shape[1])), float("nan"), device="cuda") for s in sets]
+    seeds = [61, 62, 63, 64]
+    bmm.run_pipelined(probs, L, seeds, outs)
+    torch.cuda.synchronize()
+    for pr in probs:
+        bmm.check_status(pr)
+    for i in (2, 3):  # the last product of each state
+        off, Mt, Nt = sets[i % 2]
+        ref = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+        r = bmm.run(ref, "OPL", L, seed=seeds[i], gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+        bmm.check_status(ref)
+        assert torch.equal(outs[i % 2], r["out"]), i
