@@ -309,11 +309,29 @@ def reference_arm(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(args.steps, 1),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args), "method": args.method},
+        "config": run_config(args, ws),
         "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "nproc": os.cpu_count(), "kind": "oracle",
                          "sample": sample, "stages": stages},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def pipelined_schedule(args) -> bool:
+    """The timed products run two in flight (run_pipelined) for OPL with the BF16 GEMM and the fused
+    statistics pass, unless --schedule sequential."""
+    return args.schedule == "pipelined" and args.method == "OPL" and args.mode == "bf16" and args.stats != "split"
+
+
+def run_config(args, ws) -> dict:
+    """The `config` of the single-product line, shared by the native and the reference arm."""
+    w = workload(args)
+    L = int(np.floor(w["c_blocks"] * w["n"] / w["K"] + 0.5))  # c whole blocks' worth of outer products
+    c = L if args.method not in ("SSM", "WU") else w["c_blocks"]
+    return {"workload": workload_name(args), "method": args.method, "gemm": args.mode, "c": c,
+            "schedule": ("two products in flight (run_pipelined: the next product's statistics pass "
+                         "beside this product's design and gathers)") if pipelined_schedule(args) else "sequential",
+            "l2": "small case, L2-resident" if args.small else "inputs larger than the 129 MB L2, no flush",
+            "parallelism": f"replicas x{ws}"}
 
 
 def workload_name(args):
@@ -455,8 +473,7 @@ def native_arm(args, ws, rank, local):
         return P.run(prob, args.method, c, seed=s, replicate=rank, c0=c0, gemm_mode=gm, out=out, events=events,
                      fused_stats=args.stats != "split")
 
-    pipelined = (args.schedule == "pipelined" and args.method == "OPL" and args.mode == "bf16"
-                 and args.stats != "split")
+    pipelined = pipelined_schedule(args)
     if pipelined:
         # a second problem state and output for the product in flight beside the current one
         probs = [prob, P.prepare(M, N, off, max_draws=L, gemm_mode=gm)]
@@ -559,11 +576,7 @@ def native_arm(args, ws, rank, local):
         "dtype": args.mode, "data": "synthetic",
         "norm_pass_alone": norm_alone, "gemm_part_alone": gemm_alone,
         "sequential_ms_per_step": seq_ms / args.steps, "pipeline_timeline": timeline,
-        "config": {"workload": workload_name(args), "method": args.method, "gemm": args.mode, "c": c,
-                   "schedule": ("two products in flight (run_pipelined: the next product's statistics pass "
-                                "beside this product's design and gathers)") if pipelined else "sequential",
-                   "l2": "small case, L2-resident" if args.small else "inputs larger than the 129 MB L2, no flush",
-                   "parallelism": f"replicas x{ws}"},
+        "config": run_config(args, ws),
         "roofline": roofline, "stages_ms": stages, "stage_rooflines": roof_all,
         "clocks": clocks, "gpu_launches": int(launches),
         "autotune": {f"{k[0]}x{k[1]}xL{k[2]}": v for k, v in tuned.items()},
