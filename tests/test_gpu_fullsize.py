@@ -1,0 +1,113 @@
+"""The benched product at its full size, in the launch configuration bench.py times, against the
+FP64 oracle on sampled outputs.
+
+Workload: M 8192 x 65536 and N 65536 x 8192 FP32 (row-major), N(0,1) * LogNormal(0, 1.5) block
+scales, K = 1024 blocks of 16..128, OPL with L = 8192 outer products, fused statistics pass with
+tensor-core f_k, BF16 sampled GEMM with the autotuned tile, products two in flight
+(pipeline.run_pipelined).  The oracle cannot hold the whole problem in FP64 in seconds, so it
+checks what it can compute one piece at a time:
+  x_i, y_i, a_k, s_k, ||M^k||_F^2, ||N_k||_F^2, eq. 3.8 p   on 12 sampled blocks, 1e-12 relative
+  f_k                       on the same blocks, within the TF32 Gram bound of the off-diagonal trace
+  c_k (eq. 3.9)             all K, bit for bit from the GPU's own a_k and f_k
+  idx, scale                all L draws, bit for bit from the GPU's p and c_k
+  CD                        32 sampled rows x all 8192 columns, within the BF16 element bound
+and every product of the pipelined schedule equals pipeline.run with the same seed, bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from tests._gpu_util import host, product_bound, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bmm():
+    import paper_2105_04940_gb300 as P
+    P.build()
+    P._abi.load()
+    assert torch.cuda.is_available()
+    return P
+
+
+def _gram_bound(Mb, Nb, round_in):
+    """One block: tau_M sum_{i != j} |M|^T|M| |G_N| + tau_N |G_M| |N||N|^T + tau_M tau_N (...), with
+    tau = round_in + len 2^-23 (operand rounding, FP32 accumulation over len = m or p)."""
+    m, p = Mb.shape[0], Nb.shape[1]
+    GM, GN = Mb.T @ Mb, Nb @ Nb.T
+    AM, AN = np.abs(Mb).T @ np.abs(Mb), np.abs(Nb) @ np.abs(Nb).T
+    tM, tN = round_in + m * 2.0 ** -23, round_in + p * 2.0 ** -23
+    E = tM * AM * np.abs(GN) + tN * np.abs(GM) * AN + tM * tN * AM * AN
+    np.fill_diagonal(E, 0.0)
+    return E.sum()
+
+
+def test_bench_product_full_size(bmm):
+    A = bmm._abi
+    m, n, p, K, L = 8192, 65536, 8192, 1024, 8192
+    off = S.block_offsets_uneven(n, K, 16, 128, seed=3)
+    nk = np.diff(off)
+    Mt, Nt, _ = S.scaled_gaussian_torch(m, n, p, off, 1.5, 3, dtype=torch.float32, device="cuda")
+    assert bmm.equal_budget(128, n, K) == L
+    bmm.autotune([(m, p, L)], A.GEMM_BF16, torch.device("cuda"))
+    probs = [bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16) for _ in range(2)]
+    outs = [torch.empty(m, p, device="cuda") for _ in range(2)]
+    seeds = [71, 72, 73]
+    bmm.run_pipelined(probs, L, seeds, outs)
+    torch.cuda.synchronize()
+    for pr in probs:
+        bmm.check_status(pr)
+    piped = {1: outs[1].clone(), 2: outs[0].clone()}
+    del outs
+
+    prob = probs[0]
+    for i in (1, 2):
+        r = bmm.run(prob, "OPL", L, seed=seeds[i], gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+        bmm.check_status(prob)
+        assert torch.equal(r["out"], piped[i]), i
+    del piped
+    st = {k: host(v) for k, v in prob.st.items()}
+    p_gpu = host(r["p"])
+    seed = seeds[2]
+
+    # statistics, f_k and eq. 3.8 p on sampled blocks (the largest and smallest among them)
+    rng = np.random.default_rng(9)
+    blocks = np.unique(np.concatenate([rng.choice(K, size=10, replace=False), [int(np.argmax(nk)), int(np.argmin(nk))]]))
+    for k in blocks:
+        lo, hi = int(off[k]), int(off[k + 1])
+        Mb = Mt[:, lo:hi].double().cpu().numpy()
+        Nb = Nt[lo:hi, :].double().cpu().numpy()
+        loc = np.array([0, hi - lo])
+        x, y = oracle.col_row_sq_norms(Mb, Nb)
+        ost = oracle.block_stats(x, y, loc)
+        assert rel_err(st["x"][lo:hi], x) < 1e-12 and rel_err(st["y"][lo:hi], y) < 1e-12, k
+        for key in ("a", "s", "mf", "nf"):
+            assert rel_err(st[key][k:k + 1], ost[key]) < 1e-12, (k, key)
+        assert rel_err(p_gpu[lo:hi], oracle.p_col_opt(ost["w"], ost["a"], loc)) < 1e-12, k
+        f = oracle.block_frob_sq_gram(Mb, Nb, loc)[0]
+        assert abs(st["f"][k] - f) <= _gram_bound(Mb, Nb, 2.0 ** -9) + 1e-12 * f, k
+
+    # eq. 3.9 block sizes from the GPU's own a_k and f_k, and the draws from its p and c_k
+    ck = host(r["ck"])
+    want_ck = oracle.apportion(oracle.g_with_fallback(oracle.g_opt(st["a"], st["f"]), st["a"], nk), nk, L)
+    np.testing.assert_array_equal(ck, want_ck)
+    idx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+    want_idx, want_scale = oracle.sample_alg2(p_gpu, off, ck, seed, bmm.stream_id(0, A.PURPOSE_MAIN))
+    np.testing.assert_array_equal(idx, want_idx)
+    np.testing.assert_array_equal(scale, want_scale)
+
+    # the product on 32 sampled rows, every column, within the BF16 element bound; only the drawn
+    # columns of M and rows of N enter, so the oracle gets those (indices remapped)
+    rows = np.sort(rng.choice(m, size=32, replace=False))
+    cols, loc_idx = np.unique(idx, return_inverse=True)
+    cols_t = torch.as_tensor(cols, device="cuda")
+    Mr = Mt[torch.as_tensor(rows, device="cuda")][:, cols_t].double().cpu().numpy()
+    Nr = Nt[cols_t].double().cpu().numpy()
+    want = oracle.sampled_product_columns(Mr, Nr, loc_idx, scale)
+    got = r["out"][torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
+    tol = 2.0 ** -7 + L * 2.0 ** -22
+    assert np.all(np.abs(got - want) <= tol * product_bound(Mr, Nr, loc_idx, scale) + 1e-300)
