@@ -34,6 +34,13 @@ def bmm():
     return P
 
 
+@pytest.fixture(autouse=True)
+def _default_tiles(bmm):
+    """These tests tune the GEMM tile table as the bench does; later tests start from the default."""
+    yield
+    bmm._abi.bmm_autotune_clear()
+
+
 def _gram_bound(Mb, Nb, round_in):
     """One block: tau_M sum_{i != j} |M|^T|M| |G_N| + tau_N |G_M| |N||N|^T + tau_M tau_N (...), with
     tau = round_in + len 2^-23 (operand rounding, FP32 accumulation over len = m or p)."""
@@ -111,3 +118,85 @@ def test_bench_product_full_size(bmm):
     got = r["out"][torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
     tol = 2.0 ** -7 + L * 2.0 ** -22
     assert np.all(np.abs(got - want) <= tol * product_bound(Mr, Nr, loc_idx, scale) + 1e-300)
+
+
+def test_batched_workload_full_size(bmm):
+    """The batched workload at its full size (512 BF16 products, the bench's shapes and seeds), run as
+    the bench runs it: an eager batch, the GEMM tile autotuner over the batch, then the whole batch
+    captured in one CUDA graph and replayed.  The replay reproduces the eager outputs bit for bit, and
+    four products (the largest and smallest m n, two others) are checked against the oracle: the
+    statistics and eq. 3.8 p on sampled blocks at 1e-12, f_k within the exact-product Gram bound
+    (BF16 products are exact in FP32; FP32 accumulation), every c_k and draw bit for bit from the
+    GPU's own statistics, and 16 rows of the product within the BF16 element bound."""
+    A = bmm._abi
+    shapes = S.batched_products(512, seed=5)
+    probs, outs, cs = [], [], []
+    for i, sh in enumerate(shapes):
+        m, n, p, off = sh["m"], sh["n"], sh["p"], sh["offsets"]
+        K = len(off) - 1
+        M, N, _ = S.scaled_gaussian_torch(m, n, p, off, 1.0, 5 * 1000003 + 7919 * i, dtype=torch.bfloat16,
+                                          device="cuda")
+        L = bmm.equal_budget(max(K // 8, 1), n, K)
+        probs.append(bmm.prepare(M, N, off, max_draws=L, gemm_mode=A.GEMM_BF16))
+        outs.append(torch.empty(m, p, device="cuda", dtype=torch.float32))
+        cs.append(L)
+    seeds = [11 + i for i in range(len(probs))]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+
+    def batch():
+        return bmm.run_batched(probs, "OPL", cs, seeds, gemm_mode=A.GEMM_BF16, outs=outs, streams=streams)
+
+    res = batch()
+    torch.cuda.synchronize()
+    for pr in probs:
+        bmm.check_status(pr)
+    mn = np.array([sh["m"] * sh["n"] for sh in shapes])
+    rng = np.random.default_rng(13)
+    pick = [int(np.argmax(mn)), int(np.argmin(mn))] + [int(i) for i in rng.choice(len(shapes), 2, replace=False)]
+    eager = {i: outs[i].clone() for i in pick}
+    bmm.autotune_batched(probs, res, cs, A.GEMM_BF16, outs)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        res = batch()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    for pr in probs:
+        bmm.check_status(pr)
+    sid = bmm.stream_id(0, A.PURPOSE_MAIN)
+    for i in pick:
+        assert torch.equal(outs[i], eager[i]), i
+        sh, pr, r = shapes[i], probs[i], res[i]
+        m, p, off, L = sh["m"], sh["p"], sh["offsets"], cs[i]
+        K, nk = len(off) - 1, np.diff(off)
+        st = {k: host(v) for k, v in pr.st.items()}
+        p_gpu = host(r["p"])
+        for k in np.unique(np.concatenate([rng.choice(K, size=4, replace=False), [int(np.argmax(nk))]])):
+            lo, hi = int(off[k]), int(off[k + 1])
+            Mb = pr.M[:, lo:hi].double().cpu().numpy()
+            Nb = pr.N[lo:hi, :].double().cpu().numpy()
+            loc = np.array([0, hi - lo])
+            x, y = oracle.col_row_sq_norms(Mb, Nb)
+            ost = oracle.block_stats(x, y, loc)
+            assert rel_err(st["x"][lo:hi], x) < 1e-12 and rel_err(st["y"][lo:hi], y) < 1e-12, (i, k)
+            for key in ("a", "s", "mf", "nf"):
+                assert rel_err(st[key][k:k + 1], ost[key]) < 1e-12, (i, k, key)
+            assert rel_err(p_gpu[lo:hi], oracle.p_col_opt(ost["w"], ost["a"], loc)) < 1e-12, (i, k)
+            f = oracle.block_frob_sq_gram(Mb, Nb, loc)[0]
+            assert abs(st["f"][k] - f) <= _gram_bound(Mb, Nb, 0.0) + 1e-12 * f, (i, k)
+        ck = host(r["ck"])
+        want_ck = oracle.apportion(oracle.g_with_fallback(oracle.g_opt(st["a"], st["f"]), st["a"], nk), nk, L)
+        np.testing.assert_array_equal(ck, want_ck)
+        idx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+        want_idx, want_scale = oracle.sample_alg2(p_gpu, off, ck, seeds[i], sid)
+        np.testing.assert_array_equal(idx, want_idx)
+        np.testing.assert_array_equal(scale, want_scale)
+        rows = np.sort(rng.choice(m, size=min(16, m), replace=False))
+        cols, loc_idx = np.unique(idx, return_inverse=True)
+        cols_t = torch.as_tensor(cols, device="cuda")
+        Mr = pr.M[torch.as_tensor(rows, device="cuda")][:, cols_t].double().cpu().numpy()
+        Nr = pr.N[cols_t].double().cpu().numpy()
+        want = oracle.sampled_product_columns(Mr, Nr, loc_idx, scale)
+        got = outs[i][torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
+        tol = 2.0 ** -7 + L * 2.0 ** -22
+        assert np.all(np.abs(got - want) <= tol * product_bound(Mr, Nr, loc_idx, scale) + 1e-300), i
