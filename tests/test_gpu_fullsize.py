@@ -200,3 +200,99 @@ def test_batched_workload_full_size(bmm):
         got = outs[i][torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
         tol = 2.0 ** -7 + L * 2.0 ** -22
         assert np.all(np.abs(got - want) <= tol * product_bound(Mr, Nr, loc_idx, scale) + 1e-300), i
+
+
+def _e4m3_rows_bound(Aa, Bb, al, be, L):
+    """Element-wise error bound of the e4m3 sampled product on a subset of output rows.  Per drawn
+    index j: a = M[:, c_j] sqrt(w_j), b = N[c_j, :] sqrt(w_j); the kernel scales a by 2^(e_j + gA) and b
+    by 2^(gB - e_j) (e_j balances max|a| and max|b|, gA and gB bring each operand's largest value to
+    at most 448) and rounds to e4m3: |q(x) - x| <= 2^-4 |x| in the normal range, or 2^-10 in scaled
+    units below it (a factor 4 for an exponent one off from the kernel's).  Aa = |a| on the chosen rows,
+    Bb = |b|; al and be are max|a| over all of M's rows and max|b|, recomputed here in FP64."""
+    u = 2.0 ** -4
+    e = np.zeros(len(al))
+    pos = (al > 0) & (be > 0)
+    e[pos] = np.clip(np.rint(0.5 * np.log2(be[pos] / al[pos])), -60, 60)
+    gA = int(np.floor(np.log2(448.0 / np.max(al * 2.0 ** e))))
+    gB = int(np.floor(np.log2(448.0 / np.max(be * 2.0 ** -e))))
+    da = 4 * 2.0 ** -10 * 2.0 ** -(e + gA)
+    db = 4 * 2.0 ** -10 * 2.0 ** -(gB - e)
+    bound = (2 * u + u * u + 1.2 * L * 2.0 ** -23) * (Aa @ Bb)
+    bound += (1 + u) * ((da @ Bb)[None, :] + (Aa @ db)[:, None]) + np.sum(da * db)
+    return bound
+
+
+def test_precision_workload_full_size(bmm):
+    """The tall-skinny precision configuration at full size, as the bench's precision summary runs it:
+    M 4096 x 262144 and N 262144 x 4096 FP32, each rank 32 (Gaussian factors / sqrt 32) plus 1e-3
+    N(0,1) noise, K = 4096 blocks of 64, OPL with L = 32768 draws; one sample applied in every GEMM
+    mode.  Statistics and eq. 3.8 p on sampled blocks at 1e-12, f_k within the TF32 Gram bound, all
+    c_k and draws bit for bit, and each mode's product on 16 rows within its element bound: FP64
+    1e-13 + L 2^-52, BF16 2^-7 + L 2^-22, split BF16 2^-14 + L 2^-22 (of sum_t s_t |M||N|), e4m3 the
+    bound of its power-of-two scalings and FP8 rounding."""
+    A = bmm._abi
+    m, n, p = 4096, 262144, 4096
+    K = n // 64
+    off = np.arange(0, n + 1, 64, dtype=np.int64)
+    L = bmm.equal_budget(K // 8, n, K)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(4)
+
+    def low_rank(r_, c_):
+        F = torch.randn(r_, 32, generator=g, device="cuda", dtype=torch.float64)
+        G = torch.randn(32, c_, generator=g, device="cuda", dtype=torch.float64)
+        return (F @ G / np.sqrt(32.0) + 1e-3 * torch.randn(r_, c_, generator=g, device="cuda",
+                                                          dtype=torch.float64)).float()
+
+    Mt, Nt = low_rank(m, n), low_rank(n, p)
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L)
+    res = bmm.run(prob, "OPL", L, seed=7, gemm_mode=A.GEMM_BF16, compute_product=False)
+    bmm.check_status(prob)
+    st = {k: host(v) for k, v in prob.st.items()}
+    p_gpu = host(res["p"])
+    nk = np.diff(off)
+    rng = np.random.default_rng(17)
+    for k in rng.choice(K, size=8, replace=False):
+        lo, hi = int(off[k]), int(off[k + 1])
+        Mb = Mt[:, lo:hi].double().cpu().numpy()
+        Nb = Nt[lo:hi, :].double().cpu().numpy()
+        loc = np.array([0, hi - lo])
+        x, y = oracle.col_row_sq_norms(Mb, Nb)
+        ost = oracle.block_stats(x, y, loc)
+        assert rel_err(st["x"][lo:hi], x) < 1e-12 and rel_err(st["y"][lo:hi], y) < 1e-12, k
+        for key in ("a", "s", "mf", "nf"):
+            assert rel_err(st[key][k:k + 1], ost[key]) < 1e-12, (k, key)
+        assert rel_err(p_gpu[lo:hi], oracle.p_col_opt(ost["w"], ost["a"], loc)) < 1e-12, k
+        f = oracle.block_frob_sq_gram(Mb, Nb, loc)[0]
+        assert abs(st["f"][k] - f) <= _gram_bound(Mb, Nb, 2.0 ** -9) + 1e-12 * f, k
+    ck = host(res["ck"])
+    want_ck = oracle.apportion(oracle.g_with_fallback(oracle.g_opt(st["a"], st["f"]), st["a"], nk), nk, L)
+    np.testing.assert_array_equal(ck, want_ck)
+    idx, scale = host(res["idx"]).astype(np.int64), host(res["scale"])
+    want_idx, want_scale = oracle.sample_alg2(p_gpu, off, ck, 7, bmm.stream_id(0, A.PURPOSE_MAIN))
+    np.testing.assert_array_equal(idx, want_idx)
+    np.testing.assert_array_equal(scale, want_scale)
+
+    rows = np.sort(rng.choice(m, size=16, replace=False))
+    rows_t = torch.as_tensor(rows, device="cuda")
+    cols, loc_idx = np.unique(idx, return_inverse=True)
+    cols_t = torch.as_tensor(cols, device="cuda")
+    Mr = Mt[rows_t][:, cols_t].double().cpu().numpy()
+    Nr = Nt[cols_t].double().cpu().numpy()
+    want = oracle.sampled_product_columns(Mr, Nr, loc_idx, scale)
+    bound = product_bound(Mr, Nr, loc_idx, scale)
+    sw = np.sqrt(scale)
+    col_max = Mt[:, cols_t].abs().amax(dim=0).double().cpu().numpy()  # max |M[:, c]| over every row
+    al = col_max[loc_idx] * sw
+    Bb = np.abs(Nr[loc_idx]) * sw[:, None]
+    be = Bb.max(axis=1)
+    e4_bound = _e4m3_rows_bound(np.abs(Mr[:, loc_idx]) * sw[None, :], Bb, al, be, L)
+    tols = {"f64": 1e-13 + L * 2.0 ** -52, "bf16": 2.0 ** -7 + L * 2.0 ** -22, "split_bf16": 2.0 ** -14 + L * 2.0 ** -22}
+    for mode in ("f64", "bf16", "split_bf16", "e4m3"):
+        gm = bmm.MODES[mode]
+        o = torch.empty(m, p, device="cuda", dtype=torch.float64 if mode == "f64" else torch.float32)
+        A.bmm_apply(Mt, Nt, prob.B, res["unit"], res["idx"], res["scale"], L, gm, o, False, prob.ws)
+        bmm.check_status(prob)
+        got = o[rows_t].double().cpu().numpy()
+        lim = e4_bound if mode == "e4m3" else tols[mode] * bound
+        assert np.all(np.abs(got - want) <= lim + 1e-300), (mode, float(np.max(np.abs(got - want) / lim)))
