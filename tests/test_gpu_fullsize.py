@@ -296,3 +296,67 @@ def test_precision_workload_full_size(bmm):
         got = o[rows_t].double().cpu().numpy()
         lim = e4_bound if mode == "e4m3" else tols[mode] * bound
         assert np.all(np.abs(got - want) <= lim + 1e-300), (mode, float(np.max(np.abs(got - want) / lim)))
+
+
+def test_mlp_layer_full_size(bmm):
+    """One layer of the differentiation workload at full size, through the autograd function as the
+    bench's MLP calls it: X 4096 x 16384 BF16 ~ N(0,1), W 16384 x 16384 BF16 ~ N(0, 1/16384), K = 256
+    blocks of 64, OPL with c = 64 blocks (L = 4096), BF16 mode, an FP32 upstream gradient.  The draws
+    are those of pipeline.run with the same seed; against the oracle: the product on 16 rows, dX on
+    16 rows and dW on 16 drawn rows within the BF16 bound of their sums plus the final rounding to
+    BF16, and dX, dW exactly zero outside the drawn columns / rows."""
+    A = bmm._abi
+    m, n, K = 4096, 16384, 256
+    off = S.block_offsets_equal(n, K)
+    L = bmm.equal_budget(64, n, K)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6)
+    X = torch.randn(m, n, generator=g, device="cuda", dtype=torch.float32).to(torch.bfloat16).requires_grad_(True)
+    W = (torch.randn(n, n, generator=g, device="cuda", dtype=torch.float32) / np.sqrt(n)).to(torch.bfloat16) \
+        .requires_grad_(True)
+    Gup = torch.randn(m, n, generator=g, device="cuda", dtype=torch.float32)
+    seed = 1000
+    z = bmm.sampled_matmul(X, W, off, method="OPL", c=L, seed=seed, mode="bf16")
+    z.backward(Gup)
+    torch.cuda.synchronize()
+    prob = bmm.prepare(X.detach(), W.detach(), off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    r = bmm.run(prob, "OPL", L, seed=seed, gemm_mode=A.GEMM_BF16, compute_product=False)
+    bmm.check_status(prob)
+    idx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+    cols, loc_idx = np.unique(idx, return_inverse=True)
+    cols_t = torch.as_tensor(cols, device="cuda")
+    rng = np.random.default_rng(21)
+    rows = np.sort(rng.choice(m, size=16, replace=False))
+    rows_t = torch.as_tensor(rows, device="cuda")
+    Xr = X.detach()[rows_t][:, cols_t].double().cpu().numpy()
+    Wc = W.detach()[cols_t].double().cpu().numpy()
+    tol = 2.0 ** -7 + n * 2.0 ** -22
+    # forward
+    want = oracle.sampled_product_columns(Xr, Wc, loc_idx, scale)
+    got = z.detach()[rows_t].double().cpu().numpy()
+    assert np.all(np.abs(got - want) <= (2.0 ** -7 + L * 2.0 ** -22) * product_bound(Xr, Wc, loc_idx, scale) + 1e-300)
+    # dX on 16 rows: only the drawn columns are touched
+    Gr = Gup[rows_t].double().cpu().numpy()
+    wX, _ = oracle.adjoint_columns(Xr, Wc, loc_idx, scale, Gr)
+    bX, _ = oracle.adjoint_columns(np.abs(Xr), np.abs(Wc), loc_idx, scale, np.abs(Gr))
+    dXr = X.grad[rows_t].double()
+    gotX = dXr[:, cols_t].cpu().numpy()
+    assert np.all(np.abs(gotX - wX) <= tol * bX + 2.0 ** -8 * np.abs(wX) + 1e-300)
+    dXr[:, cols_t] = 0.0
+    assert not torch.any(dXr != 0)
+    # dW on 16 drawn rows: every draw of those columns contributes X[:, i]^T G
+    pick = np.sort(rng.choice(len(cols), size=16, replace=False))
+    sel = np.isin(loc_idx, pick)
+    sub_idx = np.searchsorted(pick, loc_idx[sel])
+    pick_t = torch.as_tensor(cols[pick], device="cuda")
+    Xp = X.detach()[:, pick_t].double().cpu().numpy()
+    Wp = W.detach()[pick_t].double().cpu().numpy()
+    Gd = Gup.double().cpu().numpy()
+    _, wW = oracle.adjoint_columns(Xp, Wp, sub_idx, scale[sel], Gd)
+    _, bW = oracle.adjoint_columns(np.abs(Xp), np.abs(Wp), sub_idx, scale[sel], np.abs(Gd))
+    gotW = W.grad[pick_t].double().cpu().numpy()
+    tolW = 2.0 ** -7 + m * 2.0 ** -22
+    assert np.all(np.abs(gotW - wW) <= tolW * bW + 2.0 ** -8 * np.abs(wW) + 1e-300)
+    untouched = torch.ones(n, dtype=torch.bool, device="cuda")
+    untouched[cols_t] = False
+    assert not torch.any(W.grad[untouched] != 0)
