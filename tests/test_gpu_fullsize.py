@@ -360,3 +360,55 @@ def test_mlp_layer_full_size(bmm):
     untouched = torch.ones(n, dtype=torch.bool, device="cuda")
     untouched[cols_t] = False
     assert not torch.any(W.grad[untouched] != 0)
+
+
+@pytest.mark.parametrize("m_layout", ["row", "col"])
+def test_element_offsets_beyond_32_bits(bmm, m_layout):
+    """A product whose M holds more than 2^32 elements (16500 x 262144 FP32, 17 GB; N 262144 x 256),
+    stored row-major or column-major, through the benched OPL path (fused statistics, BF16 apply):
+    statistics on blocks at both ends of the range (the last ones at element offsets above 2^32),
+    every c_k and draw bit for bit, and the product on rows including the last one."""
+    A = bmm._abi
+    m, n, p, K = 16500, 262144, 256, 3640
+    off = S.block_offsets_uneven(n, K, 16, 128, seed=41)
+    nk = np.diff(off)
+    Ms, Nt, _ = S.scaled_gaussian_torch(m, n, p, off, 1.0, 43, dtype=torch.float32, device="cuda", m_layout=m_layout)
+    Mt = Ms if m_layout == "row" else Ms.t()
+    assert Mt.shape == (m, n) and Mt.numel() > 2 ** 32
+    L = 8192
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    r = bmm.run(prob, "OPL", L, seed=5, gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+    bmm.check_status(prob)
+    st = {k: host(v) for k, v in prob.st.items()}
+    p_gpu = host(r["p"])
+    for k in (0, 1, K // 2, K - 2, K - 1):
+        lo, hi = int(off[k]), int(off[k + 1])
+        Mb = Mt[:, lo:hi].double().cpu().numpy()
+        Nb = Nt[lo:hi, :].double().cpu().numpy()
+        loc = np.array([0, hi - lo])
+        x, y = oracle.col_row_sq_norms(Mb, Nb)
+        ost = oracle.block_stats(x, y, loc)
+        assert rel_err(st["x"][lo:hi], x) < 1e-12 and rel_err(st["y"][lo:hi], y) < 1e-12, k
+        for key in ("a", "s", "mf", "nf"):
+            assert rel_err(st[key][k:k + 1], ost[key]) < 1e-12, (k, key)
+        assert rel_err(p_gpu[lo:hi], oracle.p_col_opt(ost["w"], ost["a"], loc)) < 1e-12, k
+        f = oracle.block_frob_sq_gram(Mb, Nb, loc)[0]
+        assert abs(st["f"][k] - f) <= _gram_bound(Mb, Nb, 2.0 ** -9) + 1e-12 * f, k
+    ck = host(r["ck"])
+    want_ck = oracle.apportion(oracle.g_with_fallback(oracle.g_opt(st["a"], st["f"]), st["a"], nk), nk, L)
+    np.testing.assert_array_equal(ck, want_ck)
+    idx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+    want_idx, want_scale = oracle.sample_alg2(p_gpu, off, ck, 5, bmm.stream_id(0, A.PURPOSE_MAIN))
+    np.testing.assert_array_equal(idx, want_idx)
+    np.testing.assert_array_equal(scale, want_scale)
+    rng = np.random.default_rng(47)
+    rows = np.unique(np.concatenate([rng.choice(m, size=14, replace=False), [0, m - 1]]))
+    rows_t = torch.as_tensor(rows, device="cuda")
+    cols, loc_idx = np.unique(idx, return_inverse=True)
+    cols_t = torch.as_tensor(cols, device="cuda")
+    Mr = Mt[rows_t][:, cols_t].double().cpu().numpy()
+    Nr = Nt[cols_t].double().cpu().numpy()
+    want = oracle.sampled_product_columns(Mr, Nr, loc_idx, scale)
+    got = r["out"][rows_t].double().cpu().numpy()
+    tol = 2.0 ** -7 + L * 2.0 ** -22
+    assert np.all(np.abs(got - want) <= tol * product_bound(Mr, Nr, loc_idx, scale) + 1e-300)
