@@ -209,3 +209,61 @@ def test_pipelined_products_of_different_inputs(bmm):
         r = bmm.run(ref, "OPL", L, seed=seeds[i], gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
         bmm.check_status(ref)
         assert torch.equal(outs[i % 2], r["out"]), i
+
+
+@pytest.mark.parametrize("case", ["zero_blocks", "all_zero"])
+def test_benched_path_degenerate_inputs(bmm, case):
+    """The benched OPL path on the method's degenerate inputs.  zero_blocks: blocks whose M^k or N_k
+    is zero (a_k = 0: eq. 3.8 is 0/0 there, read as uniform p; no mass, so nothing drawn there
+    matters), and a block with a_k > 0 but M^k N_k = 0 exactly (two outer products that cancel, f_k
+    = 0 up to the Gram's rounding).  all_zero: M = 0, so every weight of eq. 3.9 is zero and the
+    block sizes fall back to n_k; the product is exactly zero.  Each stage as in the end-to-end test."""
+    A = bmm._abi
+    m, n, p, K = 300, 4096, 260, 56
+    off, M, N, _, _ = _inputs("f32", m, n, p, K, seed=361)
+    M, N = M.astype(np.float32).astype(np.float64), N.astype(np.float32).astype(np.float64)
+    K = len(off) - 1
+    nk = np.diff(off)
+    if case == "zero_blocks":
+        M[:, off[1]:off[2]] = 0.0
+        N[off[2]:off[3], :] = 0.0
+        M[:, off[5]:off[6]] = 0.0
+        N[off[5]:off[6], :] = 0.0
+        lo = int(off[7])
+        M[:, lo + 1] = M[:, lo]
+        N[lo + 1, :] = -N[lo, :]
+        M[:, lo + 2:off[8]] = 0.0
+    else:
+        M[:] = 0.0
+    Mt, Nt = torch.as_tensor(M, dtype=torch.float32, device="cuda"), torch.as_tensor(N, dtype=torch.float32, device="cuda")
+    L = 1024
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    r = bmm.run(prob, "OPL", L, seed=3, gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+    bmm.check_status(prob)
+    st = {k: host(v) for k, v in prob.st.items()}
+    x, y = oracle.col_row_sq_norms(M, N)
+    ost = oracle.block_stats(x, y, off)
+    for k in ("a", "s", "mf", "nf"):
+        np.testing.assert_allclose(st[k], ost[k], rtol=1e-12, atol=0)
+    p_gpu = host(r["p"])
+    np.testing.assert_allclose(p_gpu, oracle.p_col_opt(ost["w"], ost["a"], off), rtol=1e-12, atol=0)
+    f = oracle.block_frob_sq_gram(M, N, off)
+    bound = _gram_bound(M, N, off, 2.0 ** -9)
+    assert np.all(np.abs(st["f"] - f) <= bound + 1e-12 * f)
+    if case == "zero_blocks":
+        assert st["a"][1] == 0 and st["a"][2] == 0 and st["a"][5] == 0 and st["a"][7] > 0
+        assert st["f"][1] == 0 and st["f"][2] == 0 and st["f"][5] == 0
+    ck = host(r["ck"])
+    want_ck = oracle.apportion(oracle.g_with_fallback(oracle.g_opt(st["a"], st["f"]), st["a"], nk), nk, L)
+    np.testing.assert_array_equal(ck, want_ck)
+    idx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+    want_idx, want_scale = oracle.sample_alg2(p_gpu, off, ck, 3, bmm.stream_id(0, A.PURPOSE_MAIN))
+    np.testing.assert_array_equal(idx, want_idx)
+    np.testing.assert_array_equal(scale, want_scale)
+    got = host(r["out"]).astype(np.float64)
+    if case == "all_zero":
+        assert np.all(got == 0.0)
+    else:
+        want = oracle.sampled_product_columns(M, N, idx, scale)
+        tol = 2.0 ** -7 + L * 2.0 ** -22
+        assert np.all(np.abs(got - want) <= tol * product_bound(M, N, idx, scale) + 1e-300)
