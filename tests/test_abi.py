@@ -246,3 +246,58 @@ def test_f_tc_query_on_the_host(lib):
     bad = _abi.Mat(fake, 256, 4000, 4096, _abi.F32, _abi.ROW_MAJOR)
     assert lib.bmm_f_tc_supported(by(bad), by(N), by(B), by(r)) == _abi.ERR_SHAPE
     assert lib.bmm_f_tc_supported(by(M), by(N), by(B), None) == _abi.ERR_ARG
+
+
+def test_core_entry_points_validate_on_host(lib):
+    """bmm_blocksizes, bmm_sample and bmm_backward refuse bad arguments with the documented codes
+    before anything is launched (host only: the fake pointers are never dereferenced; a case that
+    slipped past the checks would stop at the missing workspace, BMM_ERR_WORKSPACE, instead)."""
+    from paper_2105_04940_gb300 import _abi
+    fake = 1 << 20
+    n, K, m, p = 4096, 64, 256, 128
+    M = _abi.Mat(fake, m, n, n, _abi.F32, _abi.ROW_MAJOR)
+    N = _abi.Mat(fake, n, p, p, _abi.F32, _abi.ROW_MAJOR)
+    B = _abi.Blocks(K, n, 64, fake)
+    st = _abi.Stats(*([fake] * 7))
+    st_nof = _abi.Stats(*([fake] * 6 + [None]))
+    by = ctypes.byref
+    vp = ctypes.c_void_p
+
+    def bs(ckind, c, stats=st, ck=fake, Bk=B):
+        return lib.bmm_blocksizes(by(M), by(N), by(Bk), by(stats), ckind, c, None, None, 0, vp(ck) if ck else None,
+                                  vp(fake), None, None, 0, None)
+
+    assert bs(9, 1024) == _abi.ERR_ARG                                  # unknown kind
+    assert bs(_abi.CK_OPT, 1024, ck=None) == _abi.ERR_ARG               # no output
+    assert bs(_abi.CK_OPT, 1024, stats=st_nof) == _abi.ERR_ARG          # eq. 3.9 needs f
+    assert bs(_abi.CK_TILDE, 1024) == _abi.ERR_ARG                      # Alg. 3 needs its pilot
+    assert bs(_abi.CK_OPT, K - 1) == _abi.ERR_INFEASIBLE                # fewer draws than blocks
+    assert bs(_abi.CK_OPT, n + 1) == _abi.ERR_INFEASIBLE                # more draws than vectors
+    assert bs(_abi.CK_OPT, 1024, Bk=_abi.Blocks(0, n, 64, fake)) == _abi.ERR_SHAPE
+    assert bs(_abi.CK_OPT, 1024) == _abi.ERR_WORKSPACE                  # well formed: stops at the workspace
+
+    def smp(unit, c, p_=fake, ck=fake, idx=fake):
+        return lib.bmm_sample(vp(p_) if p_ else None, unit, by(B), vp(ck) if ck else None, c, 1, 0,
+                              vp(idx) if idx else None, vp(fake), None, 0, None)
+
+    assert smp(_abi.UNIT_COLUMN, 100, p_=None) == _abi.ERR_ARG
+    assert smp(_abi.UNIT_COLUMN, 100, idx=None) == _abi.ERR_ARG
+    assert smp(_abi.UNIT_COLUMN, -1) == _abi.ERR_ARG
+    assert smp(7, 100) == _abi.ERR_ARG                                  # unknown unit
+    assert smp(_abi.UNIT_COLUMN, 100, ck=None) == _abi.ERR_ARG          # column draws need c_k
+    assert smp(_abi.UNIT_COLUMN, 1 << 31) == _abi.ERR_UNSUPPORTED       # beyond int32 indices
+    assert smp(_abi.UNIT_BLOCK, 100, ck=None) == _abi.ERR_WORKSPACE     # block draws take no c_k
+
+    def bwd(G, gemm=_abi.GEMM_BF16, unit=_abi.UNIT_COLUMN, dM=None, dN=None, c=100):
+        return lib.bmm_backward(by(G), by(M), by(N), by(B), unit, vp(fake), vp(fake), c, 1, 0, gemm,
+                                by(dM) if dM else None, by(dN) if dN else None, 0, None, 0, None)
+
+    G = _abi.Mat(fake, m, p, p, _abi.F32, _abi.ROW_MAJOR)
+    assert bwd(G, unit=5) == _abi.ERR_ARG
+    assert bwd(G, gemm=17) == _abi.ERR_ARG
+    assert bwd(G, c=-1) == _abi.ERR_ARG
+    assert bwd(G, gemm=_abi.GEMM_SPLIT_BF16) == _abi.ERR_UNSUPPORTED    # the adjoint runs BF16 or FP64
+    assert bwd(_abi.Mat(fake, m, p - 1, p, _abi.F32, _abi.ROW_MAJOR)) == _abi.ERR_SHAPE
+    assert bwd(_abi.Mat(fake, m, p, p, _abi.F64, _abi.ROW_MAJOR)) == _abi.ERR_DTYPE  # BF16 mode takes FP32 G
+    assert bwd(G, dM=_abi.Mat(fake, m, n - 1, n, _abi.F32, _abi.ROW_MAJOR)) == _abi.ERR_SHAPE
+    assert bwd(G, dN=_abi.Mat(fake, n, p, p, 9, _abi.ROW_MAJOR)) == _abi.ERR_DTYPE
