@@ -229,13 +229,15 @@ void plan_backward(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blo
     p->ldOM = round_up(p->lmax, 4);
     p->ldON = round_up(pp, 4);
     p->Gop = p->Nu = p->outM = p->GT = p->MuT = p->outN = nullptr;
+    // BF16: both GEMMs read G in BF16 as it is stored (K-major A of the first, MN-major B of the
+    // second); FP64 keeps a transposed copy for the second
+    if (want_dM || (want_dN && !f64)) p->Gop = cv.take<char>(m * p->ldG * es);
     if (want_dM) {
-        p->Gop = cv.take<char>(m * p->ldG * es);
         p->Nu = cv.take<char>(p->lmax * p->ldG * es);
         p->outM = cv.take<char>(m * p->ldOM * (f64 ? 8 : 4));
     }
     if (want_dN) {
-        p->GT = cv.take<char>(pp * p->ldGT * es);
+        if (f64) p->GT = cv.take<char>(pp * p->ldGT * es);
         p->MuT = cv.take<char>(p->lmax * p->ldGT * es);
         p->outN = cv.take<char>(p->lmax * p->ldON * (f64 ? 8 : 4));
     }
@@ -808,11 +810,12 @@ BMM_API bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_ma
         BMM_TRY(launch_expand_blocks(plan.uidx, plan.uw, imin(c, space), plan.ucount, B->offsets, B->K, B->n,
                                      B->max_nk, plan.col, plan.w, plan.ext, plan.prefix, dst, cs));
     const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
+    if (!f64)  // G in BF16, row-major, for both GEMMs
+        BMM_TRY(launch_convert_f32_to_bf16(static_cast<const float*>(G->data), m, pp, G->ld,
+                                           static_cast<__nv_bfloat16*>(plan.Gop), plan.ldG, cs));
     if (dM) {
         // outM[h][j] = sum_f G[h,f] N[col_j, f]
         if (f64) BMM_TRY(launch_convert_to_f64(G->data, G->dtype, m, pp, G->ld, false, static_cast<double*>(plan.Gop), plan.ldG, cs));
-        else BMM_TRY(launch_convert_f32_to_bf16(static_cast<const float*>(G->data), m, pp, G->ld,
-                                                static_cast<__nv_bfloat16*>(plan.Gop), plan.ldG, cs));
         BMM_TRY(launch_gather_rows(vN, plan.col, plan.ext, plan.lmax, plan.Nu, plan.ldG, f64, cs));
         if (f64)
             BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.Gop), plan.ldG, static_cast<const double*>(plan.Nu),
@@ -827,19 +830,17 @@ BMM_API bmm_status bmm_backward(const bmm_mat* G, const bmm_mat* M, const bmm_ma
                                     plan.col, plan.w, plan.ext, plan.lmax, cs));
     }
     if (dN) {
-        // outN[j][f] = sum_h M[h, col_j] G[h, f]
+        // outN[j][f] = sum_h M[h, col_j] G[h, f]; BF16: G is the GEMM's MN-major B as converted above
         if (f64) BMM_TRY(launch_convert_to_f64(G->data, G->dtype, m, pp, G->ld, true, static_cast<double*>(plan.GT), plan.ldGT, cs));
-        else BMM_TRY(launch_transpose_f32_to_bf16(static_cast<const float*>(G->data), m, pp, G->ld,
-                                                  static_cast<__nv_bfloat16*>(plan.GT), plan.ldGT, cs));
         BMM_TRY(launch_gather_rows(vM, plan.col, plan.ext, plan.lmax, plan.MuT, plan.ldGT, f64, cs));
         if (f64)
             BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.MuT), plan.ldGT, static_cast<const double*>(plan.GT),
                                     plan.ldGT, plan.lmax, pp, m, nullptr, static_cast<double*>(plan.outN), plan.ldON, 0, cs));
         else
             BMM_TRY(launch_gemm_bf16_tc(static_cast<const __nv_bfloat16*>(plan.MuT), plan.ldGT,
-                                        static_cast<const __nv_bfloat16*>(plan.GT), plan.ldGT, plan.lmax, pp, m,
+                                        static_cast<const __nv_bfloat16*>(plan.Gop), plan.ldG, plan.lmax, pp, m,
                                         round_up(m, 64), nullptr, 1, static_cast<float*>(plan.outN), plan.ldON, 0,
-                                        dst, cs));
+                                        dst, cs, GEMM_ELEM_BF16, nullptr, 0, true));
         const int mode = dN->layout == BMM_ROW_MAJOR ? VEC_CONTIG : VEC_STRIDED;
         BMM_TRY(launch_scatter_grad(const_cast<void*>(dN->data), dN->dtype, dN->ld, mode, pp, plan.outN, gd, plan.ldON, true,
                                     plan.col, plan.w, plan.ext, plan.lmax, cs));

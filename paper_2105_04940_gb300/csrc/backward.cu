@@ -3,6 +3,8 @@
 // The redrawn indices are reduced to their distinct values (ascending) with multiplicities, so the
 // gradient scatter writes every touched column/row exactly once: no float atomics, deterministic.
 // Duplicate draws of index i carry the same scale 1/(c_k p_i), hence w_i = mult_i * scale_i.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace bmm {
@@ -123,18 +125,17 @@ __global__ void convert_f32_bf16_kernel(const float* __restrict__ G, int64_t row
         if (c < cols) out[r * ldo + c] = __float2bfloat16_rn(G[r * ldg + c]);
 }
 
-__global__ void transpose_f32_bf16_kernel(const float* __restrict__ G, int64_t rows, int64_t cols, int64_t ldg,
-                                          __nv_bfloat16* __restrict__ out, int64_t ldo) {
-    __shared__ float t[32][33];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int64_t r = r0 + i, c = c0 + threadIdx.x;
-        t[i][threadIdx.x] = (r < rows && c < cols) ? G[r * ldg + c] : 0.f;
-    }
-    __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int64_t c = c0 + i, r = r0 + threadIdx.x;
-        if (c < cols && r < rows) out[c * ldo + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+// eight elements per thread: two 16-byte loads, one 16-byte store (rows of 16-byte multiples)
+__global__ void convert_f32_bf16_vec_kernel(const float* __restrict__ G, int64_t rows, int64_t cols8, int64_t ldg,
+                                            __nv_bfloat16* __restrict__ out, int64_t ldo) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    if (c >= cols8 * 8) return;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const float4 a = *reinterpret_cast<const float4*>(G + r * ldg + c);
+        const float4 b = *reinterpret_cast<const float4*>(G + r * ldg + c + 4);
+        __nv_bfloat162 o[4] = {__floats2bfloat162_rn(a.x, a.y), __floats2bfloat162_rn(a.z, a.w),
+                               __floats2bfloat162_rn(b.x, b.y), __floats2bfloat162_rn(b.z, b.w)};
+        *reinterpret_cast<uint4*>(out + r * ldo + c) = *reinterpret_cast<const uint4*>(o);
     }
 }
 
@@ -150,16 +151,14 @@ __global__ void convert_f64_kernel(const double* __restrict__ G, int64_t rows, i
 
 cudaError_t launch_convert_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg, __nv_bfloat16* out,
                                        int64_t ldo, cudaStream_t s) {
+    if (cols % 8 == 0 && ldg % 4 == 0 && ldo % 8 == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0 &&
+        (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        dim3 grid((unsigned)ceil_div(cols / 8, 256), (unsigned)imin(imax(rows, 1), 8192));
+        (count_launch(), convert_f32_bf16_vec_kernel<<<grid, 256, 0, s>>>(G, rows, cols / 8, ldg, out, ldo));
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)ceil_div(cols, 256), (unsigned)imin(imax(rows, 1), 8192));
     (count_launch(), convert_f32_bf16_kernel<<<grid, 256, 0, s>>>(G, rows, cols, ldg, out, ldo));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_transpose_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg, __nv_bfloat16* out,
-                                         int64_t ldo, cudaStream_t s) {
-    if (ceil_div(rows, 32) > 65535) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
-    (count_launch(), transpose_f32_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(G, rows, cols, ldg, out, ldo));
     return cudaGetLastError();
 }
 
@@ -176,10 +175,10 @@ cudaError_t launch_convert_to_f64(const void* G, int dtype, int64_t rows, int64_
 template <typename T, typename O>
 __global__ void gather_rows_kernel(const T* __restrict__ X, int64_t len, int64_t ld, int mode, int64_t nvec,
                                    const int32_t* __restrict__ col, const int64_t* __restrict__ ext_dev, int64_t jmax,
-                                   O* __restrict__ out, int64_t ldo) {
+                                   O* __restrict__ out, int64_t ldo, int64_t r_begin) {
     __shared__ float t[32][33];
     const int64_t ext = *ext_dev;
-    const int64_t j0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int64_t j0 = (int64_t)blockIdx.x * 32, r0 = r_begin + (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (mode == VEC_CONTIG) {  // vector j is a storage row: copy along r
         for (int jj = ty; jj < 32; jj += blockDim.y) {
@@ -226,6 +225,32 @@ __global__ void gather_rows_f64_kernel(const T* __restrict__ X, int64_t len, int
     }
 }
 
+// Contiguous vectors, eight elements per thread (16-byte BF16 stores): row j of out is storage row
+// col_j of X converted to BF16, or zeros for j >= ext; elements r < len8 * 8 only (the caller copies
+// the tail with the general kernel)
+template <typename T>
+__global__ void gather_rows_contig_vec_kernel(const T* __restrict__ X, int64_t len8, int64_t ld, int64_t nvec,
+                                              const int32_t* __restrict__ col, const int64_t* __restrict__ ext_dev,
+                                              __nv_bfloat16* __restrict__ out, int64_t ldo) {
+    const int64_t j = blockIdx.y;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    if (r >= len8 * 8) return;
+    const int64_t c = j < *ext_dev ? (int64_t)col[j] : -1;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (c >= 0 && c < nvec) {
+        if constexpr (sizeof(T) == 2) {
+            v = *reinterpret_cast<const uint4*>(X + c * ld + r);
+        } else {
+            const float4 a = *reinterpret_cast<const float4*>(X + c * ld + r);
+            const float4 b = *reinterpret_cast<const float4*>(X + c * ld + r + 4);
+            __nv_bfloat162 o[4] = {__floats2bfloat162_rn(a.x, a.y), __floats2bfloat162_rn(a.z, a.w),
+                                   __floats2bfloat162_rn(b.x, b.y), __floats2bfloat162_rn(b.z, b.w)};
+            v = *reinterpret_cast<const uint4*>(o);
+        }
+    }
+    *reinterpret_cast<uint4*>(out + j * ldo + r) = v;
+}
+
 template <typename T>
 static cudaError_t gather_rows_t(const VecSet& v, const int32_t* col, const int64_t* ext_dev, int64_t jmax, void* out,
                                  int64_t ldo, bool f64, cudaStream_t s) {
@@ -235,9 +260,23 @@ static cudaError_t gather_rows_t(const VecSet& v, const int32_t* col, const int6
                                                                static_cast<double*>(out), ldo));
     } else {
         if (ceil_div(v.len, 32) > 65535) return cudaErrorInvalidValue;
-        dim3 grid((unsigned)ceil_div(jmax, 32), (unsigned)ceil_div(v.len, 32));
+        constexpr int64_t per16 = 16 / (int64_t)sizeof(T);
+        const bool vec = (std::is_same<T, float>::value || std::is_same<T, __nv_bfloat16>::value) &&
+                         v.mode == VEC_CONTIG && v.len >= 8 && v.ld % per16 == 0 && ldo % 8 == 0 &&
+                         jmax <= 65535 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                         (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+        if (vec) {
+            const int64_t len8 = v.len / 8;
+            dim3 g((unsigned)ceil_div(len8, 256), (unsigned)jmax);
+            (count_launch(), gather_rows_contig_vec_kernel<T><<<g, 256, 0, s>>>(X, len8, v.ld, v.count, col, ext_dev,
+                                                                                 static_cast<__nv_bfloat16*>(out), ldo));
+            if (v.len % 8 == 0) return cudaGetLastError();
+        }
+        // the general kernel: everything, or the tail past the vectorised part (r0 at a multiple of 32)
+        const int64_t done = vec ? (v.len / 8) * 8 / 32 * 32 : 0;
+        dim3 grid((unsigned)ceil_div(jmax, 32), (unsigned)ceil_div(v.len - done, 32));
         (count_launch(), gather_rows_kernel<T, __nv_bfloat16><<<grid, dim3(32, 8), 0, s>>>(
-            X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax, static_cast<__nv_bfloat16*>(out), ldo));
+            X, v.len, v.ld, v.mode, v.count, col, ext_dev, jmax, static_cast<__nv_bfloat16*>(out), ldo, done));
     }
     return cudaGetLastError();
 }
@@ -257,11 +296,11 @@ template <typename D, typename S>
 __global__ void scatter_kernel(D* __restrict__ dst, int64_t dst_ld, int dst_mode, int64_t len,
                                const S* __restrict__ src, int64_t src_ld, bool src_rows,
                                const int32_t* __restrict__ col, const double* __restrict__ w,
-                               const int64_t* __restrict__ ext_dev) {
+                               const int64_t* __restrict__ ext_dev, int64_t r_begin) {
     const int64_t ext = *ext_dev;
     const int64_t j0 = (int64_t)blockIdx.x * 32;
     if (j0 >= ext) return;
-    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int64_t r0 = r_begin + (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     // dst_mode CONTIG: element r of vector c at dst[c*ld + r] -> let tx run along r
     // dst_mode STRIDED: at dst[r*ld + c] -> let tx run along j (adjacent columns)
@@ -281,11 +320,11 @@ template <>
 __global__ void scatter_kernel<float, float>(float* __restrict__ dst, int64_t dst_ld, int dst_mode, int64_t len,
                                              const float* __restrict__ src, int64_t src_ld, bool src_rows,
                                              const int32_t* __restrict__ col, const double* __restrict__ w,
-                                             const int64_t* __restrict__ ext_dev) {
+                                             const int64_t* __restrict__ ext_dev, int64_t r_begin) {
     const int64_t ext = *ext_dev;
     const int64_t j0 = (int64_t)blockIdx.x * 32;
     if (j0 >= ext) return;
-    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int64_t r0 = r_begin + (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int q = ty; q < 32; q += blockDim.y) {
         int64_t j, r;
@@ -306,11 +345,11 @@ __global__ void scatter_kernel<__nv_bfloat16, float>(__nv_bfloat16* __restrict__
                                                      int64_t len, const float* __restrict__ src, int64_t src_ld,
                                                      bool src_rows, const int32_t* __restrict__ col,
                                                      const double* __restrict__ w,
-                                                     const int64_t* __restrict__ ext_dev) {
+                                                     const int64_t* __restrict__ ext_dev, int64_t r_begin) {
     const int64_t ext = *ext_dev;
     const int64_t j0 = (int64_t)blockIdx.x * 32;
     if (j0 >= ext) return;
-    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int64_t r0 = r_begin + (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int q = ty; q < 32; q += blockDim.y) {
         int64_t j, r;
@@ -324,25 +363,60 @@ __global__ void scatter_kernel<__nv_bfloat16, float>(__nv_bfloat16* __restrict__
     }
 }
 
+// The BF16 gradient's drawn rows (contiguous vectors) from FP32 product rows, eight elements per
+// thread with 16-byte accesses: element for element the operations of scatter_kernel<bf16, float>
+// (w_j * src rounded to FP32, added to the stored value, rounded to BF16 once); r < len8 * 8 only
+__global__ void scatter_rows_bf16_vec_kernel(__nv_bfloat16* __restrict__ dst, int64_t dst_ld, int64_t len8,
+                                             const float* __restrict__ src, int64_t src_ld,
+                                             const int32_t* __restrict__ col, const double* __restrict__ w,
+                                             const int64_t* __restrict__ ext_dev) {
+    const int64_t j = blockIdx.y;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    if (j >= *ext_dev || r >= len8 * 8) return;
+    const int64_t c = col[j];
+    const float wj = (float)w[j];
+    const float4 a = *reinterpret_cast<const float4*>(src + j * src_ld + r);
+    const float4 b = *reinterpret_cast<const float4*>(src + j * src_ld + r + 4);
+    const float sv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint4* d = reinterpret_cast<uint4*>(dst + c * dst_ld + r);
+    uint4 raw = *d;
+    __nv_bfloat16* e = reinterpret_cast<__nv_bfloat16*>(&raw);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) e[u] = __float2bfloat16_rn(__fmaf_rn(wj, sv[u], __bfloat162float(e[u])));
+    *d = raw;
+}
+
 cudaError_t launch_scatter_grad(void* dst, int dst_dtype, int64_t dst_ld, int dst_mode, int64_t len, const void* src,
                                 int src_dtype, int64_t src_ld, bool src_rows, const int32_t* col, const double* w,
                                 const int64_t* ext_dev, int64_t ext_max, cudaStream_t s) {
     if (ext_max <= 0 || len <= 0) return cudaSuccess;
     if (ceil_div(len, 32) > 65535) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)ceil_div(ext_max, 32), (unsigned)ceil_div(len, 32));
+    int64_t done = 0;  // elements of each vector the vectorised kernel covers (a multiple of 32)
+    if (dst_dtype == BMM_BF16 && src_dtype == BMM_F32 && dst_mode == VEC_CONTIG && src_rows && len >= 32 &&
+        ext_max <= 65535 && dst_ld % 8 == 0 && src_ld % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 &&
+        (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int64_t len8 = len / 32 * 4;  // whole 32-element tiles, so that the rest starts at a tile
+        dim3 g((unsigned)ceil_div(len8, 256), (unsigned)ext_max);
+        (count_launch(), scatter_rows_bf16_vec_kernel<<<g, 256, 0, s>>>(static_cast<__nv_bfloat16*>(dst), dst_ld, len8,
+                                                                        static_cast<const float*>(src), src_ld, col, w,
+                                                                        ext_dev));
+        done = len8 * 8;
+        if (done == len) return cudaGetLastError();
+    }
+    dim3 grid((unsigned)ceil_div(ext_max, 32), (unsigned)ceil_div(len - done, 32));
     dim3 block(32, 8);
     if (dst_dtype == BMM_F64 && src_dtype == BMM_F64)
         (count_launch(), scatter_kernel<double, double><<<grid, block, 0, s>>>(static_cast<double*>(dst), dst_ld, dst_mode, len,
                                                              static_cast<const double*>(src), src_ld, src_rows, col, w,
-                                                             ext_dev));
+                                                             ext_dev, done));
     else if (dst_dtype == BMM_F32 && src_dtype == BMM_F32)
         (count_launch(), scatter_kernel<float, float><<<grid, block, 0, s>>>(static_cast<float*>(dst), dst_ld, dst_mode, len,
                                                            static_cast<const float*>(src), src_ld, src_rows, col, w,
-                                                           ext_dev));
+                                                           ext_dev, done));
     else if (dst_dtype == BMM_BF16 && src_dtype == BMM_F32)
         (count_launch(), scatter_kernel<__nv_bfloat16, float><<<grid, block, 0, s>>>(
                              static_cast<__nv_bfloat16*>(dst), dst_ld, dst_mode, len, static_cast<const float*>(src),
-                             src_ld, src_rows, col, w, ext_dev));
+                             src_ld, src_rows, col, w, ext_dev, done));
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

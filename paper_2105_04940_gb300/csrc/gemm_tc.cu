@@ -36,6 +36,7 @@ namespace {
 using namespace ptx;
 constexpr int BM = 128;
 constexpr int ROW_BYTES = 128;  // K per stage: one 128-byte swizzled row
+constexpr int kMnBoxBytes = 64 * ROW_BYTES;  // an MN-major B box: 64 N x 64 K rows of 128 bytes
 
 // EK: element kind, 0 = BF16 (kind::f16), 1 = FP8 e4m3 (kind::f8f6f4).  PAIR: CTA-pair tiles of
 // TILE_M = 256 output rows (128 per CTA) by BN = 256 or 512 columns, B_ROWS = BN / 2 rows of B per
@@ -98,6 +99,7 @@ struct GemmProblem {
     int tma_out;
     int raster;
     const float* scale;  // device factor applied to the product (FP8), or null
+    int b_mn;            // B is MN-major (BF16 only): rows of K, N contiguous; boxes of 64 N x 64 K
 };
 template <int G> struct GemmTable {
     int count;
@@ -210,12 +212,24 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                     if (leader) mbar_expect_tx(fb, C::STAGE_TX);
                     tma_load_2d_pair(smem_u32(sA + stage * C::A_BYTES), &pr.mapA, fb0, kb * BK,
                                      tm * C::TILE_M + BM * (int)rank);
-                    tma_load_2d_pair(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb0, kb * BK,
-                                     tn * BN + C::B_ROWS * (int)rank);
+                    if (!EK && pr.b_mn) {
+                        for (int j = 0; j < C::B_ROWS / 64; ++j)
+                            tma_load_2d_pair(smem_u32(sB + stage * C::B_BYTES + j * kMnBoxBytes), &pr.mapB, fb0,
+                                             tn * BN + C::B_ROWS * (int)rank + 64 * j, kb * BK);
+                    } else {
+                        tma_load_2d_pair(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb0, kb * BK,
+                                         tn * BN + C::B_ROWS * (int)rank);
+                    }
                 } else {
                     mbar_expect_tx(fb, C::STAGE_TX);
                     tma_load_2d(smem_u32(sA + stage * C::A_BYTES), &pr.mapA, fb, kb * BK, tm * BM);
-                    tma_load_2d(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb, kb * BK, tn * BN);
+                    if (!EK && pr.b_mn) {
+                        for (int j = 0; j < C::B_ROWS / 64; ++j)
+                            tma_load_2d(smem_u32(sB + stage * C::B_BYTES + j * kMnBoxBytes), &pr.mapB, fb,
+                                        tn * BN + 64 * j, kb * BK);
+                    } else {
+                        tma_load_2d(smem_u32(sB + stage * C::B_BYTES), &pr.mapB, fb, kb * BK, tn * BN);
+                    }
                 }
                 issued_mask |= 1u << stage;
                 issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
@@ -241,6 +255,10 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         for (int tile = first_tile; tile < num_tiles && !aborted; tile += tile_step, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             const int num_kb = problem_kb<BK>(pr);
+            // an MN-major B advances 16 rows (2 KB) per K step instead of 32 bytes
+            const bool bmn = !EK && pr.b_mn;
+            const uint32_t idesc = C::IDESC | (bmn ? (1u << 16) : 0u);
+            const uint64_t bstep = bmn ? (uint64_t)((16 * ROW_BYTES) >> 4) : 2ull;
             const int acc = C::ACCS == 2 ? (it & 1) : 0;
             const uint32_t aph = C::ACCS == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
             if (!wait_fast(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
@@ -256,7 +274,8 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 }
                 tc_fence_after();
                 const uint64_t ad = sw128_desc(smem_u32(sA + stage * C::A_BYTES));
-                const uint64_t bd = sw128_desc(smem_u32(sB + stage * C::B_BYTES));
+                const uint32_t baddr = smem_u32(sB + stage * C::B_BYTES);
+                const uint64_t bd = bmn ? sw128_mn_desc(baddr, kMnBoxBytes) : sw128_desc(baddr);
 #pragma unroll
                 for (int k = 0; k < BK / C::KMMA; ++k) {
                     const uint32_t acc_in = (kb > 0 || k > 0) ? 1u : 0u;
@@ -265,17 +284,18 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
 #pragma unroll
                         for (int h = 0; h < C::NMMA; ++h) {
                             const uint32_t dh = d + (uint32_t)(256 * h);
-                            const uint64_t bh = bd + (uint64_t)((h * 128 * ROW_BYTES) >> 4) + 2ull * k;
+                            // (128 rows of a K-major B, or two 64-column boxes of an MN-major one: 16 KB)
+                            const uint64_t bh = bd + (uint64_t)((h * 128 * ROW_BYTES) >> 4) + bstep * k;
                             if (EK)
                                 tc_mma_f8_pair(dh, ad + 2ull * k, bh, C::IDESC, acc_in);
                             else
-                                tc_mma_bf16_pair(dh, ad + 2ull * k, bh, C::IDESC, acc_in);
+                                tc_mma_bf16_pair(dh, ad + 2ull * k, bh, idesc, acc_in);
                         }
                     } else {
                         if (EK)
                             tc_mma_f8(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
                         else
-                            tc_mma_bf16(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
+                            tc_mma_bf16(d, ad + 2ull * k, bd + bstep * k, idesc, acc_in);
                     }
                 }
                 if constexpr (PAIR)
@@ -468,6 +488,20 @@ bool make_out_map(CUtensorMap* m, float* out, int64_t M, int64_t N, int64_t ldo)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// MN-major BF16 B: a row-major K x N matrix (row stride ld elements), boxes of 64 N (128 bytes) by
+// 64 K rows, 128-byte swizzle (the canonical MN-major layout: 8-row atoms of 1024 bytes)
+bool make_map_mn(CUtensorMap* m, const void* ptr, int64_t N, int64_t kdim, int64_t ld) {
+    auto fn = encode_fn();
+    if (fn == nullptr) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)kdim};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {64, 64};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int num_sms() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -480,13 +514,16 @@ int num_sms() {
 // cannot be made.
 bool fill_problem(GemmProblem* pr, int bn, int raster, const void* A, int64_t lda, const void* B, int64_t ldb,
                   int64_t M, int64_t N, int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
-                  int64_t ldo, int accumulate, int elem, const float* scale) {
+                  int64_t ldo, int accumulate, int elem, const float* scale, bool b_mn = false) {
     const int esize = elem == GEMM_ELEM_E4M3 ? 1 : 2;
     const bool pair = bn == kPairTile || bn == kPairTileWide;
     const int tile_m = pair ? 2 * BM : BM, tile_n = bn == kPairTileWide ? 512 : (pair ? 256 : bn);
     const int b_rows = pair ? tile_n / 2 : bn;
-    if (!make_map(&pr->mapA, A, M, kdim, lda, BM, esize) || !make_map(&pr->mapB, B, N, kdim, ldb, b_rows, esize))
+    if (b_mn && elem != GEMM_ELEM_BF16) return false;
+    if (!make_map(&pr->mapA, A, M, kdim, lda, BM, esize) ||
+        !(b_mn ? make_map_mn(&pr->mapB, B, N, kdim, ldb) : make_map(&pr->mapB, B, N, kdim, ldb, b_rows, esize)))
         return false;
+    pr->b_mn = b_mn ? 1 : 0;
     pr->scale = scale;
     pr->out = out;
     pr->ldo = ldo;
@@ -569,10 +606,10 @@ cudaError_t launch_any(int bn, int elem, const GemmTable<G>& tab, DevStatus* st,
 
 // strides multiples of 16 bytes, K padded to the 128-byte stage with a host extent
 bool gemm_args_ok(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N, int64_t kdim,
-                  int64_t k_host, const int64_t* k_dev, int elem) {
+                  int64_t k_host, const int64_t* k_dev, int elem, bool b_mn = false) {
     const int64_t per16 = elem == GEMM_ELEM_E4M3 ? 16 : 8, bk = elem == GEMM_ELEM_E4M3 ? 128 : 64;
     if (M > 0x7fffffff || N > 0x7fffffff || (lda % per16) != 0 || (ldb % per16) != 0 || kdim <= 0 || kdim > lda ||
-        kdim > ldb || (k_dev == nullptr && (k_host % bk) != 0))
+        (b_mn ? (N > ldb || elem != GEMM_ELEM_BF16) : kdim > ldb) || (k_dev == nullptr && (k_host % bk) != 0))
         return false;
     return !((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15));
 }
@@ -635,15 +672,15 @@ bool tc_gemm_supported() {
 cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
                                 int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out, int64_t ldo,
                                 int accumulate, DevStatus* st, cudaStream_t s, int elem, const float* scale,
-                                int64_t tune_k) {
+                                int64_t tune_k, bool b_mn) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    if (!gemm_args_ok(A, lda, B, ldb, M, N, kdim, k_host, k_dev, elem)) return cudaErrorInvalidValue;
+    if (!gemm_args_ok(A, lda, B, ldb, M, N, kdim, k_host, k_dev, elem, b_mn)) return cudaErrorInvalidValue;
     const TileChoice tc = gemm_tile_choice(elem, M, N, tune_k > 0 ? tune_k : kdim);
     const int BN = tc.bn;
     GemmTable<1> tab;
     tab.count = 1;
     if (!fill_problem(&tab.prob[0], BN, tc.raster, A, lda, B, ldb, M, N, kdim, k_host, k_dev, k_mult, out, ldo,
-                      accumulate, elem, scale))
+                      accumulate, elem, scale, b_mn))
         return cudaErrorInvalidValue;
     tab.prob[0].tile_begin = 0;
     tab.total_tiles = tab.prob[0].tiles_m * tab.prob[0].tiles_n;

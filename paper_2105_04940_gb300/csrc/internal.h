@@ -209,11 +209,14 @@ enum GemmElem { GEMM_ELEM_BF16 = 0, GEMM_ELEM_E4M3 = 1 };
 // lda/ldb (elements, 16-byte multiples).  Columns >= kdim of A and B read as zero.  The K loop runs
 // to k_mult * round_up(*k_dev, BK) if k_dev, else to k_host (a multiple of BK); BK = 64 (BF16) or
 // 128 (e4m3).  scale (device, e4m3 only) may be null.  tune_k: the depth whose tile choice to use
-// (a K-chunk of a longer product takes the whole product's), kdim if 0.
+// (a K-chunk of a longer product takes the whole product's), kdim if 0.  b_mn (BF16 only): B is
+// given MN-major instead, as a row-major K x N matrix with row stride ldb >= N (rows >= kdim read as
+// zero); every output element is the same dot product in the same K order as with a K-major B.
 cudaError_t launch_gemm_bf16_tc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
                                 int64_t kdim, int64_t k_host, const int64_t* k_dev, int k_mult, float* out,
                                 int64_t ldo, int accumulate, DevStatus* st, cudaStream_t s,
-                                int elem = GEMM_ELEM_BF16, const float* scale = nullptr, int64_t tune_k = 0);
+                                int elem = GEMM_ELEM_BF16, const float* scale = nullptr, int64_t tune_k = 0,
+                                bool b_mn = false);
 // K is k_host, or *k_dev rounded up to 64; k_max bounds it for the choice of K splits, whose
 // partial tiles go to part (gemm_f64_split_elems(M, N, k_max) doubles; without it, no split).
 cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,
@@ -259,8 +262,6 @@ int64_t unique_scratch_bytes(int64_t space, int64_t count);
 cudaError_t launch_unique(const int32_t* idx, const double* scale, int64_t count, int64_t space,
                           int32_t* uidx, double* uw, int64_t* ucount_dev, void* scratch, DevStatus* st,
                           cudaStream_t s);
-cudaError_t launch_transpose_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg,
-                                         __nv_bfloat16* out, int64_t ldo, cudaStream_t s);
 cudaError_t launch_convert_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg,
                                        __nv_bfloat16* out, int64_t ldo, cudaStream_t s);
 cudaError_t launch_convert_to_f64(const void* G, int dtype, int64_t rows, int64_t cols, int64_t ldg, bool transpose,

@@ -196,3 +196,36 @@ def test_batch_level_tuning_keeps_results(bmm):
     for a_, r in zip(before, res2):
         np.testing.assert_array_equal(host(r["out"]), a_)
     A.bmm_autotune_clear()
+
+
+@pytest.mark.parametrize("m,p", [(300, 264), (100, 70), (520, 1000)])
+def test_adjoint_tile_choices_do_not_change_gradients(bmm, m, p):
+    """The adjoint's GEMMs -- dM with G as a K-major A, dN with G as an MN-major B (rows of K, boxes
+    of 64 columns) -- give the same gradients bit for bit under every tile choice, on ragged shapes
+    (p not a multiple of 64, m below one 128-row tile)."""
+    A = bmm._abi
+    gm = A.GEMM_BF16
+    n = 3000
+    off = S.block_offsets_uneven(n, 30, 40, 160, seed=71)
+    M, N = S.scaled_gaussian(m, n, p, off, 1.0, seed=72, dtype=np.float32)
+    Mt, Nt = to_dev(M), to_dev(N)
+    L = 700
+    prob = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=gm)
+    r = bmm.run(prob, "ONC", L, seed=5, gemm_mode=gm, compute_product=False)
+    Gt = to_dev(np.random.default_rng(73).standard_normal((m, p)).astype(np.float32))
+    lmax = min(L, n)  # rows of the gathered operands: at most one per distinct draw
+    A.bmm_autotune_clear()
+    grads = []
+    for bn, ra in CHOICES:
+        A.bmm_autotune_set(m, lmax, p, gm, bn, ra)    # dM = G (m x p) times the drawn rows of N
+        A.bmm_autotune_set(lmax, p, m, gm, bn, ra)    # dN = drawn columns of M (transposed) times G
+        dM = torch.full((m, n), float("nan"), dtype=torch.float32, device=Mt.device)
+        dN = torch.full((n, p), float("nan"), dtype=torch.float32, device=Mt.device)
+        bmm.bmm_backward(Gt, Mt, Nt, prob.B, r["unit"], r["p"], r["ck"], L, 5, r["sid"], gm, dM, dN, False, prob.ws)
+        bmm.check_status(prob)
+        grads.append((host(dM), host(dN)))
+    A.bmm_autotune_clear()
+    for gM, gN in grads[1:]:
+        np.testing.assert_array_equal(gM, grads[0][0])
+        np.testing.assert_array_equal(gN, grads[0][1])
+    assert np.all(np.isfinite(grads[0][0])) and np.all(np.isfinite(grads[0][1]))
