@@ -135,6 +135,36 @@ __device__ __forceinline__ int ld_cluster_s32(uint32_t cluster_addr) {
     return v;
 }
 
+// The MMAs of one stage (BK elements of K in KMMA steps).  A is K-major (32 bytes per step); B is
+// K-major (32 bytes per step) or, with BMN, MN-major (16 rows of 128 bytes per step, the transpose-B
+// bit set).  In PAIR form MMA h takes B rows (or columns) 128 h .. 128 h + 127 of each CTA -- 16 KB
+// into the stage either way -- into accumulator columns 256 h ...
+template <class C, int EK, bool PAIR, bool BMN>
+__device__ __forceinline__ void mma_stage(uint32_t d, uint64_t ad, uint64_t bd, bool accumulate) {
+    constexpr uint32_t idesc = C::IDESC | (BMN ? (1u << 16) : 0u);
+    constexpr uint64_t bstep = BMN ? (uint64_t)((16 * ROW_BYTES) >> 4) : 2ull;
+#pragma unroll
+    for (int k = 0; k < C::BK / C::KMMA; ++k) {
+        const uint32_t acc_in = (accumulate || k > 0) ? 1u : 0u;
+        if constexpr (PAIR) {
+#pragma unroll
+            for (int h = 0; h < C::NMMA; ++h) {
+                const uint32_t dh = d + (uint32_t)(256 * h);
+                const uint64_t bh = bd + (uint64_t)((h * 128 * ROW_BYTES) >> 4) + bstep * k;
+                if (EK)
+                    tc_mma_f8_pair(dh, ad + 2ull * k, bh, idesc, acc_in);
+                else
+                    tc_mma_bf16_pair(dh, ad + 2ull * k, bh, idesc, acc_in);
+            }
+        } else {
+            if (EK)
+                tc_mma_f8(d, ad + 2ull * k, bd + bstep * k, idesc, acc_in);
+            else
+                tc_mma_bf16(d, ad + 2ull * k, bd + bstep * k, idesc, acc_in);
+        }
+    }
+}
+
 template <int BN, int G, int EK, bool PAIR>
 __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_constant__ GemmTable<G> tab, DevStatus* st) {
     using C = Cfg<BN, EK, PAIR>;
@@ -255,10 +285,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
         for (int tile = first_tile; tile < num_tiles && !aborted; tile += tile_step, ++it) {
             const GemmProblem& pr = tab.prob[find_problem(tab, tile)];
             const int num_kb = problem_kb<BK>(pr);
-            // an MN-major B advances 16 rows (2 KB) per K step instead of 32 bytes
-            const bool bmn = !EK && pr.b_mn;
-            const uint32_t idesc = C::IDESC | (bmn ? (1u << 16) : 0u);
-            const uint64_t bstep = bmn ? (uint64_t)((16 * ROW_BYTES) >> 4) : 2ull;
+            const bool bmn = !EK && pr.b_mn;  // B MN-major (BF16 only)
             const int acc = C::ACCS == 2 ? (it & 1) : 0;
             const uint32_t aph = C::ACCS == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
             if (!wait_fast(smem_u32(&bar_tempty[acc]), aph ^ 1u, &s_abort)) {
@@ -275,29 +302,11 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
                 tc_fence_after();
                 const uint64_t ad = sw128_desc(smem_u32(sA + stage * C::A_BYTES));
                 const uint32_t baddr = smem_u32(sB + stage * C::B_BYTES);
-                const uint64_t bd = bmn ? sw128_mn_desc(baddr, kMnBoxBytes) : sw128_desc(baddr);
-#pragma unroll
-                for (int k = 0; k < BK / C::KMMA; ++k) {
-                    const uint32_t acc_in = (kb > 0 || k > 0) ? 1u : 0u;
-                    if constexpr (PAIR) {
-                        // MMA h: B rows 128 h .. 128 h + 127 of each CTA into accumulator columns 256 h ..
-#pragma unroll
-                        for (int h = 0; h < C::NMMA; ++h) {
-                            const uint32_t dh = d + (uint32_t)(256 * h);
-                            // (128 rows of a K-major B, or two 64-column boxes of an MN-major one: 16 KB)
-                            const uint64_t bh = bd + (uint64_t)((h * 128 * ROW_BYTES) >> 4) + bstep * k;
-                            if (EK)
-                                tc_mma_f8_pair(dh, ad + 2ull * k, bh, C::IDESC, acc_in);
-                            else
-                                tc_mma_bf16_pair(dh, ad + 2ull * k, bh, idesc, acc_in);
-                        }
-                    } else {
-                        if (EK)
-                            tc_mma_f8(d, ad + 2ull * k, bd + 2ull * k, C::IDESC, acc_in);
-                        else
-                            tc_mma_bf16(d, ad + 2ull * k, bd + bstep * k, idesc, acc_in);
-                    }
-                }
+                // one branch per stage; each form issues with compile-time descriptor steps
+                if (bmn)
+                    mma_stage<C, EK, PAIR, true>(d, ad, sw128_mn_desc(baddr, kMnBoxBytes), kb > 0);
+                else
+                    mma_stage<C, EK, PAIR, false>(d, ad, sw128_desc(baddr), kb > 0);
                 if constexpr (PAIR)
                     tc_commit_pair_mc(smem_u32(&bar_empty[stage]), (uint16_t)3);
                 else
