@@ -304,8 +304,9 @@ def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEM
     (product i works in probs[i % len(probs)]); seeds: one per product; outs: output matrices used
     round-robin (product i writes outs[i % len(outs)], which keeps it until product i + len(outs)
     overwrites it); replicate: as in run().  Enqueues everything on the current stream and the side
-    stream and returns; the current stream has joined the side stream when it returns.  Device status
-    is read with check_status() on each state, as after run().
+    stream and returns; the current stream has joined the side stream when it returns, so a whole
+    sequence can be captured in a CUDA graph (after one eager call has created the side stream) and
+    replayed.  Device status is read with check_status() on each state, as after run().
 
     events: if a list, (name, product, torch.cuda.Event) triples are appended for a timeline (timing
     only): stats_start / stats_end and gemm_start / gemm_end on the current stream, side_start /

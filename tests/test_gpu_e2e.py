@@ -267,3 +267,35 @@ def test_benched_path_degenerate_inputs(bmm, case):
         want = oracle.sampled_product_columns(M, N, idx, scale)
         tol = 2.0 ** -7 + L * 2.0 ** -22
         assert np.all(np.abs(got - want) <= tol * product_bound(M, N, idx, scale) + 1e-300)
+
+
+def test_pipelined_products_replay_in_a_cuda_graph(bmm):
+    """run_pipelined forks from and joins back into the caller's stream with events only, so a whole
+    sequence of pipelined products can be captured in a CUDA graph; each replay recomputes every
+    product (statistics, design, draws, gathers, GEMM) and gives run()'s outputs bit for bit."""
+    A = bmm._abi
+    m, n, p, K = 700, 12288, 392, 170
+    off, _, _, Mt, Nt = _inputs("f32", m, n, p, K, seed=371)
+    L = 1536
+    seeds = [81, 82, 83]
+    probs = [bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16) for _ in range(2)]
+    outs = [torch.empty(m, p, device="cuda") for _ in range(3)]
+    bmm.run_pipelined(probs, L, seeds, outs)  # eager once: the side stream exists before the capture
+    torch.cuda.synchronize()
+    for o in outs:
+        o.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bmm.run_pipelined(probs, L, seeds, outs)
+    for o in outs:
+        o.fill_(float("nan"))
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for pr in probs:
+        bmm.check_status(pr)
+    ref = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+    for i, sd in enumerate(seeds):
+        r = bmm.run(ref, "OPL", L, seed=sd, gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
+        bmm.check_status(ref)
+        assert torch.equal(outs[i], r["out"]), i
