@@ -71,7 +71,9 @@ _UPLOADS: dict = {}
 def _upload(arr: np.ndarray, dev):
     """Device copy of a small host int64 array, without making the host wait for the stream (a
     pageable copy would): pinned staging and a non-blocking copy, cached per content and device so
-    that repeated products with the same blocks (every layer, every step) upload once."""
+    that repeated products with the same blocks (every layer, every step) upload once.  Once the copy
+    has landed no stream waits for it again, so calls captured in a CUDA graph after one eager call
+    depend on no work outside the capture."""
     torch = _torch()
     key = (str(dev), arr.dtype.str, arr.tobytes())
     hit = _UPLOADS.get(key)
@@ -89,7 +91,10 @@ def _upload(arr: np.ndarray, dev):
         hit = _UPLOADS[key] = (t, ev)
     t, ev = hit
     if ev is not None:
-        torch.cuda.current_stream(dev).wait_event(ev)  # the copy may have been issued on another stream
+        if ev.query():  # the copy has landed: no stream needs to wait for it again
+            _UPLOADS[key] = (t, None)
+        else:  # issued on some stream and still in flight
+            torch.cuda.current_stream(dev).wait_event(ev)
     return t
 
 

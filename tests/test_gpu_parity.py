@@ -1160,3 +1160,42 @@ def test_sample_batched_equals_single_products(bmm, unit):
         wi, wsc = oracle.sample_blocks(host(ps[0]), cs[0], seeds[0], sids[0])
     np.testing.assert_array_equal(host(idx_b[0]), wi)
     np.testing.assert_array_equal(host(sc_b[0]), wsc)
+
+
+def test_autograd_step_replays_in_a_cuda_graph(bmm):
+    """A forward and backward through sampled_matmul (BF16 mode) captured in a CUDA graph after one
+    eager step: each replay recomputes the statistics, draws, product and adjoint, and gives the
+    eager step's output and gradients bit for bit (same seed)."""
+    off = S.block_offsets_equal(1024, 16)
+    M, N = S.scaled_gaussian(192, 1024, 136, off, 1.0, seed=13, dtype=np.float32)
+    X = to_dev(M).to(torch.bfloat16).requires_grad_(True)
+    W = to_dev(N).to(torch.bfloat16).requires_grad_(True)
+    R = to_dev(np.random.default_rng(14).standard_normal((192, 136)).astype(np.float32))
+
+    def step():
+        y = bmm.sampled_matmul(X, W, off, method="OPL", c=256, seed=9, mode="bf16")
+        (y * R).sum().backward()
+        return y
+
+    for t in (X, W):
+        t.grad = torch.zeros_like(t)
+    y_eager = step().detach().clone()
+    gX, gW = X.grad.clone(), W.grad.clone()
+    for t in (X, W):
+        t.grad.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        y_static = step()
+    for t in (X, W):
+        t.grad.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y_static, y_eager)
+    assert torch.equal(X.grad, gX) and torch.equal(W.grad, gW)
+    assert torch.count_nonzero(X.grad) > 0
