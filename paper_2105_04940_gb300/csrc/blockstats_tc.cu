@@ -73,7 +73,6 @@ template <> struct Tr<float> {
     static constexpr int E = 32;
     static constexpr int kAlign = 4;            // elements per 16 bytes
     static constexpr int kMnSubRows = 32;       // rows of a strided sub-tile (4 MMAs of K = 8)
-    static constexpr int kMnPer = kMnRows / kMnSubRows;
     static constexpr uint32_t kMnKstep = 64;    // 8 rows x 128 bytes, in descriptor units
     static constexpr int kCornerRow0 = 32;      // first operand row of the corner MMA's A
     static constexpr uint32_t kFmt = 2;         // TF32
@@ -100,7 +99,6 @@ template <> struct Tr<__nv_bfloat16> {
     static constexpr int E = 64;
     static constexpr int kAlign = 8;
     static constexpr int kMnSubRows = 64;       // 4 MMAs of K = 16
-    static constexpr int kMnPer = kMnRows / kMnSubRows;
     static constexpr uint32_t kMnKstep = 128;   // 16 rows x 128 bytes
     static constexpr int kCornerRow0 = 64;      // an MN atom is 64 rows wide
     static constexpr uint32_t kFmt = 1;         // BF16 (kind::f16)
@@ -181,7 +179,7 @@ struct OperandMaps {
 // pass (STATS) and read (s) in the Gram-only pass; f [K] is written by both.  wins
 // [stats_windows_ints(K)] is workspace: the window starts (wins[0 .. W], wins[W] = K), wins[K + 1] = W,
 // wins[K + 2] = T and wins[K + 3 .. K + 3 + T) the order in which the last T windows are handed out.
-struct __align__(64) StatsProblem {
+struct StatsProblem {
     OperandMaps mM, mN;
     const int64_t* off;
     long long K, n, m, p;

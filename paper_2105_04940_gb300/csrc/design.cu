@@ -255,7 +255,7 @@ __device__ __forceinline__ void blocksizes_body(int kind, const double* __restri
     __shared__ int sNact[2];
     __shared__ float sRedF[32];
     __shared__ double sLam0;
-    __shared__ int sEgLo[kEndgameSteps], sEgN[kEndgameSteps], sEgPre[kEndgameSteps];
+    __shared__ int sEgLo[kEndgameSteps], sEgPre[kEndgameSteps];
     __shared__ unsigned long long sEgStep[kEndgameSteps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -397,7 +397,6 @@ __device__ __forceinline__ void blocksizes_body(int kind, const double* __restri
                     clo = count_at(bits_to_lam(lo), g[k], sNk[k]);
                     dlt = count_at(bits_to_lam(hi), g[k], sNk[k]) - clo;
                     sEgLo[tid] = (int)clo;
-                    sEgN[tid] = (int)dlt;
                 }
                 long long total_lo = clo, total_dlt = dlt;
                 block_sum2_ll(&total_lo, &total_dlt, sSum2);
