@@ -301,3 +301,16 @@ def test_core_entry_points_validate_on_host(lib):
     assert bwd(_abi.Mat(fake, m, p, p, _abi.F64, _abi.ROW_MAJOR)) == _abi.ERR_DTYPE  # BF16 mode takes FP32 G
     assert bwd(G, dM=_abi.Mat(fake, m, n - 1, n, _abi.F32, _abi.ROW_MAJOR)) == _abi.ERR_SHAPE
     assert bwd(G, dN=_abi.Mat(fake, n, p, p, 9, _abi.ROW_MAJOR)) == _abi.ERR_DTYPE
+
+
+def test_run_pipelined_refuses_on_the_host():
+    """run_pipelined checks its arguments before it touches a device."""
+    import paper_2105_04940_gb300 as P
+    with pytest.raises(ValueError):
+        P.run_pipelined([], 100, [1], [object()])
+    with pytest.raises(ValueError):
+        P.run_pipelined([object()], 100, [1], [object()])
+    with pytest.raises(ValueError):
+        P.run_pipelined([object(), object()], 100, [1], [])
+    with pytest.raises(ValueError):
+        P.run_pipelined([object(), object()], 100, [1], [object()], gemm_mode=P._abi.GEMM_F64)
