@@ -316,11 +316,11 @@ def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEM
     events: if a list, (name, product, torch.cuda.Event) triples are appended for a timeline (timing
     only): stats_start / stats_end and gemm_start / gemm_end on the current stream, side_start /
     design_end / gathers_end on the side stream."""
-    torch = _torch()
     if len(probs) < 2 or not outs:
         raise ValueError("run_pipelined needs two or more problem states and an output")
     if gemm_mode != A.GEMM_BF16:
         raise ValueError("run_pipelined runs the BF16 sampled GEMM")
+    torch = _torch()
     seeds = list(seeds)
     dev = probs[0].M.device
     main = torch.cuda.current_stream(dev)
