@@ -342,11 +342,25 @@ def workload_name(args):
 
 
 # ---------------------------------------------------------------- native arm
-def stage_work(w, L, nk, method):
+def gemm_depth(r, off):
+    """Depth of a product's sampled GEMM: the apply merges repeated draws of an index into one term
+    (multiplicity times scale), so the GEMM runs over the distinct drawn columns (column unit) or the
+    columns of the distinct drawn blocks (block unit), not over every draw."""
+    import torch
+
+    u = torch.unique(r["idx"].long()).cpu().numpy()
+    if r["unit"] == 0:
+        return int(u.size)
+    return int(np.sum(np.diff(off)[u]))
+
+
+def stage_work(w, L, nk, method, depth=None):
     """Algorithmic work per product of each stage (bytes for HBM-bound, flops for compute-bound).
     `kernel` marks the stages that are one kernel launch (the headline roofline is taken over
-    those: the statistics stage is three kernels, apply two gathers and the GEMM)."""
+    those: the statistics stage is three kernels, apply two gathers and the GEMM).  depth: the
+    sampled GEMM's depth (distinct drawn columns), L if not given."""
     m, n, p = w["m"], w["n"], w["p"]
+    L = L if depth is None else depth
     return {
         "stats": {"bound": "hbm", "bytes": (m * n + n * p) * 4 + 8 * (2 * n + 4 * w["K"]), "kernel": False},
         "exact_f": {"bound": "alu", "flops": float(2 * (m + p) * np.sum(nk.astype(np.float64) ** 2)), "kernel": True},
@@ -383,7 +397,7 @@ def time_norm_pass(P, prob, w, pk, reps=20):
             "note": "norm pass and eq. 3.8 probabilities (BMM_F_NONE), inputs larger than L2, back to back"}
 
 
-def time_gemm_part(P, prob, w, L, r, pk, reps=20):
+def time_gemm_part(P, prob, w, L, r, pk, depth, reps=20):
     """The sampled GEMM of the column-sampled BF16 product (its part of bmm_apply, on the gathered
     BF16 operands of the step's own draws r) timed alone with CUDA events outside the timed region,
     back to back: its tensor fraction on real operands, beside the autotuner's figure on constant
@@ -408,11 +422,12 @@ def time_gemm_part(P, prob, w, L, r, pk, reps=20):
     torch.cuda.synchronize()
     P.check_status(prob)
     ms = e0.elapsed_time(e1) / reps
-    tflops = 2.0 * m * p * L / (ms * 1e-3) / 1e12
+    tflops = 2.0 * m * p * depth / (ms * 1e-3) / 1e12
     tile = A.bmm_autotune_get(m, p, L, A.GEMM_BF16)
     return {"bound": "tensor", "achieved": tflops, "peak": pk["bf16"], "unit": "TFLOP/s", "frac": tflops / pk["bf16"],
-            "ms": ms, "reps": reps, "tile": tile,
-            "note": "GEMM part of the BF16 apply on the step's gathered operands, back to back, of the burst peak"}
+            "ms": ms, "reps": reps, "tile": tile, "depth": depth, "draws": L,
+            "note": "GEMM part of the BF16 apply on the step's gathered operands (depth = the distinct drawn "
+                    "columns), back to back, of the burst peak"}
 
 
 def pipeline_timeline(P, probs, c, outs, rank, nprod=12):
@@ -532,7 +547,8 @@ def native_arm(args, ws, rank, local):
     value = elapsed_ms / (args.steps * ws)
 
     pk = peaks()
-    work = stage_work(w, L, nk, args.method)
+    depth = gemm_depth(last, off) if last is not None else None
+    work = stage_work(w, L, nk, args.method, depth)
     roof_all = {}
     for name, wk in work.items():
         if name not in stages:
@@ -568,7 +584,7 @@ def native_arm(args, ws, rank, local):
     if args.method in ("OPL", "ONC", "ONU", "ONMCNR") and args.mode != "f64":
         norm_alone = time_norm_pass(P, prob, w, pk)
     if args.method in ("OPL", "ONC", "ONU", "ONMCNR") and args.mode == "bf16" and last is not None:
-        gemm_alone = time_gemm_part(P, prob, w, L, last, pk)
+        gemm_alone = time_gemm_part(P, prob, w, L, last, pk, depth)
 
     result = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -576,6 +592,9 @@ def native_arm(args, ws, rank, local):
         "dtype": args.mode, "data": "synthetic",
         "norm_pass_alone": norm_alone, "gemm_part_alone": gemm_alone,
         "sequential_ms_per_step": seq_ms / args.steps, "pipeline_timeline": timeline,
+        "gemm_depth": {"draws": c, "distinct": depth,
+                       "note": "repeated draws of an index are one GEMM term (multiplicity x scale); distinct "
+                               "drawn columns of one product"},
         "config": run_config(args, ws),
         "roofline": roofline, "stages_ms": stages, "stage_rooflines": roof_all,
         "clocks": clocks, "gpu_launches": int(launches),
@@ -732,6 +751,7 @@ def batched_run(args, ws, rank, local):
                    "streams": args.streams,
                    "statistics": "fused, grouped" if args.stats == "fused" else "norm pass grouped, Gram pass grouped",
                    "products": len(probs), "input_gb": in_bytes / 1e9, "gemm_tflop": flops / 1e12,
+                   "gemm_tflop_note": "2 m p L at L draws per product; the GEMMs run over the distinct drawn columns",
                    "l2": "inputs larger than the 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "batch_ms": batch_ms, "eager_batch_ms": eager_ms,
         "autotune": None if tune is None else {"choice": tune["choice"], "seconds": tune_s,
@@ -819,6 +839,8 @@ def mlp_run(args, ws, rank, local):
         "config": {"workload": "MLP: X 4096x16384 BF16, 4 layers W 16384x16384, GELU, OPL K=256 blocks of 64, "
                                "c=64 blocks (L=4096), forward + backward", "parallelism": f"replicas x{ws}"},
         "exact_bf16_mlp_ms": exact_ms, "sampled_gemm_tflop_per_step": gemm_flops / 1e12,
+        "sampled_gemm_tflop_note": "2 m n L per GEMM at L draws; repeated draws of an index are one term, so the "
+                                   "GEMMs run over the distinct drawn columns, fewer than L",
         "clocks": clk.summary(), "gpu_launches": int(launches),
     }
     del X, Ws, R

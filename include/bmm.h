@@ -260,8 +260,13 @@ bmm_status bmm_sample_batched(int64_t count, const double* const* p, int32_t uni
 /*
  * bmm_apply -- the sampled product CD = sum_t scale_t M^{(i_t)} N_{(i_t)} (eq. 3.3,
  * Alg. 2 step 4), or sum_t scale_t M^{k_t} N_{k_t} for BMM_UNIT_BLOCK.
- * The chosen columns/rows are gathered, multiplied by sqrt(scale_t) (Alg. 1 step 1(b)),
- * converted to the mode's operand type and multiplied on the tensor cores.
+ * Draws of the same index are one term: the draws are first reduced to their distinct indices,
+ * ascending, each weighted by its multiplicity times its scale (the same sum; draws with
+ * replacement repeat heavy columns, and one product's GEMM runs over the distinct ones).  Every draw
+ * of an index must carry the same scale, as every draw of bmm_sample does (1/(c_k p_i), 1/(c p_k));
+ * another scale is BMM_ERR_ARG on the device.  The distinct columns/rows are gathered, multiplied
+ * by the square root of their weight (Alg. 1 step 1(b)), converted to the mode's operand type and
+ * multiplied on the tensor cores.
  *   out: m x p, row-major (layout must be ROW), FP32 for the BF16 modes, FP64 for F64.
  *   accumulate: 0 -> out = CD, 1 -> out += CD.   count = number of draws (>= 0).
  */
@@ -282,8 +287,10 @@ enum {
  * out, accumulate, ws, ws_bytes, stream), so that the caller can overlap the memory-bound gathers with
  * the tensor-core GEMM on streams of its own (eq. 3.3, Alg. 1 step 1(b)); the library creates no
  * stream or event.  The operands live in ws, laid out as bmm_apply lays them out, so all parts of one
- * product take the same ws and arguments.  The GEMM of rows [row0, row1) needs GATHER_B and the
- * GATHER_A of those rows to be complete (same stream, or ordered by the caller's events).  Every
+ * product take the same ws and arguments.  GATHER_B also reduces the draws to their distinct
+ * indices in ws, so it comes first; a GATHER_A needs it complete, and the GEMM of rows [row0, row1)
+ * needs GATHER_B and the GATHER_A of those rows complete (same stream, or ordered by the caller's
+ * events).  Every
  * output element is the full-depth dot product of a single bmm_apply, so any split of the rows gives
  * the same bits.  row0 and row1: multiples of 128 (row1 may be m), 0 <= row0 <= row1 <= m;
  * count >= 1.  Errors as bmm_apply; a bad part is BMM_ERR_ARG, a bad row range BMM_ERR_SHAPE.

@@ -142,6 +142,11 @@ void* plan_sample(Carver& cv, int unit, const bmm_blocks* B) {
 }
 
 struct ApplyPlan {
+    void* uscr;        // distinct draws: scratch of the reduction,
+    int32_t* uidx;     // the distinct indices (columns, or blocks for the block unit), ascending,
+    double* uw;        // their multiplicity times their scale,
+    int64_t* ucount;   // and their count (device)
+    int64_t nuniq;     // an upper bound of that count
     int32_t* col;
     double* w;
     int64_t* prefix;
@@ -155,14 +160,20 @@ struct ApplyPlan {
 };
 void plan_apply(Carver& cv, const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int unit, int64_t count,
                 int mode, ApplyPlan* p) {
-    p->lmax = unit == BMM_UNIT_COLUMN ? count : count * B->max_nk;
+    const int64_t space = unit == BMM_UNIT_COLUMN ? B->n : B->K;
+    p->nuniq = imax(1, imin(count, space));
+    p->uscr = cv.take<char>(unique_scratch_bytes(space, count));
+    p->uidx = cv.take<int32_t>(p->nuniq);
+    p->uw = cv.take<double>(p->nuniq);
+    p->ucount = cv.take<int64_t>(1);
+    p->lmax = unit == BMM_UNIT_COLUMN ? p->nuniq : p->nuniq * B->max_nk;
     p->col = nullptr;
     p->w = nullptr;
     p->prefix = nullptr;
     if (unit == BMM_UNIT_BLOCK) {
         p->col = cv.take<int32_t>(p->lmax);
         p->w = cv.take<double>(p->lmax);
-        p->prefix = cv.take<int64_t>(count);
+        p->prefix = cv.take<int64_t>(p->nuniq);
     }
     p->ext = cv.take<int64_t>(1);
     p->kseg_max = round_up(imax(p->lmax, 1), mode == BMM_GEMM_E4M3 ? 128 : 64);
@@ -598,10 +609,15 @@ namespace {
 // (nothing left to compute) or *g describes the product's GEMM (BF16 modes; FP64 is launched here).
 // With `defer` (bmm_apply_batched), a column-unit BF16 or split-BF16 product launches nothing: its
 // two gathers are appended to *defer for one grouped launch and its GEMM uses the host extent.
+// Checks the arguments, lays out the workspace and reduces the draws to their distinct indices (each
+// with its multiplicity times its scale: the same sum of outer products, one term per index), then
+// queues the gathers (or runs them) and describes the GEMM.  reduce = false reuses the distinct draws
+// a previous call with the same arguments left in the workspace (the later parts of bmm_apply_part).
 bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, int32_t unit, const int32_t* idx,
                          const double* scale, int64_t count, int32_t gemm_mode, const bmm_mat* out,
                          int32_t accumulate, void* ws, size_t ws_bytes, cudaStream_t cs, GemmArgs* g, bool* done,
-                         std::vector<GatherJob>* defer = nullptr) {
+                         std::vector<GatherJob>* defer = nullptr, bool reduce = true,
+                         std::vector<UniqueJob>* udefer = nullptr) {
     *done = true;
     bmm_status s = check_problem(M, N, B);
     if (s != BMM_OK) return s;
@@ -625,47 +641,57 @@ bmm_status apply_prepare(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B
     Carver cv{static_cast<char*>(ws) + kStatusBytes};
     plan_apply(cv, M, N, B, unit, count, gemm_mode, &plan);
     DevStatus* dst = status_of(ws);
-    const int32_t* col = idx;
-    const double* w = scale;
+    const int64_t space = unit == BMM_UNIT_COLUMN ? B->n : B->K;
+    const bool deferred = defer != nullptr && unit == BMM_UNIT_COLUMN &&
+                          (gemm_mode == BMM_GEMM_BF16 || gemm_mode == BMM_GEMM_SPLIT_BF16);
+    if (reduce) {
+        const UniqueJob uj{idx, scale, count, space, plan.uscr, plan.uidx, plan.uw, plan.ucount, dst};
+        if (deferred && udefer != nullptr) udefer->push_back(uj);  // launched with the other products'
+        else BMM_TRY(launch_unique_grouped(&uj, 1, cs));
+    }
+    const int32_t* col = plan.uidx;
+    const double* w = plan.uw;
+    const int64_t* ext = plan.ucount;
     const VecSet vM = vecset_of_M(M), vN = vecset_of_N(N);
-    if (defer != nullptr && unit == BMM_UNIT_COLUMN &&
-        (gemm_mode == BMM_GEMM_BF16 || gemm_mode == BMM_GEMM_SPLIT_BF16)) {
-        defer->push_back(GatherJob{vM, idx, scale, count, gemm_mode, 0, plan.A, plan.ktot, dst});
-        defer->push_back(GatherJob{vN, idx, scale, count, gemm_mode, 1, plan.Bop, plan.ktot, dst});
+    if (deferred) {
+        GatherJob jA{vM, col, w, plan.nuniq, gemm_mode, 0, plan.A, plan.ktot, dst};
+        GatherJob jB{vN, col, w, plan.nuniq, gemm_mode, 1, plan.Bop, plan.ktot, dst};
+        jA.ext_dev = jB.ext_dev = ext;
+        defer->push_back(jA);
+        defer->push_back(jB);
         const int k_mult = gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1;
-        *g = GemmArgs{plan.A, plan.ktot, plan.Bop, plan.ktot, M->rows, N->cols, plan.ktot,
-                      k_mult * round_up(count, 64), nullptr, k_mult, static_cast<float*>(odata), out->ld, accumulate,
-                      GEMM_ELEM_BF16, nullptr};
+        *g = GemmArgs{plan.A, plan.ktot, plan.Bop, plan.ktot, M->rows, N->cols, plan.ktot, plan.ktot, ext, k_mult,
+                      static_cast<float*>(odata), out->ld, accumulate, GEMM_ELEM_BF16, nullptr};
         *done = false;
         return BMM_OK;
     }
-    if (unit == BMM_UNIT_COLUMN) {
-        BMM_TRY(launch_set_extent(plan.ext, count, cs));
-    } else {
-        BMM_TRY(launch_expand_blocks(idx, scale, count, nullptr, B->offsets, B->K, B->n, B->max_nk, plan.col, plan.w,
-                                     plan.ext, plan.prefix, dst, cs));
+    if (unit == BMM_UNIT_BLOCK) {
+        if (reduce)
+            BMM_TRY(launch_expand_blocks(plan.uidx, plan.uw, plan.nuniq, plan.ucount, B->offsets, B->K, B->n,
+                                         B->max_nk, plan.col, plan.w, plan.ext, plan.prefix, dst, cs));
         col = plan.col;
         w = plan.w;
+        ext = plan.ext;
     }
     if (gemm_mode == BMM_GEMM_E4M3) {
         // column maxima of C and row maxima of D, then their power-of-two scales
         BMM_TRY(cudaMemsetAsync(plan.amaxA, 0, sizeof(float) * plan.lmax, cs));
         BMM_TRY(cudaMemsetAsync(plan.amaxB, 0, sizeof(float) * plan.lmax, cs));
-        BMM_TRY(launch_vec_absmax(vM, col, w, plan.ext, plan.lmax, plan.amaxA, cs));
-        BMM_TRY(launch_vec_absmax(vN, col, w, plan.ext, plan.lmax, plan.amaxB, cs));
-        BMM_TRY(launch_fp8_scales(plan.amaxA, plan.amaxB, w, plan.ext, plan.sa, plan.sb, plan.oscale, cs));
+        BMM_TRY(launch_vec_absmax(vM, col, w, ext, plan.lmax, plan.amaxA, cs));
+        BMM_TRY(launch_vec_absmax(vN, col, w, ext, plan.lmax, plan.amaxB, cs));
+        BMM_TRY(launch_fp8_scales(plan.amaxA, plan.amaxB, w, ext, plan.sa, plan.sb, plan.oscale, cs));
     }
-    BMM_TRY(launch_gather_operand(vM, col, w, plan.ext, plan.lmax, gemm_mode, 0, true, plan.A, plan.ktot, dst, cs,
+    BMM_TRY(launch_gather_operand(vM, col, w, ext, plan.lmax, gemm_mode, 0, true, plan.A, plan.ktot, dst, cs,
                                   plan.sa));
-    BMM_TRY(launch_gather_operand(vN, col, w, plan.ext, plan.lmax, gemm_mode, 1, true, plan.Bop, plan.ktot, dst, cs,
+    BMM_TRY(launch_gather_operand(vN, col, w, ext, plan.lmax, gemm_mode, 1, true, plan.Bop, plan.ktot, dst, cs,
                                   plan.sb));
     if (gemm_mode == BMM_GEMM_F64) {
         BMM_TRY(launch_gemm_f64(static_cast<const double*>(plan.A), plan.ktot, static_cast<const double*>(plan.Bop),
-                                plan.ktot, M->rows, N->cols, 0, plan.ext, static_cast<double*>(odata), out->ld,
+                                plan.ktot, M->rows, N->cols, 0, ext, static_cast<double*>(odata), out->ld,
                                 accumulate, cs, plan.ktot, plan.kpart, plan.kpart_cap));
         return BMM_OK;
     }
-    *g = GemmArgs{plan.A, plan.ktot, plan.Bop, plan.ktot, M->rows, N->cols, plan.ktot, 0, plan.ext,
+    *g = GemmArgs{plan.A, plan.ktot, plan.Bop, plan.ktot, M->rows, N->cols, plan.ktot, plan.ktot, ext,
                   gemm_mode == BMM_GEMM_SPLIT_BF16 ? 3 : 1, static_cast<float*>(odata), out->ld, accumulate,
                   gemm_mode == BMM_GEMM_E4M3 ? GEMM_ELEM_E4M3 : GEMM_ELEM_BF16, plan.oscale};
     *done = false;
@@ -705,8 +731,10 @@ BMM_API bmm_status bmm_apply_part(const bmm_mat* M, const bmm_mat* N, const bmm_
     GemmArgs g;
     bool done = true;
     std::vector<GatherJob> jobs;
+    // the GATHER_B part also reduces the draws to their distinct indices in the workspace; the other
+    // parts, issued after it, use that reduction
     bmm_status s = apply_prepare(M, N, B, BMM_UNIT_COLUMN, idx, scale, count, BMM_GEMM_BF16, out, accumulate, ws,
-                                 ws_bytes, cs, &g, &done, &jobs);
+                                 ws_bytes, cs, &g, &done, &jobs, part == BMM_APPLY_GATHER_B);
     if (s != BMM_OK || done) return s;
     if (part == BMM_APPLY_GATHER_B) {
         BMM_TRY(launch_gather_grouped(&jobs[1], 1, cs));
@@ -741,16 +769,19 @@ BMM_API bmm_status bmm_apply_batched(int64_t count, const bmm_mat* Ms, const bmm
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     std::vector<GemmArgs> gemms;
     std::vector<GatherJob> gathers;
+    std::vector<UniqueJob> uniq;
     gemms.reserve((size_t)count);
     gathers.reserve(2 * (size_t)count);
+    uniq.reserve((size_t)count);
     for (int64_t i = 0; i < count; ++i) {
         GemmArgs g;
         bool done = true;
         const bmm_status s = apply_prepare(&Ms[i], &Ns[i], &Bs[i], unit, idx[i], scale[i], draws[i], gemm_mode, &outs[i],
-                                           accumulate, ws[i], ws_bytes[i], cs, &g, &done, &gathers);
+                                           accumulate, ws[i], ws_bytes[i], cs, &g, &done, &gathers, true, &uniq);
         if (s != BMM_OK) return s;
         if (!done) gemms.push_back(g);
     }
+    if (!uniq.empty()) BMM_TRY(launch_unique_grouped(uniq.data(), (int64_t)uniq.size(), cs));
     if (!gathers.empty()) BMM_TRY(launch_gather_grouped(gathers.data(), (int64_t)gathers.size(), cs));
     if (!gemms.empty())
         BMM_TRY(launch_gemm_bf16_tc_grouped(gemms.data(), (int64_t)gemms.size(), status_of(ws[0]), cs));

@@ -35,86 +35,178 @@ __device__ unsigned long long block_scan_incl(unsigned long long v, unsigned lon
     return r;
 }
 
-__global__ void hist_kernel(const int32_t* __restrict__ idx, const double* __restrict__ scale, int64_t count,
-                            int64_t space, int* __restrict__ cnt, double* __restrict__ sval, DevStatus* st) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const int64_t i = idx[t];
-    if (i < 0 || i >= space) {
-        set_status(st, BMM_ERR_ARG, (int)t);
-        return;
-    }
-    atomicAdd(&cnt[i], 1);
-    sval[i] = scale[t];  // identical for every draw of i
-}
-
-__global__ void __launch_bounds__(kTileScan) flag_scan_kernel(const int* __restrict__ cnt, int64_t space,
-                                                              unsigned long long* __restrict__ pos,
-                                                              unsigned long long* __restrict__ tot) {
-    __shared__ unsigned long long sm[32];
-    const int64_t i = (int64_t)blockIdx.x * kTileScan + threadIdx.x;
-    const unsigned long long f = (i < space && cnt[i] > 0) ? 1ull : 0ull;
-    const unsigned long long inc = block_scan_incl(f, sm);
-    if (i < space) pos[i] = inc - f;
-    if (threadIdx.x == kTileScan - 1) tot[blockIdx.x] = inc;
-}
-
-__global__ void __launch_bounds__(kTileScan) tot_scan_kernel(unsigned long long* __restrict__ tot, int64_t ntiles) {
-    __shared__ unsigned long long sm[32];
-    __shared__ unsigned long long carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t b = 0; b < ntiles; b += kTileScan) {
-        const int64_t i = b + threadIdx.x;
-        const unsigned long long v = i < ntiles ? tot[i] : 0ull;
-        const unsigned long long inc = block_scan_incl(v, sm);
-        const unsigned long long c0 = carry;
-        if (i < ntiles) tot[i] = c0 + inc - v;
-        __syncthreads();
-        if (threadIdx.x == kTileScan - 1) carry = c0 + inc;
-        __syncthreads();
-    }
-}
-
-__global__ void compact_kernel(const int* __restrict__ cnt, const double* __restrict__ sval,
-                               const unsigned long long* __restrict__ pos, const unsigned long long* __restrict__ tot,
-                               int64_t space, int32_t* __restrict__ uidx, double* __restrict__ uw,
-                               int64_t* __restrict__ ucount) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= space) return;
-    const unsigned long long q = pos[i] + tot[i / kTileScan];
-    const int c = cnt[i];
-    if (c > 0) {
-        uidx[q] = (int32_t)i;
-        uw[q] = __dmul_rn((double)c, sval[i]);
-    }
-    if (i == space - 1) *ucount = (int64_t)(q + (c > 0 ? 1 : 0));
-}
-
 int64_t unique_scratch_bytes(int64_t space, int64_t count) {
     (void)count;
     const int64_t ntiles = ceil_div(imax(space, 1), kTileScan);
     return round_up(space * 4, 256) + round_up(space * 8, 256) + round_up(space * 8, 256) + round_up(ntiles * 8, 256);
 }
 
+// ---------------------------------------------------------------- distinct draws, many products
+// The same reduction for a table of products in five launches whatever their number: clear the
+// counts, count the draws, scan the per-tile flags, scan each product's tile totals, compact.  Each
+// CTA finds its product by binary search over the table's running offsets.
+struct UniqueJobDev {
+    const int32_t* idx;
+    const double* scale;
+    int64_t count, space;
+    int* cnt;
+    double* sval;
+    unsigned long long* pos;
+    unsigned long long* tot;
+    int32_t* uidx;
+    double* uw;
+    int64_t* ucount;
+    DevStatus* st;
+    long long draw_begin, space_begin, tile_begin;
+};
+constexpr int kMaxUniqueJobs = 256;
+struct UniqueTable {
+    int count;
+    long long draws, spaces, tiles;
+    UniqueJobDev job[kMaxUniqueJobs];
+};
+static_assert(sizeof(UniqueTable) <= 32764, "distinct-draw table exceeds the kernel-parameter limit");
+
+template <int WHICH>  // 0: draws, 1: space elements, 2: scan tiles
+__device__ __forceinline__ int find_unique_job(const UniqueTable& tab, long long v) {
+    int lo = 0, hi = tab.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long b = WHICH == 0 ? tab.job[mid].draw_begin
+                                       : (WHICH == 1 ? tab.job[mid].space_begin : tab.job[mid].tile_begin);
+        if (b <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void unique_clear_grouped(const __grid_constant__ UniqueTable tab) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= tab.spaces) return;
+    const UniqueJobDev& jb = tab.job[find_unique_job<1>(tab, v)];
+    const long long i = v - jb.space_begin;
+    jb.cnt[i] = 0;
+    reinterpret_cast<unsigned long long*>(jb.sval)[i] = ~0ull;
+}
+
+__global__ void unique_hist_grouped(const __grid_constant__ UniqueTable tab) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= tab.draws) return;
+    const UniqueJobDev& jb = tab.job[find_unique_job<0>(tab, v)];
+    const long long t = v - jb.draw_begin;
+    const int64_t i = jb.idx[t];
+    if (i < 0 || i >= jb.space) {
+        set_status(jb.st, BMM_ERR_ARG, (int)t);
+        return;
+    }
+    atomicAdd(&jb.cnt[i], 1);
+    const unsigned long long val = (unsigned long long)__double_as_longlong(jb.scale[t]);
+    const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(jb.sval) + i, ~0ull, val);
+    if (old != ~0ull && old != val) set_status(jb.st, BMM_ERR_ARG, (int)t);
+}
+
+__global__ void __launch_bounds__(kTileScan) unique_flags_grouped(const __grid_constant__ UniqueTable tab) {
+    __shared__ unsigned long long sm[32];
+    const UniqueJobDev& jb = tab.job[find_unique_job<2>(tab, (long long)blockIdx.x)];
+    const long long tile = (long long)blockIdx.x - jb.tile_begin;
+    const int64_t i = tile * kTileScan + threadIdx.x;
+    const unsigned long long f = (i < jb.space && jb.cnt[i] > 0) ? 1ull : 0ull;
+    const unsigned long long inc = block_scan_incl(f, sm);
+    if (i < jb.space) jb.pos[i] = inc - f;
+    if (threadIdx.x == kTileScan - 1) jb.tot[tile] = inc;
+}
+
+__global__ void __launch_bounds__(kTileScan) unique_tiles_grouped(const __grid_constant__ UniqueTable tab) {
+    __shared__ unsigned long long sm[32];
+    __shared__ unsigned long long carry;
+    const UniqueJobDev& jb = tab.job[blockIdx.x];
+    const int64_t ntiles = ceil_div(jb.space, kTileScan);
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < ntiles; b += kTileScan) {
+        const int64_t i = b + threadIdx.x;
+        const unsigned long long v = i < ntiles ? jb.tot[i] : 0ull;
+        const unsigned long long inc = block_scan_incl(v, sm);
+        const unsigned long long c0 = carry;
+        if (i < ntiles) jb.tot[i] = c0 + inc - v;
+        __syncthreads();
+        if (threadIdx.x == kTileScan - 1) carry = c0 + inc;
+        __syncthreads();
+    }
+}
+
+__global__ void unique_compact_grouped(const __grid_constant__ UniqueTable tab) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= tab.spaces) return;
+    const UniqueJobDev& jb = tab.job[find_unique_job<1>(tab, v)];
+    const int64_t i = v - jb.space_begin;
+    const unsigned long long q = jb.pos[i] + jb.tot[i / kTileScan];
+    const int c = jb.cnt[i];
+    if (c > 0) {
+        jb.uidx[q] = (int32_t)i;
+        jb.uw[q] = __dmul_rn((double)c, jb.sval[i]);
+    }
+    if (i == jb.space - 1) *jb.ucount = (int64_t)(q + (c > 0 ? 1 : 0));
+}
+
+static cudaError_t launch_unique_table(const UniqueTable& tab, cudaStream_t s) {
+    if (tab.count == 0) return cudaSuccess;
+    (count_launch(), unique_clear_grouped<<<(unsigned)ceil_div(tab.spaces, 256), 256, 0, s>>>(tab));
+    if (tab.draws > 0) (count_launch(), unique_hist_grouped<<<(unsigned)ceil_div(tab.draws, 256), 256, 0, s>>>(tab));
+    (count_launch(), unique_flags_grouped<<<(unsigned)tab.tiles, kTileScan, 0, s>>>(tab));
+    (count_launch(), unique_tiles_grouped<<<(unsigned)tab.count, kTileScan, 0, s>>>(tab));
+    (count_launch(), unique_compact_grouped<<<(unsigned)ceil_div(tab.spaces, 256), 256, 0, s>>>(tab));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unique_grouped(const UniqueJob* jobs, int64_t n, cudaStream_t s) {
+    static UniqueTable tab;  // host-side staging of the kernel parameter (~31 KB)
+    tab.count = 0;
+    tab.draws = tab.spaces = tab.tiles = 0;
+    for (int64_t k = 0; k <= n; ++k) {
+        const bool full = tab.count == kMaxUniqueJobs ||
+                          (k < n && (tab.spaces + jobs[k].space > 0x7fffffffLL * 128 ||
+                                     tab.tiles + ceil_div(jobs[k].space, kTileScan) > 0x7fffffffLL));
+        if (k == n || full) {
+            cudaError_t e = launch_unique_table(tab, s);
+            if (e != cudaSuccess) return e;
+            tab.count = 0;
+            tab.draws = tab.spaces = tab.tiles = 0;
+        }
+        if (k == n) break;
+        const UniqueJob& u = jobs[k];
+        if (u.space <= 0) return cudaErrorInvalidValue;
+        UniqueJobDev& d = tab.job[tab.count++];
+        char* w = static_cast<char*>(u.scratch);
+        d.idx = u.idx;
+        d.scale = u.scale;
+        d.count = u.count;
+        d.space = u.space;
+        d.cnt = reinterpret_cast<int*>(w);
+        w += round_up(u.space * 4, 256);
+        d.sval = reinterpret_cast<double*>(w);
+        w += round_up(u.space * 8, 256);
+        d.pos = reinterpret_cast<unsigned long long*>(w);
+        w += round_up(u.space * 8, 256);
+        d.tot = reinterpret_cast<unsigned long long*>(w);
+        d.uidx = u.uidx;
+        d.uw = u.uw;
+        d.ucount = u.ucount;
+        d.st = u.st;
+        d.draw_begin = tab.draws;
+        d.space_begin = tab.spaces;
+        d.tile_begin = tab.tiles;
+        tab.draws += u.count;
+        tab.spaces += u.space;
+        tab.tiles += ceil_div(u.space, kTileScan);
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_unique(const int32_t* idx, const double* scale, int64_t count, int64_t space, int32_t* uidx,
                           double* uw, int64_t* ucount_dev, void* scratch, DevStatus* st, cudaStream_t s) {
-    char* w = static_cast<char*>(scratch);
-    int* cnt = reinterpret_cast<int*>(w);
-    w += round_up(space * 4, 256);
-    double* sval = reinterpret_cast<double*>(w);
-    w += round_up(space * 8, 256);
-    unsigned long long* pos = reinterpret_cast<unsigned long long*>(w);
-    w += round_up(space * 8, 256);
-    unsigned long long* tot = reinterpret_cast<unsigned long long*>(w);
-    const int64_t ntiles = ceil_div(space, kTileScan);
-    cudaError_t e = cudaMemsetAsync(cnt, 0, space * 4, s);
-    if (e != cudaSuccess) return e;
-    if (count > 0) (count_launch(), hist_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(idx, scale, count, space, cnt, sval, st));
-    (count_launch(), flag_scan_kernel<<<(unsigned)ntiles, kTileScan, 0, s>>>(cnt, space, pos, tot));
-    (count_launch(), tot_scan_kernel<<<1, kTileScan, 0, s>>>(tot, ntiles));
-    (count_launch(), compact_kernel<<<(unsigned)ceil_div(space, 256), 256, 0, s>>>(cnt, sval, pos, tot, space, uidx, uw, ucount_dev));
-    return cudaGetLastError();
+    const UniqueJob job{idx, scale, count, space, scratch, uidx, uw, ucount_dev, st};
+    return launch_unique_grouped(&job, 1, s);
 }
 
 // ---------------------------------------------------------------- conversions of G

@@ -99,12 +99,6 @@ cudaError_t launch_expand_blocks(const int32_t* kidx, const double* kscale, int6
     return cudaGetLastError();
 }
 
-__global__ void set_extent_kernel(int64_t* ext, int64_t v) { *ext = v; }
-
-cudaError_t launch_set_extent(int64_t* ext_dev, int64_t value, cudaStream_t s) {
-    (count_launch(), set_extent_kernel<<<1, 1, 0, s>>>(ext_dev, value));
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------- operand writers
 // V is the arithmetic type of the scaled value: float for the BF16 modes, double for F64.
@@ -467,14 +461,15 @@ struct GatherJobDev {
     int64_t len, ld, nvec;
     const int32_t* col;
     const double* w;
-    int64_t ext;
+    int64_t ext;                // draws, or their upper bound (the grid) when ext_dev is set
+    const int64_t* ext_dev;     // device count of draws, or null
     OpWriter wr;
     DevStatus* st;
     int gx, gy;
     int cta_begin;
     int vec16;  // rows readable 16 bytes at a time
 };
-constexpr int kMaxGatherJobs = 224;  // 136-byte jobs: the table stays under the 32 KB parameter limit
+constexpr int kMaxGatherJobs = 224;  // 144-byte jobs: the table stays under the 32 KB parameter limit
 struct GatherTable {
     int count;
     int total;
@@ -495,10 +490,11 @@ __global__ void __launch_bounds__(STRIDED ? 128 : 256) gather_grouped_kernel(con
     const int local = b - jb.cta_begin;
     const int64_t bx = local % jb.gx, by = local / jb.gx;
     const T* X = static_cast<const T*>(jb.X);
+    const int64_t ext = jb.ext_dev != nullptr ? imin(*jb.ext_dev, jb.ext) : jb.ext;
     if constexpr (STRIDED)
-        gather_strided_body<T, float>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, jb.ext, true, jb.wr, jb.st, bx, by, jb.gy);
+        gather_strided_body<T, float>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, ext, true, jb.wr, jb.st, bx, by, jb.gy);
     else
-        gather_contig_bf16_body<T>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, jb.ext, true, jb.vec16 != 0, jb.wr, jb.st, bx,
+        gather_contig_bf16_body<T>(X, jb.len, jb.ld, jb.nvec, jb.col, jb.w, ext, true, jb.vec16 != 0, jb.wr, jb.st, bx,
                                    by, jb.gy);
 }
 
@@ -544,6 +540,7 @@ static cudaError_t gather_grouped_t(const GatherJob* jobs, int64_t count, cudaSt
         d.col = g.col;
         d.w = g.w;
         d.ext = g.ext;
+        d.ext_dev = g.ext_dev;
         d.wr = OpWriter{g.out, g.ldo, 0, g.mode, g.role, kunit, nullptr};
         d.st = g.st;
         d.gx = (int)gx;

@@ -116,10 +116,16 @@ __device__ __forceinline__ int find_problem(const GemmTable<G>& tab, int tile) {
     return pi;
 }
 
-// K blocks of one product: with a device extent, each of the k_mult segments is padded to BK
+// K blocks of one product: with a device extent, each of the k_mult segments is padded to BK, and
+// k_host (when positive) caps the depth at the operands' capacity
 template <int BK>
 __device__ __forceinline__ int problem_kb(const GemmProblem& pr) {
-    const long long K = pr.k_dev ? (long long)pr.k_mult * (((*pr.k_dev) + BK - 1) / BK * BK) : pr.k_host;
+    long long K = pr.k_host;
+    if (pr.k_dev) {
+        const long long e = *pr.k_dev;
+        K = (long long)pr.k_mult * ((((e > 0 ? e : 0) + BK - 1) / BK) * BK);
+        if (pr.k_host > 0 && K > pr.k_host) K = pr.k_host;
+    }
     return (int)(K / BK);
 }
 

@@ -171,7 +171,6 @@ cudaError_t launch_sample(const double* p, int unit, const int64_t* off, int64_t
 cudaError_t launch_expand_blocks(const int32_t* kidx, const double* kscale, int64_t count, const int64_t* count_dev,
                                  const int64_t* off, int64_t K, int64_t n, int64_t max_nk, int32_t* col, double* w,
                                  int64_t* ext_dev, int64_t* prefix_scratch, DevStatus* st, cudaStream_t s);
-cudaError_t launch_set_extent(int64_t* ext_dev, int64_t value, cudaStream_t s);
 // Operand rows: out[r][j] = cvt(f_j * vec_{col_j}[r]) for r < v.len, j < ext, zero up to the padded
 // extent (a multiple of 64, of 128 for e4m3), with f_j = sqrt(w_j), or colscale[j] when given.
 // mode: BMM_GEMM_BF16 (bf16), BMM_GEMM_SPLIT_BF16 (bf16 segments; `split_role` 0 = [hi|hi|lo], 1 = [hi|lo|hi]),
@@ -186,11 +185,12 @@ struct GatherJob {
     VecSet v;
     const int32_t* col;
     const double* w;
-    int64_t ext;
+    int64_t ext;  // draws (host), or their upper bound when ext_dev is given
     int mode, role;
     void* out;
     int64_t ldo;
     DevStatus* st;
+    const int64_t* ext_dev = nullptr;  // device count of draws (distinct draws), read in the kernel
 };
 cudaError_t launch_gather_grouped(const GatherJob* jobs, int64_t count, cudaStream_t s);
 // FP8 operand scales.  amax[j] = sqrt(w_j) * max_r |vec_{col_j}[r]| (amax must start at zero);
@@ -258,10 +258,24 @@ cudaError_t gemm_autotune(int64_t M, int64_t N, int64_t K, int elem, void* scrat
 
 // ---- backward.cu
 int64_t unique_scratch_bytes(int64_t space, int64_t count);
-// Distinct indices of idx[0..count) (values in [0, space)), ascending, with summed weights.
+// Distinct indices of idx[0..count) (values in [0, space)), ascending, each with its multiplicity
+// times its scale (the draws of one index share one scale; another scale records BMM_ERR_ARG).
 cudaError_t launch_unique(const int32_t* idx, const double* scale, int64_t count, int64_t space,
                           int32_t* uidx, double* uw, int64_t* ucount_dev, void* scratch, DevStatus* st,
                           cudaStream_t s);
+// The same for many products at once (five launches per up to 256 products; scratch of
+// unique_scratch_bytes(space, count) bytes per product).
+struct UniqueJob {
+    const int32_t* idx;
+    const double* scale;
+    int64_t count, space;
+    void* scratch;
+    int32_t* uidx;
+    double* uw;
+    int64_t* ucount;
+    DevStatus* st;
+};
+cudaError_t launch_unique_grouped(const UniqueJob* jobs, int64_t n, cudaStream_t s);
 cudaError_t launch_convert_f32_to_bf16(const float* G, int64_t rows, int64_t cols, int64_t ldg,
                                        __nv_bfloat16* out, int64_t ldo, cudaStream_t s);
 cudaError_t launch_convert_to_f64(const void* G, int dtype, int64_t rows, int64_t cols, int64_t ldg, bool transpose,

@@ -1199,3 +1199,50 @@ def test_autograd_step_replays_in_a_cuda_graph(bmm):
     assert torch.equal(y_static, y_eager)
     assert torch.equal(X.grad, gX) and torch.equal(W.grad, gW)
     assert torch.count_nonzero(X.grad) > 0
+
+
+@pytest.mark.parametrize("mode", ["bf16", "f64"])
+@pytest.mark.parametrize("unit", ["column", "block"])
+def test_apply_merges_repeated_draws(bmm, mode, unit):
+    """bmm_apply reduces the draws to their distinct indices, each weighted by its multiplicity times
+    its scale: the product of draws with repeats equals, bit for bit, the product of the distinct
+    indices with those weights, stays within the element bound of the oracle's sum over every draw,
+    and a repeated index carrying another scale is reported (BMM_ERR_ARG)."""
+    A = bmm._abi
+    gm = bmm.MODES[mode]
+    off, M, N, Mt, Nt = _problem(300, 1500, 264, 15, seed=97, dtype=np.float32 if mode == "bf16" else np.float64,
+                                 lo=40, hi=160)
+    method, c = ("ONC", 900) if unit == "column" else ("SSM", 20)
+    u = A.UNIT_BLOCK if unit == "block" else A.UNIT_COLUMN
+    prob = bmm.prepare(Mt, Nt, off, max_draws=c, unit=u, gemm_mode=gm)
+    r = bmm.run(prob, method, c, seed=4, gemm_mode=gm, compute_product=False)
+    idx, scale = host(r["idx"]).astype(np.int64), host(r["scale"])
+    ui, inv, cnt = np.unique(idx, return_inverse=True, return_counts=True)
+    assert cnt.max() > 1  # the sample repeats some index
+    usc = np.zeros(len(ui))
+    usc[inv] = scale
+    dt = torch.float32 if mode == "bf16" else torch.float64
+    a = torch.empty(300, 264, dtype=dt, device=Mt.device)
+    b = torch.empty(300, 264, dtype=dt, device=Mt.device)
+    bmm.bmm_apply(Mt, Nt, prob.B, u, r["idx"], r["scale"], c, gm, a, False, prob.ws)
+    bmm.check_status(prob)
+    bmm.bmm_apply(Mt, Nt, prob.B, u, to_dev(ui.astype(np.int32)), to_dev(cnt * usc), len(ui), gm, b, False, prob.ws)
+    bmm.check_status(prob)
+    assert torch.equal(a, b)
+    if unit == "column":
+        want = oracle.sampled_product_columns(M, N, idx, scale)
+        bound = product_bound(M, N, idx, scale)
+        L = c
+    else:
+        want = oracle.sampled_product_blocks(M, N, off, idx, scale)
+        bound = product_bound(M, N, idx, scale, offsets=off, unit="block")
+        L = int(np.diff(off)[idx].sum())
+    assert np.all(np.abs(host(a).astype(np.float64) - want) <= _tol(mode, L) * bound + 1e-300)
+    # a repeated index with another scale
+    j = int(np.flatnonzero(cnt[inv] > 1)[0])
+    bad = scale.copy()
+    bad[j] *= 1.5
+    A.bmm_clear_device_status(prob.ws)
+    bmm.bmm_apply(Mt, Nt, prob.B, u, r["idx"], to_dev(bad), c, gm, a, False, prob.ws)
+    assert A.bmm_read_device_status(prob.ws) == A.ERR_ARG
+    A.bmm_clear_device_status(prob.ws)
