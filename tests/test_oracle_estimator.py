@@ -211,3 +211,33 @@ def test_methods_run_and_respect_budget():
         assert len(r["idx"]) == c
         if "ck" in r:
             assert r["ck"].sum() == c and np.all(r["ck"] >= 1) and np.all(r["ck"] <= np.diff(off))
+
+
+def test_repeated_draws_are_one_term_each():
+    """eq. 3.2 with repeats: every draw of index i carries the same scale 1/(c_k p_i), so the sum over
+    the draws equals the sum over the distinct indices with weight multiplicity x scale (the form
+    the apply computes); the same for block draws (1/(c p_k))."""
+    off = S.block_offsets_uneven(600, 8, 40, 110, seed=3)
+    M, N = S.scaled_gaussian(20, 600, 14, off, 1.0, seed=4)
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    p = oracle.p_col_opt(st["w"], st["a"], off)
+    ck = oracle.apportion(oracle.g_hat(st["a"]), np.diff(off), 300)
+    idx, scale = oracle.sample_alg2(p, off, ck, 5, 0)
+    ui, inv, cnt = np.unique(idx, return_inverse=True, return_counts=True)
+    assert cnt.max() > 1
+    us = np.zeros(len(ui))
+    us[inv] = scale
+    assert np.all(us[inv] == scale)  # one scale per index
+    a = oracle.sampled_product_columns(M, N, idx, scale)
+    b = oracle.sampled_product_columns(M, N, ui, cnt * us)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(a).max())
+    pblk = oracle.p_blk_normprod(st["mf"], st["nf"])
+    kidx, ks = oracle.sample_blocks(pblk, 20, 6, 0)
+    uk, kinv, kcnt = np.unique(kidx, return_inverse=True, return_counts=True)
+    assert kcnt.max() > 1
+    uks = np.zeros(len(uk))
+    uks[kinv] = ks
+    a = oracle.sampled_product_blocks(M, N, off, kidx, ks)
+    b = oracle.sampled_product_blocks(M, N, off, uk, kcnt * uks)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(a).max())
