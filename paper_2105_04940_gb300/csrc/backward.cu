@@ -160,7 +160,7 @@ static cudaError_t launch_unique_table(const UniqueTable& tab, cudaStream_t s) {
 }
 
 cudaError_t launch_unique_grouped(const UniqueJob* jobs, int64_t n, cudaStream_t s) {
-    static UniqueTable tab;  // host-side staging of the kernel parameter (~31 KB)
+    static thread_local UniqueTable tab;  // host-side staging of the kernel parameter, one per host thread (~31 KB)
     tab.count = 0;
     tab.draws = tab.spaces = tab.tiles = 0;
     for (int64_t k = 0; k <= n; ++k) {

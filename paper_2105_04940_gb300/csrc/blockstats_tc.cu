@@ -1134,15 +1134,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // plain 128-byte swizzle.  Boxes are 128 bytes wide and box_rows high.
 template <typename T>
 bool make_map(CUtensorMap* mp, const void* ptr, int64_t rows, int64_t cols, int64_t ld, bool strided, int box_rows) {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (fn == nullptr) {
+    // looked up once; a function-local static is initialised once even under concurrent callers
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* q = nullptr;
         cudaDriverEntryPointQueryResult r;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &r) != cudaSuccess ||
             r != cudaDriverEntryPointSuccess)
-            return false;
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(q);
-    }
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(q);
+    }();
+    if (fn == nullptr) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * (int64_t)sizeof(T))};
     cuuint32_t box[2] = {(cuuint32_t)Tr<T>::E, (cuuint32_t)box_rows};
@@ -1180,11 +1181,11 @@ bool fill_problem(StatsProblem* pr, const StatsArgs& g) {
 
 template <typename T, bool STATS, int G>
 cudaError_t launch_table(const StatsTable<G>& tab, int* counter, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};  // set once; setting the attribute again is harmless
+    if (!attr.load()) {
         cudaError_t e = cudaFuncSetAttribute(blockstats_tc_kernel<T, STATS, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.store(true);
     }
     if (tab.total_blocks == 0) return cudaSuccess;
     int dev = 0, sms = 1;
@@ -1208,7 +1209,7 @@ cudaError_t launch_grouped_t(const StatsArgs* args, int64_t count, int* counter,
         one.total_blocks = args[0].K;
         return launch_table<T, STATS, 1>(one, counter, s);
     }
-    static StatsTable<kMaxProducts> tab;  // host-side staging of the kernel parameter (~32 KB)
+    static thread_local StatsTable<kMaxProducts> tab;  // host-side staging of the kernel parameter, one per host thread (~32 KB)
     tab.count = 0;
     tab.total_blocks = 0;
     for (int64_t i = 0; i <= count; ++i) {

@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(1024) blocksizes_grouped_kernel(const __grid_c
 }
 
 cudaError_t launch_blocksizes_grouped(const SizesJob* jobs, int64_t count, cudaStream_t s) {
-    static SizesTable tab;  // host-side staging of the kernel parameter
+    static thread_local SizesTable tab;  // host-side staging of the kernel parameter, one per host thread
     for (int64_t i0 = 0; i0 < count; i0 += kMaxSizesJobs) {
         tab.count = (int)imin(count - i0, kMaxSizesJobs);
         for (int q = 0; q < tab.count; ++q) tab.job[q] = jobs[i0 + q];

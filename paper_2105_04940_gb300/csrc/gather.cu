@@ -507,7 +507,7 @@ static cudaError_t launch_gather_table(const GatherTable& tab, cudaStream_t s) {
 
 template <typename T, bool STRIDED>
 static cudaError_t gather_grouped_t(const GatherJob* jobs, int64_t count, cudaStream_t s) {
-    static GatherTable tab;  // host-side staging of the kernel parameter (~31 KB)
+    static thread_local GatherTable tab;  // host-side staging of the kernel parameter, one per host thread (~31 KB)
     tab.count = 0;
     tab.total = 0;
     for (int64_t i = 0; i <= count; ++i) {

@@ -462,15 +462,16 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_tc_kernel(const __grid_const
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (fn == nullptr) {
+    // looked up once; a function-local static is initialised once even under concurrent callers
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -560,8 +561,8 @@ template <int BN, int G, int EK, bool PAIR>
 cudaError_t launch_table(const GemmTable<G>& tab, DevStatus* st, cudaStream_t s) {
     using C = Cfg<BN, EK, PAIR>;
     auto kern = gemm_bf16_tc_kernel<BN, G, EK, PAIR>;
-    static int units = 0;  // CTAs, or CTA pairs, that are resident at once
-    if (units == 0) {
+    static std::atomic<int> units{0};  // CTAs, or CTA pairs, that are resident at once (set once)
+    if (units.load() == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         int n = num_sms();
@@ -582,10 +583,10 @@ cudaError_t launch_table(const GemmTable<G>& tab, DevStatus* st, cudaStream_t s)
             if (e != cudaSuccess) return e;
             n = clusters > 0 ? clusters : 1;
         }
-        units = n;
+        units.store(n);
     }
     if (tab.total_tiles == 0) return cudaSuccess;
-    const int grid = (int)imin(tab.total_tiles, units);
+    const int grid = (int)imin(tab.total_tiles, (int64_t)units.load());
     count_launch();
     if constexpr (PAIR) {
         cudaLaunchConfig_t cfg = {};
@@ -709,7 +710,7 @@ cudaError_t launch_gemm_bf16_tc_grouped(const GemmArgs* args, int64_t count, Dev
     for (int pass = 0; pass < 8; ++pass) {
         const int BN = pass % 4 == 0 ? 128 : (pass % 4 == 1 ? 256 : (pass % 4 == 2 ? kPairTile : kPairTileWide));
         const int elem = pass / 4;
-        static GemmTable<kMaxGroup> tab;  // host-side staging of the kernel parameter (30 KB)
+        static thread_local GemmTable<kMaxGroup> tab;  // host-side staging of the kernel parameter, one per host thread (30 KB)
         tab.count = 0;
         tab.total_tiles = 0;
         for (int64_t i = 0; i <= count; ++i) {

@@ -490,8 +490,8 @@ __global__ void __launch_bounds__(256) sqnorm_rows_grouped_kernel(const __grid_c
 
 template <typename T, bool STRIDED>
 static cudaError_t norm_grouped_t(const NormJobArgs* jobs, int64_t count, cudaStream_t s) {
-    static NormTable tab;  // host-side staging of the kernel parameter (~37 KB below the limit)
-    static NormTable sums;  // the slice sums of the same jobs
+    static thread_local NormTable tab;  // host-side staging of the kernel parameter, one per host thread (~37 KB below the limit)
+    static thread_local NormTable sums;  // the slice sums of the same jobs
     constexpr int E = VecTraits<T>::E;
     const int dt = std::is_same<T, float>::value ? BMM_F32 : BMM_BF16;
     tab.count = tab.total = 0;
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(256) block_stats_grouped_kernel(const __grid_c
 }
 
 cudaError_t launch_block_stats_grouped(const BlockStatsArgs* args, int64_t count, cudaStream_t s) {
-    static BlockStatsTable tab;  // host-side staging of the kernel parameter
+    static thread_local BlockStatsTable tab;  // host-side staging of the kernel parameter, one per host thread
     tab.count = 0;
     tab.total = 0;
     auto flush = [&]() -> cudaError_t {

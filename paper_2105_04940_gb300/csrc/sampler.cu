@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(128) draw_grouped_kernel(const __grid_constant
 }  // namespace
 
 cudaError_t launch_sample_grouped(const SampleArgs* args, int64_t count, cudaStream_t s) {
-    static SampleTable<kMaxSampleJobs> tab;  // host-side staging of the kernel parameter
+    static thread_local SampleTable<kMaxSampleJobs> tab;  // host-side staging of the kernel parameter, one per host thread
     int64_t i = 0;
     while (i < count) {
         tab.count = 0;

@@ -299,3 +299,53 @@ def test_pipelined_products_replay_in_a_cuda_graph(bmm):
         r = bmm.run(ref, "OPL", L, seed=sd, gemm_mode=A.GEMM_BF16, fmode=A.F_TC, fused_stats=True)
         bmm.check_status(ref)
         assert torch.equal(outs[i], r["out"]), i
+
+
+def test_concurrent_host_threads(bmm):
+    """Two host threads issue products through the C ABI at the same time, each on its own stream
+    and problem (the ctypes calls release the interpreter lock, so the launches' host staging runs
+    concurrently): each thread's products equal run() of the same problem and seed issued alone.
+    One thread takes the fused tensor-core statistics pass, the other the separate norm pass and
+    exact f, so every kernel-parameter staging table is filled from both threads."""
+    import threading
+    A = bmm._abi
+    L = 1536
+    cfgs = (("f32", (520, 8192, 264, 120), 391, dict(fmode=A.F_TC, fused_stats=True)),
+            ("bf16", (776, 12288, 200, 170), 401, dict(fmode=A.F_EXACT, fused_stats=False)))
+    jobs = []
+    for dtype, (m, n, p, K), seed, kw in cfgs:
+        off, _, _, Mt, Nt = _inputs(dtype, m, n, p, K, seed=seed)
+        jobs.append((off, Mt, Nt, kw, [seed + 7 * i for i in range(6)]))
+    got = [[] for _ in jobs]
+    errors = []
+    start = threading.Barrier(len(jobs))
+
+    def work(j):
+        try:
+            off, Mt, Nt, kw, seeds = jobs[j]
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                pr = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+                start.wait()
+                for sd in seeds:
+                    r = bmm.run(pr, "OPL", L, seed=sd, gemm_mode=A.GEMM_BF16, **kw)
+                    got[j].append((r["ck"].clone(), r["idx"].clone(), r["out"].clone()))
+            s.synchronize()
+            bmm.check_status(pr)
+        except Exception as e:  # reported below, on the test's thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(j,)) for j in range(len(jobs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for j, (off, Mt, Nt, kw, seeds) in enumerate(jobs):
+        ref = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=A.GEMM_BF16)
+        assert len(got[j]) == len(seeds)
+        for (ck, idx, out), sd in zip(got[j], seeds):
+            r = bmm.run(ref, "OPL", L, seed=sd, gemm_mode=A.GEMM_BF16, **kw)
+            bmm.check_status(ref)
+            assert torch.equal(ck, r["ck"]) and torch.equal(idx, r["idx"]), (j, sd)
+            assert torch.equal(out, r["out"]), (j, sd)
