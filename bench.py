@@ -408,6 +408,7 @@ def time_gemm_part(P, prob, w, L, r, pk, depth, reps=20):
     m, p = w["m"], w["p"]
     out = torch.empty(m, p, dtype=torch.float32, device=prob.M.device)
     part = lambda pt: A.bmm_apply_part(prob.M, prob.N, prob.B, r["idx"], r["scale"], L, out, False, pt, 0, m, prob.ws)
+    part(A.APPLY_REDUCE)
     part(A.APPLY_GATHER_B)
     part(A.APPLY_GATHER_A)
     for _ in range(3):

@@ -23,7 +23,7 @@ REUSE_STATS = 0x100
 UNIT_COLUMN, UNIT_BLOCK = 0, 1
 GEMM_F64, GEMM_BF16, GEMM_SPLIT_BF16, GEMM_E4M3 = 0, 1, 2, 3
 PURPOSE_MAIN, PURPOSE_PILOT = 0, 1
-APPLY_GATHER_B, APPLY_GATHER_A, APPLY_GEMM = 0, 1, 2
+APPLY_GATHER_B, APPLY_GATHER_A, APPLY_GEMM, APPLY_REDUCE = 0, 1, 2, 3
 TILE_PAIR = 512  # GEMM tile choice: a CTA pair per 256 x 256 tile
 TILE_PAIR_WIDE = 1024  # a CTA pair per 256 x 512 tile
 
@@ -255,7 +255,8 @@ def bmm_apply(M, N, B: Blocks, unit: int, idx, scale, count: int, gemm_mode: int
 
 def bmm_apply_part(M, N, B: Blocks, idx, scale, count: int, out, accumulate: bool, part: int, row0: int, row1: int,
                    ws, stream=None):
-    """One part (APPLY_GATHER_B, APPLY_GATHER_A, APPLY_GEMM) of a column-sampled BF16 bmm_apply."""
+    """One part (APPLY_REDUCE first, then APPLY_GATHER_B / APPLY_GATHER_A, then APPLY_GEMM) of a
+    column-sampled BF16 bmm_apply."""
     _check(load().bmm_apply_part(ctypes.byref(mat(M)), ctypes.byref(mat(N)), ctypes.byref(B), _ptr(idx), _ptr(scale),
                                  count, ctypes.byref(mat(out)), int(bool(accumulate)), part, row0, row1, ws.data_ptr(),
                                  ws.numel(), _stream(stream)), "bmm_apply_part")

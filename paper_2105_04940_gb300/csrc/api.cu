@@ -714,28 +714,31 @@ BMM_API bmm_status bmm_apply(const bmm_mat* M, const bmm_mat* N, const bmm_block
 }
 
 // One part of a column-sampled BF16 bmm_apply, so that a caller can overlap the parts on streams of
-// its own: the gather of N's drawn rows (operand B), the gather of M's drawn columns for a range of
-// output rows (operand A), and the GEMM of a range of output rows.  The operands live in the
+// its own: the reduction of the draws to distinct indices, the gather of N's drawn rows (operand B),
+// the gather of M's drawn columns for a range of output rows (operand A), and the GEMM of a range of
+// output rows.  The operands live in the
 // workspace, as bmm_apply lays them out; every output element is the full-depth dot product of a
 // single bmm_apply, so any split gives the same bits.
 BMM_API bmm_status bmm_apply_part(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, const int32_t* idx,
                                   const double* scale, int64_t count, const bmm_mat* out, int32_t accumulate,
                                   int32_t part, int64_t row0, int64_t row1, void* ws, size_t ws_bytes,
                                   bmm_stream_t stream) {
-    if (part != BMM_APPLY_GATHER_B && part != BMM_APPLY_GATHER_A && part != BMM_APPLY_GEMM) return BMM_ERR_ARG;
+    if (part != BMM_APPLY_GATHER_B && part != BMM_APPLY_GATHER_A && part != BMM_APPLY_GEMM &&
+        part != BMM_APPLY_REDUCE)
+        return BMM_ERR_ARG;
     if (count < 1 || M == nullptr || N == nullptr || M->rows < 1 || N->cols < 1) return BMM_ERR_ARG;
-    if (part != BMM_APPLY_GATHER_B &&
+    if ((part == BMM_APPLY_GATHER_A || part == BMM_APPLY_GEMM) &&
         (row0 < 0 || row1 < row0 || row1 > M->rows || row0 % 128 || (row1 % 128 && row1 != M->rows)))
         return BMM_ERR_SHAPE;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     GemmArgs g;
     bool done = true;
     std::vector<GatherJob> jobs;
-    // the GATHER_B part also reduces the draws to their distinct indices in the workspace; the other
-    // parts, issued after it, use that reduction
+    // the REDUCE part reduces the draws to their distinct indices in the workspace; the other parts,
+    // issued after it, use that reduction
     bmm_status s = apply_prepare(M, N, B, BMM_UNIT_COLUMN, idx, scale, count, BMM_GEMM_BF16, out, accumulate, ws,
-                                 ws_bytes, cs, &g, &done, &jobs, part == BMM_APPLY_GATHER_B);
-    if (s != BMM_OK || done) return s;
+                                 ws_bytes, cs, &g, &done, &jobs, part == BMM_APPLY_REDUCE);
+    if (s != BMM_OK || done || part == BMM_APPLY_REDUCE) return s;
     if (part == BMM_APPLY_GATHER_B) {
         BMM_TRY(launch_gather_grouped(&jobs[1], 1, cs));
         return BMM_OK;

@@ -148,11 +148,12 @@ def overlapped_apply_wanted(M, N, count: int, gemm_mode: int, unit: int) -> bool
 
 def apply_columns(prob: Problem, idx, scale, count: int, gemm_mode: int, out, accumulate: bool = False):
     """CD of Alg. 2's draws (bmm_apply).  For large BF16 products the output rows are split in two:
-    N's rows and the first half's columns of M are gathered on the current stream, the first half's
-    GEMM runs on a high-priority side stream while the second half's columns are gathered, then the
-    second half's GEMM -- all through bmm_apply_part, ordered by events (a fork and a join of the
-    current stream, so the sequence can be captured in a graph).  The result is bit-identical to one
-    bmm_apply: every output element is the same full-depth dot product."""
+    the draws are reduced to distinct indices, N's rows and the first half's columns of M are
+    gathered on the current stream, the first half's GEMM runs on a high-priority side stream while
+    the second half's columns are gathered, then the second half's GEMM -- all through
+    bmm_apply_part, ordered by events (a fork and a join of the current stream, so the sequence can be
+    captured in a graph).  The result is bit-identical to one bmm_apply: every output element is the
+    same full-depth dot product."""
     torch = _torch()
     M, N, B, ws = prob.M, prob.N, prob.B, prob.ws
     if not overlapped_apply_wanted(M, N, count, gemm_mode, A.UNIT_COLUMN):
@@ -163,6 +164,7 @@ def apply_columns(prob: Problem, idx, scale, count: int, gemm_mode: int, out, ac
     m = int(M.shape[0])
     half = min(m, ((m + 1) // 2 + 127) // 128 * 128)
     side.wait_stream(main)
+    A.bmm_apply_part(M, N, B, idx, scale, count, out, accumulate, A.APPLY_REDUCE, 0, 0, ws, main)
     A.bmm_apply_part(M, N, B, idx, scale, count, out, accumulate, A.APPLY_GATHER_B, 0, 0, ws, main)
     done = []
     for lo, hi in ((0, half), (half, m)):
@@ -361,6 +363,7 @@ def run_pipelined(probs: list, c: int, seeds, outs: list, gemm_mode: int = A.GEM
         A.bmm_sample(b["p"], A.UNIT_COLUMN, pr.B, b["ck"], c, seed, sid, b["idx"], b["scale"], pr.ws, side)
         if events is not None:
             mark("design_end", i, side)
+        A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_REDUCE, 0, 0, pr.ws, side)
         A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GATHER_B, 0, 0, pr.ws, side)
         A.bmm_apply_part(pr.M, pr.N, pr.B, b["idx"], b["scale"], c, out, False, A.APPLY_GATHER_A, 0, m, pr.ws, side)
         ev_g = mark("gathers_end", i, side)

@@ -218,15 +218,18 @@ def test_apply_part_refuses_bad_parts_and_row_ranges(lib):
     by = ctypes.byref
     call = lambda part, r0, r1, count=100: lib.bmm_apply_part(by(M), by(N), by(B), fake, fake, count, by(out), 0, part,
                                                              r0, r1, None, 0, None)
-    assert call(3, 0, 128) == _abi.ERR_ARG
+    assert call(4, 0, 128) == _abi.ERR_ARG
     assert call(-1, 0, 128) == _abi.ERR_ARG
     assert call(_abi.APPLY_GEMM, 0, 128, count=0) == _abi.ERR_ARG
     assert call(_abi.APPLY_GATHER_A, 64, 128) == _abi.ERR_SHAPE   # row0 not a multiple of 128
     assert call(_abi.APPLY_GEMM, 0, 100) == _abi.ERR_SHAPE        # row1 neither a multiple of 128 nor m
     assert call(_abi.APPLY_GEMM, 256, 128) == _abi.ERR_SHAPE      # row1 < row0
     assert call(_abi.APPLY_GEMM, 0, 640) == _abi.ERR_SHAPE        # row1 > m
-    # a well-formed request passes these checks and stops at the device (none here) or workspace check
+    # a well-formed request passes these checks and stops at the device (none here) or workspace check;
+    # REDUCE and GATHER_B ignore the rows
     assert call(_abi.APPLY_GEMM, 0, 512) in (_abi.ERR_UNSUPPORTED, _abi.ERR_WORKSPACE)
+    assert call(_abi.APPLY_REDUCE, 64, 100) in (_abi.ERR_UNSUPPORTED, _abi.ERR_WORKSPACE)
+    assert call(_abi.APPLY_GATHER_B, 64, 100) in (_abi.ERR_UNSUPPORTED, _abi.ERR_WORKSPACE)
 
 
 def test_f_tc_query_on_the_host(lib):

@@ -841,8 +841,11 @@ def test_apply_reports_a_bad_index(bmm):
 
 @pytest.mark.parametrize("layout", ["row", "col"])
 def test_apply_parts_equal_one_apply(bmm, layout):
-    """bmm_apply_part's three parts, in any row split (multiples of 128, the last ending at m) and on
-    one or two streams, give bmm_apply's product bit for bit, with and without accumulate."""
+    """bmm_apply_part's parts -- REDUCE, then GATHER_B and GATHER_A in either order, then the GEMMs --
+    in any row split (multiples of 128, the last ending at m) and on one or two streams, give
+    bmm_apply's product bit for bit, with and without accumulate.  The parts run in a workspace of
+    their own whose scratch starts as 0xFF bytes, so nothing left by bmm_apply's own reduction can
+    stand in for REDUCE."""
     m, n, p, K, L = 700, 3000, 300, 40, 900
     off, M, N, Mt, Nt = _problem(m, n, p, K, seed=81, dtype=np.float32, lo=40, hi=110)
     Mt = as_layout(Mt, layout)
@@ -851,18 +854,25 @@ def test_apply_parts_equal_one_apply(bmm, layout):
     A = bmm._abi
     want = torch.empty(m, p, dtype=torch.float32, device=Mt.device)
     A.bmm_apply(Mt, Nt, prob.B, A.UNIT_COLUMN, r["idx"], r["scale"], L, A.GEMM_BF16, want, False, prob.ws)
-    for split in ([0, m], [0, 128, m], [0, 384, 512, m]):
+    parts = bmm.prepare(Mt, Nt, off, max_draws=L, gemm_mode=bmm._abi.GEMM_BF16)
+    for split, b_first in (([0, m], True), ([0, 128, m], False), ([0, 384, 512, m], True)):
+        parts.ws[256:].fill_(255)
         got = torch.full((m, p), float("nan"), dtype=torch.float32, device=Mt.device)
-        A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GATHER_B, 0, 0, prob.ws)
+        A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_REDUCE, 0, 0, parts.ws)
+        if b_first:
+            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GATHER_B, 0, 0, parts.ws)
         for lo, hi in zip(split[:-1], split[1:]):
-            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GATHER_A, lo, hi, prob.ws)
+            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GATHER_A, lo, hi, parts.ws)
+        if not b_first:
+            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GATHER_B, 0, 0, parts.ws)
         for lo, hi in zip(split[:-1], split[1:]):
-            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GEMM, lo, hi, prob.ws)
-        bmm.check_status(prob)
+            A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, got, False, A.APPLY_GEMM, lo, hi, parts.ws)
+        bmm.check_status(parts)
         np.testing.assert_array_equal(host(got), host(want), err_msg=str(split))
     # accumulate: out += CD, rows split across a second stream
     acc = want.clone()
     side = torch.cuda.Stream()
+    A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, acc, True, A.APPLY_REDUCE, 0, 0, prob.ws)
     A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, acc, True, A.APPLY_GATHER_B, 0, 0, prob.ws)
     A.bmm_apply_part(Mt, Nt, prob.B, r["idx"], r["scale"], L, acc, True, A.APPLY_GATHER_A, 0, m, prob.ws)
     side.wait_stream(torch.cuda.current_stream())
