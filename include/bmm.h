@@ -289,12 +289,11 @@ enum {
  * the tensor-core GEMM on streams of its own (eq. 3.3, Alg. 1 step 1(b)); the library creates no
  * stream or event.  The operands live in ws, laid out as bmm_apply lays them out, so all parts of one
  * product take the same ws and arguments.  REDUCE comes first: it reduces the draws to their
- * distinct indices in ws (five small launches, no GEMM-sized shared memory, so they can run beside
- * another product's GEMM).  GATHER_B and every GATHER_A need it complete and may then run in either
- * order; the GEMM of rows [row0, row1) needs GATHER_B and the GATHER_A of those rows complete (same
- * stream, or ordered by the caller's events).  Every
- * output element is the full-depth dot product of a single bmm_apply, so any split of the rows gives
- * the same bits.  row0 and row1: multiples of 128 (row1 may be m), 0 <= row0 <= row1 <= m;
+ * distinct indices with summed scales in ws (five small launches).  GATHER_B and every GATHER_A need
+ * it complete and may then run in either order; the GEMM of rows [row0, row1) needs GATHER_B and the
+ * GATHER_A of those rows complete (same stream, or ordered by the caller's events).  Every output
+ * element is the full-depth dot product of a single bmm_apply, so any split of the rows gives the
+ * same bits.  row0 and row1: multiples of 128 (row1 may be m), 0 <= row0 <= row1 <= m;
  * count >= 1.  Errors as bmm_apply; a bad part is BMM_ERR_ARG, a bad row range BMM_ERR_SHAPE.
  */
 bmm_status bmm_apply_part(const bmm_mat* M, const bmm_mat* N, const bmm_blocks* B, const int32_t* idx,
