@@ -607,9 +607,10 @@ namespace bmm {
 namespace {
 // Checks and gathers of one product of bmm_apply / bmm_apply_batched.  On BMM_OK either *done
 // (nothing left to compute) or *g describes the product's GEMM (BF16 modes; FP64 is launched here).
-// With `defer` (bmm_apply_batched), a column-unit BF16 or split-BF16 product launches nothing: its
-// two gathers are appended to *defer for one grouped launch and its GEMM uses the host extent.
-// Checks the arguments, lays out the workspace and reduces the draws to their distinct indices (each
+// With `defer` (bmm_apply_batched, bmm_apply_part), a column-unit BF16 or split-BF16 product launches
+// no gather: its two gathers are appended to *defer for one grouped launch, and its reduction of the
+// draws to *udefer when given (else it is launched here); the gathers and the GEMM read the number of
+// distinct draws on the device, capped by the host capacity.  Checks the arguments, lays out the workspace and reduces the draws to their distinct indices (each
 // with its multiplicity times its scale: the same sum of outer products, one term per index), then
 // queues the gathers (or runs them) and describes the GEMM.  reduce = false reuses the distinct draws
 // a previous call with the same arguments left in the workspace (the later parts of bmm_apply_part).
