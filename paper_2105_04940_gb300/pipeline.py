@@ -16,6 +16,7 @@ products (the paper's c); for SSM/WU it counts blocks.
 """
 from __future__ import annotations
 
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -66,6 +67,7 @@ class Problem:
 
 
 _UPLOADS: dict = {}
+_UPLOADS_LOCK = threading.Lock()
 
 
 def _upload(arr: np.ndarray, dev):
@@ -76,25 +78,26 @@ def _upload(arr: np.ndarray, dev):
     depend on no work outside the capture."""
     torch = _torch()
     key = (str(dev), arr.dtype.str, arr.tobytes())
-    hit = _UPLOADS.get(key)
-    if hit is None:
-        if len(_UPLOADS) >= 64:
-            _UPLOADS.pop(next(iter(_UPLOADS)))
-        host_t = torch.from_numpy(np.ascontiguousarray(arr))
-        ev = None
-        if dev.type == "cuda":
-            t = host_t.pin_memory().to(dev, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record()
-        else:
-            t = host_t.to(dev)
-        hit = _UPLOADS[key] = (t, ev)
-    t, ev = hit
-    if ev is not None:
-        if ev.query():  # the copy has landed: no stream needs to wait for it again
-            _UPLOADS[key] = (t, None)
-        else:  # issued on some stream and still in flight
-            torch.cuda.current_stream(dev).wait_event(ev)
+    with _UPLOADS_LOCK:  # host threads may prepare problems at the same time
+        hit = _UPLOADS.get(key)
+        if hit is None:
+            if len(_UPLOADS) >= 64:
+                _UPLOADS.pop(next(iter(_UPLOADS)))
+            host_t = torch.from_numpy(np.ascontiguousarray(arr))
+            ev = None
+            if dev.type == "cuda":
+                t = host_t.pin_memory().to(dev, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record()
+            else:
+                t = host_t.to(dev)
+            hit = _UPLOADS[key] = (t, ev)
+        t, ev = hit
+        if ev is not None:
+            if ev.query():  # the copy has landed: no stream needs to wait for it again
+                _UPLOADS[key] = (t, None)
+            else:  # issued on some stream and still in flight
+                torch.cuda.current_stream(dev).wait_event(ev)
     return t
 
 
@@ -126,16 +129,19 @@ def prepare(M, N, offsets, max_draws: int, unit: int = A.UNIT_COLUMN, gemm_mode:
     return Problem(M, N, off, off_dev, B, ws, st)
 
 
-_SIDE: dict = {}
+_SIDE = threading.local()
 
 
 def _side_stream(dev):
-    """A high-priority stream per device for the GEMM halves of the overlapped apply and for the
-    design and gathers of run_pipelined (created once, outside any graph capture that uses it)."""
+    """A high-priority stream per device and host thread for the GEMM halves of the overlapped apply
+    and for the design and gathers of run_pipelined (created once, outside any graph capture that
+    uses it).  Per thread, so that callers on different threads neither wait on each other's work
+    nor enqueue onto a stream that another thread is capturing."""
     torch = _torch()
-    s = _SIDE.get(str(dev))
+    streams = _SIDE.__dict__.setdefault("streams", {})
+    s = streams.get(str(dev))
     if s is None:
-        s = _SIDE[str(dev)] = torch.cuda.Stream(device=dev, priority=-1)
+        s = streams[str(dev)] = torch.cuda.Stream(device=dev, priority=-1)
     return s
 
 

@@ -317,3 +317,40 @@ def test_run_pipelined_refuses_on_the_host():
         P.run_pipelined([object(), object()], 100, [1], [])
     with pytest.raises(ValueError):
         P.run_pipelined([object(), object()], 100, [1], [object()], gemm_mode=P._abi.GEMM_F64)
+
+
+def test_upload_cache_is_safe_across_host_threads(monkeypatch):
+    """pipeline._upload (the per-content cache of block offsets, at most 64 entries) is shared by
+    host threads that prepare problems at the same time: many threads uploading more distinct
+    arrays than the cache holds get each array back intact and no thread fails on an entry that
+    another thread evicted.  The cache's host logic runs here with CPU tensors (the package's
+    refusal to run without a GPU is lifted for this function only)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2105_04940_gb300 import pipeline
+    monkeypatch.setattr(pipeline, "_torch", lambda: torch)
+    monkeypatch.setattr(pipeline, "_UPLOADS", {})
+    dev = torch.device("cpu")
+    errors, bad = [], []
+    start = threading.Barrier(8)
+
+    def work(t):
+        try:
+            start.wait()
+            for k in range(150):
+                arr = np.arange(k, k + 5 + t, dtype=np.int64) * (t + 1)
+                if not np.array_equal(pipeline._upload(arr, dev).numpy(), arr):
+                    bad.append((t, k))
+        except Exception as e:  # reported on the test's thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(t,)) for t in range(8)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors and not bad, (errors[:3], bad[:3])
+    assert len(pipeline._UPLOADS) <= 64
