@@ -112,7 +112,8 @@ def g_equal(K: int) -> np.ndarray:
 
 
 def g_with_fallback(g, a, nk) -> np.ndarray:
-    """All-zero weights fall back to a_k, then to n_k (reading: the paper is silent)."""
+    """Weights of eq. 3.9 / 4.2 / 4.7 for the block sizes; all-zero weights fall back to a_k, then
+    to n_k (reading: the paper is silent on a product whose weights all vanish)."""
     g = np.asarray(g, dtype=np.float64)
     if np.any(g > 0):
         return g

@@ -84,7 +84,8 @@ def entry_variance_blocks(M, N, offsets, pblk, c: int, entries) -> np.ndarray:
 
 def entry_estimate_columns(M, N, offsets, ck, idx, scale, entries):
     """(CD)_hf and the one-sample variance estimate sum_{k: c_k >= 2} c_k/(c_k - 1) sum_t (Z_t - Zbar_k)^2
-    from Alg. 2's draws (block k's draws at positions [sum_{j<k} c_j, sum_{j<=k} c_j)).
+    from Alg. 2's draws (block k's draws at positions [sum_{j<k} c_j, sum_{j<=k} c_j)): the plug-in
+    estimate of eq. 3.7's per-entry variance behind Thm 3.1's normal interval.
     Returns (cd, s2, blocks with c_k = 1)."""
     M = np.asarray(M, dtype=np.float64)
     N = np.asarray(N, dtype=np.float64)
@@ -107,7 +108,8 @@ def entry_estimate_columns(M, N, offsets, ck, idx, scale, entries):
 
 def entry_estimate_blocks(M, N, offsets, kidx, scale, entries):
     """(CD)_hf and c/(c - 1) sum_t (Z_t - Zbar)^2 with Z_t = scale_t (M^{k_t} N_{k_t})_hf, for c
-    i.i.d. block draws (scale_t = 1/(c p_{k_t}))."""
+    i.i.d. block draws (scale_t = 1/(c p_{k_t}), eq. 1.2 / 1.4): the same plug-in variance estimate
+    for block sampling, whose terms are i.i.d. (Lemma 2.1's setting with one segment)."""
     M = np.asarray(M, dtype=np.float64)
     N = np.asarray(N, dtype=np.float64)
     off = np.asarray(offsets, dtype=np.int64)
@@ -141,7 +143,9 @@ REPORT_FIELDS = (
 
 
 def error_report(x, y, p, offsets, ck, a, f, mf, nf, c: int, delta: float, fhat=None) -> dict:
-    """The quantities of REPORT_FIELDS (NaN where f or fhat is missing)."""
+    """The quantities of REPORT_FIELDS (NaN where f or fhat is missing): Remark 2.2's expected squared
+    error, eq. 3.10 and Thm 3.3's bounds (eq. 3.11 / 3.12), Thm 4.2's (eq. 4.3 / 4.4) and, with the
+    pilot's fhat, Thm 4.4's (eq. 4.8 / 4.9)."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     p = np.asarray(p, dtype=np.float64)

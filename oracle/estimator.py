@@ -127,7 +127,8 @@ def pilot_frob_sq(M, N, offsets, p0, c0_per_block: int, seed: int, sid: int):
 
 
 def equal_budget(c_blocks: int, n: int, K: int) -> int:
-    """Outer-product budget matching c whole blocks: L = round(c n / K) (reading R3)."""
+    """Outer-product budget matching c whole blocks of eq. 1.2 / 1.4: L = round(c n / K) (reading R3:
+    Alg. 2 and block sampling compared at the same contraction budget)."""
     return int(np.floor(c_blocks * n / K + 0.5))
 
 
@@ -181,7 +182,8 @@ def run_method(M, N, offsets, method: str, c: int, seed: int, replicate: int = 0
 
 
 def adjoint_columns(M, N, idx, scale, G):
-    """Gradients of <G, CD> with the sample frozen (p treated as constant):
+    """Gradients of <G, CD> with the sample frozen (p treated as constant), CD the estimator of
+    eq. 3.3 (the adjoint is not in the paper; it is the derivative of that sum of outer products):
 
     dM^{(i_t)} += scale_t G N_{(i_t)}^T,  dN_{(i_t)} += scale_t M^{(i_t)T} G.
     """
@@ -197,7 +199,8 @@ def adjoint_columns(M, N, idx, scale, G):
 
 
 def adjoint_blocks(M, N, offsets, kidx, scale, G):
-    """Block-sampling adjoint: dM^{k_t} += scale_t G N_{k_t}^T, dN_{k_t} += scale_t M^{k_t T} G."""
+    """Block-sampling adjoint (the derivative of the eq. 1.2 / 1.4 estimator's sum of block products,
+    sample frozen): dM^{k_t} += scale_t G N_{k_t}^T, dN_{k_t} += scale_t M^{k_t T} G."""
     M = np.asarray(M, dtype=np.float64)
     N = np.asarray(N, dtype=np.float64)
     G = np.asarray(G, dtype=np.float64)

@@ -37,11 +37,15 @@ _PHILOX_W1 = np.uint64(0xBB67AE85)
 
 
 def stream_id(replicate: int, purpose: int) -> int:
+    """Counter words 2-3 of the draws: (replicate << 8) | purpose, so that the main draws of Alg. 1
+    step 1(a) and the pilot draws of Alg. 3 step 1 never share random bits (a convention of this
+    implementation; the paper does not say how draws are made)."""
     return (int(replicate) << 8) | int(purpose)
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
-    """Philox4x32 with 10 rounds on arrays of 32-bit words (held in uint64).
+    """Philox4x32 with 10 rounds on arrays of 32-bit words (held in uint64): the random bits behind
+    Alg. 1 step 1(a)'s draws, from the generator's published definition (Salmon et al., SC'11).
 
     Round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2 (full 64-bit products);
     new counter = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); then the key is
@@ -62,7 +66,7 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
 
 
 def uniform64(seed: int, sid: int, t) -> np.ndarray:
-    """The 64-bit uniform of draw number(s) t: (x1 << 32) | x0."""
+    """The 64-bit uniform of draw number(s) t of Alg. 1 step 1(a): (x1 << 32) | x0."""
     t = np.asarray(t, dtype=np.uint64)
     seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     sid = int(sid) & 0xFFFFFFFFFFFFFFFF
@@ -73,7 +77,8 @@ def uniform64(seed: int, sid: int, t) -> np.ndarray:
 
 
 def fixed_point_weights(p) -> np.ndarray:
-    """W_j = floor(p_j * 2^62) (exact: scaling by a power of two, then floor)."""
+    """W_j = floor(p_j * 2^62) (exact: scaling by a power of two, then floor): the probabilities of
+    eq. 3.8 / 1.2 / 1.4 as integer weights for Alg. 1 step 1(a)'s inverse-CDF draw."""
     p = np.asarray(p, dtype=np.float64)
     if np.any(~np.isfinite(p)) or np.any(p < 0) or np.any(p > 1):
         raise ValueError("probabilities must be finite and in [0, 1]")
@@ -81,14 +86,16 @@ def fixed_point_weights(p) -> np.ndarray:
 
 
 def inverse_cdf(S: np.ndarray, r: np.ndarray) -> np.ndarray:
-    """Smallest j with S_j > floor(r * T / 2^64), T = S[-1] (exact 128-bit product)."""
+    """Smallest j with S_j > floor(r * T / 2^64), T = S[-1] (exact 128-bit product): one draw of
+    Alg. 1 step 1(a), Pr(j) = W_j / T."""
     T = int(S[-1])
     target = np.array([(int(ri) * T) >> 64 for ri in r], dtype=np.uint64)
     return np.searchsorted(S, target, side="right").astype(np.int64)
 
 
 def sample_segments(p, seg_offsets, counts, seed: int, sid: int) -> np.ndarray:
-    """Draw counts[s] indices from segment s of p (global indices into p)."""
+    """Draw counts[s] indices from segment s of p (global indices into p), i.i.d. with replacement
+    inside each segment (Alg. 1 step 1(a); per block for Alg. 2, eq. 3.2)."""
     seg_offsets = np.asarray(seg_offsets, dtype=np.int64)
     counts = np.asarray(counts, dtype=np.int64)
     W = fixed_point_weights(p)

@@ -78,7 +78,7 @@ def block_frob_sq(M, N, offsets) -> np.ndarray:
 
 
 def block_frob_sq_gram(M, N, offsets) -> np.ndarray:
-    """f_k through the trace identity ||A B||_F^2 = <A^T A, B B^T>_F.
+    """f_k = ||M^k N_k||_F^2 (eq. 1.2, eq. 3.9) through the trace identity ||A B||_F^2 = <A^T A, B B^T>_F.
 
     Not in the paper; a second formula for the same quantity, used to pin
     :func:`block_frob_sq` and as the definition the GPU's Gram form follows.
