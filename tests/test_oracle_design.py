@@ -182,3 +182,26 @@ def test_apportion_tracks_real_sizes():
     real = oracle.real_block_sizes(g, c)
     assert np.all(ck >= np.floor(real))
     assert np.all(ck <= (c + K) * g / g.sum() + 1.0)
+
+
+def test_apportion_is_house_monotone():
+    """A divisor method never takes a draw away from a block when the budget grows: c_k(c + 1) >=
+    c_k(c) for every block, one block gaining exactly one, over every budget from K to n (weights with
+    ties, zeros and blocks that reach their cap n_k).  A wrong bisection bound, a remainder handed to
+    blocks that do not grow at the next lambda, or a cap applied after the remainder would break it."""
+    rng = np.random.default_rng(21)
+    for trial in range(6):
+        K = 7
+        nk = rng.integers(1, 9, size=K)
+        g = rng.choice([0.0, 0.5, 1.0, 1.0, 2.5, 7.0], size=K)
+        if trial == 0:
+            g[:] = 1.0  # all tied
+        prev = oracle.apportion(g, nk, K)
+        assert np.all(prev == 1)
+        for c in range(K + 1, int(nk.sum()) + 1):
+            cur = oracle.apportion(g, nk, c)
+            assert cur.sum() == c and np.all(cur <= nk), (trial, c)
+            d = cur - prev
+            assert np.all(d >= 0) and d.sum() == 1, (trial, c, prev, cur)
+            prev = cur
+        assert np.array_equal(prev, nk)
