@@ -241,3 +241,39 @@ def test_repeated_draws_are_one_term_each():
     a = oracle.sampled_product_blocks(M, N, off, kidx, ks)
     b = oracle.sampled_product_blocks(M, N, off, uk, kcnt * uks)
     np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(a).max())
+
+
+def test_block_draws_carry_their_scale():
+    """The block sampler's draws through the estimator of eq. 1.2 / 1.4: (i) when every block but one
+    has M^k N_k = 0, eq. 1.2 puts all mass on that block and any c draws reproduce MN exactly (zero
+    variance); (ii) over many seeds the mean of the sampled products approaches MN (Lemma 2.1) for
+    eq. 1.2 and eq. 1.4 probabilities, within five standard errors of the closed-form variance."""
+    rng = np.random.default_rng(17)
+    m, n, p, K = 6, 12, 5, 3
+    off = np.array([0, 4, 9, 12])
+    M = rng.standard_normal((m, n))
+    N = rng.standard_normal((n, p))
+    M1 = M.copy()
+    M1[:, :4] = 0.0
+    M1[:, 9:] = 0.0  # only block 1 carries the product
+    f1 = oracle.block_frob_sq(M1, N, off)
+    pblk = oracle.p_blk_prodnorm(f1)
+    assert pblk[1] == 1.0
+    for c in (1, 4, 7):
+        idx, scale = oracle.sample_blocks(pblk, c, seed=5, sid=0)
+        assert np.all(idx == 1)
+        np.testing.assert_allclose(oracle.sampled_product_blocks(M1, N, off, idx, scale), M1 @ N, rtol=1e-13,
+                                   atol=1e-13)
+    MN = M @ N
+    f = oracle.block_frob_sq(M, N, off)
+    x, y = oracle.col_row_sq_norms(M, N)
+    st = oracle.block_stats(x, y, off)
+    c, seeds = 3, 3000
+    for pb in (oracle.p_blk_prodnorm(f), oracle.p_blk_normprod(st["mf"], st["nf"])):
+        acc = np.zeros_like(MN)
+        for sd in range(seeds):
+            idx, scale = oracle.sample_blocks(pb, c, seed=sd, sid=0)
+            acc += oracle.sampled_product_blocks(M, N, off, idx, scale)
+        var = oracle.expected_sq_error_blocks(f, pb, c, float(np.sum(MN ** 2)))  # summed over entries
+        err = np.sqrt(np.sum((acc / seeds - MN) ** 2))
+        assert err <= 5.0 * np.sqrt(var / seeds), (err, np.sqrt(var / seeds))
