@@ -354,3 +354,23 @@ def test_upload_cache_is_safe_across_host_threads(monkeypatch):
         th.join()
     assert not errors and not bad, (errors[:3], bad[:3])
     assert len(pipeline._UPLOADS) <= 64
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator and #define of include/bmm.h has the same value in the ctypes binding (name
+    without the BMM_ prefix; the report fields by position in REPORT_FIELDS), so the two cannot
+    drift apart."""
+    from paper_2105_04940_gb300 import _abi
+    text = open(os.path.join(ROOT, "include", "bmm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    found = dict(re.findall(r"\b(BMM_[A-Z0-9_]+)\s*=\s*(0x[0-9a-fA-F]+|\d+)", text))
+    found.update(re.findall(r"#define\s+(BMM_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+|\d+)\b", text))
+    assert len(found) > 50
+    fields = [f.upper() for f in _abi.REPORT_FIELDS]
+    for name, val in sorted(found.items()):
+        v = int(val, 0)
+        short = name[len("BMM_"):]
+        if short.startswith("REPORT_") and short != "REPORT_LEN":
+            assert fields[v] == short[len("REPORT_"):], name
+        else:
+            assert getattr(_abi, short) == v, name
