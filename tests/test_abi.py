@@ -374,3 +374,54 @@ def test_binding_constants_match_the_header():
             assert fields[v] == short[len("REPORT_"):], name
         else:
             assert getattr(_abi, short) == v, name
+
+
+def _c_params(text):
+    """(return type, name, [parameter types]) of every function prototype in a comment-free header."""
+    out = []
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(bmm_\w+)\s*\(([^;{}]*?)\)\s*;", text):
+        ps = [] if params.strip() in ("", "void") else [p.strip() for p in params.split(",")]
+        # drop the parameter name: the last identifier unless the declarator is only a type
+        types = [re.sub(r"\s*\b\w+$", "", p) if re.search(r"[\w\*]\s+\w+$", p) else p for p in ps]
+        norm = lambda t: " ".join(t.replace("*", " * ").split())
+        out.append((norm(ret), name, [norm(t) for t in types]))
+    return out
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Each prototype of include/bmm.h against the argtypes and restype the ctypes binding declares:
+    same arity; integers and floats of the same width and signedness; descriptor structs by pointer;
+    arrays of pointers as pointers to c_void_p; other pointers as c_void_p or a pointer to the same
+    scalar type.  A binding that passed an int64 where the header takes int32 would fail here."""
+    import ctypes
+
+    from paper_2105_04940_gb300 import _abi
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "bmm.h")).read(), flags=re.S)
+    protos = _c_params(text)
+    assert sorted(name for _, name, _ in protos) == sorted(_abi.EXPORTED)
+    scalars = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+               "size_t": ctypes.c_size_t, "double": ctypes.c_double, "float": ctypes.c_float,
+               "bmm_status": ctypes.c_int32}
+    structs = {"bmm_mat": _abi.Mat, "bmm_blocks": _abi.Blocks, "bmm_stats": _abi.Stats}
+
+    def ok(ctype, t):
+        base = t.replace("const", "").replace("*", "").split()
+        stars = t.count("*")
+        if t == "bmm_stream_t" or (stars == 1 and base == ["void"]):
+            return ctype is ctypes.c_void_p
+        if stars == 0:
+            return ctype is scalars[base[0]]
+        if stars >= 2:
+            return ctype is ctypes.POINTER(ctypes.c_void_p)
+        if base[0] in structs:
+            return ctype is ctypes.POINTER(structs[base[0]])
+        return ctype is ctypes.c_void_p or ctype is ctypes.POINTER(scalars[base[0]])
+
+    for ret, name, types in protos:
+        fn = getattr(lib, name)
+        assert len(fn.argtypes) == len(types), name
+        for i, (ct, t) in enumerate(zip(fn.argtypes, types)):
+            assert ok(ct, t), (name, i, t, ct)
+        want = {"bmm_status": ctypes.c_int32, "size_t": ctypes.c_size_t, "const char *": ctypes.c_char_p,
+                "uint64_t": ctypes.c_uint64, "void": None}[ret]
+        assert fn.restype is want, (name, ret, fn.restype)
