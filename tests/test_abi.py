@@ -425,3 +425,36 @@ def test_binding_signatures_match_the_header(lib):
         want = {"bmm_status": ctypes.c_int32, "size_t": ctypes.c_size_t, "const char *": ctypes.c_char_p,
                 "uint64_t": ctypes.c_uint64, "void": None}[ret]
         assert fn.restype is want, (name, ret, fn.restype)
+
+
+def test_descriptor_structs_match_the_header(tmp_path):
+    """bmm_mat, bmm_blocks and bmm_stats as a C compiler lays them out from include/bmm.h (sizes and
+    every field's offset, from a small program built with the host compiler) against the binding's
+    ctypes structures."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2105_04940_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    layouts = {"bmm_mat": _abi.Mat, "bmm_blocks": _abi.Blocks, "bmm_stats": _abi.Stats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "bmm.h"', "int main(void) {"]
+    for cname, cls in layouts.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, cls in layouts.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
