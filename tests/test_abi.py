@@ -458,3 +458,17 @@ def test_descriptor_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def test_header_stands_alone_in_c_and_cpp(tmp_path):
+    """include/bmm.h compiles on its own, as C and as C++ (C linkage: the exported names are the
+    plain function names), with warnings treated as errors."""
+    import shutil
+    import subprocess
+    for lang, comp in (("c", shutil.which("gcc")), ("c++", shutil.which("g++"))):
+        if comp is None:
+            pytest.skip("no host compiler")
+        src = tmp_path / ("h." + ("c" if lang == "c" else "cpp"))
+        src.write_text('#include "bmm.h"\nint main(void) { return (int)sizeof(bmm_mat) == 0; }\n')
+        subprocess.run([comp, "-x", lang, "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-fsyntax-only", str(src)], check=True)
